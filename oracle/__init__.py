@@ -1,0 +1,154 @@
+"""CPU oracle for thresholded triadic queries (FOLTY, arXiv 2507.17215).
+
+TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` import this package. The CUDA library never does, and this package
+never imports the library.
+
+``folty_oracle.c`` is the plain C definition (see its header for the paper passages it
+follows); this module compiles it with gcc and wraps it with ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "folty_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, OpenMP)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", _SRC,
+                    "-o", tmp], check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    P = ctypes.c_void_p
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.oracle_graph_new.restype = P
+    lib.oracle_graph_new.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i64p]
+    lib.oracle_graph_free.argtypes = [P]
+    lib.oracle_kept_edges.restype = ctypes.c_int64
+    lib.oracle_kept_edges.argtypes = [P]
+    lib.oracle_degree.restype = ctypes.c_int32
+    lib.oracle_degree.argtypes = [P, ctypes.c_int32]
+    lib.oracle_threads.restype = ctypes.c_int
+    lib.oracle_counts.restype = ctypes.c_int
+    lib.oracle_counts.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                  i64p, i32p, i32p]
+    lib.oracle_query.restype = ctypes.c_int64
+    lib.oracle_query.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p, i32p, i32p, i32p,
+                                 i32p, i32p, i64p]
+    _lib = lib
+    return lib
+
+
+def threads() -> int:
+    return int(_load().oracle_threads())
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+class OracleGraph:
+    """A temporal graph held by the C oracle. Arrays are kept alive by this object."""
+
+    def __init__(self, n: int, src, dst, t):
+        self._lib = _load()
+        self.n = int(n)
+        self.src = np.ascontiguousarray(src, dtype=np.int32)
+        self.dst = np.ascontiguousarray(dst, dtype=np.int32)
+        self.t = np.ascontiguousarray(t, dtype=np.int64)
+        self.m = int(self.src.shape[0])
+        h = self._lib.oracle_graph_new(self.n, self.m, _ptr(self.src, ctypes.c_int32),
+                                       _ptr(self.dst, ctypes.c_int32),
+                                       _ptr(self.t, ctypes.c_int64))
+        if not h:
+            raise ValueError("oracle: invalid temporal graph (ids outside [0, n) or t < 0)")
+        self._h = h
+
+    @classmethod
+    def of(cls, g) -> "OracleGraph":
+        return cls(g.n, g.src, g.dst, g.t)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.oracle_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def degree(self, u: int) -> int:
+        return int(self._lib.oracle_degree(self._h, int(u)))
+
+    def degrees(self) -> np.ndarray:
+        return np.array([self.degree(u) for u in range(self.n)], dtype=np.int64)
+
+    def counts(self, delta: int, dir: int = 0, brute: bool = False,
+               idx: Optional[Sequence[int]] = None):
+        """(c_e, |N(x) cap N(y)|) for the given input edges (all when idx is None)."""
+        if idx is None:
+            k = self.m
+            ip = None
+        else:
+            idx_a = np.ascontiguousarray(idx, dtype=np.int64)
+            k = idx_a.shape[0]
+            ip = _ptr(idx_a, ctypes.c_int64)
+        out = np.zeros(k, dtype=np.int32)
+        com = np.zeros(k, dtype=np.int32)
+        rc = self._lib.oracle_counts(self._h, int(delta), int(dir), int(bool(brute)), k, ip,
+                                     _ptr(out, ctypes.c_int32), _ptr(com, ctypes.c_int32))
+        if rc != 0:
+            raise ValueError("oracle: bad arguments")
+        return out, com
+
+    def query(self, q, brute: bool = False) -> Dict[str, np.ndarray]:
+        """The full query: per-edge counts (input order) and the sorted pair list."""
+        m = self.m
+        counts = np.zeros(m, dtype=np.int32)
+        common = np.zeros(m, dtype=np.int32)
+        cap = max(m, 1)
+        pu = np.zeros(cap, dtype=np.int32)
+        pv = np.zeros(cap, dtype=np.int32)
+        pc = np.zeros(cap, dtype=np.int32)
+        pn = np.zeros(cap, dtype=np.int32)
+        ncert = np.zeros(1, dtype=np.int64)
+        i32 = ctypes.c_int32
+        k = self._lib.oracle_query(self._h, int(q.delta), int(q.rho_num), int(q.rho_den),
+                                   int(q.quant), int(q.dir), int(q.universe), int(bool(brute)),
+                                   _ptr(counts, i32), _ptr(common, i32), _ptr(pu, i32),
+                                   _ptr(pv, i32), _ptr(pc, i32), _ptr(pn, i32),
+                                   _ptr(ncert, ctypes.c_int64))
+        if k < 0:
+            raise ValueError("oracle: bad query parameters")
+        return {"u": pu[:k].copy(), "v": pv[:k].copy(), "count": pc[:k].copy(),
+                "ncert": pn[:k].copy(), "edge_count": counts, "common": common,
+                "n_cert_edges": int(ncert[0])}

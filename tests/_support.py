@@ -1,0 +1,130 @@
+"""Helpers shared by the tests: golden-fixture parser and an independent brute force.
+
+The brute force below is written straight from the definitions (Section 2 of the
+paper, "How to solve FOL queries", and Definition 1.1) and deliberately shares nothing
+with the C oracle: it never builds N(u) lists or E_{x,y} lists, it loops over every
+vertex triple and every pair of temporal edges. It is only usable on tiny graphs.
+"""
+from __future__ import annotations
+
+import glob
+import os
+from typing import Dict, List, Tuple
+
+import numpy as np
+
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def parse_fixture(path: str):
+    n = None
+    edges: List[Tuple[int, int, int]] = []
+    cases = []
+    for raw in open(path):
+        line = raw.split("#", 1)[0].strip()
+        if not line:
+            continue
+        tok = line.split()
+        if tok[0] == "n":
+            n = int(tok[1])
+        elif tok[0] == "edge":
+            edges.append((int(tok[1]), int(tok[2]), int(tok[3])))
+        elif tok[0] == "query":
+            d, num, den, quant, dr, uni = map(int, tok[1:7])
+            cases.append({"q": W.Query(delta=d, rho_num=num, rho_den=den, quant=quant, dir=dr,
+                                       universe=uni), "counts": None, "pairs": []})
+        elif tok[0] == "counts":
+            cases[-1]["counts"] = np.array([int(x) for x in tok[1:]], dtype=np.int32)
+        elif tok[0] == "pair":
+            cases[-1]["pairs"].append(tuple(int(x) for x in tok[1:5]))
+        else:
+            raise ValueError(f"{path}: bad line {raw!r}")
+    e = np.array(edges, dtype=np.int64).reshape(-1, 3)
+    g = W.TemporalGraph(n, e[:, 0].astype(np.int32).copy(), e[:, 1].astype(np.int32).copy(),
+                        e[:, 2].astype(np.int64).copy())
+    return g, cases
+
+
+def golden_files():
+    return sorted(glob.glob(os.path.join(GOLDEN, "*.txt")))
+
+
+def _matches(a: int, b: int, p: int, w: int, dir: int) -> bool:
+    if dir == W.DIR_OUT:
+        return a == p and b == w
+    if dir == W.DIR_IN:
+        return a == w and b == p
+    return (a == p and b == w) or (a == w and b == p)
+
+
+def brute_counts(g: W.TemporalGraph, delta: int, dir: int) -> np.ndarray:
+    """c_e for every input edge, by trying every witness vertex and every edge pair."""
+    E = list(zip(g.src.tolist(), g.dst.tolist(), g.t.tolist()))
+    out = np.zeros(len(E), dtype=np.int32)
+    for i, (x, y, t) in enumerate(E):
+        if x == y:
+            continue
+        c = 0
+        for w in range(g.n):
+            if w == x or w == y:
+                continue
+            A = [t2 for (a, b, t2) in E if _matches(a, b, x, w, dir)]
+            B = [t3 for (a, b, t3) in E if _matches(a, b, y, w, dir)]
+            if any(t <= t2 <= t3 <= t + delta for t2 in A for t3 in B):
+                c += 1
+        out[i] = c
+    return out
+
+
+def brute_neighbours(g: W.TemporalGraph):
+    nb = [set() for _ in range(g.n)]
+    for x, y in zip(g.src.tolist(), g.dst.tolist()):
+        if x != y:
+            nb[x].add(y)
+            nb[y].add(x)
+    return nb
+
+
+def brute_pairs(g: W.TemporalGraph, q: W.Query, counts: np.ndarray):
+    """Sorted (x, y, max c, #certificates) from per-edge counts, by the definitions."""
+    nb = brute_neighbours(g)
+    best: Dict[Tuple[int, int], int] = {}
+    ncert: Dict[Tuple[int, int], int] = {}
+    for i, (x, y) in enumerate(zip(g.src.tolist(), g.dst.tolist())):
+        if x == y:
+            continue
+        c = int(counts[i])
+        if q.universe == W.U_HEAD:
+            U = len(nb[x])
+        elif q.universe == W.U_TAIL:
+            U = len(nb[y])
+        else:
+            U = len(nb[x] & nb[y])
+        if q.quant == W.Q_EXISTS:
+            sat = c >= 1
+        else:
+            sat = c >= 1 and c * q.rho_den >= q.rho_num * U
+        key = (x, y)
+        best[key] = max(best.get(key, 0), c)
+        ncert[key] = ncert.get(key, 0) + int(sat)
+    return sorted((k[0], k[1], best[k], ncert[k]) for k in best if ncert[k] > 0)
+
+
+def pairs_of(res) -> List[Tuple[int, int, int, int]]:
+    return list(zip(np.asarray(res["u"]).tolist(), np.asarray(res["v"]).tolist(),
+                    np.asarray(res["count"]).tolist(), np.asarray(res["ncert"]).tolist()))
+
+
+def complete_graph(k: int, t: int = 0) -> W.TemporalGraph:
+    """Both directions of every pair of k vertices, all at time t."""
+    src, dst = [], []
+    for a in range(k):
+        for b in range(k):
+            if a != b:
+                src.append(a)
+                dst.append(b)
+    m = len(src)
+    return W.TemporalGraph(k, np.array(src, np.int32), np.array(dst, np.int32),
+                           np.full(m, t, np.int64))
