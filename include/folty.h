@@ -1,0 +1,182 @@
+/*
+ * folty.h -- C ABI of the GB300 library for thresholded first-order-logic triadic
+ * queries "exists u, exists v, forall_rho w" on temporal networks (FOLTY,
+ * arXiv 2507.17215).
+ *
+ * Problem (paper Section 1.2, Definitions 1.1 and 1.2; Section 2):
+ *   A temporal graph is a list of directed triples (u, v, t): u the head, v the
+ *   destination, t the timestamp; parallel edges in both directions are allowed.
+ *   G_S is the static graph without directions, parallel edges and self-loops, N(u)
+ *   the neighbourhood of u in G_S, E_{x,y} the time-sorted list of edges x -> y.
+ *   A temporal edge e = (x, y, t) forms a delta-temporal triangle with w when there are
+ *   edges (x, w, t2) and (y, w, t3) with t <= t2 <= t3 <= t + delta ("out" motif;
+ *   "in" uses (w, x, t2), (w, y, t3); "either" accepts both directions per edge).
+ *   c_e counts the w in N(x) cap N(y) that do (each w at most once). e is a
+ *   certificate of the query when c_e >= 1 and, for forall_rho, c_e * rho_den >=
+ *   rho_num * U(e), U(e) being |N(x)|, |N(y)| or |N(x) cap N(y)| (Algorithm 5,
+ *   Algorithm 6, Insights). An ordered pair (x, y) is a solution when at least one
+ *   edge x -> y certifies it.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a folty_status and never aborts; on failure a thread-local
+ *     message is available from folty_last_error().
+ *   - "stream" is a cudaStream_t (NULL = the legacy default stream). Device work is
+ *     ordered on it; calls that return host data synchronise it first.
+ *   - Device memory is taken from the caller's folty_allocator when one is given
+ *     (e.g. PyTorch's caching allocator), otherwise with cudaMallocAsync on the stream.
+ *   - Limits: 0 <= n < 2^30, 0 <= m < 2^31, 0 <= t < 2^62, 0 <= delta < 2^62.
+ */
+#ifndef FOLTY_H
+#define FOLTY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct folty_graph folty_graph; /* opaque; owns all of its device memory */
+
+typedef enum {
+    FOLTY_OK = 0,
+    FOLTY_EINVAL = 1,   /* bad argument: ids outside [0,n), t or delta out of range, ... */
+    FOLTY_ENOMEM = 2,   /* the allocator returned NULL (nothing leaks)                 */
+    FOLTY_ECUDA = 3,    /* a CUDA call or kernel failed                                 */
+    FOLTY_ESTATE = 4,   /* call made in the wrong state (query before preprocess)       */
+    FOLTY_ETIMEOUT = 5  /* a bounded device-side wait ran out                           */
+} folty_status;
+
+/* Device allocator supplied by the caller. alloc returns a device pointer usable on
+ * "stream" (or NULL when out of memory); free releases it in stream order. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, void *stream, void *ctx);
+    void *ctx;
+} folty_allocator;
+
+enum { FOLTY_Q_EXISTS = 0, FOLTY_Q_FORALL_T = 1 };                    /* quantifier on w */
+enum { FOLTY_DIR_OUT = 0, FOLTY_DIR_IN = 1, FOLTY_DIR_EITHER = 2 };   /* witness edges   */
+enum { FOLTY_U_HEAD = 0, FOLTY_U_TAIL = 1, FOLTY_U_COMMON = 2 };      /* universe of w   */
+
+/* One query (Definition 1.1). rho = rho_num / rho_den with 0 <= rho_num <= rho_den,
+ * rho_den > 0; compared exactly in integers. want_edge_counts != 0 also returns c_e for
+ * every input edge. */
+typedef struct {
+    int64_t delta;
+    uint32_t rho_num, rho_den;
+    uint8_t quant, dir, universe, want_edge_counts;
+} folty_query_params;
+
+/* Result of one query. The struct belongs to the caller; the arrays it points to are
+ * host memory owned by the library and released by folty_free(result).
+ *   u, v, count, ncert: n_pairs solutions sorted by (u, v) ascending; count = max c_e
+ *                       over E_{u,v}; ncert = number of certificates on E_{u,v}.
+ *   n_cert_edges:       total number of certificates.
+ *   edge_count:         c_e for input edge i (self-loops get 0), length m, or NULL
+ *                       when not requested. */
+typedef struct {
+    uint64_t tag; /* written by the library; lets folty_free tell a result from a graph */
+    int64_t n_pairs;
+    int32_t *u, *v, *count, *ncert;
+    int64_t n_cert_edges;
+    int64_t m;
+    int32_t *edge_count;
+} folty_result;
+
+/* Sizes and derived figures of a preprocessed graph. */
+typedef struct {
+    int32_t n;
+    int64_t m;              /* input edges                                     */
+    int64_t m_kept;         /* without self-loops                              */
+    int64_t static_edges;   /* |E(G_S)|                                        */
+    int32_t max_degree;     /* max |N(u)|                                      */
+    int32_t degeneracy;     /* alpha = max core number (Definition 2.1)        */
+    int32_t max_out_degree; /* max |N+(u)| in the oriented graph (<= alpha)    */
+    int32_t peel_rounds;    /* rounds of the parallel peeling                  */
+    int64_t triangles;      /* triangles of G_S                                */
+    int64_t probes;         /* sum over triangles of the sizes of its 3 edges' */
+                            /* temporal lists (= (edge, witness) pairs)        */
+    int32_t sigma_max;      /* max multiplicity sigma(u,v) of a static edge    */
+    int32_t time_sorted;    /* 1 if the input arrived sorted by t              */
+    int64_t device_bytes;   /* device memory held by the graph                 */
+} folty_graph_info;
+
+/* Model traffic of one query's passes, in bytes (see the per-role formula in the design
+ * notes): enumeration (done once at preprocess), window probes, threshold. */
+typedef struct {
+    int64_t enum_bytes;
+    int64_t probe_bytes;
+    int64_t threshold_bytes;
+} folty_traffic_model;
+
+/* Section 1.2 / Section 2 input. Copies the m edges (src[i] -> dst[i] at t[i]) into
+ * device memory owned by the new graph and validates them. The three arrays may be
+ * host or device pointers (detected per pointer); they stay owned by the caller and
+ * are not referenced after the call returns. alloc may be NULL. On success *out
+ * receives a graph in the "loaded" state. Errors: FOLTY_EINVAL (n, m out of range, an
+ * id outside [0, n), t outside [0, 2^62)), FOLTY_ENOMEM, FOLTY_ECUDA. */
+folty_status folty_load_temporal_graph(int32_t n, int64_t m, const int32_t *src,
+                                       const int32_t *dst, const int64_t *t,
+                                       const folty_allocator *alloc, void *stream,
+                                       folty_graph **out);
+
+/* Section 2 preprocessing: drops self-loops, sorts edges into E_{x,y} lists, builds
+ * G_S, its degeneracy order (Definition 2.1, by parallel peeling) and orientation,
+ * and lists every triangle of G_S once. Moves the graph to the "preprocessed" state.
+ * Errors: FOLTY_ESTATE (already preprocessed), FOLTY_ENOMEM, FOLTY_ECUDA,
+ * FOLTY_ETIMEOUT (a device-side barrier of the peeling kernel gave up). */
+folty_status folty_preprocess(folty_graph *g, void *stream);
+
+/* One query (Algorithm 6 semantics): window probes for every (edge, witness) pair,
+ * counts c_e, threshold, solution pairs. Fills *out (host arrays, library-owned).
+ * Errors: FOLTY_ESTATE (not preprocessed), FOLTY_EINVAL (bad parameters),
+ * FOLTY_ENOMEM, FOLTY_ECUDA. */
+folty_status folty_query(folty_graph *g, const folty_query_params *q, folty_result *out,
+                         void *stream);
+
+/* nq queries answered together (outs[i] for qs[i]); results equal those of nq
+ * folty_query calls. One probe pass per direction variant present serves every delta
+ * of that variant: for a fixed (edge, witness) the searched t2, t3 do not depend on
+ * delta (Theorem 3.1), so the gap t3 - t is computed once and binned by delta. */
+folty_status folty_query_batch(folty_graph *g, const folty_query_params *qs, int32_t nq,
+                               folty_result *outs, void *stream);
+
+/* Frees a folty_graph* (all of its device memory) or the library-owned arrays of a
+ * folty_result* (told apart by their tag). NULL and already-freed results are
+ * ignored. Synchronises nothing; do not free a graph with work still in flight. */
+void folty_free(void *obj);
+
+/* Thread-local message describing the last failure on this thread ("" if none). */
+const char *folty_last_error(void);
+
+/* Sizes of a preprocessed graph. Errors: FOLTY_EINVAL (NULL), FOLTY_ESTATE. */
+folty_status folty_graph_get_info(const folty_graph *g, folty_graph_info *info);
+
+/* Model traffic for one query with direction variant dir (computed on the device
+ * from the triangle list; synchronises the stream). */
+folty_status folty_graph_traffic_model(folty_graph *g, int32_t dir,
+                                       folty_traffic_model *out, void *stream);
+
+/* Number of kernels this library has launched in this process (all threads). */
+uint64_t folty_kernel_launches(void);
+
+/* Device time of the window-probe kernels (a query's dominant kernel), measured with
+ * CUDA events recorded on the launching stream around every probe launch while
+ * profiling is on. Totals are process-wide. */
+typedef struct {
+    int64_t probe_launches;
+    double probe_ms;
+} folty_profile;
+
+/* Turns probe timing on (on != 0) or off and resets the totals. */
+void folty_profile_enable(int32_t on);
+
+/* Copies the totals. Errors: FOLTY_EINVAL (NULL). */
+folty_status folty_profile_read(folty_profile *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FOLTY_H */

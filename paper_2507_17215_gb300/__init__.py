@@ -1,0 +1,310 @@
+"""Python binding of ``libfolty.so`` (include/folty.h): thresholded triadic queries
+"exists u, exists v, forall_rho w" on temporal graphs, computed by CUDA kernels on one
+GB300 (FOLTY, arXiv 2507.17215).
+
+The module-level functions carry the C names and only marshal arguments; every step
+of loading, preprocessing and querying runs in the library's kernels. PyTorch supplies
+device memory (its caching allocator, through the C allocator callbacks) and streams.
+There is no fallback: importing fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import (CFUNCTYPE, POINTER, Structure, c_char_p, c_int32, c_int64, c_size_t,
+                    c_uint8, c_uint32, c_uint64, c_void_p)
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfolty.so")
+
+FOLTY_OK, FOLTY_EINVAL, FOLTY_ENOMEM, FOLTY_ECUDA, FOLTY_ESTATE, FOLTY_ETIMEOUT = range(6)
+STATUS_NAMES = {0: "FOLTY_OK", 1: "FOLTY_EINVAL", 2: "FOLTY_ENOMEM", 3: "FOLTY_ECUDA",
+                4: "FOLTY_ESTATE", 5: "FOLTY_ETIMEOUT"}
+Q_EXISTS, Q_FORALL_T = 0, 1
+DIR_OUT, DIR_IN, DIR_EITHER = 0, 1, 2
+U_HEAD, U_TAIL, U_COMMON = 0, 1, 2
+
+# the exported C symbols (folty.h), checked by the test suite
+EXPORTED = ["folty_load_temporal_graph", "folty_preprocess", "folty_query", "folty_query_batch",
+            "folty_free", "folty_last_error", "folty_graph_get_info", "folty_graph_traffic_model",
+            "folty_kernel_launches", "folty_profile_enable", "folty_profile_read"]
+
+
+class FoltyError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+# ------------------------------------------------------------------ C structs
+
+ALLOC_FN = CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
+FREE_FN = CFUNCTYPE(None, c_void_p, c_void_p, c_void_p)
+
+
+class folty_allocator(Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", c_void_p)]
+
+
+class folty_query_params(Structure):
+    _fields_ = [("delta", c_int64), ("rho_num", c_uint32), ("rho_den", c_uint32),
+                ("quant", c_uint8), ("dir", c_uint8), ("universe", c_uint8),
+                ("want_edge_counts", c_uint8)]
+
+
+class folty_result(Structure):
+    _fields_ = [("tag", c_uint64), ("n_pairs", c_int64), ("u", POINTER(c_int32)),
+                ("v", POINTER(c_int32)), ("count", POINTER(c_int32)), ("ncert", POINTER(c_int32)),
+                ("n_cert_edges", c_int64), ("m", c_int64), ("edge_count", POINTER(c_int32))]
+
+
+class folty_graph_info(Structure):
+    _fields_ = [("n", c_int32), ("m", c_int64), ("m_kept", c_int64), ("static_edges", c_int64),
+                ("max_degree", c_int32), ("degeneracy", c_int32), ("max_out_degree", c_int32),
+                ("peel_rounds", c_int32), ("triangles", c_int64), ("probes", c_int64),
+                ("sigma_max", c_int32), ("time_sorted", c_int32), ("device_bytes", c_int64)]
+
+
+class folty_profile(Structure):
+    _fields_ = [("probe_launches", c_int64), ("probe_ms", ctypes.c_double)]
+
+
+class folty_traffic_model(Structure):
+    _fields_ = [("enum_bytes", c_int64), ("probe_bytes", c_int64), ("threshold_bytes", c_int64)]
+
+
+# ------------------------------------------------------------------ library
+
+def _load_library():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it first (python -c 'import "
+                          "__graft_entry__ as g; g.build()'). There is no CPU fallback.")
+    lib = ctypes.CDLL(LIB_PATH)
+    G = c_void_p
+    lib.folty_load_temporal_graph.restype = c_int32
+    lib.folty_load_temporal_graph.argtypes = [c_int32, c_int64, c_void_p, c_void_p, c_void_p,
+                                              POINTER(folty_allocator), c_void_p, POINTER(c_void_p)]
+    lib.folty_preprocess.restype = c_int32
+    lib.folty_preprocess.argtypes = [G, c_void_p]
+    lib.folty_query.restype = c_int32
+    lib.folty_query.argtypes = [G, POINTER(folty_query_params), POINTER(folty_result), c_void_p]
+    lib.folty_query_batch.restype = c_int32
+    lib.folty_query_batch.argtypes = [G, POINTER(folty_query_params), c_int32, POINTER(folty_result),
+                                      c_void_p]
+    lib.folty_free.restype = None
+    lib.folty_free.argtypes = [c_void_p]
+    lib.folty_last_error.restype = c_char_p
+    lib.folty_last_error.argtypes = []
+    lib.folty_graph_get_info.restype = c_int32
+    lib.folty_graph_get_info.argtypes = [G, POINTER(folty_graph_info)]
+    lib.folty_graph_traffic_model.restype = c_int32
+    lib.folty_graph_traffic_model.argtypes = [G, c_int32, POINTER(folty_traffic_model), c_void_p]
+    lib.folty_kernel_launches.restype = c_uint64
+    lib.folty_kernel_launches.argtypes = []
+    lib.folty_profile_enable.restype = None
+    lib.folty_profile_enable.argtypes = [c_int32]
+    lib.folty_profile_read.restype = c_int32
+    lib.folty_profile_read.argtypes = [POINTER(folty_profile)]
+    return lib
+
+
+lib = _load_library()
+
+
+def _check(status: int):
+    if status != FOLTY_OK:
+        raise FoltyError(status, lib.folty_last_error().decode())
+
+
+# ------------------------------------------------------------------ torch plumbing
+
+def _torch():
+    import torch
+    return torch
+
+
+@ALLOC_FN
+def _torch_alloc(nbytes, stream, ctx):
+    torch = _torch()
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), device=torch.cuda.current_device(),
+                                                  stream=int(stream or 0))
+    except Exception:  # out of memory -> NULL -> FOLTY_ENOMEM
+        return None
+
+
+@FREE_FN
+def _torch_free(ptr, stream, ctx):
+    _torch().cuda.caching_allocator_delete(int(ptr))
+
+
+TORCH_ALLOCATOR = folty_allocator(_torch_alloc, _torch_free, None)
+
+
+def current_stream() -> int:
+    return int(_torch().cuda.current_stream().cuda_stream)
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or torch tensor (host or device), contiguous."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return int(a.data_ptr())
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _dtype_ok(a, np_dtype, torch_name):
+    if isinstance(a, np.ndarray):
+        return a.dtype == np_dtype
+    return str(a.dtype) == f"torch.{torch_name}"
+
+
+# ------------------------------------------------------------------ C-named functions
+
+def folty_load_temporal_graph(n: int, src, dst, t, allocator: Optional[str] = "torch",
+                              stream: Optional[int] = None) -> int:
+    """Returns a graph handle. src, dst (int32) and t (int64) may be host numpy arrays or
+    host/device torch tensors. allocator: "torch" (caching allocator) or None
+    (cudaMallocAsync inside the library)."""
+    m = int(src.shape[0])
+    if int(dst.shape[0]) != m or int(t.shape[0]) != m:
+        raise ValueError("src, dst and t must have the same length")
+    if not (_dtype_ok(src, np.int32, "int32") and _dtype_ok(dst, np.int32, "int32")
+            and _dtype_ok(t, np.int64, "int64")):
+        raise TypeError("src/dst must be int32 and t int64")
+    out = c_void_p()
+    alloc = ctypes.byref(TORCH_ALLOCATOR) if allocator == "torch" else None
+    s = current_stream() if stream is None else stream
+    _check(lib.folty_load_temporal_graph(int(n), m, _ptr(src) if m else None,
+                                         _ptr(dst) if m else None, _ptr(t) if m else None,
+                                         alloc, s, ctypes.byref(out)))
+    return out.value
+
+
+def folty_preprocess(g: int, stream: Optional[int] = None) -> None:
+    _check(lib.folty_preprocess(g, current_stream() if stream is None else stream))
+
+
+def _params(q) -> folty_query_params:
+    return folty_query_params(int(q.delta), int(q.rho_num), int(q.rho_den), int(q.quant),
+                              int(q.dir), int(q.universe), int(bool(getattr(q, "want_edge_counts", 0))))
+
+
+def _take_result(r: folty_result) -> Dict[str, object]:
+    k = int(r.n_pairs)
+    out: Dict[str, object] = {}
+    for name in ("u", "v", "count", "ncert"):
+        p = getattr(r, name)
+        out[name] = (np.ctypeslib.as_array(p, shape=(k,)).copy() if k > 0
+                     else np.zeros(0, dtype=np.int32))
+    out["n_cert_edges"] = int(r.n_cert_edges)
+    if r.edge_count:
+        out["edge_count"] = np.ctypeslib.as_array(r.edge_count, shape=(int(r.m),)).copy()
+    else:
+        out["edge_count"] = None
+    lib.folty_free(ctypes.byref(r))
+    return out
+
+
+def folty_query(g: int, q, stream: Optional[int] = None) -> Dict[str, object]:
+    p = _params(q)
+    r = folty_result()
+    _check(lib.folty_query(g, ctypes.byref(p), ctypes.byref(r),
+                           current_stream() if stream is None else stream))
+    return _take_result(r)
+
+
+def folty_query_batch(g: int, qs: Sequence, stream: Optional[int] = None) -> List[Dict[str, object]]:
+    nq = len(qs)
+    ps = (folty_query_params * max(nq, 1))(*[_params(q) for q in qs])
+    rs = (folty_result * max(nq, 1))()
+    _check(lib.folty_query_batch(g, ps, nq, rs, current_stream() if stream is None else stream))
+    return [_take_result(rs[i]) for i in range(nq)]
+
+
+def folty_free(obj: int) -> None:
+    lib.folty_free(obj)
+
+
+def folty_last_error() -> str:
+    return lib.folty_last_error().decode()
+
+
+def folty_graph_get_info(g: int) -> Dict[str, int]:
+    info = folty_graph_info()
+    _check(lib.folty_graph_get_info(g, ctypes.byref(info)))
+    return {name: int(getattr(info, name)) for name, _ in folty_graph_info._fields_}
+
+
+def folty_graph_traffic_model(g: int, dir: int = DIR_OUT, stream: Optional[int] = None) -> Dict[str, int]:
+    tm = folty_traffic_model()
+    _check(lib.folty_graph_traffic_model(g, int(dir), ctypes.byref(tm),
+                                         current_stream() if stream is None else stream))
+    return {name: int(getattr(tm, name)) for name, _ in folty_traffic_model._fields_}
+
+
+def folty_kernel_launches() -> int:
+    return int(lib.folty_kernel_launches())
+
+
+def folty_profile_enable(on: bool = True) -> None:
+    lib.folty_profile_enable(1 if on else 0)
+
+
+def folty_profile_read() -> Dict[str, float]:
+    p = folty_profile()
+    _check(lib.folty_profile_read(ctypes.byref(p)))
+    return {"probe_launches": int(p.probe_launches), "probe_ms": float(p.probe_ms)}
+
+
+# ------------------------------------------------------------------ convenience
+
+class TemporalGraph:
+    """Owns a folty graph handle: load, preprocess, query, free."""
+
+    def __init__(self, n: int, src, dst, t, allocator: Optional[str] = "torch",
+                 stream: Optional[int] = None, preprocess: bool = True):
+        self.handle = folty_load_temporal_graph(n, src, dst, t, allocator=allocator, stream=stream)
+        if preprocess:
+            try:
+                folty_preprocess(self.handle, stream)
+            except Exception:
+                self.close()
+                raise
+
+    def query(self, q, stream: Optional[int] = None):
+        return folty_query(self.handle, q, stream)
+
+    def query_batch(self, qs, stream: Optional[int] = None):
+        return folty_query_batch(self.handle, qs, stream)
+
+    def info(self):
+        return folty_graph_get_info(self.handle)
+
+    def traffic_model(self, dir: int = DIR_OUT, stream: Optional[int] = None):
+        return folty_graph_traffic_model(self.handle, dir, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            folty_free(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

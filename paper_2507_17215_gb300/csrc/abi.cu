@@ -1,0 +1,384 @@
+// The C ABI of folty.h: argument checks, object lifetime, error reporting, and the
+// load step (copy + validation of the input edge list).
+#include <cstdio>
+#include <cstdlib>
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace folty {
+
+std::atomic<uint64_t> g_launches{0};
+
+static thread_local std::string t_last_error;
+
+static std::atomic<int> g_profile_on{0};
+static std::mutex g_profile_mu;
+static folty_profile g_profile{0, 0.0};
+
+ProbeTimer::ProbeTimer(cudaStream_t s) : s_(s) {
+    on_ = g_profile_on.load() != 0;
+    if (on_) {
+        FOLTY_CUDA(cudaEventCreate(&a_));
+        FOLTY_CUDA(cudaEventCreate(&b_));
+    }
+}
+
+ProbeTimer::~ProbeTimer() {
+    if (a_) cudaEventDestroy(a_);
+    if (b_) cudaEventDestroy(b_);
+}
+
+void ProbeTimer::start() {
+    if (on_) {
+        FOLTY_CUDA(cudaEventRecord(a_, s_));
+        started_ = true;
+    }
+}
+
+void ProbeTimer::stop() {
+    if (on_ && started_) {
+        FOLTY_CUDA(cudaEventRecord(b_, s_));
+        stopped_ = true;
+    }
+}
+
+void ProbeTimer::collect() {
+    if (!(on_ && started_ && stopped_)) return;
+    float ms = 0.f;
+    FOLTY_CUDA(cudaEventElapsedTime(&ms, a_, b_));
+    std::lock_guard<std::mutex> lock(g_profile_mu);
+    g_profile.probe_launches += 1;
+    g_profile.probe_ms += ms;
+    started_ = stopped_ = false;
+}
+
+void set_last_error(const std::string& msg) { t_last_error = msg; }
+
+int num_sms() {
+    static std::mutex mu;
+    static std::vector<int> cache;
+    int dev = 0;
+    FOLTY_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)cache.size() <= dev) cache.resize(dev + 1, 0);
+    if (cache[dev] == 0) FOLTY_CUDA(cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev));
+    return cache[dev];
+}
+
+void* Allocator::get(size_t bytes, cudaStream_t s) const {
+    if (bytes == 0) bytes = 16;
+    if (user) return a.alloc(bytes, (void*)s, a.ctx);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void Allocator::put(void* p, cudaStream_t s) const {
+    if (!p) return;
+    if (user) a.free(p, (void*)s, a.ctx);
+    else cudaFreeAsync(p, s);
+}
+
+void graph_release(folty_graph* g, void* p, cudaStream_t s) {
+    if (!p) return;
+    auto& v = *g->owned;
+    for (size_t i = 0; i < v.size(); i++) {
+        if (v[i] == p) {
+            v.erase(v.begin() + (long)i);
+            g->alloc.put(p, s);
+            return;
+        }
+    }
+}
+
+void read_back(folty_graph* g, const void* const* dev_ptrs, const int* sizes, int count, int64_t* out,
+               cudaStream_t s) {
+    if (count > 32) fail(FOLTY_EINVAL, "read_back: too many values");
+    for (int i = 0; i < count; i++)
+        FOLTY_CUDA(cudaMemcpyAsync(g->host_stage + i, dev_ptrs[i], (size_t)sizes[i], cudaMemcpyDeviceToHost, s));
+    FOLTY_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < count; i++) {
+        if (sizes[i] == 8) out[i] = g->host_stage[i];
+        else {
+            int32_t v;
+            std::memcpy(&v, &g->host_stage[i], 4);
+            out[i] = v;
+        }
+    }
+}
+
+int64_t read_i64(folty_graph* g, const int64_t* p, cudaStream_t s) {
+    const void* ptrs[1] = {p};
+    int sizes[1] = {8};
+    int64_t v;
+    read_back(g, ptrs, sizes, 1, &v, s);
+    return v;
+}
+
+int32_t read_i32(folty_graph* g, const int32_t* p, cudaStream_t s) {
+    const void* ptrs[1] = {p};
+    int sizes[1] = {4};
+    int64_t v;
+    read_back(g, ptrs, sizes, 1, &v, s);
+    return (int32_t)v;
+}
+
+void fill_result_host(folty_result* out, int64_t n_pairs, int64_t m, bool want_edges) {
+    std::memset(out, 0, sizeof(*out));
+    out->tag = RESULT_TAG;
+    out->n_pairs = n_pairs;
+    out->m = want_edges ? m : 0;
+    if (n_pairs > 0) {
+        int32_t* block = (int32_t*)std::malloc(sizeof(int32_t) * 4 * (size_t)n_pairs);
+        if (!block) fail(FOLTY_ENOMEM, "host allocation of the result failed");
+        out->u = block;
+        out->v = block + n_pairs;
+        out->count = block + 2 * n_pairs;
+        out->ncert = block + 3 * n_pairs;
+    }
+    if (want_edges) {
+        out->edge_count = (int32_t*)std::calloc((size_t)(m > 0 ? m : 1), sizeof(int32_t));
+        if (!out->edge_count) {
+            std::free(out->u);
+            out->u = nullptr;
+            fail(FOLTY_ENOMEM, "host allocation of the edge counts failed");
+        }
+    }
+}
+
+static void free_result(folty_result* r) {
+    std::free(r->u);
+    std::free(r->edge_count);
+    r->u = r->v = r->count = r->ncert = r->edge_count = nullptr;
+    r->n_pairs = 0;
+    r->tag = FREED_TAG;
+}
+
+static void free_graph(folty_graph* g) {
+    if (g->owned) {
+        for (void* p : *g->owned) g->alloc.put(p, 0);
+        delete g->owned;
+        g->owned = nullptr;
+    }
+    if (g->host_stage) cudaFreeHost(g->host_stage);
+    g->tag = FREED_TAG;
+    delete g;
+}
+
+// ------------------------------------------------------------------ load
+
+// Checks ids and timestamps, finds the t range, counts self-loops and detects
+// time-sorted input. stat: [0] first bad index + 1 (min), [1] tmin, [2] tmax,
+// [3] unsorted flag, [4] self-loops.
+__global__ void k_validate(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                           const int64_t* __restrict__ t, int64_t m, int32_t n,
+                           unsigned long long* __restrict__ stat) {
+    unsigned long long bad = ~0ull, tmin = ~0ull, tmax = 0, unsorted = 0, loops = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t x = src[i], y = dst[i];
+        int64_t ti = t[i];
+        bool ok = x >= 0 && x < n && y >= 0 && y < n && ti >= 0 && ti < (1ll << 62);
+        if (!ok && (unsigned long long)i < bad) bad = (unsigned long long)i;
+        if (ok) {
+            tmin = min(tmin, (unsigned long long)ti);
+            tmax = max(tmax, (unsigned long long)ti);
+        }
+        if (i > 0 && t[i - 1] > ti) unsorted = 1;
+        loops += (x == y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        bad = min(bad, __shfl_xor_sync(0xffffffffu, bad, o));
+        tmin = min(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+        tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+        unsorted |= __shfl_xor_sync(0xffffffffu, unsorted, o);
+        loops += __shfl_xor_sync(0xffffffffu, loops, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad != ~0ull) atomicMin(&stat[0], bad);
+        atomicMin(&stat[1], tmin);
+        atomicMax(&stat[2], tmax);
+        if (unsorted) atomicOr(&stat[3], 1ull);
+        if (loops) atomicAdd(&stat[4], loops);
+    }
+}
+
+static void load_graph(folty_graph* g, const int32_t* src, const int32_t* dst, const int64_t* t,
+                       cudaStream_t s) {
+    const int64_t m = g->m;
+    g->in_src = graph_alloc<int32_t>(g, m, s);
+    g->in_dst = graph_alloc<int32_t>(g, m, s);
+    g->in_t = graph_alloc<int64_t>(g, m, s);
+    if (m > 0) {
+        FOLTY_CUDA(cudaMemcpyAsync(g->in_src, src, sizeof(int32_t) * (size_t)m, cudaMemcpyDefault, s));
+        FOLTY_CUDA(cudaMemcpyAsync(g->in_dst, dst, sizeof(int32_t) * (size_t)m, cudaMemcpyDefault, s));
+        FOLTY_CUDA(cudaMemcpyAsync(g->in_t, t, sizeof(int64_t) * (size_t)m, cudaMemcpyDefault, s));
+    }
+    Scratch sc(g->alloc, s);
+    unsigned long long* stat = sc.get<unsigned long long>(5);
+    unsigned long long init[5] = {~0ull, ~0ull, 0ull, 0ull, 0ull};
+    std::memcpy(g->host_stage + 32, init, sizeof(init));
+    FOLTY_CUDA(cudaMemcpyAsync(stat, g->host_stage + 32, sizeof(init), cudaMemcpyHostToDevice, s));
+    if (m > 0) FOLTY_LAUNCH(k_validate, grid_for(m, 256), 256, 0, s, g->in_src, g->in_dst, g->in_t, m, g->n, stat);
+    const void* ptrs[5] = {stat, stat + 1, stat + 2, stat + 3, stat + 4};
+    int sizes[5] = {8, 8, 8, 8, 8};
+    int64_t v[5];
+    read_back(g, ptrs, sizes, 5, v, s);
+    if ((unsigned long long)v[0] != ~0ull)
+        fail(FOLTY_EINVAL, "edge " + std::to_string(v[0]) + ": vertex id outside [0, n) or timestamp outside [0, 2^62)");
+    g->tmin = (m > 0) ? v[1] : 0;
+    g->tmax = (m > 0) ? v[2] : 0;
+    g->info.time_sorted = v[3] ? 0 : 1;
+    g->m_kept = m - v[4];
+    g->info.n = g->n;
+    g->info.m = m;
+    g->info.m_kept = g->m_kept;
+}
+
+template <typename F>
+static folty_status guarded(F&& f) {
+    try {
+        f();
+        t_last_error.clear();
+        return FOLTY_OK;
+    } catch (const Error& e) {
+        t_last_error = e.msg;
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        t_last_error = "host allocation failed";
+        return FOLTY_ENOMEM;
+    } catch (...) {
+        t_last_error = "unexpected internal error";
+        return FOLTY_ECUDA;
+    }
+}
+
+static folty_graph* checked_graph(const folty_graph* g) {
+    if (!g || g->tag != GRAPH_TAG) fail(FOLTY_EINVAL, "not a folty graph");
+    return const_cast<folty_graph*>(g);
+}
+
+}  // namespace folty
+
+using namespace folty;
+
+extern "C" {
+
+folty_status folty_load_temporal_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                                       const int64_t* t, const folty_allocator* alloc, void* stream,
+                                       folty_graph** out) {
+    folty_graph* g = nullptr;
+    folty_status st = guarded([&] {
+        if (!out) fail(FOLTY_EINVAL, "out is NULL");
+        *out = nullptr;
+        if (n < 0 || n >= (1 << 30)) fail(FOLTY_EINVAL, "n outside [0, 2^30)");
+        if (m < 0 || m >= 0x7fffffffll) fail(FOLTY_EINVAL, "m outside [0, 2^31 - 1)");
+        if (m > 0 && (!src || !dst || !t)) fail(FOLTY_EINVAL, "edge arrays are NULL");
+        if (alloc && (!alloc->alloc || !alloc->free)) fail(FOLTY_EINVAL, "allocator without alloc/free");
+        cudaStream_t s = (cudaStream_t)stream;
+        g = new folty_graph();
+        std::memset((void*)g, 0, sizeof(*g));
+        g->tag = GRAPH_TAG;
+        g->owned = new std::vector<void*>();
+        if (alloc) {
+            g->alloc.a = *alloc;
+            g->alloc.user = true;
+        }
+        FOLTY_CUDA(cudaGetDevice(&g->device));
+        FOLTY_CUDA(cudaMallocHost((void**)&g->host_stage, 64 * sizeof(int64_t)));
+        g->n = n;
+        g->m = m;
+        load_graph(g, src, dst, t, s);
+        *out = g;
+    });
+    if (st != FOLTY_OK && g) free_graph(g);
+    return st;
+}
+
+folty_status folty_preprocess(folty_graph* g, void* stream) {
+    return guarded([&] {
+        checked_graph(g);
+        if (g->state != 0) fail(FOLTY_ESTATE, "graph already preprocessed");
+        preprocess_graph(g, (cudaStream_t)stream);
+    });
+}
+
+folty_status folty_query(folty_graph* g, const folty_query_params* q, folty_result* out, void* stream) {
+    return guarded([&] {
+        checked_graph(g);
+        if (!q || !out) fail(FOLTY_EINVAL, "query or result is NULL");
+        if (g->state != 1) fail(FOLTY_ESTATE, "graph not preprocessed");
+        validate_query(*q);
+        run_query(g, *q, out, (cudaStream_t)stream);
+    });
+}
+
+folty_status folty_query_batch(folty_graph* g, const folty_query_params* qs, int32_t nq, folty_result* outs,
+                               void* stream) {
+    return guarded([&] {
+        checked_graph(g);
+        if (nq < 0 || (nq > 0 && (!qs || !outs))) fail(FOLTY_EINVAL, "bad query array");
+        if (g->state != 1) fail(FOLTY_ESTATE, "graph not preprocessed");
+        for (int i = 0; i < nq; i++) validate_query(qs[i]);
+        for (int i = 0; i < nq; i++) std::memset(&outs[i], 0, sizeof(folty_result));
+        try {
+            run_query_batch(g, qs, nq, outs, (cudaStream_t)stream);
+        } catch (...) {
+            for (int i = 0; i < nq; i++)
+                if (outs[i].tag == RESULT_TAG) free_result(&outs[i]);
+            throw;
+        }
+    });
+}
+
+void folty_free(void* obj) {
+    if (!obj) return;
+    uint64_t tag;
+    std::memcpy(&tag, obj, sizeof(tag));
+    if (tag == GRAPH_TAG) free_graph((folty_graph*)obj);
+    else if (tag == RESULT_TAG) free_result((folty_result*)obj);
+}
+
+const char* folty_last_error(void) { return t_last_error.c_str(); }
+
+folty_status folty_graph_get_info(const folty_graph* g, folty_graph_info* info) {
+    return guarded([&] {
+        folty_graph* gg = checked_graph(g);
+        if (!info) fail(FOLTY_EINVAL, "info is NULL");
+        if (gg->state != 1) fail(FOLTY_ESTATE, "graph not preprocessed");
+        *info = gg->info;
+    });
+}
+
+folty_status folty_graph_traffic_model(folty_graph* g, int32_t dir, folty_traffic_model* out, void* stream) {
+    return guarded([&] {
+        checked_graph(g);
+        if (!out) fail(FOLTY_EINVAL, "out is NULL");
+        if (dir < 0 || dir > 2) fail(FOLTY_EINVAL, "unknown direction variant");
+        if (g->state != 1) fail(FOLTY_ESTATE, "graph not preprocessed");
+        traffic_model(g, dir, out, (cudaStream_t)stream);
+    });
+}
+
+uint64_t folty_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void folty_profile_enable(int32_t on) {
+    std::lock_guard<std::mutex> lock(g_profile_mu);
+    g_profile = folty_profile{0, 0.0};
+    g_profile_on.store(on ? 1 : 0);
+}
+
+folty_status folty_profile_read(folty_profile* out) {
+    return guarded([&] {
+        if (!out) fail(FOLTY_EINVAL, "out is NULL");
+        std::lock_guard<std::mutex> lock(g_profile_mu);
+        *out = g_profile;
+    });
+}
+
+}  // extern "C"

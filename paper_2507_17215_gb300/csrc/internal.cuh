@@ -1,0 +1,229 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "folty.h"
+
+namespace folty {
+
+// ------------------------------------------------------------------ errors
+
+struct Error {
+    folty_status status;
+    std::string msg;
+};
+
+[[noreturn]] inline void fail(folty_status st, const std::string& msg) { throw Error{st, msg}; }
+
+inline void cuda_check(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+        fail(FOLTY_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+}
+#define FOLTY_CUDA(expr) ::folty::cuda_check((expr), #expr)
+
+void set_last_error(const std::string& msg);
+
+// ------------------------------------------------------------------ launches
+
+extern std::atomic<uint64_t> g_launches;
+
+inline void after_launch(const char* name) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) fail(FOLTY_ECUDA, std::string("launch of ") + name + ": " + cudaGetErrorString(e));
+}
+
+#define FOLTY_LAUNCH(kernel, grid, block, smem, stream, ...)                   \
+    do {                                                                       \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);            \
+        ::folty::after_launch(#kernel);                                        \
+    } while (0)
+
+// Number of SMs of the current device (cached per device).
+int num_sms();
+
+// Grid for a grid-stride loop over n items: enough blocks to cover n, capped at a
+// whole number of waves over all SMs.
+inline unsigned grid_for(int64_t n, int block, int waves = 8) {
+    int64_t need = (n + block - 1) / block;
+    int64_t cap = (int64_t)num_sms() * waves;
+    if (need < 1) need = 1;
+    return (unsigned)(need < cap ? need : cap);
+}
+
+// ------------------------------------------------------------------ memory
+
+struct Allocator {
+    folty_allocator a{};
+    bool user = false;
+
+    void* get(size_t bytes, cudaStream_t s) const;
+    void put(void* p, cudaStream_t s) const;
+};
+
+// Temporary device buffers of one call, released (stream-ordered) when it goes out of
+// scope, also on error.
+class Scratch {
+  public:
+    Scratch(const Allocator& a, cudaStream_t s) : a_(a), s_(s) {}
+    ~Scratch() {
+        for (void* p : ptrs_) a_.put(p, s_);
+    }
+    Scratch(const Scratch&) = delete;
+    Scratch& operator=(const Scratch&) = delete;
+
+    template <typename T>
+    T* get(int64_t count) {
+        size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+        void* p = a_.get(bytes, s_);
+        if (!p) fail(FOLTY_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+        ptrs_.push_back(p);
+        return static_cast<T*>(p);
+    }
+    cudaStream_t stream() const { return s_; }
+    const Allocator& allocator() const { return a_; }
+
+  private:
+    const Allocator& a_;
+    cudaStream_t s_;
+    std::vector<void*> ptrs_;
+};
+
+// ------------------------------------------------------------------ the graph
+
+constexpr uint64_t GRAPH_TAG = 0x464f4c5459475248ull;   // "FOLTYGRH"
+constexpr uint64_t RESULT_TAG = 0x464f4c5459525354ull;  // "FOLTYRST"
+constexpr uint64_t FREED_TAG = 0x464f4c5459465245ull;   // "FOLTYFRE"
+
+struct DeviceArrays;  // defined below
+
+}  // namespace folty
+
+struct folty_graph {
+    uint64_t tag;
+    folty::Allocator alloc;
+    int device;
+    int state;  // 0 loaded, 1 preprocessed
+    int32_t n;
+    int64_t m;
+    // ---- loaded input (device copies; released by preprocess)
+    int32_t* in_src;
+    int32_t* in_dst;
+    int64_t* in_t;
+    // ---- preprocessed store (device)
+    int64_t m_kept;
+    int32_t* perm;    // [m_kept] input index of each sorted temporal edge
+    int64_t* T;       // [m_kept] timestamps, sorted by (static edge, direction, t)
+    int32_t* sd;      // [m_kept] 2 * static edge id + direction bit
+    int32_t S;        // static edges
+    int32_t* seg;     // [2S + 1]: E_{a->b} = [seg[2s], seg[2s+1]), E_{b->a} = [seg[2s+1], seg[2s+2])
+    int32_t* ea;      // [S] smaller endpoint a
+    int32_t* eb;      // [S] larger endpoint b
+    int32_t* deg;     // [n] |N(u)|
+    int32_t* common;  // [S] |N(a) cap N(b)| = triangles on the static edge
+    int64_t ntri;
+    int4* tri;        // [ntri] {s_uv, s_uw, s_vw, id-order bits}, u < v < w in degeneracy rank
+    int64_t* tri_off; // [ntri + 1] prefix of per-triangle probe counts
+    int64_t* tile_tri;  // [probe tiles + 1] triangle holding each tile's first probe
+    int64_t n_tiles;
+    int64_t enum_bytes; // model bytes of the triangle enumeration
+    int64_t tmin, tmax; // timestamp range of the input
+    // ---- statistics
+    folty_graph_info info;
+    // ---- pinned host staging for small device->host reads
+    int64_t* host_stage;  // 64 entries
+    std::vector<void*>* owned;  // device buffers owned by the graph
+};
+
+namespace folty {
+
+// Allocates a device buffer owned by the graph (freed by folty_free).
+template <typename T>
+T* graph_alloc(folty_graph* g, int64_t count, cudaStream_t s) {
+    size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+    void* p = g->alloc.get(bytes, s);
+    if (!p) fail(FOLTY_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    g->owned->push_back(p);
+    g->info.device_bytes += (int64_t)bytes;
+    return static_cast<T*>(p);
+}
+void graph_release(folty_graph* g, void* p, cudaStream_t s);
+
+// Reads `count` int64 values from device memory through the graph's pinned staging
+// buffer (synchronises the stream).
+void read_back(folty_graph* g, const void* const* dev_ptrs, const int* sizes, int count,
+               int64_t* out, cudaStream_t s);
+int64_t read_i64(folty_graph* g, const int64_t* p, cudaStream_t s);
+int32_t read_i32(folty_graph* g, const int32_t* p, cudaStream_t s);
+
+// ------------------------------------------------------------------ primitives (prims.cu)
+
+// Exclusive prefix sum of in[0..n) into out[0..n], out[n] = total. in may equal out
+// (then out needs n + 1 slots).
+void exclusive_scan(Scratch& sc, const int32_t* in, int32_t* out, int64_t n);
+void exclusive_scan(Scratch& sc, const int32_t* in, int64_t* out, int64_t n);
+void exclusive_scan(Scratch& sc, const int64_t* in, int64_t* out, int64_t n);
+void exclusive_scan(Scratch& sc, const uint32_t* in, uint32_t* out, int64_t n);
+
+// Stable LSD radix sort of (key, value) pairs on key bits [0, bits). Buffers ping-pong
+// between (keys, vals) and (keys_alt, vals_alt); returns true when the result ended
+// up in the *_alt buffers.
+bool radix_sort_pairs(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
+                      uint32_t* vals_alt, int64_t n, int bits);
+
+int bit_length(uint64_t x);
+
+// ------------------------------------------------------------------ pipeline stages
+
+void preprocess_graph(folty_graph* g, cudaStream_t s);          // preprocess.cu
+void run_query(folty_graph* g, const folty_query_params& q, folty_result* out,
+               cudaStream_t s);                                  // query.cu
+void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq,
+                     folty_result* outs, cudaStream_t s);        // batch.cu
+void traffic_model(folty_graph* g, int dir, folty_traffic_model* out, cudaStream_t s);
+
+void validate_query(const folty_query_params& q);
+
+// Event pair around probe launches when profiling is on (abi.cu holds the totals).
+class ProbeTimer {
+  public:
+    explicit ProbeTimer(cudaStream_t s);
+    ~ProbeTimer();
+    void start();
+    void stop();
+    void collect();  // call after the stream has been synchronised
+
+  private:
+    cudaStream_t s_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+    bool on_ = false, started_ = false, stopped_ = false;
+};
+void fill_result_host(folty_result* out, int64_t n_pairs, int64_t m, bool want_edges);
+
+// ------------------------------------------------------------------ device helpers
+
+// First index in [lo, hi) with a[i] >= key (hi if none).
+__device__ __forceinline__ int lower_bound_i64(const int64_t* __restrict__ a, int lo, int hi,
+                                               int64_t key) {
+    int len = hi - lo;
+    while (len > 0) {
+        int half = len >> 1;
+        if (a[lo + half] < key) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return lo;
+}
+
+}  // namespace folty

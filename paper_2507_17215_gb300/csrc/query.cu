@@ -1,0 +1,280 @@
+// One query over a preprocessed graph (Algorithm 6 semantics, Algorithm 5 threshold):
+//   A6  window probes: for every triangle {u, v, w} of G_S and every temporal edge
+//       e = (x, y, t) on one of its three static edges, with witness z the third
+//       vertex: t2 = first entry >= t of L2, t3 = first entry >= t2 of L3, hit iff both
+//       exist and t3 <= t + delta (Theorem 3.1; Algorithms 1, 2 and 6). L2 = E_{x,z},
+//       L3 = E_{y,z} for the paper's "out" motif, E_{z,x} and E_{z,y} for "in", and the
+//       union of both directions for "either" (first entry of a union = min of the
+//       first entries of its parts);
+//   A7  c_e += hit. Every (e, witness) pair is probed once (each triangle is listed
+//       once), so c_e counts distinct witnesses;
+//   A8  certificate test per edge, max c_e and certificate count per directed pair,
+//       compaction of the solution pairs and a sort by (u, v).
+#include <climits>
+
+#include "internal.cuh"
+#include "probe.cuh"
+
+namespace folty {
+
+// ================================================================== A6 + A7
+
+// Block b handles probes [b * PB_TILE, (b + 1) * PB_TILE) of the flat probe space
+// (triangle-major, then the triangle's three static edges, then their sorted temporal
+// edges). The block stages the triangles overlapping its range in shared memory,
+// threads take consecutive probes (coalesced T reads and counter updates).
+__global__ void __launch_bounds__(PB_THREADS) k_probe(const int4* __restrict__ tri,
+                                                      const int64_t* __restrict__ tri_off,
+                                                      const int64_t* __restrict__ tile_tri, int64_t P,
+                                                      const int32_t* __restrict__ seg,
+                                                      const int64_t* __restrict__ T, int64_t delta,
+                                                      int dir, int32_t* __restrict__ cnt) {
+    __shared__ TriStage st;
+    const int64_t p0 = (int64_t)blockIdx.x * PB_TILE;
+    const int64_t p1 = min(P, p0 + PB_TILE);
+    stage_triangles(st, tri, tri_off, tile_tri, seg);
+#pragma unroll 1
+    for (int it = 0; it < PB_ITEMS; it++) {
+        int64_t p = p0 + (int64_t)it * PB_THREADS + threadIdx.x;
+        if (p >= p1) break;
+        Probe pr = locate_probe(st, p);
+        Lists L = role_lists(st.off[pr.j], st.flags[pr.j], pr.e, pr.d, dir);
+        int64_t t = T[pr.pos];
+        int64_t t3 = probe_window(T, t, L);
+        if (t3 != PROBE_NONE && t3 - t <= delta) atomicAdd(&cnt[pr.pos], 1);
+    }
+}
+
+// ================================================================== A8
+
+struct ThresholdArgs {
+    const int32_t* cnt;
+    const int32_t* sd;
+    int64_t mk;
+    const int32_t* ea;
+    const int32_t* eb;
+    const int32_t* deg;
+    const int32_t* common;
+    int quant, universe;
+    int64_t num, den;
+    int32_t* seg_max;    // [2S]
+    int32_t* seg_ncert;  // [2S]
+    unsigned long long* n_cert;
+};
+
+// Certificate test of Definition 1.1 with rho = num / den, exact in int64.
+__device__ __forceinline__ bool certifies(int quant, int64_t c, int64_t U, int64_t num, int64_t den) {
+    return c >= 1 && (quant == FOLTY_Q_EXISTS || c * den >= num * U);
+}
+
+__global__ void k_threshold(ThresholdArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long my_cert = 0;
+    for (int64_t base = gw * 32; base < a.mk; base += nw * 32) {
+        int64_t i = base + lane;
+        int32_t key = -1, c = 0;
+        int sat = 0;
+        if (i < a.mk) {
+            key = a.sd[i];
+            c = a.cnt[i];
+            int32_t s = key >> 1, d = key & 1;
+            int32_t x = d ? a.eb[s] : a.ea[s];
+            int32_t y = d ? a.ea[s] : a.eb[s];
+            int64_t U = a.universe == FOLTY_U_HEAD ? a.deg[x]
+                        : a.universe == FOLTY_U_TAIL ? a.deg[y] : a.common[s];
+            sat = certifies(a.quant, c, U, a.num, a.den);
+        }
+        // equal keys are contiguous (sorted order): reduce each run once
+        unsigned peers = __match_any_sync(0xffffffffu, key);
+        int run_max = __reduce_max_sync(peers, c);
+        int run_sat = __reduce_add_sync(peers, sat);
+        if (key >= 0 && lane == __ffs(peers) - 1) {
+            if (run_max > 0) atomicMax(&a.seg_max[key], run_max);
+            if (run_sat > 0) atomicAdd(&a.seg_ncert[key], run_sat);
+        }
+        my_cert += (unsigned long long)sat;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my_cert += __shfl_xor_sync(0xffffffffu, my_cert, o);
+    if (lane == 0 && my_cert) atomicAdd(a.n_cert, my_cert);
+}
+
+__global__ void k_pair_flags(const int32_t* __restrict__ seg_ncert, int64_t n2, int32_t* __restrict__ flag) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n2;
+         j += (int64_t)gridDim.x * blockDim.x)
+        flag[j] = seg_ncert[j] > 0;
+}
+
+__global__ void k_pair_keys(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t n2,
+                            const int32_t* __restrict__ ea, const int32_t* __restrict__ eb, int nb,
+                            uint64_t* __restrict__ key, uint32_t* __restrict__ val) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n2;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[j]) continue;
+        int32_t s = (int32_t)(j >> 1), d = (int32_t)(j & 1);
+        uint64_t x = (uint64_t)(d ? eb[s] : ea[s]), y = (uint64_t)(d ? ea[s] : eb[s]);
+        key[pos[j]] = (x << nb) | y;
+        val[pos[j]] = (uint32_t)j;
+    }
+}
+
+__global__ void k_pair_out(const uint64_t* __restrict__ key, const uint32_t* __restrict__ val, int64_t np,
+                           int nb, const int32_t* __restrict__ seg_max, const int32_t* __restrict__ seg_ncert,
+                           int32_t* __restrict__ out) {
+    const uint64_t mask = (1ull << nb) - 1;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = key[p];
+        uint32_t j = val[p];
+        out[p] = (int32_t)(k >> nb);
+        out[np + p] = (int32_t)(k & mask);
+        out[2 * np + p] = seg_max[j];
+        out[3 * np + p] = seg_ncert[j];
+    }
+}
+
+__global__ void k_edge_counts_input_order(const int32_t* __restrict__ cnt, const int32_t* __restrict__ perm,
+                                          int64_t mk, int32_t* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mk;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[perm[i]] = cnt[i];
+}
+
+// ================================================================== drivers
+
+void validate_query(const folty_query_params& q) {
+    if (q.delta < 0 || q.delta >= (1ll << 62)) fail(FOLTY_EINVAL, "delta outside [0, 2^62)");
+    if (q.rho_den == 0 || q.rho_num > q.rho_den) fail(FOLTY_EINVAL, "rho must satisfy 0 <= rho_num <= rho_den, rho_den > 0");
+    if (q.quant > FOLTY_Q_FORALL_T) fail(FOLTY_EINVAL, "unknown quantifier");
+    if (q.dir > FOLTY_DIR_EITHER) fail(FOLTY_EINVAL, "unknown direction variant");
+    if (q.universe > FOLTY_U_COMMON) fail(FOLTY_EINVAL, "unknown universe");
+}
+
+void launch_probe(folty_graph* g, int64_t delta, int dir, int32_t* cnt, cudaStream_t s) {
+    const int64_t P = g->info.probes;
+    if (P <= 0) return;
+    int64_t blocks = (P + PB_TILE - 1) / PB_TILE;
+    if (blocks > 0x7fffffffll) fail(FOLTY_EINVAL, "probe space too large");
+    FOLTY_LAUNCH(k_probe, (unsigned)blocks, PB_THREADS, 0, s, g->tri, g->tri_off, g->tile_tri, P, g->seg,
+                 g->T, delta, dir, cnt);
+}
+
+// Threshold + pair output for counts cnt[m_kept] (sorted order). Allocates and fills
+// the host arrays of *out; edge counts in input order when asked.
+void finish_query(folty_graph* g, Scratch& sc, const folty_query_params& q, const int32_t* cnt,
+                  folty_result* out, cudaStream_t s) {
+    const int T = 256;
+    const int64_t mk = g->m_kept;
+    const int64_t n2 = 2 * (int64_t)g->S;
+    const int nb = bit_length((uint64_t)(g->n > 1 ? g->n - 1 : 1));
+    int32_t* seg_max = sc.get<int32_t>(n2);
+    int32_t* seg_ncert = sc.get<int32_t>(n2);
+    unsigned long long* ncert = sc.get<unsigned long long>(1);
+    FOLTY_CUDA(cudaMemsetAsync(seg_max, 0, sizeof(int32_t) * (size_t)(n2 > 0 ? n2 : 1), s));
+    FOLTY_CUDA(cudaMemsetAsync(seg_ncert, 0, sizeof(int32_t) * (size_t)(n2 > 0 ? n2 : 1), s));
+    FOLTY_CUDA(cudaMemsetAsync(ncert, 0, sizeof(unsigned long long), s));
+    if (mk > 0) {
+        ThresholdArgs a{cnt, g->sd, mk, g->ea, g->eb, g->deg, g->common, (int)q.quant, (int)q.universe,
+                        (int64_t)q.rho_num, (int64_t)q.rho_den, seg_max, seg_ncert, ncert};
+        FOLTY_LAUNCH(k_threshold, grid_for(mk, T), T, 0, s, a);
+    }
+    int32_t* flag = sc.get<int32_t>(n2 + 1);
+    int32_t* pos = sc.get<int32_t>(n2 + 1);
+    if (n2 > 0) FOLTY_LAUNCH(k_pair_flags, grid_for(n2, T), T, 0, s, seg_ncert, n2, flag);
+    exclusive_scan(sc, flag, pos, n2);
+    int64_t rb[2];
+    {
+        const void* ptrs[2] = {pos + n2, ncert};
+        int sizes[2] = {4, 8};
+        read_back(g, ptrs, sizes, 2, rb, s);
+    }
+    const int64_t np = rb[0];
+    fill_result_host(out, np, g->m, q.want_edge_counts != 0);
+    out->n_cert_edges = rb[1];
+    if (np > 0) {
+        uint64_t* key = sc.get<uint64_t>(np);
+        uint64_t* key_alt = sc.get<uint64_t>(np);
+        uint32_t* val = sc.get<uint32_t>(np);
+        uint32_t* val_alt = sc.get<uint32_t>(np);
+        FOLTY_LAUNCH(k_pair_keys, grid_for(n2, T), T, 0, s, flag, pos, n2, g->ea, g->eb, nb, key, val);
+        bool alt = radix_sort_pairs(sc, key, key_alt, val, val_alt, np, 2 * nb);
+        int32_t* packed = sc.get<int32_t>(4 * np);
+        FOLTY_LAUNCH(k_pair_out, grid_for(np, T), T, 0, s, alt ? key_alt : key, alt ? val_alt : val, np, nb,
+                     seg_max, seg_ncert, packed);
+        FOLTY_CUDA(cudaMemcpyAsync(out->u, packed, sizeof(int32_t) * 4 * (size_t)np, cudaMemcpyDeviceToHost, s));
+    }
+    if (q.want_edge_counts) {
+        int32_t* ec = sc.get<int32_t>(g->m);
+        if (g->m > 0) FOLTY_CUDA(cudaMemsetAsync(ec, 0, sizeof(int32_t) * (size_t)g->m, s));
+        if (mk > 0) FOLTY_LAUNCH(k_edge_counts_input_order, grid_for(mk, T), T, 0, s, cnt, g->perm, mk, ec);
+        if (g->m > 0)
+            FOLTY_CUDA(cudaMemcpyAsync(out->edge_count, ec, sizeof(int32_t) * (size_t)g->m, cudaMemcpyDeviceToHost, s));
+    }
+    FOLTY_CUDA(cudaStreamSynchronize(s));
+}
+
+void run_query(folty_graph* g, const folty_query_params& q, folty_result* out, cudaStream_t s) {
+    Scratch sc(g->alloc, s);
+    ProbeTimer timer(s);
+    const int64_t mk = g->m_kept;
+    int32_t* cnt = sc.get<int32_t>(mk);
+    if (mk > 0) FOLTY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)mk, s));
+    timer.start();
+    launch_probe(g, q.delta, q.dir, cnt, s);
+    timer.stop();
+    finish_query(g, sc, q, cnt, out, s);  // synchronises the stream
+    timer.collect();
+}
+
+// ================================================================== traffic model
+
+// Per role (x, y; witness z): sigma1 = |E_{x,y}|, sigma2, sigma3 = the sizes of L2, L3
+// for the direction variant. Bytes = 8 sigma1 (read L1) + 8 min(sigma2, sigma1 *
+// ceil(log2(sigma2 + 1))) + the same for L3 + 8 sigma1 (counter read-modify-write).
+__global__ void k_traffic(const int4* __restrict__ tri, int64_t ntri, const int32_t* __restrict__ seg, int dir,
+                          unsigned long long* __restrict__ out) {
+    unsigned long long acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ntri;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int4 tr = tri[i];
+        int32_t off[9];
+        const int32_t se[3] = {tr.x, tr.y, tr.z};
+#pragma unroll
+        for (int e = 0; e < 3; e++) {
+            off[3 * e] = seg[2 * se[e]];
+            off[3 * e + 1] = seg[2 * se[e] + 1];
+            off[3 * e + 2] = seg[2 * se[e] + 2];
+        }
+#pragma unroll
+        for (int e = 0; e < 3; e++) {
+#pragma unroll
+            for (int d = 0; d < 2; d++) {
+                int64_t s1 = off[3 * e + d + 1] - off[3 * e + d];
+                if (s1 == 0) continue;
+                Lists L = role_lists(off, tr.w, e, d, dir);
+                int64_t s2 = (int64_t)(L.e2 - L.b2) + (L.e2b - L.b2b);
+                int64_t s3 = (int64_t)(L.e3 - L.b3) + (L.e3b - L.b3b);
+                int64_t l2 = 64 - __clzll((unsigned long long)s2);
+                int64_t l3 = 64 - __clzll((unsigned long long)s3);
+                acc += 8 * s1 + 8 * min(s2, s1 * l2) + 8 * min(s3, s1 * l3) + 8 * s1;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
+void traffic_model(folty_graph* g, int dir, folty_traffic_model* out, cudaStream_t s) {
+    Scratch sc(g->alloc, s);
+    unsigned long long* acc = sc.get<unsigned long long>(1);
+    FOLTY_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long), s));
+    if (g->ntri > 0) FOLTY_LAUNCH(k_traffic, grid_for(g->ntri, 256), 256, 0, s, g->tri, g->ntri, g->seg, dir, acc);
+    out->probe_bytes = read_i64(g, (const int64_t*)acc, s);
+    out->enum_bytes = g->enum_bytes;
+    out->threshold_bytes = 4 * g->m_kept + 12 * 2 * (int64_t)g->S;
+}
+
+}  // namespace folty

@@ -1,0 +1,337 @@
+"""CUDA library vs the CPU oracle, element by element (bit-exact: all arithmetic is
+integer). Every call goes through the C ABI (libfolty.so) via the thin binding."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from _support import golden_files, pairs_of, parse_fixture
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2507_17215_gb300 as F
+    return F
+
+
+def _lib_results(F, g, queries, allocator="torch", batch=False):
+    with F.TemporalGraph(g.n, g.src, g.dst, g.t, allocator=allocator) as G:
+        if batch:
+            return G.query_batch(queries), G.info()
+        return [G.query(q) for q in queries], G.info()
+
+
+def _assert_same(lib_res, ora_res, what=""):
+    np.testing.assert_array_equal(lib_res["edge_count"], ora_res["edge_count"], err_msg=what)
+    assert pairs_of(lib_res) == pairs_of(ora_res), what
+    assert lib_res["n_cert_edges"] == ora_res["n_cert_edges"], what
+
+
+def _full_mix(deltas, want=True):
+    qs = []
+    for d in deltas:
+        for dr in (W.DIR_OUT, W.DIR_IN, W.DIR_EITHER):
+            qs.append(W.Query(d, 1, 2, W.Q_FORALL_T, dr, W.U_HEAD, want))
+        qs.append(W.Query(d, 1, 3, W.Q_FORALL_T, W.DIR_OUT, W.U_TAIL, want))
+        qs.append(W.Query(d, 3, 4, W.Q_FORALL_T, W.DIR_EITHER, W.U_COMMON, want))
+        qs.append(W.Query(d, 1, 2, W.Q_EXISTS, W.DIR_IN, W.U_HEAD, want))
+    return qs
+
+
+def _check_graph(F, g, queries, allocator="torch"):
+    res, info = _lib_results(F, g, queries, allocator=allocator)
+    with oracle.OracleGraph.of(g) as og:
+        for q, r in zip(queries, res):
+            _assert_same(r, og.query(q), what=str(q))
+    return info
+
+
+@pytest.mark.parametrize("path", golden_files(), ids=lambda p: p.split("/")[-1])
+def test_golden_fixtures_through_library(F, path):
+    g, cases = parse_fixture(path)
+    qs = [W.Query(c["q"].delta, c["q"].rho_num, c["q"].rho_den, c["q"].quant, c["q"].dir,
+                  c["q"].universe, True) for c in cases]
+    res, _ = _lib_results(F, g, qs)
+    for c, r in zip(cases, res):
+        np.testing.assert_array_equal(r["edge_count"], c["counts"])
+        assert pairs_of(r) == c["pairs"]
+
+
+def test_random_tiny_graphs(F):
+    rng = np.random.default_rng(2024)
+    for i in range(25):
+        g = W.random_small_graph(rng, int(rng.integers(2, 14)), int(rng.integers(1, 90)),
+                                 int(rng.integers(0, 30)), self_loops=bool(i % 2))
+        _check_graph(F, g, _full_mix((0, 3, 11, 1000)))
+
+
+def test_random_dense_graphs_default_allocator(F):
+    """Several probe tiles and ragged tails; the library's own stream-ordered allocator."""
+    rng = np.random.default_rng(77)
+    for n, m, tmax in ((30, 3000, 200), (60, 12000, 5000), (200, 40000, 100000)):
+        g = W.random_small_graph(rng, n, m, tmax)
+        _check_graph(F, g, _full_mix((0, 40, 700)), allocator=None)
+
+
+def test_config1_tiny_workload(F):
+    g = W.config_graph(1)
+    qs = [W.Query(3600, 1, 2, want_edge_counts=True)]
+    qs += _full_mix((100_000, 1_000_000))
+    qs += [W.Query(10 ** 6, k, 10, W.Q_FORALL_T, W.DIR_OUT, W.U_HEAD, True) for k in (1, 5, 9)]
+    _check_graph(F, g, qs)
+
+
+@pytest.mark.parametrize("k,scale", [(2, 0.02), (3, 0.004)])
+def test_scaled_medium_and_paper_scale_recipes(F, k, scale):
+    g = W.config_graph(k, scale=scale)
+    qs = [W.Query(d, 1, 2, W.Q_FORALL_T, W.DIR_OUT, W.U_HEAD, True) for d in (600, 3600, 86400)]
+    qs += [W.Query(3600, 3, 10, W.Q_FORALL_T, W.DIR_EITHER, W.U_COMMON, True),
+           W.Query(604800, 1, 10, W.Q_EXISTS, W.DIR_IN, W.U_TAIL, True)]
+    info = _check_graph(F, g, qs)
+    assert info["triangles"] > 100 and info["probes"] > 1000
+
+
+def test_unsorted_input_equals_sorted(F):
+    rng = np.random.default_rng(5)
+    g = W.config_graph(2, scale=0.01)
+    perm = rng.permutation(g.m)
+    gs = W.TemporalGraph(g.n, g.src[perm].copy(), g.dst[perm].copy(), g.t[perm].copy())
+    qs = [W.Query(3600, 1, 2, want_edge_counts=True), W.Query(86400, 1, 5, W.Q_FORALL_T, W.DIR_EITHER,
+                                                             W.U_COMMON, True)]
+    a, ia = _lib_results(F, g, qs)
+    b, ib = _lib_results(F, gs, qs)
+    assert ia["time_sorted"] == 1 and ib["time_sorted"] == 0
+    for q, ra, rb in zip(qs, a, b):
+        assert pairs_of(ra) == pairs_of(rb)
+        # edge i of the shuffled graph is edge perm[i] of the sorted one
+        np.testing.assert_array_equal(ra["edge_count"][perm], rb["edge_count"])
+    with oracle.OracleGraph.of(gs) as og:
+        for q, r in zip(qs, b):
+            _assert_same(r, og.query(q))
+
+
+def _edge_case_graphs():
+    out = {}
+    e = np.zeros(0, np.int32)
+    out["empty"] = W.TemporalGraph(5, e, e.copy(), np.zeros(0, np.int64))
+    out["single_vertex_loops"] = W.TemporalGraph(1, np.zeros(3, np.int32), np.zeros(3, np.int32),
+                                                 np.array([1, 2, 3], np.int64))
+    out["path_no_triangles"] = W.TemporalGraph(4, np.array([0, 1, 2], np.int32),
+                                               np.array([1, 2, 3], np.int32), np.array([1, 2, 3], np.int64))
+    k = 9
+    src, dst = zip(*[(a, b) for a in range(k) for b in range(k) if a != b])
+    src = np.array(src, np.int32)
+    dst = np.array(dst, np.int32)
+    out["complete_all_t_equal"] = W.TemporalGraph(k, src, dst, np.full(src.shape, 77, np.int64))
+    rng = np.random.default_rng(3)
+    hub_n = 300
+    hs = np.concatenate([np.zeros(hub_n - 1, np.int32), rng.integers(1, hub_n, 3000).astype(np.int32)])
+    hd = np.concatenate([np.arange(1, hub_n, dtype=np.int32), rng.integers(1, hub_n, 3000).astype(np.int32)])
+    out["hub"] = W.TemporalGraph(hub_n, hs, hd, rng.integers(0, 50, hs.shape[0]).astype(np.int64))
+    out["sigma_one"] = W.random_small_graph(np.random.default_rng(8), 400, 400, 10 ** 6, self_loops=False)
+    dup = W.random_small_graph(np.random.default_rng(9), 10, 40, 5)
+    out["duplicates"] = W.TemporalGraph(10, np.tile(dup.src, 3), np.tile(dup.dst, 3), np.tile(dup.t, 3))
+    iso = W.random_small_graph(np.random.default_rng(10), 8, 60, 20)
+    out["isolated_vertices"] = W.TemporalGraph(1000, iso.src, iso.dst, iso.t)
+    big_t = W.random_small_graph(np.random.default_rng(11), 8, 80, 20)
+    out["large_timestamps"] = W.TemporalGraph(8, big_t.src, big_t.dst,
+                                              big_t.t + np.int64((1 << 62) - 100))
+    return out
+
+
+@pytest.mark.parametrize("name", sorted(_edge_case_graphs().keys()))
+def test_edge_cases(F, name):
+    g = _edge_case_graphs()[name]
+    deltas = (0, 5, (1 << 62) - 1)
+    _check_graph(F, g, _full_mix(deltas))
+
+
+def _core_numbers(n, src, dst):
+    """Batagelj-Zaversnik bucket algorithm (textbook, sequential)."""
+    nb = [set() for _ in range(n)]
+    for a, b in zip(src.tolist(), dst.tolist()):
+        if a != b:
+            nb[a].add(b)
+            nb[b].add(a)
+    deg = [len(x) for x in nb]
+    md = max(deg) if deg else 0
+    bins = [0] * (md + 1)
+    for d in deg:
+        bins[d] += 1
+    start = 0
+    for d in range(md + 1):
+        bins[d], start = start, start + bins[d]
+    pos = [0] * n
+    vert = [0] * n
+    for v in range(n):
+        pos[v] = bins[deg[v]]
+        vert[pos[v]] = v
+        bins[deg[v]] += 1
+    for d in range(md, 0, -1):
+        bins[d] = bins[d - 1]
+    if md >= 0:
+        bins[0] = 0
+    for i in range(n):
+        v = vert[i]
+        for u in nb[v]:
+            if deg[u] > deg[v]:
+                du, pu = deg[u], pos[u]
+                pw = bins[du]
+                w = vert[pw]
+                if u != w:
+                    pos[u], vert[pu] = pw, w
+                    pos[w], vert[pw] = pu, u
+                bins[du] += 1
+                deg[u] -= 1
+    return deg
+
+
+def test_degeneracy_and_orientation(F):
+    rng = np.random.default_rng(12)
+    for g in (W.config_graph(1), W.random_small_graph(rng, 120, 5000, 10),
+              W.config_graph(3, scale=0.002)):
+        core = _core_numbers(g.n, g.src, g.dst)
+        with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
+            info = G.info()
+        assert info["degeneracy"] == max(core)
+        assert info["max_out_degree"] <= info["degeneracy"]
+        loops = int((g.src == g.dst).sum())
+        assert info["m_kept"] == g.m - loops
+
+
+def test_batch_equals_sequential(F):
+    g = W.config_graph(2, scale=0.01)
+    rng = np.random.default_rng(4)
+    qs = W.random_query_mix(40, rng, want_edge_counts=True)
+    with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
+        seq = [G.query(q) for q in qs]
+        bat = G.query_batch(qs)
+    for q, a, b in zip(qs, seq, bat):
+        np.testing.assert_array_equal(a["edge_count"], b["edge_count"])
+        assert pairs_of(a) == pairs_of(b), str(q)
+
+
+def test_full_size_medium_workload_sampled(F):
+    """The medium workload at full size (1M vertices, 20M edges), as the benchmark runs
+    it: every query of the workload, checked on sampled edges and sampled pairs."""
+    g = W.config_graph(2)
+    qs = [W.Query(d, 1, 2, want_edge_counts=True) for d in (600, 3600, 86400)]
+    rng = np.random.default_rng(99)
+    with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
+        res = [G.query(q) for q in qs]
+        info = G.info()
+    assert info["m"] == g.m and info["probes"] > 10 ** 7
+    # edges with a large count are rare: sample uniformly and among the top counts
+    key = g.src.astype(np.int64) * g.n + g.dst
+    by_key = np.argsort(key, kind="stable")
+    skey = key[by_key]
+    with oracle.OracleGraph.of(g) as og:
+        deg = np.array([og.degree(u) for u in range(g.n)], dtype=np.int64)
+        for q, r in zip(qs, res):
+            ec = r["edge_count"]
+            idx = np.unique(np.concatenate([rng.integers(0, g.m, 1500),
+                                            np.argsort(ec)[-300:]]))
+            want, _ = og.counts(q.delta, q.dir, idx=idx)
+            np.testing.assert_array_equal(ec[idx], want)
+            # sampled output pairs: recompute max count and certificates from the oracle
+            k = len(r["u"])
+            assert k == len(set(zip(r["u"].tolist(), r["v"].tolist())))
+            order = np.lexsort((r["v"], r["u"]))
+            assert (order == np.arange(k)).all(), "pairs must be sorted by (u, v)"
+            for j in rng.choice(k, size=min(k, 60), replace=False) if k else []:
+                u, v = int(r["u"][j]), int(r["v"][j])
+                lo, hi = np.searchsorted(skey, [u * g.n + v, u * g.n + v + 1])
+                edges = by_key[lo:hi]
+                c, _ = og.counts(q.delta, q.dir, idx=edges)
+                assert int(c.max()) == int(r["count"][j])
+                ncert = int(((c >= 1) & (c.astype(np.int64) * q.rho_den >= q.rho_num * deg[u])).sum())
+                assert ncert == int(r["ncert"][j])
+            # every sampled certificate appears among the pairs
+            pairs = set(zip(r["u"].tolist(), r["v"].tolist()))
+            sat = (want >= 1) & (want.astype(np.int64) * q.rho_den >= q.rho_num * deg[g.src[idx]])
+            for e in idx[sat]:
+                assert (int(g.src[e]), int(g.dst[e])) in pairs
+
+
+def test_errors(F):
+    bad = W.TemporalGraph(3, np.array([0, 5], np.int32), np.array([1, 1], np.int32),
+                          np.array([0, 0], np.int64))
+    with pytest.raises(F.FoltyError) as ei:
+        F.folty_load_temporal_graph(bad.n, bad.src, bad.dst, bad.t)
+    assert ei.value.status == F.FOLTY_EINVAL
+    neg = W.TemporalGraph(3, np.array([0], np.int32), np.array([1], np.int32), np.array([-4], np.int64))
+    with pytest.raises(F.FoltyError) as ei:
+        F.folty_load_temporal_graph(neg.n, neg.src, neg.dst, neg.t)
+    assert ei.value.status == F.FOLTY_EINVAL
+    g = W.config_graph(1)
+    h = F.folty_load_temporal_graph(g.n, g.src, g.dst, g.t)
+    try:
+        with pytest.raises(F.FoltyError) as ei:
+            F.folty_query(h, W.Query(10))
+        assert ei.value.status == F.FOLTY_ESTATE
+        F.folty_preprocess(h)
+        with pytest.raises(F.FoltyError) as ei:
+            F.folty_preprocess(h)
+        assert ei.value.status == F.FOLTY_ESTATE
+        for q in (W.Query(-1), W.Query(10, 3, 2), W.Query(10, 1, 0), W.Query(1 << 62)):
+            with pytest.raises(F.FoltyError) as ei:
+                F.folty_query(h, q)
+            assert ei.value.status == F.FOLTY_EINVAL
+        with pytest.raises(F.FoltyError) as ei:
+            F.folty_query_batch(h, [W.Query(10), W.Query(10, 1, 0)])
+        assert ei.value.status == F.FOLTY_EINVAL
+    finally:
+        F.folty_free(h)
+
+
+def test_allocator_failure_reports_enomem_without_leak(F):
+    import ctypes
+
+    import torch
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    live = {}
+    budget = {"calls": 0}
+
+    @F.ALLOC_FN
+    def alloc(nbytes, stream, ctx):
+        budget["calls"] += 1
+        if budget["calls"] > 6:
+            return None
+        p = torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        live[p] = nbytes
+        return p
+
+    @F.FREE_FN
+    def free(ptr, stream, ctx):
+        live.pop(int(ptr))
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a = F.folty_allocator(alloc, free, None)
+    g = W.config_graph(1)
+    h = ctypes.c_void_p()
+    st = F.lib.folty_load_temporal_graph(g.n, g.m, g.src.ctypes.data, g.dst.ctypes.data,
+                                         g.t.ctypes.data, ctypes.byref(a), F.current_stream(),
+                                         ctypes.byref(h))
+    if st == F.FOLTY_OK:
+        st = F.lib.folty_preprocess(h, F.current_stream())
+        assert st == F.FOLTY_ENOMEM, F.folty_last_error()
+        F.folty_free(h)
+    else:
+        assert st == F.FOLTY_ENOMEM
+    torch.cuda.synchronize()
+    assert not live, "every allocation must be returned"
+    assert torch.cuda.memory_allocated() == base
+
+
+def test_kernel_launch_counter_moves(F):
+    g = W.config_graph(1)
+    before = F.folty_kernel_launches()
+    with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
+        G.query(W.Query(3600))
+    assert F.folty_kernel_launches() > before + 10
