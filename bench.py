@@ -174,7 +174,7 @@ def run_reference(args, g, queries):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="folty", choices=["folty", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=None)

@@ -1,12 +1,123 @@
-// Batched queries. This first form answers the queries one after another on the
-// stream; it defines the results the shared-probe batch kernel must reproduce.
+// Batched queries sharing the window probes.
+//
+// For a fixed (temporal edge e, witness w, direction variant) the searched t2 and t3
+// of Theorem 3.1 do not depend on delta, so hit(delta) <=> g(e, w) = t3 - t <= delta.
+// One probe pass per direction variant therefore serves every delta of that variant:
+// the pass bins g by the sorted distinct deltas D (bin j = first D_j >= g), a prefix
+// over the bins gives c_e(D_j) = #{w : g(e, w) <= D_j} for all j at once, and each
+// query's threshold pass (the single-query code) reads its column. Quantifier, rho and
+// universe only enter that last pass. When the bins of all deltas do not fit in the
+// memory budget, the deltas are cut into chunks, one probe pass per chunk (bin 0 of a
+// chunk also holds every smaller gap).
+#include <algorithm>
+#include <map>
+
 #include "internal.cuh"
+#include "probe.cuh"
 
 namespace folty {
 
+constexpr int BATCH_MAX_BINS = 1024;
+
+__global__ void __launch_bounds__(PB_THREADS) k_probe_binned(const int4* __restrict__ tri,
+                                                             const int64_t* __restrict__ tri_off,
+                                                             const int64_t* __restrict__ tile_tri, int64_t P,
+                                                             const int32_t* __restrict__ seg,
+                                                             const int64_t* __restrict__ T, int dir,
+                                                             const int64_t* __restrict__ deltas, int k,
+                                                             int32_t* __restrict__ bins, int64_t mk) {
+    __shared__ TriStage st;
+    __shared__ int64_t sD[BATCH_MAX_BINS];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) sD[i] = deltas[i];
+    const int64_t p0 = (int64_t)blockIdx.x * PB_TILE;
+    const int64_t p1 = min(P, p0 + PB_TILE);
+    stage_triangles(st, tri, tri_off, tile_tri, seg);  // ends with __syncthreads
+    const int64_t dmax = sD[k - 1];
+#pragma unroll 1
+    for (int it = 0; it < PB_ITEMS; it++) {
+        int64_t p = p0 + (int64_t)it * PB_THREADS + threadIdx.x;
+        if (p >= p1) break;
+        Probe pr = locate_probe(st, p);
+        Lists L = role_lists(st.off[pr.j], st.flags[pr.j], pr.e, pr.d, dir);
+        int64_t t = T[pr.pos];
+        int64_t t3 = probe_window(T, t, L);
+        if (t3 == PROBE_NONE) continue;
+        int64_t gap = t3 - t;
+        if (gap > dmax) continue;
+        int j = lower_bound_i64(sD, 0, k, gap);
+        atomicAdd(&bins[(int64_t)j * mk + pr.pos], 1);
+    }
+}
+
+// bins[j][e] <- sum_{i <= j} bins[i][e]
+__global__ void k_bins_prefix(int32_t* __restrict__ bins, int k, int64_t mk) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < mk;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t run = 0;
+        for (int j = 0; j < k; j++) {
+            int64_t o = (int64_t)j * mk + e;
+            run += bins[o];
+            bins[o] = run;
+        }
+    }
+}
+
+static int64_t batch_bin_budget_bytes() {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return (int64_t)1 << 30;
+    }
+    int64_t b = (int64_t)(free_b / 4);
+    const int64_t cap = (int64_t)16 << 30;
+    return b < cap ? b : cap;
+}
+
 void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty_result* outs,
                      cudaStream_t s) {
-    for (int i = 0; i < nq; i++) run_query(g, qs[i], &outs[i], s);
+    const int64_t mk = g->m_kept;
+    const int64_t P = g->info.probes;
+    // group the queries by direction variant; distinct sorted deltas per group
+    for (int dir = 0; dir <= FOLTY_DIR_EITHER; dir++) {
+        std::vector<int> members;
+        for (int i = 0; i < nq; i++)
+            if (qs[i].dir == dir) members.push_back(i);
+        if (members.empty()) continue;
+        std::vector<int64_t> D;
+        for (int i : members) D.push_back(qs[i].delta);
+        std::sort(D.begin(), D.end());
+        D.erase(std::unique(D.begin(), D.end()), D.end());
+        const int64_t per_bin = mk * (int64_t)sizeof(int32_t);
+        int64_t chunk = per_bin > 0 ? batch_bin_budget_bytes() / per_bin : (int64_t)D.size();
+        chunk = std::max<int64_t>(1, std::min<int64_t>({chunk, (int64_t)BATCH_MAX_BINS, (int64_t)D.size()}));
+        for (size_t c0 = 0; c0 < D.size(); c0 += (size_t)chunk) {
+            const int k = (int)std::min<int64_t>(chunk, (int64_t)D.size() - (int64_t)c0);
+            Scratch sc(g->alloc, s);
+            int32_t* bins = sc.get<int32_t>(mk * k);
+            int64_t* dd = sc.get<int64_t>(k);
+            // stage the deltas through pinned memory in the graph's staging buffer region
+            std::vector<int64_t> hd(D.begin() + (long)c0, D.begin() + (long)c0 + k);
+            FOLTY_CUDA(cudaMemcpyAsync(dd, hd.data(), sizeof(int64_t) * (size_t)k, cudaMemcpyHostToDevice, s));
+            if (mk > 0) {
+                FOLTY_CUDA(cudaMemsetAsync(bins, 0, sizeof(int32_t) * (size_t)(mk * k), s));
+                ProbeTimer timer(s);
+                timer.start();
+                if (P > 0)
+                    FOLTY_LAUNCH(k_probe_binned, (unsigned)g->n_tiles, PB_THREADS, 0, s, g->tri, g->tri_off,
+                                 g->tile_tri, P, g->seg, g->T, dir, dd, k, bins, mk);
+                timer.stop();
+                if (k > 1) FOLTY_LAUNCH(k_bins_prefix, grid_for(mk, 256), 256, 0, s, bins, k, mk);
+                FOLTY_CUDA(cudaStreamSynchronize(s));  // hd must outlive the copy; timer
+                timer.collect();
+            }
+            for (int i : members) {
+                auto it = std::lower_bound(hd.begin(), hd.end(), qs[i].delta);
+                if (it == hd.end() || *it != qs[i].delta) continue;  // another chunk
+                const int j = (int)(it - hd.begin());
+                finish_query(g, qs[i], bins + (int64_t)j * mk, &outs[i], s);
+            }
+        }
+    }
 }
 
 }  // namespace folty

@@ -191,6 +191,10 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq,
 void traffic_model(folty_graph* g, int dir, folty_traffic_model* out, cudaStream_t s);
 
 void validate_query(const folty_query_params& q);
+// Threshold, pair output and result copy-out for per-edge counts cnt[m_kept] (sorted
+// order); synchronises the stream.
+void finish_query(folty_graph* g, const folty_query_params& q, const int32_t* cnt, folty_result* out,
+                  cudaStream_t s);
 
 // Event pair around probe launches when profiling is on (abi.cu holds the totals).
 class ProbeTimer {

@@ -163,9 +163,10 @@ void launch_probe(folty_graph* g, int64_t delta, int dir, int32_t* cnt, cudaStre
 
 // Threshold + pair output for counts cnt[m_kept] (sorted order). Allocates and fills
 // the host arrays of *out; edge counts in input order when asked.
-void finish_query(folty_graph* g, Scratch& sc, const folty_query_params& q, const int32_t* cnt,
-                  folty_result* out, cudaStream_t s) {
+void finish_query(folty_graph* g, const folty_query_params& q, const int32_t* cnt, folty_result* out,
+                  cudaStream_t s) {
     const int T = 256;
+    Scratch sc(g->alloc, s);
     const int64_t mk = g->m_kept;
     const int64_t n2 = 2 * (int64_t)g->S;
     const int nb = bit_length((uint64_t)(g->n > 1 ? g->n - 1 : 1));
@@ -224,7 +225,7 @@ void run_query(folty_graph* g, const folty_query_params& q, folty_result* out, c
     timer.start();
     launch_probe(g, q.delta, q.dir, cnt, s);
     timer.stop();
-    finish_query(g, sc, q, cnt, out, s);  // synchronises the stream
+    finish_query(g, q, cnt, out, s);  // synchronises the stream
     timer.collect();
 }
 
