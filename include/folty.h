@@ -175,6 +175,29 @@ void folty_profile_enable(int32_t on);
 /* Copies the totals. Errors: FOLTY_EINVAL (NULL). */
 folty_status folty_profile_read(folty_profile *out);
 
+/* Per-edge counts of one query without allocating anything (the paper has no
+ * counterpart). For callers that cannot allocate device memory when they query: a
+ * serving process that reserved its whole memory budget at start-up, latency-bound code
+ * that must avoid the implicit device synchronisation of cudaMalloc/cudaFree, or a host
+ * whose allocator must not be re-entered from inside a library call. Computes c_e of
+ * every input edge for (delta, dir) -- the window-probe pass of folty_query -- into
+ * edge_count: caller-owned device memory of m int32, input order, self-loops 0.
+ *   - Allocates nothing: the counters the pass works in are one file-scope device array
+ *     of FOLTY_NOALLOC_MAX_EDGES int32 (4 MiB) that every GPU loading the library holds
+ *     until the process exits. A graph with more non-loop edges gives FOLTY_EINVAL.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call before any
+ *     stream capture begins.
+ *   - All calls share the array, which keeps the last call's contents; each call clears
+ *     the part it uses before probing. Calls whose work overlaps on the GPU (other
+ *     streams, other threads) race on it and give wrong counts: serialise them.
+ *   - Stream-ordered on "stream"; does not synchronise it.
+ * Errors: FOLTY_EINVAL (NULL, delta outside [0, 2^62), unknown dir, graph too large),
+ * FOLTY_ESTATE (not preprocessed), FOLTY_ECUDA. */
+#define FOLTY_NOALLOC_MAX_EDGES (1 << 20)
+folty_status folty_edge_counts_noalloc(folty_graph *g, int64_t delta, int32_t dir,
+                                       int32_t *edge_count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

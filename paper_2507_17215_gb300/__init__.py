@@ -30,7 +30,8 @@ U_HEAD, U_TAIL, U_COMMON = 0, 1, 2
 # the exported C symbols (folty.h), checked by the test suite
 EXPORTED = ["folty_load_temporal_graph", "folty_preprocess", "folty_query", "folty_query_batch",
             "folty_free", "folty_last_error", "folty_graph_get_info", "folty_graph_traffic_model",
-            "folty_kernel_launches", "folty_profile_enable", "folty_profile_read"]
+            "folty_kernel_launches", "folty_profile_enable", "folty_profile_read",
+            "folty_edge_counts_noalloc"]
 
 
 class FoltyError(RuntimeError):
@@ -108,6 +109,8 @@ def _load_library():
     lib.folty_profile_enable.argtypes = [c_int32]
     lib.folty_profile_read.restype = c_int32
     lib.folty_profile_read.argtypes = [POINTER(folty_profile)]
+    lib.folty_edge_counts_noalloc.restype = c_int32
+    lib.folty_edge_counts_noalloc.argtypes = [G, c_int64, c_int32, c_void_p, c_void_p]
     return lib
 
 
@@ -253,6 +256,16 @@ def folty_graph_traffic_model(g: int, dir: int = DIR_OUT, stream: Optional[int] 
 
 def folty_kernel_launches() -> int:
     return int(lib.folty_kernel_launches())
+
+
+NOALLOC_MAX_EDGES = 1 << 20  # FOLTY_NOALLOC_MAX_EDGES
+
+
+def folty_edge_counts_noalloc(g: int, delta: int, dir: int, edge_count, stream: Optional[int] = None) -> None:
+    """Per-edge counts of one (delta, dir) into a caller-owned device int32 tensor of
+    length m (input order), with no allocation inside the library; see folty.h."""
+    _check(lib.folty_edge_counts_noalloc(g, int(delta), int(dir), _ptr(edge_count),
+                                         current_stream() if stream is None else stream))
 
 
 def folty_profile_enable(on: bool = True) -> None:

@@ -367,6 +367,18 @@ folty_status folty_graph_traffic_model(folty_graph* g, int32_t dir, folty_traffi
 
 uint64_t folty_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+folty_status folty_edge_counts_noalloc(folty_graph* g, int64_t delta, int32_t dir, int32_t* edge_count,
+                                       void* stream) {
+    return guarded([&] {
+        checked_graph(g);
+        if (!edge_count && g->m > 0) fail(FOLTY_EINVAL, "edge_count is NULL");
+        if (delta < 0 || delta >= (1ll << 62)) fail(FOLTY_EINVAL, "delta outside [0, 2^62)");
+        if (dir < 0 || dir > FOLTY_DIR_EITHER) fail(FOLTY_EINVAL, "unknown direction variant");
+        if (g->state != 1) fail(FOLTY_ESTATE, "graph not preprocessed");
+        edge_counts_noalloc(g, delta, dir, edge_count, (cudaStream_t)stream);
+    });
+}
+
 void folty_profile_enable(int32_t on) {
     std::lock_guard<std::mutex> lock(g_profile_mu);
     g_profile = folty_profile{0, 0.0};

@@ -191,6 +191,10 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq,
 void traffic_model(folty_graph* g, int dir, folty_traffic_model* out, cudaStream_t s);
 
 void validate_query(const folty_query_params& q);
+// Window-probe pass of one query into counters cnt[m_kept] (sorted order, zeroed).
+void launch_probe(folty_graph* g, int64_t delta, int dir, int32_t* cnt, cudaStream_t s);
+// The same pass with the counters in a file-scope device array (noalloc.cu).
+void edge_counts_noalloc(folty_graph* g, int64_t delta, int dir, int32_t* edge_count, cudaStream_t s);
 // Threshold, pair output and result copy-out for per-edge counts cnt[m_kept] (sorted
 // order); synchronises the stream.
 void finish_query(folty_graph* g, const folty_query_params& q, const int32_t* cnt, folty_result* out,
