@@ -169,6 +169,24 @@ def run_reference(args, g, queries):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- ranks
+
+def max_over_ranks(x: float, world: int, device: str) -> float:
+    """Slowest rank's figure (all_reduce MAX); identity for one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: int, world: int, seconds_max: float) -> float:
+    """Weak scaling over replicas: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -256,13 +274,8 @@ def main():
     prof = F.folty_profile_read()
     F.folty_profile_enable(False)
     clk = clocks.stop()
-    t_ms = ev0.elapsed_time(ev1)
-    t_max = torch.tensor([t_ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    t_ms = float(t_max.item())
-    units = world * args.steps * len(queries) * g.m
-    value = units / (t_ms / 1e3)
+    t_ms = max_over_ranks(ev0.elapsed_time(ev1), world, "cuda")
+    value = replica_throughput(args.steps * len(queries) * g.m, world, t_ms / 1e3)
 
     # ---- end-to-end through the C ABI from pinned host buffers
     ke = args.e2e_steps or args.steps
@@ -272,12 +285,8 @@ def main():
     for _ in range(ke):
         res_e = step(h_src, h_dst, h_t)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], device="cuda")
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_s = float(e2e_t.item())
-    e2e_value = world * ke * len(queries) * g.m / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+    e2e_value = replica_throughput(ke * len(queries) * g.m, world, e2e_s)
     h2d = g.m * (4 + 4 + 8)
     d2h = sum(16 * len(r["u"]) + 8 for r in res_e) + 8 * (4 + 3 * 2)
 

@@ -19,34 +19,51 @@ namespace folty {
 
 constexpr int BATCH_MAX_BINS = 1024;
 
+template <typename TS, int DIR>
 __global__ void __launch_bounds__(PB_THREADS) k_probe_binned(const int4* __restrict__ tri,
                                                              const int64_t* __restrict__ tri_off,
                                                              const int64_t* __restrict__ tile_tri, int64_t P,
                                                              const int32_t* __restrict__ seg,
-                                                             const int64_t* __restrict__ T, int dir,
-                                                             const int64_t* __restrict__ deltas, int k,
+                                                             const TS* __restrict__ T,
+                                                             const TS* __restrict__ deltas, int k,
                                                              int32_t* __restrict__ bins, int64_t mk) {
     __shared__ TriStage st;
-    __shared__ int64_t sD[BATCH_MAX_BINS];
+    __shared__ TS sD[BATCH_MAX_BINS];
     for (int i = threadIdx.x; i < k; i += blockDim.x) sD[i] = deltas[i];
     const int64_t p0 = (int64_t)blockIdx.x * PB_TILE;
-    const int64_t p1 = min(P, p0 + PB_TILE);
-    stage_triangles(st, tri, tri_off, tile_tri, seg);  // ends with __syncthreads
-    const int64_t dmax = sD[k - 1];
+    const int32_t count = (int32_t)min((int64_t)PB_TILE, P - p0);
+    stage_triangles(st, tri, tri_off, tile_tri, seg, DIR);  // ends with __syncthreads
+    const TS dmax = sD[k - 1];
 #pragma unroll 1
     for (int it = 0; it < PB_ITEMS; it++) {
-        int64_t p = p0 + (int64_t)it * PB_THREADS + threadIdx.x;
-        if (p >= p1) break;
-        Probe pr = locate_probe(st, p);
-        Lists L = role_lists(st.off[pr.j], st.flags[pr.j], pr.e, pr.d, dir);
-        int64_t t = T[pr.pos];
-        int64_t t3 = probe_window(T, t, L);
-        if (t3 == PROBE_NONE) continue;
-        int64_t gap = t3 - t;
+        const int32_t local = it * PB_THREADS + (int32_t)threadIdx.x;
+        if ((local & ~31) >= count) break;  // warp-uniform
+        const bool active = local < count;
+        Probe pr = locate_probe(st, local, active);
+        if (!active) continue;
+        const TS t = T[pr.pos];
+        const TS t3 = probe_window<TS, DIR>(T, st.off[pr.j], pr.seg2, pr.seg3, t, dmax);
+        if (t3 == TsNone<TS>::value) continue;
+        const TS gap = (TS)(t3 - t);
         if (gap > dmax) continue;
-        int j = lower_bound_i64(sD, 0, k, gap);
+        const int j = lower_bound_ts<TS>(sD, 0, k, gap);
         atomicAdd(&bins[(int64_t)j * mk + pr.pos], 1);
     }
+}
+
+template <typename TS>
+static void launch_binned(folty_graph* g, int dir, const TS* deltas, int k, int32_t* bins, cudaStream_t s) {
+    const unsigned grid = (unsigned)g->n_tiles;
+    const TS* T = (const TS*)g->T;
+    if (dir == FOLTY_DIR_OUT)
+        FOLTY_LAUNCH((k_probe_binned<TS, FOLTY_DIR_OUT>), grid, PB_THREADS, 0, s, g->tri, g->tri_off, g->tile_tri,
+                     g->info.probes, g->seg, T, deltas, k, bins, g->m_kept);
+    else if (dir == FOLTY_DIR_IN)
+        FOLTY_LAUNCH((k_probe_binned<TS, FOLTY_DIR_IN>), grid, PB_THREADS, 0, s, g->tri, g->tri_off, g->tile_tri,
+                     g->info.probes, g->seg, T, deltas, k, bins, g->m_kept);
+    else
+        FOLTY_LAUNCH((k_probe_binned<TS, FOLTY_DIR_EITHER>), grid, PB_THREADS, 0, s, g->tri, g->tri_off,
+                     g->tile_tri, g->info.probes, g->seg, T, deltas, k, bins, g->m_kept);
 }
 
 // bins[j][e] <- sum_{i <= j} bins[i][e]
@@ -95,19 +112,26 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
             Scratch sc(g->alloc, s);
             int32_t* bins = sc.get<int32_t>(mk * k);
             int64_t* dd = sc.get<int64_t>(k);
-            // stage the deltas through pinned memory in the graph's staging buffer region
             std::vector<int64_t> hd(D.begin() + (long)c0, D.begin() + (long)c0 + k);
-            FOLTY_CUDA(cudaMemcpyAsync(dd, hd.data(), sizeof(int64_t) * (size_t)k, cudaMemcpyHostToDevice, s));
+            // the bin bounds in the store's timestamp type (32-bit offsets: gaps stay
+            // below 2^32 - 1, so larger windows behave as 2^32 - 2)
+            std::vector<uint32_t> hd32(hd.size());
+            for (size_t i = 0; i < hd.size(); i++) hd32[i] = hd[i] >= 0xfffffffell ? 0xfffffffeu : (uint32_t)hd[i];
+            if (g->ts32)
+                FOLTY_CUDA(cudaMemcpyAsync(dd, hd32.data(), sizeof(uint32_t) * (size_t)k, cudaMemcpyHostToDevice, s));
+            else
+                FOLTY_CUDA(cudaMemcpyAsync(dd, hd.data(), sizeof(int64_t) * (size_t)k, cudaMemcpyHostToDevice, s));
             if (mk > 0) {
                 FOLTY_CUDA(cudaMemsetAsync(bins, 0, sizeof(int32_t) * (size_t)(mk * k), s));
                 ProbeTimer timer(s);
                 timer.start();
-                if (P > 0)
-                    FOLTY_LAUNCH(k_probe_binned, (unsigned)g->n_tiles, PB_THREADS, 0, s, g->tri, g->tri_off,
-                                 g->tile_tri, P, g->seg, g->T, dir, dd, k, bins, mk);
+                if (P > 0) {
+                    if (g->ts32) launch_binned<uint32_t>(g, dir, (const uint32_t*)dd, k, bins, s);
+                    else launch_binned<int64_t>(g, dir, (const int64_t*)dd, k, bins, s);
+                }
                 timer.stop();
                 if (k > 1) FOLTY_LAUNCH(k_bins_prefix, grid_for(mk, 256), 256, 0, s, bins, k, mk);
-                FOLTY_CUDA(cudaStreamSynchronize(s));  // hd must outlive the copy; timer
+                FOLTY_CUDA(cudaStreamSynchronize(s));  // the host bounds must outlive the copy
                 timer.collect();
             }
             for (int i : members) {

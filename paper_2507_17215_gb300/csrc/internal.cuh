@@ -121,7 +121,9 @@ struct folty_graph {
     // ---- preprocessed store (device)
     int64_t m_kept;
     int32_t* perm;    // [m_kept] input index of each sorted temporal edge
-    int64_t* T;       // [m_kept] timestamps, sorted by (static edge, direction, t)
+    void* T;          // [m_kept] timestamps sorted by (static edge, direction, t): uint32
+                      // offsets t - tmin when ts32, else int64
+    int ts32;
     int32_t* sd;      // [m_kept] 2 * static edge id + direction bit
     int32_t S;        // static edges
     int32_t* seg;     // [2S + 1]: E_{a->b} = [seg[2s], seg[2s+1]), E_{b->a} = [seg[2s+1], seg[2s+2])

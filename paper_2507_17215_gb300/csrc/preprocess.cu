@@ -53,15 +53,17 @@ __global__ void k_gather_keys(const uint64_t* __restrict__ key_in, const uint32_
         key_out[i] = key_in[order[i]];
 }
 
-// perm, T, and the "new static pair" flag of every kept sorted position.
+// perm, T (as t - tbase in TS), and the "new static pair" flag of every kept sorted
+// position.
+template <typename TS>
 __global__ void k_store(const uint64_t* __restrict__ key, const uint32_t* __restrict__ order,
-                        const int64_t* __restrict__ t, int64_t mk, int32_t* __restrict__ perm,
-                        int64_t* __restrict__ T, int32_t* __restrict__ newpair) {
+                        const int64_t* __restrict__ t, int64_t mk, int64_t tbase, int32_t* __restrict__ perm,
+                        TS* __restrict__ T, int32_t* __restrict__ newpair) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mk;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t o = order[i];
         perm[i] = (int32_t)o;
-        T[i] = t[o];
+        T[i] = (TS)(t[o] - tbase);
         newpair[i] = (i == 0) || ((key[i] >> 1) != (key[i - 1] >> 1));
     }
 }
@@ -107,20 +109,28 @@ __global__ void k_segments_fix(int32_t S, int64_t mk, int32_t* __restrict__ seg)
 
 // ================================================================== A2
 
-__global__ void k_count_degrees(const int32_t* __restrict__ ea, const int32_t* __restrict__ eb,
-                                int32_t S, int32_t* __restrict__ deg_hi, int32_t* __restrict__ deg_lo) {
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        atomicAdd(&deg_hi[ea[s]], 1);  // s lists b > a in a's row
-        atomicAdd(&deg_lo[eb[s]], 1);  // s lists a < b in b's row
+// Runs of equal values in a sorted id array: first[x] = start index, last[x] = end
+// index (exclusive) of the run of x. Ids absent from the array keep first = last = 0.
+__global__ void k_runs(const int32_t* __restrict__ ids, const uint32_t* __restrict__ order, int32_t S,
+                       int32_t* __restrict__ first, int32_t* __restrict__ last) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < S;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int32_t x = order ? ids[order[j]] : ids[j];
+        if (j == 0 || (order ? ids[order[j - 1]] : ids[j - 1]) != x) first[x] = (int32_t)j;
+        if (j == S - 1 || (order ? ids[order[j + 1]] : ids[j + 1]) != x) last[x] = (int32_t)j + 1;
     }
 }
 
-__global__ void k_add(const int32_t* __restrict__ a, const int32_t* __restrict__ b, int64_t n,
-                      int32_t* __restrict__ out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = a[i] + b[i];
+// deg_hi = #static edges (u, b > u), deg_lo = #static edges (a < u, u), deg = sum.
+__global__ void k_degrees(const int32_t* __restrict__ hi_first, const int32_t* __restrict__ hi_last,
+                          const int32_t* __restrict__ lo_first, const int32_t* __restrict__ lo_last, int64_t n,
+                          int32_t* __restrict__ deg_lo, int32_t* __restrict__ deg) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        int32_t dl = lo_last[u] - lo_first[u];
+        deg_lo[u] = dl;
+        deg[u] = dl + (hi_last[u] - hi_first[u]);
+    }
 }
 
 __global__ void k_edge_keys_b(const int32_t* __restrict__ eb, int32_t S, uint64_t* __restrict__ key,
@@ -137,7 +147,7 @@ __global__ void k_fill_adj(const int32_t* __restrict__ ea, const int32_t* __rest
                            const int32_t* __restrict__ rowptr, const int32_t* __restrict__ deg_lo,
                            const int32_t* __restrict__ hi_start, const int32_t* __restrict__ lo_start,
                            const uint32_t* __restrict__ by_b, int32_t* __restrict__ adj,
-                           int32_t* __restrict__ adj_eid) {
+                           int32_t* __restrict__ adj_eid, int32_t* __restrict__ adj_src) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < S;
          j += (int64_t)gridDim.x * blockDim.x) {
         // upper part: static edges are sorted by (a, b)
@@ -146,12 +156,14 @@ __global__ void k_fill_adj(const int32_t* __restrict__ ea, const int32_t* __rest
         int64_t p = (int64_t)rowptr[a] + deg_lo[a] + (s - hi_start[a]);
         adj[p] = eb[s];
         adj_eid[p] = s;
+        adj_src[p] = a;
         // lower part: by_b lists static edges by (b, a)
         int32_t s2 = (int32_t)by_b[j];
         int32_t b = eb[s2];
         int64_t q = (int64_t)rowptr[b] + ((int32_t)j - lo_start[b]);
         adj[q] = ea[s2];
         adj_eid[q] = s2;
+        adj_src[q] = b;
     }
 }
 
@@ -183,10 +195,16 @@ enum {
     C_ERR = 2,
     C_ACNT = 3,   // 2 slots
     C_MIN = 5,    // 2 slots
-    C_FCNT = 7,   // 3 slots
-    C_ROUNDS = 10,
-    C_ALPHA = 11,
-    C_SLOTS = 16
+    C_FCNT = 7,   // 3 slots: light frontier sizes
+    C_HCNT = 10,  // 3 slots: heavy frontier sizes
+    C_ROUNDS = 13,
+    C_ALPHA = 14,
+    C_TAIL = 15,    // 1 when the grid kernel stopped early for the single-block tail
+    C_TAIL_K = 16,  // state handed to the tail: level, round, alive buffer, alive count
+    C_TAIL_R = 17,
+    C_TAIL_AC = 18,
+    C_TAIL_N = 19,
+    C_SLOTS = 24
 };
 
 struct PeelArgs {
@@ -197,9 +215,12 @@ struct PeelArgs {
     int32_t* rnd;   // removal round, -1 while alive
     int32_t* core;  // core number
     int32_t* alive[2];
-    int32_t* fr[2];
+    int32_t* fr[2];  // light frontier (degree <= PEEL_HEAVY): one warp per vertex
+    int64_t* hr[2];  // heavy frontier as (vertex, piece) entries: piece << 32 | vertex
+    int32_t hcap;    // capacity of hr[0], hr[1]: n + 2S / PEEL_PIECE + 1
     int* ctl;
     long long timeout_ns;
+    int32_t tail_n;  // stop when at most this many vertices may still be alive
 };
 
 __device__ __forceinline__ long long global_ns() {
@@ -230,7 +251,7 @@ __device__ bool grid_barrier(int* ctl, long long timeout_ns) {
                     atomicExch(&ctl[C_ERR], 1);
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(20);
             }
         }
         __threadfence();
@@ -239,8 +260,11 @@ __device__ bool grid_barrier(int* ctl, long long timeout_ns) {
     return *(volatile int*)&ctl[C_ERR] == 0;
 }
 
-// Appends v for every lane with pred set; the whole warp must call it.
-__device__ __forceinline__ void warp_append(bool pred, int32_t v, int32_t* out, int* counter) {
+// Appends v for every lane with pred set; the whole warp must call it. A list never
+// holds more than cap entries (each vertex joins at most one frontier and one alive
+// list); an append beyond cap is dropped and recorded in *err instead of written.
+__device__ __forceinline__ void warp_append(bool pred, int32_t v, int32_t* out, int* counter, int cap,
+                                            int* err) {
     unsigned mask = __ballot_sync(0xffffffffu, pred);
     if (!mask) return;
     int lane = threadIdx.x & 31;
@@ -248,43 +272,133 @@ __device__ __forceinline__ void warp_append(bool pred, int32_t v, int32_t* out, 
     int base = 0;
     if (lane == leader) base = atomicAdd(counter, __popc(mask));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (pred) out[base + __popc(mask & ((1u << lane) - 1u))] = v;
+    if (pred) {
+        int idx = base + __popc(mask & ((1u << lane) - 1u));
+        if (idx < cap) out[idx] = v;
+        else atomicExch(err, 2);
+    }
 }
 
-constexpr int PEEL_THREADS = 256;
+constexpr int PEEL_THREADS = 1024;
+constexpr int PEEL_HEAVY = 128;     // vertices above this degree go to the heavy frontier
+constexpr int PEEL_PIECE = PEEL_THREADS;  // adjacency entries per heavy piece
+
+// Files vertex v (removed at round rr) in the frontier of round rr: light vertices as
+// themselves, heavy ones as their PEEL_PIECE-entry pieces of adjacency. The whole warp
+// must call it; b, e = v's row bounds.
+__device__ __forceinline__ void frontier_append(const PeelArgs& a, bool in, int32_t v, int32_t b, int32_t e,
+                                                int rr) {
+    const bool heavy = in && (e - b > PEEL_HEAVY);
+    warp_append(in && !heavy, v, a.fr[rr & 1], &a.ctl[C_FCNT + rr % 3], a.n, &a.ctl[C_ERR]);
+    if (heavy) {
+        const int np = (e - b + PEEL_PIECE - 1) / PEEL_PIECE;
+        const int base = atomicAdd(&a.ctl[C_HCNT + rr % 3], np);
+        if (base + np <= a.hcap) {
+            for (int q = 0; q < np; q++) a.hr[rr & 1][base + q] = ((int64_t)q << 32) | (uint32_t)v;
+        } else {
+            atomicExch(&a.ctl[C_ERR], 2);
+        }
+    }
+}
+
+// Neighbour j of a vertex leaving in round r: its degree drops, and a vertex whose degree
+// crosses k + 1 -> k joins round r + 1. A vertex that already left never crosses again
+// (its degree was <= k when it left and only falls), so no liveness test is needed.
+// The whole warp must call it.
+__device__ __forceinline__ void peel_neighbour(const PeelArgs& a, bool valid, int32_t j, int k, int r) {
+    bool cross = false;
+    int32_t v = 0, b = 0, e = 0;
+    if (valid) {
+        v = a.adj[j];
+        int old = atomicSub(&a.deg[v], 1);
+        if (old == k + 1) {
+            cross = true;
+            a.rnd[v] = r + 1;
+            a.core[v] = k;
+            b = a.rowptr[v];
+            e = a.rowptr[v + 1];
+        }
+    }
+    frontier_append(a, cross, v, b, e, r + 1);
+}
 
 // Parallel Matula-Beck peeling. Level k = smallest remaining degree; within a level,
 // round after round, every remaining vertex of current degree <= k is removed at once
 // and its neighbours' degrees drop. A vertex enters the next round exactly when its
 // degree crosses k + 1 -> k. Each vertex gets core = k and the round it left in.
-__global__ void __launch_bounds__(PEEL_THREADS) k_peel(PeelArgs a) {
+//
+// One block per SM; every phase ends with one grid barrier. A level starts with one
+// phase that compacts the alive list and, at the same time, takes the vertices of
+// degree <= k + 1 as the next frontier (levels are usually consecutive); only when that
+// frontier is empty does a second phase jump to the minimum degree. A round hands light
+// frontier vertices to single warps; heavy ones (hubs) are filed as PEEL_PIECE-entry
+// pieces of their adjacency, one block per piece, so no warp walks a hub alone.
+//
+// Counter discipline: a phase only appends to counters that no block reads before the
+// phase's closing barrier, and only reads counters completed before its opening
+// barrier. Frontier counters rotate over three slots by round number; every new
+// frontier (level start, jump, next round) is filed under round r + 1, so the slot a
+// slow block may still be reading (round r) is never written in the same phase.
+__global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gsize = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = gtid >> 5, nwarps = gsize >> 5;
     int* ctl = a.ctl;
     __shared__ int s_wmin[PEEL_THREADS / 32];
-    int k = 0, r = 0, lvl = 0, ac = 0;
+    int k = -1, r = 0, lvl = 0, ac = 0, rounds = 0;
     int nalive = a.n;
     while (true) {
-        // ---- P1: compact the alive list, find the minimum remaining degree
+        // few vertices left: hand the rest to the single-block tail (all blocks agree,
+        // nalive was read after the same barrier)
+        if (nalive <= a.tail_n) {
+            if (gtid == 0) {
+                ctl[C_TAIL] = 1;
+                ctl[C_TAIL_K] = k;
+                ctl[C_TAIL_R] = r;
+                ctl[C_TAIL_AC] = ac;
+                ctl[C_TAIL_N] = nalive;
+                ctl[C_ROUNDS] = rounds;
+            }
+            return;
+        }
+        // ---- level start: compaction + frontier at k + 1, filed as round r + 1
+        const int kk = k + 1;
         if (gtid == 0) {
             ctl[C_MIN + ((lvl + 1) & 1)] = INT_MAX;
             ctl[C_ACNT + ((lvl + 1) & 1)] = 0;
+            ctl[C_FCNT + (r + 2) % 3] = 0;
+            ctl[C_HCNT + (r + 2) % 3] = 0;
         }
         int lmin = INT_MAX;
-        const int32_t* acur = a.alive[ac];
-        int32_t* anxt = a.alive[ac ^ 1];
-        for (int64_t base = gwarp * 32; base < nalive; base += nwarps * 32) {
-            int64_t i = base + lane;
-            bool keep = false;
-            int32_t v = 0;
-            if (i < nalive) {
-                v = __ldcg(&acur[i]);
-                keep = __ldcg(&a.rnd[v]) < 0;
-                if (keep) lmin = min(lmin, __ldcg(&a.deg[v]));
+        {
+            const int32_t* acur = a.alive[ac];
+            int32_t* anxt = a.alive[ac ^ 1];
+            for (int64_t base = gwarp * 32; base < nalive; base += nwarps * 32) {
+                int64_t i = base + lane;
+                bool keep = false, in = false;
+                int32_t v = 0;
+                int32_t rb = 0, re = 0;
+                if (i < nalive) {
+                    v = __ldcg(&acur[i]);
+                    const int rv = __ldcg(&a.rnd[v]);
+                    const int d = __ldcg(&a.deg[v]);
+                    rb = a.rowptr[v];
+                    re = a.rowptr[v + 1];
+                    if (rv < 0) {
+                        if (d <= kk) {
+                            in = true;
+                            a.rnd[v] = r + 1;
+                            a.core[v] = kk;
+                        } else {
+                            keep = true;
+                            lmin = min(lmin, d);
+                        }
+                    }
+                }
+                frontier_append(a, in, v, rb, re, r + 1);
+                warp_append(keep, v, anxt, &ctl[C_ACNT + (lvl & 1)], a.n, &ctl[C_ERR]);
             }
-            warp_append(keep, v, anxt, &ctl[C_ACNT + (lvl & 1)]);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) lmin = min(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
@@ -296,70 +410,291 @@ __global__ void __launch_bounds__(PEEL_THREADS) k_peel(PeelArgs a) {
             if (bm != INT_MAX) atomicMin(&ctl[C_MIN + (lvl & 1)], bm);
         }
         if (!grid_barrier(ctl, a.timeout_ns)) return;
-        nalive = *(volatile int*)&ctl[C_ACNT + (lvl & 1)];
-        if (nalive == 0) break;
-        int mn = *(volatile int*)&ctl[C_MIN + (lvl & 1)];
-        if (mn > k) k = mn;
+        r += 1;
         ac ^= 1;
-        // ---- P2: the level's first frontier
-        {
+        nalive = *(volatile int*)&ctl[C_ACNT + (lvl & 1)];
+        const int fs = *(volatile int*)&ctl[C_FCNT + r % 3] + *(volatile int*)&ctl[C_HCNT + r % 3];
+        if (fs == 0) {
+            if (nalive == 0) break;
+            // no vertex of degree k + 1: jump to the smallest remaining degree, round r + 1
+            const int kj = *(volatile int*)&ctl[C_MIN + (lvl & 1)];
             const int32_t* al = a.alive[ac];
-            int32_t* F = a.fr[r & 1];
-            if (gtid == 0) ctl[C_FCNT + (r + 1) % 3] = 0;
             for (int64_t base = gwarp * 32; base < nalive; base += nwarps * 32) {
                 int64_t i = base + lane;
                 bool in = false;
                 int32_t v = 0;
+                int32_t rb = 0, re = 0;
                 if (i < nalive) {
                     v = __ldcg(&al[i]);
-                    if (__ldcg(&a.deg[v]) <= k) {
+                    const int d = __ldcg(&a.deg[v]);
+                    rb = a.rowptr[v];
+                    re = a.rowptr[v + 1];
+                    if (d <= kj) {
                         in = true;
-                        a.rnd[v] = r;
-                        a.core[v] = k;
+                        a.rnd[v] = r + 1;
+                        a.core[v] = kj;
                     }
                 }
-                warp_append(in, v, F, &ctl[C_FCNT + r % 3]);
+                frontier_append(a, in, v, rb, re, r + 1);
             }
+            k = kj;
+            if (!grid_barrier(ctl, a.timeout_ns)) return;
+            r += 1;
+        } else {
+            k = kk;
         }
-        if (!grid_barrier(ctl, a.timeout_ns)) return;
-        // ---- P3: rounds at level k
+        // ---- rounds at level k (the first one has a non-empty frontier)
         while (true) {
-            int fs = *(volatile int*)&ctl[C_FCNT + r % 3];
-            if (fs == 0) break;
+            const int fsz = *(volatile int*)&ctl[C_FCNT + r % 3];
+            const int hsz = *(volatile int*)&ctl[C_HCNT + r % 3];
+            if (fsz + hsz == 0) break;
+            if (gtid == 0) {
+                ctl[C_FCNT + (r + 2) % 3] = 0;
+                ctl[C_HCNT + (r + 2) % 3] = 0;
+            }
+            // light vertices: one warp each (at most PEEL_HEAVY / 32 steps)
             const int32_t* F = a.fr[r & 1];
-            int32_t* Fn = a.fr[(r + 1) & 1];
-            if (gtid == 0) ctl[C_FCNT + (r + 2) % 3] = 0;
-            for (int64_t i = gwarp; i < fs; i += nwarps) {
+            for (int64_t i = gwarp; i < fsz; i += nwarps) {
                 int32_t u = __ldcg(&F[i]);
                 int32_t b = a.rowptr[u], e = a.rowptr[u + 1];
-                for (int32_t j0 = b; j0 < e; j0 += 32) {
-                    int32_t j = j0 + lane;
-                    bool cross = false;
-                    int32_t v = 0;
-                    if (j < e) {
-                        v = a.adj[j];
-                        if (__ldcg(&a.rnd[v]) < 0) {
-                            int old = atomicSub(&a.deg[v], 1);
-                            if (old == k + 1) {
-                                cross = true;
-                                a.rnd[v] = r + 1;
-                                a.core[v] = k;
-                            }
-                        }
-                    }
-                    warp_append(cross, v, Fn, &ctl[C_FCNT + (r + 1) % 3]);
-                }
+                for (int32_t j0 = b; j0 < e; j0 += 32) peel_neighbour(a, j0 + lane < e, j0 + lane, k, r);
+            }
+            // heavy vertices: one block per piece of PEEL_PIECE adjacency entries
+            const int64_t* H = a.hr[r & 1];
+            for (int pc = blockIdx.x; pc < hsz; pc += gridDim.x) {
+                const int64_t hp = __ldcg(&H[pc]);
+                const int32_t u = (int32_t)(hp & 0xffffffffll);
+                const int32_t q = (int32_t)(hp >> 32);
+                const int32_t j = a.rowptr[u] + q * PEEL_PIECE + (int32_t)threadIdx.x;
+                peel_neighbour(a, j < a.rowptr[u + 1], j, k, r);
             }
             if (!grid_barrier(ctl, a.timeout_ns)) return;
             r++;
+            rounds++;
         }
         lvl++;
     }
     if (gtid == 0) {
-        ctl[C_ROUNDS] = r;
+        ctl[C_ROUNDS] = rounds;
         ctl[C_ALPHA] = k;
     }
 }
+
+// ================================================================== A3 tail
+
+// The last few levels run in one block on the subgraph induced by the vertices still
+// alive, renumbered 0..NL-1 ("local" ids): degrees, liveness and frontiers live in
+// shared memory and a round ends with __syncthreads instead of a grid barrier.
+constexpr int TAIL_THREADS = 1024;
+constexpr int TAIL_MAX = 12288;  // local ids fit in int16
+
+// Local ids for the vertices of alive[0..nalive) that are still alive.
+__global__ void k_tail_select(const int32_t* __restrict__ alive, int nalive, const int32_t* __restrict__ rnd,
+                              int32_t* __restrict__ L, int32_t* __restrict__ gmap, int* __restrict__ nl) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalive;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v = alive[i];
+        if (rnd[v] < 0) {
+            int li = atomicAdd(nl, 1);
+            L[li] = v;
+            gmap[v] = li;
+        }
+    }
+}
+
+// Local degree (alive neighbours = current degree) and full row length per local id.
+__global__ void k_tail_degrees(const int32_t* __restrict__ L, const int* __restrict__ nl,
+                               const int32_t* __restrict__ deg, const int32_t* __restrict__ rowptr, int tn,
+                               int32_t* __restrict__ ld, int32_t* __restrict__ d0) {
+    const int n = *nl;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < tn; i += gridDim.x * blockDim.x) {
+        if (i < n) {
+            int32_t v = L[i];
+            ld[i] = deg[v];
+            d0[i] = rowptr[v + 1] - rowptr[v];
+        } else {
+            ld[i] = 0;
+            d0[i] = 0;
+        }
+    }
+}
+
+// Entry e of the concatenated full rows of the local vertices (eoff = prefix of d0):
+// alive neighbours go to the owner's local row (order within a row is irrelevant).
+__global__ void k_tail_fill(const int32_t* __restrict__ L, const int32_t* __restrict__ eoff, int tn,
+                            const int32_t* __restrict__ rowptr, const int32_t* __restrict__ adj,
+                            const int32_t* __restrict__ rnd, const int32_t* __restrict__ gmap,
+                            const int32_t* __restrict__ lrow, const int32_t* __restrict__ ld,
+                            int32_t* __restrict__ fillc, int16_t* __restrict__ ladj, int* __restrict__ err) {
+    const int64_t total = eoff[tn];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = tn - 1;  // last owner with eoff[owner] <= e
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (eoff[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        int32_t v = adj[rowptr[L[lo]] + (int32_t)(e - eoff[lo])];
+        if (rnd[v] < 0) {
+            int p = atomicAdd(&fillc[lo], 1);
+            if (p < ld[lo]) ladj[lrow[lo] + p] = (int16_t)gmap[v];
+            else atomicExch(err, 3);  // more alive neighbours than the degree says
+        }
+    }
+}
+
+struct TailArgs {
+    const int* nl;
+    const int32_t* L;
+    const int32_t* ld;
+    const int32_t* lrow;
+    const int16_t* ladj;
+    int32_t* rnd;
+    int32_t* core;
+    int* ctl;
+};
+
+// Block-wide exclusive scan of one value per thread; returns the thread's offset and
+// writes the total to *total. Uses wtot[32].
+__device__ __forceinline__ int block_scan_excl(int v, int* wtot, int* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wtot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int x = wtot[lane], xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += y;
+        }
+        wtot[lane] = xi - x;
+        if (lane == 31) *total = xi;
+    }
+    __syncthreads();
+    return wtot[w] + inc - v;
+}
+
+// The same peeling as k_peel (levels, rounds, k + 1 -> k crossings), on the local
+// subgraph, continuing the level k and round r where the grid kernel stopped.
+__global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int32_t* sdeg = (int32_t*)smem;                        // TAIL_MAX
+    int32_t* srow = sdeg + TAIL_MAX;                       // TAIL_MAX + 1
+    int32_t* spref = srow + TAIL_MAX + 1;                  // TAIL_THREADS + 1
+    int16_t* sF0 = (int16_t*)(spref + TAIL_THREADS + 1);   // TAIL_MAX
+    int16_t* sF1 = sF0 + TAIL_MAX;                         // TAIL_MAX
+    uint8_t* salive = (uint8_t*)(sF1 + TAIL_MAX);          // TAIL_MAX
+    __shared__ int wtot[32];
+    __shared__ int s_cnt[2], s_min, s_total;
+    const int nl = *a.nl;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < nl; i += TAIL_THREADS) {
+        sdeg[i] = a.ld[i];
+        srow[i] = a.lrow[i];
+        salive[i] = 1;
+    }
+    if (tid == 0) srow[nl] = a.lrow[nl];
+    int k = a.ctl[C_TAIL_K], r = a.ctl[C_TAIL_R], rounds = a.ctl[C_ROUNDS];
+    int16_t* F = sF0;
+    int16_t* Fn = sF1;
+    __syncthreads();
+    while (true) {
+        // ---- level start: frontier at k + 1 (or at the minimum degree)
+        if (tid == 0) {
+            s_cnt[0] = 0;
+            s_min = INT_MAX;
+        }
+        __syncthreads();
+        int kk = k + 1;
+        for (int i = tid; i < nl; i += TAIL_THREADS) {
+            if (!salive[i]) continue;
+            int d = sdeg[i];
+            if (d <= kk) {
+                salive[i] = 0;
+                a.rnd[a.L[i]] = r + 1;
+                a.core[a.L[i]] = kk;
+                F[atomicAdd(&s_cnt[0], 1)] = (int16_t)i;
+            } else {
+                atomicMin(&s_min, d);
+            }
+        }
+        __syncthreads();
+        if (s_cnt[0] == 0) {
+            if (s_min == INT_MAX) break;  // nothing left
+            kk = s_min;
+            for (int i = tid; i < nl; i += TAIL_THREADS) {
+                if (salive[i] && sdeg[i] <= kk) {
+                    salive[i] = 0;
+                    a.rnd[a.L[i]] = r + 1;
+                    a.core[a.L[i]] = kk;
+                    F[atomicAdd(&s_cnt[0], 1)] = (int16_t)i;
+                }
+            }
+            __syncthreads();
+        }
+        k = kk;
+        r += 1;
+        // ---- rounds
+        while (true) {
+            const int fsz = s_cnt[0];
+            if (fsz == 0) break;
+            if (tid == 0) s_cnt[1] = 0;
+            for (int c0 = 0; c0 < fsz; c0 += TAIL_THREADS) {
+                const int i = c0 + tid;
+                int u = 0, len = 0;
+                if (i < fsz) {
+                    u = F[i];
+                    len = srow[u + 1] - srow[u];
+                }
+                const int off = block_scan_excl(len, wtot, &s_total);
+                spref[tid] = off;
+                if (tid == TAIL_THREADS - 1) spref[TAIL_THREADS] = s_total;
+                __syncthreads();
+                const int total = s_total;
+                const int nown = min(TAIL_THREADS, fsz - c0);
+                for (int e = tid; e < total; e += TAIL_THREADS) {
+                    int lo = 0, hi = nown - 1;  // last owner with spref[owner] <= e
+                    while (lo < hi) {
+                        int mid = (lo + hi + 1) >> 1;
+                        if (spref[mid] <= e) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    const int uo = F[c0 + lo];
+                    const int v = a.ladj[srow[uo] + (e - spref[lo])];
+                    const int old = atomicSub(&sdeg[v], 1);
+                    if (old == k + 1) {  // a vertex that already left never crosses again
+                        salive[v] = 0;
+                        a.rnd[a.L[v]] = r + 1;
+                        a.core[a.L[v]] = k;
+                        Fn[atomicAdd(&s_cnt[1], 1)] = (int16_t)v;
+                    }
+                }
+                __syncthreads();  // spref and wtot are reused by the next chunk
+            }
+            if (tid == 0) s_cnt[0] = s_cnt[1];
+            __syncthreads();
+            int16_t* tmp = F;
+            F = Fn;
+            Fn = tmp;
+            r++;
+            rounds++;
+        }
+    }
+    if (tid == 0) {
+        a.ctl[C_ROUNDS] = rounds;
+        a.ctl[C_ALPHA] = k;
+    }
+}
+
+constexpr size_t TAIL_SMEM = sizeof(int32_t) * (2 * (size_t)TAIL_MAX + 1 + TAIL_THREADS + 1) +
+                             sizeof(int16_t) * 2 * (size_t)TAIL_MAX + (size_t)TAIL_MAX;
 
 __global__ void k_iota(int32_t* __restrict__ a, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -374,50 +709,43 @@ __device__ __forceinline__ bool rank_less(int32_t u, int32_t v, const int32_t* _
     return ru < rv || (ru == rv && u < v);
 }
 
-// Warp per vertex: number of neighbours later in the degeneracy order.
-__global__ void k_out_degree(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ adj,
-                             const int32_t* __restrict__ rnd, int32_t n, int32_t* __restrict__ outdeg) {
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = gw; u < n; u += nw) {
-        int cnt = 0;
-        for (int32_t j = rowptr[u] + lane; j < rowptr[u + 1]; j += 32) cnt += rank_less((int32_t)u, adj[j], rnd);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        if (lane == 0) outdeg[u] = cnt;
+// Entry j of the adjacency (owner u, neighbour v) is kept as u -> v when v comes later
+// in the degeneracy order.
+__global__ void k_orient_flags(const int32_t* __restrict__ adj_src, const int32_t* __restrict__ adj,
+                               const int32_t* __restrict__ rnd, int64_t n2, int32_t* __restrict__ flag) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n2;
+         j += (int64_t)gridDim.x * blockDim.x)
+        flag[j] = rank_less(adj_src[j], adj[j], rnd);
+}
+
+// Kept entries at their scanned positions: rows stay in ascending neighbour order.
+__global__ void k_orient_fill(const int32_t* __restrict__ adj_src, const int32_t* __restrict__ adj,
+                              const int32_t* __restrict__ adj_eid, const int32_t* __restrict__ flag,
+                              const int32_t* __restrict__ opos, int64_t n2, int32_t* __restrict__ out_nbr,
+                              int32_t* __restrict__ out_eid, int32_t* __restrict__ out_src) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n2;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[j]) continue;
+        int32_t p = opos[j];
+        out_nbr[p] = adj[j];
+        out_eid[p] = adj_eid[j];
+        out_src[p] = adj_src[j];
     }
 }
 
-// Warp per vertex: out-neighbours in ascending id order (the row order), with ids of
-// the static edges and the tail vertex of each oriented edge.
-__global__ void k_out_fill(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ adj,
-                           const int32_t* __restrict__ adj_eid, const int32_t* __restrict__ rnd,
-                           int32_t n, const int32_t* __restrict__ outptr, int32_t* __restrict__ out_nbr,
-                           int32_t* __restrict__ out_eid, int32_t* __restrict__ out_src) {
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = gw; u < n; u += nw) {
-        int32_t w = outptr[u];
-        for (int32_t j0 = rowptr[u]; j0 < rowptr[u + 1]; j0 += 32) {
-            int32_t j = j0 + lane;
-            bool keep = false;
-            int32_t v = 0;
-            if (j < rowptr[u + 1]) {
-                v = adj[j];
-                keep = rank_less((int32_t)u, v, rnd);
-            }
-            unsigned mask = __ballot_sync(0xffffffffu, keep);
-            if (keep) {
-                int32_t p = w + __popc(mask & ((1u << lane) - 1u));
-                out_nbr[p] = v;
-                out_eid[p] = adj_eid[j];
-                out_src[p] = (int32_t)u;
-            }
-            w += __popc(mask);
-        }
+// outptr[u] = opos[rowptr[u]]; also the maximum out-degree.
+__global__ void k_outptr(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ opos, int64_t n,
+                         int32_t* __restrict__ outptr, int* __restrict__ max_out) {
+    int best = 0;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u <= n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        int32_t o = opos[rowptr[u]];
+        outptr[u] = o;
+        if (u < n) best = max(best, opos[rowptr[u + 1]] - o);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(max_out, best);
 }
 
 // ================================================================== A5
@@ -534,11 +862,21 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         sval = alt ? val_alt : val;
     }
     g->perm = graph_alloc<int32_t>(g, mk, s);
-    g->T = graph_alloc<int64_t>(g, mk, s);
+    // 32-bit offsets from tmin when the time range leaves room for the "none" marker
+    g->ts32 = (g->tmax - g->tmin) < (int64_t)0xffffffffll;
+    if (g->ts32) g->T = graph_alloc<uint32_t>(g, mk, s);
+    else g->T = graph_alloc<int64_t>(g, mk, s);
     g->sd = graph_alloc<int32_t>(g, mk, s);
     int32_t* newpair = sc.get<int32_t>(mk + 1);
     int32_t* pscan = sc.get<int32_t>(mk + 1);
-    if (mk > 0) FOLTY_LAUNCH(k_store, grid_for(mk, T), T, 0, s, skey, sval, g->in_t, mk, g->perm, g->T, newpair);
+    if (mk > 0) {
+        if (g->ts32)
+            FOLTY_LAUNCH(k_store<uint32_t>, grid_for(mk, T), T, 0, s, skey, sval, g->in_t, mk, g->tmin, g->perm,
+                         (uint32_t*)g->T, newpair);
+        else
+            FOLTY_LAUNCH(k_store<int64_t>, grid_for(mk, T), T, 0, s, skey, sval, g->in_t, mk, (int64_t)0, g->perm,
+                         (int64_t*)g->T, newpair);
+    }
     exclusive_scan(sc, newpair, pscan, mk);
     const int32_t S = read_i32(g, pscan + mk, s);
     g->S = S;
@@ -560,21 +898,8 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     g->in_t = nullptr;
 
     // ---------------- A2: static CSR
-    int32_t* deg_hi = sc.get<int32_t>((int64_t)n + 1);
-    int32_t* deg_lo = sc.get<int32_t>((int64_t)n + 1);
-    FOLTY_CUDA(cudaMemsetAsync(deg_hi, 0, sizeof(int32_t) * ((size_t)n + 1), s));
-    FOLTY_CUDA(cudaMemsetAsync(deg_lo, 0, sizeof(int32_t) * ((size_t)n + 1), s));
-    if (S > 0) FOLTY_LAUNCH(k_count_degrees, grid_for(S, T), T, 0, s, g->ea, g->eb, S, deg_hi, deg_lo);
-    g->deg = graph_alloc<int32_t>(g, (int64_t)n + 1, s);
-    FOLTY_LAUNCH(k_add, grid_for(n, T), T, 0, s, deg_hi, deg_lo, (int64_t)n, g->deg);
-    int32_t* rowptr = sc.get<int32_t>((int64_t)n + 1);
-    int32_t* hi_start = sc.get<int32_t>((int64_t)n + 1);
-    int32_t* lo_start = sc.get<int32_t>((int64_t)n + 1);
-    exclusive_scan(sc, g->deg, rowptr, n);
-    exclusive_scan(sc, deg_hi, hi_start, n);
-    exclusive_scan(sc, deg_lo, lo_start, n);
-    int32_t* adj = sc.get<int32_t>(2 * (int64_t)S);
-    int32_t* adj_eid = sc.get<int32_t>(2 * (int64_t)S);
+    // static edges are sorted by (a, b); a stable sort by b lists them by (b, a)
+    uint32_t* by_b = nullptr;
     if (S > 0) {
         uint64_t* bk = sc.get<uint64_t>(S);
         uint64_t* bk_alt = sc.get<uint64_t>(S);
@@ -582,9 +907,31 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         uint32_t* bv_alt = sc.get<uint32_t>(S);
         FOLTY_LAUNCH(k_edge_keys_b, grid_for(S, T), T, 0, s, g->eb, S, bk, bv);
         bool alt = radix_sort_pairs(sc, bk, bk_alt, bv, bv_alt, S, nb);
-        FOLTY_LAUNCH(k_fill_adj, grid_for(S, T), T, 0, s, g->ea, g->eb, S, rowptr, deg_lo, hi_start, lo_start,
-                     alt ? bv_alt : bv, adj, adj_eid);
+        by_b = alt ? bv_alt : bv;
     }
+    int32_t* runs = sc.get<int32_t>(4 * ((int64_t)n + 1));  // hi_first, hi_last, lo_first, lo_last
+    int32_t* hi_first = runs;
+    int32_t* hi_last = runs + (n + 1);
+    int32_t* lo_first = runs + 2 * ((int64_t)n + 1);
+    int32_t* lo_last = runs + 3 * ((int64_t)n + 1);
+    FOLTY_CUDA(cudaMemsetAsync(runs, 0, sizeof(int32_t) * 4 * ((size_t)n + 1), s));
+    if (S > 0) {
+        FOLTY_LAUNCH(k_runs, grid_for(S, T), T, 0, s, g->ea, (const uint32_t*)nullptr, S, hi_first, hi_last);
+        FOLTY_LAUNCH(k_runs, grid_for(S, T), T, 0, s, g->eb, by_b, S, lo_first, lo_last);
+    }
+    int32_t* deg_lo = sc.get<int32_t>((int64_t)n + 1);
+    g->deg = graph_alloc<int32_t>(g, (int64_t)n + 1, s);
+    FOLTY_LAUNCH(k_degrees, grid_for(n, T), T, 0, s, hi_first, hi_last, lo_first, lo_last, (int64_t)n, deg_lo,
+                 g->deg);
+    int32_t* rowptr = sc.get<int32_t>((int64_t)n + 1);
+    exclusive_scan(sc, g->deg, rowptr, n);
+    const int64_t n2 = 2 * (int64_t)S;
+    int32_t* adj = sc.get<int32_t>(n2);
+    int32_t* adj_eid = sc.get<int32_t>(n2);
+    int32_t* adj_src = sc.get<int32_t>(n2);
+    if (S > 0)
+        FOLTY_LAUNCH(k_fill_adj, grid_for(S, T), T, 0, s, g->ea, g->eb, S, rowptr, deg_lo, hi_first, lo_first,
+                     by_b, adj, adj_eid, adj_src);
 
     // ---------------- A3: peeling
     int32_t* core = sc.get<int32_t>(n);
@@ -603,8 +950,12 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         pa.alive[1] = sc.get<int32_t>(n);
         pa.fr[0] = sc.get<int32_t>(n);
         pa.fr[1] = sc.get<int32_t>(n);
+        pa.hcap = (int32_t)((int64_t)n + (2 * (int64_t)S) / PEEL_PIECE + 1);
+        pa.hr[0] = sc.get<int64_t>(pa.hcap);
+        pa.hr[1] = sc.get<int64_t>(pa.hcap);
         pa.ctl = sc.get<int>(C_SLOTS);
         pa.timeout_ns = 10ll * 1000 * 1000 * 1000;
+        pa.tail_n = TAIL_MAX;
         int init[C_SLOTS] = {0};
         init[C_MIN] = INT_MAX;
         init[C_MIN + 1] = INT_MAX;
@@ -615,46 +966,81 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         int per_sm = 0;
         FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel, PEEL_THREADS, 0));
         if (per_sm < 1) fail(FOLTY_ECUDA, "peeling kernel cannot be resident");
-        if (per_sm > 4) per_sm = 4;
+        if (per_sm > 1) per_sm = 1;
         dim3 grid(num_sms() * per_sm), block(PEEL_THREADS);
         void* args[] = {&pa};
         if (n > 0) {
             FOLTY_CUDA(cudaLaunchCooperativeKernel((const void*)k_peel, grid, block, args, 0, s));
             after_launch("k_peel");
         }
-        const void* ptrs[3] = {pa.ctl + C_ERR, pa.ctl + C_ROUNDS, pa.ctl + C_ALPHA};
-        int sizes[3] = {4, 4, 4};
-        int64_t outv[3];
-        read_back(g, ptrs, sizes, 3, outv, s);
+        const void* ptrs[5] = {pa.ctl + C_ERR, pa.ctl + C_TAIL, pa.ctl + C_TAIL_AC, pa.ctl + C_TAIL_N,
+                               pa.ctl + C_ALPHA};
+        int sizes[5] = {4, 4, 4, 4, 4};
+        int64_t outv[5];
+        read_back(g, ptrs, sizes, 5, outv, s);
+        if (n > 0 && outv[0] == 2) fail(FOLTY_ECUDA, "peeling: a vertex list overflowed (internal error)");
         if (n > 0 && outv[0] != 0) fail(FOLTY_ETIMEOUT, "peeling: a grid barrier wait ran out");
-        g->info.peel_rounds = (int32_t)(n > 0 ? outv[1] : 0);
-        g->info.degeneracy = (int32_t)(n > 0 ? outv[2] : 0);
+        if (n > 0 && outv[1] == 1) {
+            // single-block tail on the induced subgraph of the remaining vertices
+            const int nalive = (int)outv[3];
+            const int32_t* alive = pa.alive[outv[2]];
+            const int tn = TAIL_MAX;
+            int32_t* L = sc.get<int32_t>(tn);
+            int32_t* gmap = sc.get<int32_t>(n);
+            int* nl = sc.get<int>(1);
+            int32_t* ld = sc.get<int32_t>(tn + 1);
+            int32_t* d0 = sc.get<int32_t>(tn + 1);
+            int32_t* lrow = sc.get<int32_t>(tn + 1);
+            int32_t* eoff = sc.get<int32_t>(tn + 1);
+            int32_t* fillc = sc.get<int32_t>(tn);
+            int16_t* ladj = sc.get<int16_t>(2 * (int64_t)S);
+            FOLTY_CUDA(cudaMemsetAsync(nl, 0, sizeof(int), s));
+            FOLTY_CUDA(cudaMemsetAsync(fillc, 0, sizeof(int32_t) * (size_t)tn, s));
+            FOLTY_LAUNCH(k_tail_select, grid_for(nalive, T), T, 0, s, alive, nalive, rnd, L, gmap, nl);
+            FOLTY_LAUNCH(k_tail_degrees, grid_for(tn, T), T, 0, s, L, nl, pa.deg, rowptr, tn, ld, d0);
+            exclusive_scan(sc, ld, lrow, tn);
+            exclusive_scan(sc, d0, eoff, tn);
+            FOLTY_LAUNCH(k_tail_fill, grid_for(2 * (int64_t)S, T), T, 0, s, L, eoff, tn, rowptr, adj, rnd, gmap,
+                         lrow, ld, fillc, ladj, pa.ctl + C_ERR);
+            TailArgs ta{nl, L, ld, lrow, ladj, rnd, core, pa.ctl};
+            FOLTY_CUDA(cudaFuncSetAttribute(k_peel_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TAIL_SMEM));
+            FOLTY_LAUNCH(k_peel_tail, 1, TAIL_THREADS, TAIL_SMEM, s, ta);
+        }
+        const void* ptrs2[3] = {pa.ctl + C_ROUNDS, pa.ctl + C_ALPHA, pa.ctl + C_ERR};
+        int sizes2[3] = {4, 4, 4};
+        int64_t outv2[3];
+        read_back(g, ptrs2, sizes2, 3, outv2, s);
+        if (n > 0 && outv2[2] != 0) fail(FOLTY_ECUDA, "peeling: inconsistent degrees in the tail (internal error)");
+        g->info.peel_rounds = (int32_t)(n > 0 ? outv2[0] : 0);
+        g->info.degeneracy = (int32_t)(n > 0 ? outv2[1] : 0);
     }
 
     // ---------------- A4: orientation
-    int32_t* outdeg = sc.get<int32_t>((int64_t)n + 1);
+    int* stat = sc.get<int>(4);  // max degree, max out-degree, max sigma, (pad)
+    FOLTY_CUDA(cudaMemsetAsync(stat, 0, sizeof(int) * 4, s));
+    int32_t* oflag = sc.get<int32_t>(n2 + 1);
+    int32_t* opos = sc.get<int32_t>(n2 + 1);
+    if (n2 > 0) FOLTY_LAUNCH(k_orient_flags, grid_for(n2, T), T, 0, s, adj_src, adj, rnd, n2, oflag);
+    exclusive_scan(sc, oflag, opos, n2);
     int32_t* outptr = sc.get<int32_t>((int64_t)n + 1);
-    FOLTY_LAUNCH(k_out_degree, grid_for((int64_t)n * 32, T), T, 0, s, rowptr, adj, rnd, n, outdeg);
-    exclusive_scan(sc, outdeg, outptr, n);
+    FOLTY_LAUNCH(k_outptr, grid_for((int64_t)n + 1, T), T, 0, s, rowptr, opos, (int64_t)n, outptr, stat + 1);
     int32_t* out_nbr = sc.get<int32_t>(S);
     int32_t* out_eid = sc.get<int32_t>(S);
     int32_t* out_src = sc.get<int32_t>(S);
-    FOLTY_LAUNCH(k_out_fill, grid_for((int64_t)n * 32, T), T, 0, s, rowptr, adj, adj_eid, rnd, n, outptr,
-                 out_nbr, out_eid, out_src);
+    if (n2 > 0)
+        FOLTY_LAUNCH(k_orient_fill, grid_for(n2, T), T, 0, s, adj_src, adj, adj_eid, oflag, opos, n2, out_nbr,
+                     out_eid, out_src);
 
     // ---------------- A5: triangles
     g->common = graph_alloc<int32_t>(g, S, s);
     FOLTY_CUDA(cudaMemsetAsync(g->common, 0, sizeof(int32_t) * ((size_t)S > 0 ? (size_t)S : 1), s));
     int32_t* tcnt = sc.get<int32_t>((int64_t)S + 1);
     int64_t* toff = sc.get<int64_t>((int64_t)S + 1);
-    int* stat = sc.get<int>(4);  // max degree, max out-degree, max sigma, (pad)
     unsigned long long* merged = sc.get<unsigned long long>(1);
-    FOLTY_CUDA(cudaMemsetAsync(stat, 0, sizeof(int) * 4, s));
     FOLTY_CUDA(cudaMemsetAsync(merged, 0, sizeof(unsigned long long), s));
     if (S > 0) FOLTY_LAUNCH(k_tri_count, grid_for(S, T), T, 0, s, outptr, out_nbr, out_src, S, tcnt, merged);
     exclusive_scan(sc, tcnt, toff, S);
     FOLTY_LAUNCH(k_max_i32, grid_for(n, T), T, 0, s, g->deg, (int64_t)n, stat + 0);
-    FOLTY_LAUNCH(k_max_i32, grid_for(n, T), T, 0, s, outdeg, (int64_t)n, stat + 1);
     if (S > 0) FOLTY_LAUNCH(k_max_sigma, grid_for(S, T), T, 0, s, g->seg, S, stat + 2);
     {
         const void* ptrs[5] = {toff + S, stat + 0, stat + 1, stat + 2, merged};

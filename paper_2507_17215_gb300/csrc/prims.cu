@@ -2,7 +2,7 @@
 //
 // Both are bandwidth-bound streaming passes: tiles of 2048 (scan) or 4096 (sort)
 // elements per 256-thread block, coalesced loads, block offsets from a recursive scan
-// of per-tile totals.
+// of per-tile totals. The sort takes 11-bit digits (a 41-bit key in 4 passes).
 #include "internal.cuh"
 
 namespace folty {
@@ -130,7 +130,7 @@ constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 4096 keys per block
-constexpr int RS_BITS = 8;
+constexpr int RS_BITS = 11;
 constexpr int RS_BINS = 1 << RS_BITS;
 
 // Per-tile digit histogram, stored digit-major: hist[d * nblocks + block].
@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __res
                                                            int shift,
                                                            const uint32_t* __restrict__ offs,
                                                            int nblocks) {
-    __shared__ uint32_t wh[RS_WARPS][RS_BINS];
+    // per-warp digit counts and offsets; at most RS_TILE = 4096 keys per block, so 16 bits
+    __shared__ uint16_t wh[RS_WARPS][RS_BINS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&wh[0][0])[i] = 0;
     __syncthreads();
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __res
         unsigned before = 0;
         if (valid) before = wh[warp][d];
         __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) wh[warp][d] = before + __popc(peers);
+        if (valid && lane == __ffs(peers) - 1) wh[warp][d] = (uint16_t)(before + __popc(peers));
         __syncwarp();
         rank[i] = before + __popc(peers & lt_mask);
     }
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __res
 #pragma unroll
         for (int w = 0; w < RS_WARPS; w++) {
             uint32_t c = wh[w][d];
-            wh[w][d] = run;
+            wh[w][d] = (uint16_t)run;
             run += c;
         }
     }

@@ -23,25 +23,27 @@ namespace folty {
 // (triangle-major, then the triangle's three static edges, then their sorted temporal
 // edges). The block stages the triangles overlapping its range in shared memory,
 // threads take consecutive probes (coalesced T reads and counter updates).
+template <typename TS, int DIR>
 __global__ void __launch_bounds__(PB_THREADS) k_probe(const int4* __restrict__ tri,
                                                       const int64_t* __restrict__ tri_off,
                                                       const int64_t* __restrict__ tile_tri, int64_t P,
                                                       const int32_t* __restrict__ seg,
-                                                      const int64_t* __restrict__ T, int64_t delta,
-                                                      int dir, int32_t* __restrict__ cnt) {
+                                                      const TS* __restrict__ T, TS delta,
+                                                      int32_t* __restrict__ cnt) {
     __shared__ TriStage st;
     const int64_t p0 = (int64_t)blockIdx.x * PB_TILE;
-    const int64_t p1 = min(P, p0 + PB_TILE);
-    stage_triangles(st, tri, tri_off, tile_tri, seg);
+    const int32_t count = (int32_t)min((int64_t)PB_TILE, P - p0);
+    stage_triangles(st, tri, tri_off, tile_tri, seg, DIR);
 #pragma unroll 1
     for (int it = 0; it < PB_ITEMS; it++) {
-        int64_t p = p0 + (int64_t)it * PB_THREADS + threadIdx.x;
-        if (p >= p1) break;
-        Probe pr = locate_probe(st, p);
-        Lists L = role_lists(st.off[pr.j], st.flags[pr.j], pr.e, pr.d, dir);
-        int64_t t = T[pr.pos];
-        int64_t t3 = probe_window(T, t, L);
-        if (t3 != PROBE_NONE && t3 - t <= delta) atomicAdd(&cnt[pr.pos], 1);
+        const int32_t local = it * PB_THREADS + (int32_t)threadIdx.x;
+        if ((local & ~31) >= count) break;  // warp-uniform
+        const bool active = local < count;
+        Probe pr = locate_probe(st, local, active);
+        if (!active) continue;
+        const TS t = T[pr.pos];
+        const TS t3 = probe_window<TS, DIR>(T, st.off[pr.j], pr.seg2, pr.seg3, t, delta);
+        if (t3 != TsNone<TS>::value && (TS)(t3 - t) <= delta) atomicAdd(&cnt[pr.pos], 1);
     }
 }
 
@@ -152,13 +154,26 @@ void validate_query(const folty_query_params& q) {
     if (q.universe > FOLTY_U_COMMON) fail(FOLTY_EINVAL, "unknown universe");
 }
 
+template <typename TS, int DIR>
+static void launch_probe_t(folty_graph* g, TS delta, int32_t* cnt, cudaStream_t s) {
+    FOLTY_LAUNCH((k_probe<TS, DIR>), (unsigned)g->n_tiles, PB_THREADS, 0, s, g->tri, g->tri_off, g->tile_tri,
+                 g->info.probes, g->seg, (const TS*)g->T, delta, cnt);
+}
+
 void launch_probe(folty_graph* g, int64_t delta, int dir, int32_t* cnt, cudaStream_t s) {
-    const int64_t P = g->info.probes;
-    if (P <= 0) return;
-    int64_t blocks = (P + PB_TILE - 1) / PB_TILE;
-    if (blocks > 0x7fffffffll) fail(FOLTY_EINVAL, "probe space too large");
-    FOLTY_LAUNCH(k_probe, (unsigned)blocks, PB_THREADS, 0, s, g->tri, g->tri_off, g->tile_tri, P, g->seg,
-                 g->T, delta, dir, cnt);
+    if (g->info.probes <= 0) return;
+    if (g->n_tiles > 0x7fffffffll) fail(FOLTY_EINVAL, "probe space too large");
+    if (g->ts32) {
+        // every gap is below 2^32 - 1, so larger windows behave as 2^32 - 2
+        const uint32_t d = delta >= 0xfffffffell ? 0xfffffffeu : (uint32_t)delta;
+        if (dir == FOLTY_DIR_OUT) launch_probe_t<uint32_t, FOLTY_DIR_OUT>(g, d, cnt, s);
+        else if (dir == FOLTY_DIR_IN) launch_probe_t<uint32_t, FOLTY_DIR_IN>(g, d, cnt, s);
+        else launch_probe_t<uint32_t, FOLTY_DIR_EITHER>(g, d, cnt, s);
+    } else {
+        if (dir == FOLTY_DIR_OUT) launch_probe_t<int64_t, FOLTY_DIR_OUT>(g, delta, cnt, s);
+        else if (dir == FOLTY_DIR_IN) launch_probe_t<int64_t, FOLTY_DIR_IN>(g, delta, cnt, s);
+        else launch_probe_t<int64_t, FOLTY_DIR_EITHER>(g, delta, cnt, s);
+    }
 }
 
 // Threshold + pair output for counts cnt[m_kept] (sorted order). Allocates and fills
@@ -232,10 +247,11 @@ void run_query(folty_graph* g, const folty_query_params& q, folty_result* out, c
 // ================================================================== traffic model
 
 // Per role (x, y; witness z): sigma1 = |E_{x,y}|, sigma2, sigma3 = the sizes of L2, L3
-// for the direction variant. Bytes = 8 sigma1 (read L1) + 8 min(sigma2, sigma1 *
-// ceil(log2(sigma2 + 1))) + the same for L3 + 8 sigma1 (counter read-modify-write).
+// for the direction variant, w = bytes per stored timestamp. Bytes = w sigma1 (read L1)
+// + w min(sigma2, sigma1 * ceil(log2(sigma2 + 1))) + the same for L3 + 8 sigma1
+// (counter read-modify-write).
 __global__ void k_traffic(const int4* __restrict__ tri, int64_t ntri, const int32_t* __restrict__ seg, int dir,
-                          unsigned long long* __restrict__ out) {
+                          int64_t w, unsigned long long* __restrict__ out) {
     unsigned long long acc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ntri;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -254,12 +270,14 @@ __global__ void k_traffic(const int4* __restrict__ tri, int64_t ntri, const int3
             for (int d = 0; d < 2; d++) {
                 int64_t s1 = off[3 * e + d + 1] - off[3 * e + d];
                 if (s1 == 0) continue;
-                Lists L = role_lists(off, tr.w, e, d, dir);
-                int64_t s2 = (int64_t)(L.e2 - L.b2) + (L.e2b - L.b2b);
-                int64_t s3 = (int64_t)(L.e3 - L.b3) + (L.e3b - L.b3b);
+                int c2, c3;
+                role_segments(tr.w, e, d, dir, c2, c3);
+                const int o2 = 3 * (c2 >> 1) + (c2 & 1), o3 = 3 * (c3 >> 1) + (c3 & 1);
+                int64_t s2 = dir == FOLTY_DIR_EITHER ? off[o2 + 2] - off[o2] : off[o2 + 1] - off[o2];
+                int64_t s3 = dir == FOLTY_DIR_EITHER ? off[o3 + 2] - off[o3] : off[o3 + 1] - off[o3];
                 int64_t l2 = 64 - __clzll((unsigned long long)s2);
                 int64_t l3 = 64 - __clzll((unsigned long long)s3);
-                acc += 8 * s1 + 8 * min(s2, s1 * l2) + 8 * min(s3, s1 * l3) + 8 * s1;
+                acc += w * s1 + w * min(s2, s1 * l2) + w * min(s3, s1 * l3) + 8 * s1;
             }
         }
     }
@@ -272,7 +290,9 @@ void traffic_model(folty_graph* g, int dir, folty_traffic_model* out, cudaStream
     Scratch sc(g->alloc, s);
     unsigned long long* acc = sc.get<unsigned long long>(1);
     FOLTY_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long), s));
-    if (g->ntri > 0) FOLTY_LAUNCH(k_traffic, grid_for(g->ntri, 256), 256, 0, s, g->tri, g->ntri, g->seg, dir, acc);
+    if (g->ntri > 0)
+        FOLTY_LAUNCH(k_traffic, grid_for(g->ntri, 256), 256, 0, s, g->tri, g->ntri, g->seg, dir,
+                     (int64_t)(g->ts32 ? 4 : 8), acc);
     out->probe_bytes = read_i64(g, (const int64_t*)acc, s);
     out->enum_bytes = g->enum_bytes;
     out->threshold_bytes = 4 * g->m_kept + 12 * 2 * (int64_t)g->S;
