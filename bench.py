@@ -189,6 +189,44 @@ def replica_throughput(units_per_rank: int, world: int, seconds_max: float) -> f
 
 # ----------------------------------------------------------------------------- GPU arm
 
+def measure_batch(F, g, d_src, d_dst, d_t, sh, nq, stream, reps=3):
+    """nq mixed queries (delta log-uniform on [60 s, 7 d], rho = k/10, quantifier and
+    direction uniform) on the preprocessed graph: folty_query_batch against nq
+    back-to-back folty_query calls, results compared pair list by pair list."""
+    import torch
+    rng = np.random.default_rng(4)
+    qs = W.random_query_mix(nq, rng)
+    h = F.folty_load_temporal_graph(g.n, d_src, d_dst, d_t, stream=sh)
+    try:
+        F.folty_preprocess(h, sh)
+        F.folty_query_batch(h, qs, sh)  # warm-up (allocator, module load)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        batch_ms = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            res_b = F.folty_query_batch(h, qs, sh)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            batch_ms.append(ev[0].elapsed_time(ev[1]))
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        res_s = [F.folty_query(h, q, sh) for q in qs]
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        seq_ms = ev[0].elapsed_time(ev[1])
+    finally:
+        F.folty_free(h)
+    same = all(a["n_cert_edges"] == b["n_cert_edges"] and all(np.array_equal(a[k], b[k]) for k in
+               ("u", "v", "count", "ncert")) for a, b in zip(res_b, res_s))
+    bm = float(np.median(batch_ms))
+    return {"queries": nq, "workload": "medium graph, mixed queries (delta log-uniform 60 s..7 d, "
+            "rho k/10, exists/forall, out/in/either, universe N(u))",
+            "batch_ms": bm, "sequential_ms": seq_ms, "speedup": seq_ms / bm,
+            "edges_per_s": nq * g.m / (bm / 1e3), "results_equal": bool(same),
+            "solution_pairs_total": int(sum(len(r["u"]) for r in res_b))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -200,6 +238,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=4.0,
                     help="seconds of sampled oracle evaluation per step")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (debug only)")
+    ap.add_argument("--batch", type=int, default=256,
+                    help="queries of the batched measurement (0 = skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -277,6 +317,11 @@ def main():
     t_ms = max_over_ranks(ev0.elapsed_time(ev1), world, "cuda")
     value = replica_throughput(args.steps * len(queries) * g.m, world, t_ms / 1e3)
 
+    # ---- batched queries: 256 mixed queries on the same graph vs one at a time
+    batched = None
+    if args.batch > 0:
+        batched = measure_batch(F, g, d_src, d_dst, d_t, sh, args.batch, stream)
+
     # ---- end-to-end through the C ABI from pinned host buffers
     ke = args.e2e_steps or args.steps
     barrier()
@@ -313,6 +358,7 @@ def main():
                      "kernel": "k_probe", "peak_kind": f"{peak_kind} hbm_gbs",
                      "model_bytes_per_launch": tm["probe_bytes"]},
         "clocks": clk,
+        "batched": batched,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         step_s, sample, cores = oracle_sample_time(g, queries, budget_s=args.ref_budget)

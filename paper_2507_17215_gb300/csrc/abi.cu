@@ -97,7 +97,7 @@ void graph_release(folty_graph* g, void* p, cudaStream_t s) {
 
 void read_back(folty_graph* g, const void* const* dev_ptrs, const int* sizes, int count, int64_t* out,
                cudaStream_t s) {
-    if (count > 32) fail(FOLTY_EINVAL, "read_back: too many values");
+    if (count > READBACK_MAX) fail(FOLTY_EINVAL, "read_back: too many values");
     for (int i = 0; i < count; i++)
         FOLTY_CUDA(cudaMemcpyAsync(g->host_stage + i, dev_ptrs[i], (size_t)sizes[i], cudaMemcpyDeviceToHost, s));
     FOLTY_CUDA(cudaStreamSynchronize(s));
@@ -222,8 +222,8 @@ static void load_graph(folty_graph* g, const int32_t* src, const int32_t* dst, c
     Scratch sc(g->alloc, s);
     unsigned long long* stat = sc.get<unsigned long long>(5);
     unsigned long long init[5] = {~0ull, ~0ull, 0ull, 0ull, 0ull};
-    std::memcpy(g->host_stage + 32, init, sizeof(init));
-    FOLTY_CUDA(cudaMemcpyAsync(stat, g->host_stage + 32, sizeof(init), cudaMemcpyHostToDevice, s));
+    std::memcpy(g->host_stage + READBACK_MAX, init, sizeof(init));
+    FOLTY_CUDA(cudaMemcpyAsync(stat, g->host_stage + READBACK_MAX, sizeof(init), cudaMemcpyHostToDevice, s));
     if (m > 0) FOLTY_LAUNCH(k_validate, grid_for(m, 256), 256, 0, s, g->in_src, g->in_dst, g->in_t, m, g->n, stat);
     const void* ptrs[5] = {stat, stat + 1, stat + 2, stat + 3, stat + 4};
     int sizes[5] = {8, 8, 8, 8, 8};
@@ -290,7 +290,7 @@ folty_status folty_load_temporal_graph(int32_t n, int64_t m, const int32_t* src,
             g->alloc.user = true;
         }
         FOLTY_CUDA(cudaGetDevice(&g->device));
-        FOLTY_CUDA(cudaMallocHost((void**)&g->host_stage, 64 * sizeof(int64_t)));
+        FOLTY_CUDA(cudaMallocHost((void**)&g->host_stage, HOST_STAGE * sizeof(int64_t)));
         g->n = n;
         g->m = m;
         load_graph(g, src, dst, t, s);

@@ -134,12 +134,18 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
                 FOLTY_CUDA(cudaStreamSynchronize(s));  // the host bounds must outlive the copy
                 timer.collect();
             }
+            std::vector<const folty_query_params*> fq;
+            std::vector<const int32_t*> fc;
+            std::vector<folty_result*> fo;
             for (int i : members) {
                 auto it = std::lower_bound(hd.begin(), hd.end(), qs[i].delta);
                 if (it == hd.end() || *it != qs[i].delta) continue;  // another chunk
                 const int j = (int)(it - hd.begin());
-                finish_query(g, qs[i], bins + (int64_t)j * mk, &outs[i], s);
+                fq.push_back(&qs[i]);
+                fc.push_back(bins + (int64_t)j * mk);
+                fo.push_back(&outs[i]);
             }
+            finish_queries(g, fq.data(), fc.data(), (int)fq.size(), fo.data(), s);
         }
     }
 }

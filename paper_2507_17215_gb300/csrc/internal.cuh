@@ -99,6 +99,8 @@ class Scratch {
 
 // ------------------------------------------------------------------ the graph
 
+constexpr int HOST_STAGE = 512;      // pinned int64 slots per graph
+constexpr int READBACK_MAX = 384;    // slots [0, READBACK_MAX) serve read_back
 constexpr uint64_t GRAPH_TAG = 0x464f4c5459475248ull;   // "FOLTYGRH"
 constexpr uint64_t RESULT_TAG = 0x464f4c5459525354ull;  // "FOLTYRST"
 constexpr uint64_t FREED_TAG = 0x464f4c5459465245ull;   // "FOLTYFRE"
@@ -131,6 +133,7 @@ struct folty_graph {
     int32_t* eb;      // [S] larger endpoint b
     int32_t* deg;     // [n] |N(u)|
     int32_t* common;  // [S] |N(a) cap N(b)| = triangles on the static edge
+    int32_t* by_b;    // [S] static edge ids ordered by (b, a)
     int64_t ntri;
     int4* tri;        // [ntri] {s_uv, s_uw, s_vw, id-order bits}, u < v < w in degeneracy rank
     int64_t* tri_off; // [ntri + 1] prefix of per-triangle probe counts
@@ -141,7 +144,7 @@ struct folty_graph {
     // ---- statistics
     folty_graph_info info;
     // ---- pinned host staging for small device->host reads
-    int64_t* host_stage;  // 64 entries
+    int64_t* host_stage;  // HOST_STAGE entries
     std::vector<void*>* owned;  // device buffers owned by the graph
 };
 
@@ -201,6 +204,10 @@ void edge_counts_noalloc(folty_graph* g, int64_t delta, int dir, int32_t* edge_c
 // order); synchronises the stream.
 void finish_query(folty_graph* g, const folty_query_params& q, const int32_t* cnt, folty_result* out,
                   cudaStream_t s);
+// The same for nq queries at once (counts cnts[i]), with two stream synchronisations
+// for the whole group.
+void finish_queries(folty_graph* g, const folty_query_params* const* qs, const int32_t* const* cnts, int nq,
+                    folty_result* const* outs, cudaStream_t s);
 
 // Event pair around probe launches when profiling is on (abi.cu holds the totals).
 class ProbeTimer {

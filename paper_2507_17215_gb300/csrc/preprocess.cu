@@ -909,6 +909,8 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         bool alt = radix_sort_pairs(sc, bk, bk_alt, bv, bv_alt, S, nb);
         by_b = alt ? bv_alt : bv;
     }
+    g->by_b = graph_alloc<int32_t>(g, S, s);
+    if (S > 0) FOLTY_CUDA(cudaMemcpyAsync(g->by_b, by_b, sizeof(int32_t) * (size_t)S, cudaMemcpyDeviceToDevice, s));
     int32_t* runs = sc.get<int32_t>(4 * ((int64_t)n + 1));  // hi_first, hi_last, lo_first, lo_last
     int32_t* hi_first = runs;
     int32_t* hi_last = runs + (n + 1);
@@ -959,7 +961,7 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         int init[C_SLOTS] = {0};
         init[C_MIN] = INT_MAX;
         init[C_MIN + 1] = INT_MAX;
-        int* init_dev = (int*)(g->host_stage + 48);  // pinned staging
+        int* init_dev = (int*)(g->host_stage + READBACK_MAX + 16);  // pinned staging
         std::memcpy(init_dev, init, sizeof(init));
         FOLTY_CUDA(cudaMemcpyAsync(pa.ctl, init_dev, sizeof(init), cudaMemcpyHostToDevice, s));
         FOLTY_LAUNCH(k_iota, grid_for(n, T), T, 0, s, pa.alive[0], (int64_t)n);

@@ -10,6 +10,7 @@
 //       once), so c_e counts distinct witnesses;
 //   A8  certificate test per edge, max c_e and certificate count per directed pair,
 //       compaction of the solution pairs and a sort by (u, v).
+#include <algorithm>
 #include <climits>
 
 #include "internal.cuh"
@@ -103,37 +104,71 @@ __global__ void k_threshold(ThresholdArgs a) {
     if (lane == 0 && my_cert) atomicAdd(a.n_cert, my_cert);
 }
 
-__global__ void k_pair_flags(const int32_t* __restrict__ seg_ncert, int64_t n2, int32_t* __restrict__ flag) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n2;
-         j += (int64_t)gridDim.x * blockDim.x)
-        flag[j] = seg_ncert[j] > 0;
+// Solution pairs come in two lists that are already sorted by (x, y): pairs x < y in
+// static-edge order (sorted by (a, b)), and pairs x > y in by_b order (sorted by (b, a)).
+// Entry i < S of the flag array is static edge i's a -> b direction, entry S + j is the
+// b -> a direction of static edge by_b[j].
+__global__ void k_pair_flags(const int32_t* __restrict__ seg_ncert, const int32_t* __restrict__ by_b, int64_t S,
+                             int32_t* __restrict__ flag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * S;
+         i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = (i < S) ? (seg_ncert[2 * i] > 0) : (seg_ncert[2 * (int64_t)by_b[i - S] + 1] > 0);
 }
 
-__global__ void k_pair_keys(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t n2,
-                            const int32_t* __restrict__ ea, const int32_t* __restrict__ eb, int nb,
-                            uint64_t* __restrict__ key, uint32_t* __restrict__ val) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n2;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        if (!flag[j]) continue;
-        int32_t s = (int32_t)(j >> 1), d = (int32_t)(j & 1);
-        uint64_t x = (uint64_t)(d ? eb[s] : ea[s]), y = (uint64_t)(d ? ea[s] : eb[s]);
-        key[pos[j]] = (x << nb) | y;
-        val[pos[j]] = (uint32_t)j;
+// Compacts both lists: key (x, y), max count and certificates of each solution pair.
+__global__ void k_pair_compact(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t S,
+                               const int32_t* __restrict__ ea, const int32_t* __restrict__ eb,
+                               const int32_t* __restrict__ by_b, const int32_t* __restrict__ seg_max,
+                               const int32_t* __restrict__ seg_ncert, uint64_t* __restrict__ key,
+                               int32_t* __restrict__ cnt_c, int32_t* __restrict__ nc_c) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * S;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[i]) continue;
+        int64_t sdir;
+        uint64_t x, y;
+        if (i < S) {
+            sdir = 2 * i;
+            x = (uint64_t)ea[i];
+            y = (uint64_t)eb[i];
+        } else {
+            const int32_t st = by_b[i - S];
+            sdir = 2 * (int64_t)st + 1;
+            x = (uint64_t)eb[st];
+            y = (uint64_t)ea[st];
+        }
+        const int32_t p = pos[i];
+        key[p] = (x << 32) | y;
+        cnt_c[p] = seg_max[sdir];
+        nc_c[p] = seg_ncert[sdir];
     }
 }
 
-__global__ void k_pair_out(const uint64_t* __restrict__ key, const uint32_t* __restrict__ val, int64_t np,
-                           int nb, const int32_t* __restrict__ seg_max, const int32_t* __restrict__ seg_ncert,
-                           int32_t* __restrict__ out) {
-    const uint64_t mask = (1ull << nb) - 1;
+__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* __restrict__ a, int64_t n, uint64_t key) {
+    int64_t lo = 0;
+    while (n > 0) {
+        int64_t half = n >> 1;
+        if (a[lo + half] < key) {
+            lo += half + 1;
+            n -= half + 1;
+        } else {
+            n = half;
+        }
+    }
+    return lo;
+}
+
+// Merge by rank: an entry's place in the output is its index in its own list plus the
+// number of entries of the other list with a smaller key (keys of the lists differ).
+__global__ void k_pair_merge(const uint64_t* __restrict__ key, const int32_t* __restrict__ cnt_c,
+                             const int32_t* __restrict__ nc_c, int64_t nA, int64_t np, int32_t* __restrict__ out) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
          p += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t k = key[p];
-        uint32_t j = val[p];
-        out[p] = (int32_t)(k >> nb);
-        out[np + p] = (int32_t)(k & mask);
-        out[2 * np + p] = seg_max[j];
-        out[3 * np + p] = seg_ncert[j];
+        const uint64_t k = key[p];
+        const int64_t f = (p < nA) ? p + lower_bound_u64(key + nA, np - nA, k) : (p - nA) + lower_bound_u64(key, nA, k);
+        out[f] = (int32_t)(k >> 32);
+        out[np + f] = (int32_t)(k & 0xffffffffull);
+        out[2 * np + f] = cnt_c[p];
+        out[3 * np + f] = nc_c[p];
     }
 }
 
@@ -176,59 +211,104 @@ void launch_probe(folty_graph* g, int64_t delta, int dir, int32_t* cnt, cudaStre
     }
 }
 
-// Threshold + pair output for counts cnt[m_kept] (sorted order). Allocates and fills
-// the host arrays of *out; edge counts in input order when asked.
-void finish_query(folty_graph* g, const folty_query_params& q, const int32_t* cnt, folty_result* out,
-                  cudaStream_t s) {
-    const int T = 256;
-    Scratch sc(g->alloc, s);
-    const int64_t mk = g->m_kept;
+// Per-query device buffers of the threshold and output passes.
+struct PairStage {
+    int32_t* seg_max;    // [2S] max c_e per directed pair
+    int32_t* seg_ncert;  // [2S] certificates per directed pair
+    int32_t* flag;       // [2S + 1]
+    int32_t* pos;        // [2S + 1]; pos[S] = pairs x < y, pos[2S] = all pairs
+    uint64_t* key;       // [2S] compacted (x, y)
+    int32_t* cnt_c;      // [2S]
+    int32_t* nc_c;       // [2S]
+    unsigned long long* n_cert;
+};
+
+static PairStage pair_stage(Scratch& sc, const folty_graph* g) {
     const int64_t n2 = 2 * (int64_t)g->S;
-    const int nb = bit_length((uint64_t)(g->n > 1 ? g->n - 1 : 1));
-    int32_t* seg_max = sc.get<int32_t>(n2);
-    int32_t* seg_ncert = sc.get<int32_t>(n2);
-    unsigned long long* ncert = sc.get<unsigned long long>(1);
-    FOLTY_CUDA(cudaMemsetAsync(seg_max, 0, sizeof(int32_t) * (size_t)(n2 > 0 ? n2 : 1), s));
-    FOLTY_CUDA(cudaMemsetAsync(seg_ncert, 0, sizeof(int32_t) * (size_t)(n2 > 0 ? n2 : 1), s));
-    FOLTY_CUDA(cudaMemsetAsync(ncert, 0, sizeof(unsigned long long), s));
+    PairStage p;
+    p.seg_max = sc.get<int32_t>(2 * n2 + 2);
+    p.seg_ncert = p.seg_max + n2 + 1;
+    p.flag = sc.get<int32_t>(2 * n2 + 2);
+    p.pos = p.flag + n2 + 1;
+    p.key = sc.get<uint64_t>(n2);
+    p.cnt_c = sc.get<int32_t>(2 * n2 + 2);
+    p.nc_c = p.cnt_c + n2 + 1;
+    p.n_cert = sc.get<unsigned long long>(1);
+    return p;
+}
+
+// Certificate test, per-pair reduction, flags, positions, compaction (no host sync).
+static void pairs_device(folty_graph* g, const folty_query_params& q, const int32_t* cnt, const PairStage& p,
+                         Scratch& sc, cudaStream_t s) {
+    const int T = 256;
+    const int64_t mk = g->m_kept;
+    const int64_t S = g->S, n2 = 2 * S;
+    FOLTY_CUDA(cudaMemsetAsync(p.seg_max, 0, sizeof(int32_t) * (size_t)(2 * n2 + 2), s));
+    FOLTY_CUDA(cudaMemsetAsync(p.n_cert, 0, sizeof(unsigned long long), s));
     if (mk > 0) {
         ThresholdArgs a{cnt, g->sd, mk, g->ea, g->eb, g->deg, g->common, (int)q.quant, (int)q.universe,
-                        (int64_t)q.rho_num, (int64_t)q.rho_den, seg_max, seg_ncert, ncert};
+                        (int64_t)q.rho_num, (int64_t)q.rho_den, p.seg_max, p.seg_ncert, p.n_cert};
         FOLTY_LAUNCH(k_threshold, grid_for(mk, T), T, 0, s, a);
     }
-    int32_t* flag = sc.get<int32_t>(n2 + 1);
-    int32_t* pos = sc.get<int32_t>(n2 + 1);
-    if (n2 > 0) FOLTY_LAUNCH(k_pair_flags, grid_for(n2, T), T, 0, s, seg_ncert, n2, flag);
-    exclusive_scan(sc, flag, pos, n2);
-    int64_t rb[2];
-    {
-        const void* ptrs[2] = {pos + n2, ncert};
-        int sizes[2] = {4, 8};
-        read_back(g, ptrs, sizes, 2, rb, s);
+    if (n2 > 0) FOLTY_LAUNCH(k_pair_flags, grid_for(n2, T), T, 0, s, p.seg_ncert, g->by_b, S, p.flag);
+    exclusive_scan(sc, p.flag, p.pos, n2);
+    if (n2 > 0)
+        FOLTY_LAUNCH(k_pair_compact, grid_for(n2, T), T, 0, s, p.flag, p.pos, S, g->ea, g->eb, g->by_b, p.seg_max,
+                     p.seg_ncert, p.key, p.cnt_c, p.nc_c);
+}
+
+void finish_queries(folty_graph* g, const folty_query_params* const* qs, const int32_t* const* cnts, int nq,
+                    folty_result* const* outs, cudaStream_t s) {
+    const int T = 256;
+    const int64_t S = g->S;
+    const int64_t mk = g->m_kept;
+    const int G = READBACK_MAX / 3;
+    for (int g0 = 0; g0 < nq; g0 += G) {
+        const int ng = std::min(G, nq - g0);
+        Scratch sc(g->alloc, s);
+        std::vector<PairStage> st;
+        for (int i = 0; i < ng; i++) {
+            st.push_back(pair_stage(sc, g));
+            pairs_device(g, *qs[g0 + i], cnts[g0 + i], st.back(), sc, s);
+        }
+        // one read-back for the group: pairs x < y, all pairs, certificates
+        std::vector<const void*> ptrs;
+        std::vector<int> sizes;
+        for (int i = 0; i < ng; i++) {
+            ptrs.push_back(st[i].pos + S);
+            ptrs.push_back(st[i].pos + 2 * S);
+            ptrs.push_back(st[i].n_cert);
+            sizes.insert(sizes.end(), {4, 4, 8});
+        }
+        std::vector<int64_t> rb(3 * (size_t)ng);
+        read_back(g, ptrs.data(), sizes.data(), 3 * ng, rb.data(), s);
+        for (int i = 0; i < ng; i++) {
+            const folty_query_params& q = *qs[g0 + i];
+            folty_result* out = outs[g0 + i];
+            const int64_t nA = rb[3 * i], np = rb[3 * i + 1];
+            fill_result_host(out, np, g->m, q.want_edge_counts != 0);
+            out->n_cert_edges = rb[3 * i + 2];
+            if (np > 0) {
+                int32_t* packed = sc.get<int32_t>(4 * np);
+                FOLTY_LAUNCH(k_pair_merge, grid_for(np, T), T, 0, s, st[i].key, st[i].cnt_c, st[i].nc_c, nA, np,
+                             packed);
+                FOLTY_CUDA(cudaMemcpyAsync(out->u, packed, sizeof(int32_t) * 4 * (size_t)np, cudaMemcpyDeviceToHost, s));
+            }
+            if (q.want_edge_counts && g->m > 0) {
+                int32_t* ec = sc.get<int32_t>(g->m);
+                FOLTY_CUDA(cudaMemsetAsync(ec, 0, sizeof(int32_t) * (size_t)g->m, s));
+                if (mk > 0) FOLTY_LAUNCH(k_edge_counts_input_order, grid_for(mk, T), T, 0, s, cnts[g0 + i], g->perm, mk, ec);
+                FOLTY_CUDA(cudaMemcpyAsync(out->edge_count, ec, sizeof(int32_t) * (size_t)g->m, cudaMemcpyDeviceToHost, s));
+            }
+        }
+        FOLTY_CUDA(cudaStreamSynchronize(s));
     }
-    const int64_t np = rb[0];
-    fill_result_host(out, np, g->m, q.want_edge_counts != 0);
-    out->n_cert_edges = rb[1];
-    if (np > 0) {
-        uint64_t* key = sc.get<uint64_t>(np);
-        uint64_t* key_alt = sc.get<uint64_t>(np);
-        uint32_t* val = sc.get<uint32_t>(np);
-        uint32_t* val_alt = sc.get<uint32_t>(np);
-        FOLTY_LAUNCH(k_pair_keys, grid_for(n2, T), T, 0, s, flag, pos, n2, g->ea, g->eb, nb, key, val);
-        bool alt = radix_sort_pairs(sc, key, key_alt, val, val_alt, np, 2 * nb);
-        int32_t* packed = sc.get<int32_t>(4 * np);
-        FOLTY_LAUNCH(k_pair_out, grid_for(np, T), T, 0, s, alt ? key_alt : key, alt ? val_alt : val, np, nb,
-                     seg_max, seg_ncert, packed);
-        FOLTY_CUDA(cudaMemcpyAsync(out->u, packed, sizeof(int32_t) * 4 * (size_t)np, cudaMemcpyDeviceToHost, s));
-    }
-    if (q.want_edge_counts) {
-        int32_t* ec = sc.get<int32_t>(g->m);
-        if (g->m > 0) FOLTY_CUDA(cudaMemsetAsync(ec, 0, sizeof(int32_t) * (size_t)g->m, s));
-        if (mk > 0) FOLTY_LAUNCH(k_edge_counts_input_order, grid_for(mk, T), T, 0, s, cnt, g->perm, mk, ec);
-        if (g->m > 0)
-            FOLTY_CUDA(cudaMemcpyAsync(out->edge_count, ec, sizeof(int32_t) * (size_t)g->m, cudaMemcpyDeviceToHost, s));
-    }
-    FOLTY_CUDA(cudaStreamSynchronize(s));
+}
+
+void finish_query(folty_graph* g, const folty_query_params& q, const int32_t* cnt, folty_result* out,
+                  cudaStream_t s) {
+    const folty_query_params* qp = &q;
+    finish_queries(g, &qp, &cnt, 1, &out, s);
 }
 
 void run_query(folty_graph* g, const folty_query_params& q, folty_result* out, cudaStream_t s) {
