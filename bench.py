@@ -189,6 +189,72 @@ def replica_throughput(units_per_rank: int, world: int, seconds_max: float) -> f
 
 # ----------------------------------------------------------------------------- GPU arm
 
+SERVE_SIZES = (100_000, 500_000, 1_000_000, 2_000_000, 5_000_000, 10_000_000, 15_000_000, 20_000_000)
+
+
+def measure_serving(F, seconds, rate=200.0, sizes=SERVE_SIZES, seed=5):
+    """Poisson arrivals (rate per second) of mixed queries over resident graphs of the
+    medium recipe (n = m / 20), each query for a uniformly drawn graph; latency is
+    arrival -> results on the host, as stamped by the server."""
+    import queue as _queue
+    gens = [W.medium_graph_of_size(m, 5000 + i) for i, m in enumerate(sizes)]
+    handles = [F.TemporalGraph(g.n, g.src, g.dst, g.t, allocator=None) for g in gens]
+    ms = [g.m for g in gens]
+    del gens
+    rng = np.random.default_rng(seed)
+    arrivals = []
+    t = 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= seconds:
+            break
+        arrivals.append(t)
+    qs = W.random_query_mix(len(arrivals), rng)
+    gi = rng.integers(0, len(sizes), len(arrivals))
+    sv = F.folty_server_create([h.handle for h in handles])
+    try:
+        for i in range(len(sizes)):  # warm-up: one query per graph
+            F.folty_server_wait(sv, F.folty_server_submit(sv, i, qs[0]))
+        pending = _queue.Queue()
+        infos = []
+
+        def collect():
+            while True:
+                item = pending.get()
+                if item is None:
+                    return
+                res = F.folty_server_wait(sv, item[0])
+                infos.append((res["info"], item[1]))
+
+        th = threading.Thread(target=collect, daemon=True)
+        th.start()
+        t0 = time.perf_counter()
+        for at, q, g in zip(arrivals, qs, gi):
+            delay = t0 + at - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            pending.put((F.folty_server_submit(sv, int(g), q), int(g)))
+        pending.put(None)
+        th.join()
+        elapsed = time.perf_counter() - t0
+        stats = F.folty_server_get_stats(sv)
+    finally:
+        F.folty_server_destroy(sv)
+        for h in handles:
+            h.close()
+    lat = np.array([inf["latency_ms"] for inf, _ in infos])
+    edges = sum(ms[g] for _, g in infos)
+    return {"workload": "8 resident graphs of the medium recipe, m in " + ",".join(str(m) for m in sizes)
+            + "; Poisson arrivals, mixed queries", "seconds": seconds, "rate_qps": rate,
+            "queries": len(infos), "throughput_qps": len(infos) / elapsed,
+            "edges_per_s": edges / elapsed,
+            "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+            "mean_batch": float(np.mean([inf["batch_size"] for inf, _ in infos])) if infos else None,
+            "batches": stats["batches"], "max_batches_in_flight": stats["max_batches_in_flight"],
+            "peak_memory_bytes": stats["peak_memory_bytes"]}
+
+
 def measure_batch(F, g, d_src, d_dst, d_t, sh, nq, stream, reps=3):
     """nq mixed queries (delta log-uniform on [60 s, 7 d], rho = k/10, quantifier and
     direction uniform) on the preprocessed graph: folty_query_batch against nq
@@ -240,6 +306,8 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (debug only)")
     ap.add_argument("--batch", type=int, default=256,
                     help="queries of the batched measurement (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the serving measurement (0 = skip; 60 for the full run)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -322,6 +390,10 @@ def main():
     if args.batch > 0:
         batched = measure_batch(F, g, d_src, d_dst, d_t, sh, args.batch, stream)
 
+    serving = None
+    if args.serve_seconds > 0 and world == 1:
+        serving = measure_serving(F, args.serve_seconds)
+
     # ---- end-to-end through the C ABI from pinned host buffers
     ke = args.e2e_steps or args.steps
     barrier()
@@ -359,6 +431,7 @@ def main():
                      "model_bytes_per_launch": tm["probe_bytes"]},
         "clocks": clk,
         "batched": batched,
+        "serving": serving,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         step_s, sample, cores = oracle_sample_time(g, queries, budget_s=args.ref_budget)

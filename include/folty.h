@@ -175,6 +175,60 @@ void folty_profile_enable(int32_t on);
 /* Copies the totals. Errors: FOLTY_EINVAL (NULL). */
 folty_status folty_profile_read(folty_profile *out);
 
+/* ------------------------------------------------------------------ serving
+ * A server keeps preprocessed graphs resident and answers queries as they arrive
+ * (not in the paper: a serving layer over folty_query_batch). Each graph gets one
+ * worker thread and one CUDA stream, so work on different graphs overlaps on the
+ * device. A worker takes every query queued for its graph (up to max_batch) as one
+ * batch -- queries that arrive while a batch runs form the next one (continuous
+ * batching) -- shrinks the batch until its device footprint (per-delta bins and output
+ * stages) fits the memory budget, waits until the budget has room, runs it and
+ * completes the tickets. Results equal those of folty_query on the same graph. The
+ * graphs stay owned by the caller and must outlive the server. */
+typedef struct folty_server folty_server;
+
+typedef struct {
+    int64_t memory_budget_bytes; /* device bytes for in-flight batches; 0: half the free memory */
+    int32_t max_batch;           /* queries per batch; 0: 256                                 */
+} folty_server_config;
+
+typedef struct {
+    double queued_ms;   /* submit -> start of its batch       */
+    double run_ms;      /* batch start -> results on the host */
+    double latency_ms;  /* submit -> results on the host      */
+    int64_t batch_id;
+    int32_t batch_size;
+    int32_t graph_index;
+} folty_ticket_info;
+
+typedef struct {
+    int64_t batches, queries, queued;
+    int64_t memory_budget_bytes, peak_memory_bytes;
+    int64_t max_batches_in_flight;
+} folty_server_stats;
+
+/* Starts one worker per graph (all preprocessed). cfg may be NULL. Errors:
+ * FOLTY_EINVAL, FOLTY_ESTATE (a graph not preprocessed), FOLTY_ECUDA. */
+folty_status folty_server_create(folty_graph *const *graphs, int32_t n_graphs,
+                                 const folty_server_config *cfg, folty_server **out);
+
+/* Queues query q for graphs[graph_index]; *ticket identifies it. Thread-safe. Errors:
+ * FOLTY_EINVAL (bad index or parameters), FOLTY_ESTATE (server shutting down). */
+folty_status folty_server_submit(folty_server *sv, int32_t graph_index,
+                                 const folty_query_params *q, int64_t *ticket);
+
+/* Waits for a ticket (timeout_ms < 0: no limit) and moves its result into *out (free
+ * it with folty_free); info (may be NULL) receives its timings. A ticket can be
+ * collected once. Errors: FOLTY_EINVAL (unknown ticket), FOLTY_ETIMEOUT (not done in
+ * time; the ticket stays collectable), or the status its batch failed with. */
+folty_status folty_server_wait(folty_server *sv, int64_t ticket, int64_t timeout_ms,
+                               folty_result *out, folty_ticket_info *info);
+
+folty_status folty_server_get_stats(folty_server *sv, folty_server_stats *out);
+
+/* Runs every queued query, stops the workers and frees uncollected results. */
+void folty_server_destroy(folty_server *sv);
+
 /* Per-edge counts of one query without allocating anything (the paper has no
  * counterpart). For callers that cannot allocate device memory when they query: a
  * serving process that reserved its whole memory budget at start-up, latency-bound code

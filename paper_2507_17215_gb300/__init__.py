@@ -31,7 +31,8 @@ U_HEAD, U_TAIL, U_COMMON = 0, 1, 2
 EXPORTED = ["folty_load_temporal_graph", "folty_preprocess", "folty_query", "folty_query_batch",
             "folty_free", "folty_last_error", "folty_graph_get_info", "folty_graph_traffic_model",
             "folty_kernel_launches", "folty_profile_enable", "folty_profile_read",
-            "folty_edge_counts_noalloc"]
+            "folty_edge_counts_noalloc", "folty_server_create", "folty_server_submit",
+            "folty_server_wait", "folty_server_get_stats", "folty_server_destroy"]
 
 
 class FoltyError(RuntimeError):
@@ -67,6 +68,22 @@ class folty_graph_info(Structure):
                 ("max_degree", c_int32), ("degeneracy", c_int32), ("max_out_degree", c_int32),
                 ("peel_rounds", c_int32), ("triangles", c_int64), ("probes", c_int64),
                 ("sigma_max", c_int32), ("time_sorted", c_int32), ("device_bytes", c_int64)]
+
+
+class folty_server_config(Structure):
+    _fields_ = [("memory_budget_bytes", c_int64), ("max_batch", c_int32)]
+
+
+class folty_ticket_info(Structure):
+    _fields_ = [("queued_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double), ("batch_id", c_int64), ("batch_size", c_int32),
+                ("graph_index", c_int32)]
+
+
+class folty_server_stats(Structure):
+    _fields_ = [("batches", c_int64), ("queries", c_int64), ("queued", c_int64),
+                ("memory_budget_bytes", c_int64), ("peak_memory_bytes", c_int64),
+                ("max_batches_in_flight", c_int64)]
 
 
 class folty_profile(Structure):
@@ -109,6 +126,18 @@ def _load_library():
     lib.folty_profile_enable.argtypes = [c_int32]
     lib.folty_profile_read.restype = c_int32
     lib.folty_profile_read.argtypes = [POINTER(folty_profile)]
+    lib.folty_server_create.restype = c_int32
+    lib.folty_server_create.argtypes = [POINTER(c_void_p), c_int32, POINTER(folty_server_config),
+                                        POINTER(c_void_p)]
+    lib.folty_server_submit.restype = c_int32
+    lib.folty_server_submit.argtypes = [c_void_p, c_int32, POINTER(folty_query_params), POINTER(c_int64)]
+    lib.folty_server_wait.restype = c_int32
+    lib.folty_server_wait.argtypes = [c_void_p, c_int64, c_int64, POINTER(folty_result),
+                                      POINTER(folty_ticket_info)]
+    lib.folty_server_get_stats.restype = c_int32
+    lib.folty_server_get_stats.argtypes = [c_void_p, POINTER(folty_server_stats)]
+    lib.folty_server_destroy.restype = None
+    lib.folty_server_destroy.argtypes = [c_void_p]
     lib.folty_edge_counts_noalloc.restype = c_int32
     lib.folty_edge_counts_noalloc.argtypes = [G, c_int64, c_int32, c_void_p, c_void_p]
     return lib
@@ -276,6 +305,40 @@ def folty_profile_read() -> Dict[str, float]:
     p = folty_profile()
     _check(lib.folty_profile_read(ctypes.byref(p)))
     return {"probe_launches": int(p.probe_launches), "probe_ms": float(p.probe_ms)}
+
+
+def folty_server_create(graphs: Sequence[int], memory_budget_bytes: int = 0, max_batch: int = 0) -> int:
+    arr = (c_void_p * len(graphs))(*graphs)
+    cfg = folty_server_config(int(memory_budget_bytes), int(max_batch))
+    out = c_void_p()
+    _check(lib.folty_server_create(arr, len(graphs), ctypes.byref(cfg), ctypes.byref(out)))
+    return out.value
+
+
+def folty_server_submit(sv: int, graph_index: int, q) -> int:
+    p = _params(q)
+    t = c_int64()
+    _check(lib.folty_server_submit(sv, int(graph_index), ctypes.byref(p), ctypes.byref(t)))
+    return int(t.value)
+
+
+def folty_server_wait(sv: int, ticket: int, timeout_ms: int = -1):
+    r = folty_result()
+    info = folty_ticket_info()
+    _check(lib.folty_server_wait(sv, int(ticket), int(timeout_ms), ctypes.byref(r), ctypes.byref(info)))
+    res = _take_result(r)
+    res["info"] = {name: getattr(info, name) for name, _ in folty_ticket_info._fields_}
+    return res
+
+
+def folty_server_get_stats(sv: int) -> Dict[str, int]:
+    st = folty_server_stats()
+    _check(lib.folty_server_get_stats(sv, ctypes.byref(st)))
+    return {name: int(getattr(st, name)) for name, _ in folty_server_stats._fields_}
+
+
+def folty_server_destroy(sv: int) -> None:
+    lib.folty_server_destroy(sv)
 
 
 # ------------------------------------------------------------------ convenience

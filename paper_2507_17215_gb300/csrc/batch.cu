@@ -90,8 +90,33 @@ static int64_t batch_bin_budget_bytes() {
     return b < cap ? b : cap;
 }
 
+// Bins of one probe pass: the largest number of distinct deltas of one direction variant.
+int64_t batch_footprint(const folty_graph* g, const folty_query_params* qs, int nq, int64_t* bins_part) {
+    int64_t kmax = 0;
+    for (int dir = 0; dir <= FOLTY_DIR_EITHER; dir++) {
+        std::vector<int64_t> D;
+        for (int i = 0; i < nq; i++)
+            if (qs[i].dir == dir) D.push_back(qs[i].delta);
+        std::sort(D.begin(), D.end());
+        D.erase(std::unique(D.begin(), D.end()), D.end());
+        kmax = std::max<int64_t>(kmax, (int64_t)D.size());
+    }
+    kmax = std::min<int64_t>(kmax, BATCH_MAX_BINS);
+    const int64_t bins = kmax * g->m_kept * 4;
+    // output stage per query of a read-back group (see finish_queries): 6 int32 arrays
+    // of 2S + 1, compacted keys, packed output, edge counts when asked
+    const int64_t n2 = 2 * (int64_t)g->S;
+    int64_t per_q = 6 * 4 * (n2 + 1) + 8 * n2 + 16 * n2 + 64;
+    bool edges = false;
+    for (int i = 0; i < nq; i++) edges = edges || qs[i].want_edge_counts;
+    if (edges) per_q += 4 * g->m;
+    const int64_t group = std::min<int64_t>(nq, READBACK_MAX / 3);
+    if (bins_part) *bins_part = bins;
+    return bins + group * per_q;
+}
+
 void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty_result* outs,
-                     cudaStream_t s) {
+                     cudaStream_t s, int64_t bin_budget) {
     const int64_t mk = g->m_kept;
     const int64_t P = g->info.probes;
     // group the queries by direction variant; distinct sorted deltas per group
@@ -105,7 +130,8 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
         std::sort(D.begin(), D.end());
         D.erase(std::unique(D.begin(), D.end()), D.end());
         const int64_t per_bin = mk * (int64_t)sizeof(int32_t);
-        int64_t chunk = per_bin > 0 ? batch_bin_budget_bytes() / per_bin : (int64_t)D.size();
+        const int64_t budget = bin_budget > 0 ? bin_budget : batch_bin_budget_bytes();
+        int64_t chunk = per_bin > 0 ? budget / per_bin : (int64_t)D.size();
         chunk = std::max<int64_t>(1, std::min<int64_t>({chunk, (int64_t)BATCH_MAX_BINS, (int64_t)D.size()}));
         for (size_t c0 = 0; c0 < D.size(); c0 += (size_t)chunk) {
             const int k = (int)std::min<int64_t>(chunk, (int64_t)D.size() - (int64_t)c0);

@@ -191,8 +191,12 @@ int bit_length(uint64_t x);
 void preprocess_graph(folty_graph* g, cudaStream_t s);          // preprocess.cu
 void run_query(folty_graph* g, const folty_query_params& q, folty_result* out,
                cudaStream_t s);                                  // query.cu
+// bin_budget: device bytes the per-delta bins may take (<= 0: a quarter of the free
+// memory, at most 16 GiB); deltas beyond it are handled in further probe passes.
 void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq,
-                     folty_result* outs, cudaStream_t s);        // batch.cu
+                     folty_result* outs, cudaStream_t s, int64_t bin_budget = 0);  // batch.cu
+// Device bytes a batch of these queries takes beyond the graph (bins + output stages).
+int64_t batch_footprint(const folty_graph* g, const folty_query_params* qs, int nq, int64_t* bins_part);
 void traffic_model(folty_graph* g, int dir, folty_traffic_model* out, cudaStream_t s);
 
 void validate_query(const folty_query_params& q);
