@@ -59,6 +59,11 @@ def _load():
     lib.oracle_query.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p, i32p, i32p, i32p,
                                  i32p, i32p, i64p]
+    lib.oracle_vertices.restype = ctypes.c_int64
+    lib.oracle_vertices.argtypes = [P, ctypes.c_int64, i32p, ctypes.c_int64, ctypes.c_int64, i32p, i32p]
+    lib.oracle_certificates.restype = ctypes.c_int64
+    lib.oracle_certificates.argtypes = [P, i32p, i32p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                        ctypes.c_int, i64p]
     _lib = lib
     return lib
 
@@ -149,6 +154,22 @@ class OracleGraph:
                                    _ptr(ncert, ctypes.c_int64))
         if k < 0:
             raise ValueError("oracle: bad query parameters")
-        return {"u": pu[:k].copy(), "v": pv[:k].copy(), "count": pc[:k].copy(),
-                "ncert": pn[:k].copy(), "edge_count": counts, "common": common,
-                "n_cert_edges": int(ncert[0])}
+        res = {"u": pu[:k].copy(), "v": pv[:k].copy(), "count": pc[:k].copy(),
+               "ncert": pn[:k].copy(), "edge_count": counts, "common": common,
+               "n_cert_edges": int(ncert[0])}
+        certs = np.zeros(max(int(ncert[0]), 1), dtype=np.int64)
+        nc = self._lib.oracle_certificates(self._h, _ptr(counts, i32), _ptr(common, i32), int(q.rho_num),
+                                           int(q.rho_den), int(q.quant), int(q.universe),
+                                           _ptr(certs, ctypes.c_int64))
+        res["certificates"] = certs[:nc].copy()
+        if getattr(q, "outer", 0):
+            vout = np.zeros(max(self.n, 1), dtype=np.int32)
+            cout = np.zeros(max(self.n, 1), dtype=np.int32)
+            heads = np.ascontiguousarray(res["u"], dtype=np.int32)
+            nv = self._lib.oracle_vertices(self._h, heads.shape[0], _ptr(heads, i32), int(q.outer_rho_num),
+                                           int(q.outer_rho_den), _ptr(vout, i32), _ptr(cout, i32))
+            if nv < 0:
+                raise ValueError("oracle: bad outer threshold")
+            res["vertex"] = vout[:nv].copy()
+            res["vertex_count"] = cout[:nv].copy()
+        return res

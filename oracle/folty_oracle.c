@@ -31,7 +31,13 @@
  *   5. Solutions (Definition 1.2 and the certificate discussion of Section 1.2): an
  *      ordered pair (x, y) is a solution when at least one temporal edge x -> y is a
  *      certificate; it is reported with max c_e over E_{x,y} and the number of
- *      certificates, sorted by (x, y).
+ *      certificates, sorted by (x, y). The certificates themselves are listed by
+ *      input index.
+ *   6. Vertex queries (Section 4, exists-forall-forall and exists-forall-exists): with the
+ *      pairs of step 5 as the set L, vertex u is a solution when the number of v with
+ *      (u, v) in L is >= 1 and, for an outer rho1 = num1/den1, count * den1 >=
+ *      num1 * |N(u)|. The inner query is the pair query itself (forall_rho2 for
+ *      exists-forall-forall, the existential quantifier for exists-forall-exists).
  *
  * Self-loops are not edges of G_S; they get c_e = 0 and are never certificates.
  * Parallelism: each temporal edge's c_e is independent, so an OpenMP loop over
@@ -314,4 +320,40 @@ int64_t oracle_query(void *p, int64_t delta, int64_t rho_num, int64_t rho_den, i
     }
     if (n_cert_edges) *n_cert_edges = ncert_total;
     return np_;
+}
+
+/* Section 4: vertices u with count(u) = #{v : (u, v) a solution pair} meeting the outer
+ * threshold. pu[0..np) are the solution pairs' heads (any order). Writes the vertex ids
+ * ascending with their counts; returns how many. */
+int64_t oracle_vertices(void *p, int64_t np, const int32_t *pu, int64_t num1, int64_t den1, int32_t *vout,
+                        int32_t *cout) {
+    oracle_graph *g = (oracle_graph *)p;
+    if (!g || den1 <= 0 || num1 < 0 || num1 > den1) return -1;
+    int32_t *cnt = (int32_t *)calloc((size_t)g->n + 1, sizeof(int32_t));
+    for (int64_t i = 0; i < np; i++) cnt[pu[i]]++;  /* each pair (u, v) appears once */
+    int64_t k = 0;
+    for (int32_t u = 0; u < g->n; u++) {
+        int64_t deg = g->nbr_ptr[u + 1] - g->nbr_ptr[u];
+        if (cnt[u] >= 1 && (int64_t)cnt[u] * den1 >= num1 * deg) {
+            vout[k] = u;
+            cout[k] = cnt[u];
+            k++;
+        }
+    }
+    free(cnt);
+    return k;
+}
+
+/* Input indices (ascending) of the certificates, from per-edge counts in input order. */
+int64_t oracle_certificates(void *p, const int32_t *counts, const int32_t *common, int64_t rho_num,
+                            int64_t rho_den, int quant, int universe, int64_t *out) {
+    oracle_graph *g = (oracle_graph *)p;
+    int64_t k = 0;
+    for (int64_t e = 0; e < g->m; e++) {
+        if (g->src[e] == g->dst[e]) continue;
+        if (certifies(quant, counts[e], universe_size(g, universe, g->src[e], g->dst[e], common[e]), rho_num,
+                      rho_den))
+            out[k++] = e;
+    }
+    return k;
 }

@@ -7,6 +7,7 @@ vertex triple and every pair of temporal edges. It is only usable on tiny graphs
 """
 from __future__ import annotations
 
+import dataclasses
 import glob
 import os
 from typing import Dict, List, Tuple
@@ -35,6 +36,12 @@ def parse_fixture(path: str):
             d, num, den, quant, dr, uni = map(int, tok[1:7])
             cases.append({"q": W.Query(delta=d, rho_num=num, rho_den=den, quant=quant, dir=dr,
                                        universe=uni), "counts": None, "pairs": []})
+        elif tok[0] == "outer":
+            cases[-1]["q"] = dataclasses.replace(cases[-1]["q"], outer=W.OUTER_FORALL_T,
+                                                 outer_rho_num=int(tok[1]), outer_rho_den=int(tok[2]))
+            cases[-1]["vertices"] = []
+        elif tok[0] == "vertex":
+            cases[-1]["vertices"].append((int(tok[1]), int(tok[2])))
         elif tok[0] == "counts":
             cases[-1]["counts"] = np.array([int(x) for x in tok[1:]], dtype=np.int32)
         elif tok[0] == "pair":
@@ -110,6 +117,35 @@ def brute_pairs(g: W.TemporalGraph, q: W.Query, counts: np.ndarray):
         best[key] = max(best.get(key, 0), c)
         ncert[key] = ncert.get(key, 0) + int(sat)
     return sorted((k[0], k[1], best[k], ncert[k]) for k in best if ncert[k] > 0)
+
+
+def brute_vertices(g: W.TemporalGraph, q: W.Query, pairs):
+    """Section 4 reduction by its definition: count(u) = #{v : (u, v) a solution pair};
+    u is a solution when count >= 1 and count * den1 >= num1 * |N(u)|."""
+    nb = brute_neighbours(g)
+    cnt: Dict[int, int] = {}
+    for u, v, _, _ in pairs:
+        cnt[u] = cnt.get(u, 0) + 1
+    return sorted((u, c) for u, c in cnt.items()
+                  if c >= 1 and c * q.outer_rho_den >= q.outer_rho_num * len(nb[u]))
+
+
+def brute_certificates(g: W.TemporalGraph, q: W.Query, counts: np.ndarray):
+    nb = brute_neighbours(g)
+    out = []
+    for i, (x, y) in enumerate(zip(g.src.tolist(), g.dst.tolist())):
+        if x == y:
+            continue
+        c = int(counts[i])
+        U = len(nb[x]) if q.universe == W.U_HEAD else len(nb[y]) if q.universe == W.U_TAIL \
+            else len(nb[x] & nb[y])
+        if c >= 1 and (q.quant == W.Q_EXISTS or c * q.rho_den >= q.rho_num * U):
+            out.append(i)
+    return out
+
+
+def vertices_of(res):
+    return list(zip(np.asarray(res["vertex"]).tolist(), np.asarray(res["vertex_count"]).tolist()))
 
 
 def pairs_of(res) -> List[Tuple[int, int, int, int]]:

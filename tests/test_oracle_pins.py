@@ -15,8 +15,8 @@ import pytest
 
 import oracle
 import workloads as W
-from _support import (brute_counts, brute_pairs, complete_graph, golden_files, pairs_of,
-                      parse_fixture)
+from _support import (brute_certificates, brute_counts, brute_pairs, brute_vertices, complete_graph,
+                      golden_files, pairs_of, parse_fixture, vertices_of)
 
 
 @pytest.mark.parametrize("path", golden_files(), ids=os.path.basename)
@@ -29,6 +29,8 @@ def test_golden_fixture(path):
                 r = og.query(case["q"], brute=brute)
                 np.testing.assert_array_equal(r["edge_count"], case["counts"])
                 assert pairs_of(r) == case["pairs"]
+                if "vertices" in case:
+                    assert vertices_of(r) == case["vertices"]
 
 
 def _tiny_graphs():
@@ -181,3 +183,43 @@ def test_invalid_graph_rejected():
     with pytest.raises(ValueError):
         oracle.OracleGraph(3, np.array([0], np.int32), np.array([1], np.int32),
                            np.array([-1], np.int64))
+
+
+def test_vertex_queries_and_certificates_match_brute_force():
+    """Section 4 reductions and the certificate list, against their definitions."""
+    import dataclasses
+    for g in _tiny_graphs():
+        for delta in (0, 3, 30):
+            for dr in (W.DIR_OUT, W.DIR_EITHER):
+                counts = brute_counts(g, delta, dr)
+                with oracle.OracleGraph.of(g) as og:
+                    for q in (W.Query(delta, 1, 3, W.Q_FORALL_T, dr, W.U_TAIL),
+                              W.Query(delta, 1, 2, W.Q_EXISTS, dr, W.U_HEAD)):
+                        for num1, den1 in ((0, 1), (1, 4), (1, 2), (1, 1)):
+                            qq = dataclasses.replace(q, outer=W.OUTER_FORALL_T, outer_rho_num=num1,
+                                                     outer_rho_den=den1)
+                            r = og.query(qq)
+                            pairs = brute_pairs(g, qq, counts)
+                            assert vertices_of(r) == brute_vertices(g, qq, pairs)
+                        assert r["certificates"].tolist() == brute_certificates(g, q, counts)
+
+
+def test_forall_forall_solutions_are_forall_exists_solutions():
+    """Every exists-forall-forall solution is an exists-forall-exists solution (Section 5,
+    Insights), and vertex solutions shrink as the outer threshold grows."""
+    import dataclasses
+    g = _medium_random(13)
+    with oracle.OracleGraph.of(g) as og:
+        for num1 in (1, 2, 3, 5):
+            q_ff = W.Query(60, 1, 4, W.Q_FORALL_T, outer=W.OUTER_FORALL_T, outer_rho_num=num1, outer_rho_den=10)
+            q_fe = dataclasses.replace(q_ff, quant=W.Q_EXISTS)
+            ff = set(og.query(q_ff)["vertex"].tolist())
+            fe = set(og.query(q_fe)["vertex"].tolist())
+            assert ff <= fe
+        prev = None
+        for num1 in (0, 1, 2, 4, 7, 10):
+            cur = set(og.query(W.Query(60, 0, 1, W.Q_EXISTS, outer=W.OUTER_FORALL_T, outer_rho_num=num1,
+                                       outer_rho_den=10))["vertex"].tolist())
+            if prev is not None:
+                assert cur <= prev
+            prev = cur

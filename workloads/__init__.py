@@ -33,6 +33,7 @@ YEAR_S = 31_536_000
 
 # query-parameter codes shared by every caller (plain data, no arithmetic)
 Q_EXISTS, Q_FORALL_T = 0, 1
+OUTER_NONE, OUTER_FORALL_T = 0, 1
 DIR_OUT, DIR_IN, DIR_EITHER = 0, 1, 2
 U_HEAD, U_TAIL, U_COMMON = 0, 1, 2
 
@@ -57,6 +58,10 @@ class Query:
     dir: int = DIR_OUT
     universe: int = U_HEAD
     want_edge_counts: bool = True
+    outer: int = OUTER_NONE      # OUTER_FORALL_T: also the vertex solutions (Section 4)
+    outer_rho_num: int = 1
+    outer_rho_den: int = 2
+    want_certificates: bool = False
 
 
 # --------------------------------------------------------------------------- samplers
