@@ -58,14 +58,21 @@ typedef struct {
 enum { FOLTY_Q_EXISTS = 0, FOLTY_Q_FORALL_T = 1 };                    /* quantifier on w */
 enum { FOLTY_DIR_OUT = 0, FOLTY_DIR_IN = 1, FOLTY_DIR_EITHER = 2 };   /* witness edges   */
 enum { FOLTY_U_HEAD = 0, FOLTY_U_TAIL = 1, FOLTY_U_COMMON = 2 };      /* universe of w   */
+enum { FOLTY_OUTER_NONE = 0, FOLTY_OUTER_FORALL_T = 1 };              /* quantifier on v */
 
 /* One query (Definition 1.1). rho = rho_num / rho_den with 0 <= rho_num <= rho_den,
  * rho_den > 0; compared exactly in integers. want_edge_counts != 0 also returns c_e for
- * every input edge. */
+ * every input edge; want_certificates != 0 also lists every certificate.
+ * outer = FOLTY_OUTER_FORALL_T adds the vertex queries of Section 4: with the solution
+ * pairs as the set L, vertex u is a solution when #{v : (u, v) in L} >= 1 and
+ * #{v : (u, v) in L} * outer_rho_den >= outer_rho_num * |N(u)| -- exists-forall-forall
+ * when quant is FOLTY_Q_FORALL_T, exists-forall-exists when it is FOLTY_Q_EXISTS. */
 typedef struct {
     int64_t delta;
     uint32_t rho_num, rho_den;
     uint8_t quant, dir, universe, want_edge_counts;
+    uint8_t outer, want_certificates, reserved[2];
+    uint32_t outer_rho_num, outer_rho_den;
 } folty_query_params;
 
 /* Result of one query. The struct belongs to the caller; the arrays it points to are
@@ -74,7 +81,11 @@ typedef struct {
  *                       over E_{u,v}; ncert = number of certificates on E_{u,v}.
  *   n_cert_edges:       total number of certificates.
  *   edge_count:         c_e for input edge i (self-loops get 0), length m, or NULL
- *                       when not requested. */
+ *                       when not requested.
+ *   vertex, vertex_count: outer queries: the n_vertices solutions ascending, with the
+ *                       number of solution pairs they head (NULL otherwise).
+ *   certificate:        want_certificates: input indices of the n_cert_edges
+ *                       certificates, ascending (NULL otherwise). */
 typedef struct {
     uint64_t tag; /* written by the library; lets folty_free tell a result from a graph */
     int64_t n_pairs;
@@ -82,6 +93,9 @@ typedef struct {
     int64_t n_cert_edges;
     int64_t m;
     int32_t *edge_count;
+    int64_t n_vertices;
+    int32_t *vertex, *vertex_count;
+    int64_t *certificate;
 } folty_result;
 
 /* Sizes and derived figures of a preprocessed graph. */
@@ -157,6 +171,13 @@ folty_status folty_graph_get_info(const folty_graph *g, folty_graph_info *info);
  * from the triangle list; synchronises the stream). */
 folty_status folty_graph_traffic_model(folty_graph *g, int32_t dir,
                                        folty_traffic_model *out, void *stream);
+
+/* The per-static-edge common-neighbour counts c_uv = |N(u) cap N(v)| of Section 3 (the
+ * number of triangles of G_S on the edge): a[i] < b[i], c[i] for the static_edges
+ * entries (host arrays of folty_graph_info.static_edges entries, caller-owned),
+ * sorted by (a, b). Synchronises the stream. Errors: FOLTY_EINVAL, FOLTY_ESTATE. */
+folty_status folty_graph_common_counts(folty_graph *g, int32_t *a, int32_t *b, int32_t *c,
+                                       void *stream);
 
 /* Number of kernels this library has launched in this process (all threads). */
 uint64_t folty_kernel_launches(void);

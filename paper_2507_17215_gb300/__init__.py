@@ -31,7 +31,7 @@ U_HEAD, U_TAIL, U_COMMON = 0, 1, 2
 EXPORTED = ["folty_load_temporal_graph", "folty_preprocess", "folty_query", "folty_query_batch",
             "folty_free", "folty_last_error", "folty_graph_get_info", "folty_graph_traffic_model",
             "folty_kernel_launches", "folty_profile_enable", "folty_profile_read",
-            "folty_edge_counts_noalloc", "folty_server_create", "folty_server_submit",
+            "folty_edge_counts_noalloc", "folty_graph_common_counts", "folty_server_create", "folty_server_submit",
             "folty_server_wait", "folty_server_get_stats", "folty_server_destroy"]
 
 
@@ -54,13 +54,16 @@ class folty_allocator(Structure):
 class folty_query_params(Structure):
     _fields_ = [("delta", c_int64), ("rho_num", c_uint32), ("rho_den", c_uint32),
                 ("quant", c_uint8), ("dir", c_uint8), ("universe", c_uint8),
-                ("want_edge_counts", c_uint8)]
+                ("want_edge_counts", c_uint8), ("outer", c_uint8), ("want_certificates", c_uint8),
+                ("reserved", c_uint8 * 2), ("outer_rho_num", c_uint32), ("outer_rho_den", c_uint32)]
 
 
 class folty_result(Structure):
     _fields_ = [("tag", c_uint64), ("n_pairs", c_int64), ("u", POINTER(c_int32)),
                 ("v", POINTER(c_int32)), ("count", POINTER(c_int32)), ("ncert", POINTER(c_int32)),
-                ("n_cert_edges", c_int64), ("m", c_int64), ("edge_count", POINTER(c_int32))]
+                ("n_cert_edges", c_int64), ("m", c_int64), ("edge_count", POINTER(c_int32)),
+                ("n_vertices", c_int64), ("vertex", POINTER(c_int32)), ("vertex_count", POINTER(c_int32)),
+                ("certificate", POINTER(c_int64))]
 
 
 class folty_graph_info(Structure):
@@ -126,6 +129,8 @@ def _load_library():
     lib.folty_profile_enable.argtypes = [c_int32]
     lib.folty_profile_read.restype = c_int32
     lib.folty_profile_read.argtypes = [POINTER(folty_profile)]
+    lib.folty_graph_common_counts.restype = c_int32
+    lib.folty_graph_common_counts.argtypes = [G, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.folty_server_create.restype = c_int32
     lib.folty_server_create.argtypes = [POINTER(c_void_p), c_int32, POINTER(folty_server_config),
                                         POINTER(c_void_p)]
@@ -226,8 +231,15 @@ def folty_preprocess(g: int, stream: Optional[int] = None) -> None:
 
 
 def _params(q) -> folty_query_params:
-    return folty_query_params(int(q.delta), int(q.rho_num), int(q.rho_den), int(q.quant),
-                              int(q.dir), int(q.universe), int(bool(getattr(q, "want_edge_counts", 0))))
+    p = folty_query_params()
+    p.delta, p.rho_num, p.rho_den = int(q.delta), int(q.rho_num), int(q.rho_den)
+    p.quant, p.dir, p.universe = int(q.quant), int(q.dir), int(q.universe)
+    p.want_edge_counts = int(bool(getattr(q, "want_edge_counts", 0)))
+    p.outer = int(getattr(q, "outer", 0))
+    p.want_certificates = int(bool(getattr(q, "want_certificates", 0)))
+    p.outer_rho_num = int(getattr(q, "outer_rho_num", 1))
+    p.outer_rho_den = int(getattr(q, "outer_rho_den", 2))
+    return p
 
 
 def _take_result(r: folty_result) -> Dict[str, object]:
@@ -242,6 +254,16 @@ def _take_result(r: folty_result) -> Dict[str, object]:
         out["edge_count"] = np.ctypeslib.as_array(r.edge_count, shape=(int(r.m),)).copy()
     else:
         out["edge_count"] = None
+    nv = int(r.n_vertices)
+    if r.vertex:
+        out["vertex"] = (np.ctypeslib.as_array(r.vertex, shape=(nv,)).copy() if nv > 0
+                         else np.zeros(0, dtype=np.int32))
+        out["vertex_count"] = (np.ctypeslib.as_array(r.vertex_count, shape=(nv,)).copy() if nv > 0
+                               else np.zeros(0, dtype=np.int32))
+    nc = int(r.n_cert_edges)
+    if r.certificate:
+        out["certificates"] = (np.ctypeslib.as_array(r.certificate, shape=(nc,)).copy() if nc > 0
+                               else np.zeros(0, dtype=np.int64))
     lib.folty_free(ctypes.byref(r))
     return out
 
@@ -281,6 +303,17 @@ def folty_graph_traffic_model(g: int, dir: int = DIR_OUT, stream: Optional[int] 
     _check(lib.folty_graph_traffic_model(g, int(dir), ctypes.byref(tm),
                                          current_stream() if stream is None else stream))
     return {name: int(getattr(tm, name)) for name, _ in folty_traffic_model._fields_}
+
+
+def folty_graph_common_counts(g: int, stream: Optional[int] = None):
+    """(a, b, c_ab) for every static edge a < b, sorted by (a, b)."""
+    S = folty_graph_get_info(g)["static_edges"]
+    a = np.zeros(max(S, 1), np.int32)
+    b = np.zeros(max(S, 1), np.int32)
+    c = np.zeros(max(S, 1), np.int32)
+    _check(lib.folty_graph_common_counts(g, a.ctypes.data, b.ctypes.data, c.ctypes.data,
+                                         current_stream() if stream is None else stream))
+    return a[:S], b[:S], c[:S]
 
 
 def folty_kernel_launches() -> int:

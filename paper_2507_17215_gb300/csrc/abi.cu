@@ -127,7 +127,8 @@ int32_t read_i32(folty_graph* g, const int32_t* p, cudaStream_t s) {
     return (int32_t)v;
 }
 
-void fill_result_host(folty_result* out, int64_t n_pairs, int64_t m, bool want_edges) {
+void fill_result_host(folty_result* out, int64_t n_pairs, int64_t m, bool want_edges, int64_t n_vertices,
+                      bool want_vertices, int64_t n_certs, bool want_certs) {
     std::memset(out, 0, sizeof(*out));
     out->tag = RESULT_TAG;
     out->n_pairs = n_pairs;
@@ -140,20 +141,39 @@ void fill_result_host(folty_result* out, int64_t n_pairs, int64_t m, bool want_e
         out->count = block + 2 * n_pairs;
         out->ncert = block + 3 * n_pairs;
     }
+    bool ok = true;
     if (want_edges) {
         out->edge_count = (int32_t*)std::calloc((size_t)(m > 0 ? m : 1), sizeof(int32_t));
-        if (!out->edge_count) {
-            std::free(out->u);
-            out->u = nullptr;
-            fail(FOLTY_ENOMEM, "host allocation of the edge counts failed");
-        }
+        ok = ok && out->edge_count;
+    }
+    if (want_vertices) {
+        out->n_vertices = n_vertices;
+        out->vertex = (int32_t*)std::malloc(sizeof(int32_t) * 2 * (size_t)(n_vertices > 0 ? n_vertices : 1));
+        out->vertex_count = out->vertex ? out->vertex + n_vertices : nullptr;
+        ok = ok && out->vertex;
+    }
+    if (want_certs) {
+        out->certificate = (int64_t*)std::malloc(sizeof(int64_t) * (size_t)(n_certs > 0 ? n_certs : 1));
+        ok = ok && out->certificate;
+    }
+    if (!ok) {
+        std::free(out->u);
+        std::free(out->edge_count);
+        std::free(out->vertex);
+        std::free(out->certificate);
+        std::memset(out, 0, sizeof(*out));
+        fail(FOLTY_ENOMEM, "host allocation of the result failed");
     }
 }
 
 static void free_result(folty_result* r) {
     std::free(r->u);
     std::free(r->edge_count);
+    std::free(r->vertex);
+    std::free(r->certificate);
     r->u = r->v = r->count = r->ncert = r->edge_count = nullptr;
+    r->vertex = r->vertex_count = nullptr;
+    r->certificate = nullptr;
     r->n_pairs = 0;
     r->tag = FREED_TAG;
 }
@@ -362,6 +382,22 @@ folty_status folty_graph_traffic_model(folty_graph* g, int32_t dir, folty_traffi
         if (dir < 0 || dir > 2) fail(FOLTY_EINVAL, "unknown direction variant");
         if (g->state != 1) fail(FOLTY_ESTATE, "graph not preprocessed");
         traffic_model(g, dir, out, (cudaStream_t)stream);
+    });
+}
+
+folty_status folty_graph_common_counts(folty_graph* g, int32_t* a, int32_t* b, int32_t* c, void* stream) {
+    return guarded([&] {
+        checked_graph(g);
+        if (g->state != 1) fail(FOLTY_ESTATE, "graph not preprocessed");
+        if (g->S > 0 && (!a || !b || !c)) fail(FOLTY_EINVAL, "output arrays are NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        const size_t bytes = sizeof(int32_t) * (size_t)g->S;
+        if (g->S > 0) {
+            FOLTY_CUDA(cudaMemcpyAsync(a, g->ea, bytes, cudaMemcpyDeviceToHost, s));
+            FOLTY_CUDA(cudaMemcpyAsync(b, g->eb, bytes, cudaMemcpyDeviceToHost, s));
+            FOLTY_CUDA(cudaMemcpyAsync(c, g->common, bytes, cudaMemcpyDeviceToHost, s));
+        }
+        FOLTY_CUDA(cudaStreamSynchronize(s));
     });
 }
 

@@ -107,10 +107,16 @@ int64_t batch_footprint(const folty_graph* g, const folty_query_params* qs, int 
     // of 2S + 1, compacted keys, packed output, edge counts when asked
     const int64_t n2 = 2 * (int64_t)g->S;
     int64_t per_q = 6 * 4 * (n2 + 1) + 8 * n2 + 16 * n2 + 64;
-    bool edges = false;
-    for (int i = 0; i < nq; i++) edges = edges || qs[i].want_edge_counts;
+    bool edges = false, certs = false, outer = false;
+    for (int i = 0; i < nq; i++) {
+        edges = edges || qs[i].want_edge_counts;
+        certs = certs || qs[i].want_certificates;
+        outer = outer || qs[i].outer;
+    }
     if (edges) per_q += 4 * g->m;
-    const int64_t group = std::min<int64_t>(nq, READBACK_MAX / 3);
+    if (certs) per_q += 16 * (g->m + 1);
+    if (outer) per_q += 14 * ((int64_t)g->n + 1);
+    const int64_t group = std::min<int64_t>(nq, READBACK_MAX / 4);
     if (bins_part) *bins_part = bins;
     return bins + group * per_q;
 }

@@ -227,7 +227,8 @@ class ProbeTimer {
     cudaEvent_t a_ = nullptr, b_ = nullptr;
     bool on_ = false, started_ = false, stopped_ = false;
 };
-void fill_result_host(folty_result* out, int64_t n_pairs, int64_t m, bool want_edges);
+void fill_result_host(folty_result* out, int64_t n_pairs, int64_t m, bool want_edges, int64_t n_vertices,
+                      bool want_vertices, int64_t n_certs, bool want_certs);
 
 // ------------------------------------------------------------------ device helpers
 

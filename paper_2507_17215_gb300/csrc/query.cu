@@ -63,6 +63,8 @@ struct ThresholdArgs {
     int32_t* seg_max;    // [2S]
     int32_t* seg_ncert;  // [2S]
     unsigned long long* n_cert;
+    const int32_t* perm;  // with cert_in: certificate flag of input edge perm[i]
+    int32_t* cert_in;     // [m] or null
 };
 
 // Certificate test of Definition 1.1 with rho = num / den, exact in int64.
@@ -88,6 +90,7 @@ __global__ void k_threshold(ThresholdArgs a) {
             int64_t U = a.universe == FOLTY_U_HEAD ? a.deg[x]
                         : a.universe == FOLTY_U_TAIL ? a.deg[y] : a.common[s];
             sat = certifies(a.quant, c, U, a.num, a.den);
+            if (a.cert_in) a.cert_in[a.perm[i]] = sat;
         }
         // equal keys are contiguous (sorted order): reduce each run once
         unsigned peers = __match_any_sync(0xffffffffu, key);
@@ -179,6 +182,47 @@ __global__ void k_edge_counts_input_order(const int32_t* __restrict__ cnt, const
         out[perm[i]] = cnt[i];
 }
 
+// Input indices of the flagged edges, ascending (pos = exclusive scan of flag).
+__global__ void k_compact_indices(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t m,
+                                  int64_t* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        if (flag[e]) out[pos[e]] = e;
+}
+
+// Section 4: number of solution pairs headed by each vertex (flag = pair flags of the
+// two sorted lists, see k_pair_flags).
+__global__ void k_vertex_count(const int32_t* __restrict__ flag, int64_t S, const int32_t* __restrict__ ea,
+                               const int32_t* __restrict__ eb, const int32_t* __restrict__ by_b,
+                               int32_t* __restrict__ vcnt) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * S;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[i]) continue;
+        const int32_t x = (i < S) ? ea[i] : eb[by_b[i - S]];
+        atomicAdd(&vcnt[x], 1);
+    }
+}
+
+// Outer threshold of Section 4: count >= 1 and count * den1 >= num1 * |N(u)|.
+__global__ void k_vertex_flags(const int32_t* __restrict__ vcnt, const int32_t* __restrict__ deg, int64_t n,
+                               int64_t num1, int64_t den1, int32_t* __restrict__ vflag) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = vcnt[u];
+        vflag[u] = c >= 1 && c * den1 >= num1 * (int64_t)deg[u];
+    }
+}
+
+__global__ void k_vertex_compact(const int32_t* __restrict__ vflag, const int32_t* __restrict__ vpos,
+                                 const int32_t* __restrict__ vcnt, int64_t n, int64_t nv, int32_t* __restrict__ out) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        if (!vflag[u]) continue;
+        out[vpos[u]] = (int32_t)u;
+        out[nv + vpos[u]] = vcnt[u];
+    }
+}
+
 // ================================================================== drivers
 
 void validate_query(const folty_query_params& q) {
@@ -187,6 +231,9 @@ void validate_query(const folty_query_params& q) {
     if (q.quant > FOLTY_Q_FORALL_T) fail(FOLTY_EINVAL, "unknown quantifier");
     if (q.dir > FOLTY_DIR_EITHER) fail(FOLTY_EINVAL, "unknown direction variant");
     if (q.universe > FOLTY_U_COMMON) fail(FOLTY_EINVAL, "unknown universe");
+    if (q.outer > FOLTY_OUTER_FORALL_T) fail(FOLTY_EINVAL, "unknown outer quantifier");
+    if (q.outer && (q.outer_rho_den == 0 || q.outer_rho_num > q.outer_rho_den))
+        fail(FOLTY_EINVAL, "outer rho must satisfy 0 <= outer_rho_num <= outer_rho_den, outer_rho_den > 0");
 }
 
 template <typename TS, int DIR>
@@ -221,11 +268,26 @@ struct PairStage {
     int32_t* cnt_c;      // [2S]
     int32_t* nc_c;       // [2S]
     unsigned long long* n_cert;
+    int32_t* cert_flag;  // [m + 1] certificate flags in input order (want_certificates)
+    int32_t* cert_pos;   // [m + 1]
+    int32_t* vcnt;       // [n + 1] solution pairs per head vertex (outer queries)
+    int32_t* vflag;      // [n + 1]
+    int32_t* vpos;       // [n + 1]
 };
 
-static PairStage pair_stage(Scratch& sc, const folty_graph* g) {
+static PairStage pair_stage(Scratch& sc, const folty_graph* g, const folty_query_params& q) {
     const int64_t n2 = 2 * (int64_t)g->S;
     PairStage p;
+    p.cert_flag = p.cert_pos = p.vcnt = p.vflag = p.vpos = nullptr;
+    if (q.want_certificates) {
+        p.cert_flag = sc.get<int32_t>(2 * (g->m + 1));
+        p.cert_pos = p.cert_flag + g->m + 1;
+    }
+    if (q.outer) {
+        p.vcnt = sc.get<int32_t>(3 * ((int64_t)g->n + 1));
+        p.vflag = p.vcnt + g->n + 1;
+        p.vpos = p.vflag + g->n + 1;
+    }
     p.seg_max = sc.get<int32_t>(2 * n2 + 2);
     p.seg_ncert = p.seg_max + n2 + 1;
     p.flag = sc.get<int32_t>(2 * n2 + 2);
@@ -245,16 +307,27 @@ static void pairs_device(folty_graph* g, const folty_query_params& q, const int3
     const int64_t S = g->S, n2 = 2 * S;
     FOLTY_CUDA(cudaMemsetAsync(p.seg_max, 0, sizeof(int32_t) * (size_t)(2 * n2 + 2), s));
     FOLTY_CUDA(cudaMemsetAsync(p.n_cert, 0, sizeof(unsigned long long), s));
+    if (p.cert_flag) FOLTY_CUDA(cudaMemsetAsync(p.cert_flag, 0, sizeof(int32_t) * (size_t)(g->m + 1), s));
     if (mk > 0) {
         ThresholdArgs a{cnt, g->sd, mk, g->ea, g->eb, g->deg, g->common, (int)q.quant, (int)q.universe,
-                        (int64_t)q.rho_num, (int64_t)q.rho_den, p.seg_max, p.seg_ncert, p.n_cert};
+                        (int64_t)q.rho_num, (int64_t)q.rho_den, p.seg_max, p.seg_ncert, p.n_cert,
+                        g->perm, p.cert_flag};
         FOLTY_LAUNCH(k_threshold, grid_for(mk, T), T, 0, s, a);
     }
+    if (p.cert_flag) exclusive_scan(sc, p.cert_flag, p.cert_pos, g->m);
     if (n2 > 0) FOLTY_LAUNCH(k_pair_flags, grid_for(n2, T), T, 0, s, p.seg_ncert, g->by_b, S, p.flag);
     exclusive_scan(sc, p.flag, p.pos, n2);
     if (n2 > 0)
         FOLTY_LAUNCH(k_pair_compact, grid_for(n2, T), T, 0, s, p.flag, p.pos, S, g->ea, g->eb, g->by_b, p.seg_max,
                      p.seg_ncert, p.key, p.cnt_c, p.nc_c);
+    if (p.vcnt) {
+        const int64_t n = g->n;
+        FOLTY_CUDA(cudaMemsetAsync(p.vcnt, 0, sizeof(int32_t) * (size_t)(n + 1), s));
+        if (n2 > 0) FOLTY_LAUNCH(k_vertex_count, grid_for(n2, T), T, 0, s, p.flag, S, g->ea, g->eb, g->by_b, p.vcnt);
+        FOLTY_LAUNCH(k_vertex_flags, grid_for(n, T), T, 0, s, p.vcnt, g->deg, n, (int64_t)q.outer_rho_num,
+                     (int64_t)q.outer_rho_den, p.vflag);
+        exclusive_scan(sc, p.vflag, p.vpos, n);
+    }
 }
 
 void finish_queries(folty_graph* g, const folty_query_params* const* qs, const int32_t* const* cnts, int nq,
@@ -262,13 +335,13 @@ void finish_queries(folty_graph* g, const folty_query_params* const* qs, const i
     const int T = 256;
     const int64_t S = g->S;
     const int64_t mk = g->m_kept;
-    const int G = READBACK_MAX / 3;
+    const int G = READBACK_MAX / 4;
     for (int g0 = 0; g0 < nq; g0 += G) {
         const int ng = std::min(G, nq - g0);
         Scratch sc(g->alloc, s);
         std::vector<PairStage> st;
         for (int i = 0; i < ng; i++) {
-            st.push_back(pair_stage(sc, g));
+            st.push_back(pair_stage(sc, g, *qs[g0 + i]));
             pairs_device(g, *qs[g0 + i], cnts[g0 + i], st.back(), sc, s);
         }
         // one read-back for the group: pairs x < y, all pairs, certificates
@@ -278,16 +351,29 @@ void finish_queries(folty_graph* g, const folty_query_params* const* qs, const i
             ptrs.push_back(st[i].pos + S);
             ptrs.push_back(st[i].pos + 2 * S);
             ptrs.push_back(st[i].n_cert);
-            sizes.insert(sizes.end(), {4, 4, 8});
+            ptrs.push_back(st[i].vpos ? (const void*)(st[i].vpos + g->n) : (const void*)st[i].pos);
+            sizes.insert(sizes.end(), {4, 4, 8, 4});
         }
-        std::vector<int64_t> rb(3 * (size_t)ng);
-        read_back(g, ptrs.data(), sizes.data(), 3 * ng, rb.data(), s);
+        std::vector<int64_t> rb(4 * (size_t)ng);
+        read_back(g, ptrs.data(), sizes.data(), 4 * ng, rb.data(), s);
         for (int i = 0; i < ng; i++) {
             const folty_query_params& q = *qs[g0 + i];
             folty_result* out = outs[g0 + i];
-            const int64_t nA = rb[3 * i], np = rb[3 * i + 1];
-            fill_result_host(out, np, g->m, q.want_edge_counts != 0);
-            out->n_cert_edges = rb[3 * i + 2];
+            const int64_t nA = rb[4 * i], np = rb[4 * i + 1], nc = rb[4 * i + 2];
+            const int64_t nv = q.outer ? rb[4 * i + 3] : 0;
+            fill_result_host(out, np, g->m, q.want_edge_counts != 0, nv, q.outer != 0, nc, q.want_certificates != 0);
+            out->n_cert_edges = nc;
+            if (q.outer && nv > 0) {
+                int32_t* vout = sc.get<int32_t>(2 * nv);
+                FOLTY_LAUNCH(k_vertex_compact, grid_for(g->n, T), T, 0, s, st[i].vflag, st[i].vpos, st[i].vcnt,
+                             (int64_t)g->n, nv, vout);
+                FOLTY_CUDA(cudaMemcpyAsync(out->vertex, vout, sizeof(int32_t) * 2 * (size_t)nv, cudaMemcpyDeviceToHost, s));
+            }
+            if (q.want_certificates && nc > 0) {
+                int64_t* cout = sc.get<int64_t>(nc);
+                FOLTY_LAUNCH(k_compact_indices, grid_for(g->m, T), T, 0, s, st[i].cert_flag, st[i].cert_pos, g->m, cout);
+                FOLTY_CUDA(cudaMemcpyAsync(out->certificate, cout, sizeof(int64_t) * (size_t)nc, cudaMemcpyDeviceToHost, s));
+            }
             if (np > 0) {
                 int32_t* packed = sc.get<int32_t>(4 * np);
                 FOLTY_LAUNCH(k_pair_merge, grid_for(np, T), T, 0, s, st[i].key, st[i].cnt_c, st[i].nc_c, nA, np,

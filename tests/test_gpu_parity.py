@@ -5,7 +5,9 @@ import pytest
 
 import oracle
 import workloads as W
-from _support import golden_files, pairs_of, parse_fixture
+import dataclasses
+
+from _support import golden_files, pairs_of, parse_fixture, vertices_of
 
 pytestmark = pytest.mark.gpu
 
@@ -54,12 +56,13 @@ def _check_graph(F, g, queries, allocator="torch"):
 @pytest.mark.parametrize("path", golden_files(), ids=lambda p: p.split("/")[-1])
 def test_golden_fixtures_through_library(F, path):
     g, cases = parse_fixture(path)
-    qs = [W.Query(c["q"].delta, c["q"].rho_num, c["q"].rho_den, c["q"].quant, c["q"].dir,
-                  c["q"].universe, True) for c in cases]
+    qs = [dataclasses.replace(c["q"], want_edge_counts=True) for c in cases]
     res, _ = _lib_results(F, g, qs)
     for c, r in zip(cases, res):
         np.testing.assert_array_equal(r["edge_count"], c["counts"])
         assert pairs_of(r) == c["pairs"]
+        if "vertices" in c:
+            assert vertices_of(r) == c["vertices"]
 
 
 def test_random_tiny_graphs(F):
@@ -335,3 +338,60 @@ def test_kernel_launch_counter_moves(F):
     with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
         G.query(W.Query(3600))
     assert F.folty_kernel_launches() > before + 10
+
+
+def _outer_mix(deltas):
+    qs = []
+    for d in deltas:
+        for quant in (W.Q_FORALL_T, W.Q_EXISTS):
+            for num1, den1 in ((0, 1), (1, 10), (1, 3), (1, 1)):
+                qs.append(W.Query(d, 1, 3, quant, W.DIR_OUT if num1 % 2 else W.DIR_EITHER, W.U_TAIL, False,
+                                  outer=W.OUTER_FORALL_T, outer_rho_num=num1, outer_rho_den=den1,
+                                  want_certificates=True))
+    return qs
+
+
+@pytest.mark.parametrize("which", ["tiny", "config1", "medium_small"])
+def test_vertex_queries_and_certificates(F, which):
+    rng = np.random.default_rng(31)
+    if which == "tiny":
+        graphs = [W.random_small_graph(rng, 12, 80, 20) for _ in range(5)]
+        deltas = (0, 4, 30)
+    elif which == "config1":
+        graphs = [W.config_graph(1)]
+        deltas = (100_000, 1_000_000)
+    else:
+        graphs = [W.config_graph(2, scale=0.01)]
+        deltas = (3600, 604_800)
+    for g in graphs:
+        qs = _outer_mix(deltas)
+        res, _ = _lib_results(F, g, qs)
+        bat, _ = _lib_results(F, g, qs, batch=True)
+        with oracle.OracleGraph.of(g) as og:
+            for q, r, rb in zip(qs, res, bat):
+                want = og.query(q)
+                for got in (r, rb):
+                    assert pairs_of(got) == pairs_of(want), str(q)
+                    assert vertices_of(got) == vertices_of(want), str(q)
+                    np.testing.assert_array_equal(got["certificates"], want["certificates"])
+                    assert got["n_cert_edges"] == len(want["certificates"])
+
+
+def test_common_neighbour_counts(F):
+    for g in (W.config_graph(1), W.config_graph(3, scale=0.002)):
+        with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
+            a, b, c = F.folty_graph_common_counts(G.handle)
+        keep = g.src != g.dst
+        lo = np.minimum(g.src, g.dst)[keep].astype(np.int64)
+        hi = np.maximum(g.src, g.dst)[keep].astype(np.int64)
+        key = np.unique(lo * g.n + hi)
+        np.testing.assert_array_equal(a.astype(np.int64) * g.n + b, key)
+        # one input edge per static edge: the oracle's |N(x) cap N(y)|
+        first = {}
+        for i in np.nonzero(keep)[0]:
+            k = int(min(g.src[i], g.dst[i])) * g.n + int(max(g.src[i], g.dst[i]))
+            first.setdefault(k, int(i))
+        idx = np.array([first[int(k)] for k in key], dtype=np.int64)
+        with oracle.OracleGraph.of(g) as og:
+            _, common = og.counts(0, W.DIR_OUT, idx=idx)
+        np.testing.assert_array_equal(c, common)
