@@ -2,8 +2,9 @@
 //
 // For a fixed (temporal edge e, witness w, direction variant) the searched t2 and t3
 // of Theorem 3.1 do not depend on delta, so hit(delta) <=> g(e, w) = t3 - t <= delta.
-// One probe pass per direction variant therefore serves every delta of that variant:
-// the pass bins g by the sorted distinct deltas D (bin j = first D_j >= g), a prefix
+// One probe pass per direction variant therefore serves every delta of that variant
+// (live.cu, binning mode, roles kept for the largest delta of the pass): the pass bins
+// g by the sorted distinct deltas D (bin j = first D_j >= g), a prefix
 // over the bins gives c_e(D_j) = #{w : g(e, w) <= D_j} for all j at once, and each
 // query's threshold pass (the single-query code) reads its column. Quantifier, rho and
 // universe only enter that last pass. When the bins of all deltas do not fit in the
@@ -18,53 +19,6 @@
 namespace folty {
 
 constexpr int BATCH_MAX_BINS = 1024;
-
-template <typename TS, int DIR>
-__global__ void __launch_bounds__(PB_THREADS) k_probe_binned(const int4* __restrict__ tri,
-                                                             const int64_t* __restrict__ tri_off,
-                                                             const int64_t* __restrict__ tile_tri, int64_t P,
-                                                             const int32_t* __restrict__ seg,
-                                                             const TS* __restrict__ T,
-                                                             const TS* __restrict__ deltas, int k,
-                                                             int32_t* __restrict__ bins, int64_t mk) {
-    __shared__ TriStage st;
-    __shared__ TS sD[BATCH_MAX_BINS];
-    for (int i = threadIdx.x; i < k; i += blockDim.x) sD[i] = deltas[i];
-    const int64_t p0 = (int64_t)blockIdx.x * PB_TILE;
-    const int32_t count = (int32_t)min((int64_t)PB_TILE, P - p0);
-    stage_triangles(st, tri, tri_off, tile_tri, seg, DIR);  // ends with __syncthreads
-    const TS dmax = sD[k - 1];
-#pragma unroll 1
-    for (int it = 0; it < PB_ITEMS; it++) {
-        const int32_t local = it * PB_THREADS + (int32_t)threadIdx.x;
-        if ((local & ~31) >= count) break;  // warp-uniform
-        const bool active = local < count;
-        Probe pr = locate_probe(st, local, active);
-        if (!active) continue;
-        const TS t = T[pr.pos];
-        const TS t3 = probe_window<TS, DIR>(T, st.off[pr.j], pr.seg2, pr.seg3, t, dmax);
-        if (t3 == TsNone<TS>::value) continue;
-        const TS gap = (TS)(t3 - t);
-        if (gap > dmax) continue;
-        const int j = lower_bound_ts<TS>(sD, 0, k, gap);
-        atomicAdd(&bins[(int64_t)j * mk + pr.pos], 1);
-    }
-}
-
-template <typename TS>
-static void launch_binned(folty_graph* g, int dir, const TS* deltas, int k, int32_t* bins, cudaStream_t s) {
-    const unsigned grid = (unsigned)g->n_tiles;
-    const TS* T = (const TS*)g->T;
-    if (dir == FOLTY_DIR_OUT)
-        FOLTY_LAUNCH((k_probe_binned<TS, FOLTY_DIR_OUT>), grid, PB_THREADS, 0, s, g->tri, g->tri_off, g->tile_tri,
-                     g->info.probes, g->seg, T, deltas, k, bins, g->m_kept);
-    else if (dir == FOLTY_DIR_IN)
-        FOLTY_LAUNCH((k_probe_binned<TS, FOLTY_DIR_IN>), grid, PB_THREADS, 0, s, g->tri, g->tri_off, g->tile_tri,
-                     g->info.probes, g->seg, T, deltas, k, bins, g->m_kept);
-    else
-        FOLTY_LAUNCH((k_probe_binned<TS, FOLTY_DIR_EITHER>), grid, PB_THREADS, 0, s, g->tri, g->tri_off,
-                     g->tile_tri, g->info.probes, g->seg, T, deltas, k, bins, g->m_kept);
-}
 
 // bins[j][e] <- sum_{i <= j} bins[i][e]
 __global__ void k_bins_prefix(int32_t* __restrict__ bins, int k, int64_t mk) {
@@ -156,12 +110,7 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
             if (mk > 0) {
                 FOLTY_CUDA(cudaMemsetAsync(bins, 0, sizeof(int32_t) * (size_t)(mk * k), s));
                 ProbeTimer timer(s);
-                timer.start();
-                if (P > 0) {
-                    if (g->ts32) launch_binned<uint32_t>(g, dir, (const uint32_t*)dd, k, bins, s);
-                    else launch_binned<int64_t>(g, dir, (const int64_t*)dd, k, bins, s);
-                }
-                timer.stop();
+                if (P > 0) launch_probe_live(g, hd[k - 1], dir, 1, nullptr, bins, k, dd, &timer, s);
                 if (k > 1) FOLTY_LAUNCH(k_bins_prefix, grid_for(mk, 256), 256, 0, s, bins, k, mk);
                 FOLTY_CUDA(cudaStreamSynchronize(s));  // the host bounds must outlive the copy
                 timer.collect();

@@ -138,6 +138,8 @@ struct folty_graph {
     int4* tri;        // [ntri] {s_uv, s_uw, s_vw, id-order bits}, u < v < w in degeneracy rank
     int64_t* tri_off; // [ntri + 1] prefix of per-triangle probe counts
     int64_t* tile_tri;  // [probe tiles + 1] triangle holding each tile's first probe
+    int32_t* rsig;      // [6][ntri] |L1| of every role (role r = 2 * edge + direction)
+    uint8_t* rmin;      // [3][6][ntri] bucket of the smallest window a role can hit with
     int64_t n_tiles;
     int64_t enum_bytes; // model bytes of the triangle enumeration
     int64_t tmin, tmax; // timestamp range of the input
@@ -200,19 +202,6 @@ int64_t batch_footprint(const folty_graph* g, const folty_query_params* qs, int 
 void traffic_model(folty_graph* g, int dir, folty_traffic_model* out, cudaStream_t s);
 
 void validate_query(const folty_query_params& q);
-// Window-probe pass of one query into counters cnt[m_kept] (sorted order, zeroed).
-void launch_probe(folty_graph* g, int64_t delta, int dir, int32_t* cnt, cudaStream_t s);
-// The same pass with the counters in a file-scope device array (noalloc.cu).
-void edge_counts_noalloc(folty_graph* g, int64_t delta, int dir, int32_t* edge_count, cudaStream_t s);
-// Threshold, pair output and result copy-out for per-edge counts cnt[m_kept] (sorted
-// order); synchronises the stream.
-void finish_query(folty_graph* g, const folty_query_params& q, const int32_t* cnt, folty_result* out,
-                  cudaStream_t s);
-// The same for nq queries at once (counts cnts[i]), with two stream synchronisations
-// for the whole group.
-void finish_queries(folty_graph* g, const folty_query_params* const* qs, const int32_t* const* cnts, int nq,
-                    folty_result* const* outs, cudaStream_t s);
-
 // Event pair around probe launches when profiling is on (abi.cu holds the totals).
 class ProbeTimer {
   public:
@@ -227,6 +216,26 @@ class ProbeTimer {
     cudaEvent_t a_ = nullptr, b_ = nullptr;
     bool on_ = false, started_ = false, stopped_ = false;
 };
+
+// Window-probe pass of one query into counters cnt[m_kept] (sorted order, zeroed).
+void launch_probe(folty_graph* g, int64_t delta, int dir, int32_t* cnt, cudaStream_t s);
+// Window probes of the roles that can hit (live.cu): mode 0 counts hits at delta into
+// cnt; mode 1 bins gaps <= delta into bins[k][m_kept] against the k sorted bounds
+// `deltas` (in the timestamp store's type).
+void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t* cnt, int32_t* bins, int k,
+                       const void* deltas, ProbeTimer* timer, cudaStream_t s);
+void build_role_summary(folty_graph* g, cudaStream_t s);
+// The same pass with the counters in a file-scope device array (noalloc.cu).
+void edge_counts_noalloc(folty_graph* g, int64_t delta, int dir, int32_t* edge_count, cudaStream_t s);
+// Threshold, pair output and result copy-out for per-edge counts cnt[m_kept] (sorted
+// order); synchronises the stream.
+void finish_query(folty_graph* g, const folty_query_params& q, const int32_t* cnt, folty_result* out,
+                  cudaStream_t s);
+// The same for nq queries at once (counts cnts[i]), with two stream synchronisations
+// for the whole group.
+void finish_queries(folty_graph* g, const folty_query_params* const* qs, const int32_t* const* cnts, int nq,
+                    folty_result* const* outs, cudaStream_t s);
+
 void fill_result_host(folty_result* out, int64_t n_pairs, int64_t m, bool want_edges, int64_t n_vertices,
                       bool want_vertices, int64_t n_certs, bool want_certs);
 

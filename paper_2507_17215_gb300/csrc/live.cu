@@ -1,0 +1,316 @@
+// Window probes restricted to roles that can hit.
+//
+// A role (temporal edges x -> y of one static edge, witness z; lists L1 = E_{x,y}, L2,
+// L3 of its direction variant) can only produce a window match t <= t2 <= t3 <= t + delta
+// if its runs overlap in time: L2 must end at or after L1 starts, L3 must end at or
+// after max(L1.first, L2.first), and L2 and L3 must start by L1.last + delta. The first
+// two conditions do not depend on delta; the last two hold exactly when
+// delta >= dmin = max(0, L2.first - L1.last, L3.first - L1.last).
+//
+// Preprocessing stores, per triangle and role, sigma1 = |L1| and a conservative bucket of
+// dmin per direction variant: its bit length b (0 for dmin = 0, 255 for "never"), so
+// 2^(b-1) <= dmin. A query keeps a role when delta >= 2^(b-1), which holds whenever
+// delta >= dmin: no role that can hit is dropped (a few that cannot are kept). Each
+// query then lists the triangles with a kept role, lays their kept roles out in a flat
+// probe space (3 idle slots per triangle keep the tile staging bound) and probes only
+// those, with the exact window test of Theorem 3.1. On the synthetic workloads about
+// 1-7 % of all (edge, witness) pairs lie in kept roles.
+#include "internal.cuh"
+#include "probe.cuh"
+
+namespace folty {
+
+constexpr int LIVE_IDLE = 3;  // idle slots per kept triangle (keeps >= 3 slots per triangle)
+constexpr uint8_t DMIN_NEVER = 255;
+
+template <typename TS>
+__device__ __forceinline__ void run_range(const TS* __restrict__ T, int32_t b, int32_t e, int64_t& first,
+                                          int64_t& last, bool& any) {
+    if (b < e) {
+        const int64_t f = (int64_t)T[b], l = (int64_t)T[e - 1];
+        first = any ? (f < first ? f : first) : f;
+        last = any ? (l > last ? l : last) : l;
+        any = true;
+    }
+}
+
+// rsig[r][t] = sigma1 of role r = 2e + d; rmin[dir][r][t] = dmin bucket.
+template <typename TS>
+__global__ void k_role_summary(const int4* __restrict__ tri, int64_t ntri, const int32_t* __restrict__ seg,
+                               const TS* __restrict__ T, int32_t* __restrict__ rsig, uint8_t* __restrict__ rmin) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntri;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int4 tr = tri[t];
+        int32_t off[9];
+        const int32_t se[3] = {tr.x, tr.y, tr.z};
+#pragma unroll
+        for (int e = 0; e < 3; e++) {
+            off[3 * e] = seg[2 * se[e]];
+            off[3 * e + 1] = seg[2 * se[e] + 1];
+            off[3 * e + 2] = seg[2 * se[e] + 2];
+        }
+#pragma unroll
+        for (int r = 0; r < 6; r++) {
+            const int e = r >> 1, d = r & 1;
+            const int32_t b1 = off[3 * e + d], e1 = off[3 * e + d + 1];
+            rsig[r * ntri + t] = e1 - b1;
+            for (int dir = 0; dir < 3; dir++) {
+                uint8_t bucket = DMIN_NEVER;
+                if (e1 > b1) {
+                    int s2, s3;
+                    role_segments(tr.w, e, d, dir, s2, s3);
+                    const int o2 = 3 * (s2 >> 1) + (s2 & 1), o3 = 3 * (s3 >> 1) + (s3 & 1);
+                    int64_t f2 = 0, l2 = 0, f3 = 0, l3 = 0;
+                    bool a2 = false, a3 = false;
+                    run_range(T, off[o2], off[o2 + 1], f2, l2, a2);
+                    run_range(T, off[o3], off[o3 + 1], f3, l3, a3);
+                    if (dir == FOLTY_DIR_EITHER) {
+                        run_range(T, off[o2 + 1], off[o2 + 2], f2, l2, a2);
+                        run_range(T, off[o3 + 1], off[o3 + 2], f3, l3, a3);
+                    }
+                    const int64_t f1 = (int64_t)T[b1], l1 = (int64_t)T[e1 - 1];
+                    if (a2 && a3 && l2 >= f1 && l3 >= (f2 > f1 ? f2 : f1)) {
+                        int64_t dmin = f2 - l1;
+                        if (f3 - l1 > dmin) dmin = f3 - l1;
+                        if (dmin < 0) dmin = 0;
+                        bucket = (uint8_t)(64 - __clzll((unsigned long long)dmin));  // 0 for dmin = 0
+                    }
+                }
+                rmin[((int64_t)dir * 6 + r) * ntri + t] = bucket;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ bool bucket_live(uint8_t b, int64_t delta) {
+    return b != DMIN_NEVER && (b == 0 || delta >= ((int64_t)1 << (b - 1)));
+}
+
+// Kept roles of every triangle for one query: mask, kept probes + idle slots.
+__global__ void k_live_tri(const int32_t* __restrict__ rsig, const uint8_t* __restrict__ rmin_dir, int64_t ntri,
+                           int64_t delta, int32_t* __restrict__ flag, int64_t* __restrict__ cost,
+                           uint8_t* __restrict__ mask) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntri;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int m = 0;
+        int64_t lp = 0;
+#pragma unroll
+        for (int r = 0; r < 6; r++) {
+            const int32_t s1 = rsig[r * ntri + t];
+            if (s1 > 0 && bucket_live(rmin_dir[r * ntri + t], delta)) {
+                m |= 1 << r;
+                lp += s1;
+            }
+        }
+        flag[t] = lp > 0;
+        cost[t] = lp > 0 ? lp + LIVE_IDLE : 0;
+        mask[t] = (uint8_t)m;
+    }
+}
+
+__global__ void k_live_compact(const int32_t* __restrict__ flag, const int32_t* __restrict__ lpos,
+                               const int64_t* __restrict__ lcost, const uint8_t* __restrict__ mask, int64_t ntri,
+                               int32_t* __restrict__ L, int64_t* __restrict__ loff, uint8_t* __restrict__ lmask) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= ntri;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (t == ntri) {
+            loff[lpos[ntri]] = lcost[ntri];
+            continue;
+        }
+        if (!flag[t]) continue;
+        const int32_t j = lpos[t];
+        L[j] = (int32_t)t;
+        loff[j] = lcost[t];
+        lmask[j] = mask[t];
+    }
+}
+
+// ltile[b] = kept triangle holding slot min(b * PB_TILE, P - 1) (P, nlive on the device).
+__global__ void k_live_tiles(const int64_t* __restrict__ loff, const int32_t* __restrict__ nlive_p,
+                             const int64_t* __restrict__ P_p, int64_t max_tiles, int64_t* __restrict__ ltile) {
+    const int64_t P = *P_p;
+    const int64_t nlive = *nlive_p;
+    if (P <= 0) return;
+    const int64_t tiles = (P + PB_TILE - 1) / PB_TILE;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b <= tiles && b <= max_tiles;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = min(b * (int64_t)PB_TILE, P - 1);
+        int64_t lo = 0, hi = nlive - 1;
+        while (lo < hi) {
+            int64_t mid = (lo + hi + 1) >> 1;
+            if (loff[mid] <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        ltile[b] = lo;
+    }
+}
+
+struct LiveArgs {
+    const int4* tri;
+    const int32_t* seg;
+    const int32_t* L;
+    const int64_t* loff;
+    const uint8_t* lmask;
+    const int64_t* ltile;
+    const int64_t* P;  // device: total slots
+    int32_t* cnt;      // MODE 0
+    int32_t* bins;     // MODE 1
+    int64_t mk;
+    int k;             // MODE 1: number of bins
+};
+
+// MODE 0: cnt[pos] += hit at window delta. MODE 1: bin the gap t3 - t (<= delta, the
+// largest bin bound) against the sorted bounds deltas[0..k).
+template <typename TS, int DIR, int MODE>
+__global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS* __restrict__ T, TS delta,
+                                                           const TS* __restrict__ deltas) {
+    __shared__ TriStage st;
+    __shared__ uint8_t smask[PB_MAXTRI];
+    __shared__ TS sD[1024];
+    if (MODE == 1)
+        for (int i = threadIdx.x; i < a.k; i += blockDim.x) sD[i] = deltas[i];
+    const int64_t P = *a.P;
+    const int64_t tiles = (P + PB_TILE - 1) / PB_TILE;
+    for (int64_t b = blockIdx.x; b < tiles; b += gridDim.x) {
+        __syncthreads();  // the previous tile's stage is no longer read
+        const int64_t t0 = a.ltile[b];
+        const int nt = (int)(a.ltile[b + 1] - t0 + 1);
+        const int64_t p0 = b * (int64_t)PB_TILE;
+        for (int j = threadIdx.x; j < nt; j += blockDim.x) {
+            const int4 tr = a.tri[a.L[t0 + j]];
+            st.base[j] = (int32_t)(a.loff[t0 + j] - p0);
+            st.desc[j] = role_descriptor(tr.w, DIR);
+            smask[j] = a.lmask[t0 + j];
+            const int32_t se[3] = {tr.x, tr.y, tr.z};
+#pragma unroll
+            for (int e = 0; e < 3; e++) {
+                st.off[j][3 * e] = a.seg[2 * se[e]];
+                st.off[j][3 * e + 1] = a.seg[2 * se[e] + 1];
+                st.off[j][3 * e + 2] = a.seg[2 * se[e] + 2];
+            }
+        }
+        if (threadIdx.x == 0) {
+            st.nt = nt;
+            st.base[nt] = INT_MAX;
+        }
+        __syncthreads();
+        const int32_t count = (int32_t)min((int64_t)PB_TILE, P - p0);
+#pragma unroll 1
+        for (int it = 0; it < PB_ITEMS; it++) {
+            const int32_t local = it * PB_THREADS + (int32_t)threadIdx.x;
+            if ((local & ~31) >= count) break;  // warp-uniform
+            bool active = local < count;
+            // triangle of the slot: one lane bisects for the warp, lanes walk forward
+            const int lane = threadIdx.x & 31;
+            const int32_t first = __shfl_sync(0xffffffffu, local, 0);
+            int j0 = 0;
+            if (lane == 0) {
+                int lo = 0, hi = st.nt - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (st.base[mid] <= first) lo = mid;
+                    else hi = mid - 1;
+                }
+                j0 = lo;
+            }
+            int j = __shfl_sync(0xffffffffu, j0, 0);
+            if (!active) continue;
+            while (st.base[j + 1] <= local) j++;
+            int32_t o = local - st.base[j] - LIVE_IDLE;
+            if (o < 0) continue;  // idle slot
+            const int32_t* off = st.off[j];
+            const int m = smask[j];
+            int r = 0;
+            for (; r < 6; r++) {
+                if (!((m >> r) & 1)) continue;
+                const int32_t s1 = off[3 * (r >> 1) + (r & 1) + 1] - off[3 * (r >> 1) + (r & 1)];
+                if (o < s1) break;
+                o -= s1;
+            }
+            if (r == 6) continue;  // cannot happen: o < the kept roles' total
+            const int32_t pos = off[3 * (r >> 1) + (r & 1)] + o;
+            const int code = (int)((st.desc[j] >> (6 * r)) & 63);
+            const TS t = T[pos];
+            const TS t3 = probe_window<TS, DIR>(T, off, code & 7, code >> 3, t, delta);
+            if (t3 == TsNone<TS>::value) continue;
+            const TS gap = (TS)(t3 - t);
+            if (gap > delta) continue;
+            if (MODE == 0) {
+                atomicAdd(&a.cnt[pos], 1);
+            } else {
+                const int jb = lower_bound_ts<TS>(sD, 0, a.k, gap);
+                atomicAdd(&a.bins[(int64_t)jb * a.mk + pos], 1);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+void build_role_summary(folty_graph* g, cudaStream_t s) {
+    const int64_t ntri = g->ntri;
+    g->rsig = graph_alloc<int32_t>(g, 6 * ntri, s);
+    g->rmin = graph_alloc<uint8_t>(g, 18 * ntri, s);
+    if (ntri == 0) return;
+    if (g->ts32)
+        FOLTY_LAUNCH(k_role_summary<uint32_t>, grid_for(ntri, 256), 256, 0, s, g->tri, ntri, g->seg,
+                     (const uint32_t*)g->T, g->rsig, g->rmin);
+    else
+        FOLTY_LAUNCH(k_role_summary<int64_t>, grid_for(ntri, 256), 256, 0, s, g->tri, ntri, g->seg,
+                     (const int64_t*)g->T, g->rsig, g->rmin);
+}
+
+template <typename TS, int MODE>
+static void launch_live_t(const folty_graph* g, int dir, const LiveArgs& la, unsigned grid, TS delta,
+                          const TS* deltas, cudaStream_t s) {
+    const TS* T = (const TS*)g->T;
+    if (dir == FOLTY_DIR_OUT)
+        FOLTY_LAUNCH((k_probe_live<TS, FOLTY_DIR_OUT, MODE>), grid, PB_THREADS, 0, s, la, T, delta, deltas);
+    else if (dir == FOLTY_DIR_IN)
+        FOLTY_LAUNCH((k_probe_live<TS, FOLTY_DIR_IN, MODE>), grid, PB_THREADS, 0, s, la, T, delta, deltas);
+    else
+        FOLTY_LAUNCH((k_probe_live<TS, FOLTY_DIR_EITHER, MODE>), grid, PB_THREADS, 0, s, la, T, delta, deltas);
+}
+
+// Kept roles for delta (the largest window of the pass), then the probe kernel.
+// mode 0: counts into cnt; mode 1: bins (deltas = k sorted bounds in the store's type).
+void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t* cnt, int32_t* bins, int k,
+                       const void* deltas, ProbeTimer* timer, cudaStream_t s) {
+    const int64_t ntri = g->ntri;
+    if (ntri == 0 || g->info.probes == 0) return;
+    const int T = 256;
+    Scratch sc(g->alloc, s);
+    int32_t* flag = sc.get<int32_t>(2 * (ntri + 1));
+    int32_t* lpos = flag + ntri + 1;
+    int64_t* cost = sc.get<int64_t>(2 * (ntri + 1));
+    int64_t* lcost = cost + ntri + 1;
+    uint8_t* mask = sc.get<uint8_t>(2 * (ntri + 1));
+    uint8_t* lmask = mask + ntri + 1;
+    int32_t* L = sc.get<int32_t>(ntri + 1);
+    int64_t* loff = sc.get<int64_t>(ntri + 1);
+    const int64_t max_tiles = (g->info.probes + LIVE_IDLE * ntri + PB_TILE - 1) / PB_TILE;
+    int64_t* ltile = sc.get<int64_t>(max_tiles + 2);
+    if (timer) timer->start();
+    FOLTY_LAUNCH(k_live_tri, grid_for(ntri, T), T, 0, s, g->rsig, g->rmin + (int64_t)dir * 6 * ntri, ntri, delta,
+                 flag, cost, mask);
+    exclusive_scan(sc, flag, lpos, ntri);
+    exclusive_scan(sc, cost, lcost, ntri);
+    FOLTY_LAUNCH(k_live_compact, grid_for(ntri + 1, T), T, 0, s, flag, lpos, lcost, mask, ntri, L, loff, lmask);
+    FOLTY_LAUNCH(k_live_tiles, grid_for(max_tiles + 1, T), T, 0, s, loff, lpos + ntri, lcost + ntri, max_tiles, ltile);
+    LiveArgs la{g->tri, g->seg, L, loff, lmask, ltile, lcost + ntri, cnt, bins, g->m_kept, k};
+    int per_sm = 0;
+    if (g->ts32) FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<uint32_t, 0, 0>, PB_THREADS, 0));
+    else FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<int64_t, 0, 0>, PB_THREADS, 0));
+    const unsigned grid = (unsigned)(num_sms() * (per_sm > 0 ? per_sm : 1));
+    if (g->ts32) {
+        const uint32_t d32 = delta >= 0xfffffffell ? 0xfffffffeu : (uint32_t)delta;
+        if (mode == 0) launch_live_t<uint32_t, 0>(g, dir, la, grid, d32, nullptr, s);
+        else launch_live_t<uint32_t, 1>(g, dir, la, grid, d32, (const uint32_t*)deltas, s);
+    } else {
+        if (mode == 0) launch_live_t<int64_t, 0>(g, dir, la, grid, delta, nullptr, s);
+        else launch_live_t<int64_t, 1>(g, dir, la, grid, delta, (const int64_t*)deltas, s);
+    }
+    if (timer) timer->stop();
+}
+
+}  // namespace folty

@@ -403,9 +403,7 @@ void run_query(folty_graph* g, const folty_query_params& q, folty_result* out, c
     const int64_t mk = g->m_kept;
     int32_t* cnt = sc.get<int32_t>(mk);
     if (mk > 0) FOLTY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)mk, s));
-    timer.start();
-    launch_probe(g, q.delta, q.dir, cnt, s);
-    timer.stop();
+    launch_probe_live(g, q.delta, q.dir, 0, cnt, nullptr, 0, nullptr, &timer, s);
     finish_query(g, q, cnt, out, s);  // synchronises the stream
     timer.collect();
 }
