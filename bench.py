@@ -47,6 +47,37 @@ WORKLOAD = ("medium synthetic temporal graph: n=1,000,000, m=20,000,000, Chung-L
             "3 queries exists-exists-forall_{1/2} over N(u), delta in {600,3600,86400} s")
 
 
+STAGE_KERNELS = {
+    "probe": "window-probe stage: k_live_tri, scans, k_live_compact, k_live_tiles, k_probe_live",
+    "sort": "one radix pass: k_rs_hist, digit-offset scan, k_rs_scatter",
+    "peel": "k_peel (cooperative) + k_tail_* + k_peel_tail",
+    "threshold": "k_threshold",
+}
+
+
+def stage_traffic(stage, model_bytes):
+    """DRAM bytes per span of a stage from the committed ncu summary, when it was taken
+    on the current sources (profiles/traffic_medium_workload.md lists 'traffic <stage>
+    <bytes> <sha256 of the stage's sources>'); None otherwise."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "traffic_medium_workload.md")
+    if not os.path.exists(path):
+        return None
+    for m in re.finditer(r"^traffic (\w+) (\d+) ([0-9a-f]{64})$", open(path).read(), re.M):
+        if m.group(1) != stage:
+            continue
+        h = hashlib.sha256()
+        for f in STAGE_SOURCES.get(stage, ()):
+            h.update(open(os.path.join(ROOT, "paper_2507_17215_gb300", "csrc", f), "rb").read())
+        return int(m.group(2)) if h.hexdigest() == m.group(3) else None
+    return None
+
+
+STAGE_SOURCES = {"probe": ("live.cu", "probe.cuh"), "sort": ("prims.cu",),
+                 "peel": ("preprocess.cu",), "threshold": ("query.cu",)}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -395,22 +426,39 @@ def main():
         serving = measure_serving(F, args.serve_seconds)
 
     # ---- end-to-end through the C ABI from pinned host buffers
-    ke = args.e2e_steps or args.steps
+    ke = args.e2e_steps if args.e2e_steps is not None else args.steps
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    res_e = []
     for _ in range(ke):
         res_e = step(h_src, h_dst, h_t)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
-    e2e_value = replica_throughput(ke * len(queries) * g.m, world, e2e_s)
+    e2e_value = replica_throughput(ke * len(queries) * g.m, world, e2e_s) if ke > 0 else None
     h2d = g.m * (4 + 4 + 8)
     d2h = sum(16 * len(r["u"]) + 8 for r in res_e) + 8 * (4 + 3 * 2)
 
     peak, peak_kind = _peaks()
-    probe_launches = max(prof["probe_launches"], 1)
-    probe_s = prof["probe_ms"] / 1e3 / probe_launches
-    achieved = tm["probe_bytes"] / probe_s / 1e9 if probe_s > 0 else 0.0
+    stages = {}
+    for name, p in prof.items():
+        if p["launches"] == 0 or p["ms"] <= 0:
+            continue
+        gbs = p["bytes"] / (p["ms"] / 1e3) / 1e9
+        stages[name] = {"ms_per_step": p["ms"] / args.steps, "spans_per_step": p["launches"] / args.steps,
+                        "model_bytes_per_span": p["bytes"] / p["launches"], "achieved_gbs": gbs,
+                        "frac": gbs / peak}
+    dom = max(stages, key=lambda k: stages[k]["ms_per_step"]) if stages else None
+    roofline = None
+    if dom is not None:
+        d = prof[dom]
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": stage_traffic(dom, d["bytes"] / d["launches"]),
+                    "stage": dom, "kernel": STAGE_KERNELS[dom], "peak_kind": f"{peak_kind} hbm_gbs",
+                    "model_bytes_per_launch": d["bytes"] / d["launches"],
+                    "launch_ms": d["ms"] / d["launches"]}
+    probe_ms = prof["probe"]["ms"] / max(prof["probe"]["launches"], 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -422,13 +470,12 @@ def main():
                    "static_edges": info["static_edges"], "triangles": info["triangles"],
                    "probes_per_query": info["probes"], "degeneracy": info["degeneracy"],
                    "peel_rounds": info["peel_rounds"], "solution_pairs": [len(r["u"]) for r in res],
-                   "probe_ms_per_query": probe_s * 1e3},
+                   "probe_ms_per_query": probe_ms,
+                   "probe_model_bytes_all_roles": tm["probe_bytes"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_probe", "peak_kind": f"{peak_kind} hbm_gbs",
-                     "model_bytes_per_launch": tm["probe_bytes"]},
+        "roofline": roofline,
+        "stages": stages,
         "clocks": clk,
         "batched": batched,
         "serving": serving,

@@ -182,19 +182,30 @@ folty_status folty_graph_common_counts(folty_graph *g, int32_t *a, int32_t *b, i
 /* Number of kernels this library has launched in this process (all threads). */
 uint64_t folty_kernel_launches(void);
 
-/* Device time of the window-probe kernels (a query's dominant kernel), measured with
- * CUDA events recorded on the launching stream around every probe launch while
- * profiling is on. Totals are process-wide. */
+/* Device time by stage, measured with CUDA events recorded on the launching stream
+ * around every launch of the stage while profiling is on (collected after the calling
+ * API function's final synchronisation), with the stage's model bytes:
+ *   PROBE     window probes of a query or batch pass (liveness pass over the triangles'
+ *             role summaries + probes of the kept roles, per-role bytes as in the design
+ *             notes);
+ *   SORT      one radix pass: 8 B read for the histogram, 12 B read + 12 B written per key;
+ *   PEEL      the degeneracy peeling: 12 B per adjacency entry + 16 B per vertex;
+ *   THRESHOLD certificate test and per-pair reduction: 8 B per temporal edge + 20 B per
+ *             directed pair.
+ * Totals are process-wide; profile one thread at a time. */
+enum { FOLTY_STAGE_PROBE = 0, FOLTY_STAGE_SORT = 1, FOLTY_STAGE_PEEL = 2, FOLTY_STAGE_THRESHOLD = 3,
+       FOLTY_STAGE_COUNT = 4 };
 typedef struct {
-    int64_t probe_launches;
-    double probe_ms;
-} folty_profile;
+    int64_t launches; /* timed spans */
+    double ms;        /* total device time */
+    int64_t bytes;    /* total model bytes */
+} folty_stage_profile;
 
-/* Turns probe timing on (on != 0) or off and resets the totals. */
+/* Turns stage timing on (on != 0) or off and resets the totals. */
 void folty_profile_enable(int32_t on);
 
-/* Copies the totals. Errors: FOLTY_EINVAL (NULL). */
-folty_status folty_profile_read(folty_profile *out);
+/* Copies the totals of one stage. Errors: FOLTY_EINVAL (NULL, unknown stage). */
+folty_status folty_profile_read(int32_t stage, folty_stage_profile *out);
 
 /* ------------------------------------------------------------------ serving
  * A server keeps preprocessed graphs resident and answers queries as they arrive

@@ -89,8 +89,11 @@ class folty_server_stats(Structure):
                 ("max_batches_in_flight", c_int64)]
 
 
-class folty_profile(Structure):
-    _fields_ = [("probe_launches", c_int64), ("probe_ms", ctypes.c_double)]
+class folty_stage_profile(Structure):
+    _fields_ = [("launches", c_int64), ("ms", ctypes.c_double), ("bytes", c_int64)]
+
+
+STAGES = {"probe": 0, "sort": 1, "peel": 2, "threshold": 3}
 
 
 class folty_traffic_model(Structure):
@@ -128,7 +131,7 @@ def _load_library():
     lib.folty_profile_enable.restype = None
     lib.folty_profile_enable.argtypes = [c_int32]
     lib.folty_profile_read.restype = c_int32
-    lib.folty_profile_read.argtypes = [POINTER(folty_profile)]
+    lib.folty_profile_read.argtypes = [c_int32, POINTER(folty_stage_profile)]
     lib.folty_graph_common_counts.restype = c_int32
     lib.folty_graph_common_counts.argtypes = [G, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.folty_server_create.restype = c_int32
@@ -334,10 +337,14 @@ def folty_profile_enable(on: bool = True) -> None:
     lib.folty_profile_enable(1 if on else 0)
 
 
-def folty_profile_read() -> Dict[str, float]:
-    p = folty_profile()
-    _check(lib.folty_profile_read(ctypes.byref(p)))
-    return {"probe_launches": int(p.probe_launches), "probe_ms": float(p.probe_ms)}
+def folty_profile_read() -> Dict[str, Dict[str, float]]:
+    """Per stage: timed spans, total device ms, total model bytes."""
+    out = {}
+    for name, idx in STAGES.items():
+        p = folty_stage_profile()
+        _check(lib.folty_profile_read(idx, ctypes.byref(p)))
+        out[name] = {"launches": int(p.launches), "ms": float(p.ms), "bytes": int(p.bytes)}
+    return out
 
 
 def folty_server_create(graphs: Sequence[int], memory_budget_bytes: int = 0, max_batch: int = 0) -> int:

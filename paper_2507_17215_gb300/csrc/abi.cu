@@ -14,43 +14,70 @@ static thread_local std::string t_last_error;
 
 static std::atomic<int> g_profile_on{0};
 static std::mutex g_profile_mu;
-static folty_profile g_profile{0, 0.0};
+static folty_stage_profile g_stages[ST_COUNT];
 
-ProbeTimer::ProbeTimer(cudaStream_t s) : s_(s) {
-    on_ = g_profile_on.load() != 0;
-    if (on_) {
-        FOLTY_CUDA(cudaEventCreate(&a_));
-        FOLTY_CUDA(cudaEventCreate(&b_));
+struct StageRecord {
+    int stage;
+    cudaEvent_t a, b;
+    int64_t bytes;
+    const unsigned long long* dev_bytes;
+};
+static thread_local std::vector<StageRecord>* t_records = nullptr;
+
+bool profiling_on() { return g_profile_on.load() != 0; }
+
+StageSpan::StageSpan(int stage, cudaStream_t s, int64_t bytes, const unsigned long long* dev_bytes) : s_(s) {
+    if (!t_records) return;
+    StageRecord r{stage, nullptr, nullptr, bytes, dev_bytes};
+    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    cudaEventRecord(r.a, s);
+    t_records->push_back(r);
+    idx_ = (int)t_records->size() - 1;
+}
+
+StageSpan::~StageSpan() {
+    if (idx_ >= 0 && t_records && idx_ < (int)t_records->size()) cudaEventRecord((*t_records)[idx_].b, s_);
+}
+
+ProfileScope::ProfileScope() {
+    if (profiling_on() && !t_records) {
+        t_records = new std::vector<StageRecord>();
+        active_ = true;
     }
 }
 
-ProbeTimer::~ProbeTimer() {
-    if (a_) cudaEventDestroy(a_);
-    if (b_) cudaEventDestroy(b_);
-}
-
-void ProbeTimer::start() {
-    if (on_) {
-        FOLTY_CUDA(cudaEventRecord(a_, s_));
-        started_ = true;
-    }
-}
-
-void ProbeTimer::stop() {
-    if (on_ && started_) {
-        FOLTY_CUDA(cudaEventRecord(b_, s_));
-        stopped_ = true;
-    }
-}
-
-void ProbeTimer::collect() {
-    if (!(on_ && started_ && stopped_)) return;
-    float ms = 0.f;
-    FOLTY_CUDA(cudaEventElapsedTime(&ms, a_, b_));
+void ProfileScope::commit() {
+    if (!active_) return;
     std::lock_guard<std::mutex> lock(g_profile_mu);
-    g_profile.probe_launches += 1;
-    g_profile.probe_ms += ms;
-    started_ = stopped_ = false;
+    for (auto& r : *t_records) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        int64_t bytes = r.bytes;
+        if (r.dev_bytes) {
+            unsigned long long v = 0;
+            if (cudaMemcpy(&v, r.dev_bytes, sizeof(v), cudaMemcpyDeviceToHost) == cudaSuccess) bytes += (int64_t)v;
+            else cudaGetLastError();
+        }
+        g_stages[r.stage].launches += 1;
+        g_stages[r.stage].ms += ms;
+        g_stages[r.stage].bytes += bytes;
+    }
+}
+
+ProfileScope::~ProfileScope() {
+    if (!active_) return;
+    for (auto& r : *t_records) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    delete t_records;
+    t_records = nullptr;
 }
 
 void set_last_error(const std::string& msg) { t_last_error = msg; }
@@ -324,7 +351,9 @@ folty_status folty_preprocess(folty_graph* g, void* stream) {
     return guarded([&] {
         checked_graph(g);
         if (g->state != 0) fail(FOLTY_ESTATE, "graph already preprocessed");
-        preprocess_graph(g, (cudaStream_t)stream);
+        ProfileScope prof;
+        preprocess_graph(g, (cudaStream_t)stream);  // ends with a stream synchronisation
+        prof.commit();
     });
 }
 
@@ -334,7 +363,9 @@ folty_status folty_query(folty_graph* g, const folty_query_params* q, folty_resu
         if (!q || !out) fail(FOLTY_EINVAL, "query or result is NULL");
         if (g->state != 1) fail(FOLTY_ESTATE, "graph not preprocessed");
         validate_query(*q);
-        run_query(g, *q, out, (cudaStream_t)stream);
+        ProfileScope prof;
+        run_query(g, *q, out, (cudaStream_t)stream);  // ends with a stream synchronisation
+        prof.commit();
     });
 }
 
@@ -347,7 +378,9 @@ folty_status folty_query_batch(folty_graph* g, const folty_query_params* qs, int
         for (int i = 0; i < nq; i++) validate_query(qs[i]);
         for (int i = 0; i < nq; i++) std::memset(&outs[i], 0, sizeof(folty_result));
         try {
-            run_query_batch(g, qs, nq, outs, (cudaStream_t)stream);
+            ProfileScope prof;
+            run_query_batch(g, qs, nq, outs, (cudaStream_t)stream);  // ends synchronised
+            prof.commit();
         } catch (...) {
             for (int i = 0; i < nq; i++)
                 if (outs[i].tag == RESULT_TAG) free_result(&outs[i]);
@@ -417,15 +450,16 @@ folty_status folty_edge_counts_noalloc(folty_graph* g, int64_t delta, int32_t di
 
 void folty_profile_enable(int32_t on) {
     std::lock_guard<std::mutex> lock(g_profile_mu);
-    g_profile = folty_profile{0, 0.0};
+    for (auto& st : g_stages) st = folty_stage_profile{0, 0.0, 0};
     g_profile_on.store(on ? 1 : 0);
 }
 
-folty_status folty_profile_read(folty_profile* out) {
+folty_status folty_profile_read(int32_t stage, folty_stage_profile* out) {
     return guarded([&] {
         if (!out) fail(FOLTY_EINVAL, "out is NULL");
+        if (stage < 0 || stage >= ST_COUNT) fail(FOLTY_EINVAL, "unknown stage");
         std::lock_guard<std::mutex> lock(g_profile_mu);
-        *out = g_profile;
+        *out = g_stages[stage];
     });
 }
 

@@ -109,11 +109,9 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
                 FOLTY_CUDA(cudaMemcpyAsync(dd, hd.data(), sizeof(int64_t) * (size_t)k, cudaMemcpyHostToDevice, s));
             if (mk > 0) {
                 FOLTY_CUDA(cudaMemsetAsync(bins, 0, sizeof(int32_t) * (size_t)(mk * k), s));
-                ProbeTimer timer(s);
-                if (P > 0) launch_probe_live(g, hd[k - 1], dir, 1, nullptr, bins, k, dd, &timer, s);
+                if (P > 0) launch_probe_live(g, hd[k - 1], dir, 1, nullptr, bins, k, dd, s);
                 if (k > 1) FOLTY_LAUNCH(k_bins_prefix, grid_for(mk, 256), 256, 0, s, bins, k, mk);
                 FOLTY_CUDA(cudaStreamSynchronize(s));  // the host bounds must outlive the copy
-                timer.collect();
             }
             std::vector<const folty_query_params*> fq;
             std::vector<const int32_t*> fc;

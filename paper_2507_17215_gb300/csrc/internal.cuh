@@ -99,6 +99,7 @@ class Scratch {
 
 // ------------------------------------------------------------------ the graph
 
+constexpr int PROF_SLOTS = 64;       // probe-stage byte counters per graph
 constexpr int HOST_STAGE = 512;      // pinned int64 slots per graph
 constexpr int READBACK_MAX = 384;    // slots [0, READBACK_MAX) serve read_back
 constexpr uint64_t GRAPH_TAG = 0x464f4c5459475248ull;   // "FOLTYGRH"
@@ -138,6 +139,8 @@ struct folty_graph {
     int4* tri;        // [ntri] {s_uv, s_uw, s_vw, id-order bits}, u < v < w in degeneracy rank
     int64_t* tri_off; // [ntri + 1] prefix of per-triangle probe counts
     int64_t* tile_tri;  // [probe tiles + 1] triangle holding each tile's first probe
+    unsigned long long* prof_bytes;  // [PROF_SLOTS] device counters of probe-stage model bytes
+    int prof_next;                   // next slot
     int32_t* rsig;      // [6][ntri] |L1| of every role (role r = 2 * edge + direction)
     uint8_t* rmin;      // [3][6][ntri] bucket of the smallest window a role can hit with
     int64_t n_tiles;
@@ -182,9 +185,10 @@ void exclusive_scan(Scratch& sc, const uint32_t* in, uint32_t* out, int64_t n);
 
 // Stable LSD radix sort of (key, value) pairs on key bits [0, bits). Buffers ping-pong
 // between (keys, vals) and (keys_alt, vals_alt); returns true when the result ended
-// up in the *_alt buffers.
+// up in the *_alt buffers. A look-back wait that runs out sets the device int *err to 1
+// (the caller zeroes it, and must read it before using the output).
 bool radix_sort_pairs(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
-                      uint32_t* vals_alt, int64_t n, int bits);
+                      uint32_t* vals_alt, int64_t n, int bits, int* err);
 
 int bit_length(uint64_t x);
 
@@ -202,20 +206,36 @@ int64_t batch_footprint(const folty_graph* g, const folty_query_params* qs, int 
 void traffic_model(folty_graph* g, int dir, folty_traffic_model* out, cudaStream_t s);
 
 void validate_query(const folty_query_params& q);
-// Event pair around probe launches when profiling is on (abi.cu holds the totals).
-class ProbeTimer {
+// Device-time profiling by stage (folty_profile_enable/read). While profiling is on,
+// a ProfileScope at an API entry collects the StageSpans opened during the call: each
+// span records CUDA events on the launching stream around a stage's launches, with the
+// stage's model bytes (host-known, plus an optional device-side counter). The scope's
+// commit(), called after the call's final stream synchronisation, adds the elapsed
+// times to process-wide totals.
+enum { ST_PROBE = 0, ST_SORT = 1, ST_PEEL = 2, ST_THRESHOLD = 3, ST_COUNT = 4 };
+
+class StageSpan {
   public:
-    explicit ProbeTimer(cudaStream_t s);
-    ~ProbeTimer();
-    void start();
-    void stop();
-    void collect();  // call after the stream has been synchronised
+    StageSpan(int stage, cudaStream_t s, int64_t bytes, const unsigned long long* dev_bytes = nullptr);
+    ~StageSpan();
+    StageSpan(const StageSpan&) = delete;
+    StageSpan& operator=(const StageSpan&) = delete;
 
   private:
+    int idx_ = -1;
     cudaStream_t s_;
-    cudaEvent_t a_ = nullptr, b_ = nullptr;
-    bool on_ = false, started_ = false, stopped_ = false;
 };
+
+class ProfileScope {
+  public:
+    ProfileScope();
+    ~ProfileScope();
+    void commit();  // after the call's final synchronisation
+
+  private:
+    bool active_ = false;
+};
+bool profiling_on();
 
 // Window-probe pass of one query into counters cnt[m_kept] (sorted order, zeroed).
 void launch_probe(folty_graph* g, int64_t delta, int dir, int32_t* cnt, cudaStream_t s);
@@ -223,7 +243,7 @@ void launch_probe(folty_graph* g, int64_t delta, int dir, int32_t* cnt, cudaStre
 // cnt; mode 1 bins gaps <= delta into bins[k][m_kept] against the k sorted bounds
 // `deltas` (in the timestamp store's type).
 void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t* cnt, int32_t* bins, int k,
-                       const void* deltas, ProbeTimer* timer, cudaStream_t s);
+                       const void* deltas, cudaStream_t s);
 void build_role_summary(folty_graph* g, cudaStream_t s);
 // The same pass with the counters in a file-scope device array (noalloc.cu).
 void edge_counts_noalloc(folty_graph* g, int64_t delta, int dir, int32_t* edge_count, cudaStream_t s);

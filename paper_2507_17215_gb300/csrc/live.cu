@@ -145,6 +145,27 @@ __global__ void k_live_tiles(const int64_t* __restrict__ loff, const int32_t* __
     }
 }
 
+// Model bytes of a staged triangle's kept roles (its first slot lies in this tile):
+// staging 61 B, and per role w sigma1 + w min(sigma2, sigma1 ceil(log2(sigma2 + 1))) + the
+// same for L3 + 8 sigma1, w = bytes per timestamp.
+template <typename TS, int DIR>
+__device__ __forceinline__ unsigned long long kept_role_bytes(const int32_t* off, int m, uint64_t desc) {
+    const int64_t w = sizeof(TS);
+    unsigned long long b = 61;
+    for (int r = 0; r < 6; r++) {
+        if (!((m >> r) & 1)) continue;
+        const int64_t s1 = off[3 * (r >> 1) + (r & 1) + 1] - off[3 * (r >> 1) + (r & 1)];
+        const int code = (int)((desc >> (6 * r)) & 63);
+        const int c2 = code & 7, c3 = code >> 3;
+        const int o2 = 3 * (c2 >> 1) + (c2 & 1), o3 = 3 * (c3 >> 1) + (c3 & 1);
+        const int64_t s2 = DIR == FOLTY_DIR_EITHER ? off[o2 + 2] - off[o2] : off[o2 + 1] - off[o2];
+        const int64_t s3 = DIR == FOLTY_DIR_EITHER ? off[o3 + 2] - off[o3] : off[o3 + 1] - off[o3];
+        const int64_t l2 = 64 - __clzll((unsigned long long)s2), l3 = 64 - __clzll((unsigned long long)s3);
+        b += (unsigned long long)(w * s1 + w * min(s2, s1 * l2) + w * min(s3, s1 * l3) + 8 * s1);
+    }
+    return b;
+}
+
 struct LiveArgs {
     const int4* tri;
     const int32_t* seg;
@@ -157,6 +178,7 @@ struct LiveArgs {
     int32_t* bins;     // MODE 1
     int64_t mk;
     int k;             // MODE 1: number of bins
+    unsigned long long* prof;  // model bytes of the kept roles (may be null)
 };
 
 // MODE 0: cnt[pos] += hit at window delta. MODE 1: bin the gap t3 - t (<= delta, the
@@ -176,6 +198,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS*
         const int64_t t0 = a.ltile[b];
         const int nt = (int)(a.ltile[b + 1] - t0 + 1);
         const int64_t p0 = b * (int64_t)PB_TILE;
+        unsigned long long pbytes = 0;
         for (int j = threadIdx.x; j < nt; j += blockDim.x) {
             const int4 tr = a.tri[a.L[t0 + j]];
             st.base[j] = (int32_t)(a.loff[t0 + j] - p0);
@@ -188,6 +211,12 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS*
                 st.off[j][3 * e + 1] = a.seg[2 * se[e] + 1];
                 st.off[j][3 * e + 2] = a.seg[2 * se[e] + 2];
             }
+            if (a.prof && st.base[j] >= 0) pbytes += kept_role_bytes<TS, DIR>(st.off[j], smask[j], st.desc[j]);
+        }
+        if (a.prof) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pbytes += __shfl_xor_sync(0xffffffffu, pbytes, o);
+            if ((threadIdx.x & 31) == 0 && pbytes) atomicAdd(a.prof, pbytes);
         }
         if (threadIdx.x == 0) {
             st.nt = nt;
@@ -275,7 +304,7 @@ static void launch_live_t(const folty_graph* g, int dir, const LiveArgs& la, uns
 // Kept roles for delta (the largest window of the pass), then the probe kernel.
 // mode 0: counts into cnt; mode 1: bins (deltas = k sorted bounds in the store's type).
 void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t* cnt, int32_t* bins, int k,
-                       const void* deltas, ProbeTimer* timer, cudaStream_t s) {
+                       const void* deltas, cudaStream_t s) {
     const int64_t ntri = g->ntri;
     if (ntri == 0 || g->info.probes == 0) return;
     const int T = 256;
@@ -290,14 +319,20 @@ void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t
     int64_t* loff = sc.get<int64_t>(ntri + 1);
     const int64_t max_tiles = (g->info.probes + LIVE_IDLE * ntri + PB_TILE - 1) / PB_TILE;
     int64_t* ltile = sc.get<int64_t>(max_tiles + 2);
-    if (timer) timer->start();
+    // liveness pass reads 30 B and writes 13 B per triangle; scans and compaction ~53 B
+    unsigned long long* prof = nullptr;
+    if (profiling_on()) {
+        prof = g->prof_bytes + (g->prof_next++ % PROF_SLOTS);
+        FOLTY_CUDA(cudaMemsetAsync(prof, 0, sizeof(unsigned long long), s));
+    }
+    StageSpan span(ST_PROBE, s, 96 * ntri, prof);
     FOLTY_LAUNCH(k_live_tri, grid_for(ntri, T), T, 0, s, g->rsig, g->rmin + (int64_t)dir * 6 * ntri, ntri, delta,
                  flag, cost, mask);
     exclusive_scan(sc, flag, lpos, ntri);
     exclusive_scan(sc, cost, lcost, ntri);
     FOLTY_LAUNCH(k_live_compact, grid_for(ntri + 1, T), T, 0, s, flag, lpos, lcost, mask, ntri, L, loff, lmask);
     FOLTY_LAUNCH(k_live_tiles, grid_for(max_tiles + 1, T), T, 0, s, loff, lpos + ntri, lcost + ntri, max_tiles, ltile);
-    LiveArgs la{g->tri, g->seg, L, loff, lmask, ltile, lcost + ntri, cnt, bins, g->m_kept, k};
+    LiveArgs la{g->tri, g->seg, L, loff, lmask, ltile, lcost + ntri, cnt, bins, g->m_kept, k, prof};
     int per_sm = 0;
     if (g->ts32) FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<uint32_t, 0, 0>, PB_THREADS, 0));
     else FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<int64_t, 0, 0>, PB_THREADS, 0));
@@ -310,7 +345,6 @@ void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t
         if (mode == 0) launch_live_t<int64_t, 0>(g, dir, la, grid, delta, nullptr, s);
         else launch_live_t<int64_t, 1>(g, dir, la, grid, delta, (const int64_t*)deltas, s);
     }
-    if (timer) timer->stop();
 }
 
 }  // namespace folty

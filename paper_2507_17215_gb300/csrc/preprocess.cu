@@ -824,6 +824,11 @@ __global__ void k_tri_write(const int32_t* __restrict__ outptr, const int32_t* _
 
 // ================================================================== driver
 
+// The sorted values index other arrays: a sort whose look-back ran out must stop here.
+static void sort_check(folty_graph* g, const int* err, cudaStream_t s) {
+    if (read_i32(g, err, s)) fail(FOLTY_ETIMEOUT, "radix sort: a look-back wait ran out");
+}
+
 void preprocess_graph(folty_graph* g, cudaStream_t s) {
     const int T = 256;
     const int64_t m = g->m;
@@ -839,6 +844,8 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     uint64_t* key_alt = sc.get<uint64_t>(m);
     uint32_t* val = sc.get<uint32_t>(m);
     uint32_t* val_alt = sc.get<uint32_t>(m);
+    int* sort_err = sc.get<int>(1);
+    FOLTY_CUDA(cudaMemsetAsync(sort_err, 0, sizeof(int), s));
     FOLTY_LAUNCH(k_build_keys, grid_for(m, T), T, 0, s, g->in_src, g->in_dst, m, nb, loop_key, key, val);
     uint64_t* skey = key;
     uint32_t* sval = val;
@@ -848,16 +855,20 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         uint64_t* tk = sc.get<uint64_t>(m);
         uint64_t* tk_alt = sc.get<uint64_t>(m);
         FOLTY_LAUNCH(k_time_keys, grid_for(m, T), T, 0, s, g->in_t, m, tmin, tk, val);
-        bool alt = radix_sort_pairs(sc, tk, tk_alt, val, val_alt, m, bit_length((uint64_t)(tmax - tmin)));
+        bool alt = radix_sort_pairs(sc, tk, tk_alt, val, val_alt, m, bit_length((uint64_t)(tmax - tmin)),
+                                    sort_err);
+        sort_check(g, sort_err, s);
         uint32_t* order = alt ? val_alt : val;
         uint32_t* other = alt ? val : val_alt;
         FOLTY_LAUNCH(k_gather_keys, grid_for(m, T), T, 0, s, key, order, m, key_alt);
         // keys now in key_alt, values in order; sort (key_alt, order)
-        bool alt2 = radix_sort_pairs(sc, key_alt, key, order, other, m, key_bits);
+        bool alt2 = radix_sort_pairs(sc, key_alt, key, order, other, m, key_bits, sort_err);
+        sort_check(g, sort_err, s);
         skey = alt2 ? key : key_alt;
         sval = alt2 ? other : order;
     } else {
-        bool alt = radix_sort_pairs(sc, key, key_alt, val, val_alt, m, key_bits);
+        bool alt = radix_sort_pairs(sc, key, key_alt, val, val_alt, m, key_bits, sort_err);
+        sort_check(g, sort_err, s);
         skey = alt ? key_alt : key;
         sval = alt ? val_alt : val;
     }
@@ -906,8 +917,9 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         uint32_t* bv = sc.get<uint32_t>(S);
         uint32_t* bv_alt = sc.get<uint32_t>(S);
         FOLTY_LAUNCH(k_edge_keys_b, grid_for(S, T), T, 0, s, g->eb, S, bk, bv);
-        bool alt = radix_sort_pairs(sc, bk, bk_alt, bv, bv_alt, S, nb);
+        bool alt = radix_sort_pairs(sc, bk, bk_alt, bv, bv_alt, S, nb, sort_err);
         by_b = alt ? bv_alt : bv;
+        sort_check(g, sort_err, s);
     }
     g->by_b = graph_alloc<int32_t>(g, S, s);
     if (S > 0) FOLTY_CUDA(cudaMemcpyAsync(g->by_b, by_b, sizeof(int32_t) * (size_t)S, cudaMemcpyDeviceToDevice, s));
@@ -971,6 +983,7 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         if (per_sm > 1) per_sm = 1;
         dim3 grid(num_sms() * per_sm), block(PEEL_THREADS);
         void* args[] = {&pa};
+        StageSpan span(ST_PEEL, s, 12 * 2 * (int64_t)S + 16 * (int64_t)n);
         if (n > 0) {
             FOLTY_CUDA(cudaLaunchCooperativeKernel((const void*)k_peel, grid, block, args, 0, s));
             after_launch("k_peel");
@@ -1072,6 +1085,7 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         FOLTY_LAUNCH(k_tile_starts, grid_for(g->n_tiles + 1, T), T, 0, s, g->tri_off, ntri, g->info.probes,
                      g->n_tiles, PB_TILE, g->tile_tri);
     build_role_summary(g, s);
+    g->prof_bytes = graph_alloc<unsigned long long>(g, PROF_SLOTS, s);
     g->info.static_edges = S;
     g->state = 1;
     FOLTY_CUDA(cudaStreamSynchronize(s));

@@ -312,6 +312,7 @@ static void pairs_device(folty_graph* g, const folty_query_params& q, const int3
         ThresholdArgs a{cnt, g->sd, mk, g->ea, g->eb, g->deg, g->common, (int)q.quant, (int)q.universe,
                         (int64_t)q.rho_num, (int64_t)q.rho_den, p.seg_max, p.seg_ncert, p.n_cert,
                         g->perm, p.cert_flag};
+        StageSpan span(ST_THRESHOLD, s, 8 * mk + 20 * n2);
         FOLTY_LAUNCH(k_threshold, grid_for(mk, T), T, 0, s, a);
     }
     if (p.cert_flag) exclusive_scan(sc, p.cert_flag, p.cert_pos, g->m);
@@ -399,13 +400,11 @@ void finish_query(folty_graph* g, const folty_query_params& q, const int32_t* cn
 
 void run_query(folty_graph* g, const folty_query_params& q, folty_result* out, cudaStream_t s) {
     Scratch sc(g->alloc, s);
-    ProbeTimer timer(s);
     const int64_t mk = g->m_kept;
     int32_t* cnt = sc.get<int32_t>(mk);
     if (mk > 0) FOLTY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)mk, s));
-    launch_probe_live(g, q.delta, q.dir, 0, cnt, nullptr, 0, nullptr, &timer, s);
+    launch_probe_live(g, q.delta, q.dir, 0, cnt, nullptr, 0, nullptr, s);
     finish_query(g, q, cnt, out, s);  // synchronises the stream
-    timer.collect();
 }
 
 // ================================================================== traffic model
