@@ -49,7 +49,7 @@ WORKLOAD = ("medium synthetic temporal graph: n=1,000,000, m=20,000,000, Chung-L
 
 STAGE_KERNELS = {
     "probe": "window-probe stage: k_live_tri, scans, k_live_compact, k_live_tiles, k_probe_live",
-    "sort": "one radix pass: k_rs_hist, digit-offset scan, k_rs_scatter",
+    "sort": "radix sort spans: k_rs_hist_all + k_rs_bases (all digit histograms), or one k_rs_onesweep digit pass",
     "peel": "k_peel (cooperative) + k_tail_* + k_peel_tail",
     "threshold": "k_threshold",
 }

@@ -179,6 +179,12 @@ folty_status folty_graph_traffic_model(folty_graph *g, int32_t dir,
 folty_status folty_graph_common_counts(folty_graph *g, int32_t *a, int32_t *b, int32_t *c,
                                        void *stream);
 
+/* Core numbers of the static graph G_S (the k-core decomposition the degeneracy order of
+ * Section 3 comes from): core[u] = the largest k such that u lies in a subgraph of
+ * minimum degree k. core is a caller-owned host array of n entries. Synchronises the
+ * stream. Errors: FOLTY_EINVAL (NULL), FOLTY_ESTATE (not preprocessed). */
+folty_status folty_graph_core_numbers(folty_graph *g, int32_t *core, void *stream);
+
 /* Number of kernels this library has launched in this process (all threads). */
 uint64_t folty_kernel_launches(void);
 

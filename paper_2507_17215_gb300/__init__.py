@@ -31,7 +31,8 @@ U_HEAD, U_TAIL, U_COMMON = 0, 1, 2
 EXPORTED = ["folty_load_temporal_graph", "folty_preprocess", "folty_query", "folty_query_batch",
             "folty_free", "folty_last_error", "folty_graph_get_info", "folty_graph_traffic_model",
             "folty_kernel_launches", "folty_profile_enable", "folty_profile_read",
-            "folty_edge_counts_noalloc", "folty_graph_common_counts", "folty_server_create", "folty_server_submit",
+            "folty_edge_counts_noalloc", "folty_graph_common_counts", "folty_graph_core_numbers",
+            "folty_server_create", "folty_server_submit",
             "folty_server_wait", "folty_server_get_stats", "folty_server_destroy"]
 
 
@@ -134,6 +135,8 @@ def _load_library():
     lib.folty_profile_read.argtypes = [c_int32, POINTER(folty_stage_profile)]
     lib.folty_graph_common_counts.restype = c_int32
     lib.folty_graph_common_counts.argtypes = [G, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.folty_graph_core_numbers.restype = c_int32
+    lib.folty_graph_core_numbers.argtypes = [G, c_void_p, c_void_p]
     lib.folty_server_create.restype = c_int32
     lib.folty_server_create.argtypes = [POINTER(c_void_p), c_int32, POINTER(folty_server_config),
                                         POINTER(c_void_p)]
@@ -319,6 +322,14 @@ def folty_graph_common_counts(g: int, stream: Optional[int] = None):
     return a[:S], b[:S], c[:S]
 
 
+def folty_graph_core_numbers(g: int, stream: Optional[int] = None) -> np.ndarray:
+    """Core number of every vertex of the static graph (int32[n])."""
+    n = folty_graph_get_info(g)["n"]
+    core = np.zeros(max(n, 1), np.int32)
+    _check(lib.folty_graph_core_numbers(g, core.ctypes.data, current_stream() if stream is None else stream))
+    return core[:n]
+
+
 def folty_kernel_launches() -> int:
     return int(lib.folty_kernel_launches())
 
@@ -407,6 +418,9 @@ class TemporalGraph:
 
     def traffic_model(self, dir: int = DIR_OUT, stream: Optional[int] = None):
         return folty_graph_traffic_model(self.handle, dir, stream)
+
+    def core_numbers(self, stream: Optional[int] = None):
+        return folty_graph_core_numbers(self.handle, stream)
 
     def close(self):
         if getattr(self, "handle", None):

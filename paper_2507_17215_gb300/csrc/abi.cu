@@ -127,7 +127,14 @@ void read_back(folty_graph* g, const void* const* dev_ptrs, const int* sizes, in
     if (count > READBACK_MAX) fail(FOLTY_EINVAL, "read_back: too many values");
     for (int i = 0; i < count; i++)
         FOLTY_CUDA(cudaMemcpyAsync(g->host_stage + i, dev_ptrs[i], (size_t)sizes[i], cudaMemcpyDeviceToHost, s));
+    int32_t* herr = (int32_t*)(g->host_stage + ERR_SLOT);
+    *herr = 0;
+    if (g->dev_err) FOLTY_CUDA(cudaMemcpyAsync(herr, g->dev_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     FOLTY_CUDA(cudaStreamSynchronize(s));
+    if (*herr) {
+        FOLTY_CUDA(cudaMemsetAsync(g->dev_err, 0, sizeof(int32_t), s));
+        fail(FOLTY_ETIMEOUT, "a bounded wait in a device look-back ran out; the results of this call are void");
+    }
     for (int i = 0; i < count; i++) {
         if (sizes[i] == 8) out[i] = g->host_stage[i];
         else {
@@ -261,12 +268,14 @@ static void load_graph(folty_graph* g, const int32_t* src, const int32_t* dst, c
     g->in_src = graph_alloc<int32_t>(g, m, s);
     g->in_dst = graph_alloc<int32_t>(g, m, s);
     g->in_t = graph_alloc<int64_t>(g, m, s);
+    g->dev_err = graph_alloc<int>(g, 1, s);
+    FOLTY_CUDA(cudaMemsetAsync(g->dev_err, 0, sizeof(int), s));
     if (m > 0) {
         FOLTY_CUDA(cudaMemcpyAsync(g->in_src, src, sizeof(int32_t) * (size_t)m, cudaMemcpyDefault, s));
         FOLTY_CUDA(cudaMemcpyAsync(g->in_dst, dst, sizeof(int32_t) * (size_t)m, cudaMemcpyDefault, s));
         FOLTY_CUDA(cudaMemcpyAsync(g->in_t, t, sizeof(int64_t) * (size_t)m, cudaMemcpyDefault, s));
     }
-    Scratch sc(g->alloc, s);
+    Scratch sc(g->alloc, s, g->dev_err);
     unsigned long long* stat = sc.get<unsigned long long>(5);
     unsigned long long init[5] = {~0ull, ~0ull, 0ull, 0ull, 0ull};
     std::memcpy(g->host_stage + READBACK_MAX, init, sizeof(init));
@@ -430,6 +439,18 @@ folty_status folty_graph_common_counts(folty_graph* g, int32_t* a, int32_t* b, i
             FOLTY_CUDA(cudaMemcpyAsync(b, g->eb, bytes, cudaMemcpyDeviceToHost, s));
             FOLTY_CUDA(cudaMemcpyAsync(c, g->common, bytes, cudaMemcpyDeviceToHost, s));
         }
+        FOLTY_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+folty_status folty_graph_core_numbers(folty_graph* g, int32_t* core, void* stream) {
+    return guarded([&] {
+        checked_graph(g);
+        if (g->state != 1) fail(FOLTY_ESTATE, "graph not preprocessed");
+        if (g->n > 0 && !core) fail(FOLTY_EINVAL, "core is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        if (g->n > 0)
+            FOLTY_CUDA(cudaMemcpyAsync(core, g->core, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, s));
         FOLTY_CUDA(cudaStreamSynchronize(s));
     });
 }

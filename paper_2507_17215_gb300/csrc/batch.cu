@@ -95,7 +95,7 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
         chunk = std::max<int64_t>(1, std::min<int64_t>({chunk, (int64_t)BATCH_MAX_BINS, (int64_t)D.size()}));
         for (size_t c0 = 0; c0 < D.size(); c0 += (size_t)chunk) {
             const int k = (int)std::min<int64_t>(chunk, (int64_t)D.size() - (int64_t)c0);
-            Scratch sc(g->alloc, s);
+            Scratch sc(g->alloc, s, g->dev_err);
             int32_t* bins = sc.get<int32_t>(mk * k);
             int64_t* dd = sc.get<int64_t>(k);
             std::vector<int64_t> hd(D.begin() + (long)c0, D.begin() + (long)c0 + k);

@@ -73,7 +73,8 @@ struct Allocator {
 // scope, also on error.
 class Scratch {
   public:
-    Scratch(const Allocator& a, cudaStream_t s) : a_(a), s_(s) {}
+    // err: the device error word of the graph the call works on (see read_back)
+    Scratch(const Allocator& a, cudaStream_t s, int* err) : a_(a), s_(s), err_(err) {}
     ~Scratch() {
         for (void* p : ptrs_) a_.put(p, s_);
     }
@@ -90,10 +91,12 @@ class Scratch {
     }
     cudaStream_t stream() const { return s_; }
     const Allocator& allocator() const { return a_; }
+    int* err() const { return err_; }
 
   private:
     const Allocator& a_;
     cudaStream_t s_;
+    int* err_;
     std::vector<void*> ptrs_;
 };
 
@@ -102,6 +105,7 @@ class Scratch {
 constexpr int PROF_SLOTS = 64;       // probe-stage byte counters per graph
 constexpr int HOST_STAGE = 512;      // pinned int64 slots per graph
 constexpr int READBACK_MAX = 384;    // slots [0, READBACK_MAX) serve read_back
+constexpr int ERR_SLOT = READBACK_MAX + 8;  // the device error word's copy (load uses +0..+4, peeling +16..+27)
 constexpr uint64_t GRAPH_TAG = 0x464f4c5459475248ull;   // "FOLTYGRH"
 constexpr uint64_t RESULT_TAG = 0x464f4c5459525354ull;  // "FOLTYRST"
 constexpr uint64_t FREED_TAG = 0x464f4c5459465245ull;   // "FOLTYFRE"
@@ -132,7 +136,8 @@ struct folty_graph {
     int32_t* seg;     // [2S + 1]: E_{a->b} = [seg[2s], seg[2s+1]), E_{b->a} = [seg[2s+1], seg[2s+2])
     int32_t* ea;      // [S] smaller endpoint a
     int32_t* eb;      // [S] larger endpoint b
-    int32_t* deg;     // [n] |N(u)|
+    int32_t* deg;
+    int32_t* core;  // [n] core numbers of G_S     // [n] |N(u)|
     int32_t* common;  // [S] |N(a) cap N(b)| = triangles on the static edge
     int32_t* by_b;    // [S] static edge ids ordered by (b, a)
     int64_t ntri;
@@ -150,6 +155,7 @@ struct folty_graph {
     folty_graph_info info;
     // ---- pinned host staging for small device->host reads
     int64_t* host_stage;  // HOST_STAGE entries
+    int* dev_err;         // device error word: a bounded wait in a kernel ran out
     std::vector<void*>* owned;  // device buffers owned by the graph
 };
 
@@ -168,7 +174,9 @@ T* graph_alloc(folty_graph* g, int64_t count, cudaStream_t s) {
 void graph_release(folty_graph* g, void* p, cudaStream_t s);
 
 // Reads `count` int64 values from device memory through the graph's pinned staging
-// buffer (synchronises the stream).
+// buffer (synchronises the stream). Also reads the graph's device error word: when a
+// bounded wait in an earlier kernel ran out, the word is cleared and the call fails with
+// FOLTY_ETIMEOUT before any value is used. count may be 0 (a plain check).
 void read_back(folty_graph* g, const void* const* dev_ptrs, const int* sizes, int count,
                int64_t* out, cudaStream_t s);
 int64_t read_i64(folty_graph* g, const int64_t* p, cudaStream_t s);
@@ -185,10 +193,10 @@ void exclusive_scan(Scratch& sc, const uint32_t* in, uint32_t* out, int64_t n);
 
 // Stable LSD radix sort of (key, value) pairs on key bits [0, bits). Buffers ping-pong
 // between (keys, vals) and (keys_alt, vals_alt); returns true when the result ended
-// up in the *_alt buffers. A look-back wait that runs out sets the device int *err to 1
-// (the caller zeroes it, and must read it before using the output).
+// up in the *_alt buffers. A look-back wait that runs out sets the scratch error word and
+// leaves the output unusable: the caller checks the word before the values index anything.
 bool radix_sort_pairs(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
-                      uint32_t* vals_alt, int64_t n, int bits, int* err);
+                      uint32_t* vals_alt, int64_t n, int bits);
 
 int bit_length(uint64_t x);
 

@@ -23,18 +23,37 @@ namespace folty {
 constexpr int LIVE_IDLE = 3;  // idle slots per kept triangle (keeps >= 3 slots per triangle)
 constexpr uint8_t DMIN_NEVER = 255;
 
-template <typename TS>
-__device__ __forceinline__ void run_range(const TS* __restrict__ T, int32_t b, int32_t e, int64_t& first,
-                                          int64_t& last, bool& any) {
-    if (b < e) {
-        const int64_t f = (int64_t)T[b], l = (int64_t)T[e - 1];
-        first = any ? (f < first ? f : first) : f;
-        last = any ? (l > last ? l : last) : l;
-        any = true;
-    }
+// x[i] for a run index i in [0, 6) known only at run time, by selects, so that the
+// arrays stay in registers.
+template <typename V>
+__device__ __forceinline__ V pick6(const V* x, int i) {
+    V v = x[0];
+#pragma unroll
+    for (int q = 1; q < 6; q++) v = (i == q) ? x[q] : v;
+    return v;
 }
 
-// rsig[r][t] = sigma1 of role r = 2e + d; rmin[dir][r][t] = dmin bucket.
+// Time span of the union of runs a and b (b < 0: run a alone) from the first and last
+// timestamps of the six runs of a triangle.
+__device__ __forceinline__ bool span_of(const int64_t* f, const int64_t* l, const bool* ne, int a, int b,
+                                        int64_t& first, int64_t& last) {
+    bool any = false;
+    if (pick6(ne, a)) {
+        first = pick6(f, a);
+        last = pick6(l, a);
+        any = true;
+    }
+    if (b >= 0 && pick6(ne, b)) {
+        const int64_t fb = pick6(f, b), lb = pick6(l, b);
+        first = any ? min(first, fb) : fb;
+        last = any ? max(last, lb) : lb;
+        any = true;
+    }
+    return any;
+}
+
+// rsig[r][t] = sigma1 of role r = 2e + d; rmin[dir][r][t] = dmin bucket. The first and
+// last timestamps of the triangle's six runs are loaded once, together.
 template <typename TS>
 __global__ void k_role_summary(const int4* __restrict__ tri, int64_t ntri, const int32_t* __restrict__ seg,
                                const TS* __restrict__ T, int32_t* __restrict__ rsig, uint8_t* __restrict__ rmin) {
@@ -49,26 +68,29 @@ __global__ void k_role_summary(const int4* __restrict__ tri, int64_t ntri, const
             off[3 * e + 1] = seg[2 * se[e] + 1];
             off[3 * e + 2] = seg[2 * se[e] + 2];
         }
+        int64_t f[6], l[6];
+        bool ne[6];
+#pragma unroll
+        for (int q = 0; q < 6; q++) {  // run q = 2e + d = [off[3e + d], off[3e + d + 1])
+            const int32_t b = off[3 * (q >> 1) + (q & 1)], en = off[3 * (q >> 1) + (q & 1) + 1];
+            ne[q] = b < en;
+            f[q] = ne[q] ? (int64_t)T[b] : 0;
+            l[q] = ne[q] ? (int64_t)T[en - 1] : 0;
+        }
 #pragma unroll
         for (int r = 0; r < 6; r++) {
-            const int e = r >> 1, d = r & 1;
-            const int32_t b1 = off[3 * e + d], e1 = off[3 * e + d + 1];
-            rsig[r * ntri + t] = e1 - b1;
+            rsig[r * ntri + t] = off[3 * (r >> 1) + (r & 1) + 1] - off[3 * (r >> 1) + (r & 1)];
+#pragma unroll
             for (int dir = 0; dir < 3; dir++) {
                 uint8_t bucket = DMIN_NEVER;
-                if (e1 > b1) {
+                if (ne[r]) {
                     int s2, s3;
-                    role_segments(tr.w, e, d, dir, s2, s3);
-                    const int o2 = 3 * (s2 >> 1) + (s2 & 1), o3 = 3 * (s3 >> 1) + (s3 & 1);
+                    role_segments(tr.w, r >> 1, r & 1, dir, s2, s3);
+                    const bool both = dir == FOLTY_DIR_EITHER;  // s2, s3 are the d = 0 runs then
                     int64_t f2 = 0, l2 = 0, f3 = 0, l3 = 0;
-                    bool a2 = false, a3 = false;
-                    run_range(T, off[o2], off[o2 + 1], f2, l2, a2);
-                    run_range(T, off[o3], off[o3 + 1], f3, l3, a3);
-                    if (dir == FOLTY_DIR_EITHER) {
-                        run_range(T, off[o2 + 1], off[o2 + 2], f2, l2, a2);
-                        run_range(T, off[o3 + 1], off[o3 + 2], f3, l3, a3);
-                    }
-                    const int64_t f1 = (int64_t)T[b1], l1 = (int64_t)T[e1 - 1];
+                    const bool a2 = span_of(f, l, ne, s2, both ? s2 + 1 : -1, f2, l2);
+                    const bool a3 = span_of(f, l, ne, s3, both ? s3 + 1 : -1, f3, l3);
+                    const int64_t f1 = f[r], l1 = l[r];
                     if (a2 && a3 && l2 >= f1 && l3 >= (f2 > f1 ? f2 : f1)) {
                         int64_t dmin = f2 - l1;
                         if (f3 - l1 > dmin) dmin = f3 - l1;
@@ -308,7 +330,7 @@ void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t
     const int64_t ntri = g->ntri;
     if (ntri == 0 || g->info.probes == 0) return;
     const int T = 256;
-    Scratch sc(g->alloc, s);
+    Scratch sc(g->alloc, s, g->dev_err);
     int32_t* flag = sc.get<int32_t>(2 * (ntri + 1));
     int32_t* lpos = flag + ntri + 1;
     int64_t* cost = sc.get<int64_t>(2 * (ntri + 1));

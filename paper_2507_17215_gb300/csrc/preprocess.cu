@@ -53,19 +53,28 @@ __global__ void k_gather_keys(const uint64_t* __restrict__ key_in, const uint32_
         key_out[i] = key_in[order[i]];
 }
 
-// perm, T (as t - tbase in TS), and the "new static pair" flag of every kept sorted
-// position.
+// perm, T (gathered from t: 32-bit offsets from tmin, or the raw int64 timestamps), and
+// the "new static pair" flag of every kept sorted position.
 template <typename TS>
 __global__ void k_store(const uint64_t* __restrict__ key, const uint32_t* __restrict__ order,
-                        const int64_t* __restrict__ t, int64_t mk, int64_t tbase, int32_t* __restrict__ perm,
+                        const TS* __restrict__ t, int64_t mk, int32_t* __restrict__ perm,
                         TS* __restrict__ T, int32_t* __restrict__ newpair) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mk;
          i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t o = order[i];
-        perm[i] = (int32_t)o;
-        T[i] = (TS)(t[o] - tbase);
-        newpair[i] = (i == 0) || ((key[i] >> 1) != (key[i - 1] >> 1));
+        const uint32_t o = __ldcs(order + i);
+        __stcs(perm + i, (int32_t)o);
+        T[i] = t[o];
+        const uint64_t k = __ldcs(key + i);
+        __stcs(newpair + i, (int32_t)((i == 0) || ((k >> 1) != (key[i - 1] >> 1))));
     }
+}
+
+// 32-bit offsets t - tbase of the input timestamps. 4 bytes an edge keep the gather of
+// k_store inside L2 for inputs of up to ~25M edges (the int64 input is twice that).
+__global__ void k_offsets32(const int64_t* __restrict__ t, int64_t m, int64_t tbase, uint32_t* __restrict__ t32) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        t32[i] = (uint32_t)(__ldcs(t + i) - tbase);
 }
 
 // Static edge ids, endpoints, segment starts. pscan = exclusive scan of newpair.
@@ -289,12 +298,13 @@ constexpr int PEEL_PIECE = PEEL_THREADS;  // adjacency entries per heavy piece
 __device__ __forceinline__ void frontier_append(const PeelArgs& a, bool in, int32_t v, int32_t b, int32_t e,
                                                 int rr) {
     const bool heavy = in && (e - b > PEEL_HEAVY);
-    warp_append(in && !heavy, v, a.fr[rr & 1], &a.ctl[C_FCNT + rr % 3], a.n, &a.ctl[C_ERR]);
+    warp_append(in && !heavy, v, (rr & 1) ? a.fr[1] : a.fr[0], &a.ctl[C_FCNT + rr % 3], a.n, &a.ctl[C_ERR]);
     if (heavy) {
         const int np = (e - b + PEEL_PIECE - 1) / PEEL_PIECE;
         const int base = atomicAdd(&a.ctl[C_HCNT + rr % 3], np);
         if (base + np <= a.hcap) {
-            for (int q = 0; q < np; q++) a.hr[rr & 1][base + q] = ((int64_t)q << 32) | (uint32_t)v;
+            int64_t* hr = (rr & 1) ? a.hr[1] : a.hr[0];
+            for (int q = 0; q < np; q++) hr[base + q] = ((int64_t)q << 32) | (uint32_t)v;
         } else {
             atomicExch(&a.ctl[C_ERR], 2);
         }
@@ -372,8 +382,8 @@ __global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
         }
         int lmin = INT_MAX;
         {
-            const int32_t* acur = a.alive[ac];
-            int32_t* anxt = a.alive[ac ^ 1];
+            const int32_t* acur = ac ? a.alive[1] : a.alive[0];
+            int32_t* anxt = ac ? a.alive[0] : a.alive[1];
             for (int64_t base = gwarp * 32; base < nalive; base += nwarps * 32) {
                 int64_t i = base + lane;
                 bool keep = false, in = false;
@@ -418,7 +428,7 @@ __global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
             if (nalive == 0) break;
             // no vertex of degree k + 1: jump to the smallest remaining degree, round r + 1
             const int kj = *(volatile int*)&ctl[C_MIN + (lvl & 1)];
-            const int32_t* al = a.alive[ac];
+            const int32_t* al = ac ? a.alive[1] : a.alive[0];
             for (int64_t base = gwarp * 32; base < nalive; base += nwarps * 32) {
                 int64_t i = base + lane;
                 bool in = false;
@@ -452,15 +462,42 @@ __global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
                 ctl[C_FCNT + (r + 2) % 3] = 0;
                 ctl[C_HCNT + (r + 2) % 3] = 0;
             }
-            // light vertices: one warp each (at most PEEL_HEAVY / 32 steps)
-            const int32_t* F = a.fr[r & 1];
-            for (int64_t i = gwarp; i < fsz; i += nwarps) {
-                int32_t u = __ldcg(&F[i]);
-                int32_t b = a.rowptr[u], e = a.rowptr[u + 1];
-                for (int32_t j0 = b; j0 < e; j0 += 32) peel_neighbour(a, j0 + lane < e, j0 + lane, k, r);
+            // light vertices: one warp each, two per pass; every row entry of both is
+            // loaded, then every decrement issued, before the first result is used
+            const int32_t* F = (r & 1) ? a.fr[1] : a.fr[0];
+            for (int64_t i0 = gwarp; i0 < fsz; i0 += 2 * nwarps) {
+                constexpr int Q = PEEL_HEAVY / 32;
+                const int64_t i1 = i0 + nwarps;
+                const bool two = i1 < fsz;
+                const int32_t u0 = __ldcg(&F[i0]);
+                const int32_t u1 = two ? __ldcg(&F[i1]) : 0;
+                const int32_t b0 = a.rowptr[u0], e0 = a.rowptr[u0 + 1];
+                const int32_t b1 = two ? a.rowptr[u1] : 0, e1 = two ? a.rowptr[u1 + 1] : 0;
+                int32_t v[2 * Q];
+                int old[2 * Q];
+#pragma unroll
+                for (int q = 0; q < Q; q++) {
+                    const int32_t j0 = b0 + q * 32 + lane, j1 = b1 + q * 32 + lane;
+                    v[q] = (j0 < e0) ? a.adj[j0] : -1;
+                    v[Q + q] = (j1 < e1) ? a.adj[j1] : -1;
+                }
+#pragma unroll
+                for (int q = 0; q < 2 * Q; q++) old[q] = (v[q] >= 0) ? atomicSub(&a.deg[v[q]], 1) : 0;
+#pragma unroll
+                for (int q = 0; q < 2 * Q; q++) {
+                    const bool cross = v[q] >= 0 && old[q] == k + 1;
+                    int32_t rb = 0, re = 0;
+                    if (cross) {
+                        a.rnd[v[q]] = r + 1;
+                        a.core[v[q]] = k;
+                        rb = a.rowptr[v[q]];
+                        re = a.rowptr[v[q] + 1];
+                    }
+                    frontier_append(a, cross, v[q], rb, re, r + 1);
+                }
             }
             // heavy vertices: one block per piece of PEEL_PIECE adjacency entries
-            const int64_t* H = a.hr[r & 1];
+            const int64_t* H = (r & 1) ? a.hr[1] : a.hr[0];
             for (int pc = blockIdx.x; pc < hsz; pc += gridDim.x) {
                 const int64_t hp = __ldcg(&H[pc]);
                 const int32_t u = (int32_t)(hp & 0xffffffffll);
@@ -555,134 +592,170 @@ struct TailArgs {
     int* ctl;
 };
 
-// Block-wide exclusive scan of one value per thread; returns the thread's offset and
-// writes the total to *total. Uses wtot[32].
-__device__ __forceinline__ int block_scan_excl(int v, int* wtot, int* total) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) wtot[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-        int x = wtot[lane], xi = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, xi, o);
-            if (lane >= o) xi += y;
+constexpr int TAIL_LIGHT = 256;   // rows up to this length: one warp, all loads in flight at once
+constexpr int TAIL_HCAP = 1024;   // heavy-frontier capacity per round (overflow goes to the light list)
+
+// Removes local vertex v at level k in round rr: global round and core number, and the
+// frontier of round rr (slot rr % 3 of the counters, buffer rr & 1).
+__device__ __forceinline__ void tail_remove(const TailArgs& a, const int32_t* sL, const int32_t* srow,
+                                            uint8_t* salive, int16_t* FL, int16_t* FH, int* cntL, int* cntH,
+                                            int v, int k, int rr) {
+    salive[v] = 0;
+    a.rnd[sL[v]] = rr;
+    a.core[sL[v]] = k;
+    if (srow[v + 1] - srow[v] > TAIL_LIGHT) {
+        const int h = atomicAdd(&cntH[rr % 3], 1);
+        if (h < TAIL_HCAP) {
+            FH[(rr & 1) * TAIL_HCAP + h] = (int16_t)v;
+            return;
         }
-        wtot[lane] = xi - x;
-        if (lane == 31) *total = xi;
     }
-    __syncthreads();
-    return wtot[w] + inc - v;
+    FL[(rr & 1) * TAIL_MAX + atomicAdd(&cntL[rr % 3], 1)] = (int16_t)v;
+}
+
+// tail_remove for the lanes with rem set, with one counter atomic per warp for the light
+// ones. The whole warp must call it.
+__device__ __forceinline__ void tail_remove_warp(const TailArgs& a, const int32_t* sL, const int32_t* srow,
+                                                 uint8_t* salive, int16_t* FL, int16_t* FH, int* cntL, int* cntH,
+                                                 bool rem, int v, int k, int rr) {
+    bool light = rem;
+    if (rem) {
+        salive[v] = 0;
+        a.rnd[sL[v]] = rr;
+        a.core[sL[v]] = k;
+        if (srow[v + 1] - srow[v] > TAIL_LIGHT) {
+            const int h = atomicAdd(&cntH[rr % 3], 1);
+            if (h < TAIL_HCAP) {
+                FH[(rr & 1) * TAIL_HCAP + h] = (int16_t)v;
+                light = false;
+            }
+        }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, light);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&cntL[rr % 3], __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (light) FL[(rr & 1) * TAIL_MAX + base + __popc(m & ((1u << lane) - 1u))] = (int16_t)v;
 }
 
 // The same peeling as k_peel (levels, rounds, k + 1 -> k crossings), on the local
 // subgraph, continuing the level k and round r where the grid kernel stopped.
+//
+// One __syncthreads per round. Frontier counters rotate over three slots by round
+// number (round r reads slot r % 3, appends to (r + 1) % 3, and thread 0 clears
+// (r + 2) % 3, which nobody reads or writes during round r); frontier buffers alternate
+// by round parity. A light vertex (row <= TAIL_LIGHT) takes one warp that issues all of
+// its row's loads before the first decrement; a heavy one takes the whole block.
 __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    int32_t* sdeg = (int32_t*)smem;                        // TAIL_MAX
-    int32_t* srow = sdeg + TAIL_MAX;                       // TAIL_MAX + 1
-    int32_t* spref = srow + TAIL_MAX + 1;                  // TAIL_THREADS + 1
-    int16_t* sF0 = (int16_t*)(spref + TAIL_THREADS + 1);   // TAIL_MAX
-    int16_t* sF1 = sF0 + TAIL_MAX;                         // TAIL_MAX
-    uint8_t* salive = (uint8_t*)(sF1 + TAIL_MAX);          // TAIL_MAX
-    __shared__ int wtot[32];
-    __shared__ int s_cnt[2], s_min, s_total;
+    int32_t* sdeg = (int32_t*)smem;                     // TAIL_MAX
+    int32_t* srow = sdeg + TAIL_MAX;                    // TAIL_MAX + 1 (+ 3 pad)
+    int32_t* sL = srow + TAIL_MAX + 4;                  // TAIL_MAX
+    int16_t* FL = (int16_t*)(sL + TAIL_MAX);            // 2 x TAIL_MAX
+    int16_t* FH = FL + 2 * TAIL_MAX;                    // 2 x TAIL_HCAP
+    uint8_t* salive = (uint8_t*)(FH + 2 * TAIL_HCAP);   // TAIL_MAX
+    __shared__ int cntL[3], cntH[3], s_min;
     const int nl = *a.nl;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = TAIL_THREADS / 32;
     for (int i = tid; i < nl; i += TAIL_THREADS) {
         sdeg[i] = a.ld[i];
         srow[i] = a.lrow[i];
+        sL[i] = a.L[i];
         salive[i] = 1;
     }
     if (tid == 0) srow[nl] = a.lrow[nl];
+    if (tid < 3) {
+        cntL[tid] = 0;
+        cntH[tid] = 0;
+    }
     int k = a.ctl[C_TAIL_K], r = a.ctl[C_TAIL_R], rounds = a.ctl[C_ROUNDS];
-    int16_t* F = sF0;
-    int16_t* Fn = sF1;
     __syncthreads();
     while (true) {
-        // ---- level start: frontier at k + 1 (or at the minimum degree)
+        // ---- level start: vertices of degree <= k + 1 form the frontier of round r + 1
+        // (the scan takes whole warps: the minimum and the light appends are aggregated
+        // per warp, so the shared counters see one atomic per warp, not one per vertex)
         if (tid == 0) {
-            s_cnt[0] = 0;
             s_min = INT_MAX;
+            cntL[(r + 2) % 3] = 0;
+            cntH[(r + 2) % 3] = 0;
         }
-        __syncthreads();
         int kk = k + 1;
-        for (int i = tid; i < nl; i += TAIL_THREADS) {
-            if (!salive[i]) continue;
-            int d = sdeg[i];
-            if (d <= kk) {
-                salive[i] = 0;
-                a.rnd[a.L[i]] = r + 1;
-                a.core[a.L[i]] = kk;
-                F[atomicAdd(&s_cnt[0], 1)] = (int16_t)i;
-            } else {
-                atomicMin(&s_min, d);
+        int lmin = INT_MAX;
+        for (int i0 = 0; i0 < nl; i0 += TAIL_THREADS) {
+            const int i = i0 + tid;
+            bool rem = false;
+            if (i < nl && salive[i]) {
+                const int d = sdeg[i];
+                if (d <= kk) rem = true;
+                else lmin = min(lmin, d);
             }
+            tail_remove_warp(a, sL, srow, salive, FL, FH, cntL, cntH, rem, i, kk, r + 1);
         }
+        lmin = __reduce_min_sync(0xffffffffu, lmin);
+        if (lane == 0 && lmin != INT_MAX) atomicMin(&s_min, lmin);
         __syncthreads();
-        if (s_cnt[0] == 0) {
+        if (cntL[(r + 1) % 3] + cntH[(r + 1) % 3] == 0) {
             if (s_min == INT_MAX) break;  // nothing left
-            kk = s_min;
-            for (int i = tid; i < nl; i += TAIL_THREADS) {
-                if (salive[i] && sdeg[i] <= kk) {
-                    salive[i] = 0;
-                    a.rnd[a.L[i]] = r + 1;
-                    a.core[a.L[i]] = kk;
-                    F[atomicAdd(&s_cnt[0], 1)] = (int16_t)i;
-                }
+            kk = s_min;                   // jump to the smallest remaining degree
+            for (int i0 = 0; i0 < nl; i0 += TAIL_THREADS) {
+                const int i = i0 + tid;
+                const bool rem = i < nl && salive[i] && sdeg[i] <= kk;
+                tail_remove_warp(a, sL, srow, salive, FL, FH, cntL, cntH, rem, i, kk, r + 1);
             }
             __syncthreads();
         }
         k = kk;
         r += 1;
-        // ---- rounds
+        // ---- rounds at level k
         while (true) {
-            const int fsz = s_cnt[0];
-            if (fsz == 0) break;
-            if (tid == 0) s_cnt[1] = 0;
-            for (int c0 = 0; c0 < fsz; c0 += TAIL_THREADS) {
-                const int i = c0 + tid;
-                int u = 0, len = 0;
-                if (i < fsz) {
-                    u = F[i];
-                    len = srow[u + 1] - srow[u];
-                }
-                const int off = block_scan_excl(len, wtot, &s_total);
-                spref[tid] = off;
-                if (tid == TAIL_THREADS - 1) spref[TAIL_THREADS] = s_total;
-                __syncthreads();
-                const int total = s_total;
-                const int nown = min(TAIL_THREADS, fsz - c0);
-                for (int e = tid; e < total; e += TAIL_THREADS) {
-                    int lo = 0, hi = nown - 1;  // last owner with spref[owner] <= e
-                    while (lo < hi) {
-                        int mid = (lo + hi + 1) >> 1;
-                        if (spref[mid] <= e) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    const int uo = F[c0 + lo];
-                    const int v = a.ladj[srow[uo] + (e - spref[lo])];
-                    const int old = atomicSub(&sdeg[v], 1);
-                    if (old == k + 1) {  // a vertex that already left never crosses again
-                        salive[v] = 0;
-                        a.rnd[a.L[v]] = r + 1;
-                        a.core[a.L[v]] = k;
-                        Fn[atomicAdd(&s_cnt[1], 1)] = (int16_t)v;
-                    }
-                }
-                __syncthreads();  // spref and wtot are reused by the next chunk
+            const int nL = cntL[r % 3];
+            const int nH = min(cntH[r % 3], TAIL_HCAP);
+            if (nL + nH == 0) break;
+            if (tid == 0) {
+                cntL[(r + 2) % 3] = 0;
+                cntH[(r + 2) % 3] = 0;
             }
-            if (tid == 0) s_cnt[0] = s_cnt[1];
+            const int16_t* fl = FL + (r & 1) * TAIL_MAX;
+            const int16_t* fh = FH + (r & 1) * TAIL_HCAP;
+            for (int i = warp; i < nL; i += NW) {
+                const int u = fl[i];
+                const int b = srow[u], e = srow[u + 1];
+                for (int j0 = b; j0 < e; j0 += TAIL_LIGHT) {
+                    int vv[TAIL_LIGHT / 32];
+#pragma unroll
+                    for (int q = 0; q < TAIL_LIGHT / 32; q++) {
+                        const int j = j0 + q * 32 + lane;
+                        vv[q] = (j < e) ? (int)a.ladj[j] : -1;
+                    }
+#pragma unroll
+                    for (int q = 0; q < TAIL_LIGHT / 32; q++) {
+                        if (vv[q] >= 0 && atomicSub(&sdeg[vv[q]], 1) == k + 1)
+                            tail_remove(a, sL, srow, salive, FL, FH, cntL, cntH, vv[q], k, r + 1);
+                    }
+                }
+            }
+            for (int h = 0; h < nH; h++) {
+                const int u = fh[h];
+                const int b = srow[u], e = srow[u + 1];
+                for (int j0 = b; j0 < e; j0 += 4 * TAIL_THREADS) {
+                    int vv[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const int j = j0 + q * TAIL_THREADS + tid;
+                        vv[q] = (j < e) ? (int)a.ladj[j] : -1;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        if (vv[q] >= 0 && atomicSub(&sdeg[vv[q]], 1) == k + 1)
+                            tail_remove(a, sL, srow, salive, FL, FH, cntL, cntH, vv[q], k, r + 1);
+                    }
+                }
+            }
             __syncthreads();
-            int16_t* tmp = F;
-            F = Fn;
-            Fn = tmp;
             r++;
             rounds++;
         }
@@ -693,8 +766,8 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
     }
 }
 
-constexpr size_t TAIL_SMEM = sizeof(int32_t) * (2 * (size_t)TAIL_MAX + 1 + TAIL_THREADS + 1) +
-                             sizeof(int16_t) * 2 * (size_t)TAIL_MAX + (size_t)TAIL_MAX;
+constexpr size_t TAIL_SMEM = sizeof(int32_t) * (3 * (size_t)TAIL_MAX + 4) +
+                             sizeof(int16_t) * 2 * ((size_t)TAIL_MAX + TAIL_HCAP) + (size_t)TAIL_MAX;
 
 __global__ void k_iota(int32_t* __restrict__ a, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -824,16 +897,15 @@ __global__ void k_tri_write(const int32_t* __restrict__ outptr, const int32_t* _
 
 // ================================================================== driver
 
-// The sorted values index other arrays: a sort whose look-back ran out must stop here.
-static void sort_check(folty_graph* g, const int* err, cudaStream_t s) {
-    if (read_i32(g, err, s)) fail(FOLTY_ETIMEOUT, "radix sort: a look-back wait ran out");
-}
+// The sorted values index other arrays: a sort whose look-back ran out must stop here
+// (read_back checks the graph's error word).
+static void sort_check(folty_graph* g, cudaStream_t s) { read_back(g, nullptr, nullptr, 0, nullptr, s); }
 
 void preprocess_graph(folty_graph* g, cudaStream_t s) {
     const int T = 256;
     const int64_t m = g->m;
     const int32_t n = g->n;
-    Scratch sc(g->alloc, s);
+    Scratch sc(g->alloc, s, g->dev_err);
 
     // ---------------- A1: canonical order
     const int nb = bit_length((uint64_t)(n > 1 ? n - 1 : 1));
@@ -844,8 +916,6 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     uint64_t* key_alt = sc.get<uint64_t>(m);
     uint32_t* val = sc.get<uint32_t>(m);
     uint32_t* val_alt = sc.get<uint32_t>(m);
-    int* sort_err = sc.get<int>(1);
-    FOLTY_CUDA(cudaMemsetAsync(sort_err, 0, sizeof(int), s));
     FOLTY_LAUNCH(k_build_keys, grid_for(m, T), T, 0, s, g->in_src, g->in_dst, m, nb, loop_key, key, val);
     uint64_t* skey = key;
     uint32_t* sval = val;
@@ -855,20 +925,19 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         uint64_t* tk = sc.get<uint64_t>(m);
         uint64_t* tk_alt = sc.get<uint64_t>(m);
         FOLTY_LAUNCH(k_time_keys, grid_for(m, T), T, 0, s, g->in_t, m, tmin, tk, val);
-        bool alt = radix_sort_pairs(sc, tk, tk_alt, val, val_alt, m, bit_length((uint64_t)(tmax - tmin)),
-                                    sort_err);
-        sort_check(g, sort_err, s);
+        bool alt = radix_sort_pairs(sc, tk, tk_alt, val, val_alt, m, bit_length((uint64_t)(tmax - tmin)));
+        sort_check(g, s);
         uint32_t* order = alt ? val_alt : val;
         uint32_t* other = alt ? val : val_alt;
         FOLTY_LAUNCH(k_gather_keys, grid_for(m, T), T, 0, s, key, order, m, key_alt);
         // keys now in key_alt, values in order; sort (key_alt, order)
-        bool alt2 = radix_sort_pairs(sc, key_alt, key, order, other, m, key_bits, sort_err);
-        sort_check(g, sort_err, s);
+        bool alt2 = radix_sort_pairs(sc, key_alt, key, order, other, m, key_bits);
+        sort_check(g, s);
         skey = alt2 ? key : key_alt;
         sval = alt2 ? other : order;
     } else {
-        bool alt = radix_sort_pairs(sc, key, key_alt, val, val_alt, m, key_bits, sort_err);
-        sort_check(g, sort_err, s);
+        bool alt = radix_sort_pairs(sc, key, key_alt, val, val_alt, m, key_bits);
+        sort_check(g, s);
         skey = alt ? key_alt : key;
         sval = alt ? val_alt : val;
     }
@@ -881,12 +950,15 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     int32_t* newpair = sc.get<int32_t>(mk + 1);
     int32_t* pscan = sc.get<int32_t>(mk + 1);
     if (mk > 0) {
-        if (g->ts32)
-            FOLTY_LAUNCH(k_store<uint32_t>, grid_for(mk, T), T, 0, s, skey, sval, g->in_t, mk, g->tmin, g->perm,
-                         (uint32_t*)g->T, newpair);
-        else
-            FOLTY_LAUNCH(k_store<int64_t>, grid_for(mk, T), T, 0, s, skey, sval, g->in_t, mk, (int64_t)0, g->perm,
-                         (int64_t*)g->T, newpair);
+        if (g->ts32) {
+            uint32_t* t32 = sc.get<uint32_t>(m);
+            FOLTY_LAUNCH(k_offsets32, grid_for(m, T), T, 0, s, g->in_t, m, g->tmin, t32);
+            FOLTY_LAUNCH(k_store<uint32_t>, grid_for(mk, T), T, 0, s, skey, sval, t32, mk, g->perm, (uint32_t*)g->T,
+                         newpair);
+        } else {
+            FOLTY_LAUNCH(k_store<int64_t>, grid_for(mk, T), T, 0, s, skey, sval, g->in_t, mk, g->perm, (int64_t*)g->T,
+                         newpair);
+        }
     }
     exclusive_scan(sc, newpair, pscan, mk);
     const int32_t S = read_i32(g, pscan + mk, s);
@@ -917,9 +989,9 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         uint32_t* bv = sc.get<uint32_t>(S);
         uint32_t* bv_alt = sc.get<uint32_t>(S);
         FOLTY_LAUNCH(k_edge_keys_b, grid_for(S, T), T, 0, s, g->eb, S, bk, bv);
-        bool alt = radix_sort_pairs(sc, bk, bk_alt, bv, bv_alt, S, nb, sort_err);
+        bool alt = radix_sort_pairs(sc, bk, bk_alt, bv, bv_alt, S, nb);
         by_b = alt ? bv_alt : bv;
-        sort_check(g, sort_err, s);
+        sort_check(g, s);
     }
     g->by_b = graph_alloc<int32_t>(g, S, s);
     if (S > 0) FOLTY_CUDA(cudaMemcpyAsync(g->by_b, by_b, sizeof(int32_t) * (size_t)S, cudaMemcpyDeviceToDevice, s));
@@ -948,7 +1020,8 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
                      by_b, adj, adj_eid, adj_src);
 
     // ---------------- A3: peeling
-    int32_t* core = sc.get<int32_t>(n);
+    g->core = graph_alloc<int32_t>(g, n, s);
+    int32_t* core = g->core;
     int32_t* rnd = sc.get<int32_t>(n);
     {
         PeelArgs pa;

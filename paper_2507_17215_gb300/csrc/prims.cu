@@ -1,8 +1,10 @@
 // Device-wide primitives: exclusive prefix sum and a stable LSD radix sort.
 //
-// Both are bandwidth-bound streaming passes: tiles of 2048 (scan) or 4096 (sort)
-// elements per 256-thread block, coalesced loads, block offsets from a recursive scan
-// of per-tile totals (scan); one kernel per 8-bit digit with a decoupled look-back (sort).
+// Both are bandwidth-bound streaming passes over tiles of 4096 elements (2048 for 8-byte
+// scans) per 256-thread block, with coalesced loads and stores; a tile's offset comes
+// from a decoupled look-back over the totals that earlier tiles publish, so each pass is
+// a single kernel. Every look-back wait is bounded in time and reports through the
+// scratch error word.
 #include "internal.cuh"
 
 namespace folty {
@@ -17,10 +19,24 @@ int bit_length(uint64_t x) {
 }
 
 // ================================================================== scan
+//
+// Single pass: tiles are taken in the order blocks start (a dynamic tile counter); each
+// tile publishes its total, then warp 0 looks back over up to 32 earlier tiles at a
+// time until it meets one whose entry already holds an inclusive prefix (decoupled
+// look-back). Entries pack a 2-bit status with a 62-bit value, so totals must stay
+// below 2^62 (all scanned values are non-negative counts).
 
 constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_ITEMS = 8;
-constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+constexpr unsigned long long SC_AGG = 1ull << 62;
+constexpr unsigned long long SC_PREFIX = 1ull << 63;
+constexpr unsigned long long SC_VALUE = SC_AGG - 1;
+constexpr long long LOOKBACK_TIMEOUT_NS = 10ll * 1000 * 1000 * 1000;
+
+__device__ __forceinline__ long long globaltimer_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 template <typename T>
 __device__ __forceinline__ T block_exclusive_sum(T v, T* warp_tot, T* block_total) {
@@ -48,57 +64,106 @@ __device__ __forceinline__ T block_exclusive_sum(T v, T* warp_tot, T* block_tota
     return warp_tot[warp] + inc - v;
 }
 
-template <typename TIn, typename TOut>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const TIn* __restrict__ in, int64_t n,
-                                                              TOut* __restrict__ bsum) {
-    __shared__ TOut warp_tot[SCAN_THREADS / 32];
-    __shared__ TOut total;
-    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
-    TOut acc = 0;
+// Decoupled look-back by one warp: the sum of all tiles before `tile`. Publishes the
+// tile's inclusive prefix. A wait that runs out sets *err and returns the partial sum
+// (which never exceeds the true prefix: every value is non-negative).
+__device__ unsigned long long warp_lookback(volatile unsigned long long* lb, int64_t tile, unsigned long long total,
+                                            int* err) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long excl = 0;
+    int64_t p = tile - 1;
+    long long t_start = 0;
+    while (p >= 0) {
+        const int64_t q = p - lane;
+        const unsigned long long e = (q >= 0) ? lb[q] : (SC_PREFIX | 0ull);
+        const unsigned prefix = __ballot_sync(0xffffffffu, (e & SC_PREFIX) != 0);
+        const unsigned waiting = __ballot_sync(0xffffffffu, e == 0);
+        const int first = prefix ? __ffs(prefix) - 1 : 31;  // the lanes that matter: 0..first
+        const unsigned need = (first == 31) ? 0xffffffffu : ((2u << first) - 1u);
+        if (waiting & need) {
+            const long long t = globaltimer_ns();
+            if (t_start == 0) t_start = t;
+            else if (t - t_start > LOOKBACK_TIMEOUT_NS) {
+                if (lane == 0) atomicExch(err, 1);
+                break;  // partial sum
+            }
+            __nanosleep(64);
+            continue;
+        }
+        unsigned long long v = (lane <= first) ? (e & SC_VALUE) : 0ull;
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; i++) {
-        int64_t idx = base + (int64_t)i * SCAN_THREADS + threadIdx.x;
-        if (idx < n) acc += (TOut)in[idx];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (prefix) break;
+        p -= 32;
     }
-    block_exclusive_sum<TOut>(acc, warp_tot, &total);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+    if (lane == 0) lb[tile] = SC_PREFIX | (excl + total);
+    return excl;
 }
 
-// Scans one tile; adds the tile's offset (boff[block], or 0 when boff is null). The
-// last tile also writes out[n] = grand total.
-template <typename TIn, typename TOut>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const TIn* in, TOut* out, int64_t n,
-                                                            const TOut* __restrict__ boff) {
-    __shared__ TOut tile[SCAN_TILE];
+// One tile of TILE = SCAN_THREADS * ITEMS elements: coalesced loads into shared memory
+// (padded so that each thread's run of ITEMS is conflict-free), a sequential sum per
+// thread, a block scan, the look-back, and coalesced stores. The last tile also writes
+// out[n] = the grand total. in may equal out.
+template <typename TIn, typename TOut, int ITEMS>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan(const TIn* in, TOut* out, int64_t n,
+                                                       unsigned long long* lb, unsigned int* counter, int* err) {
+    constexpr int TILE = SCAN_THREADS * ITEMS;
+    constexpr int PADW = 128 / sizeof(TOut);  // one pad element per 128 bytes
+    __shared__ TOut buf[TILE + TILE / PADW];
     __shared__ TOut warp_tot[SCAN_THREADS / 32];
     __shared__ TOut total;
-    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    __shared__ unsigned long long s_excl;
+    __shared__ int64_t s_tile;
+    auto pad = [](int i) { return i + i / PADW; };
+    if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * TILE;
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; i++) {
-        int idx = i * SCAN_THREADS + threadIdx.x;
-        int64_t g = base + idx;
-        tile[idx] = (g < n) ? (TOut)in[g] : TOut(0);
+    for (int i = 0; i < ITEMS; i++) {
+        const int idx = i * SCAN_THREADS + threadIdx.x;
+        const int64_t g = base + idx;
+        buf[pad(idx)] = (g < n) ? (TOut)in[g] : TOut(0);
     }
     __syncthreads();
-    TOut loc[SCAN_ITEMS];
+    TOut loc[ITEMS];
     TOut sum = 0;
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; i++) {
-        loc[i] = sum;
-        sum += tile[threadIdx.x * SCAN_ITEMS + i];
+    for (int i = 0; i < ITEMS; i++) {
+        loc[i] = buf[pad(threadIdx.x * ITEMS + i)];
+        sum += loc[i];
     }
-    TOut off = block_exclusive_sum<TOut>(sum, warp_tot, &total);
-    TOut bo = boff ? boff[blockIdx.x] : TOut(0);
+    const TOut off = block_exclusive_sum<TOut>(sum, warp_tot, &total);
+    if (threadIdx.x < 32) {
+        volatile unsigned long long* vlb = lb;
+        const unsigned long long tot = (unsigned long long)total;
+        if (tile == 0) {
+            if (threadIdx.x == 0) {
+                vlb[0] = SC_PREFIX | tot;
+                s_excl = 0;
+            }
+        } else {
+            if (threadIdx.x == 0) vlb[tile] = SC_AGG | tot;
+            const unsigned long long ex = warp_lookback(vlb, tile, tot, err);
+            if (threadIdx.x == 0) s_excl = ex;
+        }
+    }
+    __syncthreads();
+    TOut run = (TOut)s_excl + off;
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; i++) tile[threadIdx.x * SCAN_ITEMS + i] = loc[i] + off + bo;
+    for (int i = 0; i < ITEMS; i++) {
+        buf[pad(threadIdx.x * ITEMS + i)] = run;
+        run += loc[i];
+    }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; i++) {
-        int idx = i * SCAN_THREADS + threadIdx.x;
-        int64_t g = base + idx;
-        if (g < n) out[g] = tile[idx];
+    for (int i = 0; i < ITEMS; i++) {
+        const int idx = i * SCAN_THREADS + threadIdx.x;
+        const int64_t g = base + idx;
+        if (g < n) out[g] = buf[pad(idx)];
     }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = bo + total;
+    if (base + TILE >= n && threadIdx.x == 0) out[n] = (TOut)s_excl + total;
 }
 
 template <typename TIn, typename TOut>
@@ -108,15 +173,14 @@ static void scan_impl(Scratch& sc, const TIn* in, TOut* out, int64_t n) {
         FOLTY_CUDA(cudaMemsetAsync(out, 0, sizeof(TOut), s));
         return;
     }
-    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-    if (nb == 1) {
-        FOLTY_LAUNCH((k_scan_down<TIn, TOut>), 1, SCAN_THREADS, 0, s, in, out, n, (const TOut*)nullptr);
-        return;
-    }
-    TOut* bsum = sc.get<TOut>(nb + 1);
-    FOLTY_LAUNCH((k_scan_reduce<TIn, TOut>), (unsigned)nb, SCAN_THREADS, 0, s, in, n, bsum);
-    scan_impl<TOut, TOut>(sc, bsum, bsum, nb);
-    FOLTY_LAUNCH((k_scan_down<TIn, TOut>), (unsigned)nb, SCAN_THREADS, 0, s, in, out, n, (const TOut*)bsum);
+    constexpr int ITEMS = sizeof(TOut) == 4 ? 16 : 8;
+    constexpr int TILE = SCAN_THREADS * ITEMS;
+    const int64_t tiles = (n + TILE - 1) / TILE;
+    // one zeroed block: the tile counter, then one look-back entry per tile
+    unsigned long long* ctl = sc.get<unsigned long long>(tiles + 1);
+    FOLTY_CUDA(cudaMemsetAsync(ctl, 0, sizeof(unsigned long long) * (size_t)(tiles + 1), s));
+    FOLTY_LAUNCH((k_scan<TIn, TOut, ITEMS>), (unsigned)tiles, SCAN_THREADS, 0, s, in, out, n, ctl + 1,
+                 (unsigned int*)ctl, sc.err());
 }
 
 void exclusive_scan(Scratch& sc, const int32_t* in, int32_t* out, int64_t n) { scan_impl(sc, in, out, n); }
@@ -128,12 +192,11 @@ void exclusive_scan(Scratch& sc, const uint32_t* in, uint32_t* out, int64_t n) {
 //
 // Stable LSD radix sort, one kernel per 8-bit digit ("onesweep"): the histograms of all
 // digits come from one read of the keys up front; each pass takes tiles of 4096 keys in
-// the order blocks start (a dynamic tile counter), ranks them by digit within the tile
-// (warp multisplit with __match_any_sync), publishes the tile's digit counts, and adds
-// the counts of all earlier tiles by looking back over their published values (decoupled
-// look-back: a tile's entry holds either its own count or its inclusive prefix). Keys are
-// then staged in shared memory in digit order, so that the global writes of each digit's
-// run are contiguous.
+// the order blocks start (a dynamic tile counter), ranks them by digit within the tile,
+// publishes the tile's digit counts, and adds the counts of all earlier tiles by looking
+// back over their published values (decoupled look-back: a tile's entry holds either its
+// own count or its inclusive prefix). The tile is then listed in digit order through
+// shared memory, so that the global writes of each digit's run are contiguous.
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
@@ -199,20 +262,37 @@ struct OnesweepArgs {
     long long timeout_ns;
 };
 
-__device__ __forceinline__ long long rs_now() {
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
+// Lanes whose 8-bit digit equals this lane's, from one ballot per bit (far cheaper than
+// __match_any_sync on this GPU).
+__device__ __forceinline__ unsigned digit_peers(unsigned d) {
+    unsigned m = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < RS_BITS; b++) {
+        const bool bit = (d >> b) & 1u;
+        const unsigned on = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? on : ~on;
+    }
+    return m;
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_rs_onesweep(OnesweepArgs a) {
+// One pass of one 8-bit digit over a tile of RS_TILE keys:
+//  1. every load of the tile is issued before any is used; keys and values are staged
+//     in shared memory in load order;
+//  2. ranks within the tile: warp w owns keys [w * 32 * ITEMS, ...) in order, ranked by
+//     digit with per-bit ballots and per-warp 16-bit counters (stable);
+//  3. thread d (one per digit) turns the per-warp counts into offsets, publishes the
+//     tile's count of digit d and looks back over earlier tiles for its global offset;
+//  4. a 16-bit permutation in shared memory lists the tile in digit order, and the
+//     writes of each digit's run are contiguous. Positions are 32-bit (n < 2^32).
+__global__ void __launch_bounds__(RS_THREADS, 3) k_rs_onesweep(OnesweepArgs a) {
     extern __shared__ __align__(16) unsigned char rs_smem[];
-    uint64_t* skey = (uint64_t*)rs_smem;                  // RS_TILE
-    uint32_t* sval = (uint32_t*)(skey + RS_TILE);         // RS_TILE
-    __shared__ uint16_t wh[RS_WARPS][RS_BINS];            // per-warp counts, then offsets
-    __shared__ uint32_t bstart[RS_BINS];                  // tile-local start of each digit
-    __shared__ unsigned long long gofs[RS_BINS];          // global start of each digit's run
-    __shared__ uint32_t wt[RS_THREADS / 32];
+    uint64_t* skey = (uint64_t*)rs_smem;                    // RS_TILE, load order
+    uint32_t* sval = (uint32_t*)(skey + RS_TILE);           // RS_TILE, load order
+    uint16_t* sperm = (uint16_t*)(sval + RS_TILE);          // RS_TILE, digit order -> load order
+    __shared__ uint16_t wh[RS_WARPS][RS_BINS];              // per-warp counts, then offsets
+    __shared__ uint32_t bstart[RS_BINS];                    // tile-local start of each digit
+    __shared__ uint32_t adj[RS_BINS];                       // final position of digit-order slot j: adj + j
+    __shared__ uint32_t wt[RS_BINS / 32];
     __shared__ int s_tile, s_fail;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&wh[0][0])[i] = 0;
@@ -224,29 +304,47 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_onesweep(OnesweepArgs a) {
     const int64_t tile = s_tile;
     const int64_t t0 = tile * RS_TILE;
     const int tn = (int)min((int64_t)RS_TILE, a.n - t0);
-    // ---- rank within the tile: warp w owns keys [w * 32 * ITEMS, ...) in order
+    const uint64_t* kin = a.keys + t0;
+    const uint32_t* vin = a.vals + t0;
     const int wbase = warp * 32 * RS_ITEMS;
+    // ---- 1. loads, staging, digits
+    uint32_t info[RS_ITEMS];  // digit | rank within (warp, digit) << 8
+    {
+        uint64_t kr[RS_ITEMS];
+        uint32_t vr[RS_ITEMS];
+#pragma unroll
+        for (int i = 0; i < RS_ITEMS; i++) {
+            const int idx = wbase + i * 32 + lane;
+            kr[i] = (idx < tn) ? kin[idx] : 0ull;
+            vr[i] = (idx < tn) ? vin[idx] : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < RS_ITEMS; i++) {
+            const int idx = wbase + i * 32 + lane;
+            if (idx < tn) {
+                skey[idx] = kr[i];
+                sval[idx] = vr[i];
+            }
+            info[i] = (unsigned)(kr[i] >> a.shift) & (RS_BINS - 1);
+        }
+    }
+    // ---- 2. ranks
     const unsigned lt_mask = (1u << lane) - 1u;
-    uint64_t k[RS_ITEMS];
-    uint32_t v[RS_ITEMS];
-    uint16_t rank[RS_ITEMS];
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; i++) {
         const int idx = wbase + i * 32 + lane;
         const bool valid = idx < tn;
-        k[i] = valid ? a.keys[t0 + idx] : 0ull;
-        v[i] = valid ? a.vals[t0 + idx] : 0u;
-        const unsigned d = valid ? ((unsigned)(k[i] >> a.shift) & (RS_BINS - 1)) : (unsigned)RS_BINS;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned d = info[i];
+        const unsigned peers = digit_peers(d) & __ballot_sync(0xffffffffu, valid);
         unsigned before = 0;
         if (valid) before = wh[warp][d];
         __syncwarp();
         if (valid && lane == __ffs(peers) - 1) wh[warp][d] = (uint16_t)(before + __popc(peers));
         __syncwarp();
-        rank[i] = (uint16_t)(before + __popc(peers & lt_mask));
+        info[i] = d | ((before + __popc(peers & lt_mask)) << 8);
     }
     __syncthreads();
-    // ---- per digit (thread d): warp offsets, tile count, publish, look back
+    // ---- 3. per digit (thread d): warp offsets, tile count, publish, look back
     const int d = threadIdx.x;  // RS_THREADS == RS_BINS
     uint32_t cnt = 0;
 #pragma unroll
@@ -257,6 +355,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_onesweep(OnesweepArgs a) {
     }
     volatile unsigned long long* lb = a.lb;
     lb[tile * RS_BINS + d] = (tile == 0 ? LB_PREFIX : LB_AGG) | cnt;
+    uint32_t bs;
     {   // tile-local exclusive scan of the digit counts
         uint32_t inc = cnt;
 #pragma unroll
@@ -268,57 +367,72 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_onesweep(OnesweepArgs a) {
         __syncthreads();
         uint32_t off = 0;
         for (int j = 0; j < warp; j++) off += wt[j];
-        bstart[d] = off + inc - cnt;
+        bs = off + inc - cnt;
+        bstart[d] = bs;
     }
     unsigned long long excl = 0;
     if (tile > 0) {
+        // four entries in flight per step; an entry not yet published is polled again
         int64_t p = tile - 1;
-        const long long t_start = rs_now();
-        while (p >= 0) {
-            const unsigned long long e = lb[p * RS_BINS + d];
-            if (e == 0) {  // predecessor has not published yet
-                if (rs_now() - t_start > a.timeout_ns) {
+        long long t_start = 0;
+        bool done = false;
+        while (!done) {
+            unsigned long long e[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) e[j] = (p - j >= 0) ? (unsigned long long)lb[(p - j) * RS_BINS + d] : LB_PREFIX;
+            bool stall = false;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if (!done && !stall) {
+                    if (e[j] == 0) {
+                        stall = true;
+                    } else {
+                        excl += e[j] & LB_VALUE;
+                        p--;
+                        if (e[j] & LB_PREFIX) done = true;
+                    }
+                }
+            }
+            if (stall && !done) {
+                const long long t = globaltimer_ns();
+                if (t_start == 0) {
+                    t_start = t;
+                } else if (t - t_start > a.timeout_ns) {
                     s_fail = 1;
                     atomicExch(a.err, 1);
                     break;
                 }
                 __nanosleep(32);
-                continue;
             }
-            excl += e & LB_VALUE;
-            if (e & LB_PREFIX) break;
-            p--;
         }
         lb[tile * RS_BINS + d] = LB_PREFIX | (excl + cnt);
     }
-    gofs[d] = (unsigned long long)a.base[d] + excl;
+    adj[d] = (uint32_t)((unsigned long long)a.base[d] + excl) - bs;  // mod 2^32
     __syncthreads();
     if (s_fail) return;  // block-uniform: positions are unknown
-    // ---- stage in digit order, then write each digit's run contiguously
+    // ---- 4. digit-order permutation, then contiguous runs
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; i++) {
         const int idx = wbase + i * 32 + lane;
         if (idx < tn) {
-            const unsigned dd = (unsigned)(k[i] >> a.shift) & (RS_BINS - 1);
-            const int lpos = (int)bstart[dd] + wh[warp][dd] + rank[i];
-            skey[lpos] = k[i];
-            sval[lpos] = v[i];
+            const unsigned dd = info[i] & (RS_BINS - 1);
+            sperm[bstart[dd] + wh[warp][dd] + (info[i] >> 8)] = (uint16_t)idx;
         }
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < tn; idx += RS_THREADS) {
-        const uint64_t kk = skey[idx];
-        const unsigned dd = (unsigned)(kk >> a.shift) & (RS_BINS - 1);
-        const unsigned long long pos = gofs[dd] + (unsigned long long)(idx - (int)bstart[dd]);
+    for (int j = threadIdx.x; j < tn; j += RS_THREADS) {
+        const int src = sperm[j];
+        const uint64_t kk = skey[src];
+        const uint32_t pos = adj[(unsigned)(kk >> a.shift) & (RS_BINS - 1)] + (uint32_t)j;
         a.okeys[pos] = kk;
-        a.ovals[pos] = sval[idx];
+        a.ovals[pos] = sval[src];
     }
 }
 
-constexpr size_t RS_DYN_SMEM = RS_TILE * (sizeof(uint64_t) + sizeof(uint32_t));
+constexpr size_t RS_DYN_SMEM = RS_TILE * (sizeof(uint64_t) + sizeof(uint32_t) + sizeof(uint16_t));
 
 bool radix_sort_pairs(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
-                      uint32_t* vals_alt, int64_t n, int bits, int* err) {
+                      uint32_t* vals_alt, int64_t n, int bits) {
     if (n <= 1 || bits <= 0) return false;
     if (n >= (int64_t)0xffffffffll) fail(FOLTY_EINVAL, "radix sort: too many keys");
     cudaStream_t s = sc.stream();
@@ -341,7 +455,7 @@ bool radix_sort_pairs(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uint32_t*
         FOLTY_CUDA(cudaMemsetAsync(lb, 0, sizeof(unsigned long long) * (size_t)(tiles * RS_BINS), s));
         FOLTY_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
         OnesweepArgs oa{alt ? keys_alt : keys, alt ? vals_alt : vals, alt ? keys : keys_alt, alt ? vals : vals_alt,
-                        n, RS_BITS * p, base + p * RS_BINS, lb, counter, err, 10ll * 1000 * 1000 * 1000};
+                        n, RS_BITS * p, base + p * RS_BINS, lb, counter, sc.err(), LOOKBACK_TIMEOUT_NS};
         FOLTY_LAUNCH(k_rs_onesweep, (unsigned)tiles, RS_THREADS, RS_DYN_SMEM, s, oa);
         alt = !alt;
     }

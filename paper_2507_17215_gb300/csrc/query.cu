@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe(const int4* __restrict__ t
 
 struct ThresholdArgs {
     const int32_t* cnt;
-    const int32_t* sd;
+    const int32_t* sd;  // 2 * static id + direction of every sorted edge
     int64_t mk;
     const int32_t* ea;
     const int32_t* eb;
@@ -60,8 +60,8 @@ struct ThresholdArgs {
     const int32_t* common;
     int quant, universe;
     int64_t num, den;
-    int32_t* seg_max;    // [2S]
-    int32_t* seg_ncert;  // [2S]
+    int32_t* seg_max;    // [2S], zeroed
+    int32_t* seg_ncert;  // [2S], zeroed
     unsigned long long* n_cert;
     const int32_t* perm;  // with cert_in: certificate flag of input edge perm[i]
     int32_t* cert_in;     // [m] or null
@@ -72,35 +72,67 @@ __device__ __forceinline__ bool certifies(int quant, int64_t c, int64_t U, int64
     return c >= 1 && (quant == FOLTY_Q_EXISTS || c * den >= num * U);
 }
 
-__global__ void k_threshold(ThresholdArgs a) {
+constexpr int TH_THREADS = 256;
+constexpr int TH_BATCH = 8;  // 32-edge chunks whose loads are in flight together, per warp
+
+// Edge-major, so every warp gets the same amount of work: a warp takes TH_BATCH chunks
+// of 32 consecutive sorted edges, loads their pair keys and counts together, and reduces
+// each run of one directed pair within a chunk (runs are contiguous: the order is sorted
+// by pair) with a ballot of run heads; a run with a non-zero max or certificates adds
+// them to its pair with one atomic. The universe size is looked up only for edges with
+// c >= 1 (no other edge can certify).
+__global__ void __launch_bounds__(TH_THREADS) k_threshold(ThresholdArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long my_cert = 0;
-    for (int64_t base = gw * 32; base < a.mk; base += nw * 32) {
-        int64_t i = base + lane;
-        int32_t key = -1, c = 0;
-        int sat = 0;
-        if (i < a.mk) {
-            key = a.sd[i];
-            c = a.cnt[i];
-            int32_t s = key >> 1, d = key & 1;
-            int32_t x = d ? a.eb[s] : a.ea[s];
-            int32_t y = d ? a.ea[s] : a.eb[s];
-            int64_t U = a.universe == FOLTY_U_HEAD ? a.deg[x]
-                        : a.universe == FOLTY_U_TAIL ? a.deg[y] : a.common[s];
-            sat = certifies(a.quant, c, U, a.num, a.den);
-            if (a.cert_in) a.cert_in[a.perm[i]] = sat;
+    for (int64_t b0 = gw * 32 * TH_BATCH; b0 < a.mk; b0 += nw * 32 * TH_BATCH) {
+        int32_t kb[TH_BATCH], cb[TH_BATCH], ub[TH_BATCH];
+#pragma unroll
+        for (int k = 0; k < TH_BATCH; k++) {
+            const int64_t i = b0 + k * 32 + lane;
+            kb[k] = (i < a.mk) ? a.sd[i] : -1;
+            cb[k] = (i < a.mk) ? a.cnt[i] : 0;
         }
-        // equal keys are contiguous (sorted order): reduce each run once
-        unsigned peers = __match_any_sync(0xffffffffu, key);
-        int run_max = __reduce_max_sync(peers, c);
-        int run_sat = __reduce_add_sync(peers, sat);
-        if (key >= 0 && lane == __ffs(peers) - 1) {
-            if (run_max > 0) atomicMax(&a.seg_max[key], run_max);
-            if (run_sat > 0) atomicAdd(&a.seg_ncert[key], run_sat);
+        // universe sizes of the edges with c >= 1, the lookups of all chunks in flight at once
+#pragma unroll
+        for (int k = 0; k < TH_BATCH; k++) {
+            ub[k] = -1;
+            if (cb[k] >= 1) {
+                const int64_t s = kb[k] >> 1;
+                if (a.universe == FOLTY_U_COMMON) ub[k] = a.common[s];
+                else ub[k] = ((a.universe == FOLTY_U_HEAD) != (bool)(kb[k] & 1)) ? a.ea[s] : a.eb[s];
+            }
         }
-        my_cert += (unsigned long long)sat;
+        if (a.universe != FOLTY_U_COMMON) {
+#pragma unroll
+            for (int k = 0; k < TH_BATCH; k++)
+                if (cb[k] >= 1) ub[k] = a.deg[ub[k]];
+        }
+#pragma unroll
+        for (int k = 0; k < TH_BATCH; k++) {
+            if (b0 + k * 32 < a.mk) {  // warp-uniform
+                const int64_t i = b0 + k * 32 + lane;
+                const int32_t key = kb[k], c = cb[k];
+                const int sat = (c >= 1) ? certifies(a.quant, c, ub[k], a.num, a.den) : 0;
+                if (a.cert_in && i < a.mk) a.cert_in[a.perm[i]] = sat;
+                // runs of one pair are contiguous lanes (past-the-end lanes hold key -1
+                // and come last, as a run of their own)
+                const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+                const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || key != prev);
+                const unsigned above = heads & ~((2u << lane) - 1u);
+                const int start = 31 - __clz(heads & ((2u << lane) - 1u));
+                const unsigned peers =
+                    (above ? (above & (0u - above)) - 1u : 0xffffffffu) & ~((1u << start) - 1u);
+                const int run_max = __reduce_max_sync(peers, c);
+                const int run_sat = __reduce_add_sync(peers, sat);
+                if (key >= 0 && lane == start) {
+                    if (run_max > 0) atomicMax(&a.seg_max[key], run_max);
+                    if (run_sat > 0) atomicAdd(&a.seg_ncert[key], run_sat);
+                }
+                my_cert += (unsigned long long)sat;
+            }
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) my_cert += __shfl_xor_sync(0xffffffffu, my_cert, o);
@@ -312,8 +344,8 @@ static void pairs_device(folty_graph* g, const folty_query_params& q, const int3
         ThresholdArgs a{cnt, g->sd, mk, g->ea, g->eb, g->deg, g->common, (int)q.quant, (int)q.universe,
                         (int64_t)q.rho_num, (int64_t)q.rho_den, p.seg_max, p.seg_ncert, p.n_cert,
                         g->perm, p.cert_flag};
-        StageSpan span(ST_THRESHOLD, s, 8 * mk + 20 * n2);
-        FOLTY_LAUNCH(k_threshold, grid_for(mk, T), T, 0, s, a);
+        StageSpan span(ST_THRESHOLD, s, 8 * mk);  // pair key + count per edge
+        FOLTY_LAUNCH(k_threshold, grid_for((mk + TH_BATCH - 1) / TH_BATCH, TH_THREADS), TH_THREADS, 0, s, a);
     }
     if (p.cert_flag) exclusive_scan(sc, p.cert_flag, p.cert_pos, g->m);
     if (n2 > 0) FOLTY_LAUNCH(k_pair_flags, grid_for(n2, T), T, 0, s, p.seg_ncert, g->by_b, S, p.flag);
@@ -339,7 +371,7 @@ void finish_queries(folty_graph* g, const folty_query_params* const* qs, const i
     const int G = READBACK_MAX / 4;
     for (int g0 = 0; g0 < nq; g0 += G) {
         const int ng = std::min(G, nq - g0);
-        Scratch sc(g->alloc, s);
+        Scratch sc(g->alloc, s, g->dev_err);
         std::vector<PairStage> st;
         for (int i = 0; i < ng; i++) {
             st.push_back(pair_stage(sc, g, *qs[g0 + i]));
@@ -399,7 +431,7 @@ void finish_query(folty_graph* g, const folty_query_params& q, const int32_t* cn
 }
 
 void run_query(folty_graph* g, const folty_query_params& q, folty_result* out, cudaStream_t s) {
-    Scratch sc(g->alloc, s);
+    Scratch sc(g->alloc, s, g->dev_err);
     const int64_t mk = g->m_kept;
     int32_t* cnt = sc.get<int32_t>(mk);
     if (mk > 0) FOLTY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)mk, s));
@@ -450,7 +482,7 @@ __global__ void k_traffic(const int4* __restrict__ tri, int64_t ntri, const int3
 }
 
 void traffic_model(folty_graph* g, int dir, folty_traffic_model* out, cudaStream_t s) {
-    Scratch sc(g->alloc, s);
+    Scratch sc(g->alloc, s, g->dev_err);
     unsigned long long* acc = sc.get<unsigned long long>(1);
     FOLTY_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long), s));
     if (g->ntri > 0)

@@ -196,11 +196,15 @@ def _core_numbers(n, src, dst):
 
 def test_degeneracy_and_orientation(F):
     rng = np.random.default_rng(12)
+    # the first three fit the single-block tail from the start; the last two run the
+    # grid-wide phases first (more than 12,288 vertices) and reach hubs in the tail
     for g in (W.config_graph(1), W.random_small_graph(rng, 120, 5000, 10),
-              W.config_graph(3, scale=0.002)):
+              W.config_graph(3, scale=0.002), W.config_graph(2, scale=0.05), W.config_graph(2, scale=0.2)):
         core = _core_numbers(g.n, g.src, g.dst)
         with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
             info = G.info()
+            got = G.core_numbers()
+        np.testing.assert_array_equal(got, np.asarray(core, dtype=np.int32))
         assert info["degeneracy"] == max(core)
         assert info["max_out_degree"] <= info["degeneracy"]
         loops = int((g.src == g.dst).sum())
