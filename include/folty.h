@@ -62,7 +62,11 @@ enum { FOLTY_OUTER_NONE = 0, FOLTY_OUTER_FORALL_T = 1 };              /* quantif
 
 /* One query (Definition 1.1). rho = rho_num / rho_den with 0 <= rho_num <= rho_den,
  * rho_den > 0; compared exactly in integers. want_edge_counts != 0 also returns c_e for
- * every input edge; want_certificates != 0 also lists every certificate.
+ * every input edge; want_certificates != 0 also lists every certificate;
+ * want_triples != 0 also returns the solutions of the all-existential query
+ * (Definition 1.2 with exists on u, v and w): every (x, y, w) such that some temporal
+ * edge x -> y forms a delta-temporal triangle with witness w (direction variant dir;
+ * rho, quant and universe do not apply to them).
  * outer = FOLTY_OUTER_FORALL_T adds the vertex queries of Section 4: with the solution
  * pairs as the set L, vertex u is a solution when #{v : (u, v) in L} >= 1 and
  * #{v : (u, v) in L} * outer_rho_den >= outer_rho_num * |N(u)| -- exists-forall-forall
@@ -71,7 +75,7 @@ typedef struct {
     int64_t delta;
     uint32_t rho_num, rho_den;
     uint8_t quant, dir, universe, want_edge_counts;
-    uint8_t outer, want_certificates, reserved[2];
+    uint8_t outer, want_certificates, want_triples, reserved;
     uint32_t outer_rho_num, outer_rho_den;
 } folty_query_params;
 
@@ -85,7 +89,9 @@ typedef struct {
  *   vertex, vertex_count: outer queries: the n_vertices solutions ascending, with the
  *                       number of solution pairs they head (NULL otherwise).
  *   certificate:        want_certificates: input indices of the n_cert_edges
- *                       certificates, ascending (NULL otherwise). */
+ *                       certificates, ascending (NULL otherwise).
+ *   triple_x, triple_y, triple_w: want_triples: the n_triples all-existential
+ *                       solutions (x, y, w), sorted by (x, y, w) (NULL otherwise). */
 typedef struct {
     uint64_t tag; /* written by the library; lets folty_free tell a result from a graph */
     int64_t n_pairs;
@@ -96,6 +102,8 @@ typedef struct {
     int64_t n_vertices;
     int32_t *vertex, *vertex_count;
     int64_t *certificate;
+    int64_t n_triples;
+    int32_t *triple_x, *triple_y, *triple_w;
 } folty_result;
 
 /* Sizes and derived figures of a preprocessed graph. */

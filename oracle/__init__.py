@@ -5,7 +5,9 @@ leg of ``bench.py`` import this package. The CUDA library never does, and this p
 never imports the library.
 
 ``folty_oracle.c`` is the plain C definition (see its header for the paper passages it
-follows); this module compiles it with gcc and wraps it with ctypes.
+follows); ``folty_paper.c`` is the paper's own source-only procedure (out- and
+in-neighbour cases, interval lists, three-phase segment trees), an independent
+cross-check of the first. This module compiles both with gcc and wraps them with ctypes.
 """
 from __future__ import annotations
 
@@ -17,7 +19,7 @@ from typing import Dict, Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "folty_oracle.c")
+_SRCS = [os.path.join(_HERE, "folty_oracle.c"), os.path.join(_HERE, "folty_paper.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lib = None
@@ -27,10 +29,10 @@ def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, OpenMP)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(s) for s in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", _SRC,
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", *_SRCS,
                     "-o", tmp], check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -61,6 +63,13 @@ def _load():
                                  i32p, i32p, i64p]
     lib.oracle_vertices.restype = ctypes.c_int64
     lib.oracle_vertices.argtypes = [P, ctypes.c_int64, i32p, ctypes.c_int64, ctypes.c_int64, i32p, i32p]
+    lib.oracle_triples.restype = ctypes.c_int64
+    lib.oracle_triples.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, i32p, i32p, i32p]
+    lib.paper_counts.restype = ctypes.c_int
+    lib.paper_counts.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i64p, ctypes.c_int64, i32p]
+    lib.paper_segtree_counts.restype = ctypes.c_int
+    lib.paper_segtree_counts.argtypes = [i64p, ctypes.c_int, i64p, i64p, i32p, ctypes.c_int, i64p, ctypes.c_int,
+                                         i64p]
     lib.oracle_certificates.restype = ctypes.c_int64
     lib.oracle_certificates.argtypes = [P, i32p, i32p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                         ctypes.c_int, i64p]
@@ -74,6 +83,40 @@ def threads() -> int:
 
 def _ptr(a: np.ndarray, ctype):
     return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def paper_counts(g, delta: int) -> np.ndarray:
+    """c_e (input order) of the out motif by the paper's procedure (folty_paper.c)."""
+    lib = _load()
+    src = np.ascontiguousarray(g.src, dtype=np.int32)
+    dst = np.ascontiguousarray(g.dst, dtype=np.int32)
+    t = np.ascontiguousarray(g.t, dtype=np.int64)
+    out = np.zeros(max(src.shape[0], 1), dtype=np.int32)
+    rc = lib.paper_counts(int(g.n), src.shape[0], _ptr(src, ctypes.c_int32), _ptr(dst, ctypes.c_int32),
+                          _ptr(t, ctypes.c_int64), int(delta), _ptr(out, ctypes.c_int32))
+    if rc != 0:
+        raise ValueError("paper_counts: bad arguments")
+    return out[:src.shape[0]]
+
+
+def paper_segtree_counts(timestamps, lists, queries) -> np.ndarray:
+    """The appendix's segment tree on its own: a tree over the distinct ascending
+    `timestamps`, the interval lists of successive sources inserted in order
+    (`lists[s]` = [(lo, hi), ...]), then the root-to-leaf counter sums at `queries`."""
+    lib = _load()
+    ts = np.ascontiguousarray(timestamps, dtype=np.int64)
+    lo = np.array([a for L in lists for a, _ in L] or [0], dtype=np.int64)
+    hi = np.array([b for L in lists for _, b in L] or [0], dtype=np.int64)
+    off = np.zeros(len(lists) + 1, dtype=np.int32)
+    off[1:] = np.cumsum([len(L) for L in lists])
+    q = np.ascontiguousarray(queries, dtype=np.int64)
+    out = np.zeros(max(q.shape[0], 1), dtype=np.int64)
+    rc = lib.paper_segtree_counts(_ptr(ts, ctypes.c_int64), ts.shape[0], _ptr(lo, ctypes.c_int64),
+                                  _ptr(hi, ctypes.c_int64), _ptr(off, ctypes.c_int32), len(lists),
+                                  _ptr(q, ctypes.c_int64), q.shape[0], _ptr(out, ctypes.c_int64))
+    if rc != 0:
+        raise MemoryError("paper_segtree_counts")
+    return out[:q.shape[0]]
 
 
 class OracleGraph:
@@ -110,6 +153,19 @@ class OracleGraph:
 
     def __exit__(self, *exc):
         self.close()
+
+    def triples(self, delta: int, dir: int = 0) -> np.ndarray:
+        """Sorted (x, y, w) rows of the all-existential query (Definition 1.2)."""
+        i32 = ctypes.c_int32
+        z = np.zeros(1, dtype=np.int32)
+        k = self._lib.oracle_triples(self._h, int(delta), int(dir), 0, _ptr(z, i32), _ptr(z, i32), _ptr(z, i32))
+        if k < 0:
+            raise ValueError("oracle: bad triple query")
+        tx = np.zeros(max(k, 1), dtype=np.int32)
+        ty = np.zeros(max(k, 1), dtype=np.int32)
+        tw = np.zeros(max(k, 1), dtype=np.int32)
+        self._lib.oracle_triples(self._h, int(delta), int(dir), k, _ptr(tx, i32), _ptr(ty, i32), _ptr(tw, i32))
+        return np.stack([tx[:k], ty[:k], tw[:k]], axis=1)
 
     def degree(self, u: int) -> int:
         return int(self._lib.oracle_degree(self._h, int(u)))
@@ -162,6 +218,8 @@ class OracleGraph:
                                            int(q.rho_den), int(q.quant), int(q.universe),
                                            _ptr(certs, ctypes.c_int64))
         res["certificates"] = certs[:nc].copy()
+        if getattr(q, "want_triples", False):
+            res["triples"] = self.triples(q.delta, q.dir)
         if getattr(q, "outer", 0):
             vout = np.zeros(max(self.n, 1), dtype=np.int32)
             cout = np.zeros(max(self.n, 1), dtype=np.int32)

@@ -33,7 +33,10 @@
  *      certificate; it is reported with max c_e over E_{x,y} and the number of
  *      certificates, sorted by (x, y). The certificates themselves are listed by
  *      input index.
- *   6. Vertex queries (Section 4, exists-forall-forall and exists-forall-exists): with the
+ *   6. Triples (Definition 1.2, all three quantifiers existential): (x, y, w) for every
+ *      directed pair with a temporal edge x -> y that forms a triangle with witness w,
+ *      sorted by (x, y, w).
+ *   7. Vertex queries (Section 4, exists-forall-forall and exists-forall-exists): with the
  *      pairs of step 5 as the set L, vertex u is a solution when the number of v with
  *      (u, v) in L is >= 1 and, for an outer rho1 = num1/den1, count * den1 >=
  *      num1 * |N(u)|. The inner query is the pair query itself (forall_rho2 for
@@ -246,6 +249,42 @@ static int32_t edge_count(const oracle_graph *g, int64_t e, int64_t delta, int d
     }
     if (common) *common = cn;
     return c;
+}
+
+/* Definition 1.2 with three existential quantifiers: the triples (x, y, w) for which
+ * some temporal edge x -> y forms a delta-temporal triangle with witness w (Section 2,
+ * the same witness test as c_e), sorted by (x, y, w). Writes the first cap triples and
+ * returns how many there are, or -1 on a bad argument. */
+int64_t oracle_triples(void *p, int64_t delta, int dir, int64_t cap, int32_t *tx, int32_t *ty, int32_t *tw) {
+    oracle_graph *g = (oracle_graph *)p;
+    if (!g || delta < 0 || dir < 0 || dir > 2 || cap < 0) return -1;
+    buf64 A = {0}, B = {0};
+    int64_t k = 0;
+    for (int64_t b = 0; b < g->m_kept;) {
+        int32_t x = g->s_src[b], y = g->s_dst[b];
+        int64_t e = b;
+        while (e < g->m_kept && g->s_src[e] == x && g->s_dst[e] == y) e++;
+        int64_t i = g->nbr_ptr[x], ie = g->nbr_ptr[x + 1];
+        int64_t j = g->nbr_ptr[y], je = g->nbr_ptr[y + 1];
+        while (i < ie && j < je) {  /* w in N(x) cap N(y), ascending */
+            if (g->nbr[i] < g->nbr[j]) { i++; continue; }
+            if (g->nbr[i] > g->nbr[j]) { j++; continue; }
+            int32_t w = g->nbr[i];
+            i++; j++;
+            witness_list(g, dir, x, w, &A);
+            witness_list(g, dir, y, w, &B);
+            int hit = 0;
+            for (int64_t q = b; q < e && !hit; q++) hit = witness_greedy(&A, &B, g->s_t[q], delta);
+            if (hit) {
+                if (k < cap) { tx[k] = x; ty[k] = y; tw[k] = w; }
+                k++;
+            }
+        }
+        b = e;
+    }
+    free(A.v);
+    free(B.v);
+    return k;
 }
 
 /* c_e for the input edges idx[0..n_idx) (all m edges when idx is NULL), into out[],

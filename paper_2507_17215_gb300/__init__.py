@@ -56,7 +56,8 @@ class folty_query_params(Structure):
     _fields_ = [("delta", c_int64), ("rho_num", c_uint32), ("rho_den", c_uint32),
                 ("quant", c_uint8), ("dir", c_uint8), ("universe", c_uint8),
                 ("want_edge_counts", c_uint8), ("outer", c_uint8), ("want_certificates", c_uint8),
-                ("reserved", c_uint8 * 2), ("outer_rho_num", c_uint32), ("outer_rho_den", c_uint32)]
+                ("want_triples", c_uint8), ("reserved", c_uint8), ("outer_rho_num", c_uint32),
+                ("outer_rho_den", c_uint32)]
 
 
 class folty_result(Structure):
@@ -64,7 +65,8 @@ class folty_result(Structure):
                 ("v", POINTER(c_int32)), ("count", POINTER(c_int32)), ("ncert", POINTER(c_int32)),
                 ("n_cert_edges", c_int64), ("m", c_int64), ("edge_count", POINTER(c_int32)),
                 ("n_vertices", c_int64), ("vertex", POINTER(c_int32)), ("vertex_count", POINTER(c_int32)),
-                ("certificate", POINTER(c_int64))]
+                ("certificate", POINTER(c_int64)), ("n_triples", c_int64), ("triple_x", POINTER(c_int32)),
+                ("triple_y", POINTER(c_int32)), ("triple_w", POINTER(c_int32))]
 
 
 class folty_graph_info(Structure):
@@ -243,6 +245,7 @@ def _params(q) -> folty_query_params:
     p.want_edge_counts = int(bool(getattr(q, "want_edge_counts", 0)))
     p.outer = int(getattr(q, "outer", 0))
     p.want_certificates = int(bool(getattr(q, "want_certificates", 0)))
+    p.want_triples = int(bool(getattr(q, "want_triples", 0)))
     p.outer_rho_num = int(getattr(q, "outer_rho_num", 1))
     p.outer_rho_den = int(getattr(q, "outer_rho_den", 2))
     return p
@@ -270,6 +273,11 @@ def _take_result(r: folty_result) -> Dict[str, object]:
     if r.certificate:
         out["certificates"] = (np.ctypeslib.as_array(r.certificate, shape=(nc,)).copy() if nc > 0
                                else np.zeros(0, dtype=np.int64))
+    nt = int(r.n_triples)
+    if r.triple_x:
+        cols = [np.ctypeslib.as_array(getattr(r, f), shape=(nt,)).copy() if nt > 0 else np.zeros(0, np.int32)
+                for f in ("triple_x", "triple_y", "triple_w")]
+        out["triples"] = np.stack(cols, axis=1)
     lib.folty_free(ctypes.byref(r))
     return out
 

@@ -200,15 +200,27 @@ void fill_result_host(folty_result* out, int64_t n_pairs, int64_t m, bool want_e
     }
 }
 
-static void free_result(folty_result* r) {
+void fill_result_triples(folty_result* out, int64_t n) {
+    out->n_triples = n;
+    int32_t* block = (int32_t*)std::malloc(sizeof(int32_t) * 3 * (size_t)(n > 0 ? n : 1));
+    if (!block) fail(FOLTY_ENOMEM, "host allocation of the result failed");
+    out->triple_x = block;
+    out->triple_y = block + n;
+    out->triple_w = block + 2 * n;
+}
+
+void release_result(folty_result* r) {
     std::free(r->u);
     std::free(r->edge_count);
     std::free(r->vertex);
     std::free(r->certificate);
+    std::free(r->triple_x);
     r->u = r->v = r->count = r->ncert = r->edge_count = nullptr;
     r->vertex = r->vertex_count = nullptr;
     r->certificate = nullptr;
+    r->triple_x = r->triple_y = r->triple_w = nullptr;
     r->n_pairs = 0;
+    r->n_triples = 0;
     r->tag = FREED_TAG;
 }
 
@@ -392,7 +404,7 @@ folty_status folty_query_batch(folty_graph* g, const folty_query_params* qs, int
             prof.commit();
         } catch (...) {
             for (int i = 0; i < nq; i++)
-                if (outs[i].tag == RESULT_TAG) free_result(&outs[i]);
+                if (outs[i].tag == RESULT_TAG) release_result(&outs[i]);
             throw;
         }
     });
@@ -403,7 +415,7 @@ void folty_free(void* obj) {
     uint64_t tag;
     std::memcpy(&tag, obj, sizeof(tag));
     if (tag == GRAPH_TAG) free_graph((folty_graph*)obj);
-    else if (tag == RESULT_TAG) free_result((folty_result*)obj);
+    else if (tag == RESULT_TAG) release_result((folty_result*)obj);
 }
 
 const char* folty_last_error(void) { return t_last_error.c_str(); }

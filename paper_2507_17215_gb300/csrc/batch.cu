@@ -71,19 +71,28 @@ int64_t batch_footprint(const folty_graph* g, const folty_query_params* qs, int 
     if (certs) per_q += 16 * (g->m + 1);
     if (outer) per_q += 14 * ((int64_t)g->n + 1);
     const int64_t group = std::min<int64_t>(nq, READBACK_MAX / 4);
+    // a triple query runs alone: role flags and scan (9 B per role), and up to one triple
+    // per role through the two sorts (44 B each), on top of its own counters
+    bool triples = false;
+    for (int i = 0; i < nq; i++) triples = triples || qs[i].want_triples;
+    const int64_t tri_part = triples ? 53 * 6 * g->ntri + 4 * g->m_kept + per_q : 0;
     if (bins_part) *bins_part = bins;
-    return bins + group * per_q;
+    return std::max(bins + group * per_q, tri_part);
 }
 
 void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty_result* outs,
                      cudaStream_t s, int64_t bin_budget) {
     const int64_t mk = g->m_kept;
     const int64_t P = g->info.probes;
+    // a query that also wants the all-existential triples needs its own probe pass (the
+    // role flags are per window, not per bin)
+    for (int i = 0; i < nq; i++)
+        if (qs[i].want_triples) run_query(g, qs[i], &outs[i], s);
     // group the queries by direction variant; distinct sorted deltas per group
     for (int dir = 0; dir <= FOLTY_DIR_EITHER; dir++) {
         std::vector<int> members;
         for (int i = 0; i < nq; i++)
-            if (qs[i].dir == dir) members.push_back(i);
+            if (qs[i].dir == dir && !qs[i].want_triples) members.push_back(i);
         if (members.empty()) continue;
         std::vector<int64_t> D;
         for (int i : members) D.push_back(qs[i].delta);

@@ -250,8 +250,9 @@ void launch_probe(folty_graph* g, int64_t delta, int dir, int32_t* cnt, cudaStre
 // Window probes of the roles that can hit (live.cu): mode 0 counts hits at delta into
 // cnt; mode 1 bins gaps <= delta into bins[k][m_kept] against the k sorted bounds
 // `deltas` (in the timestamp store's type).
+// rflag (mode 0, may be null): byte 6 * triangle + role set to 1 when the role has a hit.
 void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t* cnt, int32_t* bins, int k,
-                       const void* deltas, cudaStream_t s);
+                       const void* deltas, cudaStream_t s, uint8_t* rflag = nullptr);
 void build_role_summary(folty_graph* g, cudaStream_t s);
 // The same pass with the counters in a file-scope device array (noalloc.cu).
 void edge_counts_noalloc(folty_graph* g, int64_t delta, int dir, int32_t* edge_count, cudaStream_t s);
@@ -266,6 +267,10 @@ void finish_queries(folty_graph* g, const folty_query_params* const* qs, const i
 
 void fill_result_host(folty_result* out, int64_t n_pairs, int64_t m, bool want_edges, int64_t n_vertices,
                       bool want_vertices, int64_t n_certs, bool want_certs);
+// Host arrays for n all-existential triples in a filled result.
+void fill_result_triples(folty_result* out, int64_t n);
+// Frees a result's host arrays and marks it freed.
+void release_result(folty_result* r);
 
 // ------------------------------------------------------------------ device helpers
 

@@ -201,6 +201,7 @@ struct LiveArgs {
     int64_t mk;
     int k;             // MODE 1: number of bins
     unsigned long long* prof;  // model bytes of the kept roles (may be null)
+    uint8_t* rflag;    // MODE 0, may be null: 6 * triangle + role flags of roles with a hit
 };
 
 // MODE 0: cnt[pos] += hit at window delta. MODE 1: bin the gap t3 - t (<= delta, the
@@ -288,6 +289,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS*
             if (gap > delta) continue;
             if (MODE == 0) {
                 atomicAdd(&a.cnt[pos], 1);
+                if (a.rflag) a.rflag[6 * (int64_t)a.L[t0 + j] + r] = 1;
             } else {
                 const int jb = lower_bound_ts<TS>(sD, 0, a.k, gap);
                 atomicAdd(&a.bins[(int64_t)jb * a.mk + pos], 1);
@@ -326,7 +328,7 @@ static void launch_live_t(const folty_graph* g, int dir, const LiveArgs& la, uns
 // Kept roles for delta (the largest window of the pass), then the probe kernel.
 // mode 0: counts into cnt; mode 1: bins (deltas = k sorted bounds in the store's type).
 void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t* cnt, int32_t* bins, int k,
-                       const void* deltas, cudaStream_t s) {
+                       const void* deltas, cudaStream_t s, uint8_t* rflag) {
     const int64_t ntri = g->ntri;
     if (ntri == 0 || g->info.probes == 0) return;
     const int T = 256;
@@ -354,7 +356,7 @@ void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t
     exclusive_scan(sc, cost, lcost, ntri);
     FOLTY_LAUNCH(k_live_compact, grid_for(ntri + 1, T), T, 0, s, flag, lpos, lcost, mask, ntri, L, loff, lmask);
     FOLTY_LAUNCH(k_live_tiles, grid_for(max_tiles + 1, T), T, 0, s, loff, lpos + ntri, lcost + ntri, max_tiles, ltile);
-    LiveArgs la{g->tri, g->seg, L, loff, lmask, ltile, lcost + ntri, cnt, bins, g->m_kept, k, prof};
+    LiveArgs la{g->tri, g->seg, L, loff, lmask, ltile, lcost + ntri, cnt, bins, g->m_kept, k, prof, rflag};
     int per_sm = 0;
     if (g->ts32) FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<uint32_t, 0, 0>, PB_THREADS, 0));
     else FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<int64_t, 0, 0>, PB_THREADS, 0));

@@ -11,6 +11,9 @@
 #include <climits>
 
 #include "internal.cuh"
+
+#include <cooperative_groups.h>
+namespace cg = cooperative_groups;
 #include "probe.cuh"
 
 namespace folty {
@@ -213,6 +216,7 @@ enum {
     C_TAIL_R = 17,
     C_TAIL_AC = 18,
     C_TAIL_N = 19,
+    C_RM = 20,  // 2 slots by level parity: vertices removed after the level's compaction
     C_SLOTS = 24
 };
 
@@ -288,7 +292,16 @@ __device__ __forceinline__ void warp_append(bool pred, int32_t v, int32_t* out, 
     }
 }
 
+// Adds the number of lanes with pred set to *counter (one atomic per warp). The whole
+// warp must call it.
+__device__ __forceinline__ void warp_count(bool pred, int* counter) {
+    const unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (m && (threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(counter, __popc(m));
+}
+
 constexpr int PEEL_THREADS = 1024;
+constexpr int PEEL_SHORT = 32;      // rows up to this length are walked by one thread,
+constexpr int PEEL_CHUNK = 8;       // PEEL_CHUNK entries at a time
 constexpr int PEEL_HEAVY = 128;     // vertices above this degree go to the heavy frontier
 constexpr int PEEL_PIECE = PEEL_THREADS;  // adjacency entries per heavy piece
 
@@ -315,7 +328,7 @@ __device__ __forceinline__ void frontier_append(const PeelArgs& a, bool in, int3
 // crosses k + 1 -> k joins round r + 1. A vertex that already left never crosses again
 // (its degree was <= k when it left and only falls), so no liveness test is needed.
 // The whole warp must call it.
-__device__ __forceinline__ void peel_neighbour(const PeelArgs& a, bool valid, int32_t j, int k, int r) {
+__device__ __forceinline__ void peel_neighbour(const PeelArgs& a, bool valid, int32_t j, int k, int r, int* rm) {
     bool cross = false;
     int32_t v = 0, b = 0, e = 0;
     if (valid) {
@@ -329,7 +342,22 @@ __device__ __forceinline__ void peel_neighbour(const PeelArgs& a, bool valid, in
             e = a.rowptr[v + 1];
         }
     }
+    warp_count(cross, rm);
     frontier_append(a, cross, v, b, e, r + 1);
+}
+
+// Vertex v (valid when cross) crossed k + 1 -> k in round r: it leaves in round r + 1.
+// The whole warp must call it.
+__device__ __forceinline__ void peel_crossing(const PeelArgs& a, bool cross, int32_t v, int k, int r, int* rm) {
+    warp_count(cross, rm);
+    int32_t rb = 0, re = 0;
+    if (cross) {
+        a.rnd[v] = r + 1;
+        a.core[v] = k;
+        rb = a.rowptr[v];
+        re = a.rowptr[v + 1];
+    }
+    frontier_append(a, cross, v, rb, re, r + 1);
 }
 
 // Parallel Matula-Beck peeling. Level k = smallest remaining degree; within a level,
@@ -359,9 +387,10 @@ __global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
     int k = -1, r = 0, lvl = 0, ac = 0, rounds = 0;
     int nalive = a.n;
     while (true) {
-        // few vertices left: hand the rest to the single-block tail (all blocks agree,
-        // nalive was read after the same barrier)
-        if (nalive <= a.tail_n) {
+        // few vertices left: hand the rest to the cluster tail (all blocks agree: nalive
+        // and the removals since the last compaction were read after the same barrier)
+        const int removed = lvl > 0 ? *(volatile int*)&ctl[C_RM + ((lvl - 1) & 1)] : 0;
+        if (nalive - removed <= a.tail_n) {
             if (gtid == 0) {
                 ctl[C_TAIL] = 1;
                 ctl[C_TAIL_K] = k;
@@ -377,6 +406,7 @@ __global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
         if (gtid == 0) {
             ctl[C_MIN + ((lvl + 1) & 1)] = INT_MAX;
             ctl[C_ACNT + ((lvl + 1) & 1)] = 0;
+            ctl[C_RM + (lvl & 1)] = 0;
             ctl[C_FCNT + (r + 2) % 3] = 0;
             ctl[C_HCNT + (r + 2) % 3] = 0;
         }
@@ -445,6 +475,7 @@ __global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
                         a.core[v] = kj;
                     }
                 }
+                warp_count(in, &ctl[C_RM + (lvl & 1)]);
                 frontier_append(a, in, v, rb, re, r + 1);
             }
             k = kj;
@@ -462,38 +493,47 @@ __global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
                 ctl[C_FCNT + (r + 2) % 3] = 0;
                 ctl[C_HCNT + (r + 2) % 3] = 0;
             }
-            // light vertices: one warp each, two per pass; every row entry of both is
-            // loaded, then every decrement issued, before the first result is used
+            // light vertices: a row of at most PEEL_SHORT entries is walked by one thread,
+            // PEEL_CHUNK entries at a time, a longer one (up to PEEL_HEAVY) by the whole warp
+            // in turn; every load of a chunk is issued, then every decrement, before a result
+            // is used
             const int32_t* F = (r & 1) ? a.fr[1] : a.fr[0];
-            for (int64_t i0 = gwarp; i0 < fsz; i0 += 2 * nwarps) {
-                constexpr int Q = PEEL_HEAVY / 32;
-                const int64_t i1 = i0 + nwarps;
-                const bool two = i1 < fsz;
-                const int32_t u0 = __ldcg(&F[i0]);
-                const int32_t u1 = two ? __ldcg(&F[i1]) : 0;
-                const int32_t b0 = a.rowptr[u0], e0 = a.rowptr[u0 + 1];
-                const int32_t b1 = two ? a.rowptr[u1] : 0, e1 = two ? a.rowptr[u1 + 1] : 0;
-                int32_t v[2 * Q];
-                int old[2 * Q];
+            for (int64_t i0 = gwarp * 32; i0 < fsz; i0 += nwarps * 32) {
+                const int64_t i = i0 + lane;
+                const bool have = i < fsz;
+                const int32_t u = have ? __ldcg(&F[i]) : 0;
+                const int32_t b = have ? a.rowptr[u] : 0, e = have ? a.rowptr[u + 1] : 0;
+                const bool shortrow = have && e - b <= PEEL_SHORT;
+                const int chunks = __reduce_max_sync(0xffffffffu, shortrow ? (e - b + PEEL_CHUNK - 1) / PEEL_CHUNK : 0);
+                for (int c = 0; c < chunks; c++) {  // warp-uniform trip count
+                    const int32_t j0 = b + c * PEEL_CHUNK;
+                    int32_t v[PEEL_CHUNK];
+                    int old[PEEL_CHUNK];
 #pragma unroll
-                for (int q = 0; q < Q; q++) {
-                    const int32_t j0 = b0 + q * 32 + lane, j1 = b1 + q * 32 + lane;
-                    v[q] = (j0 < e0) ? a.adj[j0] : -1;
-                    v[Q + q] = (j1 < e1) ? a.adj[j1] : -1;
+                    for (int t = 0; t < PEEL_CHUNK; t++) v[t] = (shortrow && j0 + t < e) ? a.adj[j0 + t] : -1;
+#pragma unroll
+                    for (int t = 0; t < PEEL_CHUNK; t++) old[t] = (v[t] >= 0) ? atomicSub(&a.deg[v[t]], 1) : 0;
+#pragma unroll
+                    for (int t = 0; t < PEEL_CHUNK; t++)
+                        peel_crossing(a, v[t] >= 0 && old[t] == k + 1, v[t], k, r, &ctl[C_RM + (lvl & 1)]);
                 }
+                unsigned mm = __ballot_sync(0xffffffffu, have && !shortrow);
+                while (mm) {
+                    const int src = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    const int32_t bb = __shfl_sync(0xffffffffu, b, src), ee = __shfl_sync(0xffffffffu, e, src);
+                    constexpr int Q = PEEL_HEAVY / 32;
+                    int32_t v[Q];
+                    int old[Q];
 #pragma unroll
-                for (int q = 0; q < 2 * Q; q++) old[q] = (v[q] >= 0) ? atomicSub(&a.deg[v[q]], 1) : 0;
-#pragma unroll
-                for (int q = 0; q < 2 * Q; q++) {
-                    const bool cross = v[q] >= 0 && old[q] == k + 1;
-                    int32_t rb = 0, re = 0;
-                    if (cross) {
-                        a.rnd[v[q]] = r + 1;
-                        a.core[v[q]] = k;
-                        rb = a.rowptr[v[q]];
-                        re = a.rowptr[v[q] + 1];
+                    for (int q = 0; q < Q; q++) {
+                        const int32_t j = bb + q * 32 + lane;
+                        v[q] = (j < ee) ? a.adj[j] : -1;
                     }
-                    frontier_append(a, cross, v[q], rb, re, r + 1);
+#pragma unroll
+                    for (int q = 0; q < Q; q++) old[q] = (v[q] >= 0) ? atomicSub(&a.deg[v[q]], 1) : 0;
+#pragma unroll
+                    for (int q = 0; q < Q; q++) peel_crossing(a, v[q] >= 0 && old[q] == k + 1, v[q], k, r, &ctl[C_RM + (lvl & 1)]);
                 }
             }
             // heavy vertices: one block per piece of PEEL_PIECE adjacency entries
@@ -503,7 +543,7 @@ __global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
                 const int32_t u = (int32_t)(hp & 0xffffffffll);
                 const int32_t q = (int32_t)(hp >> 32);
                 const int32_t j = a.rowptr[u] + q * PEEL_PIECE + (int32_t)threadIdx.x;
-                peel_neighbour(a, j < a.rowptr[u + 1], j, k, r);
+                peel_neighbour(a, j < a.rowptr[u + 1], j, k, r, &ctl[C_RM + (lvl & 1)]);
             }
             if (!grid_barrier(ctl, a.timeout_ns)) return;
             r++;
@@ -519,22 +559,34 @@ __global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
 
 // ================================================================== A3 tail
 
-// The last few levels run in one block on the subgraph induced by the vertices still
-// alive, renumbered 0..NL-1 ("local" ids): degrees, liveness and frontiers live in
-// shared memory and a round ends with __syncthreads instead of a grid barrier.
+// The last levels run on one thread-block cluster, on the subgraph induced by the vertices
+// still alive, renumbered 0..NL-1 ("local" ids): degrees, row bounds and frontiers live
+// in the CTAs' shared memory (each CTA owns the local ids congruent to its rank) and a
+// round ends with one cluster barrier instead of a grid barrier.
 constexpr int TAIL_THREADS = 1024;
-constexpr int TAIL_MAX = 12288;  // local ids fit in int16
+constexpr int TAIL_OWN = 10240;  // local vertices owned per CTA: a C-CTA tail takes up to 10240 C
 
-// Local ids for the vertices of alive[0..nalive) that are still alive.
-__global__ void k_tail_select(const int32_t* __restrict__ alive, int nalive, const int32_t* __restrict__ rnd,
-                              int32_t* __restrict__ L, int32_t* __restrict__ gmap, int* __restrict__ nl) {
+// Local ids for the vertices of the grid kernel's alive list that are still alive (at
+// most cap; more would be an internal error, recorded in *err instead of written).
+// Nothing to do when the grid kernel finished the peeling itself (ctl[C_TAIL] == 0).
+__global__ void k_tail_select(const int32_t* __restrict__ alive0, const int32_t* __restrict__ alive1,
+                              const int* __restrict__ ctl, const int32_t* __restrict__ rnd, int cap,
+                              int32_t* __restrict__ L, int32_t* __restrict__ gmap, int* __restrict__ nl,
+                              int* __restrict__ err) {
+    if (ctl[C_TAIL] != 1) return;
+    const int nalive = ctl[C_TAIL_N];
+    const int32_t* __restrict__ alive = ctl[C_TAIL_AC] ? alive1 : alive0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalive;
          i += (int64_t)gridDim.x * blockDim.x) {
         int32_t v = alive[i];
         if (rnd[v] < 0) {
             int li = atomicAdd(nl, 1);
-            L[li] = v;
-            gmap[v] = li;
+            if (li < cap) {
+                L[li] = v;
+                gmap[v] = li;
+            } else {
+                atomicExch(err, 2);
+            }
         }
     }
 }
@@ -562,7 +614,7 @@ __global__ void k_tail_fill(const int32_t* __restrict__ L, const int32_t* __rest
                             const int32_t* __restrict__ rowptr, const int32_t* __restrict__ adj,
                             const int32_t* __restrict__ rnd, const int32_t* __restrict__ gmap,
                             const int32_t* __restrict__ lrow, const int32_t* __restrict__ ld,
-                            int32_t* __restrict__ fillc, int16_t* __restrict__ ladj, int* __restrict__ err) {
+                            int32_t* __restrict__ fillc, uint32_t* __restrict__ ladj, int* __restrict__ err) {
     const int64_t total = eoff[tn];
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -575,7 +627,7 @@ __global__ void k_tail_fill(const int32_t* __restrict__ L, const int32_t* __rest
         int32_t v = adj[rowptr[L[lo]] + (int32_t)(e - eoff[lo])];
         if (rnd[v] < 0) {
             int p = atomicAdd(&fillc[lo], 1);
-            if (p < ld[lo]) ladj[lrow[lo] + p] = (int16_t)gmap[v];
+            if (p < ld[lo]) ladj[lrow[lo] + p] = (uint32_t)gmap[v];
             else atomicExch(err, 3);  // more alive neighbours than the degree says
         }
     }
@@ -586,188 +638,301 @@ struct TailArgs {
     const int32_t* L;
     const int32_t* ld;
     const int32_t* lrow;
-    const int16_t* ladj;
+    const uint32_t* ladj;
     int32_t* rnd;
     int32_t* core;
     int* ctl;
 };
 
-constexpr int TAIL_LIGHT = 256;   // rows up to this length: one warp, all loads in flight at once
-constexpr int TAIL_HCAP = 1024;   // heavy-frontier capacity per round (overflow goes to the light list)
+constexpr int TAIL_SHORT = 32;   // rows up to this length: one thread, TAIL_CHUNK loads at a time
+constexpr int TAIL_CHUNK = 8;
+constexpr int TAIL_LIGHT = 256;  // rows up to this length: one warp, all loads in flight at once
+constexpr int TAIL_HCAP = 512;   // heavy vertices per CTA and round (more wait for the next pass)
 
-// Removes local vertex v at level k in round rr: global round and core number, and the
-// frontier of round rr (slot rr % 3 of the counters, buffer rr & 1).
-__device__ __forceinline__ void tail_remove(const TailArgs& a, const int32_t* sL, const int32_t* srow,
-                                            uint8_t* salive, int16_t* FL, int16_t* FH, int* cntL, int* cntH,
-                                            int v, int k, int rr) {
-    salive[v] = 0;
-    a.rnd[sL[v]] = rr;
-    a.core[sL[v]] = k;
-    if (srow[v + 1] - srow[v] > TAIL_LIGHT) {
-        const int h = atomicAdd(&cntH[rr % 3], 1);
-        if (h < TAIL_HCAP) {
-            FH[(rr & 1) * TAIL_HCAP + h] = (int16_t)v;
-            return;
+// Shared memory of one tail CTA of a C-CTA cluster. Local vertex v is owned by CTA v % C
+// at slot q = v / C; the owner keeps its degree, row bounds and global id, and the
+// frontier lists hold owned slots: a thread that drives a vertex's degree across k + 1 -> k
+// files it directly in the owner's next frontier through distributed shared memory.
+template <int C>
+struct TailShared {
+    static constexpr int OWN = TAIL_OWN;
+    int32_t odeg[OWN];
+    int32_t orb[OWN], ore[OWN];  // row [orb, ore) of ladj
+    int32_t oL[OWN];             // global id
+    uint16_t FL[2][OWN];         // frontier by round parity (owned slots)
+    uint16_t FH[TAIL_HCAP];      // heavy rows of the current round
+    int cntL[3], cntH[2], smin[2];
+    int bc[2][2];                // cluster-wide values, published by tail_gather
+};
+
+// Neighbours vv[0..N) (negative: none) lose one degree each in round r at level k: all N
+// decrements are issued before any result is used, then every k + 1 -> k crossing files
+// its vertex in the owner's frontier of round r + 1.
+template <int C, int N>
+__device__ __forceinline__ void tail_decrement(TailShared<C>& sh, cg::cluster_group& cl, const int (&vv)[N], int k,
+                                               int r) {
+    int old[N];
+#pragma unroll
+    for (int t = 0; t < N; t++)
+        old[t] = (vv[t] >= 0) ? atomicSub(&cl.map_shared_rank(sh.odeg, vv[t] % C)[vv[t] / C], 1) : 0;
+#pragma unroll
+    for (int t = 0; t < N; t++) {
+        if (vv[t] >= 0 && old[t] == k + 1) {
+            TailShared<C>* p = cl.map_shared_rank(&sh, vv[t] % C);
+            const int at = atomicAdd(&p->cntL[(r + 1) % 3], 1);
+            p->FL[(r + 1) & 1][at] = (uint16_t)(vv[t] / C);
         }
     }
-    FL[(rr & 1) * TAIL_MAX + atomicAdd(&cntL[rr % 3], 1)] = (int16_t)v;
 }
 
-// tail_remove for the lanes with rem set, with one counter atomic per warp for the light
-// ones. The whole warp must call it.
-__device__ __forceinline__ void tail_remove_warp(const TailArgs& a, const int32_t* sL, const int32_t* srow,
-                                                 uint8_t* salive, int16_t* FL, int16_t* FH, int* cntL, int* cntH,
-                                                 bool rem, int v, int k, int rr) {
-    bool light = rem;
-    if (rem) {
-        salive[v] = 0;
-        a.rnd[sL[v]] = rr;
-        a.core[sL[v]] = k;
-        if (srow[v + 1] - srow[v] > TAIL_LIGHT) {
-            const int h = atomicAdd(&cntH[rr % 3], 1);
-            if (h < TAIL_HCAP) {
-                FH[(rr & 1) * TAIL_HCAP + h] = (int16_t)v;
-                light = false;
-            }
+// Cluster-wide frontier size of round t and minimum of the level minima smin[p]: warp 0
+// reads every CTA's values (lane c reads CTA c) and publishes them in this CTA's shared
+// memory slot s (callers alternate s, so that a slot is rewritten only after a barrier
+// that follows every read of it). The whole CTA must call it; every CTA gets the same
+// values when no CTA appends to slot t % 3 or lowers smin[p] meanwhile.
+template <int C>
+__device__ __forceinline__ int2 tail_gather(TailShared<C>& sh, cg::cluster_group& cl, int t, int p, int s) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int v = 0, m = INT_MAX;
+        if (lane < C) {
+            const TailShared<C>* q = cl.map_shared_rank(&sh, lane);
+            v = q->cntL[t % 3];
+            m = q->smin[p];
+        }
+        v = __reduce_add_sync(0xffffffffu, v);
+        m = __reduce_min_sync(0xffffffffu, m);
+        if (lane == 0) {
+            sh.bc[s][0] = v;
+            sh.bc[s][1] = m;
         }
     }
-    const unsigned m = __ballot_sync(0xffffffffu, light);
-    if (!m) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(m) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(&cntL[rr % 3], __popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (light) FL[(rr & 1) * TAIL_MAX + base + __popc(m & ((1u << lane) - 1u))] = (int16_t)v;
+    __syncthreads();
+    return make_int2(sh.bc[s][0], sh.bc[s][1]);
 }
 
 // The same peeling as k_peel (levels, rounds, k + 1 -> k crossings), on the local
 // subgraph, continuing the level k and round r where the grid kernel stopped.
 //
-// One __syncthreads per round. Frontier counters rotate over three slots by round
-// number (round r reads slot r % 3, appends to (r + 1) % 3, and thread 0 clears
-// (r + 2) % 3, which nobody reads or writes during round r); frontier buffers alternate
-// by round parity. A light vertex (row <= TAIL_LIGHT) takes one warp that issues all of
-// its row's loads before the first decrement; a heavy one takes the whole block.
+// A vertex is alive at a level start exactly when its degree exceeds the finished level
+// k (a removed vertex had degree <= k when it left, and degrees only fall). Frontier
+// counters rotate over three rounds (round r reads slot r % 3 of every CTA, crossings
+// append to (r + 1) % 3, and each CTA clears its own (r + 2) % 3, which no CTA touches in
+// round r); the level minima alternate by level parity. Every decision that ends a loop
+// is taken by all CTAs from the same values read between the same two cluster barriers,
+// so the CTAs always meet at the same barrier. In a round, the owner of each frontier
+// vertex writes its round and core number and walks its row: its own thread for a short
+// row, its warp for a medium one, the whole CTA for a heavy one, every load of a walk in
+// flight before its first decrement.
+template <int C>
 __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
+    using Sh = TailShared<C>;
+    constexpr int OWN = Sh::OWN;
+    cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem[];
-    int32_t* sdeg = (int32_t*)smem;                     // TAIL_MAX
-    int32_t* srow = sdeg + TAIL_MAX;                    // TAIL_MAX + 1 (+ 3 pad)
-    int32_t* sL = srow + TAIL_MAX + 4;                  // TAIL_MAX
-    int16_t* FL = (int16_t*)(sL + TAIL_MAX);            // 2 x TAIL_MAX
-    int16_t* FH = FL + 2 * TAIL_MAX;                    // 2 x TAIL_HCAP
-    uint8_t* salive = (uint8_t*)(FH + 2 * TAIL_HCAP);   // TAIL_MAX
-    __shared__ int cntL[3], cntH[3], s_min;
+    Sh& sh = *reinterpret_cast<Sh*>(smem);
+    if (a.ctl[C_TAIL] != 1) return;  // the grid kernel finished (every CTA reads the same value)
+    const int rank = (int)cl.block_rank();
     const int nl = *a.nl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int NW = TAIL_THREADS / 32;
-    for (int i = tid; i < nl; i += TAIL_THREADS) {
-        sdeg[i] = a.ld[i];
-        srow[i] = a.lrow[i];
-        sL[i] = a.L[i];
-        salive[i] = 1;
+    for (int q = tid; q < OWN; q += TAIL_THREADS) {
+        const int v = q * C + rank;
+        const bool in = v < nl;
+        sh.odeg[q] = in ? a.ld[v] : 0;
+        sh.orb[q] = in ? a.lrow[v] : 0;
+        sh.ore[q] = in ? a.lrow[v + 1] : 0;
+        sh.oL[q] = in ? a.L[v] : 0;
     }
-    if (tid == 0) srow[nl] = a.lrow[nl];
-    if (tid < 3) {
-        cntL[tid] = 0;
-        cntH[tid] = 0;
+    if (tid < 3) sh.cntL[tid] = 0;
+    if (tid < 2) {
+        sh.cntH[tid] = 0;
+        sh.smin[tid] = INT_MAX;
     }
-    int k = a.ctl[C_TAIL_K], r = a.ctl[C_TAIL_R], rounds = a.ctl[C_ROUNDS];
-    __syncthreads();
+    int k = a.ctl[C_TAIL_K], r = a.ctl[C_TAIL_R], rounds = a.ctl[C_ROUNDS], lvl = 0, gs = 0;
+    cl.sync();
     while (true) {
-        // ---- level start: vertices of degree <= k + 1 form the frontier of round r + 1
-        // (the scan takes whole warps: the minimum and the light appends are aggregated
-        // per warp, so the shared counters see one atomic per warp, not one per vertex)
+        // ---- level start: owned vertices of degree k + 1 join round r + 1
         if (tid == 0) {
-            s_min = INT_MAX;
-            cntL[(r + 2) % 3] = 0;
-            cntH[(r + 2) % 3] = 0;
+            sh.cntL[(r + 2) % 3] = 0;
+            sh.cntH[(r + 1) & 1] = 0;
+            sh.smin[(lvl + 1) & 1] = INT_MAX;
         }
         int kk = k + 1;
         int lmin = INT_MAX;
-        for (int i0 = 0; i0 < nl; i0 += TAIL_THREADS) {
-            const int i = i0 + tid;
+        for (int q0 = 0; q0 < OWN; q0 += TAIL_THREADS) {
+            const int q = q0 + tid;
             bool rem = false;
-            if (i < nl && salive[i]) {
-                const int d = sdeg[i];
-                if (d <= kk) rem = true;
-                else lmin = min(lmin, d);
+            if (q < OWN && q * C + rank < nl) {
+                const int d = sh.odeg[q];
+                if (d > k) {
+                    if (d <= kk) rem = true;
+                    else lmin = min(lmin, d);
+                }
             }
-            tail_remove_warp(a, sL, srow, salive, FL, FH, cntL, cntH, rem, i, kk, r + 1);
+            const unsigned m = __ballot_sync(0xffffffffu, rem);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(&sh.cntL[(r + 1) % 3], __popc(m));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (rem) sh.FL[(r + 1) & 1][base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)q;
+            }
         }
         lmin = __reduce_min_sync(0xffffffffu, lmin);
-        if (lane == 0 && lmin != INT_MAX) atomicMin(&s_min, lmin);
-        __syncthreads();
-        if (cntL[(r + 1) % 3] + cntH[(r + 1) % 3] == 0) {
-            if (s_min == INT_MAX) break;  // nothing left
-            kk = s_min;                   // jump to the smallest remaining degree
-            for (int i0 = 0; i0 < nl; i0 += TAIL_THREADS) {
-                const int i = i0 + tid;
-                const bool rem = i < nl && salive[i] && sdeg[i] <= kk;
-                tail_remove_warp(a, sL, srow, salive, FL, FH, cntL, cntH, rem, i, kk, r + 1);
+        if (lane == 0 && lmin != INT_MAX) atomicMin(&sh.smin[lvl & 1], lmin);
+        cl.sync();
+        const int2 g = tail_gather(sh, cl, r + 1, lvl & 1, gs++ & 1);
+        int total = g.x;
+        if (total == 0) {
+            if (g.y == INT_MAX) break;  // nothing left anywhere
+            kk = g.y;                   // jump to the smallest remaining degree
+            cl.sync();                  // every CTA has read the empty totals before appends resume
+            for (int q0 = 0; q0 < OWN; q0 += TAIL_THREADS) {
+                const int q = q0 + tid;
+                bool rem = false;
+                if (q < OWN && q * C + rank < nl) {
+                    const int d = sh.odeg[q];
+                    rem = d > k && d <= kk;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, rem);
+                if (m) {
+                    const int leader = __ffs(m) - 1;
+                    int base = 0;
+                    if (lane == leader) base = atomicAdd(&sh.cntL[(r + 1) % 3], __popc(m));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    if (rem) sh.FL[(r + 1) & 1][base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)q;
+                }
             }
-            __syncthreads();
+            cl.sync();
+            total = 1;  // some vertex has the minimum degree: the jump frontier is not empty
         }
         k = kk;
         r += 1;
         // ---- rounds at level k
-        while (true) {
-            const int nL = cntL[r % 3];
-            const int nH = min(cntH[r % 3], TAIL_HCAP);
-            if (nL + nH == 0) break;
+        while (total > 0) {
+            const int nL = sh.cntL[r % 3];
             if (tid == 0) {
-                cntL[(r + 2) % 3] = 0;
-                cntH[(r + 2) % 3] = 0;
+                sh.cntL[(r + 2) % 3] = 0;
+                sh.cntH[(r + 1) & 1] = 0;  // read in round r + 1, after this round's barriers
             }
-            const int16_t* fl = FL + (r & 1) * TAIL_MAX;
-            const int16_t* fh = FH + (r & 1) * TAIL_HCAP;
-            for (int i = warp; i < nL; i += NW) {
-                const int u = fl[i];
-                const int b = srow[u], e = srow[u + 1];
-                for (int j0 = b; j0 < e; j0 += TAIL_LIGHT) {
-                    int vv[TAIL_LIGHT / 32];
-#pragma unroll
-                    for (int q = 0; q < TAIL_LIGHT / 32; q++) {
-                        const int j = j0 + q * 32 + lane;
-                        vv[q] = (j < e) ? (int)a.ladj[j] : -1;
+            // one pass, up to 32 frontier vertices per warp, dealt round-robin over the warps
+            // (a small frontier spreads one vertex per warp): round and core number; a short
+            // row is walked by its own lane, a medium one by the whole warp in turn, and a
+            // heavy one is left to the whole CTA below
+            const uint16_t* fl = sh.FL[r & 1];
+            constexpr int NW = TAIL_THREADS / 32;
+            for (int i0 = warp; i0 - warp < nL; i0 += TAIL_THREADS) {
+                const int i = i0 + lane * NW;
+                const bool have = i < nL;
+                const int q = have ? fl[i] : 0;
+                const int b = have ? sh.orb[q] : 0, e = have ? sh.ore[q] : 0;
+                if (have) {
+                    a.rnd[sh.oL[q]] = r;
+                    a.core[sh.oL[q]] = k;
+                }
+                const bool shortrow = have && e - b <= TAIL_SHORT;
+                bool medium = have && !shortrow;
+                if (have && e - b > TAIL_LIGHT) {
+                    const int h = atomicAdd(&sh.cntH[r & 1], 1);
+                    if (h < TAIL_HCAP) {
+                        sh.FH[h] = (uint16_t)q;
+                        medium = false;
                     }
+                }
+                if (shortrow) {
+                    for (int j0 = b; j0 < e; j0 += TAIL_CHUNK) {
+                        int vv[TAIL_CHUNK];
 #pragma unroll
-                    for (int q = 0; q < TAIL_LIGHT / 32; q++) {
-                        if (vv[q] >= 0 && atomicSub(&sdeg[vv[q]], 1) == k + 1)
-                            tail_remove(a, sL, srow, salive, FL, FH, cntL, cntH, vv[q], k, r + 1);
+                        for (int t = 0; t < TAIL_CHUNK; t++) vv[t] = (j0 + t < e) ? (int)a.ladj[j0 + t] : -1;
+                        tail_decrement<C>(sh, cl, vv, k, r);
+                    }
+                }
+                unsigned mm = __ballot_sync(0xffffffffu, medium);
+                while (mm) {
+                    const int src = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    const int bb = __shfl_sync(0xffffffffu, b, src), ee = __shfl_sync(0xffffffffu, e, src);
+                    for (int j0 = bb; j0 < ee; j0 += TAIL_LIGHT) {
+                        int vv[TAIL_LIGHT / 32];
+#pragma unroll
+                        for (int t = 0; t < TAIL_LIGHT / 32; t++) {
+                            const int j = j0 + t * 32 + lane;
+                            vv[t] = (j < ee) ? (int)a.ladj[j] : -1;
+                        }
+                        tail_decrement<C>(sh, cl, vv, k, r);
                     }
                 }
             }
+            __syncthreads();  // this round's heavy list is complete
+            // the whole CTA per heavy row
+            const int nH = min(sh.cntH[r & 1], TAIL_HCAP);
             for (int h = 0; h < nH; h++) {
-                const int u = fh[h];
-                const int b = srow[u], e = srow[u + 1];
+                const int q = sh.FH[h];
+                const int b = sh.orb[q], e = sh.ore[q];
                 for (int j0 = b; j0 < e; j0 += 4 * TAIL_THREADS) {
                     int vv[4];
 #pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        const int j = j0 + q * TAIL_THREADS + tid;
-                        vv[q] = (j < e) ? (int)a.ladj[j] : -1;
+                    for (int t = 0; t < 4; t++) {
+                        const int j = j0 + t * TAIL_THREADS + tid;
+                        vv[t] = (j < e) ? (int)a.ladj[j] : -1;
                     }
-#pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        if (vv[q] >= 0 && atomicSub(&sdeg[vv[q]], 1) == k + 1)
-                            tail_remove(a, sL, srow, salive, FL, FH, cntL, cntH, vv[q], k, r + 1);
-                    }
+                    tail_decrement<C>(sh, cl, vv, k, r);
                 }
             }
-            __syncthreads();
+            cl.sync();
             r++;
             rounds++;
+            total = tail_gather(sh, cl, r, 0, gs++ & 1).x;
         }
+        lvl++;
     }
-    if (tid == 0) {
+    if (rank == 0 && tid == 0) {
         a.ctl[C_ROUNDS] = rounds;
         a.ctl[C_ALPHA] = k;
     }
+    cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
-constexpr size_t TAIL_SMEM = sizeof(int32_t) * (3 * (size_t)TAIL_MAX + 4) +
-                             sizeof(int16_t) * 2 * ((size_t)TAIL_MAX + TAIL_HCAP) + (size_t)TAIL_MAX;
+// Launch configuration of the tail on one cluster of C CTAs.
+template <int C>
+static cudaLaunchConfig_t tail_config(cudaLaunchAttribute* attr, cudaStream_t s) {
+    const size_t smem = sizeof(TailShared<C>);
+    FOLTY_CUDA(cudaFuncSetAttribute(k_peel_tail<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (C > 8) FOLTY_CUDA(cudaFuncSetAttribute(k_peel_tail<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(TAIL_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// CTAs of the tail's cluster: 16 when the device places such a cluster, else 8.
+static int tail_cluster_size(cudaStream_t s) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = tail_config<16>(attr, s);
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_peel_tail<16>, &cfg) == cudaSuccess && clusters >= 1) return 16;
+    cudaGetLastError();
+    cfg = tail_config<8>(attr, s);
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_peel_tail<8>, &cfg) == cudaSuccess && clusters >= 1) return 8;
+    cudaGetLastError();
+    fail(FOLTY_ECUDA, "peeling: the device cannot place the tail's thread-block cluster");
+}
+
+template <int C>
+static void launch_tail(const TailArgs& ta, cudaStream_t s) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = tail_config<C>(attr, s);
+    FOLTY_CUDA(cudaLaunchKernelEx(&cfg, k_peel_tail<C>, ta));
+    after_launch("k_peel_tail");
+}
 
 __global__ void k_iota(int32_t* __restrict__ a, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -1020,6 +1185,7 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
                      by_b, adj, adj_eid, adj_src);
 
     // ---------------- A3: peeling
+    int* peel_ctl = nullptr;
     g->core = graph_alloc<int32_t>(g, n, s);
     int32_t* core = g->core;
     int32_t* rnd = sc.get<int32_t>(n);
@@ -1042,7 +1208,8 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         pa.hr[1] = sc.get<int64_t>(pa.hcap);
         pa.ctl = sc.get<int>(C_SLOTS);
         pa.timeout_ns = 10ll * 1000 * 1000 * 1000;
-        pa.tail_n = TAIL_MAX;
+        const int tail_c = tail_cluster_size(s);
+        pa.tail_n = TAIL_OWN * tail_c;
         int init[C_SLOTS] = {0};
         init[C_MIN] = INT_MAX;
         init[C_MIN + 1] = INT_MAX;
@@ -1061,18 +1228,11 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
             FOLTY_CUDA(cudaLaunchCooperativeKernel((const void*)k_peel, grid, block, args, 0, s));
             after_launch("k_peel");
         }
-        const void* ptrs[5] = {pa.ctl + C_ERR, pa.ctl + C_TAIL, pa.ctl + C_TAIL_AC, pa.ctl + C_TAIL_N,
-                               pa.ctl + C_ALPHA};
-        int sizes[5] = {4, 4, 4, 4, 4};
-        int64_t outv[5];
-        read_back(g, ptrs, sizes, 5, outv, s);
-        if (n > 0 && outv[0] == 2) fail(FOLTY_ECUDA, "peeling: a vertex list overflowed (internal error)");
-        if (n > 0 && outv[0] != 0) fail(FOLTY_ETIMEOUT, "peeling: a grid barrier wait ran out");
-        if (n > 0 && outv[1] == 1) {
-            // single-block tail on the induced subgraph of the remaining vertices
-            const int nalive = (int)outv[3];
-            const int32_t* alive = pa.alive[outv[2]];
-            const int tn = TAIL_MAX;
+        if (n > 0) {
+            // cluster tail on the induced subgraph of the vertices the grid kernel left;
+            // always enqueued (its kernels do nothing when the grid kernel finished), so
+            // no host round trip separates the two
+            const int tn = pa.tail_n;
             int32_t* L = sc.get<int32_t>(tn);
             int32_t* gmap = sc.get<int32_t>(n);
             int* nl = sc.get<int>(1);
@@ -1081,26 +1241,21 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
             int32_t* lrow = sc.get<int32_t>(tn + 1);
             int32_t* eoff = sc.get<int32_t>(tn + 1);
             int32_t* fillc = sc.get<int32_t>(tn);
-            int16_t* ladj = sc.get<int16_t>(2 * (int64_t)S);
+            uint32_t* ladj = sc.get<uint32_t>(2 * (int64_t)S);
             FOLTY_CUDA(cudaMemsetAsync(nl, 0, sizeof(int), s));
             FOLTY_CUDA(cudaMemsetAsync(fillc, 0, sizeof(int32_t) * (size_t)tn, s));
-            FOLTY_LAUNCH(k_tail_select, grid_for(nalive, T), T, 0, s, alive, nalive, rnd, L, gmap, nl);
+            FOLTY_LAUNCH(k_tail_select, grid_for(n, T), T, 0, s, pa.alive[0], pa.alive[1], pa.ctl, rnd, tn, L, gmap,
+                         nl, pa.ctl + C_ERR);
             FOLTY_LAUNCH(k_tail_degrees, grid_for(tn, T), T, 0, s, L, nl, pa.deg, rowptr, tn, ld, d0);
             exclusive_scan(sc, ld, lrow, tn);
             exclusive_scan(sc, d0, eoff, tn);
             FOLTY_LAUNCH(k_tail_fill, grid_for(2 * (int64_t)S, T), T, 0, s, L, eoff, tn, rowptr, adj, rnd, gmap,
                          lrow, ld, fillc, ladj, pa.ctl + C_ERR);
             TailArgs ta{nl, L, ld, lrow, ladj, rnd, core, pa.ctl};
-            FOLTY_CUDA(cudaFuncSetAttribute(k_peel_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TAIL_SMEM));
-            FOLTY_LAUNCH(k_peel_tail, 1, TAIL_THREADS, TAIL_SMEM, s, ta);
+            if (tail_c == 16) launch_tail<16>(ta, s);
+            else launch_tail<8>(ta, s);
         }
-        const void* ptrs2[3] = {pa.ctl + C_ROUNDS, pa.ctl + C_ALPHA, pa.ctl + C_ERR};
-        int sizes2[3] = {4, 4, 4};
-        int64_t outv2[3];
-        read_back(g, ptrs2, sizes2, 3, outv2, s);
-        if (n > 0 && outv2[2] != 0) fail(FOLTY_ECUDA, "peeling: inconsistent degrees in the tail (internal error)");
-        g->info.peel_rounds = (int32_t)(n > 0 ? outv2[0] : 0);
-        g->info.degeneracy = (int32_t)(n > 0 ? outv2[1] : 0);
+        peel_ctl = pa.ctl;  // rounds, alpha and the error word are read with the triangle totals
     }
 
     // ---------------- A4: orientation
@@ -1131,10 +1286,15 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     FOLTY_LAUNCH(k_max_i32, grid_for(n, T), T, 0, s, g->deg, (int64_t)n, stat + 0);
     if (S > 0) FOLTY_LAUNCH(k_max_sigma, grid_for(S, T), T, 0, s, g->seg, S, stat + 2);
     {
-        const void* ptrs[5] = {toff + S, stat + 0, stat + 1, stat + 2, merged};
-        int sizes[5] = {8, 4, 4, 4, 8};
-        int64_t outv[5];
-        read_back(g, ptrs, sizes, 5, outv, s);
+        const void* ptrs[8] = {toff + S, stat + 0, stat + 1, stat + 2, merged, peel_ctl + C_ERR,
+                               peel_ctl + C_ROUNDS, peel_ctl + C_ALPHA};
+        int sizes[8] = {8, 4, 4, 4, 8, 4, 4, 4};
+        int64_t outv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        read_back(g, ptrs, sizes, peel_ctl ? 8 : 5, outv, s);  // no peeling state for n = 0
+        if (outv[5] == 1) fail(FOLTY_ETIMEOUT, "peeling: a grid barrier wait ran out");
+        if (outv[5] != 0) fail(FOLTY_ECUDA, "peeling: a vertex list overflowed (internal error)");
+        g->info.peel_rounds = (int32_t)outv[6];
+        g->info.degeneracy = (int32_t)outv[7];
         g->ntri = outv[0];
         g->info.max_degree = (int32_t)outv[1];
         g->info.max_out_degree = (int32_t)outv[2];

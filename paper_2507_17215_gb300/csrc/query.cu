@@ -430,13 +430,122 @@ void finish_query(folty_graph* g, const folty_query_params& q, const int32_t* cn
     finish_queries(g, &qp, &cnt, 1, &out, s);
 }
 
+// ------------------------------------------------------------------ all-existential triples
+
+// Flag i of the 6 * ntri roles as an int32 (input of the scan).
+__global__ void k_triple_flags(const uint8_t* __restrict__ rflag, int64_t n6, int32_t* __restrict__ flag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n6; i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = rflag[i];
+}
+
+// (x, y, w) of every role with a hit, in input vertex ids: role r = 2e + d of triangle t
+// has certificate edge x -> y (static edge e, direction d) and witness z = 2 - e. The
+// witness goes to key_w (the first sort key), x and y to xs and ys.
+__global__ void k_triple_write(const int4* __restrict__ tri, const int32_t* __restrict__ ea,
+                               const int32_t* __restrict__ eb, const uint8_t* __restrict__ rflag,
+                               const int32_t* __restrict__ pos, int64_t ntri, uint64_t* __restrict__ key_w,
+                               uint32_t* __restrict__ idx, int32_t* __restrict__ xs, int32_t* __restrict__ ys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 6 * ntri;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (!rflag[i]) continue;
+        const int64_t t = i / 6;
+        const int r = (int)(i % 6);
+        const int4 tr = tri[t];
+        int32_t P[3];
+        P[0] = (tr.w & 1) ? ea[tr.x] : eb[tr.x];  // u: bit 0 says u has the smaller id of {u, v}
+        P[1] = ea[tr.x] + eb[tr.x] - P[0];
+        P[2] = ea[tr.y] + eb[tr.y] - P[0];        // s_uw = {u, w}
+        const int e = r >> 1, d = r & 1;
+        const int p = (e == 2) ? 1 : 0, q = (e == 0) ? 1 : 2;
+        const int x = ((d == 0) == id_less(tr.w, p, q)) ? p : q;
+        const int k = pos[i];
+        key_w[k] = (uint64_t)P[2 - e];
+        idx[k] = (uint32_t)k;
+        xs[k] = P[x];
+        ys[k] = P[p + q - x];
+    }
+}
+
+__global__ void k_triple_key_xy(const uint32_t* __restrict__ order, const int32_t* __restrict__ xs,
+                                const int32_t* __restrict__ ys, int64_t n, int nb, uint64_t* __restrict__ key) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t o = order[i];
+        key[i] = ((uint64_t)(uint32_t)xs[o] << nb) | (uint64_t)(uint32_t)ys[o];
+    }
+}
+
+// out = [x... | y... | w...] in (x, y, w) order; order[i] indexes the written triples.
+__global__ void k_triple_out(const uint32_t* __restrict__ order, const int32_t* __restrict__ xs,
+                             const int32_t* __restrict__ ys, const uint64_t* __restrict__ ws, int64_t n,
+                             int32_t* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t o = order[i];
+        out[i] = xs[o];
+        out[n + i] = ys[o];
+        out[2 * n + i] = (int32_t)ws[o];
+    }
+}
+
+// Triples of the roles flagged by the probe pass, sorted by (x, y, w) with two stable
+// radix sorts (by w, then by (x, y)), into the result's host arrays. Synchronises.
+static void triples_result(folty_graph* g, const uint8_t* rflag, folty_result* out, cudaStream_t s) {
+    const int T = 256;
+    const int64_t n6 = 6 * g->ntri;
+    Scratch sc(g->alloc, s, g->dev_err);
+    int32_t* flag = sc.get<int32_t>(n6 + 1);
+    int32_t* pos = sc.get<int32_t>(n6 + 1);
+    if (n6 > 0) FOLTY_LAUNCH(k_triple_flags, grid_for(n6, T), T, 0, s, rflag, n6, flag);
+    exclusive_scan(sc, flag, pos, n6);
+    const int64_t nt = read_i32(g, pos + n6, s);
+    fill_result_triples(out, nt);
+    if (nt == 0) return;
+    uint64_t* kw = sc.get<uint64_t>(nt);
+    uint64_t* kw_alt = sc.get<uint64_t>(nt);
+    uint32_t* ix = sc.get<uint32_t>(nt);
+    uint32_t* ix_alt = sc.get<uint32_t>(nt);
+    int32_t* xs = sc.get<int32_t>(nt);
+    int32_t* ys = sc.get<int32_t>(nt);
+    FOLTY_LAUNCH(k_triple_write, grid_for(n6, T), T, 0, s, g->tri, g->ea, g->eb, rflag, pos, g->ntri, kw, ix, xs, ys);
+    const int nb = bit_length((uint64_t)(g->n > 1 ? g->n - 1 : 1));
+    // the witness value of written triple j stays in kw_src[j] (kept before sorting)
+    uint64_t* kw_src = sc.get<uint64_t>(nt);
+    FOLTY_CUDA(cudaMemcpyAsync(kw_src, kw, sizeof(uint64_t) * (size_t)nt, cudaMemcpyDeviceToDevice, s));
+    const bool a1 = radix_sort_pairs(sc, kw, kw_alt, ix, ix_alt, nt, nb);
+    read_back(g, nullptr, nullptr, 0, nullptr, s);  // the permutation indexes arrays next
+    uint32_t* order1 = a1 ? ix_alt : ix;
+    uint32_t* spare = a1 ? ix : ix_alt;
+    uint64_t* kxy = a1 ? kw : kw_alt;  // free key buffers after the first sort
+    uint64_t* kxy_alt = a1 ? kw_alt : kw;
+    FOLTY_LAUNCH(k_triple_key_xy, grid_for(nt, T), T, 0, s, order1, xs, ys, nt, nb, kxy);
+    const bool a2 = radix_sort_pairs(sc, kxy, kxy_alt, order1, spare, nt, 2 * nb);
+    const uint32_t* order = a2 ? spare : order1;
+    read_back(g, nullptr, nullptr, 0, nullptr, s);  // the sorts' look-backs completed
+    int32_t* packed = sc.get<int32_t>(3 * nt);
+    FOLTY_LAUNCH(k_triple_out, grid_for(nt, T), T, 0, s, order, xs, ys, kw_src, nt, packed);
+    FOLTY_CUDA(cudaMemcpyAsync(out->triple_x, packed, sizeof(int32_t) * 3 * (size_t)nt, cudaMemcpyDeviceToHost, s));
+    FOLTY_CUDA(cudaStreamSynchronize(s));
+}
+
 void run_query(folty_graph* g, const folty_query_params& q, folty_result* out, cudaStream_t s) {
     Scratch sc(g->alloc, s, g->dev_err);
     const int64_t mk = g->m_kept;
     int32_t* cnt = sc.get<int32_t>(mk);
     if (mk > 0) FOLTY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)mk, s));
-    launch_probe_live(g, q.delta, q.dir, 0, cnt, nullptr, 0, nullptr, s);
+    uint8_t* rflag = nullptr;
+    if (q.want_triples) {
+        rflag = sc.get<uint8_t>(6 * g->ntri + 1);
+        FOLTY_CUDA(cudaMemsetAsync(rflag, 0, (size_t)(6 * g->ntri + 1), s));
+    }
+    launch_probe_live(g, q.delta, q.dir, 0, cnt, nullptr, 0, nullptr, s, rflag);
     finish_query(g, q, cnt, out, s);  // synchronises the stream
+    if (q.want_triples) {
+        try {
+            triples_result(g, rflag, out, s);
+        } catch (...) {
+            release_result(out);
+            throw;
+        }
+    }
 }
 
 // ================================================================== traffic model

@@ -42,6 +42,11 @@ def parse_fixture(path: str):
             cases[-1]["vertices"] = []
         elif tok[0] == "vertex":
             cases[-1]["vertices"].append((int(tok[1]), int(tok[2])))
+        elif tok[0] == "triples":
+            cases[-1]["q"] = dataclasses.replace(cases[-1]["q"], want_triples=True)
+            cases[-1]["triples"] = []
+        elif tok[0] == "triple":
+            cases[-1]["triples"].append(tuple(int(x) for x in tok[1:4]))
         elif tok[0] == "counts":
             cases[-1]["counts"] = np.array([int(x) for x in tok[1:]], dtype=np.int32)
         elif tok[0] == "pair":
@@ -83,6 +88,23 @@ def brute_counts(g: W.TemporalGraph, delta: int, dir: int) -> np.ndarray:
                 c += 1
         out[i] = c
     return out
+
+
+def brute_triples(g: W.TemporalGraph, delta: int, dir: int):
+    """Sorted (x, y, w): some temporal edge x -> y forms a triangle with witness w."""
+    E = list(zip(g.src.tolist(), g.dst.tolist(), g.t.tolist()))
+    out = set()
+    for (x, y, t) in E:
+        if x == y:
+            continue
+        for w in range(g.n):
+            if w == x or w == y or (x, y, w) in out:
+                continue
+            A = [t2 for (a, b, t2) in E if _matches(a, b, x, w, dir)]
+            B = [t3 for (a, b, t3) in E if _matches(a, b, y, w, dir)]
+            if any(t <= t2 <= t3 <= t + delta for t2 in A for t3 in B):
+                out.add((x, y, w))
+    return sorted(out)
 
 
 def brute_neighbours(g: W.TemporalGraph):

@@ -63,6 +63,8 @@ def test_golden_fixtures_through_library(F, path):
         assert pairs_of(r) == c["pairs"]
         if "vertices" in c:
             assert vertices_of(r) == c["vertices"]
+        if "triples" in c:
+            assert [tuple(x) for x in r["triples"].tolist()] == c["triples"]
 
 
 def test_random_tiny_graphs(F):
@@ -196,10 +198,11 @@ def _core_numbers(n, src, dst):
 
 def test_degeneracy_and_orientation(F):
     rng = np.random.default_rng(12)
-    # the first three fit the single-block tail from the start; the last two run the
-    # grid-wide phases first (more than 12,288 vertices) and reach hubs in the tail
+    # the first four fit the cluster tail from the start; the last two run grid-wide
+    # levels first (more than 163,840 vertices alive) and reach hubs in the tail
     for g in (W.config_graph(1), W.random_small_graph(rng, 120, 5000, 10),
-              W.config_graph(3, scale=0.002), W.config_graph(2, scale=0.05), W.config_graph(2, scale=0.2)):
+              W.config_graph(3, scale=0.002), W.config_graph(2, scale=0.05), W.config_graph(2, scale=0.2),
+              W.config_graph(2, scale=0.5)):
         core = _core_numbers(g.n, g.src, g.dst)
         with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
             info = G.info()
@@ -399,3 +402,34 @@ def test_common_neighbour_counts(F):
         with oracle.OracleGraph.of(g) as og:
             _, common = og.counts(0, W.DIR_OUT, idx=idx)
         np.testing.assert_array_equal(c, common)
+
+
+@pytest.mark.parametrize("which", ["tiny", "config1", "medium_small"])
+def test_all_existential_triples(F, which):
+    """Definition 1.2 with three existential quantifiers: the (x, y, w) solutions, sorted,
+    against the oracle, for every direction variant, alone and inside a batch."""
+    rng = np.random.default_rng(41)
+    if which == "tiny":
+        graphs = [W.random_small_graph(rng, 14, 120, 25) for _ in range(6)]
+        deltas = (0, 3, 40)
+    elif which == "config1":
+        graphs = [W.config_graph(1)]
+        deltas = (100_000, 1_000_000)
+    else:
+        graphs = [W.config_graph(2, scale=0.01)]
+        deltas = (600, 86_400)
+    for g in graphs:
+        qs = [W.Query(d, 1, 2, W.Q_FORALL_T, dr, W.U_HEAD, False, want_triples=True)
+              for d in deltas for dr in (W.DIR_OUT, W.DIR_IN, W.DIR_EITHER)]
+        mixed = qs + [W.Query(deltas[-1], 1, 2, W.Q_EXISTS, W.DIR_OUT, W.U_HEAD, True)]
+        res, _ = _lib_results(F, g, qs)
+        bat, _ = _lib_results(F, g, mixed, batch=True)
+        with oracle.OracleGraph.of(g) as og:
+            for q, r, rb in zip(qs, res, bat):
+                want = og.triples(q.delta, q.dir)
+                for got in (r, rb):
+                    np.testing.assert_array_equal(got["triples"], want, err_msg=str(q))
+                    assert pairs_of(got) == pairs_of(og.query(q)), str(q)
+            want_last = og.query(mixed[-1])
+            assert pairs_of(bat[-1]) == pairs_of(want_last)
+            assert "triples" not in bat[-1]

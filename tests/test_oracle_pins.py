@@ -15,8 +15,8 @@ import pytest
 
 import oracle
 import workloads as W
-from _support import (brute_certificates, brute_counts, brute_pairs, brute_vertices, complete_graph,
-                      golden_files, pairs_of, parse_fixture, vertices_of)
+from _support import (brute_certificates, brute_counts, brute_pairs, brute_triples, brute_vertices,
+                      complete_graph, golden_files, pairs_of, parse_fixture, vertices_of)
 
 
 @pytest.mark.parametrize("path", golden_files(), ids=os.path.basename)
@@ -31,6 +31,8 @@ def test_golden_fixture(path):
                 assert pairs_of(r) == case["pairs"]
                 if "vertices" in case:
                     assert vertices_of(r) == case["vertices"]
+                if "triples" in case:
+                    assert [tuple(x) for x in r["triples"].tolist()] == case["triples"]
 
 
 def _tiny_graphs():
@@ -223,3 +225,21 @@ def test_forall_forall_solutions_are_forall_exists_solutions():
             if prev is not None:
                 assert cur <= prev
             prev = cur
+
+
+def test_triples_match_brute_force():
+    """Definition 1.2's all-existential query: triples (x, y, w) against the definition."""
+    for g in _tiny_graphs():
+        with oracle.OracleGraph.of(g) as og:
+            for dr in (W.DIR_OUT, W.DIR_IN, W.DIR_EITHER):
+                for delta in (0, 3, 30):
+                    got = [tuple(x) for x in og.triples(delta, dr).tolist()]
+                    assert got == brute_triples(g, delta, dr)
+                    # a pair's triples are the union of its edges' witnesses: at least c_e
+                    c, _ = og.counts(delta, dr)
+                    per_pair = {}
+                    for (x, y, _w) in got:
+                        per_pair[(x, y)] = per_pair.get((x, y), 0) + 1
+                    for i, (x, y) in enumerate(zip(g.src.tolist(), g.dst.tolist())):
+                        if x != y:
+                            assert per_pair.get((x, y), 0) >= c[i]

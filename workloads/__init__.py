@@ -62,6 +62,7 @@ class Query:
     outer_rho_num: int = 1
     outer_rho_den: int = 2
     want_certificates: bool = False
+    want_triples: bool = False   # also the (x, y, w) solutions of the all-existential query
 
 
 # --------------------------------------------------------------------------- samplers
