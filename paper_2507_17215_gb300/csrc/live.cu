@@ -23,33 +23,53 @@ namespace folty {
 constexpr int LIVE_IDLE = 3;  // idle slots per kept triangle (keeps >= 3 slots per triangle)
 constexpr uint8_t DMIN_NEVER = 255;
 
-// x[i] for a run index i in [0, 6) known only at run time, by selects, so that the
-// arrays stay in registers.
-template <typename V>
-__device__ __forceinline__ V pick6(const V* x, int i) {
-    V v = x[0];
-#pragma unroll
-    for (int q = 1; q < 6; q++) v = (i == q) ? x[q] : v;
-    return v;
-}
-
 // Time span of the union of runs a and b (b < 0: run a alone) from the first and last
-// timestamps of the six runs of a triangle.
+// timestamps of the six runs of a triangle. Called with indices the compiler knows, so
+// the arrays stay in registers.
 __device__ __forceinline__ bool span_of(const int64_t* f, const int64_t* l, const bool* ne, int a, int b,
                                         int64_t& first, int64_t& last) {
     bool any = false;
-    if (pick6(ne, a)) {
-        first = pick6(f, a);
-        last = pick6(l, a);
+    if (ne[a]) {
+        first = f[a];
+        last = l[a];
         any = true;
     }
-    if (b >= 0 && pick6(ne, b)) {
-        const int64_t fb = pick6(f, b), lb = pick6(l, b);
-        first = any ? min(first, fb) : fb;
-        last = any ? max(last, lb) : lb;
+    if (b >= 0 && ne[b]) {
+        first = any ? min(first, f[b]) : f[b];
+        last = any ? max(last, l[b]) : l[b];
         any = true;
     }
     return any;
+}
+
+// The eighteen (role, direction variant) buckets of one triangle whose id-order bits are
+// FLAGS (a template parameter, so that every run index below is a constant).
+template <int FLAGS>
+__device__ __forceinline__ void role_buckets(const int64_t* f, const int64_t* l, const bool* ne, int64_t t,
+                                             int64_t ntri, uint8_t* __restrict__ rmin) {
+#pragma unroll
+    for (int r = 0; r < 6; r++) {
+#pragma unroll
+        for (int dir = 0; dir < 3; dir++) {
+            uint8_t bucket = DMIN_NEVER;
+            if (ne[r]) {
+                int s2, s3;
+                role_segments(FLAGS, r >> 1, r & 1, dir, s2, s3);
+                const bool both = dir == FOLTY_DIR_EITHER;  // s2, s3 are the d = 0 runs then
+                int64_t f2 = 0, l2 = 0, f3 = 0, l3 = 0;
+                const bool a2 = span_of(f, l, ne, s2, both ? s2 + 1 : -1, f2, l2);
+                const bool a3 = span_of(f, l, ne, s3, both ? s3 + 1 : -1, f3, l3);
+                const int64_t f1 = f[r], l1 = l[r];
+                if (a2 && a3 && l2 >= f1 && l3 >= (f2 > f1 ? f2 : f1)) {
+                    int64_t dmin = f2 - l1;
+                    if (f3 - l1 > dmin) dmin = f3 - l1;
+                    if (dmin < 0) dmin = 0;
+                    bucket = (uint8_t)(64 - __clzll((unsigned long long)dmin));  // 0 for dmin = 0
+                }
+            }
+            rmin[((int64_t)dir * 6 + r) * ntri + t] = bucket;
+        }
+    }
 }
 
 // rsig[r][t] = sigma1 of role r = 2e + d; rmin[dir][r][t] = dmin bucket. The first and
@@ -78,28 +98,16 @@ __global__ void k_role_summary(const int4* __restrict__ tri, int64_t ntri, const
             l[q] = ne[q] ? (int64_t)T[en - 1] : 0;
         }
 #pragma unroll
-        for (int r = 0; r < 6; r++) {
-            rsig[r * ntri + t] = off[3 * (r >> 1) + (r & 1) + 1] - off[3 * (r >> 1) + (r & 1)];
-#pragma unroll
-            for (int dir = 0; dir < 3; dir++) {
-                uint8_t bucket = DMIN_NEVER;
-                if (ne[r]) {
-                    int s2, s3;
-                    role_segments(tr.w, r >> 1, r & 1, dir, s2, s3);
-                    const bool both = dir == FOLTY_DIR_EITHER;  // s2, s3 are the d = 0 runs then
-                    int64_t f2 = 0, l2 = 0, f3 = 0, l3 = 0;
-                    const bool a2 = span_of(f, l, ne, s2, both ? s2 + 1 : -1, f2, l2);
-                    const bool a3 = span_of(f, l, ne, s3, both ? s3 + 1 : -1, f3, l3);
-                    const int64_t f1 = f[r], l1 = l[r];
-                    if (a2 && a3 && l2 >= f1 && l3 >= (f2 > f1 ? f2 : f1)) {
-                        int64_t dmin = f2 - l1;
-                        if (f3 - l1 > dmin) dmin = f3 - l1;
-                        if (dmin < 0) dmin = 0;
-                        bucket = (uint8_t)(64 - __clzll((unsigned long long)dmin));  // 0 for dmin = 0
-                    }
-                }
-                rmin[((int64_t)dir * 6 + r) * ntri + t] = bucket;
-            }
+        for (int r = 0; r < 6; r++) rsig[r * ntri + t] = off[3 * (r >> 1) + (r & 1) + 1] - off[3 * (r >> 1) + (r & 1)];
+        switch (tr.w & 7) {
+            case 0: role_buckets<0>(f, l, ne, t, ntri, rmin); break;
+            case 1: role_buckets<1>(f, l, ne, t, ntri, rmin); break;
+            case 2: role_buckets<2>(f, l, ne, t, ntri, rmin); break;
+            case 3: role_buckets<3>(f, l, ne, t, ntri, rmin); break;
+            case 4: role_buckets<4>(f, l, ne, t, ntri, rmin); break;
+            case 5: role_buckets<5>(f, l, ne, t, ntri, rmin); break;
+            case 6: role_buckets<6>(f, l, ne, t, ntri, rmin); break;
+            default: role_buckets<7>(f, l, ne, t, ntri, rmin); break;
         }
     }
 }

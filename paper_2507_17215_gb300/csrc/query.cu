@@ -80,63 +80,87 @@ constexpr int TH_BATCH = 8;  // 32-edge chunks whose loads are in flight togethe
 // each run of one directed pair within a chunk (runs are contiguous: the order is sorted
 // by pair) with a ballot of run heads; a run with a non-zero max or certificates adds
 // them to its pair with one atomic. The universe size is looked up only for edges with
-// c >= 1 (no other edge can certify).
+// c >= 1 (no other edge can certify), and a chunk without such an edge is skipped. The
+// universe, the quantifier and the certificate list are template parameters.
+template <int UNI, int QUANT, bool CERT>
 __global__ void __launch_bounds__(TH_THREADS) k_threshold(ThresholdArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long my_cert = 0;
     for (int64_t b0 = gw * 32 * TH_BATCH; b0 < a.mk; b0 += nw * 32 * TH_BATCH) {
+        const int32_t* sd = a.sd + b0;
+        const int32_t* cn = a.cnt + b0;
+        const int32_t rem = (int32_t)min((int64_t)32 * TH_BATCH, a.mk - b0);
         int32_t kb[TH_BATCH], cb[TH_BATCH], ub[TH_BATCH];
 #pragma unroll
         for (int k = 0; k < TH_BATCH; k++) {
-            const int64_t i = b0 + k * 32 + lane;
-            kb[k] = (i < a.mk) ? a.sd[i] : -1;
-            cb[k] = (i < a.mk) ? a.cnt[i] : 0;
+            const int32_t i = k * 32 + lane;
+            kb[k] = (i < rem) ? sd[i] : -1;
+            cb[k] = (i < rem) ? cn[i] : 0;
         }
         // universe sizes of the edges with c >= 1, the lookups of all chunks in flight at once
 #pragma unroll
         for (int k = 0; k < TH_BATCH; k++) {
-            ub[k] = -1;
-            if (cb[k] >= 1) {
-                const int64_t s = kb[k] >> 1;
-                if (a.universe == FOLTY_U_COMMON) ub[k] = a.common[s];
-                else ub[k] = ((a.universe == FOLTY_U_HEAD) != (bool)(kb[k] & 1)) ? a.ea[s] : a.eb[s];
+            ub[k] = 0;
+            if (QUANT != FOLTY_Q_EXISTS && cb[k] >= 1) {
+                const int32_t s = kb[k] >> 1;
+                if (UNI == FOLTY_U_COMMON) ub[k] = a.common[s];
+                else ub[k] = ((UNI == FOLTY_U_HEAD) != (bool)(kb[k] & 1)) ? a.ea[s] : a.eb[s];
             }
         }
-        if (a.universe != FOLTY_U_COMMON) {
+        if (QUANT != FOLTY_Q_EXISTS && UNI != FOLTY_U_COMMON) {
 #pragma unroll
             for (int k = 0; k < TH_BATCH; k++)
                 if (cb[k] >= 1) ub[k] = a.deg[ub[k]];
         }
 #pragma unroll
         for (int k = 0; k < TH_BATCH; k++) {
-            if (b0 + k * 32 < a.mk) {  // warp-uniform
-                const int64_t i = b0 + k * 32 + lane;
-                const int32_t key = kb[k], c = cb[k];
-                const int sat = (c >= 1) ? certifies(a.quant, c, ub[k], a.num, a.den) : 0;
-                if (a.cert_in && i < a.mk) a.cert_in[a.perm[i]] = sat;
-                // runs of one pair are contiguous lanes (past-the-end lanes hold key -1
-                // and come last, as a run of their own)
-                const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-                const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || key != prev);
-                const unsigned above = heads & ~((2u << lane) - 1u);
-                const int start = 31 - __clz(heads & ((2u << lane) - 1u));
-                const unsigned peers =
-                    (above ? (above & (0u - above)) - 1u : 0xffffffffu) & ~((1u << start) - 1u);
-                const int run_max = __reduce_max_sync(peers, c);
-                const int run_sat = __reduce_add_sync(peers, sat);
-                if (key >= 0 && lane == start) {
-                    if (run_max > 0) atomicMax(&a.seg_max[key], run_max);
-                    if (run_sat > 0) atomicAdd(&a.seg_ncert[key], run_sat);
-                }
-                my_cert += (unsigned long long)sat;
+            if (k * 32 >= rem) break;  // warp-uniform
+            const int32_t i = k * 32 + lane;
+            const int32_t key = kb[k], c = cb[k];
+            const bool sat = c >= 1 && (QUANT == FOLTY_Q_EXISTS ||
+                                        (int64_t)c * a.den >= a.num * (int64_t)ub[k]);
+            if (CERT && i < rem) a.cert_in[a.perm[b0 + i]] = sat;
+            if (!__any_sync(0xffffffffu, c > 0)) continue;  // nothing to reduce in this chunk
+            // runs of one pair are contiguous lanes (past-the-end lanes hold key -1 and
+            // come last, as a run of their own)
+            const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+            const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || key != prev);
+            const unsigned above = heads & ~((2u << lane) - 1u);
+            const int start = 31 - __clz(heads & ((2u << lane) - 1u));
+            const unsigned peers = (above ? (above & (0u - above)) - 1u : 0xffffffffu) & ~((1u << start) - 1u);
+            const int run_max = __reduce_max_sync(peers, c);
+            const int run_sat = __reduce_add_sync(peers, sat ? 1 : 0);
+            if (key >= 0 && lane == start) {
+                if (run_max > 0) atomicMax(&a.seg_max[key], run_max);
+                if (run_sat > 0) atomicAdd(&a.seg_ncert[key], run_sat);
             }
+            my_cert += sat ? 1ull : 0ull;
         }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) my_cert += __shfl_xor_sync(0xffffffffu, my_cert, o);
     if (lane == 0 && my_cert) atomicAdd(a.n_cert, my_cert);
+}
+
+template <int UNI, int QUANT>
+static void launch_threshold_q(const ThresholdArgs& a, bool cert, unsigned grid, cudaStream_t s) {
+    if (cert) FOLTY_LAUNCH((k_threshold<UNI, QUANT, true>), grid, TH_THREADS, 0, s, a);
+    else FOLTY_LAUNCH((k_threshold<UNI, QUANT, false>), grid, TH_THREADS, 0, s, a);
+}
+
+template <int UNI>
+static void launch_threshold_u(const ThresholdArgs& a, bool cert, unsigned grid, cudaStream_t s) {
+    if (a.quant == FOLTY_Q_EXISTS) launch_threshold_q<UNI, FOLTY_Q_EXISTS>(a, cert, grid, s);
+    else launch_threshold_q<UNI, FOLTY_Q_FORALL_T>(a, cert, grid, s);
+}
+
+static void launch_threshold(const ThresholdArgs& a, unsigned grid, cudaStream_t s) {
+    const bool cert = a.cert_in != nullptr;
+    if (a.universe == FOLTY_U_HEAD) launch_threshold_u<FOLTY_U_HEAD>(a, cert, grid, s);
+    else if (a.universe == FOLTY_U_TAIL) launch_threshold_u<FOLTY_U_TAIL>(a, cert, grid, s);
+    else launch_threshold_u<FOLTY_U_COMMON>(a, cert, grid, s);
 }
 
 // Solution pairs come in two lists that are already sorted by (x, y): pairs x < y in
@@ -345,7 +369,7 @@ static void pairs_device(folty_graph* g, const folty_query_params& q, const int3
                         (int64_t)q.rho_num, (int64_t)q.rho_den, p.seg_max, p.seg_ncert, p.n_cert,
                         g->perm, p.cert_flag};
         StageSpan span(ST_THRESHOLD, s, 8 * mk);  // pair key + count per edge
-        FOLTY_LAUNCH(k_threshold, grid_for((mk + TH_BATCH - 1) / TH_BATCH, TH_THREADS), TH_THREADS, 0, s, a);
+        launch_threshold(a, grid_for((mk + TH_BATCH - 1) / TH_BATCH, TH_THREADS), s);
     }
     if (p.cert_flag) exclusive_scan(sc, p.cert_flag, p.cert_pos, g->m);
     if (n2 > 0) FOLTY_LAUNCH(k_pair_flags, grid_for(n2, T), T, 0, s, p.seg_ncert, g->by_b, S, p.flag);
