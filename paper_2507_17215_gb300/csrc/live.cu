@@ -42,19 +42,22 @@ __device__ __forceinline__ bool span_of(const int64_t* f, const int64_t* l, cons
     return any;
 }
 
-// The eighteen (role, direction variant) buckets of one triangle whose id-order bits are
-// FLAGS (a template parameter, so that every run index below is a constant).
-template <int FLAGS>
-__device__ __forceinline__ void role_buckets(const int64_t* f, const int64_t* l, const bool* ne, int64_t t,
-                                             int64_t ntri, uint8_t* __restrict__ rmin) {
+// The eighteen (role, direction variant) buckets of one triangle whose local vertices
+// 0, 1, 2 are in id order (flags = 7, so that every run index below is a constant). The
+// caller relabels each triangle into that frame; role 2k + d of the frame is role
+// 2 oe[k] + d of the triangle as stored.
+__device__ __forceinline__ void role_buckets_sorted(const int64_t* f, const int64_t* l, const bool* ne,
+                                                    const int* oe, int64_t t, int64_t ntri,
+                                                    uint8_t* __restrict__ rmin) {
 #pragma unroll
     for (int r = 0; r < 6; r++) {
+        const int64_t row = 2 * oe[r >> 1] + (r & 1);
 #pragma unroll
         for (int dir = 0; dir < 3; dir++) {
             uint8_t bucket = DMIN_NEVER;
             if (ne[r]) {
                 int s2, s3;
-                role_segments(FLAGS, r >> 1, r & 1, dir, s2, s3);
+                role_segments(7, r >> 1, r & 1, dir, s2, s3);
                 const bool both = dir == FOLTY_DIR_EITHER;  // s2, s3 are the d = 0 runs then
                 int64_t f2 = 0, l2 = 0, f3 = 0, l3 = 0;
                 const bool a2 = span_of(f, l, ne, s2, both ? s2 + 1 : -1, f2, l2);
@@ -67,48 +70,75 @@ __device__ __forceinline__ void role_buckets(const int64_t* f, const int64_t* l,
                     bucket = (uint8_t)(64 - __clzll((unsigned long long)dmin));  // 0 for dmin = 0
                 }
             }
-            rmin[((int64_t)dir * 6 + r) * ntri + t] = bucket;
+            rmin[((int64_t)dir * 6 + row) * ntri + t] = bucket;
         }
     }
 }
 
-// rsig[r][t] = sigma1 of role r = 2e + d; rmin[dir][r][t] = dmin bucket. The first and
-// last timestamps of the triangle's six runs are loaded once, together.
+// First and last timestamp and size of both runs of one static edge (direction 0 =
+// small id -> large id, then direction 1); first = last = 0 for an empty run.
 template <typename TS>
-__global__ void k_role_summary(const int4* __restrict__ tri, int64_t ntri, const int32_t* __restrict__ seg,
-                               const TS* __restrict__ T, int32_t* __restrict__ rsig, uint8_t* __restrict__ rmin) {
+struct __align__(16) RunEnds {
+    TS f0, l0, f1, l1;
+    int32_t n0, n1, pad0, pad1;
+};
+
+template <typename TS>
+__global__ void k_run_ends(const int32_t* __restrict__ seg, int64_t S, const TS* __restrict__ T,
+                           RunEnds<TS>* __restrict__ ends) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < S; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t o0 = seg[2 * e], o1 = seg[2 * e + 1], o2 = seg[2 * e + 2];
+        RunEnds<TS> r;
+        r.n0 = o1 - o0;
+        r.n1 = o2 - o1;
+        r.f0 = r.n0 > 0 ? T[o0] : (TS)0;
+        r.l0 = r.n0 > 0 ? T[o1 - 1] : (TS)0;
+        r.f1 = r.n1 > 0 ? T[o1] : (TS)0;
+        r.l1 = r.n1 > 0 ? T[o2 - 1] : (TS)0;
+        r.pad0 = r.pad1 = 0;
+        ends[e] = r;
+    }
+}
+
+// rsig[r][t] = sigma1 of role r = 2e + d; rmin[dir][r][t] = dmin bucket. Each triangle
+// is relabelled so that its local vertices are in id order (a rank per vertex from the
+// three id-order bits); its three static edges are then read from the run-ends table in
+// that frame, one aligned record each, and every thread runs the same code whatever the
+// triangle's id order.
+template <typename TS>
+__global__ void k_role_summary(const int4* __restrict__ tri, int64_t ntri, const RunEnds<TS>* __restrict__ ends,
+                               int32_t* __restrict__ rsig, uint8_t* __restrict__ rmin) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntri;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int4 tr = tri[t];
-        int32_t off[9];
-        const int32_t se[3] = {tr.x, tr.y, tr.z};
+        const int b0 = tr.w & 1, b1 = (tr.w >> 1) & 1, b2 = (tr.w >> 2) & 1;
+        // rank of each local vertex among the three ids
+        const int rk0 = (b0 ^ 1) + (b1 ^ 1), rk1 = b0 + (b2 ^ 1), rk2 = b1 + b2;
+        // stored edge e joins local vertices (0,1), (0,2), (1,2); in the sorted frame it
+        // joins ranks (rk_p, rk_q), i.e. frame edge rk_p + rk_q - 1
+        const int k0 = rk0 + rk1 - 1, k1 = rk0 + rk2 - 1;
+        int oe[3];
+        int32_t se[3];
 #pragma unroll
-        for (int e = 0; e < 3; e++) {
-            off[3 * e] = seg[2 * se[e]];
-            off[3 * e + 1] = seg[2 * se[e] + 1];
-            off[3 * e + 2] = seg[2 * se[e] + 2];
+        for (int k = 0; k < 3; k++) {
+            oe[k] = (k == k0) ? 0 : (k == k1) ? 1 : 2;
+            se[k] = (k == k0) ? tr.x : (k == k1) ? tr.y : tr.z;
         }
         int64_t f[6], l[6];
         bool ne[6];
 #pragma unroll
-        for (int q = 0; q < 6; q++) {  // run q = 2e + d = [off[3e + d], off[3e + d + 1])
-            const int32_t b = off[3 * (q >> 1) + (q & 1)], en = off[3 * (q >> 1) + (q & 1) + 1];
-            ne[q] = b < en;
-            f[q] = ne[q] ? (int64_t)T[b] : 0;
-            l[q] = ne[q] ? (int64_t)T[en - 1] : 0;
+        for (int k = 0; k < 3; k++) {
+            const RunEnds<TS> re = ends[se[k]];
+            ne[2 * k] = re.n0 > 0;
+            ne[2 * k + 1] = re.n1 > 0;
+            f[2 * k] = (int64_t)re.f0;
+            l[2 * k] = (int64_t)re.l0;
+            f[2 * k + 1] = (int64_t)re.f1;
+            l[2 * k + 1] = (int64_t)re.l1;
+            rsig[(int64_t)(2 * oe[k]) * ntri + t] = re.n0;
+            rsig[(int64_t)(2 * oe[k] + 1) * ntri + t] = re.n1;
         }
-#pragma unroll
-        for (int r = 0; r < 6; r++) rsig[r * ntri + t] = off[3 * (r >> 1) + (r & 1) + 1] - off[3 * (r >> 1) + (r & 1)];
-        switch (tr.w & 7) {
-            case 0: role_buckets<0>(f, l, ne, t, ntri, rmin); break;
-            case 1: role_buckets<1>(f, l, ne, t, ntri, rmin); break;
-            case 2: role_buckets<2>(f, l, ne, t, ntri, rmin); break;
-            case 3: role_buckets<3>(f, l, ne, t, ntri, rmin); break;
-            case 4: role_buckets<4>(f, l, ne, t, ntri, rmin); break;
-            case 5: role_buckets<5>(f, l, ne, t, ntri, rmin); break;
-            case 6: role_buckets<6>(f, l, ne, t, ntri, rmin); break;
-            default: role_buckets<7>(f, l, ne, t, ntri, rmin); break;
-        }
+        role_buckets_sorted(f, l, ne, oe, t, ntri, rmin);
     }
 }
 
@@ -308,17 +338,22 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS*
 
 // ------------------------------------------------------------------ host side
 
+template <typename TS>
+static void role_summary_t(folty_graph* g, cudaStream_t s) {
+    const int64_t S = g->S, ntri = g->ntri;
+    Scratch sc(g->alloc, s, g->dev_err);
+    RunEnds<TS>* ends = sc.get<RunEnds<TS>>(S);
+    FOLTY_LAUNCH(k_run_ends<TS>, grid_for(S, 256), 256, 0, s, g->seg, S, (const TS*)g->T, ends);
+    FOLTY_LAUNCH(k_role_summary<TS>, grid_for(ntri, 256), 256, 0, s, g->tri, ntri, ends, g->rsig, g->rmin);
+}
+
 void build_role_summary(folty_graph* g, cudaStream_t s) {
     const int64_t ntri = g->ntri;
     g->rsig = graph_alloc<int32_t>(g, 6 * ntri, s);
     g->rmin = graph_alloc<uint8_t>(g, 18 * ntri, s);
     if (ntri == 0) return;
-    if (g->ts32)
-        FOLTY_LAUNCH(k_role_summary<uint32_t>, grid_for(ntri, 256), 256, 0, s, g->tri, ntri, g->seg,
-                     (const uint32_t*)g->T, g->rsig, g->rmin);
-    else
-        FOLTY_LAUNCH(k_role_summary<int64_t>, grid_for(ntri, 256), 256, 0, s, g->tri, ntri, g->seg,
-                     (const int64_t*)g->T, g->rsig, g->rmin);
+    if (g->ts32) role_summary_t<uint32_t>(g, s);
+    else role_summary_t<int64_t>(g, s);
 }
 
 template <typename TS, int MODE>
