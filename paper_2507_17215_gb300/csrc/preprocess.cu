@@ -20,10 +20,13 @@ namespace folty {
 
 // ================================================================== A1
 
-// Sort key of a temporal edge: (a, b, dir) with a = min, b = max id, dir = (src > dst).
+// Sort key of a temporal edge: 2 p(a, b) + dir with a = min, b = max id, dir = (src > dst)
+// and p(a, b) = a (2n - a - 1) / 2 + (b - a - 1) the rank of the pair among all pairs
+// a < b in (a, b) order, so keys order edges by (a, b, dir) within n (n - 1) values (one
+// bit narrower than packing a and b side by side: 40 bits for a million vertices).
 // Self-loops get the all-ones key of the used width and sort last.
 __global__ void k_build_keys(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                             int64_t m, int nb, uint64_t loop_key, uint64_t* __restrict__ key,
+                             int64_t m, int32_t n, uint64_t loop_key, uint64_t* __restrict__ key,
                              uint32_t* __restrict__ val) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -32,8 +35,9 @@ __global__ void k_build_keys(const int32_t* __restrict__ src, const int32_t* __r
         if (x == y) {
             k = loop_key;
         } else {
-            uint64_t a = (uint64_t)min(x, y), b = (uint64_t)max(x, y);
-            k = (a << (nb + 1)) | (b << 1) | (uint64_t)(x > y);
+            const uint64_t a = (uint64_t)min(x, y), b = (uint64_t)max(x, y);
+            const uint64_t p = a * (2 * (uint64_t)n - a - 1) / 2 + (b - a - 1);
+            k = 2 * p + (uint64_t)(x > y);
         }
         key[i] = k;
         val[i] = (uint32_t)i;
@@ -80,12 +84,10 @@ __global__ void k_offsets32(const int64_t* __restrict__ t, int64_t m, int64_t tb
         t32[i] = (uint32_t)(__ldcs(t + i) - tbase);
 }
 
-// Static edge ids, endpoints, segment starts. pscan = exclusive scan of newpair.
+// Static edge ids and segment starts. pscan = exclusive scan of newpair.
 __global__ void k_segments(const uint64_t* __restrict__ key, const int32_t* __restrict__ newpair,
-                           const int32_t* __restrict__ pscan, int64_t mk, int nb,
-                           int32_t* __restrict__ sd, int32_t* __restrict__ ea,
-                           int32_t* __restrict__ eb, int32_t* __restrict__ seg) {
-    const uint64_t vmask = (nb >= 31) ? 0x7fffffffull : ((1ull << nb) - 1);
+                           const int32_t* __restrict__ pscan, int64_t mk, int32_t* __restrict__ sd,
+                           int32_t* __restrict__ seg) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mk;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint64_t k = key[i];
@@ -93,11 +95,42 @@ __global__ void k_segments(const uint64_t* __restrict__ key, const int32_t* __re
         int dir = (int)(k & 1);
         sd[i] = 2 * s + dir;
         if (newpair[i]) {
-            ea[s] = (int32_t)(k >> (nb + 1));
-            eb[s] = (int32_t)((k >> 1) & vmask);
             seg[2 * s] = (int32_t)i;
             seg[2 * s + 1] = -1;
         }
+    }
+}
+
+// Pairs a < b with first element below x: x (2n - x - 1) / 2.
+__device__ __forceinline__ uint64_t pairs_before(int64_t x, int32_t n) {
+    return (uint64_t)x * (uint64_t)(2 * (int64_t)n - x - 1) / 2;
+}
+
+// The pair (a, b) of rank p (inverse of the key of k_build_keys): a is the largest x with
+// pairs_before(x) <= p, first estimated from the smaller root of x^2 - (2n - 1) x + 2p = 0
+// (the discriminant (2n - 1)^2 - 8p is exact in 64 bits for n < 2^31; its square root is
+// taken in single precision, a few units off at most for ids below 2^24), then corrected
+// by exact integer comparisons.
+__device__ __forceinline__ void pair_of_rank(uint64_t p, int32_t n, int32_t& a, int32_t& b) {
+    const uint64_t c = 2 * (uint64_t)n - 1;
+    const uint64_t disc = c * c - 8 * p;
+    int64_t x = (int64_t)(((float)c - sqrtf((float)disc)) * 0.5f);
+    x = x < 0 ? 0 : (x > n - 2 ? n - 2 : x);
+    while (x > 0 && pairs_before(x, n) > p) x--;
+    while (x + 1 <= n - 2 && pairs_before(x + 1, n) <= p) x++;
+    a = (int32_t)x;
+    b = (int32_t)(p - pairs_before(x, n) + (uint64_t)x + 1);
+}
+
+// Endpoints of static edge s from the key of its first temporal edge (one thread per
+// static edge, so that no warp idles through the decoding).
+__global__ void k_pair_ends(const uint64_t* __restrict__ key, const int32_t* __restrict__ seg, int32_t S,
+                            int32_t n, int32_t* __restrict__ ea, int32_t* __restrict__ eb) {
+    for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
+        int32_t x, y;
+        pair_of_rank(key[seg[2 * s]] >> 1, n, x, y);
+        ea[s] = x;
+        eb[s] = y;
     }
 }
 
@@ -217,7 +250,10 @@ enum {
     C_TAIL_AC = 18,
     C_TAIL_N = 19,
     C_RM = 20,  // 2 slots by level parity: vertices removed after the level's compaction
-    C_SLOTS = 24
+    C_SOLO = 22,    // 1 when the cluster tail stopped early for the single-CTA phase
+    C_SOLO_K = 23,  // level and round handed to the single-CTA phase
+    C_SOLO_R = 24,
+    C_SLOTS = 28
 };
 
 struct PeelArgs {
@@ -642,6 +678,13 @@ struct TailArgs {
     int32_t* rnd;
     int32_t* core;
     int* ctl;
+    // hand-off to the single-CTA phase once at most solo_cap vertices are left: their
+    // local ids (slist), current degrees (sdeg), and map2[local id] = position in slist
+    int solo_cap;
+    int* ns;
+    int32_t* slist;
+    int32_t* sdeg;
+    int32_t* map2;
 };
 
 constexpr int TAIL_SHORT = 32;   // rows up to this length: one thread, TAIL_CHUNK loads at a time
@@ -662,7 +705,8 @@ struct TailShared {
     uint16_t FL[2][OWN];         // frontier by round parity (owned slots)
     uint16_t FH[TAIL_HCAP];      // heavy rows of the current round
     int cntL[3], cntH[2], smin[2];
-    int bc[2][2];                // cluster-wide values, published by tail_gather
+    int acnt[2];                 // owned vertices alive at the level start, by level parity
+    int bc[2][3];                // cluster-wide values, published by tail_gather
 };
 
 // Neighbours vv[0..N) (negative: none) lose one degree each in round r at level k: all N
@@ -685,30 +729,34 @@ __device__ __forceinline__ void tail_decrement(TailShared<C>& sh, cg::cluster_gr
     }
 }
 
-// Cluster-wide frontier size of round t and minimum of the level minima smin[p]: warp 0
-// reads every CTA's values (lane c reads CTA c) and publishes them in this CTA's shared
-// memory slot s (callers alternate s, so that a slot is rewritten only after a barrier
-// that follows every read of it). The whole CTA must call it; every CTA gets the same
-// values when no CTA appends to slot t % 3 or lowers smin[p] meanwhile.
+// Cluster-wide frontier size of round t, minimum of the level minima smin[p] and sum of
+// the alive counts acnt[p]: warp 0 reads every CTA's values (lane c reads CTA c) and
+// publishes them in this CTA's shared memory slot s (callers alternate s, so that a slot
+// is rewritten only after a barrier that follows every read of it). The whole CTA must
+// call it; every CTA gets the same values when no CTA appends to slot t % 3 or changes
+// smin[p] or acnt[p] meanwhile.
 template <int C>
-__device__ __forceinline__ int2 tail_gather(TailShared<C>& sh, cg::cluster_group& cl, int t, int p, int s) {
+__device__ __forceinline__ int3 tail_gather(TailShared<C>& sh, cg::cluster_group& cl, int t, int p, int s) {
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
-        int v = 0, m = INT_MAX;
+        int v = 0, m = INT_MAX, al = 0;
         if (lane < C) {
             const TailShared<C>* q = cl.map_shared_rank(&sh, lane);
             v = q->cntL[t % 3];
             m = q->smin[p];
+            al = q->acnt[p];
         }
         v = __reduce_add_sync(0xffffffffu, v);
         m = __reduce_min_sync(0xffffffffu, m);
+        al = __reduce_add_sync(0xffffffffu, al);
         if (lane == 0) {
             sh.bc[s][0] = v;
             sh.bc[s][1] = m;
+            sh.bc[s][2] = al;
         }
     }
     __syncthreads();
-    return make_int2(sh.bc[s][0], sh.bc[s][1]);
+    return make_int3(sh.bc[s][0], sh.bc[s][1], sh.bc[s][2]);
 }
 
 // The same peeling as k_peel (levels, rounds, k + 1 -> k crossings), on the local
@@ -747,8 +795,10 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
     if (tid < 2) {
         sh.cntH[tid] = 0;
         sh.smin[tid] = INT_MAX;
+        sh.acnt[tid] = 0;
     }
     int k = a.ctl[C_TAIL_K], r = a.ctl[C_TAIL_R], rounds = a.ctl[C_ROUNDS], lvl = 0, gs = 0;
+    bool handed = false;
     cl.sync();
     while (true) {
         // ---- level start: owned vertices of degree k + 1 join round r + 1
@@ -756,19 +806,22 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
             sh.cntL[(r + 2) % 3] = 0;
             sh.cntH[(r + 1) & 1] = 0;
             sh.smin[(lvl + 1) & 1] = INT_MAX;
+            sh.acnt[(lvl + 1) & 1] = 0;
         }
         int kk = k + 1;
         int lmin = INT_MAX;
         for (int q0 = 0; q0 < OWN; q0 += TAIL_THREADS) {
             const int q = q0 + tid;
-            bool rem = false;
+            bool rem = false, alive = false;
             if (q < OWN && q * C + rank < nl) {
                 const int d = sh.odeg[q];
                 if (d > k) {
+                    alive = true;
                     if (d <= kk) rem = true;
                     else lmin = min(lmin, d);
                 }
             }
+            warp_count(alive, &sh.acnt[lvl & 1]);
             const unsigned m = __ballot_sync(0xffffffffu, rem);
             if (m) {
                 const int leader = __ffs(m) - 1;
@@ -781,7 +834,41 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
         lmin = __reduce_min_sync(0xffffffffu, lmin);
         if (lane == 0 && lmin != INT_MAX) atomicMin(&sh.smin[lvl & 1], lmin);
         cl.sync();
-        const int2 g = tail_gather(sh, cl, r + 1, lvl & 1, gs++ & 1);
+        const int3 g = tail_gather(sh, cl, r + 1, lvl & 1, gs++ & 1);
+        if (g.z > 0 && g.z <= a.solo_cap) {
+            // few vertices left: export them (local id, current degree) to the single-CTA
+            // phase, which starts this level again; the frontier filed above is dropped
+            for (int q0 = 0; q0 < OWN; q0 += TAIL_THREADS) {
+                const int q = q0 + tid;
+                const int v = q * C + rank;
+                const bool alive = q < OWN && v < nl && sh.odeg[q] > k;
+                const unsigned m = __ballot_sync(0xffffffffu, alive);
+                if (m) {
+                    const int leader = __ffs(m) - 1;
+                    int base = 0;
+                    if (lane == leader) base = atomicAdd(a.ns, __popc(m));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    if (alive) {
+                        const int i = base + __popc(m & ((1u << lane) - 1u));
+                        if (i < a.solo_cap) {
+                            a.slist[i] = v;
+                            a.sdeg[i] = sh.odeg[q];
+                            a.map2[v] = i;
+                        } else {
+                            atomicExch(&a.ctl[C_ERR], 2);
+                        }
+                    }
+                }
+            }
+            if (rank == 0 && tid == 0) {
+                a.ctl[C_SOLO] = 1;
+                a.ctl[C_SOLO_K] = k;
+                a.ctl[C_SOLO_R] = r;
+                a.ctl[C_ROUNDS] = rounds;
+            }
+            handed = true;
+            break;
+        }
         int total = g.x;
         if (total == 0) {
             if (g.y == INT_MAX) break;  // nothing left anywhere
@@ -886,7 +973,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
         }
         lvl++;
     }
-    if (rank == 0 && tid == 0) {
+    if (rank == 0 && tid == 0 && !handed) {
         a.ctl[C_ROUNDS] = rounds;
         a.ctl[C_ALPHA] = k;
     }
@@ -932,6 +1019,351 @@ static void launch_tail(const TailArgs& ta, cudaStream_t s) {
     cudaLaunchConfig_t cfg = tail_config<C>(attr, s);
     FOLTY_CUDA(cudaLaunchKernelEx(&cfg, k_peel_tail<C>, ta));
     after_launch("k_peel_tail");
+}
+
+// ================================================================== A3 last levels
+
+// Once at most SOLO_CAP vertices are left, a single CTA finishes the peeling: degrees, row
+// starts and frontiers of the remaining subgraph fit in its shared memory, so a round ends
+// with __syncthreads instead of a cluster barrier. Vertices are renumbered 0..ns-1 again
+// ("solo" ids, 16-bit) in the order the cluster exported them.
+constexpr int SOLO_THREADS = 1024;
+constexpr int SOLO_CAP = 12288;  // vertices of the single-CTA phase
+constexpr int SOLO_PASS = 2048;  // frontier vertices laid out per pass (2 per thread)
+constexpr int SOLO_CHUNK = 8;    // adjacency entries per thread with loads in flight together
+
+// Cluster row length and global id of each exported vertex (0 past the exported count).
+__global__ void k_solo_rows(const int* __restrict__ ctl, const int* __restrict__ ns_p,
+                            const int32_t* __restrict__ slist, const int32_t* __restrict__ lrow,
+                            const int32_t* __restrict__ L, int32_t* __restrict__ dl, int32_t* __restrict__ sgid) {
+    if (ctl[C_SOLO] != 1) return;
+    const int ns = *ns_p;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < SOLO_CAP; i += gridDim.x * blockDim.x) {
+        if (i < ns) {
+            const int32_t v = slist[i];
+            dl[i] = lrow[v + 1] - lrow[v];
+            sgid[i] = L[v];
+        } else {
+            dl[i] = 0;
+        }
+    }
+}
+
+// Entry e of the concatenated cluster rows of the exported vertices (eo = prefix of dl):
+// an alive neighbour (map2 >= 0) goes to its owner's row of the remaining subgraph, in
+// solo ids (order within a row is irrelevant). Every row must come out with exactly the
+// degree the cluster exported (its alive neighbours): fc counts them, and the
+// single-CTA kernel checks the count; an entry beyond it is recorded in *err (4).
+__global__ void k_solo_fill(const int* __restrict__ ctl, const int32_t* __restrict__ eo,
+                            const int32_t* __restrict__ slist, const int32_t* __restrict__ sdeg,
+                            const int32_t* __restrict__ srow, const int32_t* __restrict__ lrow,
+                            const uint32_t* __restrict__ ladj, const int32_t* __restrict__ map2,
+                            int32_t* __restrict__ fc, uint16_t* __restrict__ sadj, int* __restrict__ err) {
+    if (ctl[C_SOLO] != 1 || ctl[C_ERR] != 0) return;
+    const int64_t total = eo[SOLO_CAP];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = SOLO_CAP - 1;  // last owner with eo[owner] <= e
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (eo[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        const int32_t m = map2[ladj[lrow[slist[lo]] + (int32_t)(e - eo[lo])]];
+        if (m >= 0) {
+            const int p = atomicAdd(&fc[lo], 1);
+            if (p < sdeg[lo]) sadj[srow[lo] + p] = (uint16_t)m;
+            else atomicExch(err, 4);
+        }
+    }
+}
+
+struct SoloArgs {
+    const int* ns;
+    const int32_t* sdeg;
+    const int32_t* fc;    // entries k_solo_fill wrote per row (must equal sdeg)
+    const int32_t* srow;  // exclusive prefix of sdeg: row i = sadj[srow[i], srow[i + 1])
+    const uint16_t* sadj;
+    const int32_t* sgid;  // global vertex id
+    int32_t* rnd;
+    int32_t* core;
+    int* ctl;
+};
+
+struct SoloShared {
+    int32_t deg[SOLO_CAP];
+    int32_t rs[SOLO_CAP + 1];
+    uint16_t FL[2][SOLO_CAP];  // frontier by round parity
+    int32_t P[SOLO_PASS + 1];  // prefix of the row lengths of one pass of a large frontier
+    int32_t D[SOLO_PASS];      // row start - P: adjacency index of flat entry x is D[o] + x
+    int cnt[3];                // frontier sizes, rotating over three rounds
+    int smin[2];               // smallest degree above the level, by level parity
+    int wsum[SOLO_THREADS / 32];
+};
+
+constexpr int SOLO_SLOTS = SOLO_CAP / SOLO_THREADS;  // vertices each thread checks at level starts
+static_assert(SOLO_CAP % SOLO_THREADS == 0 && SOLO_SLOTS <= 32, "level-start slots fit one mask word");
+
+// Appends solo id v to the frontier list for every lane with pred set (one shared-memory
+// atomic per warp). A list never holds more than SOLO_CAP entries (a vertex joins one
+// frontier); an append beyond that is dropped and the count, above SOLO_CAP, reports it.
+// The whole warp must call it.
+__device__ __forceinline__ void solo_append(bool pred, int v, uint16_t* fl, int* cnt) {
+    const unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    const int at = base + __popc(m & ((1u << lane) - 1u));
+    if (pred && at < SOLO_CAP) fl[at] = (uint16_t)v;
+}
+
+// The same append for one thread alone (no warp-wide step).
+__device__ __forceinline__ void solo_push(int v, uint16_t* fl, int* cnt) {
+    const int at = atomicAdd(cnt, 1);
+    if (at < SOLO_CAP) fl[at] = (uint16_t)v;
+}
+
+// Neighbours vv[0..N) (negative: none) lose one degree each at level k; a k + 1 -> k
+// crossing files the vertex in the next frontier. The whole warp must call it.
+template <int N>
+__device__ __forceinline__ void solo_decrement(SoloShared& sh, const int (&vv)[N], int k, uint16_t* fn, int* cn) {
+    int old[N];
+#pragma unroll
+    for (int c = 0; c < N; c++) old[c] = vv[c] >= 0 ? atomicSub(&sh.deg[vv[c]], 1) : 0;
+#pragma unroll
+    for (int c = 0; c < N; c++) solo_append(vv[c] >= 0 && old[c] == k + 1, vv[c], fn, cn);
+}
+
+// The same peeling once more (levels, rounds, k + 1 -> k crossings), continuing the level
+// k and round r where the cluster stopped. A round lays the frontier's rows out flat (a
+// prefix of their lengths) and deals the entries to all threads alike. A frontier of at
+// most 32 vertices (most rounds) is laid out by every warp in its own registers, so such
+// a round costs one barrier, one adjacency load and one shared-memory decrement per
+// entry; a larger one goes through shared memory in passes of SOLO_PASS vertices. At a
+// level start each thread checks the vertices it owns (tid + j SOLO_THREADS) that were
+// still alive at the previous one.
+__global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    SoloShared& sh = *reinterpret_cast<SoloShared*>(smem);
+    if (a.ctl[C_SOLO] != 1 || a.ctl[C_ERR] != 0) return;
+    const int ns = *a.ns;
+    if (ns > SOLO_CAP) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int miscount = 0;
+    for (int i = tid; i <= ns; i += SOLO_THREADS) {
+        if (i < ns) {
+            sh.deg[i] = a.sdeg[i];
+            miscount |= a.fc[i] != a.sdeg[i];
+        }
+        sh.rs[i] = a.srow[i];
+    }
+    unsigned mine = 0;  // owned slots alive at the last level start
+    for (int j = 0; j < SOLO_SLOTS; j++)
+        if (tid + j * SOLO_THREADS < ns) mine |= 1u << j;
+    if (tid < 3) sh.cnt[tid] = 0;
+    if (tid < 2) sh.smin[tid] = INT_MAX;
+    int k = a.ctl[C_SOLO_K], r = a.ctl[C_SOLO_R], rounds = a.ctl[C_ROUNDS], lvl = 0;
+    // every level and every round removes at least one vertex: more than 2 ns + 2 steps
+    // (or a frontier above SOLO_CAP) can only come from an internal error
+    int steps = 0;
+    bool bad = false;
+    if (__syncthreads_or(miscount)) {
+        if (tid == 0) atomicExch(&a.ctl[C_ERR], 4);
+        return;
+    }
+    while (true) {
+        // ---- level start: vertices of degree k + 1 (or the smallest degree) join round
+        // r + 1 (r is the empty round that ended the last level, or the hand-off round)
+        uint16_t* fs = sh.FL[(r + 1) & 1];
+        int* cs = &sh.cnt[(r + 1) % 3];
+        int kk = k + 1, lmin = INT_MAX;
+        for (unsigned m = mine; m; m &= m - 1) {
+            const int j = __ffs(m) - 1, i = tid + j * SOLO_THREADS;
+            const int d = sh.deg[i];
+            if (d <= k) mine &= ~(1u << j);  // left at an earlier level
+            else if (d <= kk) solo_push(i, fs, cs);
+            else lmin = min(lmin, d);
+        }
+        lmin = __reduce_min_sync(0xffffffffu, lmin);
+        if (lane == 0 && lmin != INT_MAX) atomicMin(&sh.smin[lvl & 1], lmin);
+        __syncthreads();
+        const int c0 = *cs, m0 = sh.smin[lvl & 1];
+        if (tid == 0) sh.smin[(lvl + 1) & 1] = INT_MAX;  // last read at the previous level start
+        if (++steps > 2 * ns + 2 || c0 > SOLO_CAP) {
+            bad = true;
+            break;
+        }
+        if (c0 == 0) {
+            if (m0 == INT_MAX) break;  // nothing left
+            kk = m0;                   // jump to the smallest remaining degree
+            __syncthreads();           // every thread has read c0 before the jump appends
+            for (unsigned m = mine; m; m &= m - 1) {
+                const int i = tid + (__ffs(m) - 1) * SOLO_THREADS;
+                if (sh.deg[i] <= kk) solo_push(i, fs, cs);  // every kept slot has degree > k + 1
+            }
+        }
+        k = kk;
+        r += 1;
+        lvl++;
+        // ---- rounds at level k
+        while (true) {
+            __syncthreads();  // the round's frontier is complete
+            const int nL = sh.cnt[r % 3];
+            if (tid == 0) sh.cnt[(r + 2) % 3] = 0;  // read in round r - 1, appended to in round r + 1
+            if (nL == 0) break;
+            if (++steps > 2 * ns + 2 || nL > SOLO_CAP) {
+                bad = true;
+                break;
+            }
+            const uint16_t* fl = sh.FL[r & 1];
+            uint16_t* fn = sh.FL[(r + 1) & 1];
+            int* cn = &sh.cnt[(r + 1) % 3];
+            if (nL <= 32) {
+                // lane o holds frontier vertex o: row start, length, exclusive prefix
+                const bool have = lane < nL;
+                const int q = have ? fl[lane] : 0;
+                const int rb = have ? sh.rs[q] : 0;
+                const int len = have ? sh.rs[q + 1] - rb : 0;
+                int inc = len;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += y;
+                }
+                const int ex = inc - len;
+                const int W = __shfl_sync(0xffffffffu, inc, 31);
+                const int gid = (warp == 0 && have) ? a.sgid[q] : -1;
+                for (int x0 = 0; x0 < W; x0 += SOLO_THREADS * SOLO_CHUNK) {
+                    const int nch = min(SOLO_CHUNK, (W - x0 + SOLO_THREADS - 1) / SOLO_THREADS);  // block-uniform
+                    int vv[SOLO_CHUNK];
+#pragma unroll
+                    for (int c = 0; c < SOLO_CHUNK; c++) {
+                        vv[c] = -1;
+                        if (c >= nch) continue;
+                        const int x = x0 + c * SOLO_THREADS + tid;
+                        int lo = 0;  // last row o < nL with ex_o <= x
+#pragma unroll
+                        for (int st = 16; st > 0; st >>= 1) {
+                            const int mid = lo + st;
+                            const int em = __shfl_sync(0xffffffffu, ex, mid);
+                            if (mid < nL && em <= x) lo = mid;
+                        }
+                        const int base = __shfl_sync(0xffffffffu, rb, lo) - __shfl_sync(0xffffffffu, ex, lo);
+                        if (x < W) {
+                            vv[c] = a.sadj[base + x];
+                            if (vv[c] >= ns) {  // cannot happen for rows k_solo_fill checked
+                                atomicExch(&a.ctl[C_ERR], 5);
+                                vv[c] = -1;
+                            }
+                        }
+                    }
+                    solo_decrement(sh, vv, k, fn, cn);
+                }
+                if (gid >= 0) {
+                    a.rnd[gid] = r;
+                    a.core[gid] = k;
+                }
+            } else {
+                for (int p0 = 0; p0 < nL; p0 += SOLO_PASS) {
+                    const int np = min(SOLO_PASS, nL - p0);
+                    // two frontier vertices per thread: row lengths, global ids
+                    int len[2], rb[2], gid[2];
+#pragma unroll
+                    for (int u = 0; u < 2; u++) {
+                        const int i = 2 * tid + u;
+                        len[u] = 0;
+                        rb[u] = 0;
+                        gid[u] = -1;
+                        if (i < np) {
+                            const int q = fl[p0 + i];
+                            rb[u] = sh.rs[q];
+                            len[u] = sh.rs[q + 1] - rb[u];
+                            gid[u] = a.sgid[q];
+                        }
+                    }
+                    // block-wide exclusive prefix of the thread sums
+                    const int mysum = len[0] + len[1];
+                    int inc = mysum;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += y;
+                    }
+                    if (lane == 31) sh.wsum[warp] = inc;
+                    __syncthreads();
+                    if (warp == 0) {
+                        int w = sh.wsum[lane], wi = w;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+                            if (lane >= o) wi += y;
+                        }
+                        sh.wsum[lane] = wi - w;  // exclusive warp offsets
+                        if (lane == 31) sh.P[np] = wi;
+                    }
+                    __syncthreads();
+                    const int ex = sh.wsum[warp] + inc - mysum;
+#pragma unroll
+                    for (int u = 0; u < 2; u++) {
+                        const int i = 2 * tid + u;
+                        if (i < np) {
+                            const int off = ex + (u ? len[0] : 0);
+                            sh.P[i] = off;
+                            sh.D[i] = rb[u] - off;
+                        }
+                    }
+                    __syncthreads();
+                    const int W = sh.P[np];
+                    for (int x0 = 0; x0 < W; x0 += SOLO_THREADS * SOLO_CHUNK) {
+                        int vv[SOLO_CHUNK];
+#pragma unroll
+                        for (int c = 0; c < SOLO_CHUNK; c++) {
+                            const int x = x0 + c * SOLO_THREADS + tid;
+                            vv[c] = -1;
+                            if (x < W) {
+                                int lo = 0, hi = np - 1;  // last row with P[row] <= x
+                                while (lo < hi) {
+                                    const int mid = (lo + hi + 1) >> 1;
+                                    if (sh.P[mid] <= x) lo = mid;
+                                    else hi = mid - 1;
+                                }
+                                vv[c] = a.sadj[sh.D[lo] + x];
+                                if (vv[c] >= ns) {
+                                    atomicExch(&a.ctl[C_ERR], 5);
+                                    vv[c] = -1;
+                                }
+                            }
+                        }
+                        solo_decrement(sh, vv, k, fn, cn);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 2; u++) {
+                        if (gid[u] >= 0) {
+                            a.rnd[gid[u]] = r;
+                            a.core[gid[u]] = k;
+                        }
+                    }
+                    __syncthreads();  // P and D are rewritten by the next pass
+                }
+            }
+            r++;
+            rounds++;
+        }
+        if (bad) break;
+    }
+    if (tid == 0) {
+        if (bad) atomicExch(&a.ctl[C_ERR], 2);
+        a.ctl[C_ROUNDS] = rounds;
+        a.ctl[C_ALPHA] = k;
+    }
+}
+
+static void launch_solo(const SoloArgs& sa, cudaStream_t s) {
+    const int smem = (int)sizeof(SoloShared);
+    FOLTY_CUDA(cudaFuncSetAttribute(k_peel_solo, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    FOLTY_LAUNCH(k_peel_solo, 1, SOLO_THREADS, smem, s, sa);
 }
 
 __global__ void k_iota(int32_t* __restrict__ a, int64_t n) {
@@ -1074,14 +1506,14 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
 
     // ---------------- A1: canonical order
     const int nb = bit_length((uint64_t)(n > 1 ? n - 1 : 1));
-    const int key_bits = 2 * nb + 1;
+    const int key_bits = n > 1 ? bit_length((uint64_t)n * (uint64_t)(n - 1)) : 1;  // keys < n (n - 1)
     const uint64_t loop_key = (key_bits >= 64) ? ~0ull : ((1ull << key_bits) - 1);
     const int64_t mk = g->m_kept;
     uint64_t* key = sc.get<uint64_t>(m);
     uint64_t* key_alt = sc.get<uint64_t>(m);
     uint32_t* val = sc.get<uint32_t>(m);
     uint32_t* val_alt = sc.get<uint32_t>(m);
-    FOLTY_LAUNCH(k_build_keys, grid_for(m, T), T, 0, s, g->in_src, g->in_dst, m, nb, loop_key, key, val);
+    FOLTY_LAUNCH(k_build_keys, grid_for(m, T), T, 0, s, g->in_src, g->in_dst, m, n, loop_key, key, val);
     uint64_t* skey = key;
     uint32_t* sval = val;
     if (!g->info.time_sorted && m > 1) {
@@ -1132,7 +1564,8 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     g->eb = graph_alloc<int32_t>(g, S, s);
     g->seg = graph_alloc<int32_t>(g, 2 * (int64_t)S + 1, s);
     if (mk > 0) {
-        FOLTY_LAUNCH(k_segments, grid_for(mk, T), T, 0, s, skey, newpair, pscan, mk, nb, g->sd, g->ea, g->eb, g->seg);
+        FOLTY_LAUNCH(k_segments, grid_for(mk, T), T, 0, s, skey, newpair, pscan, mk, g->sd, g->seg);
+        FOLTY_LAUNCH(k_pair_ends, grid_for(S, T), T, 0, s, skey, g->seg, S, n, g->ea, g->eb);
         FOLTY_LAUNCH(k_segments_split, grid_for(mk, T), T, 0, s, g->sd, mk, S, g->seg);
         FOLTY_LAUNCH(k_segments_fix, grid_for(S, T), T, 0, s, S, mk, g->seg);
     } else {
@@ -1251,9 +1684,31 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
             exclusive_scan(sc, d0, eoff, tn);
             FOLTY_LAUNCH(k_tail_fill, grid_for(2 * (int64_t)S, T), T, 0, s, L, eoff, tn, rowptr, adj, rnd, gmap,
                          lrow, ld, fillc, ladj, pa.ctl + C_ERR);
-            TailArgs ta{nl, L, ld, lrow, ladj, rnd, core, pa.ctl};
+            // single-CTA phase for the last SOLO_CAP vertices (does nothing unless the
+            // cluster hands off)
+            int* ns = sc.get<int>(1);
+            int32_t* slist = sc.get<int32_t>(SOLO_CAP);
+            int32_t* sdeg = sc.get<int32_t>(SOLO_CAP + 1);
+            int32_t* srow = sc.get<int32_t>(SOLO_CAP + 1);
+            int32_t* dl = sc.get<int32_t>(SOLO_CAP + 1);
+            int32_t* eo = sc.get<int32_t>(SOLO_CAP + 1);
+            int32_t* fc = sc.get<int32_t>(SOLO_CAP);
+            int32_t* sgid = sc.get<int32_t>(SOLO_CAP);
+            int32_t* map2 = sc.get<int32_t>(tn);
+            uint16_t* sadj = sc.get<uint16_t>(2 * (int64_t)S);
+            FOLTY_CUDA(cudaMemsetAsync(ns, 0, sizeof(int), s));
+            FOLTY_CUDA(cudaMemsetAsync(sdeg, 0, sizeof(int32_t) * (SOLO_CAP + 1), s));
+            FOLTY_CUDA(cudaMemsetAsync(fc, 0, sizeof(int32_t) * SOLO_CAP, s));
+            FOLTY_CUDA(cudaMemsetAsync(map2, 0xff, sizeof(int32_t) * (size_t)tn, s));
+            TailArgs ta{nl, L, ld, lrow, ladj, rnd, core, pa.ctl, SOLO_CAP, ns, slist, sdeg, map2};
             if (tail_c == 16) launch_tail<16>(ta, s);
             else launch_tail<8>(ta, s);
+            FOLTY_LAUNCH(k_solo_rows, grid_for(SOLO_CAP, T), T, 0, s, pa.ctl, ns, slist, lrow, L, dl, sgid);
+            exclusive_scan(sc, sdeg, srow, SOLO_CAP);
+            exclusive_scan(sc, dl, eo, SOLO_CAP);
+            FOLTY_LAUNCH(k_solo_fill, grid_for(2 * (int64_t)S, T), T, 0, s, pa.ctl, eo, slist, sdeg, srow, lrow, ladj,
+                         map2, fc, sadj, pa.ctl + C_ERR);
+            launch_solo(SoloArgs{ns, sdeg, fc, srow, sadj, sgid, rnd, core, pa.ctl}, s);
         }
         peel_ctl = pa.ctl;  // rounds, alpha and the error word are read with the triangle totals
     }
@@ -1292,7 +1747,10 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         int64_t outv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         read_back(g, ptrs, sizes, peel_ctl ? 8 : 5, outv, s);  // no peeling state for n = 0
         if (outv[5] == 1) fail(FOLTY_ETIMEOUT, "peeling: a grid barrier wait ran out");
-        if (outv[5] != 0) fail(FOLTY_ECUDA, "peeling: a vertex list overflowed (internal error)");
+        if (outv[5] != 0)
+            fail(FOLTY_ECUDA, "peeling: internal error " + std::to_string(outv[5]) +
+                                  " (2: a vertex list overflowed, 3/4: a subgraph row count differs, 5: a row entry "
+                                  "is out of range)");
         g->info.peel_rounds = (int32_t)outv[6];
         g->info.degeneracy = (int32_t)outv[7];
         g->ntri = outv[0];
