@@ -1030,7 +1030,8 @@ static void launch_tail(const TailArgs& ta, cudaStream_t s) {
 constexpr int SOLO_THREADS = 1024;
 constexpr int SOLO_CAP = 12288;  // vertices of the single-CTA phase
 constexpr int SOLO_PASS = 2048;  // frontier vertices laid out per pass (2 per thread)
-constexpr int SOLO_CHUNK = 8;    // adjacency entries per thread with loads in flight together
+constexpr int SOLO_CHUNK = 8;    // adjacency entries per thread in flight together (large frontiers)
+constexpr int SOLO_CHUNK_S = 2;  // the same for small frontiers (W <= 2048 in one step; less code)
 
 // Cluster row length and global id of each exported vertex (0 past the exported count).
 __global__ void k_solo_rows(const int* __restrict__ ctl, const int* __restrict__ ns_p,
@@ -1090,16 +1091,30 @@ struct SoloArgs {
     int* ctl;
 };
 
+// Once at most BM_CAP vertices are left, their induced subgraph moves into shared memory
+// as a bit matrix (row v, bit u: edge v-u), so that a round reads no global memory.
+constexpr int BM_CAP = 960;
+constexpr int BM_W = BM_CAP / 32;  // words per row
+
 struct SoloShared {
-    int32_t deg[SOLO_CAP];
-    int32_t rs[SOLO_CAP + 1];
-    uint16_t FL[2][SOLO_CAP];  // frontier by round parity
-    int32_t P[SOLO_PASS + 1];  // prefix of the row lengths of one pass of a large frontier
-    int32_t D[SOLO_PASS];      // row start - P: adjacency index of flat entry x is D[o] + x
     int cnt[3];                // frontier sizes, rotating over three rounds
     int smin[2];               // smallest degree above the level, by level parity
+    int acnt[2];               // vertices alive at the level start, by level parity
     int wsum[SOLO_THREADS / 32];
+    int sx[32], sb[32];        // small frontier: exclusive prefix of row lengths, row start - prefix
+    int sW;                    // small frontier: total row length
+    int32_t rs[SOLO_CAP + 1];
+    uint16_t FL[2][SOLO_CAP];  // frontier by round parity; FL[0] / FL[1] hold the bit-matrix phase's
+                               // id map / its small arrays
+    int32_t P[SOLO_PASS + 1];  // prefix of the row lengths of one pass of a large frontier
+    int32_t D[SOLO_PASS];      // row start - P: adjacency index of flat entry x is D[o] + x
+    union {
+        int32_t deg[SOLO_CAP];
+        uint32_t bm[BM_CAP * BM_W];  // bit-matrix phase (replaces deg)
+    } u;
 };
+static_assert(sizeof(SoloShared) <= 232448, "single-CTA phase exceeds the shared memory of a CTA");
+static_assert(4 * BM_CAP * 2 + 2 * BM_CAP * 3 <= 2 * SOLO_CAP, "bit-matrix phase arrays fit one frontier list");
 
 constexpr int SOLO_SLOTS = SOLO_CAP / SOLO_THREADS;  // vertices each thread checks at level starts
 static_assert(SOLO_CAP % SOLO_THREADS == 0 && SOLO_SLOTS <= 32, "level-start slots fit one mask word");
@@ -1119,21 +1134,166 @@ __device__ __forceinline__ void solo_append(bool pred, int v, uint16_t* fl, int*
     if (pred && at < SOLO_CAP) fl[at] = (uint16_t)v;
 }
 
-// The same append for one thread alone (no warp-wide step).
-__device__ __forceinline__ void solo_push(int v, uint16_t* fl, int* cnt) {
+// The same append for one thread alone (no warp-wide step), into a list of cap entries.
+__device__ __forceinline__ void solo_push(int v, uint16_t* fl, int* cnt, int cap = SOLO_CAP) {
     const int at = atomicAdd(cnt, 1);
-    if (at < SOLO_CAP) fl[at] = (uint16_t)v;
+    if (at < cap) fl[at] = (uint16_t)v;
 }
 
 // Neighbours vv[0..N) (negative: none) lose one degree each at level k; a k + 1 -> k
-// crossing files the vertex in the next frontier. The whole warp must call it.
+// crossing files the vertex in the next frontier. Only the first nch items can hold
+// neighbours; nch must be the same across the warp, which must call it whole.
 template <int N>
-__device__ __forceinline__ void solo_decrement(SoloShared& sh, const int (&vv)[N], int k, uint16_t* fn, int* cn) {
+__device__ __forceinline__ void solo_decrement(SoloShared& sh, const int (&vv)[N], int nch, int k, uint16_t* fn,
+                                               int* cn) {
     int old[N];
 #pragma unroll
-    for (int c = 0; c < N; c++) old[c] = vv[c] >= 0 ? atomicSub(&sh.deg[vv[c]], 1) : 0;
+    for (int c = 0; c < N; c++) old[c] = vv[c] >= 0 ? atomicSub(&sh.u.deg[vv[c]], 1) : 0;
 #pragma unroll
-    for (int c = 0; c < N; c++) solo_append(vv[c] >= 0 && old[c] == k + 1, vv[c], fn, cn);
+    for (int c = 0; c < N; c++)
+        if (c < nch) solo_append(vv[c] >= 0 && old[c] == k + 1, vv[c], fn, cn);
+}
+
+// The last levels on the bit matrix. At entry every thread's mask lists its alive slots
+// (degree > k) at the start of level k + 1, n3 <= BM_CAP of them in all; the level starts
+// again here. New ids 0..n3-1 follow the slots in thread order; FL[0] maps slot -> new
+// id while the matrix is built, FL[1] holds the new ids' degrees, global ids, frontier
+// lists and slots. A round hands each frontier vertex to one warp, whose lanes each take
+// one 32-bit word of its row and decrement the degree of every neighbour in it.
+__device__ __forceinline__ void bm_phase(SoloShared& sh, const SoloArgs& a, int ns, int n3, unsigned mine, int& k,
+                                         int& r, int& rounds, int& lvl, int& steps, bool& bad) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr uint16_t NONE = 0xffff;
+    uint16_t* map = sh.FL[0];
+    int32_t* deg3 = reinterpret_cast<int32_t*>(sh.FL[1]);
+    int32_t* gid3 = deg3 + BM_CAP;
+    uint16_t* fl3 = reinterpret_cast<uint16_t*>(gid3 + BM_CAP);  // two lists of BM_CAP
+    uint16_t* n2o = fl3 + 2 * BM_CAP;
+    // ---- new ids: block-wide exclusive prefix of the alive slot counts
+    for (int i = tid; i < SOLO_CAP; i += SOLO_THREADS) map[i] = NONE;
+    const int mc = __popc(mine);
+    int inc = mc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    __syncthreads();  // the level start's reads of wsum and the frontier counts are done
+    if (lane == 31) sh.wsum[warp] = inc;
+    if (tid == 0) {
+        sh.cnt[(r + 1) % 3] = 0;  // the frontier filed by the level start is dropped
+        sh.smin[lvl & 1] = INT_MAX;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int w = sh.wsum[lane];
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        sh.wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    int id = sh.wsum[warp] + inc - mc;
+    for (unsigned m = mine; m; m &= m - 1) {
+        const int i = tid + (__ffs(m) - 1) * SOLO_THREADS;
+        if (id < BM_CAP) {
+            map[i] = (uint16_t)id;
+            n2o[id] = (uint16_t)i;
+            deg3[id] = sh.u.deg[i];
+            gid3[id] = a.sgid[i];
+        }
+        id++;
+    }
+    __syncthreads();
+    // ---- the matrix (it overlays the degrees just copied)
+    for (int w = tid; w < BM_CAP * BM_W; w += SOLO_THREADS) sh.u.bm[w] = 0;
+    __syncthreads();
+    for (int v = warp; v < n3; v += SOLO_THREADS / 32) {
+        const int o = n2o[v];
+        const int b = sh.rs[o], e = sh.rs[o + 1];
+        for (int j0 = b; j0 < e; j0 += 8 * 32) {
+            int nb[8];
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                const int j = j0 + t * 32 + lane;
+                nb[t] = j < e ? a.sadj[j] : -1;
+            }
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                if (nb[t] < 0 || nb[t] >= ns) continue;
+                const int u = map[nb[t]];
+                if (u != NONE) atomicOr(&sh.u.bm[v * BM_W + (u >> 5)], 1u << (u & 31));
+            }
+        }
+    }
+    // ---- levels and rounds on the matrix
+    while (true) {
+        __syncthreads();
+        uint16_t* fs = fl3 + ((r + 1) & 1) * BM_CAP;
+        int* cs = &sh.cnt[(r + 1) % 3];
+        int kk = k + 1, lmin = INT_MAX;
+        if (tid < n3) {
+            const int d = deg3[tid];
+            if (d > k) {
+                if (d <= kk) solo_push(tid, fs, cs, BM_CAP);
+                else lmin = d;
+            }
+        }
+        lmin = __reduce_min_sync(0xffffffffu, lmin);
+        if (lane == 0 && lmin != INT_MAX) atomicMin(&sh.smin[lvl & 1], lmin);
+        __syncthreads();
+        const int c0 = *cs, m0 = sh.smin[lvl & 1];
+        if (tid == 0) sh.smin[(lvl + 1) & 1] = INT_MAX;
+        if (++steps > 2 * ns + 2 || c0 > BM_CAP) {
+            bad = true;
+            return;
+        }
+        if (c0 == 0) {
+            if (m0 == INT_MAX) return;  // nothing left
+            kk = m0;
+            __syncthreads();  // every thread has read c0 before the jump appends
+            if (tid < n3) {
+                const int d = deg3[tid];
+                if (d > k && d <= kk) solo_push(tid, fs, cs, BM_CAP);
+            }
+        }
+        k = kk;
+        r += 1;
+        lvl++;
+        while (true) {
+            __syncthreads();  // the round's frontier is complete
+            const int nL = sh.cnt[r % 3];
+            if (tid == 0) sh.cnt[(r + 2) % 3] = 0;
+            if (nL == 0) break;
+            if (++steps > 2 * ns + 2 || nL > BM_CAP) {
+                bad = true;
+                return;
+            }
+            const uint16_t* fl = fl3 + (r & 1) * BM_CAP;
+            uint16_t* fn = fl3 + ((r + 1) & 1) * BM_CAP;
+            int* cn = &sh.cnt[(r + 1) % 3];
+            for (int i = warp; i < nL; i += SOLO_THREADS / 32) {
+                const int v = fl[i];
+                if (lane < BM_W) {
+                    unsigned w = sh.u.bm[v * BM_W + lane];
+                    while (w) {
+                        const int u = lane * 32 + __ffs(w) - 1;
+                        w &= w - 1;
+                        if (atomicSub(&deg3[u], 1) == k + 1) solo_push(u, fn, cn, BM_CAP);
+                    }
+                }
+                if (lane == 0) {
+                    a.rnd[gid3[v]] = r;
+                    a.core[gid3[v]] = k;
+                }
+            }
+            r++;
+            rounds++;
+        }
+    }
 }
 
 // The same peeling once more (levels, rounds, k + 1 -> k crossings), continuing the level
@@ -1154,7 +1314,7 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
     int miscount = 0;
     for (int i = tid; i <= ns; i += SOLO_THREADS) {
         if (i < ns) {
-            sh.deg[i] = a.sdeg[i];
+            sh.u.deg[i] = a.sdeg[i];
             miscount |= a.fc[i] != a.sdeg[i];
         }
         sh.rs[i] = a.srow[i];
@@ -1163,8 +1323,12 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
     for (int j = 0; j < SOLO_SLOTS; j++)
         if (tid + j * SOLO_THREADS < ns) mine |= 1u << j;
     if (tid < 3) sh.cnt[tid] = 0;
-    if (tid < 2) sh.smin[tid] = INT_MAX;
+    if (tid < 2) {
+        sh.smin[tid] = INT_MAX;
+        sh.acnt[tid] = 0;
+    }
     int k = a.ctl[C_SOLO_K], r = a.ctl[C_SOLO_R], rounds = a.ctl[C_ROUNDS], lvl = 0;
+    int n3 = 0;  // vertices handed to the bit-matrix phase
     // every level and every round removes at least one vertex: more than 2 ns + 2 steps
     // (or a frontier above SOLO_CAP) can only come from an internal error
     int steps = 0;
@@ -1178,30 +1342,45 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
         // r + 1 (r is the empty round that ended the last level, or the hand-off round)
         uint16_t* fs = sh.FL[(r + 1) & 1];
         int* cs = &sh.cnt[(r + 1) % 3];
-        int kk = k + 1, lmin = INT_MAX;
+        int kk = k + 1, lmin = INT_MAX, na = 0;
         for (unsigned m = mine; m; m &= m - 1) {
             const int j = __ffs(m) - 1, i = tid + j * SOLO_THREADS;
-            const int d = sh.deg[i];
-            if (d <= k) mine &= ~(1u << j);  // left at an earlier level
-            else if (d <= kk) solo_push(i, fs, cs);
+            const int d = sh.u.deg[i];
+            if (d <= k) {
+                mine &= ~(1u << j);  // left at an earlier level
+                continue;
+            }
+            na++;
+            if (d <= kk) solo_push(i, fs, cs);
             else lmin = min(lmin, d);
         }
         lmin = __reduce_min_sync(0xffffffffu, lmin);
-        if (lane == 0 && lmin != INT_MAX) atomicMin(&sh.smin[lvl & 1], lmin);
+        na = __reduce_add_sync(0xffffffffu, na);
+        if (lane == 0) {
+            if (lmin != INT_MAX) atomicMin(&sh.smin[lvl & 1], lmin);
+            if (na) atomicAdd(&sh.acnt[lvl & 1], na);
+        }
         __syncthreads();
-        const int c0 = *cs, m0 = sh.smin[lvl & 1];
-        if (tid == 0) sh.smin[(lvl + 1) & 1] = INT_MAX;  // last read at the previous level start
+        const int c0 = *cs, m0 = sh.smin[lvl & 1], alive = sh.acnt[lvl & 1];
+        if (tid == 0) {  // both last read at the previous level start
+            sh.smin[(lvl + 1) & 1] = INT_MAX;
+            sh.acnt[(lvl + 1) & 1] = 0;
+        }
         if (++steps > 2 * ns + 2 || c0 > SOLO_CAP) {
             bad = true;
             break;
         }
+        if (c0 == 0 && m0 == INT_MAX) break;  // nothing left
+        if (alive <= BM_CAP) {  // the rest fits the bit matrix (this level starts again there)
+            n3 = alive;
+            break;
+        }
         if (c0 == 0) {
-            if (m0 == INT_MAX) break;  // nothing left
             kk = m0;                   // jump to the smallest remaining degree
             __syncthreads();           // every thread has read c0 before the jump appends
             for (unsigned m = mine; m; m &= m - 1) {
                 const int i = tid + (__ffs(m) - 1) * SOLO_THREADS;
-                if (sh.deg[i] <= kk) solo_push(i, fs, cs);  // every kept slot has degree > k + 1
+                if (sh.u.deg[i] <= kk) solo_push(i, fs, cs);  // every kept slot has degree > k + 1
             }
         }
         k = kk;
@@ -1221,45 +1400,47 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
             uint16_t* fn = sh.FL[(r + 1) & 1];
             int* cn = &sh.cnt[(r + 1) % 3];
             if (nL <= 32) {
-                // lane o holds frontier vertex o: row start, length, exclusive prefix
-                const bool have = lane < nL;
-                const int q = have ? fl[lane] : 0;
-                const int rb = have ? sh.rs[q] : 0;
-                const int len = have ? sh.rs[q + 1] - rb : 0;
-                int inc = len;
+                // warp 0 lays the (at most 32) rows out: lane o holds frontier vertex o
+                int gid = -1;
+                if (warp == 0) {
+                    const bool have = lane < nL;
+                    const int q = have ? fl[lane] : 0;
+                    const int rb = have ? sh.rs[q] : 0;
+                    const int len = have ? sh.rs[q + 1] - rb : 0;
+                    if (have) gid = a.sgid[q];
+                    int inc = len;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, inc, o);
-                    if (lane >= o) inc += y;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += y;
+                    }
+                    sh.sx[lane] = inc - len;
+                    sh.sb[lane] = rb - (inc - len);
+                    if (lane == 31) sh.sW = inc;
                 }
-                const int ex = inc - len;
-                const int W = __shfl_sync(0xffffffffu, inc, 31);
-                const int gid = (warp == 0 && have) ? a.sgid[q] : -1;
-                for (int x0 = 0; x0 < W; x0 += SOLO_THREADS * SOLO_CHUNK) {
-                    const int nch = min(SOLO_CHUNK, (W - x0 + SOLO_THREADS - 1) / SOLO_THREADS);  // block-uniform
-                    int vv[SOLO_CHUNK];
+                __syncthreads();
+                const int W = sh.sW;
+                for (int x0 = 0; x0 < W; x0 += SOLO_THREADS * SOLO_CHUNK_S) {
+                    const int nch = min(SOLO_CHUNK_S, (W - x0 + SOLO_THREADS - 1) / SOLO_THREADS);  // block-uniform
+                    int vv[SOLO_CHUNK_S];
 #pragma unroll
-                    for (int c = 0; c < SOLO_CHUNK; c++) {
-                        vv[c] = -1;
-                        if (c >= nch) continue;
+                    for (int c = 0; c < SOLO_CHUNK_S; c++) {
                         const int x = x0 + c * SOLO_THREADS + tid;
-                        int lo = 0;  // last row o < nL with ex_o <= x
+                        vv[c] = -1;
+                        if (c < nch && x < W) {
+                            int lo = 0;  // last row o < nL with sx[o] <= x
 #pragma unroll
-                        for (int st = 16; st > 0; st >>= 1) {
-                            const int mid = lo + st;
-                            const int em = __shfl_sync(0xffffffffu, ex, mid);
-                            if (mid < nL && em <= x) lo = mid;
-                        }
-                        const int base = __shfl_sync(0xffffffffu, rb, lo) - __shfl_sync(0xffffffffu, ex, lo);
-                        if (x < W) {
-                            vv[c] = a.sadj[base + x];
+                            for (int st = 16; st > 0; st >>= 1)
+                                if (lo + st < nL && sh.sx[lo + st] <= x) lo += st;
+                            vv[c] = a.sadj[sh.sb[lo] + x];
                             if (vv[c] >= ns) {  // cannot happen for rows k_solo_fill checked
                                 atomicExch(&a.ctl[C_ERR], 5);
                                 vv[c] = -1;
                             }
                         }
                     }
-                    solo_decrement(sh, vv, k, fn, cn);
+                    // a warp whose entries all lie beyond W has nothing to decrement
+                    solo_decrement(sh, vv, x0 + warp * 32 < W ? nch : 0, k, fn, cn);
                 }
                 if (gid >= 0) {
                     a.rnd[gid] = r;
@@ -1317,12 +1498,13 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
                     __syncthreads();
                     const int W = sh.P[np];
                     for (int x0 = 0; x0 < W; x0 += SOLO_THREADS * SOLO_CHUNK) {
+                        const int nch = min(SOLO_CHUNK, (W - x0 + SOLO_THREADS - 1) / SOLO_THREADS);
                         int vv[SOLO_CHUNK];
 #pragma unroll
                         for (int c = 0; c < SOLO_CHUNK; c++) {
                             const int x = x0 + c * SOLO_THREADS + tid;
                             vv[c] = -1;
-                            if (x < W) {
+                            if (c < nch && x < W) {
                                 int lo = 0, hi = np - 1;  // last row with P[row] <= x
                                 while (lo < hi) {
                                     const int mid = (lo + hi + 1) >> 1;
@@ -1336,7 +1518,7 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
                                 }
                             }
                         }
-                        solo_decrement(sh, vv, k, fn, cn);
+                        solo_decrement(sh, vv, nch, k, fn, cn);
                     }
 #pragma unroll
                     for (int u = 0; u < 2; u++) {
@@ -1353,6 +1535,7 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
         }
         if (bad) break;
     }
+    if (n3 > 0 && !bad) bm_phase(sh, a, ns, n3, mine, k, r, rounds, lvl, steps, bad);
     if (tid == 0) {
         if (bad) atomicExch(&a.ctl[C_ERR], 2);
         a.ctl[C_ROUNDS] = rounds;
