@@ -1275,17 +1275,24 @@ __device__ __forceinline__ void bm_phase(SoloShared& sh, const SoloArgs& a, int 
             const uint16_t* fl = fl3 + (r & 1) * BM_CAP;
             uint16_t* fn = fl3 + ((r + 1) & 1) * BM_CAP;
             int* cn = &sh.cnt[(r + 1) % 3];
-            for (int i = warp; i < nL; i += SOLO_THREADS / 32) {
+            // 32 S threads per frontier vertex (S = 4, 2, 1 as the frontier grows): thread t
+            // takes bits [(t / 32) 32 / S, (t / 32 + 1) 32 / S) of word t % 32 of the row, so
+            // that a small frontier spreads its decrements over more lanes
+            const int S = nL <= 8 ? 4 : nL <= 16 ? 2 : 1;
+            const int per = 32 * S, bits = 32 / S;
+            const int sub = tid % per, wd = sub & 31;
+            const unsigned slice = S == 1 ? 0xffffffffu : (((1u << bits) - 1u) << ((sub >> 5) * bits));
+            for (int i = tid / per; i < nL; i += SOLO_THREADS / per) {
                 const int v = fl[i];
-                if (lane < BM_W) {
-                    unsigned w = sh.u.bm[v * BM_W + lane];
+                if (wd < BM_W) {
+                    unsigned w = sh.u.bm[v * BM_W + wd] & slice;
                     while (w) {
-                        const int u = lane * 32 + __ffs(w) - 1;
+                        const int u = wd * 32 + __ffs(w) - 1;
                         w &= w - 1;
                         if (atomicSub(&deg3[u], 1) == k + 1) solo_push(u, fn, cn, BM_CAP);
                     }
                 }
-                if (lane == 0) {
+                if (sub == 0) {
                     a.rnd[gid3[v]] = r;
                     a.core[gid3[v]] = k;
                 }
@@ -1421,6 +1428,7 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
                 __syncthreads();
                 const int W = sh.sW;
                 for (int x0 = 0; x0 < W; x0 += SOLO_THREADS * SOLO_CHUNK_S) {
+                    if (x0 + warp * 32 >= W) break;  // nothing left for this warp (warp-uniform)
                     const int nch = min(SOLO_CHUNK_S, (W - x0 + SOLO_THREADS - 1) / SOLO_THREADS);  // block-uniform
                     int vv[SOLO_CHUNK_S];
 #pragma unroll
@@ -1439,8 +1447,7 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
                             }
                         }
                     }
-                    // a warp whose entries all lie beyond W has nothing to decrement
-                    solo_decrement(sh, vv, x0 + warp * 32 < W ? nch : 0, k, fn, cn);
+                    solo_decrement(sh, vv, nch, k, fn, cn);
                 }
                 if (gid >= 0) {
                     a.rnd[gid] = r;
@@ -1498,6 +1505,7 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
                     __syncthreads();
                     const int W = sh.P[np];
                     for (int x0 = 0; x0 < W; x0 += SOLO_THREADS * SOLO_CHUNK) {
+                        if (x0 + warp * 32 >= W) break;  // nothing left for this warp (warp-uniform)
                         const int nch = min(SOLO_CHUNK, (W - x0 + SOLO_THREADS - 1) / SOLO_THREADS);
                         int vv[SOLO_CHUNK];
 #pragma unroll
