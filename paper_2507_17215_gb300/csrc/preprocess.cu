@@ -340,14 +340,70 @@ constexpr int PEEL_SHORT = 32;      // rows up to this length are walked by one 
 constexpr int PEEL_CHUNK = 8;       // PEEL_CHUNK entries at a time
 constexpr int PEEL_HEAVY = 128;     // vertices above this degree go to the heavy frontier
 constexpr int PEEL_PIECE = PEEL_THREADS;  // adjacency entries per heavy piece
+constexpr int PEEL_BUF = 4096;            // entries of each block-local append buffer
+
+// Block-local staging of list appends: warps append into shared memory (one shared-memory
+// atomic per warp) and peel_flush moves a phase's entries to the global list with one
+// global atomic per block, instead of one contended global atomic per warp. Entries
+// beyond PEEL_BUF go to the global list directly.
+struct PeelBuf {
+    int32_t* fr;  // light-frontier entries
+    int32_t* al;  // alive-list entries
+    int* n;       // n[0], n[1]: entries staged in fr, al; n[2]: removals counted; n[3], n[4]: bases
+};
+
+// Appends v for every lane with pred set to the block's buffer sbuf (count *scnt), or past
+// its capacity to the global list (out, counter, cap). The whole warp must call it.
+__device__ __forceinline__ void buf_append(bool pred, int32_t v, int32_t* sbuf, int* scnt, int32_t* out,
+                                           int* counter, int cap, int* err) {
+    const unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(scnt, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    const int idx = base + __popc(m & ((1u << lane) - 1u));
+    if (pred && idx < PEEL_BUF) sbuf[idx] = v;
+    warp_append(pred && idx >= PEEL_BUF, v, out, counter, cap, err);
+}
+
+// Moves the block's staged entries to the global lists and its removal count to rm_cnt
+// (null when the phase counts none); every thread of the block calls it after its last
+// append of the phase. A list never holds more than cap entries: an entry beyond is
+// dropped and recorded in *err.
+__device__ __forceinline__ void peel_flush(PeelBuf pb, int32_t* fr_out, int* fr_cnt, int32_t* al_out, int* al_cnt,
+                                           int* rm_cnt, int cap, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nf = min(pb.n[0], PEEL_BUF), na = min(pb.n[1], PEEL_BUF);
+        pb.n[3] = nf ? atomicAdd(fr_cnt, nf) : 0;
+        pb.n[4] = na ? atomicAdd(al_cnt, na) : 0;
+        if (pb.n[2]) atomicAdd(rm_cnt, pb.n[2]);
+    }
+    __syncthreads();
+    const int nf = min(pb.n[0], PEEL_BUF), na = min(pb.n[1], PEEL_BUF);
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+        const int idx = pb.n[3] + i;
+        if (idx < cap) fr_out[idx] = pb.fr[i];
+        else atomicExch(err, 2);
+    }
+    for (int i = threadIdx.x; i < na; i += blockDim.x) {
+        const int idx = pb.n[4] + i;
+        if (idx < cap) al_out[idx] = pb.al[i];
+        else atomicExch(err, 2);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) pb.n[0] = pb.n[1] = pb.n[2] = 0;
+}
 
 // Files vertex v (removed at round rr) in the frontier of round rr: light vertices as
-// themselves, heavy ones as their PEEL_PIECE-entry pieces of adjacency. The whole warp
-// must call it; b, e = v's row bounds.
-__device__ __forceinline__ void frontier_append(const PeelArgs& a, bool in, int32_t v, int32_t b, int32_t e,
-                                                int rr) {
+// themselves (staged in the block's buffer), heavy ones as their PEEL_PIECE-entry pieces
+// of adjacency. The whole warp must call it; b, e = v's row bounds.
+__device__ __forceinline__ void frontier_append(const PeelArgs& a, const PeelBuf& pb, bool in, int32_t v, int32_t b,
+                                                int32_t e, int rr) {
     const bool heavy = in && (e - b > PEEL_HEAVY);
-    warp_append(in && !heavy, v, (rr & 1) ? a.fr[1] : a.fr[0], &a.ctl[C_FCNT + rr % 3], a.n, &a.ctl[C_ERR]);
+    buf_append(in && !heavy, v, pb.fr, &pb.n[0], (rr & 1) ? a.fr[1] : a.fr[0], &a.ctl[C_FCNT + rr % 3], a.n,
+               &a.ctl[C_ERR]);
     if (heavy) {
         const int np = (e - b + PEEL_PIECE - 1) / PEEL_PIECE;
         const int base = atomicAdd(&a.ctl[C_HCNT + rr % 3], np);
@@ -364,7 +420,8 @@ __device__ __forceinline__ void frontier_append(const PeelArgs& a, bool in, int3
 // crosses k + 1 -> k joins round r + 1. A vertex that already left never crosses again
 // (its degree was <= k when it left and only falls), so no liveness test is needed.
 // The whole warp must call it.
-__device__ __forceinline__ void peel_neighbour(const PeelArgs& a, bool valid, int32_t j, int k, int r, int* rm) {
+__device__ __forceinline__ void peel_neighbour(const PeelArgs& a, const PeelBuf& pb, bool valid, int32_t j, int k,
+                                               int r) {
     bool cross = false;
     int32_t v = 0, b = 0, e = 0;
     if (valid) {
@@ -378,14 +435,15 @@ __device__ __forceinline__ void peel_neighbour(const PeelArgs& a, bool valid, in
             e = a.rowptr[v + 1];
         }
     }
-    warp_count(cross, rm);
-    frontier_append(a, cross, v, b, e, r + 1);
+    warp_count(cross, &pb.n[2]);
+    frontier_append(a, pb, cross, v, b, e, r + 1);
 }
 
 // Vertex v (valid when cross) crossed k + 1 -> k in round r: it leaves in round r + 1.
 // The whole warp must call it.
-__device__ __forceinline__ void peel_crossing(const PeelArgs& a, bool cross, int32_t v, int k, int r, int* rm) {
-    warp_count(cross, rm);
+__device__ __forceinline__ void peel_crossing(const PeelArgs& a, const PeelBuf& pb, bool cross, int32_t v, int k,
+                                              int r) {
+    warp_count(cross, &pb.n[2]);
     int32_t rb = 0, re = 0;
     if (cross) {
         a.rnd[v] = r + 1;
@@ -393,7 +451,7 @@ __device__ __forceinline__ void peel_crossing(const PeelArgs& a, bool cross, int
         rb = a.rowptr[v];
         re = a.rowptr[v + 1];
     }
-    frontier_append(a, cross, v, rb, re, r + 1);
+    frontier_append(a, pb, cross, v, rb, re, r + 1);
 }
 
 // Parallel Matula-Beck peeling. Level k = smallest remaining degree; within a level,
@@ -420,6 +478,11 @@ __global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
     const int64_t gwarp = gtid >> 5, nwarps = gsize >> 5;
     int* ctl = a.ctl;
     __shared__ int s_wmin[PEEL_THREADS / 32];
+    __shared__ int32_t s_fr[PEEL_BUF], s_al[PEEL_BUF];
+    __shared__ int s_n[5];
+    const PeelBuf pb{s_fr, s_al, s_n};
+    if (threadIdx.x < 5) s_n[threadIdx.x] = 0;
+    __syncthreads();
     int k = -1, r = 0, lvl = 0, ac = 0, rounds = 0;
     int nalive = a.n;
     while (true) {
@@ -472,8 +535,8 @@ __global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
                         }
                     }
                 }
-                frontier_append(a, in, v, rb, re, r + 1);
-                warp_append(keep, v, anxt, &ctl[C_ACNT + (lvl & 1)], a.n, &ctl[C_ERR]);
+                frontier_append(a, pb, in, v, rb, re, r + 1);
+                buf_append(keep, v, pb.al, &pb.n[1], anxt, &ctl[C_ACNT + (lvl & 1)], a.n, &ctl[C_ERR]);
             }
         }
 #pragma unroll
@@ -485,6 +548,8 @@ __global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
             for (int w = 0; w < PEEL_THREADS / 32; w++) bm = min(bm, s_wmin[w]);
             if (bm != INT_MAX) atomicMin(&ctl[C_MIN + (lvl & 1)], bm);
         }
+        peel_flush(pb, ((r + 1) & 1) ? a.fr[1] : a.fr[0], &ctl[C_FCNT + (r + 1) % 3], ac ? a.alive[0] : a.alive[1],
+                   &ctl[C_ACNT + (lvl & 1)], nullptr, a.n, &ctl[C_ERR]);
         if (!grid_barrier(ctl, a.timeout_ns)) return;
         r += 1;
         ac ^= 1;
@@ -511,10 +576,12 @@ __global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
                         a.core[v] = kj;
                     }
                 }
-                warp_count(in, &ctl[C_RM + (lvl & 1)]);
-                frontier_append(a, in, v, rb, re, r + 1);
+                warp_count(in, &pb.n[2]);
+                frontier_append(a, pb, in, v, rb, re, r + 1);
             }
             k = kj;
+            peel_flush(pb, ((r + 1) & 1) ? a.fr[1] : a.fr[0], &ctl[C_FCNT + (r + 1) % 3], nullptr, nullptr,
+                       &ctl[C_RM + (lvl & 1)], a.n, &ctl[C_ERR]);
             if (!grid_barrier(ctl, a.timeout_ns)) return;
             r += 1;
         } else {
@@ -551,7 +618,7 @@ __global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
                     for (int t = 0; t < PEEL_CHUNK; t++) old[t] = (v[t] >= 0) ? atomicSub(&a.deg[v[t]], 1) : 0;
 #pragma unroll
                     for (int t = 0; t < PEEL_CHUNK; t++)
-                        peel_crossing(a, v[t] >= 0 && old[t] == k + 1, v[t], k, r, &ctl[C_RM + (lvl & 1)]);
+                        peel_crossing(a, pb, v[t] >= 0 && old[t] == k + 1, v[t], k, r);
                 }
                 unsigned mm = __ballot_sync(0xffffffffu, have && !shortrow);
                 while (mm) {
@@ -569,7 +636,7 @@ __global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
 #pragma unroll
                     for (int q = 0; q < Q; q++) old[q] = (v[q] >= 0) ? atomicSub(&a.deg[v[q]], 1) : 0;
 #pragma unroll
-                    for (int q = 0; q < Q; q++) peel_crossing(a, v[q] >= 0 && old[q] == k + 1, v[q], k, r, &ctl[C_RM + (lvl & 1)]);
+                    for (int q = 0; q < Q; q++) peel_crossing(a, pb, v[q] >= 0 && old[q] == k + 1, v[q], k, r);
                 }
             }
             // heavy vertices: one block per piece of PEEL_PIECE adjacency entries
@@ -579,8 +646,10 @@ __global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
                 const int32_t u = (int32_t)(hp & 0xffffffffll);
                 const int32_t q = (int32_t)(hp >> 32);
                 const int32_t j = a.rowptr[u] + q * PEEL_PIECE + (int32_t)threadIdx.x;
-                peel_neighbour(a, j < a.rowptr[u + 1], j, k, r, &ctl[C_RM + (lvl & 1)]);
+                peel_neighbour(a, pb, j < a.rowptr[u + 1], j, k, r);
             }
+            peel_flush(pb, ((r + 1) & 1) ? a.fr[1] : a.fr[0], &ctl[C_FCNT + (r + 1) % 3], nullptr, nullptr,
+                       &ctl[C_RM + (lvl & 1)], a.n, &ctl[C_ERR]);
             if (!grid_barrier(ctl, a.timeout_ns)) return;
             r++;
             rounds++;
