@@ -197,6 +197,8 @@ void exclusive_scan(Scratch& sc, const uint32_t* in, uint32_t* out, int64_t n);
 // leaves the output unusable: the caller checks the word before the values index anything.
 bool radix_sort_pairs(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
                       uint32_t* vals_alt, int64_t n, int bits);
+// The same for keys alone, ordered by key bits [lo, lo + bits) (lower bits ride along).
+bool radix_sort_keys(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, int64_t n, int lo, int bits);
 
 int bit_length(uint64_t x);
 

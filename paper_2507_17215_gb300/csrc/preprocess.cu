@@ -8,7 +8,10 @@
 //   A4  orientation G->pi: u -> v iff (round(u), u) < (round(v), v); out-degree <= alpha;
 //   A5  every triangle of G_S exactly once: (u, v) in G->, w in N+(u) cap N+(v)
 //       (Algorithm 3's enumeration skeleton), with its per-triangle probe count.
+#include <algorithm>
 #include <climits>
+#include <cstdlib>
+#include <cstring>
 
 #include "internal.cuh"
 
@@ -131,6 +134,162 @@ __global__ void k_pair_ends(const uint64_t* __restrict__ key, const int32_t* __r
         pair_of_rank(key[seg[2 * s]] >> 1, n, x, y);
         ea[s] = x;
         eb[s] = y;
+    }
+}
+
+// ---------------------------------------------------------------- dense pair ids
+//
+// When the distinct pairs are few enough, the edges are sorted by (pair id, direction)
+// with pair ids numbered 0..S-1 in (a, b) order, instead of by the full pair key: the id
+// and the direction bit need about log2(2S) bits, which leaves room for the edge's
+// time rank in the same 64-bit word. The sort is then keys only and takes 3 digit
+// passes on the medium graph instead of 5 passes with values. The distinct pairs come
+// from an open-addressed table (linear probing from a multiplicative hash of the pair
+// rank); they are sorted on their own (S entries), and each edge looks its id up by the
+// table slot it kept from the insert.
+
+constexpr int PAIR_MAX_PROBE = 4096;              // longer probe sequences abandon the table
+constexpr int PAIR_COMPACT_ITEMS = 16;            // table slots per thread and step of the compaction
+constexpr uint64_t PAIR_HASH_MUL = 0x9E3779B97F4A7C15ull;  // 2^64 / golden ratio (Fibonacci hashing)
+
+__device__ __forceinline__ uint64_t pair_rank_of(int32_t x, int32_t y, int32_t n) {
+    const uint64_t a = (uint64_t)min(x, y), b = (uint64_t)max(x, y);
+    return a * (2 * (uint64_t)n - a - 1) / 2 + (b - a - 1);
+}
+
+// Slot holding table value key (rank + 1), placing it in the first empty slot of its probe
+// sequence when absent; -1 after PAIR_MAX_PROBE steps.
+__device__ __forceinline__ int64_t pair_slot(uint64_t* table, int lg, uint64_t key) {
+    const uint64_t mask = (1ull << lg) - 1;
+    uint64_t h = (key * PAIR_HASH_MUL) >> (64 - lg);
+    for (int pr = 0; pr < PAIR_MAX_PROBE; pr++) {
+        const uint64_t cur = __ldcg(&table[h]);
+        if (cur == key) return (int64_t)h;
+        if (cur == 0) {
+            const unsigned long long old =
+                atomicCAS((unsigned long long*)&table[h], 0ull, (unsigned long long)key);
+            if (old == 0 || old == key) return (int64_t)h;
+        }
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+constexpr uint32_t PAIR_LOOP = 0x7fffffffu;  // slot word of a self-loop
+constexpr uint32_t PAIR_DIR = 0x80000000u;   // direction bit of a slot word (tables hold < 2^31 slots)
+
+// Every non-loop edge's pair goes into the table (value rank + 1, 0 = empty), and edge i
+// keeps its slot and direction in slotw[i] (PAIR_LOOP for a self-loop). A probe sequence
+// that runs out sets *over.
+__global__ void k_pair_insert(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m, int32_t n,
+                              uint64_t* __restrict__ table, int lg, uint32_t* __restrict__ slotw,
+                              int* __restrict__ over) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x = src[i], y = dst[i];
+        uint32_t w = PAIR_LOOP;
+        if (x != y) {
+            const int64_t sl = pair_slot(table, lg, pair_rank_of(x, y, n) + 1);
+            if (sl < 0) atomicExch(over, 1);
+            else w = (uint32_t)sl | (x > y ? PAIR_DIR : 0u);
+        }
+        __stcs(slotw + i, w);
+    }
+}
+
+// The occupied slots as (rank, slot) lists, in no particular order: each block takes
+// PAIR_COMPACT_ITEMS * blockDim.x slots per step and reserves their entries with one
+// global atomic. *cnt ends at the number of distinct pairs; entries past cap are not
+// written (the caller then abandons the table).
+__global__ void k_pair_compact(const uint64_t* __restrict__ table, int64_t tb, uint64_t* __restrict__ urank,
+                               uint32_t* __restrict__ uslot, int* __restrict__ cnt, int cap) {
+    __shared__ int wsum[32], base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t step = (int64_t)PAIR_COMPACT_ITEMS * blockDim.x;
+    for (int64_t s0 = blockIdx.x * step; s0 < tb; s0 += gridDim.x * step) {
+        uint64_t v[PAIR_COMPACT_ITEMS];
+        int c = 0;
+#pragma unroll
+        for (int q = 0; q < PAIR_COMPACT_ITEMS; q++) {
+            const int64_t sl = s0 + (int64_t)q * blockDim.x + threadIdx.x;
+            v[q] = sl < tb ? table[sl] : 0;
+            c += v[q] != 0;
+        }
+        int inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int w = 0; w < nw; w++) {
+                const int x = wsum[w];
+                wsum[w] = t;
+                t += x;
+            }
+            base = t ? atomicAdd(cnt, t) : 0;
+        }
+        __syncthreads();
+        int at = base + wsum[warp] + inc - c;
+#pragma unroll
+        for (int q = 0; q < PAIR_COMPACT_ITEMS; q++) {
+            if (v[q] != 0) {
+                if (at < cap) {
+                    urank[at] = v[q] - 1;
+                    uslot[at] = (uint32_t)(s0 + (int64_t)q * blockDim.x + threadIdx.x);
+                }
+                at++;
+            }
+        }
+        __syncthreads();  // wsum and base are rewritten by the next step
+    }
+}
+
+// Pair id j (position in rank order) of every table slot in use, and the pair's ends.
+__global__ void k_pair_ids(const uint64_t* __restrict__ urank, const uint32_t* __restrict__ uslot, int32_t S,
+                           int32_t n, int32_t* __restrict__ sid, int32_t* __restrict__ ea, int32_t* __restrict__ eb) {
+    for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < S; j += gridDim.x * blockDim.x) {
+        sid[uslot[j]] = j;
+        int32_t x, y;
+        pair_of_rank(urank[j], n, x, y);
+        ea[j] = x;
+        eb[j] = y;
+    }
+}
+
+// Sort word of the edge at time rank j (input index order[j], or j when the input is in
+// time order): (2 pair id + direction) << ib | j; self-loops get 2S and sort last.
+__global__ void k_pair_pack(const uint32_t* __restrict__ slotw, const uint32_t* __restrict__ order, int64_t m,
+                            const int32_t* __restrict__ sid, int32_t S, int ib, uint64_t* __restrict__ packed) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = order ? slotw[order[j]] : __ldcs(slotw + j);
+        uint64_t c = 2 * (uint64_t)S;
+        if (w != PAIR_LOOP) c = 2 * (uint64_t)sid[w & ~PAIR_DIR] + (w >> 31);
+        packed[j] = (c << ib) | (uint64_t)j;
+    }
+}
+
+// perm, T, sd and the pair starts from the sorted words: position i holds time rank
+// j = word mod 2^ib (input index order[j], or j) of pair id and direction word >> ib.
+template <typename TS>
+__global__ void k_pair_store(const uint64_t* __restrict__ packed, const uint32_t* __restrict__ order, int64_t mk,
+                             int ib, const TS* __restrict__ t, int32_t* __restrict__ perm, TS* __restrict__ T,
+                             int32_t* __restrict__ sd, int32_t* __restrict__ seg) {
+    const uint64_t jm = (1ull << ib) - 1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mk; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t pk = __ldcs(packed + i);
+        const int64_t j = (int64_t)(pk & jm);
+        const uint32_t o = order ? order[j] : (uint32_t)j;
+        __stcs(perm + i, (int32_t)o);
+        T[i] = t[o];
+        const int32_t c = (int32_t)(pk >> ib);
+        __stcs(sd + i, c);
+        if (i == 0 || (int32_t)(packed[i - 1] >> (ib + 1)) != (c >> 1)) {
+            seg[c & ~1] = (int32_t)i;
+            seg[(c & ~1) + 1] = -1;
+        }
     }
 }
 
@@ -1758,17 +1917,90 @@ __global__ void k_tri_write(const int32_t* __restrict__ outptr, const int32_t* _
 // (read_back checks the graph's error word).
 static void sort_check(folty_graph* g, cudaStream_t s) { read_back(g, nullptr, nullptr, 0, nullptr, s); }
 
-void preprocess_graph(folty_graph* g, cudaStream_t s) {
+// A1 with dense pair ids (see k_pair_insert): false, with nothing of the graph written,
+// when the table cannot serve (too many distinct pairs, a probe sequence ran out, or
+// ids and time ranks do not fit one word); FOLTY_PAIR_SORT=keys forces that answer.
+static bool pair_ids_sort(folty_graph* g, Scratch& sc, const uint32_t* order, const uint32_t* t32, cudaStream_t s) {
     const int T = 256;
-    const int64_t m = g->m;
+    const int64_t m = g->m, mk = g->m_kept;
     const int32_t n = g->n;
-    Scratch sc(g->alloc, s, g->dev_err);
+    const char* env = std::getenv("FOLTY_PAIR_SORT");
+    if (env && std::strcmp(env, "keys") == 0) return false;
+    if (mk == 0 || n < 2) return false;
+    const int ib = bit_length((uint64_t)(m - 1));
+    // at least 2m slots, up to 2^23; a first try with at most 2^21 slots (16 MB, which
+    // stays in L2) serves up to a million distinct pairs
+    const int lg_max = std::min(23, std::max(10, bit_length((uint64_t)(2 * m - 1))));
+    int lg = std::min(21, lg_max);
+    int64_t tb = 0, S64 = 0;
+    int cap = 0;
+    uint64_t* table = nullptr;
+    uint64_t* urank = nullptr;
+    uint32_t* uslot = nullptr;
+    int* flags = sc.get<int>(2);  // [0] a probe ran out, [1] distinct pairs
+    uint32_t* slotw = sc.get<uint32_t>(m);
+    while (true) {
+        tb = 1ll << lg;
+        cap = (int)(tb / 2);  // load factor at most 1/2
+        table = sc.get<uint64_t>(tb);
+        FOLTY_CUDA(cudaMemsetAsync(table, 0, sizeof(uint64_t) * (size_t)tb, s));
+        FOLTY_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), s));
+        FOLTY_LAUNCH(k_pair_insert, grid_for(m, T), T, 0, s, g->in_src, g->in_dst, m, n, table, lg, slotw, flags);
+        urank = sc.get<uint64_t>(cap);
+        uslot = sc.get<uint32_t>(cap);
+        FOLTY_LAUNCH(k_pair_compact, grid_for(tb, (int64_t)T * PAIR_COMPACT_ITEMS), T, 0, s, table, tb, urank, uslot,
+                     flags + 1, cap);
+        const void* ptrs[2] = {flags, flags + 1};
+        int sizes[2] = {4, 4};
+        int64_t fv[2];
+        read_back(g, ptrs, sizes, 2, fv, s);
+        S64 = fv[1];
+        if (fv[0] == 0 && S64 <= cap) break;
+        if (lg == lg_max) return false;
+        lg = lg_max;
+    }
+    if (bit_length((uint64_t)(2 * S64)) + ib > 64) return false;
+    const int32_t S = (int32_t)S64;
+    // the distinct pairs in (a, b) order: ids, ends
+    uint64_t* urank_alt = sc.get<uint64_t>(S);
+    uint32_t* uslot_alt = sc.get<uint32_t>(S);
+    const int rank_bits = bit_length((uint64_t)n * (uint64_t)(n - 1) / 2);
+    const bool ualt = radix_sort_pairs(sc, urank, urank_alt, uslot, uslot_alt, S, rank_bits);
+    sort_check(g, s);
+    const uint64_t* ur = ualt ? urank_alt : urank;
+    const uint32_t* us = ualt ? uslot_alt : uslot;
+    g->S = S;
+    g->ea = graph_alloc<int32_t>(g, S, s);
+    g->eb = graph_alloc<int32_t>(g, S, s);
+    g->seg = graph_alloc<int32_t>(g, 2 * (int64_t)S + 1, s);
+    int32_t* sid = sc.get<int32_t>(tb);
+    FOLTY_LAUNCH(k_pair_ids, grid_for(S, T), T, 0, s, ur, us, S, n, sid, g->ea, g->eb);
+    // edges by (pair id, direction, time rank): keys only, on the id and direction bits
+    uint64_t* packed = sc.get<uint64_t>(m);
+    uint64_t* packed_alt = sc.get<uint64_t>(m);
+    FOLTY_LAUNCH(k_pair_pack, grid_for(m, T), T, 0, s, slotw, order, m, sid, S, ib, packed);
+    const bool palt = radix_sort_keys(sc, packed, packed_alt, m, ib, bit_length((uint64_t)(2 * S)));
+    const uint64_t* sp = palt ? packed_alt : packed;
+    if (g->ts32)
+        FOLTY_LAUNCH(k_pair_store<uint32_t>, grid_for(mk, T), T, 0, s, sp, order, mk, ib, t32, g->perm,
+                     (uint32_t*)g->T, g->sd, g->seg);
+    else
+        FOLTY_LAUNCH(k_pair_store<int64_t>, grid_for(mk, T), T, 0, s, sp, order, mk, ib, g->in_t, g->perm,
+                     (int64_t*)g->T, g->sd, g->seg);
+    FOLTY_LAUNCH(k_segments_split, grid_for(mk, T), T, 0, s, g->sd, mk, S, g->seg);
+    FOLTY_LAUNCH(k_segments_fix, grid_for(S, T), T, 0, s, S, mk, g->seg);
+    sort_check(g, s);  // the sort's look-back and the pair lookups
+    return true;
+}
 
-    // ---------------- A1: canonical order
-    const int nb = bit_length((uint64_t)(n > 1 ? n - 1 : 1));
+// A1 with the full pair key (2 p(a, b) + direction, see k_build_keys) and the input
+// index (or time rank) as the value.
+static void pair_key_sort(folty_graph* g, Scratch& sc, const uint32_t* order, const uint32_t* t32, cudaStream_t s) {
+    const int T = 256;
+    const int64_t m = g->m, mk = g->m_kept;
+    const int32_t n = g->n;
     const int key_bits = n > 1 ? bit_length((uint64_t)n * (uint64_t)(n - 1)) : 1;  // keys < n (n - 1)
     const uint64_t loop_key = (key_bits >= 64) ? ~0ull : ((1ull << key_bits) - 1);
-    const int64_t mk = g->m_kept;
     uint64_t* key = sc.get<uint64_t>(m);
     uint64_t* key_alt = sc.get<uint64_t>(m);
     uint32_t* val = sc.get<uint32_t>(m);
@@ -1776,46 +2008,28 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     FOLTY_LAUNCH(k_build_keys, grid_for(m, T), T, 0, s, g->in_src, g->in_dst, m, n, loop_key, key, val);
     uint64_t* skey = key;
     uint32_t* sval = val;
-    if (!g->info.time_sorted && m > 1) {
-        // stable sort by t first, then (stably) by the pair key
-        int64_t tmin = g->tmin, tmax = g->tmax;
-        uint64_t* tk = sc.get<uint64_t>(m);
-        uint64_t* tk_alt = sc.get<uint64_t>(m);
-        FOLTY_LAUNCH(k_time_keys, grid_for(m, T), T, 0, s, g->in_t, m, tmin, tk, val);
-        bool alt = radix_sort_pairs(sc, tk, tk_alt, val, val_alt, m, bit_length((uint64_t)(tmax - tmin)));
-        sort_check(g, s);
-        uint32_t* order = alt ? val_alt : val;
-        uint32_t* other = alt ? val : val_alt;
+    if (order) {
+        // keys in time order, values the input indices: the stable sort keeps time order
         FOLTY_LAUNCH(k_gather_keys, grid_for(m, T), T, 0, s, key, order, m, key_alt);
-        // keys now in key_alt, values in order; sort (key_alt, order)
-        bool alt2 = radix_sort_pairs(sc, key_alt, key, order, other, m, key_bits);
-        sort_check(g, s);
-        skey = alt2 ? key : key_alt;
-        sval = alt2 ? other : order;
+        FOLTY_CUDA(cudaMemcpyAsync(val, order, sizeof(uint32_t) * (size_t)m, cudaMemcpyDeviceToDevice, s));
+        const bool alt = radix_sort_pairs(sc, key_alt, key, val, val_alt, m, key_bits);
+        skey = alt ? key : key_alt;
+        sval = alt ? val_alt : val;
     } else {
-        bool alt = radix_sort_pairs(sc, key, key_alt, val, val_alt, m, key_bits);
-        sort_check(g, s);
+        const bool alt = radix_sort_pairs(sc, key, key_alt, val, val_alt, m, key_bits);
         skey = alt ? key_alt : key;
         sval = alt ? val_alt : val;
     }
-    g->perm = graph_alloc<int32_t>(g, mk, s);
-    // 32-bit offsets from tmin when the time range leaves room for the "none" marker
-    g->ts32 = (g->tmax - g->tmin) < (int64_t)0xffffffffll;
-    if (g->ts32) g->T = graph_alloc<uint32_t>(g, mk, s);
-    else g->T = graph_alloc<int64_t>(g, mk, s);
-    g->sd = graph_alloc<int32_t>(g, mk, s);
+    sort_check(g, s);
     int32_t* newpair = sc.get<int32_t>(mk + 1);
     int32_t* pscan = sc.get<int32_t>(mk + 1);
     if (mk > 0) {
-        if (g->ts32) {
-            uint32_t* t32 = sc.get<uint32_t>(m);
-            FOLTY_LAUNCH(k_offsets32, grid_for(m, T), T, 0, s, g->in_t, m, g->tmin, t32);
+        if (g->ts32)
             FOLTY_LAUNCH(k_store<uint32_t>, grid_for(mk, T), T, 0, s, skey, sval, t32, mk, g->perm, (uint32_t*)g->T,
                          newpair);
-        } else {
+        else
             FOLTY_LAUNCH(k_store<int64_t>, grid_for(mk, T), T, 0, s, skey, sval, g->in_t, mk, g->perm, (int64_t*)g->T,
                          newpair);
-        }
     }
     exclusive_scan(sc, newpair, pscan, mk);
     const int32_t S = read_i32(g, pscan + mk, s);
@@ -1831,6 +2045,42 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     } else {
         FOLTY_CUDA(cudaMemsetAsync(g->seg, 0, sizeof(int32_t), s));
     }
+}
+
+void preprocess_graph(folty_graph* g, cudaStream_t s) {
+    const int T = 256;
+    const int64_t m = g->m;
+    const int32_t n = g->n;
+    Scratch sc(g->alloc, s, g->dev_err);
+
+    // ---------------- A1: canonical order
+    const int nb = bit_length((uint64_t)(n > 1 ? n - 1 : 1));
+    const int64_t mk = g->m_kept;
+    g->perm = graph_alloc<int32_t>(g, mk, s);
+    // 32-bit offsets from tmin when the time range leaves room for the "none" marker
+    g->ts32 = (g->tmax - g->tmin) < (int64_t)0xffffffffll;
+    if (g->ts32) g->T = graph_alloc<uint32_t>(g, mk, s);
+    else g->T = graph_alloc<int64_t>(g, mk, s);
+    g->sd = graph_alloc<int32_t>(g, mk, s);
+    uint32_t* t32 = nullptr;
+    if (g->ts32 && mk > 0) {
+        t32 = sc.get<uint32_t>(m);
+        FOLTY_LAUNCH(k_offsets32, grid_for(m, T), T, 0, s, g->in_t, m, g->tmin, t32);
+    }
+    // time order of an input that is not sorted by time (stable): order[j] = input index
+    uint32_t* order = nullptr;
+    if (!g->info.time_sorted && m > 1) {
+        uint64_t* tk = sc.get<uint64_t>(m);
+        uint64_t* tk_alt = sc.get<uint64_t>(m);
+        uint32_t* iv = sc.get<uint32_t>(m);
+        uint32_t* iv_alt = sc.get<uint32_t>(m);
+        FOLTY_LAUNCH(k_time_keys, grid_for(m, T), T, 0, s, g->in_t, m, g->tmin, tk, iv);
+        const bool alt = radix_sort_pairs(sc, tk, tk_alt, iv, iv_alt, m, bit_length((uint64_t)(g->tmax - g->tmin)));
+        sort_check(g, s);
+        order = alt ? iv_alt : iv;
+    }
+    if (!pair_ids_sort(g, sc, order, t32, s)) pair_key_sort(g, sc, order, t32, s);
+    const int32_t S = g->S;
     // the raw input is no longer needed
     graph_release(g, g->in_src, s);
     graph_release(g, g->in_dst, s);

@@ -209,16 +209,17 @@ constexpr unsigned long long LB_AGG = 1ull << 62;     // entry holds the tile's 
 constexpr unsigned long long LB_PREFIX = 1ull << 63;  // entry holds the inclusive prefix
 constexpr unsigned long long LB_VALUE = LB_AGG - 1;
 
-// hist[p][b] = number of keys whose digit p is b, for all passes at once.
-__global__ void __launch_bounds__(RS_THREADS) k_rs_hist_all(const uint64_t* __restrict__ keys, int64_t n, int passes,
-                                                            uint32_t* __restrict__ hist) {
+// hist[p][b] = number of keys whose digit p (bits lo + 8p ...) is b, for all passes at once.
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist_all(const uint64_t* __restrict__ keys, int64_t n, int lo,
+                                                            int passes, uint32_t* __restrict__ hist) {
     __shared__ uint32_t h[2][RS_MAX_PASSES][RS_BINS];  // two copies: even and odd warps
     for (int i = threadIdx.x; i < 2 * RS_MAX_PASSES * RS_BINS; i += RS_THREADS) (&h[0][0][0])[i] = 0;
     __syncthreads();
     const int copy = (threadIdx.x >> 5) & 1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t k = keys[i];
-        for (int p = 0; p < passes; p++) atomicAdd(&h[copy][p][(unsigned)(k >> (RS_BITS * p)) & (RS_BINS - 1)], 1u);
+        for (int p = 0; p < passes; p++)
+            atomicAdd(&h[copy][p][(unsigned)(k >> (lo + RS_BITS * p)) & (RS_BINS - 1)], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * RS_BINS; i += RS_THREADS) {
@@ -250,7 +251,7 @@ __global__ void k_rs_bases(const uint32_t* __restrict__ hist, int passes, uint32
 
 struct OnesweepArgs {
     const uint64_t* keys;
-    const uint32_t* vals;
+    const uint32_t* vals;  // null for a keys-only sort
     uint64_t* okeys;
     uint32_t* ovals;
     int64_t n;
@@ -284,11 +285,13 @@ __device__ __forceinline__ unsigned digit_peers(unsigned d) {
 //     tile's count of digit d and looks back over earlier tiles for its global offset;
 //  4. a 16-bit permutation in shared memory lists the tile in digit order, and the
 //     writes of each digit's run are contiguous. Positions are 32-bit (n < 2^32).
-__global__ void __launch_bounds__(RS_THREADS, 3) k_rs_onesweep(OnesweepArgs a) {
+// V: values travel with the keys (a keys-only sort moves 8 bytes a key instead of 12).
+template <bool V>
+__global__ void __launch_bounds__(RS_THREADS, V ? 3 : 4) k_rs_onesweep(OnesweepArgs a) {
     extern __shared__ __align__(16) unsigned char rs_smem[];
     uint64_t* skey = (uint64_t*)rs_smem;                    // RS_TILE, load order
-    uint32_t* sval = (uint32_t*)(skey + RS_TILE);           // RS_TILE, load order
-    uint16_t* sperm = (uint16_t*)(sval + RS_TILE);          // RS_TILE, digit order -> load order
+    uint32_t* sval = (uint32_t*)(skey + RS_TILE);           // RS_TILE, load order (V only)
+    uint16_t* sperm = (uint16_t*)(V ? (void*)(sval + RS_TILE) : (void*)sval);  // RS_TILE, digit order -> load order
     __shared__ uint16_t wh[RS_WARPS][RS_BINS];              // per-warp counts, then offsets
     __shared__ uint32_t bstart[RS_BINS];                    // tile-local start of each digit
     __shared__ uint32_t adj[RS_BINS];                       // final position of digit-order slot j: adj + j
@@ -316,26 +319,30 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_rs_onesweep(OnesweepArgs a) {
         for (int i = 0; i < RS_ITEMS; i++) {
             const int idx = wbase + i * 32 + lane;
             kr[i] = (idx < tn) ? kin[idx] : 0ull;
-            vr[i] = (idx < tn) ? vin[idx] : 0u;
+            if (V) vr[i] = (idx < tn) ? vin[idx] : 0u;
         }
 #pragma unroll
         for (int i = 0; i < RS_ITEMS; i++) {
             const int idx = wbase + i * 32 + lane;
             if (idx < tn) {
                 skey[idx] = kr[i];
-                sval[idx] = vr[i];
+                if (V) sval[idx] = vr[i];
             }
             info[i] = (unsigned)(kr[i] >> a.shift) & (RS_BINS - 1);
         }
     }
-    // ---- 2. ranks
+    // ---- 2. ranks: every item's peer mask first (independent ballot chains the scheduler
+    // can interleave), then the per-warp counters item by item
     const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned pm[RS_ITEMS];
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; i++) pm[i] = digit_peers(info[i]);
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; i++) {
         const int idx = wbase + i * 32 + lane;
         const bool valid = idx < tn;
         const unsigned d = info[i];
-        const unsigned peers = digit_peers(d) & __ballot_sync(0xffffffffu, valid);
+        const unsigned peers = pm[i] & __ballot_sync(0xffffffffu, valid);
         unsigned before = 0;
         if (valid) before = wh[warp][d];
         __syncwarp();
@@ -425,14 +432,16 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_rs_onesweep(OnesweepArgs a) {
         const uint64_t kk = skey[src];
         const uint32_t pos = adj[(unsigned)(kk >> a.shift) & (RS_BINS - 1)] + (uint32_t)j;
         a.okeys[pos] = kk;
-        a.ovals[pos] = sval[src];
+        if (V) a.ovals[pos] = sval[src];
     }
 }
 
 constexpr size_t RS_DYN_SMEM = RS_TILE * (sizeof(uint64_t) + sizeof(uint32_t) + sizeof(uint16_t));
+constexpr size_t RS_DYN_SMEM_K = RS_TILE * (sizeof(uint64_t) + sizeof(uint16_t));
 
-bool radix_sort_pairs(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
-                      uint32_t* vals_alt, int64_t n, int bits) {
+// Sorts by the digits of bits [lo, lo + bits); vals may be null (keys only).
+static bool radix_sort_impl(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
+                            int64_t n, int lo, int bits) {
     if (n <= 1 || bits <= 0) return false;
     if (n >= (int64_t)0xffffffffll) fail(FOLTY_EINVAL, "radix sort: too many keys");
     cudaStream_t s = sc.stream();
@@ -445,21 +454,34 @@ bool radix_sort_pairs(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uint32_t*
     FOLTY_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * RS_MAX_PASSES * RS_BINS, s));
     {
         StageSpan span(ST_SORT, s, 8 * n);  // all digit histograms: one read of the keys
-        FOLTY_LAUNCH(k_rs_hist_all, grid_for(n, RS_THREADS, 4), RS_THREADS, 0, s, keys, n, passes, hist);
+        FOLTY_LAUNCH(k_rs_hist_all, grid_for(n, RS_THREADS, 4), RS_THREADS, 0, s, keys, n, lo, passes, hist);
         FOLTY_LAUNCH(k_rs_bases, 1, RS_BINS, 0, s, hist, passes, base);
     }
-    FOLTY_CUDA(cudaFuncSetAttribute(k_rs_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_DYN_SMEM));
+    const bool kv = vals != nullptr;
+    if (kv) FOLTY_CUDA(cudaFuncSetAttribute(k_rs_onesweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_DYN_SMEM));
+    else FOLTY_CUDA(cudaFuncSetAttribute(k_rs_onesweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_DYN_SMEM_K));
     bool alt = false;
     for (int p = 0; p < passes; p++) {
-        StageSpan span(ST_SORT, s, 24 * n);  // 12 B read + 12 B written per key
+        StageSpan span(ST_SORT, s, (kv ? 24 : 16) * n);  // keys (and values) read and written once
         FOLTY_CUDA(cudaMemsetAsync(lb, 0, sizeof(unsigned long long) * (size_t)(tiles * RS_BINS), s));
         FOLTY_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
-        OnesweepArgs oa{alt ? keys_alt : keys, alt ? vals_alt : vals, alt ? keys : keys_alt, alt ? vals : vals_alt,
-                        n, RS_BITS * p, base + p * RS_BINS, lb, counter, sc.err(), LOOKBACK_TIMEOUT_NS};
-        FOLTY_LAUNCH(k_rs_onesweep, (unsigned)tiles, RS_THREADS, RS_DYN_SMEM, s, oa);
+        OnesweepArgs oa{alt ? keys_alt : keys, kv ? (alt ? vals_alt : vals) : nullptr, alt ? keys : keys_alt,
+                        kv ? (alt ? vals : vals_alt) : nullptr, n, lo + RS_BITS * p, base + p * RS_BINS, lb, counter,
+                        sc.err(), LOOKBACK_TIMEOUT_NS};
+        if (kv) FOLTY_LAUNCH(k_rs_onesweep<true>, (unsigned)tiles, RS_THREADS, RS_DYN_SMEM, s, oa);
+        else FOLTY_LAUNCH(k_rs_onesweep<false>, (unsigned)tiles, RS_THREADS, RS_DYN_SMEM_K, s, oa);
         alt = !alt;
     }
     return alt;
+}
+
+bool radix_sort_pairs(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
+                      uint32_t* vals_alt, int64_t n, int bits) {
+    return radix_sort_impl(sc, keys, keys_alt, vals, vals_alt, n, 0, bits);
+}
+
+bool radix_sort_keys(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, int64_t n, int lo, int bits) {
+    return radix_sort_impl(sc, keys, keys_alt, nullptr, nullptr, n, lo, bits);
 }
 
 }  // namespace folty

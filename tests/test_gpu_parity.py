@@ -433,3 +433,47 @@ def test_all_existential_triples(F, which):
             want_last = og.query(mixed[-1])
             assert pairs_of(bat[-1]) == pairs_of(want_last)
             assert "triples" not in bat[-1]
+
+
+def test_full_key_sort_path(F, monkeypatch):
+    """The pair sort without dense pair ids (the 64-bit pair key with the input index as
+    the value), which the library takes when its pair table cannot serve; forced here."""
+    monkeypatch.setenv("FOLTY_PAIR_SORT", "keys")
+    rng = np.random.default_rng(91)
+    for n, m, tmax in ((12, 60, 25), (60, 6000, 3000), (300, 30000, 100000)):
+        g = W.random_small_graph(rng, n, m, tmax, self_loops=True)
+        _check_graph(F, g, _full_mix((0, 40, 700)))
+        perm = rng.permutation(g.m)  # an edge list not in time order
+        g2 = W.TemporalGraph(g.n, g.src[perm], g.dst[perm], g.t[perm])
+        _check_graph(F, g2, _full_mix((40,)))
+    monkeypatch.delenv("FOLTY_PAIR_SORT")
+    g = W.config_graph(2, scale=0.01)
+    perm = rng.permutation(g.m)
+    _check_graph(F, W.TemporalGraph(g.n, g.src[perm], g.dst[perm], g.t[perm]),
+                 [W.Query(3600, 1, 2, W.Q_FORALL_T, W.DIR_OUT, W.U_HEAD, True)])
+
+
+def _many_pairs_graph(seed=5):
+    """Over 2^20 distinct pairs (random pairs of 200K vertices) plus a dense block of 200
+    vertices with many triangles, in time order."""
+    rng = np.random.default_rng(seed)
+    n, m1, m2 = 200_000, 1_150_000, 60_000
+    src = rng.integers(0, n, m1 + m2).astype(np.int32)
+    dst = rng.integers(0, n, m1 + m2).astype(np.int32)
+    block = rng.choice(n, 200, replace=False).astype(np.int32)
+    src[m1:] = block[rng.integers(0, 200, m2)]
+    dst[m1:] = block[rng.integers(0, 200, m2)]
+    t = rng.integers(0, 10 ** 6, m1 + m2).astype(np.int64)
+    t[m1:] = rng.integers(0, 20_000, m2)
+    o = np.argsort(t, kind="stable")
+    return W.TemporalGraph(n, src[o], dst[o], t[o])
+
+
+def test_pair_table_past_its_first_size(F):
+    """More distinct pairs than the pair table's first size holds: the library retries
+    with a larger table (or sorts full keys); results are the oracle's either way."""
+    g = _many_pairs_graph()
+    qs = [W.Query(d, 1, 2, W.Q_FORALL_T, dr, W.U_HEAD, True) for d in (50, 2000) for dr in (W.DIR_OUT, W.DIR_EITHER)]
+    qs.append(W.Query(500, 1, 10, W.Q_FORALL_T, W.DIR_IN, W.U_COMMON, True))
+    info = _check_graph(F, g, qs)
+    assert info["static_edges"] > (1 << 20)
