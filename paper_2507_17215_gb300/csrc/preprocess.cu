@@ -1920,7 +1920,7 @@ static void sort_check(folty_graph* g, cudaStream_t s) { read_back(g, nullptr, n
 // A1 with dense pair ids (see k_pair_insert): false, with nothing of the graph written,
 // when the table cannot serve (too many distinct pairs, a probe sequence ran out, or
 // ids and time ranks do not fit one word); FOLTY_PAIR_SORT=keys forces that answer.
-static bool pair_ids_sort(folty_graph* g, Scratch& sc, const uint32_t* order, const uint32_t* t32, cudaStream_t s) {
+static bool pair_ids_sort(folty_graph* g, Scratch& sc, const uint32_t* order, uint32_t* t32, cudaStream_t s) {
     const int T = 256;
     const int64_t m = g->m, mk = g->m_kept;
     const int32_t n = g->n;
@@ -1981,6 +1981,7 @@ static bool pair_ids_sort(folty_graph* g, Scratch& sc, const uint32_t* order, co
     FOLTY_LAUNCH(k_pair_pack, grid_for(m, T), T, 0, s, slotw, order, m, sid, S, ib, packed);
     const bool palt = radix_sort_keys(sc, packed, packed_alt, m, ib, bit_length((uint64_t)(2 * S)));
     const uint64_t* sp = palt ? packed_alt : packed;
+    if (t32) FOLTY_LAUNCH(k_offsets32, grid_for(m, T), T, 0, s, g->in_t, m, g->tmin, t32);
     if (g->ts32)
         FOLTY_LAUNCH(k_pair_store<uint32_t>, grid_for(mk, T), T, 0, s, sp, order, mk, ib, t32, g->perm,
                      (uint32_t*)g->T, g->sd, g->seg);
@@ -1995,7 +1996,7 @@ static bool pair_ids_sort(folty_graph* g, Scratch& sc, const uint32_t* order, co
 
 // A1 with the full pair key (2 p(a, b) + direction, see k_build_keys) and the input
 // index (or time rank) as the value.
-static void pair_key_sort(folty_graph* g, Scratch& sc, const uint32_t* order, const uint32_t* t32, cudaStream_t s) {
+static void pair_key_sort(folty_graph* g, Scratch& sc, const uint32_t* order, uint32_t* t32, cudaStream_t s) {
     const int T = 256;
     const int64_t m = g->m, mk = g->m_kept;
     const int32_t n = g->n;
@@ -2024,6 +2025,7 @@ static void pair_key_sort(folty_graph* g, Scratch& sc, const uint32_t* order, co
     int32_t* newpair = sc.get<int32_t>(mk + 1);
     int32_t* pscan = sc.get<int32_t>(mk + 1);
     if (mk > 0) {
+        if (t32) FOLTY_LAUNCH(k_offsets32, grid_for(m, T), T, 0, s, g->in_t, m, g->tmin, t32);
         if (g->ts32)
             FOLTY_LAUNCH(k_store<uint32_t>, grid_for(mk, T), T, 0, s, skey, sval, t32, mk, g->perm, (uint32_t*)g->T,
                          newpair);
@@ -2062,11 +2064,9 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     if (g->ts32) g->T = graph_alloc<uint32_t>(g, mk, s);
     else g->T = graph_alloc<int64_t>(g, mk, s);
     g->sd = graph_alloc<int32_t>(g, mk, s);
-    uint32_t* t32 = nullptr;
-    if (g->ts32 && mk > 0) {
-        t32 = sc.get<uint32_t>(m);
-        FOLTY_LAUNCH(k_offsets32, grid_for(m, T), T, 0, s, g->in_t, m, g->tmin, t32);
-    }
+    // 32-bit offsets of the input timestamps, written by the sort path right before its
+    // gather so that they are still in L2 there
+    uint32_t* t32 = (g->ts32 && mk > 0) ? sc.get<uint32_t>(m) : nullptr;
     // time order of an input that is not sorted by time (stable): order[j] = input index
     uint32_t* order = nullptr;
     if (!g->info.time_sorted && m > 1) {
