@@ -459,7 +459,11 @@ static bool radix_sort_impl(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uin
     }
     const bool kv = vals != nullptr;
     if (kv) FOLTY_CUDA(cudaFuncSetAttribute(k_rs_onesweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_DYN_SMEM));
-    else FOLTY_CUDA(cudaFuncSetAttribute(k_rs_onesweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_DYN_SMEM_K));
+    else {
+        FOLTY_CUDA(cudaFuncSetAttribute(k_rs_onesweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_DYN_SMEM_K));
+        // four blocks of 46 KB each need the largest shared-memory carveout
+        FOLTY_CUDA(cudaFuncSetAttribute(k_rs_onesweep<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    }
     bool alt = false;
     for (int p = 0; p < passes; p++) {
         StageSpan span(ST_SORT, s, (kv ? 24 : 16) * n);  // keys (and values) read and written once
