@@ -466,6 +466,11 @@ def main():
                     "stage": dom, "kernel": STAGE_KERNELS[dom], "peak_kind": f"{peak_kind} hbm_gbs",
                     "model_bytes_per_launch": d["bytes"] / d["launches"],
                     "launch_ms": d["ms"] / d["launches"]}
+        if dom == "peel":
+            roofline["note"] = ("the peel is bound by the latency of its dependent rounds (304 on this graph: "
+                                "grid, cluster and single-CTA phases), not by bandwidth; its model bytes are "
+                                "tiny, so the fraction is near zero by construction. The sort, probe and "
+                                "threshold stages in 'stages' are the bandwidth-bound ones")
     probe_ms = prof["probe"]["ms"] / max(prof["probe"]["launches"], 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

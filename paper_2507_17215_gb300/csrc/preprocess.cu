@@ -381,11 +381,16 @@ __global__ void k_max_i32(const int32_t* __restrict__ a, int64_t n, int* __restr
     if ((threadIdx.x & 31) == 0) atomicMax(out, best);
 }
 
-__global__ void k_max_sigma(const int32_t* __restrict__ seg, int32_t S, int* __restrict__ out) {
+// sig[s] = temporal edges of static edge s (both directions), and their maximum.
+__global__ void k_max_sigma(const int32_t* __restrict__ seg, int32_t S, int32_t* __restrict__ sig,
+                            int* __restrict__ out) {
     int best = 0;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S;
-         s += (int64_t)gridDim.x * blockDim.x)
-        best = max(best, seg[2 * s + 2] - seg[2 * s]);
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = seg[2 * s + 2] - seg[2 * s];
+        sig[s] = c;
+        best = max(best, c);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out, best);
@@ -1259,7 +1264,8 @@ constexpr int SOLO_THREADS = 1024;
 constexpr int SOLO_CAP = 12288;  // vertices of the single-CTA phase
 constexpr int SOLO_PASS = 2048;  // frontier vertices laid out per pass (2 per thread)
 constexpr int SOLO_CHUNK = 8;    // adjacency entries per thread in flight together (large frontiers)
-constexpr int SOLO_CHUNK_S = 2;  // the same for small frontiers (W <= 2048 in one step; less code)
+constexpr int SOLO_CHUNK_S = 2;
+constexpr int SOLO_COARSE = 1024;  // coarse owner table of a large frontier's flat entries  // the same for small frontiers (W <= 2048 in one step; less code)
 
 // Cluster row length and global id of each exported vertex (0 past the exported count).
 __global__ void k_solo_rows(const int* __restrict__ ctl, const int* __restrict__ ns_p,
@@ -1331,6 +1337,7 @@ struct SoloShared {
     int wsum[SOLO_THREADS / 32];
     int sx[32], sb[32];        // small frontier: exclusive prefix of row lengths, row start - prefix
     int sW;                    // small frontier: total row length
+    uint16_t coarse[SOLO_COARSE];  // large frontier: row holding flat entry b << cs
     int32_t rs[SOLO_CAP + 1];
     uint16_t FL[2][SOLO_CAP];  // frontier by round parity; FL[0] / FL[1] hold the bit-matrix phase's
                                // id map / its small arrays
@@ -1732,6 +1739,18 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
                     }
                     __syncthreads();
                     const int W = sh.P[np];
+                    // coarse owners: entry b << cs lies in row coarse[b] (cs keeps W >> cs below
+                    // SOLO_COARSE), so that an entry's row is searched between two of them
+                    const int cs = max(4, 32 - __clz(max(W, 1) >> 10));
+#pragma unroll
+                    for (int u = 0; u < 2; u++) {
+                        const int i = 2 * tid + u;
+                        if (i < np) {
+                            const int b0 = (sh.P[i] + (1 << cs) - 1) >> cs, b1 = (sh.P[i + 1] + (1 << cs) - 1) >> cs;
+                            for (int b = b0; b < b1 && b < SOLO_COARSE; b++) sh.coarse[b] = (uint16_t)i;
+                        }
+                    }
+                    __syncthreads();
                     for (int x0 = 0; x0 < W; x0 += SOLO_THREADS * SOLO_CHUNK) {
                         if (x0 + warp * 32 >= W) break;  // nothing left for this warp (warp-uniform)
                         const int nch = min(SOLO_CHUNK, (W - x0 + SOLO_THREADS - 1) / SOLO_THREADS);
@@ -1741,7 +1760,8 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
                             const int x = x0 + c * SOLO_THREADS + tid;
                             vv[c] = -1;
                             if (c < nch && x < W) {
-                                int lo = 0, hi = np - 1;  // last row with P[row] <= x
+                                const int b = x >> cs;  // last row with P[row] <= x, from coarse[b]
+                                int lo = sh.coarse[b], hi = ((b + 1) << cs) < W ? sh.coarse[b + 1] : np - 1;
                                 while (lo < hi) {
                                     const int mid = (lo + hi + 1) >> 1;
                                     if (sh.P[mid] <= x) lo = mid;
@@ -1840,6 +1860,45 @@ __global__ void k_outptr(const int32_t* __restrict__ rowptr, const int32_t* __re
 // ================================================================== A5
 
 // Thread per oriented edge (u, v): merge N+(u) and N+(v) (both ascending by id).
+// Triangles of oriented edge u -> v: the common out-neighbours w of u and v (both lists
+// sorted). The counting pass merges the two lists in one thread per edge. The writing
+// pass (more work per triangle) does the same for a light edge, while the lists of a
+// heavy edge (|out(u)| + |out(v)| > TRI_HEAVY, the degeneracy core) are intersected by
+// the whole warp: out(v) is staged in shared memory and every lane binary-searches its
+// share of out(u) in it, so that the latency is a few searches instead of one long
+// merge chain. Both passes find the same set, so the counts match the writes.
+constexpr int TRI_THREADS = 256;
+constexpr int TRI_HEAVY = 48;
+constexpr int TRI_STAGE = 256;  // staged out-list entries per warp (longer lists are merged by one lane)
+
+// Lane-parallel intersection of out(u) = nbr[i1, e1) with out(v) = nbr[i2, e2) staged in
+// sb (e2 - i2 <= TRI_STAGE). Calls hit(ia, ib) for every common entry (ia in out(u), ib in
+// out(v)) on the lane that found it. The whole warp must call it.
+template <typename F>
+__device__ __forceinline__ void warp_intersect(const int32_t* __restrict__ nbr, int32_t i1, int32_t e1, int32_t i2,
+                                               int32_t e2, int32_t* sb, F&& hit) {
+    const int lane = threadIdx.x & 31;
+    const int nb = e2 - i2;
+    for (int t = lane; t < nb; t += 32) sb[t] = nbr[i2 + t];
+    __syncwarp();
+    for (int32_t ia0 = i1; ia0 < e1; ia0 += 32) {
+        const int32_t ia = ia0 + lane;
+        int pos = -1;
+        if (ia < e1) {
+            const int32_t x = nbr[ia];
+            int lo = 0, hi = nb;  // first staged entry >= x
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (sb[mid] < x) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < nb && sb[lo] == x) pos = lo;
+        }
+        hit(ia, pos);
+    }
+    __syncwarp();
+}
+
 __global__ void k_tri_count(const int32_t* __restrict__ outptr, const int32_t* __restrict__ out_nbr,
                             const int32_t* __restrict__ out_src, int32_t S, int32_t* __restrict__ cnt,
                             unsigned long long* __restrict__ merged) {
@@ -1879,35 +1938,79 @@ __global__ void k_tile_starts(const int64_t* __restrict__ tri_off, int64_t ntri,
     }
 }
 
-__global__ void k_tri_write(const int32_t* __restrict__ outptr, const int32_t* __restrict__ out_nbr,
-                            const int32_t* __restrict__ out_eid, const int32_t* __restrict__ out_src,
-                            int32_t S, const int64_t* __restrict__ toff, const int32_t* __restrict__ seg,
-                            int4* __restrict__ tri, int64_t* __restrict__ cost,
-                            int32_t* __restrict__ common) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < S;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        int32_t u = out_src[j], v = out_nbr[j], s_uv = out_eid[j];
-        int32_t i1 = outptr[u], e1 = outptr[u + 1], i2 = outptr[v], e2 = outptr[v + 1];
-        int64_t p = toff[j];
-        int32_t n_here = 0;
-        int32_t sig_uv = seg[2 * s_uv + 2] - seg[2 * s_uv];
-        while (i1 < e1 && i2 < e2) {
-            int32_t x = out_nbr[i1], y = out_nbr[i2];
-            if (x == y) {
-                int32_t w = x, s_uw = out_eid[i1], s_vw = out_eid[i2];
-                int flags = (u < v ? 1 : 0) | (u < w ? 2 : 0) | (v < w ? 4 : 0);
-                tri[p] = make_int4(s_uv, s_uw, s_vw, flags);
-                cost[p] = (int64_t)sig_uv + (seg[2 * s_uw + 2] - seg[2 * s_uw]) +
-                          (seg[2 * s_vw + 2] - seg[2 * s_vw]);
-                atomicAdd(&common[s_uw], 1);
-                atomicAdd(&common[s_vw], 1);
-                p++;
-                n_here++;
-            }
-            i1 += (x <= y);
-            i2 += (y <= x);
+__global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __restrict__ outptr,
+                                                           const int32_t* __restrict__ out_nbr,
+                                                           const int32_t* __restrict__ out_eid,
+                                                           const int32_t* __restrict__ out_src, int32_t S,
+                                                           const int64_t* __restrict__ toff,
+                                                           const int32_t* __restrict__ sig, int4* __restrict__ tri,
+                                                           int64_t* __restrict__ cost, int32_t* __restrict__ common) {
+    __shared__ int32_t stage[TRI_THREADS / 32][TRI_STAGE];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); j0 < S; j0 += stride) {
+        const int64_t j = j0 + lane;
+        int32_t u = 0, v = 0, s_uv = 0, i1 = 0, e1 = 0, i2 = 0, e2 = 0;
+        if (j < S) {
+            u = out_src[j];
+            v = out_nbr[j];
+            s_uv = out_eid[j];
+            i1 = outptr[u];
+            e1 = outptr[u + 1];
+            i2 = outptr[v];
+            e2 = outptr[v + 1];
         }
-        if (n_here) atomicAdd(&common[s_uv], n_here);
+        const bool heavy = j < S && (e1 - i1) + (e2 - i2) > TRI_HEAVY && e2 - i2 <= TRI_STAGE;
+        if (j < S && !heavy) {
+            int64_t p = toff[j];
+            int32_t n_here = 0;
+            const int32_t sig_uv = sig[s_uv];
+            int32_t a1 = i1, a2 = i2;
+            while (a1 < e1 && a2 < e2) {
+                const int32_t x = out_nbr[a1], y = out_nbr[a2];
+                if (x == y) {
+                    const int32_t w = x, s_uw = out_eid[a1], s_vw = out_eid[a2];
+                    const int flags = (u < v ? 1 : 0) | (u < w ? 2 : 0) | (v < w ? 4 : 0);
+                    tri[p] = make_int4(s_uv, s_uw, s_vw, flags);
+                    cost[p] = (int64_t)sig_uv + sig[s_uw] + sig[s_vw];
+                    atomicAdd(&common[s_uw], 1);
+                    atomicAdd(&common[s_vw], 1);
+                    p++;
+                    n_here++;
+                }
+                a1 += (x <= y);
+                a2 += (y <= x);
+            }
+            if (n_here) atomicAdd(&common[s_uv], n_here);
+        }
+        unsigned hm = __ballot_sync(0xffffffffu, heavy);
+        while (hm) {
+            const int src = __ffs(hm) - 1;
+            hm &= hm - 1;
+            const int32_t b1 = __shfl_sync(0xffffffffu, i1, src), f1 = __shfl_sync(0xffffffffu, e1, src);
+            const int32_t b2 = __shfl_sync(0xffffffffu, i2, src), f2 = __shfl_sync(0xffffffffu, e2, src);
+            const int32_t hu = __shfl_sync(0xffffffffu, u, src), hv = __shfl_sync(0xffffffffu, v, src);
+            const int32_t hs = __shfl_sync(0xffffffffu, s_uv, src);
+            int64_t p = (lane == 0) ? toff[j0 + src] : 0;
+            p = __shfl_sync(0xffffffffu, p, 0);
+            const int32_t sig_uv = sig[hs];
+            int n_here = 0;
+            warp_intersect(out_nbr, b1, f1, b2, f2, stage[warp], [&](int32_t ia, int pos) {
+                const unsigned m = __ballot_sync(0xffffffffu, pos >= 0);
+                if (pos >= 0) {
+                    const int64_t at = p + __popc(m & ((1u << lane) - 1u));
+                    const int32_t w = out_nbr[ia], s_uw = out_eid[ia], s_vw = out_eid[b2 + pos];
+                    const int flags = (hu < hv ? 1 : 0) | (hu < w ? 2 : 0) | (hv < w ? 4 : 0);
+                    tri[at] = make_int4(hs, s_uw, s_vw, flags);
+                    cost[at] = (int64_t)sig_uv + sig[s_uw] + sig[s_vw];
+                    atomicAdd(&common[s_uw], 1);
+                    atomicAdd(&common[s_vw], 1);
+                }
+                p += __popc(m);
+                n_here += __popc(m);
+            });
+            if (lane == 0 && n_here) atomicAdd(&common[hs], n_here);
+        }
     }
 }
 
@@ -2249,7 +2352,8 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     if (S > 0) FOLTY_LAUNCH(k_tri_count, grid_for(S, T), T, 0, s, outptr, out_nbr, out_src, S, tcnt, merged);
     exclusive_scan(sc, tcnt, toff, S);
     FOLTY_LAUNCH(k_max_i32, grid_for(n, T), T, 0, s, g->deg, (int64_t)n, stat + 0);
-    if (S > 0) FOLTY_LAUNCH(k_max_sigma, grid_for(S, T), T, 0, s, g->seg, S, stat + 2);
+    int32_t* sig = sc.get<int32_t>(S);
+    if (S > 0) FOLTY_LAUNCH(k_max_sigma, grid_for(S, T), T, 0, s, g->seg, S, sig, stat + 2);
     {
         const void* ptrs[8] = {toff + S, stat + 0, stat + 1, stat + 2, merged, peel_ctl + C_ERR,
                                peel_ctl + C_ROUNDS, peel_ctl + C_ALPHA};
@@ -2274,7 +2378,7 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     g->tri_off = graph_alloc<int64_t>(g, ntri + 1, s);
     int64_t* cost = sc.get<int64_t>(ntri + 1);
     if (S > 0)
-        FOLTY_LAUNCH(k_tri_write, grid_for(S, T), T, 0, s, outptr, out_nbr, out_eid, out_src, S, toff, g->seg,
+        FOLTY_LAUNCH(k_tri_write, grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr, out_eid, out_src, S, toff, sig,
                      g->tri, cost, g->common);
     exclusive_scan(sc, cost, g->tri_off, ntri);
     g->info.triangles = ntri;
