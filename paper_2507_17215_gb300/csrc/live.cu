@@ -17,6 +17,7 @@
 // 1-7 % of all (edge, witness) pairs lie in kept roles.
 #include "internal.cuh"
 #include "probe.cuh"
+#include "scan.cuh"
 
 namespace folty {
 
@@ -146,47 +147,120 @@ __device__ __forceinline__ bool bucket_live(uint8_t b, int64_t delta) {
     return b != DMIN_NEVER && (b == 0 || delta >= ((int64_t)1 << (b - 1)));
 }
 
-// Kept roles of every triangle for one query: mask, kept probes + idle slots.
-__global__ void k_live_tri(const int32_t* __restrict__ rsig, const uint8_t* __restrict__ rmin_dir, int64_t ntri,
-                           int64_t delta, int32_t* __restrict__ flag, int64_t* __restrict__ cost,
-                           uint8_t* __restrict__ mask) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntri;
-         t += (int64_t)gridDim.x * blockDim.x) {
+// Kept roles of every triangle for one query, selected and compacted in one pass: kept
+// triangle j = L[j] with its role mask lmask[j] and its first probe slot loff[j] (prefix
+// of the kept triangles' costs = kept probes + LIVE_IDLE idle slots); totals[0] = kept
+// triangles, totals[1] = slots, loff[totals[0]] = totals[1]. Tiles of LS_TILE triangles
+// are taken in block start order; the two prefix sums (kept count, cost) come from a
+// block scan and two decoupled look-backs by warp 0. *prof (may be null) gets the bytes
+// written for the kept triangles.
+constexpr int LS_ITEMS = 8;
+constexpr int LS_TILE = SCAN_THREADS * LS_ITEMS;  // 2048 triangles
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const int32_t* __restrict__ rsig,
+                                                              const uint8_t* __restrict__ rmin_dir, int64_t ntri,
+                                                              int64_t delta, unsigned long long* lbc,
+                                                              unsigned long long* lbp, unsigned int* counter,
+                                                              int* err, int32_t* __restrict__ L,
+                                                              int64_t* __restrict__ loff, uint8_t* __restrict__ lmask,
+                                                              int64_t* __restrict__ totals,
+                                                              unsigned long long* __restrict__ prof) {
+    constexpr int PADW = 16;  // one pad element per 128 bytes of int64
+    __shared__ int64_t scost[LS_TILE + LS_TILE / PADW];
+    __shared__ uint8_t smask[LS_TILE];
+    __shared__ int32_t wc[SCAN_THREADS / 32];
+    __shared__ int64_t wp[SCAN_THREADS / 32];
+    __shared__ int32_t totc;
+    __shared__ int64_t totp;
+    __shared__ unsigned long long s_exc, s_exp;
+    __shared__ int64_t s_tile;
+    auto pad = [](int i) { return i + i / PADW; };
+    if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * LS_TILE;
+    // ---- the kept roles, in coalesced order
+#pragma unroll
+    for (int i = 0; i < LS_ITEMS; i++) {
+        const int idx = i * SCAN_THREADS + threadIdx.x;
+        const int64_t t = base + idx;
         int m = 0;
         int64_t lp = 0;
+        if (t < ntri) {
 #pragma unroll
-        for (int r = 0; r < 6; r++) {
-            const int32_t s1 = rsig[r * ntri + t];
-            if (s1 > 0 && bucket_live(rmin_dir[r * ntri + t], delta)) {
-                m |= 1 << r;
-                lp += s1;
+            for (int r = 0; r < 6; r++) {
+                const int32_t s1 = rsig[r * ntri + t];
+                if (s1 > 0 && bucket_live(rmin_dir[r * ntri + t], delta)) {
+                    m |= 1 << r;
+                    lp += s1;
+                }
             }
         }
-        flag[t] = lp > 0;
-        cost[t] = lp > 0 ? lp + LIVE_IDLE : 0;
-        mask[t] = (uint8_t)m;
+        scost[pad(idx)] = lp > 0 ? lp + LIVE_IDLE : 0;
+        smask[idx] = (uint8_t)m;
     }
-}
-
-__global__ void k_live_compact(const int32_t* __restrict__ flag, const int32_t* __restrict__ lpos,
-                               const int64_t* __restrict__ lcost, const uint8_t* __restrict__ mask, int64_t ntri,
-                               int32_t* __restrict__ L, int64_t* __restrict__ loff, uint8_t* __restrict__ lmask) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= ntri;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        if (t == ntri) {
-            loff[lpos[ntri]] = lcost[ntri];
-            continue;
+    __syncthreads();
+    // ---- thread sums over LS_ITEMS consecutive triangles, block scans, look-backs
+    int32_t c = 0;
+    int64_t cs = 0;
+#pragma unroll
+    for (int i = 0; i < LS_ITEMS; i++) {
+        const int64_t v = scost[pad(threadIdx.x * LS_ITEMS + i)];
+        c += v > 0;
+        cs += v;
+    }
+    const int32_t offc = block_exclusive_sum<int32_t>(c, wc, &totc);
+    const int64_t offp = block_exclusive_sum<int64_t>(cs, wp, &totp);
+    if (threadIdx.x < 32) {
+        volatile unsigned long long* vc = lbc;
+        volatile unsigned long long* vp = lbp;
+        const unsigned long long tc = (unsigned long long)totc, tp = (unsigned long long)totp;
+        if (tile == 0) {
+            if (threadIdx.x == 0) {
+                vc[0] = SC_PREFIX | tc;
+                vp[0] = SC_PREFIX | tp;
+                s_exc = 0;
+                s_exp = 0;
+            }
+        } else {
+            if (threadIdx.x == 0) {
+                vc[tile] = SC_AGG | tc;
+                vp[tile] = SC_AGG | tp;
+            }
+            const unsigned long long ec = warp_lookback(vc, tile, tc, err);
+            const unsigned long long ep = warp_lookback(vp, tile, tp, err);
+            if (threadIdx.x == 0) {
+                s_exc = ec;
+                s_exp = ep;
+            }
         }
-        if (!flag[t]) continue;
-        const int32_t j = lpos[t];
-        L[j] = (int32_t)t;
-        loff[j] = lcost[t];
-        lmask[j] = mask[t];
+    }
+    __syncthreads();
+    // ---- the kept triangles of this thread's run
+    int64_t jc = (int64_t)s_exc + offc, jp = (int64_t)s_exp + offp;
+#pragma unroll
+    for (int i = 0; i < LS_ITEMS; i++) {
+        const int item = threadIdx.x * LS_ITEMS + i;
+        const int64_t v = scost[pad(item)];
+        if (v > 0) {
+            L[jc] = (int32_t)(base + item);
+            loff[jc] = jp;
+            lmask[jc] = smask[item];
+            jc++;
+            jp += v;
+        }
+    }
+    if (base + LS_TILE >= ntri && threadIdx.x == 0) {
+        const int64_t nl = (int64_t)s_exc + totc, P = (int64_t)s_exp + totp;
+        totals[0] = nl;
+        totals[1] = P;
+        loff[nl] = P;
+        if (prof) atomicAdd(prof, (unsigned long long)(13 * nl));
     }
 }
 
 // ltile[b] = kept triangle holding slot min(b * PB_TILE, P - 1) (P, nlive on the device).
-__global__ void k_live_tiles(const int64_t* __restrict__ loff, const int32_t* __restrict__ nlive_p,
+__global__ void k_live_tiles(const int64_t* __restrict__ loff, const int64_t* __restrict__ nlive_p,
                              const int64_t* __restrict__ P_p, int64_t max_tiles, int64_t* __restrict__ ltile) {
     const int64_t P = *P_p;
     const int64_t nlive = *nlive_p;
@@ -376,30 +450,27 @@ void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t
     if (ntri == 0 || g->info.probes == 0) return;
     const int T = 256;
     Scratch sc(g->alloc, s, g->dev_err);
-    int32_t* flag = sc.get<int32_t>(2 * (ntri + 1));
-    int32_t* lpos = flag + ntri + 1;
-    int64_t* cost = sc.get<int64_t>(2 * (ntri + 1));
-    int64_t* lcost = cost + ntri + 1;
-    uint8_t* mask = sc.get<uint8_t>(2 * (ntri + 1));
-    uint8_t* lmask = mask + ntri + 1;
     int32_t* L = sc.get<int32_t>(ntri + 1);
     int64_t* loff = sc.get<int64_t>(ntri + 1);
+    uint8_t* lmask = sc.get<uint8_t>(ntri + 1);
+    int64_t* totals = sc.get<int64_t>(2);  // kept triangles, slots
     const int64_t max_tiles = (g->info.probes + LIVE_IDLE * ntri + PB_TILE - 1) / PB_TILE;
     int64_t* ltile = sc.get<int64_t>(max_tiles + 2);
-    // liveness pass reads 30 B and writes 13 B per triangle; scans and compaction ~53 B
+    const int64_t stiles = (ntri + LS_TILE - 1) / LS_TILE;
+    unsigned long long* lsctl = sc.get<unsigned long long>(2 * stiles + 1);  // tile counter, two look-backs
+    // the selection reads 30 B per triangle (6 sigma1, 6 buckets) and writes 13 B per
+    // kept one (counted on the device)
     unsigned long long* prof = nullptr;
     if (profiling_on()) {
         prof = g->prof_bytes + (g->prof_next++ % PROF_SLOTS);
         FOLTY_CUDA(cudaMemsetAsync(prof, 0, sizeof(unsigned long long), s));
     }
-    StageSpan span(ST_PROBE, s, 96 * ntri, prof);
-    FOLTY_LAUNCH(k_live_tri, grid_for(ntri, T), T, 0, s, g->rsig, g->rmin + (int64_t)dir * 6 * ntri, ntri, delta,
-                 flag, cost, mask);
-    exclusive_scan(sc, flag, lpos, ntri);
-    exclusive_scan(sc, cost, lcost, ntri);
-    FOLTY_LAUNCH(k_live_compact, grid_for(ntri + 1, T), T, 0, s, flag, lpos, lcost, mask, ntri, L, loff, lmask);
-    FOLTY_LAUNCH(k_live_tiles, grid_for(max_tiles + 1, T), T, 0, s, loff, lpos + ntri, lcost + ntri, max_tiles, ltile);
-    LiveArgs la{g->tri, g->seg, L, loff, lmask, ltile, lcost + ntri, cnt, bins, g->m_kept, k, prof, rflag};
+    StageSpan span(ST_PROBE, s, 30 * ntri, prof);
+    FOLTY_CUDA(cudaMemsetAsync(lsctl, 0, sizeof(unsigned long long) * (size_t)(2 * stiles + 1), s));
+    FOLTY_LAUNCH(k_live_select, (unsigned)stiles, SCAN_THREADS, 0, s, g->rsig, g->rmin + (int64_t)dir * 6 * ntri, ntri,
+                 delta, lsctl + 1, lsctl + 1 + stiles, (unsigned int*)lsctl, sc.err(), L, loff, lmask, totals, prof);
+    FOLTY_LAUNCH(k_live_tiles, grid_for(max_tiles + 1, T), T, 0, s, loff, totals, totals + 1, max_tiles, ltile);
+    LiveArgs la{g->tri, g->seg, L, loff, lmask, ltile, totals + 1, cnt, bins, g->m_kept, k, prof, rflag};
     int per_sm = 0;
     if (g->ts32) FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<uint32_t, 0, 0>, PB_THREADS, 0));
     else FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<int64_t, 0, 0>, PB_THREADS, 0));
