@@ -200,7 +200,7 @@ __global__ void k_pair_insert(const int32_t* __restrict__ src, const int32_t* __
 // PAIR_COMPACT_ITEMS * blockDim.x slots per step and reserves their entries with one
 // global atomic. *cnt ends at the number of distinct pairs; entries past cap are not
 // written (the caller then abandons the table).
-__global__ void k_pair_compact(const uint64_t* __restrict__ table, int64_t tb, uint64_t* __restrict__ urank,
+__global__ void k_pair_table_compact(const uint64_t* __restrict__ table, int64_t tb, uint64_t* __restrict__ urank,
                                uint32_t* __restrict__ uslot, int* __restrict__ cnt, int cap) {
     __shared__ int wsum[32], base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -2051,7 +2051,7 @@ static bool pair_ids_sort(folty_graph* g, Scratch& sc, const uint32_t* order, ui
         FOLTY_LAUNCH(k_pair_insert, grid_for(m, T), T, 0, s, g->in_src, g->in_dst, m, n, table, lg, slotw, flags);
         urank = sc.get<uint64_t>(cap);
         uslot = sc.get<uint32_t>(cap);
-        FOLTY_LAUNCH(k_pair_compact, grid_for(tb, (int64_t)T * PAIR_COMPACT_ITEMS), T, 0, s, table, tb, urank, uslot,
+        FOLTY_LAUNCH(k_pair_table_compact, grid_for(tb, (int64_t)T * PAIR_COMPACT_ITEMS), T, 0, s, table, tb, urank, uslot,
                      flags + 1, cap);
         const void* ptrs[2] = {flags, flags + 1};
         int sizes[2] = {4, 4};

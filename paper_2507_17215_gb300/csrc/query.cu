@@ -14,6 +14,7 @@
 #include <climits>
 
 #include "internal.cuh"
+#include "scan.cuh"
 #include "probe.cuh"
 
 namespace folty {
@@ -165,42 +166,92 @@ static void launch_threshold(const ThresholdArgs& a, unsigned grid, cudaStream_t
 
 // Solution pairs come in two lists that are already sorted by (x, y): pairs x < y in
 // static-edge order (sorted by (a, b)), and pairs x > y in by_b order (sorted by (b, a)).
-// Entry i < S of the flag array is static edge i's a -> b direction, entry S + j is the
-// b -> a direction of static edge by_b[j].
-__global__ void k_pair_flags(const int32_t* __restrict__ seg_ncert, const int32_t* __restrict__ by_b, int64_t S,
-                             int32_t* __restrict__ flag) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * S;
-         i += (int64_t)gridDim.x * blockDim.x)
-        flag[i] = (i < S) ? (seg_ncert[2 * i] > 0) : (seg_ncert[2 * (int64_t)by_b[i - S] + 1] > 0);
-}
 
-// Compacts both lists: key (x, y), max count and certificates of each solution pair.
-__global__ void k_pair_compact(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t S,
-                               const int32_t* __restrict__ ea, const int32_t* __restrict__ eb,
-                               const int32_t* __restrict__ by_b, const int32_t* __restrict__ seg_max,
-                               const int32_t* __restrict__ seg_ncert, uint64_t* __restrict__ key,
-                               int32_t* __restrict__ cnt_c, int32_t* __restrict__ nc_c) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * S;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        if (!flag[i]) continue;
+// Flags, positions and compaction of the solution pairs in one pass: entry i < S is the
+// directed pair ea -> eb of static edge i, entry S + j the pair eb -> ea of static edge
+// by_b[j] (so both halves come out sorted by (x, y)); an entry is kept when the pair has a
+// certificate. flag[i] (read by the vertex queries), the kept pairs at their prefix
+// positions, and pos[S] = kept pairs x < y, pos[2S] = kept pairs in all. Tiles of
+// PS_TILE entries in block start order, one decoupled look-back by warp 0.
+constexpr int PS_ITEMS = 8;
+constexpr int PS_TILE = SCAN_THREADS * PS_ITEMS;
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_pair_select(const int32_t* __restrict__ seg_ncert,
+                                                              const int32_t* __restrict__ seg_max,
+                                                              const int32_t* __restrict__ ea,
+                                                              const int32_t* __restrict__ eb,
+                                                              const int32_t* __restrict__ by_b, int64_t S,
+                                                              unsigned long long* lb, unsigned int* counter, int* err,
+                                                              int32_t* __restrict__ flag, int32_t* __restrict__ pos,
+                                                              uint64_t* __restrict__ key, int32_t* __restrict__ cnt_c,
+                                                              int32_t* __restrict__ nc_c) {
+    __shared__ uint8_t sflag[PS_TILE];
+    __shared__ int32_t wc[SCAN_THREADS / 32];
+    __shared__ int32_t totc;
+    __shared__ unsigned long long s_exc;
+    __shared__ int64_t s_tile;
+    if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile, n2 = 2 * S;
+    const int64_t base = tile * PS_TILE;
+#pragma unroll
+    for (int i = 0; i < PS_ITEMS; i++) {
+        const int idx = i * SCAN_THREADS + threadIdx.x;
+        const int64_t e = base + idx;
+        int f = 0;
+        if (e < n2) {
+            f = (e < S) ? (seg_ncert[2 * e] > 0) : (seg_ncert[2 * (int64_t)by_b[e - S] + 1] > 0);
+            flag[e] = f;
+        }
+        sflag[idx] = (uint8_t)f;
+    }
+    __syncthreads();
+    int32_t c = 0;
+#pragma unroll
+    for (int i = 0; i < PS_ITEMS; i++) c += sflag[threadIdx.x * PS_ITEMS + i];
+    const int32_t off = block_exclusive_sum<int32_t>(c, wc, &totc);
+    if (threadIdx.x < 32) {
+        volatile unsigned long long* v = lb;
+        const unsigned long long tc = (unsigned long long)totc;
+        if (tile == 0) {
+            if (threadIdx.x == 0) {
+                v[0] = SC_PREFIX | tc;
+                s_exc = 0;
+            }
+        } else {
+            if (threadIdx.x == 0) v[tile] = SC_AGG | tc;
+            const unsigned long long ex = warp_lookback(v, tile, tc, err);
+            if (threadIdx.x == 0) s_exc = ex;
+        }
+    }
+    __syncthreads();
+    int32_t p = (int32_t)s_exc + off;
+#pragma unroll
+    for (int i = 0; i < PS_ITEMS; i++) {
+        const int item = threadIdx.x * PS_ITEMS + i;
+        const int64_t e = base + item;
+        if (e == S) pos[S] = p;
+        if (!sflag[item]) continue;
         int64_t sdir;
         uint64_t x, y;
-        if (i < S) {
-            sdir = 2 * i;
-            x = (uint64_t)ea[i];
-            y = (uint64_t)eb[i];
+        if (e < S) {
+            sdir = 2 * e;
+            x = (uint64_t)ea[e];
+            y = (uint64_t)eb[e];
         } else {
-            const int32_t st = by_b[i - S];
+            const int32_t st = by_b[e - S];
             sdir = 2 * (int64_t)st + 1;
             x = (uint64_t)eb[st];
             y = (uint64_t)ea[st];
         }
-        const int32_t p = pos[i];
         key[p] = (x << 32) | y;
         cnt_c[p] = seg_max[sdir];
         nc_c[p] = seg_ncert[sdir];
+        p++;
     }
+    if (base + PS_TILE >= n2 && threadIdx.x == 0) pos[n2] = (int32_t)s_exc + totc;
 }
+
 
 __device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* __restrict__ a, int64_t n, uint64_t key) {
     int64_t lo = 0;
@@ -247,7 +298,7 @@ __global__ void k_compact_indices(const int32_t* __restrict__ flag, const int32_
 }
 
 // Section 4: number of solution pairs headed by each vertex (flag = pair flags of the
-// two sorted lists, see k_pair_flags).
+// two sorted lists, see k_pair_select).
 __global__ void k_vertex_count(const int32_t* __restrict__ flag, int64_t S, const int32_t* __restrict__ ea,
                                const int32_t* __restrict__ eb, const int32_t* __restrict__ by_b,
                                int32_t* __restrict__ vcnt) {
@@ -372,11 +423,15 @@ static void pairs_device(folty_graph* g, const folty_query_params& q, const int3
         launch_threshold(a, grid_for((mk + TH_BATCH - 1) / TH_BATCH, TH_THREADS), s);
     }
     if (p.cert_flag) exclusive_scan(sc, p.cert_flag, p.cert_pos, g->m);
-    if (n2 > 0) FOLTY_LAUNCH(k_pair_flags, grid_for(n2, T), T, 0, s, p.seg_ncert, g->by_b, S, p.flag);
-    exclusive_scan(sc, p.flag, p.pos, n2);
-    if (n2 > 0)
-        FOLTY_LAUNCH(k_pair_compact, grid_for(n2, T), T, 0, s, p.flag, p.pos, S, g->ea, g->eb, g->by_b, p.seg_max,
-                     p.seg_ncert, p.key, p.cnt_c, p.nc_c);
+    if (n2 > 0) {
+        const int64_t tiles = (n2 + PS_TILE - 1) / PS_TILE;
+        unsigned long long* ctl = sc.get<unsigned long long>(tiles + 1);  // tile counter, look-back
+        FOLTY_CUDA(cudaMemsetAsync(ctl, 0, sizeof(unsigned long long) * (size_t)(tiles + 1), s));
+        FOLTY_LAUNCH(k_pair_select, (unsigned)tiles, SCAN_THREADS, 0, s, p.seg_ncert, p.seg_max, g->ea, g->eb, g->by_b,
+                     S, ctl + 1, (unsigned int*)ctl, sc.err(), p.flag, p.pos, p.key, p.cnt_c, p.nc_c);
+    } else {
+        FOLTY_CUDA(cudaMemsetAsync(p.pos, 0, sizeof(int32_t), s));
+    }
     if (p.vcnt) {
         const int64_t n = g->n;
         FOLTY_CUDA(cudaMemsetAsync(p.vcnt, 0, sizeof(int32_t) * (size_t)(n + 1), s));
