@@ -21,14 +21,15 @@ namespace folty {
 constexpr int BATCH_MAX_BINS = 1024;
 
 // bins[j][e] <- sum_{i <= j} bins[i][e]
-__global__ void k_bins_prefix(int32_t* __restrict__ bins, int k, int64_t mk) {
+template <typename C>
+__global__ void k_bins_prefix(C* __restrict__ bins, int k, int64_t mk) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < mk;
          e += (int64_t)gridDim.x * blockDim.x) {
-        int32_t run = 0;
+        uint32_t run = 0;
         for (int j = 0; j < k; j++) {
             int64_t o = (int64_t)j * mk + e;
             run += bins[o];
-            bins[o] = run;
+            bins[o] = (C)run;
         }
     }
 }
@@ -98,14 +99,19 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
         for (int i : members) D.push_back(qs[i].delta);
         std::sort(D.begin(), D.end());
         D.erase(std::unique(D.begin(), D.end()), D.end());
-        const int64_t per_bin = mk * (int64_t)sizeof(int32_t);
+        // 16-bit bins while no count can reach 2^16 (a count is at most the number of
+        // common neighbours of an edge's ends, at most the largest degree): half the
+        // memory traffic of the bins, their prefix and the threshold's column reads
+        const bool b16 = g->info.max_degree < 65535;
+        const int64_t per_bin = mk * (int64_t)(b16 ? sizeof(uint16_t) : sizeof(int32_t));
         const int64_t budget = bin_budget > 0 ? bin_budget : batch_bin_budget_bytes();
         int64_t chunk = per_bin > 0 ? budget / per_bin : (int64_t)D.size();
         chunk = std::max<int64_t>(1, std::min<int64_t>({chunk, (int64_t)BATCH_MAX_BINS, (int64_t)D.size()}));
         for (size_t c0 = 0; c0 < D.size(); c0 += (size_t)chunk) {
             const int k = (int)std::min<int64_t>(chunk, (int64_t)D.size() - (int64_t)c0);
             Scratch sc(g->alloc, s, g->dev_err);
-            int32_t* bins = sc.get<int32_t>(mk * k);
+            int32_t* bins = b16 ? nullptr : sc.get<int32_t>(mk * k);
+            uint16_t* bins16 = b16 ? sc.get<uint16_t>(mk * k + 2) : nullptr;  // + 2: the last word is whole
             int64_t* dd = sc.get<int64_t>(k);
             std::vector<int64_t> hd(D.begin() + (long)c0, D.begin() + (long)c0 + k);
             // the bin bounds in the store's timestamp type (32-bit offsets: gaps stay
@@ -117,20 +123,23 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
             else
                 FOLTY_CUDA(cudaMemcpyAsync(dd, hd.data(), sizeof(int64_t) * (size_t)k, cudaMemcpyHostToDevice, s));
             if (mk > 0) {
-                FOLTY_CUDA(cudaMemsetAsync(bins, 0, sizeof(int32_t) * (size_t)(mk * k), s));
-                if (P > 0) launch_probe_live(g, hd[k - 1], dir, 1, nullptr, bins, k, dd, s);
-                if (k > 1) FOLTY_LAUNCH(k_bins_prefix, grid_for(mk, 256), 256, 0, s, bins, k, mk);
+                if (b16) FOLTY_CUDA(cudaMemsetAsync(bins16, 0, sizeof(uint16_t) * (size_t)(mk * k + 2), s));
+                else FOLTY_CUDA(cudaMemsetAsync(bins, 0, sizeof(int32_t) * (size_t)(mk * k), s));
+                if (P > 0) launch_probe_live(g, hd[k - 1], dir, 1, nullptr, bins, k, dd, s, nullptr, bins16);
+                if (k > 1 && b16) FOLTY_LAUNCH(k_bins_prefix<uint16_t>, grid_for(mk, 256), 256, 0, s, bins16, k, mk);
+                if (k > 1 && !b16) FOLTY_LAUNCH(k_bins_prefix<int32_t>, grid_for(mk, 256), 256, 0, s, bins, k, mk);
                 FOLTY_CUDA(cudaStreamSynchronize(s));  // the host bounds must outlive the copy
             }
             std::vector<const folty_query_params*> fq;
-            std::vector<const int32_t*> fc;
+            std::vector<CountView> fc;
             std::vector<folty_result*> fo;
             for (int i : members) {
                 auto it = std::lower_bound(hd.begin(), hd.end(), qs[i].delta);
                 if (it == hd.end() || *it != qs[i].delta) continue;  // another chunk
                 const int j = (int)(it - hd.begin());
                 fq.push_back(&qs[i]);
-                fc.push_back(bins + (int64_t)j * mk);
+                if (b16) fc.push_back(CountView{nullptr, bins16 + (int64_t)j * mk});
+                else fc.push_back(CountView{bins + (int64_t)j * mk, nullptr});
                 fo.push_back(&outs[i]);
             }
             finish_queries(g, fq.data(), fc.data(), (int)fq.size(), fo.data(), s);

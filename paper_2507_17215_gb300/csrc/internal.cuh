@@ -251,10 +251,11 @@ bool profiling_on();
 void launch_probe(folty_graph* g, int64_t delta, int dir, int32_t* cnt, cudaStream_t s);
 // Window probes of the roles that can hit (live.cu): mode 0 counts hits at delta into
 // cnt; mode 1 bins gaps <= delta into bins[k][m_kept] against the k sorted bounds
-// `deltas` (in the timestamp store's type).
+// `deltas` (in the timestamp store's type), as int32 or, with bins16 (bins null), as
+// 16-bit counts (element j * m_kept + e of a uint16 array; counts must stay below 2^16).
 // rflag (mode 0, may be null): byte 6 * triangle + role set to 1 when the role has a hit.
 void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t* cnt, int32_t* bins, int k,
-                       const void* deltas, cudaStream_t s, uint8_t* rflag = nullptr);
+                       const void* deltas, cudaStream_t s, uint8_t* rflag = nullptr, uint16_t* bins16 = nullptr);
 void build_role_summary(folty_graph* g, cudaStream_t s);
 // The same pass with the counters in a file-scope device array (noalloc.cu).
 void edge_counts_noalloc(folty_graph* g, int64_t delta, int dir, int32_t* edge_count, cudaStream_t s);
@@ -262,9 +263,14 @@ void edge_counts_noalloc(folty_graph* g, int64_t delta, int dir, int32_t* edge_c
 // order); synchronises the stream.
 void finish_query(folty_graph* g, const folty_query_params& q, const int32_t* cnt, folty_result* out,
                   cudaStream_t s);
+// Per-edge counts of one query: int32 (c32) or 16-bit (c16), the other null.
+struct CountView {
+    const int32_t* c32;
+    const uint16_t* c16;
+};
 // The same for nq queries at once (counts cnts[i]), with two stream synchronisations
 // for the whole group.
-void finish_queries(folty_graph* g, const folty_query_params* const* qs, const int32_t* const* cnts, int nq,
+void finish_queries(folty_graph* g, const folty_query_params* const* qs, const CountView* cnts, int nq,
                     folty_result* const* outs, cudaStream_t s);
 
 void fill_result_host(folty_result* out, int64_t n_pairs, int64_t m, bool want_edges, int64_t n_vertices,

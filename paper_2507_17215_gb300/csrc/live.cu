@@ -309,7 +309,8 @@ struct LiveArgs {
     const int64_t* ltile;
     const int64_t* P;  // device: total slots
     int32_t* cnt;      // MODE 0
-    int32_t* bins;     // MODE 1
+    int32_t* bins;     // MODE 1, or
+    uint32_t* bins16;  // MODE 1: 16-bit counts, two to a word
     int64_t mk;
     int k;             // MODE 1: number of bins
     unsigned long long* prof;  // model bytes of the kept roles (may be null)
@@ -404,7 +405,9 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS*
                 if (a.rflag) a.rflag[6 * (int64_t)a.L[t0 + j] + r] = 1;
             } else {
                 const int jb = lower_bound_ts<TS>(sD, 0, a.k, gap);
-                atomicAdd(&a.bins[(int64_t)jb * a.mk + pos], 1);
+                const int64_t x = (int64_t)jb * a.mk + pos;
+                if (a.bins16) atomicAdd(&a.bins16[x >> 1], 1u << (16 * (int)(x & 1)));
+                else atomicAdd(&a.bins[x], 1);
             }
         }
     }
@@ -445,7 +448,7 @@ static void launch_live_t(const folty_graph* g, int dir, const LiveArgs& la, uns
 // Kept roles for delta (the largest window of the pass), then the probe kernel.
 // mode 0: counts into cnt; mode 1: bins (deltas = k sorted bounds in the store's type).
 void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t* cnt, int32_t* bins, int k,
-                       const void* deltas, cudaStream_t s, uint8_t* rflag) {
+                       const void* deltas, cudaStream_t s, uint8_t* rflag, uint16_t* bins16) {
     const int64_t ntri = g->ntri;
     if (ntri == 0 || g->info.probes == 0) return;
     const int T = 256;
@@ -470,7 +473,8 @@ void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t
     FOLTY_LAUNCH(k_live_select, (unsigned)stiles, SCAN_THREADS, 0, s, g->rsig, g->rmin + (int64_t)dir * 6 * ntri, ntri,
                  delta, lsctl + 1, lsctl + 1 + stiles, (unsigned int*)lsctl, sc.err(), L, loff, lmask, totals, prof);
     FOLTY_LAUNCH(k_live_tiles, grid_for(max_tiles + 1, T), T, 0, s, loff, totals, totals + 1, max_tiles, ltile);
-    LiveArgs la{g->tri, g->seg, L, loff, lmask, ltile, totals + 1, cnt, bins, g->m_kept, k, prof, rflag};
+    LiveArgs la{g->tri, g->seg, L, loff, lmask, ltile, totals + 1, cnt, bins, (uint32_t*)bins16, g->m_kept, k, prof,
+                rflag};
     int per_sm = 0;
     if (g->ts32) FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<uint32_t, 0, 0>, PB_THREADS, 0));
     else FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<int64_t, 0, 0>, PB_THREADS, 0));

@@ -66,6 +66,7 @@ struct ThresholdArgs {
     unsigned long long* n_cert;
     const int32_t* perm;  // with cert_in: certificate flag of input edge perm[i]
     int32_t* cert_in;     // [m] or null
+    const uint16_t* cnt16;  // 16-bit counts instead of cnt (batched queries), or null
 };
 
 // Certificate test of Definition 1.1 with rho = num / den, exact in int64.
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(TH_THREADS) k_threshold(ThresholdArgs a) {
         for (int k = 0; k < TH_BATCH; k++) {
             const int32_t i = k * 32 + lane;
             kb[k] = (i < rem) ? sd[i] : -1;
-            cb[k] = (i < rem) ? cn[i] : 0;
+            cb[k] = (i < rem) ? (a.cnt16 ? (int32_t)a.cnt16[b0 + i] : cn[i]) : 0;
         }
         // universe sizes of the edges with c >= 1, the lookups of all chunks in flight at once
 #pragma unroll
@@ -282,7 +283,8 @@ __global__ void k_pair_merge(const uint64_t* __restrict__ key, const int32_t* __
     }
 }
 
-__global__ void k_edge_counts_input_order(const int32_t* __restrict__ cnt, const int32_t* __restrict__ perm,
+template <typename C>
+__global__ void k_edge_counts_input_order(const C* __restrict__ cnt, const int32_t* __restrict__ perm,
                                           int64_t mk, int32_t* __restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mk;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -407,7 +409,7 @@ static PairStage pair_stage(Scratch& sc, const folty_graph* g, const folty_query
 }
 
 // Certificate test, per-pair reduction, flags, positions, compaction (no host sync).
-static void pairs_device(folty_graph* g, const folty_query_params& q, const int32_t* cnt, const PairStage& p,
+static void pairs_device(folty_graph* g, const folty_query_params& q, const CountView& cnt, const PairStage& p,
                          Scratch& sc, cudaStream_t s) {
     const int T = 256;
     const int64_t mk = g->m_kept;
@@ -416,9 +418,9 @@ static void pairs_device(folty_graph* g, const folty_query_params& q, const int3
     FOLTY_CUDA(cudaMemsetAsync(p.n_cert, 0, sizeof(unsigned long long), s));
     if (p.cert_flag) FOLTY_CUDA(cudaMemsetAsync(p.cert_flag, 0, sizeof(int32_t) * (size_t)(g->m + 1), s));
     if (mk > 0) {
-        ThresholdArgs a{cnt, g->sd, mk, g->ea, g->eb, g->deg, g->common, (int)q.quant, (int)q.universe,
+        ThresholdArgs a{cnt.c32, g->sd, mk, g->ea, g->eb, g->deg, g->common, (int)q.quant, (int)q.universe,
                         (int64_t)q.rho_num, (int64_t)q.rho_den, p.seg_max, p.seg_ncert, p.n_cert,
-                        g->perm, p.cert_flag};
+                        g->perm, p.cert_flag, cnt.c16};
         StageSpan span(ST_THRESHOLD, s, 8 * mk);  // pair key + count per edge
         launch_threshold(a, grid_for((mk + TH_BATCH - 1) / TH_BATCH, TH_THREADS), s);
     }
@@ -442,7 +444,7 @@ static void pairs_device(folty_graph* g, const folty_query_params& q, const int3
     }
 }
 
-void finish_queries(folty_graph* g, const folty_query_params* const* qs, const int32_t* const* cnts, int nq,
+void finish_queries(folty_graph* g, const folty_query_params* const* qs, const CountView* cnts, int nq,
                     folty_result* const* outs, cudaStream_t s) {
     const int T = 256;
     const int64_t S = g->S;
@@ -495,7 +497,12 @@ void finish_queries(folty_graph* g, const folty_query_params* const* qs, const i
             if (q.want_edge_counts && g->m > 0) {
                 int32_t* ec = sc.get<int32_t>(g->m);
                 FOLTY_CUDA(cudaMemsetAsync(ec, 0, sizeof(int32_t) * (size_t)g->m, s));
-                if (mk > 0) FOLTY_LAUNCH(k_edge_counts_input_order, grid_for(mk, T), T, 0, s, cnts[g0 + i], g->perm, mk, ec);
+                if (mk > 0 && cnts[g0 + i].c16)
+                    FOLTY_LAUNCH(k_edge_counts_input_order<uint16_t>, grid_for(mk, T), T, 0, s, cnts[g0 + i].c16, g->perm,
+                                 mk, ec);
+                else if (mk > 0)
+                    FOLTY_LAUNCH(k_edge_counts_input_order<int32_t>, grid_for(mk, T), T, 0, s, cnts[g0 + i].c32, g->perm,
+                                 mk, ec);
                 FOLTY_CUDA(cudaMemcpyAsync(out->edge_count, ec, sizeof(int32_t) * (size_t)g->m, cudaMemcpyDeviceToHost, s));
             }
         }
@@ -506,7 +513,8 @@ void finish_queries(folty_graph* g, const folty_query_params* const* qs, const i
 void finish_query(folty_graph* g, const folty_query_params& q, const int32_t* cnt, folty_result* out,
                   cudaStream_t s) {
     const folty_query_params* qp = &q;
-    finish_queries(g, &qp, &cnt, 1, &out, s);
+    const CountView cv{cnt, nullptr};
+    finish_queries(g, &qp, &cv, 1, &out, s);
 }
 
 // ------------------------------------------------------------------ all-existential triples

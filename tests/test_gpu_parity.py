@@ -226,6 +226,33 @@ def test_batch_equals_sequential(F):
         assert pairs_of(a) == pairs_of(b), str(q)
 
 
+def test_batch_with_a_hub_of_degree_past_16_bits(F):
+    """A vertex with 66,000 neighbours: batched counts no longer fit 16-bit bins, so the
+    batch keeps 32-bit ones; results equal the single queries' and the oracle's."""
+    rng = np.random.default_rng(12)
+    n, leaves = 70_000, 66_000
+    src = [np.zeros(leaves, np.int32)]
+    dst = [np.arange(1, leaves + 1, dtype=np.int32)]
+    a = rng.integers(1, 3000, 40_000).astype(np.int32)  # edges among low leaves: triangles with the hub
+    b = rng.integers(1, 3000, 40_000).astype(np.int32)
+    src.append(a)
+    dst.append(b)
+    src, dst = np.concatenate(src), np.concatenate(dst)
+    t = rng.integers(0, 5000, src.shape[0]).astype(np.int64)
+    o = np.argsort(t, kind="stable")
+    g = W.TemporalGraph(n, src[o], dst[o], t[o])
+    qs = [W.Query(d, 1, 10, W.Q_FORALL_T, dr, W.U_COMMON, True) for d in (5, 100, 2000) for dr in (W.DIR_OUT, W.DIR_EITHER)]
+    with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
+        assert G.info()["max_degree"] >= 65535
+        seq = [G.query(q) for q in qs]
+        bat = G.query_batch(qs)
+    with oracle.OracleGraph.of(g) as og:
+        for q, a1, b1 in zip(qs, seq, bat):
+            want = og.query(q)
+            _assert_same(a1, want, str(q))
+            _assert_same(b1, want, str(q))
+
+
 def test_full_size_medium_workload_sampled(F):
     """The medium workload at full size (1M vertices, 20M edges), as the benchmark runs
     it: every query of the workload, checked on sampled edges and sampled pairs."""
