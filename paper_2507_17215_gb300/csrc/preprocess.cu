@@ -879,25 +879,46 @@ __global__ void k_tail_degrees(const int32_t* __restrict__ L, const int* __restr
 
 // Entry e of the concatenated full rows of the local vertices (eoff = prefix of d0):
 // alive neighbours go to the owner's local row (order within a row is irrelevant).
+constexpr int FILL_RUN = 8;  // consecutive entries per thread in the subgraph fills
+
 __global__ void k_tail_fill(const int32_t* __restrict__ L, const int32_t* __restrict__ eoff, int tn,
                             const int32_t* __restrict__ rowptr, const int32_t* __restrict__ adj,
                             const int32_t* __restrict__ rnd, const int32_t* __restrict__ gmap,
                             const int32_t* __restrict__ lrow, const int32_t* __restrict__ ld,
                             int32_t* __restrict__ fillc, uint32_t* __restrict__ ladj, int* __restrict__ err) {
     const int64_t total = eoff[tn];
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int lo = 0, hi = tn - 1;  // last owner with eoff[owner] <= e
+    // a thread takes FILL_RUN consecutive entries: one search for the first one's owner,
+    // then the owner moves forward (rows average a few entries), and the alive entries of
+    // each owner's part of the run take their places with one atomic (a hub's counter
+    // would serialise one atomic per entry)
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * FILL_RUN;
+    for (int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * FILL_RUN; e0 < total; e0 += step) {
+        int lo = 0, hi = tn - 1;  // last owner with eoff[owner] <= e0
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
-            if (eoff[mid] <= e) lo = mid;
+            if (eoff[mid] <= e0) lo = mid;
             else hi = mid - 1;
         }
-        int32_t v = adj[rowptr[L[lo]] + (int32_t)(e - eoff[lo])];
-        if (rnd[v] < 0) {
-            int p = atomicAdd(&fillc[lo], 1);
-            if (p < ld[lo]) ladj[lrow[lo] + p] = (uint32_t)gmap[v];
-            else atomicExch(err, 3);  // more alive neighbours than the degree says
+        const int64_t e1 = min(e0 + FILL_RUN, total);
+        int64_t e = e0;
+        while (e < e1) {
+            while (lo + 1 < tn && eoff[lo + 1] <= e) lo++;
+            const int64_t end = (lo + 1 < tn) ? min(e1, (int64_t)eoff[lo + 1]) : e1;  // this owner's part
+            uint32_t keep[FILL_RUN];
+            int nk = 0;
+            const int32_t rb = rowptr[L[lo]];
+            for (; e < end; e++) {
+                const int32_t v = adj[rb + (int32_t)(e - eoff[lo])];
+                if (rnd[v] < 0) keep[nk++] = (uint32_t)gmap[v];
+            }
+            if (nk) {
+                const int p = atomicAdd(&fillc[lo], nk);
+                if (p + nk <= ld[lo]) {
+                    for (int q = 0; q < nk; q++) ladj[lrow[lo] + p + q] = keep[q];
+                } else {
+                    atomicExch(err, 3);  // more alive neighbours than the degree says
+                }
+            }
         }
     }
 }
@@ -1296,19 +1317,23 @@ __global__ void k_solo_fill(const int* __restrict__ ctl, const int32_t* __restri
                             int32_t* __restrict__ fc, uint16_t* __restrict__ sadj, int* __restrict__ err) {
     if (ctl[C_SOLO] != 1 || ctl[C_ERR] != 0) return;
     const int64_t total = eo[SOLO_CAP];
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int lo = 0, hi = SOLO_CAP - 1;  // last owner with eo[owner] <= e
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * FILL_RUN;
+    for (int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * FILL_RUN; e0 < total; e0 += step) {
+        int lo = 0, hi = SOLO_CAP - 1;  // last owner with eo[owner] <= e0
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (eo[mid] <= e) lo = mid;
+            if (eo[mid] <= e0) lo = mid;
             else hi = mid - 1;
         }
-        const int32_t m = map2[ladj[lrow[slist[lo]] + (int32_t)(e - eo[lo])]];
-        if (m >= 0) {
-            const int p = atomicAdd(&fc[lo], 1);
-            if (p < sdeg[lo]) sadj[srow[lo] + p] = (uint16_t)m;
-            else atomicExch(err, 4);
+        const int64_t e1 = min(e0 + FILL_RUN, total);
+        for (int64_t e = e0; e < e1; e++) {
+            while (lo + 1 < SOLO_CAP && eo[lo + 1] <= e) lo++;
+            const int32_t m = map2[ladj[lrow[slist[lo]] + (int32_t)(e - eo[lo])]];
+            if (m >= 0) {
+                const int p = atomicAdd(&fc[lo], 1);
+                if (p < sdeg[lo]) sadj[srow[lo] + p] = (uint16_t)m;
+                else atomicExch(err, 4);
+            }
         }
     }
 }
