@@ -202,37 +202,44 @@ __device__ __forceinline__ unsigned digit_peers(unsigned d) {
     return m;
 }
 
-// One pass of one 8-bit digit over a tile of RS_TILE keys:
+// One pass of one 8-bit digit over a tile of NT * RS_ITEMS keys:
 //  1. every load of the tile is issued before any is used; keys and values are staged
 //     in shared memory in load order;
 //  2. ranks within the tile: warp w owns keys [w * 32 * ITEMS, ...) in order, ranked by
 //     digit with per-bit ballots and per-warp 16-bit counters (stable);
-//  3. thread d (one per digit) turns the per-warp counts into offsets, publishes the
-//     tile's count of digit d and looks back over earlier tiles for its global offset;
+//  3. thread d < RS_BINS (one per digit) turns the per-warp counts into offsets,
+//     publishes the tile's count of digit d and looks back over earlier tiles for its
+//     global offset;
 //  4. a 16-bit permutation in shared memory lists the tile in digit order, and the
 //     writes of each digit's run are contiguous. Positions are 32-bit (n < 2^32).
 // V: values travel with the keys (a keys-only sort moves 8 bytes a key instead of 12).
-template <bool V>
-__global__ void __launch_bounds__(RS_THREADS, V ? 3 : 4) k_rs_onesweep(OnesweepArgs a) {
+// NT: threads per block. The keys-only sort runs 512-thread blocks: tiles of 8192 keys
+// halve the tiles in flight, and with them the depth of every look-back, and double the
+// length of each digit's written run.
+template <bool V, int NT>
+__global__ void __launch_bounds__(NT, V ? 3 : (NT == 512 ? 2 : 4)) k_rs_onesweep(OnesweepArgs a) {
+    constexpr int WARPS = NT / 32;
+    constexpr int TILE = NT * RS_ITEMS;
+    static_assert(NT % RS_BINS == 0 && NT >= RS_BINS, "one thread per digit at least");
     extern __shared__ __align__(16) unsigned char rs_smem[];
-    uint64_t* skey = (uint64_t*)rs_smem;                    // RS_TILE, load order
-    uint32_t* sval = (uint32_t*)(skey + RS_TILE);           // RS_TILE, load order (V only)
-    uint16_t* sperm = (uint16_t*)(V ? (void*)(sval + RS_TILE) : (void*)sval);  // RS_TILE, digit order -> load order
-    __shared__ uint16_t wh[RS_WARPS][RS_BINS];              // per-warp counts, then offsets
+    uint64_t* skey = (uint64_t*)rs_smem;                    // TILE, load order
+    uint32_t* sval = (uint32_t*)(skey + TILE);              // TILE, load order (V only)
+    uint16_t* sperm = (uint16_t*)(V ? (void*)(sval + TILE) : (void*)sval);  // TILE, digit order -> load order
+    __shared__ uint16_t wh[WARPS][RS_BINS];                 // per-warp counts, then offsets
     __shared__ uint32_t bstart[RS_BINS];                    // tile-local start of each digit
     __shared__ uint32_t adj[RS_BINS];                       // final position of digit-order slot j: adj + j
     __shared__ uint32_t wt[RS_BINS / 32];
     __shared__ int s_tile, s_fail;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&wh[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < WARPS * RS_BINS; i += NT) (&wh[0][0])[i] = 0;
     if (threadIdx.x == 0) {
         s_tile = (int)atomicAdd(a.tile_counter, 1u);
         s_fail = 0;
     }
     __syncthreads();
     const int64_t tile = s_tile;
-    const int64_t t0 = tile * RS_TILE;
-    const int tn = (int)min((int64_t)RS_TILE, a.n - t0);
+    const int64_t t0 = tile * TILE;
+    const int tn = (int)min((int64_t)TILE, a.n - t0);
     const uint64_t* kin = a.keys + t0;
     const uint32_t* vin = a.vals + t0;
     const int wbase = warp * 32 * RS_ITEMS;
@@ -267,44 +274,49 @@ __global__ void __launch_bounds__(RS_THREADS, V ? 3 : 4) k_rs_onesweep(OnesweepA
     for (int i = 0; i < RS_ITEMS; i++) {
         const int idx = wbase + i * 32 + lane;
         const bool valid = idx < tn;
-        const unsigned d = info[i];
+        const unsigned dd = info[i];
         const unsigned peers = pm[i] & __ballot_sync(0xffffffffu, valid);
         unsigned before = 0;
-        if (valid) before = wh[warp][d];
+        if (valid) before = wh[warp][dd];
         __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) wh[warp][d] = (uint16_t)(before + __popc(peers));
+        if (valid && lane == __ffs(peers) - 1) wh[warp][dd] = (uint16_t)(before + __popc(peers));
         __syncwarp();
-        info[i] = d | ((before + __popc(peers & lt_mask)) << 8);
+        info[i] = dd | ((before + __popc(peers & lt_mask)) << 8);
     }
     __syncthreads();
-    // ---- 3. per digit (thread d): warp offsets, tile count, publish, look back
-    const int d = threadIdx.x;  // RS_THREADS == RS_BINS
+    // ---- 3. per digit (thread d < RS_BINS): warp offsets, tile count, publish, look back
+    const int d = threadIdx.x;
+    const bool dig = d < RS_BINS;  // whole warps: RS_BINS is a multiple of 32
     uint32_t cnt = 0;
+    if (dig) {
 #pragma unroll
-    for (int w = 0; w < RS_WARPS; w++) {
-        const uint32_t c = wh[w][d];
-        wh[w][d] = (uint16_t)cnt;
-        cnt += c;
+        for (int w = 0; w < WARPS; w++) {
+            const uint32_t c = wh[w][d];
+            wh[w][d] = (uint16_t)cnt;
+            cnt += c;
+        }
     }
     volatile unsigned long long* lb = a.lb;
-    lb[tile * RS_BINS + d] = (tile == 0 ? LB_PREFIX : LB_AGG) | cnt;
-    uint32_t bs;
-    {   // tile-local exclusive scan of the digit counts
+    if (dig) lb[tile * RS_BINS + d] = (tile == 0 ? LB_PREFIX : LB_AGG) | cnt;
+    uint32_t bs = 0;
+    {   // tile-local exclusive scan of the digit counts (warps of digit threads)
         uint32_t inc = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += y;
         }
-        if (lane == 31) wt[warp] = inc;
+        if (dig && lane == 31) wt[warp] = inc;
         __syncthreads();
-        uint32_t off = 0;
-        for (int j = 0; j < warp; j++) off += wt[j];
-        bs = off + inc - cnt;
-        bstart[d] = bs;
+        if (dig) {
+            uint32_t off = 0;
+            for (int j = 0; j < warp; j++) off += wt[j];
+            bs = off + inc - cnt;
+            bstart[d] = bs;
+        }
     }
     unsigned long long excl = 0;
-    if (tile > 0) {
+    if (dig && tile > 0) {
         // four entries in flight per step; an entry not yet published is polled again
         int64_t p = tile - 1;
         long long t_start = 0;
@@ -340,7 +352,7 @@ __global__ void __launch_bounds__(RS_THREADS, V ? 3 : 4) k_rs_onesweep(OnesweepA
         }
         lb[tile * RS_BINS + d] = LB_PREFIX | (excl + cnt);
     }
-    adj[d] = (uint32_t)((unsigned long long)a.base[d] + excl) - bs;  // mod 2^32
+    if (dig) adj[d] = (uint32_t)((unsigned long long)a.base[d] + excl) - bs;  // mod 2^32
     __syncthreads();
     if (s_fail) return;  // block-uniform: positions are unknown
     // ---- 4. digit-order permutation, then contiguous runs
@@ -353,7 +365,7 @@ __global__ void __launch_bounds__(RS_THREADS, V ? 3 : 4) k_rs_onesweep(OnesweepA
         }
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < tn; j += RS_THREADS) {
+    for (int j = threadIdx.x; j < tn; j += NT) {
         const int src = sperm[j];
         const uint64_t kk = skey[src];
         const uint32_t pos = adj[(unsigned)(kk >> a.shift) & (RS_BINS - 1)] + (uint32_t)j;
@@ -362,8 +374,9 @@ __global__ void __launch_bounds__(RS_THREADS, V ? 3 : 4) k_rs_onesweep(OnesweepA
     }
 }
 
+constexpr int RS_NT_K = 512;  // threads of a keys-only block
 constexpr size_t RS_DYN_SMEM = RS_TILE * (sizeof(uint64_t) + sizeof(uint32_t) + sizeof(uint16_t));
-constexpr size_t RS_DYN_SMEM_K = RS_TILE * (sizeof(uint64_t) + sizeof(uint16_t));
+constexpr size_t RS_DYN_SMEM_K = (size_t)RS_NT_K * RS_ITEMS * (sizeof(uint64_t) + sizeof(uint16_t));
 
 // Sorts by the digits of bits [lo, lo + bits); vals may be null (keys only).
 static bool radix_sort_impl(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
@@ -371,8 +384,10 @@ static bool radix_sort_impl(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uin
     if (n <= 1 || bits <= 0) return false;
     if (n >= (int64_t)0xffffffffll) fail(FOLTY_EINVAL, "radix sort: too many keys");
     cudaStream_t s = sc.stream();
+    const bool kv = vals != nullptr;
     const int passes = (bits + RS_BITS - 1) / RS_BITS;
-    const int64_t tiles = (n + RS_TILE - 1) / RS_TILE;
+    const int64_t tile = kv ? RS_TILE : (int64_t)RS_NT_K * RS_ITEMS;
+    const int64_t tiles = (n + tile - 1) / tile;
     uint32_t* hist = sc.get<uint32_t>(2 * RS_MAX_PASSES * RS_BINS);
     uint32_t* base = hist + RS_MAX_PASSES * RS_BINS;
     unsigned long long* lb = sc.get<unsigned long long>(tiles * RS_BINS);
@@ -383,12 +398,14 @@ static bool radix_sort_impl(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uin
         FOLTY_LAUNCH(k_rs_hist_all, grid_for(n, RS_THREADS, 4), RS_THREADS, 0, s, keys, n, lo, passes, hist);
         FOLTY_LAUNCH(k_rs_bases, 1, RS_BINS, 0, s, hist, passes, base);
     }
-    const bool kv = vals != nullptr;
-    if (kv) FOLTY_CUDA(cudaFuncSetAttribute(k_rs_onesweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_DYN_SMEM));
-    else {
-        FOLTY_CUDA(cudaFuncSetAttribute(k_rs_onesweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_DYN_SMEM_K));
-        // four blocks of 46 KB each need the largest shared-memory carveout
-        FOLTY_CUDA(cudaFuncSetAttribute(k_rs_onesweep<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    if (kv) {
+        FOLTY_CUDA(cudaFuncSetAttribute(k_rs_onesweep<true, RS_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)RS_DYN_SMEM));
+    } else {
+        FOLTY_CUDA(cudaFuncSetAttribute(k_rs_onesweep<false, RS_NT_K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)RS_DYN_SMEM_K));
+        // two blocks of 90 KB each need the largest shared-memory carveout
+        FOLTY_CUDA(cudaFuncSetAttribute(k_rs_onesweep<false, RS_NT_K>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     }
     bool alt = false;
     for (int p = 0; p < passes; p++) {
@@ -398,8 +415,8 @@ static bool radix_sort_impl(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uin
         OnesweepArgs oa{alt ? keys_alt : keys, kv ? (alt ? vals_alt : vals) : nullptr, alt ? keys : keys_alt,
                         kv ? (alt ? vals : vals_alt) : nullptr, n, lo + RS_BITS * p, base + p * RS_BINS, lb, counter,
                         sc.err(), LOOKBACK_TIMEOUT_NS};
-        if (kv) FOLTY_LAUNCH(k_rs_onesweep<true>, (unsigned)tiles, RS_THREADS, RS_DYN_SMEM, s, oa);
-        else FOLTY_LAUNCH(k_rs_onesweep<false>, (unsigned)tiles, RS_THREADS, RS_DYN_SMEM_K, s, oa);
+        if (kv) FOLTY_LAUNCH((k_rs_onesweep<true, RS_THREADS>), (unsigned)tiles, RS_THREADS, RS_DYN_SMEM, s, oa);
+        else FOLTY_LAUNCH((k_rs_onesweep<false, RS_NT_K>), (unsigned)tiles, RS_NT_K, RS_DYN_SMEM_K, s, oa);
         alt = !alt;
     }
     return alt;
