@@ -248,14 +248,19 @@ __global__ void k_pair_table_compact(const uint64_t* __restrict__ table, int64_t
 }
 
 // Pair id j (position in rank order) of every table slot in use, and the pair's ends.
+// The ranks come from a sort whose look-back could in principle run out (the graph's
+// error word, checked by the host before the ids are used, then says so): slots and ends
+// are kept inside their arrays whatever the input.
 __global__ void k_pair_ids(const uint64_t* __restrict__ urank, const uint32_t* __restrict__ uslot, int32_t S,
-                           int32_t n, int32_t* __restrict__ sid, int32_t* __restrict__ ea, int32_t* __restrict__ eb) {
+                           int32_t n, int64_t tb, int32_t* __restrict__ sid, int32_t* __restrict__ ea,
+                           int32_t* __restrict__ eb) {
     for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < S; j += gridDim.x * blockDim.x) {
-        sid[uslot[j]] = j;
+        const uint32_t sl = uslot[j];
+        if (sl < tb) sid[sl] = j;
         int32_t x, y;
         pair_of_rank(urank[j], n, x, y);
-        ea[j] = x;
-        eb[j] = y;
+        ea[j] = min(x, n - 1);
+        eb[j] = min(y, n - 1);
     }
 }
 
@@ -275,8 +280,8 @@ __global__ void k_pair_pack(const uint32_t* __restrict__ slotw, const uint32_t* 
 // j = word mod 2^ib (input index order[j], or j) of pair id and direction word >> ib.
 template <typename TS>
 __global__ void k_pair_store(const uint64_t* __restrict__ packed, const uint32_t* __restrict__ order, int64_t mk,
-                             int ib, const TS* __restrict__ t, int32_t* __restrict__ perm, TS* __restrict__ T,
-                             int32_t* __restrict__ sd, int32_t* __restrict__ seg) {
+                             int32_t S, int ib, const TS* __restrict__ t, int32_t* __restrict__ perm,
+                             TS* __restrict__ T, int32_t* __restrict__ sd, int32_t* __restrict__ seg) {
     const uint64_t jm = (1ull << ib) - 1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mk; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t pk = __ldcs(packed + i);
@@ -286,7 +291,8 @@ __global__ void k_pair_store(const uint64_t* __restrict__ packed, const uint32_t
         T[i] = t[o];
         const int32_t c = (int32_t)(pk >> ib);
         __stcs(sd + i, c);
-        if (i == 0 || (int32_t)(packed[i - 1] >> (ib + 1)) != (c >> 1)) {
+        // (c < 2S unless the pair ids' sort failed, which the host learns right after)
+        if ((unsigned)c < (unsigned)(2 * S) && (i == 0 || (int32_t)(packed[i - 1] >> (ib + 1)) != (c >> 1))) {
             seg[c & ~1] = (int32_t)i;
             seg[(c & ~1) + 1] = -1;
         }
@@ -299,7 +305,7 @@ __global__ void k_segments_split(const int32_t* __restrict__ sd, int64_t mk, int
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mk;
          i += (int64_t)gridDim.x * blockDim.x) {
         int32_t c = sd[i];
-        if ((c & 1) && (i == 0 || sd[i - 1] != c)) seg[c] = (int32_t)i;  // c = 2s+1
+        if ((c & 1) && (unsigned)c < (unsigned)(2 * S) && (i == 0 || sd[i - 1] != c)) seg[c] = (int32_t)i;  // c = 2s+1
     }
 }
 
@@ -1924,27 +1930,40 @@ __device__ __forceinline__ void warp_intersect(const int32_t* __restrict__ nbr, 
     __syncwarp();
 }
 
+// Also the probe slots of all triangles (sum over triangles of the three edges' temporal
+// edge counts sig) into *probes, so that they are known before the triangles are written.
 __global__ void k_tri_count(const int32_t* __restrict__ outptr, const int32_t* __restrict__ out_nbr,
-                            const int32_t* __restrict__ out_src, int32_t S, int32_t* __restrict__ cnt,
-                            unsigned long long* __restrict__ merged) {
-    unsigned long long acc = 0;
+                            const int32_t* __restrict__ out_src, const int32_t* __restrict__ out_eid,
+                            const int32_t* __restrict__ sig, int32_t S, int32_t* __restrict__ cnt,
+                            unsigned long long* __restrict__ merged, unsigned long long* __restrict__ probes) {
+    unsigned long long acc = 0, pacc = 0;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < S;
          j += (int64_t)gridDim.x * blockDim.x) {
         int32_t u = out_src[j], v = out_nbr[j];
         int32_t i1 = outptr[u], e1 = outptr[u + 1], i2 = outptr[v], e2 = outptr[v + 1];
         acc += (unsigned long long)((e1 - i1) + (e2 - i2));
         int32_t c = 0;
+        unsigned long long ps = 0;
         while (i1 < e1 && i2 < e2) {
             int32_t x = out_nbr[i1], y = out_nbr[i2];
-            c += (x == y);
+            if (x == y) {
+                c++;
+                ps += (unsigned long long)(sig[out_eid[i1]] + sig[out_eid[i2]]);
+            }
             i1 += (x <= y);
             i2 += (y <= x);
         }
+        if (c) ps += (unsigned long long)c * (unsigned long long)sig[out_eid[j]];
+        pacc += ps;
         cnt[j] = c;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        pacc += __shfl_xor_sync(0xffffffffu, pacc, o);
+    }
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(merged, acc);
+    if ((threadIdx.x & 31) == 0 && pacc) atomicAdd(probes, pacc);
 }
 
 // tile_tri[b] = triangle holding probe min(b * tile, P - 1), for b in [0, tiles].
@@ -2094,7 +2113,6 @@ static bool pair_ids_sort(folty_graph* g, Scratch& sc, const uint32_t* order, ui
     uint32_t* uslot_alt = sc.get<uint32_t>(S);
     const int rank_bits = bit_length((uint64_t)n * (uint64_t)(n - 1) / 2);
     const bool ualt = radix_sort_pairs(sc, urank, urank_alt, uslot, uslot_alt, S, rank_bits);
-    sort_check(g, s);
     const uint64_t* ur = ualt ? urank_alt : urank;
     const uint32_t* us = ualt ? uslot_alt : uslot;
     g->S = S;
@@ -2102,7 +2120,7 @@ static bool pair_ids_sort(folty_graph* g, Scratch& sc, const uint32_t* order, ui
     g->eb = graph_alloc<int32_t>(g, S, s);
     g->seg = graph_alloc<int32_t>(g, 2 * (int64_t)S + 1, s);
     int32_t* sid = sc.get<int32_t>(tb);
-    FOLTY_LAUNCH(k_pair_ids, grid_for(S, T), T, 0, s, ur, us, S, n, sid, g->ea, g->eb);
+    FOLTY_LAUNCH(k_pair_ids, grid_for(S, T), T, 0, s, ur, us, S, n, tb, sid, g->ea, g->eb);
     // edges by (pair id, direction, time rank): keys only, on the id and direction bits
     uint64_t* packed = sc.get<uint64_t>(m);
     uint64_t* packed_alt = sc.get<uint64_t>(m);
@@ -2111,10 +2129,10 @@ static bool pair_ids_sort(folty_graph* g, Scratch& sc, const uint32_t* order, ui
     const uint64_t* sp = palt ? packed_alt : packed;
     if (t32) FOLTY_LAUNCH(k_offsets32, grid_for(m, T), T, 0, s, g->in_t, m, g->tmin, t32);
     if (g->ts32)
-        FOLTY_LAUNCH(k_pair_store<uint32_t>, grid_for(mk, T), T, 0, s, sp, order, mk, ib, t32, g->perm,
+        FOLTY_LAUNCH(k_pair_store<uint32_t>, grid_for(mk, T), T, 0, s, sp, order, mk, S, ib, t32, g->perm,
                      (uint32_t*)g->T, g->sd, g->seg);
     else
-        FOLTY_LAUNCH(k_pair_store<int64_t>, grid_for(mk, T), T, 0, s, sp, order, mk, ib, g->in_t, g->perm,
+        FOLTY_LAUNCH(k_pair_store<int64_t>, grid_for(mk, T), T, 0, s, sp, order, mk, S, ib, g->in_t, g->perm,
                      (int64_t*)g->T, g->sd, g->seg);
     FOLTY_LAUNCH(k_segments_split, grid_for(mk, T), T, 0, s, g->sd, mk, S, g->seg);
     FOLTY_LAUNCH(k_segments_fix, grid_for(S, T), T, 0, s, S, mk, g->seg);
@@ -2372,26 +2390,29 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     FOLTY_CUDA(cudaMemsetAsync(g->common, 0, sizeof(int32_t) * ((size_t)S > 0 ? (size_t)S : 1), s));
     int32_t* tcnt = sc.get<int32_t>((int64_t)S + 1);
     int64_t* toff = sc.get<int64_t>((int64_t)S + 1);
-    unsigned long long* merged = sc.get<unsigned long long>(1);
-    FOLTY_CUDA(cudaMemsetAsync(merged, 0, sizeof(unsigned long long), s));
-    if (S > 0) FOLTY_LAUNCH(k_tri_count, grid_for(S, T), T, 0, s, outptr, out_nbr, out_src, S, tcnt, merged);
-    exclusive_scan(sc, tcnt, toff, S);
-    FOLTY_LAUNCH(k_max_i32, grid_for(n, T), T, 0, s, g->deg, (int64_t)n, stat + 0);
+    unsigned long long* merged = sc.get<unsigned long long>(2);  // list lengths merged, probe slots
+    FOLTY_CUDA(cudaMemsetAsync(merged, 0, 2 * sizeof(unsigned long long), s));
     int32_t* sig = sc.get<int32_t>(S);
     if (S > 0) FOLTY_LAUNCH(k_max_sigma, grid_for(S, T), T, 0, s, g->seg, S, sig, stat + 2);
+    if (S > 0)
+        FOLTY_LAUNCH(k_tri_count, grid_for(S, T), T, 0, s, outptr, out_nbr, out_src, out_eid, sig, S, tcnt, merged,
+                     merged + 1);
+    exclusive_scan(sc, tcnt, toff, S);
+    FOLTY_LAUNCH(k_max_i32, grid_for(n, T), T, 0, s, g->deg, (int64_t)n, stat + 0);
     {
-        const void* ptrs[8] = {toff + S, stat + 0, stat + 1, stat + 2, merged, peel_ctl + C_ERR,
+        const void* ptrs[9] = {toff + S, stat + 0, stat + 1, stat + 2, merged, merged + 1, peel_ctl + C_ERR,
                                peel_ctl + C_ROUNDS, peel_ctl + C_ALPHA};
-        int sizes[8] = {8, 4, 4, 4, 8, 4, 4, 4};
-        int64_t outv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        read_back(g, ptrs, sizes, peel_ctl ? 8 : 5, outv, s);  // no peeling state for n = 0
-        if (outv[5] == 1) fail(FOLTY_ETIMEOUT, "peeling: a grid barrier wait ran out");
-        if (outv[5] != 0)
-            fail(FOLTY_ECUDA, "peeling: internal error " + std::to_string(outv[5]) +
+        int sizes[9] = {8, 4, 4, 4, 8, 8, 4, 4, 4};
+        int64_t outv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        read_back(g, ptrs, sizes, peel_ctl ? 9 : 6, outv, s);  // no peeling state for n = 0
+        if (outv[6] == 1) fail(FOLTY_ETIMEOUT, "peeling: a grid barrier wait ran out");
+        if (outv[6] != 0)
+            fail(FOLTY_ECUDA, "peeling: internal error " + std::to_string(outv[6]) +
                                   " (2: a vertex list overflowed, 3/4: a subgraph row count differs, 5: a row entry "
                                   "is out of range)");
-        g->info.peel_rounds = (int32_t)outv[6];
-        g->info.degeneracy = (int32_t)outv[7];
+        g->info.peel_rounds = (int32_t)outv[7];
+        g->info.degeneracy = (int32_t)outv[8];
+        g->info.probes = outv[5];
         g->ntri = outv[0];
         g->info.max_degree = (int32_t)outv[1];
         g->info.max_out_degree = (int32_t)outv[2];
@@ -2407,7 +2428,6 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
                      g->tri, cost, g->common);
     exclusive_scan(sc, cost, g->tri_off, ntri);
     g->info.triangles = ntri;
-    g->info.probes = read_i64(g, g->tri_off + ntri, s);
     // tile -> first triangle map of the probe kernels (query independent)
     g->n_tiles = (g->info.probes + PB_TILE - 1) / PB_TILE;
     g->tile_tri = graph_alloc<int64_t>(g, g->n_tiles + 1, s);
