@@ -150,10 +150,12 @@ __device__ __forceinline__ bool bucket_live(uint8_t b, int64_t delta) {
 // Kept roles of every triangle for one query, selected and compacted in one pass: kept
 // triangle j = L[j] with its role mask lmask[j] and its first probe slot loff[j] (prefix
 // of the kept triangles' costs = kept probes + LIVE_IDLE idle slots); totals[0] = kept
-// triangles, totals[1] = slots, loff[totals[0]] = totals[1]. Tiles of LS_TILE triangles
-// are taken in block start order; the two prefix sums (kept count, cost) come from a
-// block scan and two decoupled look-backs by warp 0. *prof (may be null) gets the bytes
-// written for the kept triangles.
+// triangles, totals[1] = slots, loff[totals[0]] = totals[1]; and the probe tiles' map:
+// ltile[b] = kept triangle holding slot min(b * PB_TILE, slots - 1) for b <= the number
+// of probe tiles (each kept triangle writes the tile starts inside its slots). Tiles of
+// LS_TILE triangles are taken in block start order; the two prefix sums (kept count,
+// cost) come from a block scan and two decoupled look-backs by warp 0. *prof (may be
+// null) gets the bytes written for the kept triangles.
 constexpr int LS_ITEMS = 8;
 constexpr int LS_TILE = SCAN_THREADS * LS_ITEMS;  // 2048 triangles
 
@@ -164,6 +166,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const int32_t* __r
                                                               int* err, int32_t* __restrict__ L,
                                                               int64_t* __restrict__ loff, uint8_t* __restrict__ lmask,
                                                               int64_t* __restrict__ totals,
+                                                              int64_t* __restrict__ ltile, int64_t max_tiles,
                                                               unsigned long long* __restrict__ prof) {
     constexpr int PADW = 16;  // one pad element per 128 bytes of int64
     __shared__ int64_t scost[LS_TILE + LS_TILE / PADW];
@@ -246,6 +249,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const int32_t* __r
             L[jc] = (int32_t)(base + item);
             loff[jc] = jp;
             lmask[jc] = smask[item];
+            for (int64_t b = (jp + PB_TILE - 1) / PB_TILE; b * PB_TILE < jp + v && b <= max_tiles; b++) ltile[b] = jc;
             jc++;
             jp += v;
         }
@@ -255,29 +259,12 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const int32_t* __r
         totals[0] = nl;
         totals[1] = P;
         loff[nl] = P;
+        const int64_t tiles = (P + PB_TILE - 1) / PB_TILE;
+        if (P > 0 && tiles <= max_tiles) ltile[tiles] = nl - 1;
         if (prof) atomicAdd(prof, (unsigned long long)(13 * nl));
     }
 }
 
-// ltile[b] = kept triangle holding slot min(b * PB_TILE, P - 1) (P, nlive on the device).
-__global__ void k_live_tiles(const int64_t* __restrict__ loff, const int64_t* __restrict__ nlive_p,
-                             const int64_t* __restrict__ P_p, int64_t max_tiles, int64_t* __restrict__ ltile) {
-    const int64_t P = *P_p;
-    const int64_t nlive = *nlive_p;
-    if (P <= 0) return;
-    const int64_t tiles = (P + PB_TILE - 1) / PB_TILE;
-    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b <= tiles && b <= max_tiles;
-         b += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = min(b * (int64_t)PB_TILE, P - 1);
-        int64_t lo = 0, hi = nlive - 1;
-        while (lo < hi) {
-            int64_t mid = (lo + hi + 1) >> 1;
-            if (loff[mid] <= p) lo = mid;
-            else hi = mid - 1;
-        }
-        ltile[b] = lo;
-    }
-}
 
 // Model bytes of a staged triangle's kept roles (its first slot lies in this tile):
 // staging 61 B, and per role w sigma1 + w min(sigma2, sigma1 ceil(log2(sigma2 + 1))) + the
@@ -451,7 +438,6 @@ void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t
                        const void* deltas, cudaStream_t s, uint8_t* rflag, uint16_t* bins16) {
     const int64_t ntri = g->ntri;
     if (ntri == 0 || g->info.probes == 0) return;
-    const int T = 256;
     Scratch sc(g->alloc, s, g->dev_err);
     int32_t* L = sc.get<int32_t>(ntri + 1);
     int64_t* loff = sc.get<int64_t>(ntri + 1);
@@ -471,8 +457,8 @@ void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t
     StageSpan span(ST_PROBE, s, 30 * ntri, prof);
     FOLTY_CUDA(cudaMemsetAsync(lsctl, 0, sizeof(unsigned long long) * (size_t)(2 * stiles + 1), s));
     FOLTY_LAUNCH(k_live_select, (unsigned)stiles, SCAN_THREADS, 0, s, g->rsig, g->rmin + (int64_t)dir * 6 * ntri, ntri,
-                 delta, lsctl + 1, lsctl + 1 + stiles, (unsigned int*)lsctl, sc.err(), L, loff, lmask, totals, prof);
-    FOLTY_LAUNCH(k_live_tiles, grid_for(max_tiles + 1, T), T, 0, s, loff, totals, totals + 1, max_tiles, ltile);
+                 delta, lsctl + 1, lsctl + 1 + stiles, (unsigned int*)lsctl, sc.err(), L, loff, lmask, totals, ltile,
+                 max_tiles, prof);
     LiveArgs la{g->tri, g->seg, L, loff, lmask, ltile, totals + 1, cnt, bins, (uint32_t*)bins16, g->m_kept, k, prof,
                 rflag};
     int per_sm = 0;

@@ -2324,15 +2324,16 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
             const int tn = pa.tail_n;
             int32_t* L = sc.get<int32_t>(tn);
             int32_t* gmap = sc.get<int32_t>(n);
-            int* nl = sc.get<int>(1);
             int32_t* ld = sc.get<int32_t>(tn + 1);
             int32_t* d0 = sc.get<int32_t>(tn + 1);
             int32_t* lrow = sc.get<int32_t>(tn + 1);
             int32_t* eoff = sc.get<int32_t>(tn + 1);
-            int32_t* fillc = sc.get<int32_t>(tn);
+            // zeroed together: the local vertex count, then the fill counters
+            int32_t* zblk = sc.get<int32_t>(tn + 1);
+            int* nl = zblk;
+            int32_t* fillc = zblk + 1;
             uint32_t* ladj = sc.get<uint32_t>(2 * (int64_t)S);
-            FOLTY_CUDA(cudaMemsetAsync(nl, 0, sizeof(int), s));
-            FOLTY_CUDA(cudaMemsetAsync(fillc, 0, sizeof(int32_t) * (size_t)tn, s));
+            FOLTY_CUDA(cudaMemsetAsync(zblk, 0, sizeof(int32_t) * (size_t)(tn + 1), s));
             FOLTY_LAUNCH(k_tail_select, grid_for(n, T), T, 0, s, pa.alive[0], pa.alive[1], pa.ctl, rnd, tn, L, gmap,
                          nl, pa.ctl + C_ERR);
             FOLTY_LAUNCH(k_tail_degrees, grid_for(tn, T), T, 0, s, L, nl, pa.deg, rowptr, tn, ld, d0);
@@ -2342,19 +2343,19 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
                          lrow, ld, fillc, ladj, pa.ctl + C_ERR);
             // single-CTA phase for the last SOLO_CAP vertices (does nothing unless the
             // cluster hands off)
-            int* ns = sc.get<int>(1);
+            // zeroed together: the exported count, the degrees, the fill counters
+            int32_t* sblk = sc.get<int32_t>(1 + (SOLO_CAP + 1) + SOLO_CAP);
+            int* ns = sblk;
+            int32_t* sdeg = sblk + 1;
+            int32_t* fc = sdeg + (SOLO_CAP + 1);
             int32_t* slist = sc.get<int32_t>(SOLO_CAP);
-            int32_t* sdeg = sc.get<int32_t>(SOLO_CAP + 1);
             int32_t* srow = sc.get<int32_t>(SOLO_CAP + 1);
             int32_t* dl = sc.get<int32_t>(SOLO_CAP + 1);
             int32_t* eo = sc.get<int32_t>(SOLO_CAP + 1);
-            int32_t* fc = sc.get<int32_t>(SOLO_CAP);
             int32_t* sgid = sc.get<int32_t>(SOLO_CAP);
             int32_t* map2 = sc.get<int32_t>(tn);
             uint16_t* sadj = sc.get<uint16_t>(2 * (int64_t)S);
-            FOLTY_CUDA(cudaMemsetAsync(ns, 0, sizeof(int), s));
-            FOLTY_CUDA(cudaMemsetAsync(sdeg, 0, sizeof(int32_t) * (SOLO_CAP + 1), s));
-            FOLTY_CUDA(cudaMemsetAsync(fc, 0, sizeof(int32_t) * SOLO_CAP, s));
+            FOLTY_CUDA(cudaMemsetAsync(sblk, 0, sizeof(int32_t) * (size_t)(1 + (SOLO_CAP + 1) + SOLO_CAP), s));
             FOLTY_CUDA(cudaMemsetAsync(map2, 0xff, sizeof(int32_t) * (size_t)tn, s));
             TailArgs ta{nl, L, ld, lrow, ladj, rnd, core, pa.ctl, SOLO_CAP, ns, slist, sdeg, map2};
             if (tail_c == 16) launch_tail<16>(ta, s);

@@ -125,7 +125,6 @@ void exclusive_scan(Scratch& sc, const uint32_t* in, uint32_t* out, int64_t n) {
 // shared memory, so that the global writes of each digit's run are contiguous.
 
 constexpr int RS_THREADS = 256;
-constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 4096 keys per tile
 constexpr int RS_BITS = 8;
@@ -390,8 +389,10 @@ static bool radix_sort_impl(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uin
     const int64_t tiles = (n + tile - 1) / tile;
     uint32_t* hist = sc.get<uint32_t>(2 * RS_MAX_PASSES * RS_BINS);
     uint32_t* base = hist + RS_MAX_PASSES * RS_BINS;
-    unsigned long long* lb = sc.get<unsigned long long>(tiles * RS_BINS);
-    unsigned int* counter = sc.get<unsigned int>(1);
+    // one zeroed block per pass: the tile counter, then the look-back entries
+    unsigned long long* lbc = sc.get<unsigned long long>(tiles * RS_BINS + 1);
+    unsigned int* counter = (unsigned int*)lbc;
+    unsigned long long* lb = lbc + 1;
     FOLTY_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * RS_MAX_PASSES * RS_BINS, s));
     {
         StageSpan span(ST_SORT, s, 8 * n);  // all digit histograms: one read of the keys
@@ -410,8 +411,7 @@ static bool radix_sort_impl(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uin
     bool alt = false;
     for (int p = 0; p < passes; p++) {
         StageSpan span(ST_SORT, s, (kv ? 24 : 16) * n);  // keys (and values) read and written once
-        FOLTY_CUDA(cudaMemsetAsync(lb, 0, sizeof(unsigned long long) * (size_t)(tiles * RS_BINS), s));
-        FOLTY_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
+        FOLTY_CUDA(cudaMemsetAsync(lbc, 0, sizeof(unsigned long long) * (size_t)(tiles * RS_BINS + 1), s));
         OnesweepArgs oa{alt ? keys_alt : keys, kv ? (alt ? vals_alt : vals) : nullptr, alt ? keys : keys_alt,
                         kv ? (alt ? vals : vals_alt) : nullptr, n, lo + RS_BITS * p, base + p * RS_BINS, lb, counter,
                         sc.err(), LOOKBACK_TIMEOUT_NS};
