@@ -23,7 +23,9 @@
  *   - "stream" is a cudaStream_t (NULL = the legacy default stream). Device work is
  *     ordered on it; calls that return host data synchronise it first.
  *   - Device memory is taken from the caller's folty_allocator when one is given
- *     (e.g. PyTorch's caching allocator), otherwise with cudaMallocAsync on the stream.
+ *     (e.g. PyTorch's caching allocator), otherwise stream-ordered from a pool the
+ *     library creates per device (cudaMemPoolCreate), which keeps up to a quarter of
+ *     the device's memory cached between calls for reuse.
  *   - Limits: 0 <= n < 2^30, 0 <= m < 2^31, 0 <= t < 2^62, 0 <= delta < 2^62.
  */
 #ifndef FOLTY_H

@@ -214,11 +214,11 @@ def _dtype_ok(a, np_dtype, torch_name):
 
 # ------------------------------------------------------------------ C-named functions
 
-def folty_load_temporal_graph(n: int, src, dst, t, allocator: Optional[str] = "torch",
+def folty_load_temporal_graph(n: int, src, dst, t, allocator: Optional[str] = None,
                               stream: Optional[int] = None) -> int:
     """Returns a graph handle. src, dst (int32) and t (int64) may be host numpy arrays or
-    host/device torch tensors. allocator: "torch" (caching allocator) or None
-    (cudaMallocAsync inside the library)."""
+    host/device torch tensors. allocator: None (the library's own stream-ordered pool) or
+    "torch" (PyTorch's caching allocator, through a callback per allocation)."""
     m = int(src.shape[0])
     if int(dst.shape[0]) != m or int(t.shape[0]) != m:
         raise ValueError("src, dst and t must have the same length")
@@ -405,7 +405,7 @@ def folty_server_destroy(sv: int) -> None:
 class TemporalGraph:
     """Owns a folty graph handle: load, preprocess, query, free."""
 
-    def __init__(self, n: int, src, dst, t, allocator: Optional[str] = "torch",
+    def __init__(self, n: int, src, dst, t, allocator: Optional[str] = None,
                  stream: Optional[int] = None, preprocess: bool = True):
         self.handle = folty_load_temporal_graph(n, src, dst, t, allocator=allocator, stream=stream)
         if preprocess:

@@ -93,11 +93,40 @@ int num_sms() {
     return cache[dev];
 }
 
+// The library's own stream-ordered pool of the current device: created on first use and
+// kept for the process. Unlike the device's default pool (release threshold 0, which
+// hands freed memory back to the driver at every synchronisation, so that the next
+// preprocessing maps it again), it keeps up to a quarter of the device's memory cached
+// across calls.
+static cudaMemPool_t library_pool() {
+    static std::mutex mu;
+    static std::vector<cudaMemPool_t> pools;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) total_b = 0;
+        uint64_t keep = total_b / 4;
+        if (cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) cudaGetLastError();
+        pools[dev] = p;
+    }
+    return pools[dev];
+}
+
 void* Allocator::get(size_t bytes, cudaStream_t s) const {
     if (bytes == 0) bytes = 16;
     if (user) return a.alloc(bytes, (void*)s, a.ctx);
+    cudaMemPool_t pool = library_pool();
     void* p = nullptr;
-    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    if (!pool || cudaMallocFromPoolAsync(&p, bytes, pool, s) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }

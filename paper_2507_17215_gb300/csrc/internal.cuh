@@ -81,23 +81,42 @@ class Scratch {
     Scratch(const Scratch&) = delete;
     Scratch& operator=(const Scratch&) = delete;
 
+    // Buffers of at least CHUNK / 4 bytes are allocated on their own; smaller ones are
+    // carved, 256-byte aligned, from shared chunks of CHUNK bytes, so that the many
+    // counters, block aggregates and per-vertex arrays of one call cost a few allocator
+    // calls rather than one each (a caller's allocator may be a costly callback).
+    static constexpr size_t CHUNK = size_t(8) << 20;
     template <typename T>
     T* get(int64_t count) {
         size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
-        void* p = a_.get(bytes, s_);
-        if (!p) fail(FOLTY_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
-        ptrs_.push_back(p);
-        return static_cast<T*>(p);
+        bytes = (bytes + 255) & ~size_t(255);
+        if (bytes >= CHUNK / 4) return static_cast<T*>(take(bytes));
+        if (bytes > left_) {
+            cur_ = static_cast<char*>(take(CHUNK));
+            left_ = CHUNK;
+        }
+        T* p = reinterpret_cast<T*>(cur_);
+        cur_ += bytes;
+        left_ -= bytes;
+        return p;
     }
     cudaStream_t stream() const { return s_; }
     const Allocator& allocator() const { return a_; }
     int* err() const { return err_; }
 
   private:
+    void* take(size_t bytes) {
+        void* p = a_.get(bytes, s_);
+        if (!p) fail(FOLTY_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+        ptrs_.push_back(p);
+        return p;
+    }
     const Allocator& a_;
     cudaStream_t s_;
     int* err_;
     std::vector<void*> ptrs_;
+    char* cur_ = nullptr;
+    size_t left_ = 0;
 };
 
 // ------------------------------------------------------------------ the graph
