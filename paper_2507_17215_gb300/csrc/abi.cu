@@ -154,12 +154,14 @@ void graph_release(folty_graph* g, void* p, cudaStream_t s) {
 void read_back(folty_graph* g, const void* const* dev_ptrs, const int* sizes, int count, int64_t* out,
                cudaStream_t s) {
     if (count > READBACK_MAX) fail(FOLTY_EINVAL, "read_back: too many values");
+    g->stage_busy = 1;
     for (int i = 0; i < count; i++)
         FOLTY_CUDA(cudaMemcpyAsync(g->host_stage + i, dev_ptrs[i], (size_t)sizes[i], cudaMemcpyDeviceToHost, s));
     int32_t* herr = (int32_t*)(g->host_stage + ERR_SLOT);
     *herr = 0;
     if (g->dev_err) FOLTY_CUDA(cudaMemcpyAsync(herr, g->dev_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     FOLTY_CUDA(cudaStreamSynchronize(s));
+    g->stage_busy = 0;
     if (*herr) {
         FOLTY_CUDA(cudaMemsetAsync(g->dev_err, 0, sizeof(int32_t), s));
         fail(FOLTY_ETIMEOUT, "a bounded wait in a device look-back ran out; the results of this call are void");
@@ -253,13 +255,46 @@ void release_result(folty_result* r) {
     r->tag = FREED_TAG;
 }
 
+// Pinned staging blocks of HOST_STAGE entries, recycled across graphs: a cudaMallocHost
+// and its cudaFreeHost (which synchronises the device) cost more than a medium
+// graph's whole query. A block goes back to the list only when no copy into or out of
+// it can still be pending; otherwise it is freed.
+static std::mutex g_stage_mu;
+static std::vector<int64_t*> g_stage_free;
+constexpr size_t STAGE_KEEP = 64;
+
+static int64_t* stage_take() {
+    {
+        std::lock_guard<std::mutex> lock(g_stage_mu);
+        if (!g_stage_free.empty()) {
+            int64_t* p = g_stage_free.back();
+            g_stage_free.pop_back();
+            return p;
+        }
+    }
+    int64_t* p = nullptr;
+    FOLTY_CUDA(cudaMallocHost((void**)&p, HOST_STAGE * sizeof(int64_t)));
+    return p;
+}
+
+static void stage_give(int64_t* p, bool busy) {
+    if (!busy) {
+        std::lock_guard<std::mutex> lock(g_stage_mu);
+        if (g_stage_free.size() < STAGE_KEEP) {
+            g_stage_free.push_back(p);
+            return;
+        }
+    }
+    cudaFreeHost(p);
+}
+
 static void free_graph(folty_graph* g) {
     if (g->owned) {
         for (void* p : *g->owned) g->alloc.put(p, 0);
         delete g->owned;
         g->owned = nullptr;
     }
-    if (g->host_stage) cudaFreeHost(g->host_stage);
+    if (g->host_stage) stage_give(g->host_stage, g->stage_busy != 0);
     g->tag = FREED_TAG;
     delete g;
 }
@@ -269,38 +304,117 @@ static void free_graph(folty_graph* g) {
 // Checks ids and timestamps, finds the t range, counts self-loops and detects
 // time-sorted input. stat: [0] first bad index + 1 (min), [1] tmin, [2] tmax,
 // [3] unsorted flag, [4] self-loops.
-__global__ void k_validate(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                           const int64_t* __restrict__ t, int64_t m, int32_t n,
-                           unsigned long long* __restrict__ stat) {
+struct EdgeStat {
     unsigned long long bad = ~0ull, tmin = ~0ull, tmax = 0, unsorted = 0, loops = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t x = src[i], y = dst[i];
-        int64_t ti = t[i];
+
+    __device__ __forceinline__ void edge(int64_t i, int32_t x, int32_t y, int64_t ti, int64_t tprev, int32_t n) {
         bool ok = x >= 0 && x < n && y >= 0 && y < n && ti >= 0 && ti < (1ll << 62);
         if (!ok && (unsigned long long)i < bad) bad = (unsigned long long)i;
         if (ok) {
             tmin = min(tmin, (unsigned long long)ti);
             tmax = max(tmax, (unsigned long long)ti);
         }
-        if (i > 0 && t[i - 1] > ti) unsorted = 1;
+        if (tprev > ti) unsorted = 1;
         loops += (x == y);
     }
+
+    __device__ __forceinline__ void flush(unsigned long long* __restrict__ stat) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        bad = min(bad, __shfl_xor_sync(0xffffffffu, bad, o));
-        tmin = min(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
-        tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
-        unsorted |= __shfl_xor_sync(0xffffffffu, unsorted, o);
-        loops += __shfl_xor_sync(0xffffffffu, loops, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            bad = min(bad, __shfl_xor_sync(0xffffffffu, bad, o));
+            tmin = min(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+            tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+            unsorted |= __shfl_xor_sync(0xffffffffu, unsorted, o);
+            loops += __shfl_xor_sync(0xffffffffu, loops, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            if (bad != ~0ull) atomicMin(&stat[0], bad);
+            atomicMin(&stat[1], tmin);
+            atomicMax(&stat[2], tmax);
+            if (unsorted) atomicOr(&stat[3], 1ull);
+            if (loops) atomicAdd(&stat[4], loops);
+        }
     }
-    if ((threadIdx.x & 31) == 0) {
-        if (bad != ~0ull) atomicMin(&stat[0], bad);
-        atomicMin(&stat[1], tmin);
-        atomicMax(&stat[2], tmax);
-        if (unsorted) atomicOr(&stat[3], 1ull);
-        if (loops) atomicAdd(&stat[4], loops);
+};
+
+__global__ void k_validate(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                           const int64_t* __restrict__ t, int64_t m, int32_t n,
+                           unsigned long long* __restrict__ stat) {
+    EdgeStat st;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        st.edge(i, src[i], dst[i], t[i], i > 0 ? t[i - 1] : 0, n);
+    st.flush(stat);
+}
+
+// The same checks fused with the copy of the input into the graph's own arrays: one
+// read and one write of every input byte. The input is device memory or pinned host
+// memory (read over the host link, as fast as a copy engine's pull). Four edges per
+// thread and iteration (16-byte accesses; all six pointers 16-byte aligned), the
+// previous edge's timestamp from the neighbouring lane, the m mod 4 last edges one by
+// one.
+__global__ void k_load_copy(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                            const int64_t* __restrict__ t, int64_t m, int32_t n, int32_t* __restrict__ osrc,
+                            int32_t* __restrict__ odst, int64_t* __restrict__ ot,
+                            unsigned long long* __restrict__ stat) {
+    EdgeStat st;
+    const int lane = threadIdx.x & 31;
+    const int64_t m4 = m >> 2;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;  // a multiple of 32
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int64_t j0 = tid - lane; j0 < m4; j0 += stride) {  // warp-uniform trip count
+        const int64_t j = j0 + lane;
+        const bool act = j < m4;
+        int4 x{}, y{};
+        longlong2 t01{}, t23{};
+        if (act) {
+            x = __ldcs(reinterpret_cast<const int4*>(src) + j);
+            y = __ldcs(reinterpret_cast<const int4*>(dst) + j);
+            t01 = __ldcs(reinterpret_cast<const longlong2*>(t) + 2 * j);
+            t23 = __ldcs(reinterpret_cast<const longlong2*>(t) + 2 * j + 1);
+        }
+        int64_t tp = __shfl_up_sync(0xffffffffu, (long long)t23.y, 1);
+        if (lane == 0) tp = j > 0 ? t[4 * j - 1] : 0;
+        if (act) {
+            reinterpret_cast<int4*>(osrc)[j] = x;
+            reinterpret_cast<int4*>(odst)[j] = y;
+            reinterpret_cast<longlong2*>(ot)[2 * j] = t01;
+            reinterpret_cast<longlong2*>(ot)[2 * j + 1] = t23;
+            const int64_t i = 4 * j;
+            st.edge(i, x.x, y.x, t01.x, tp, n);
+            st.edge(i + 1, x.y, y.y, t01.y, t01.x, n);
+            st.edge(i + 2, x.z, y.z, t23.x, t01.y, n);
+            st.edge(i + 3, x.w, y.w, t23.y, t23.x, n);
+        }
     }
+    for (int64_t i = 4 * m4 + tid; i < m; i += stride) {
+        const int32_t x = src[i], y = dst[i];
+        const int64_t ti = t[i];
+        osrc[i] = x;
+        odst[i] = y;
+        ot[i] = ti;
+        st.edge(i, x, y, ti, i > 0 ? t[i - 1] : 0, n);
+    }
+    st.flush(stat);
+}
+
+// The address under which kernels of the current device read p: p itself for memory
+// of this device, the mapped address for pinned host memory; NULL otherwise (pageable
+// host memory, another device's memory).
+static const void* kernel_address(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice && a.device == dev) return p;
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+    return nullptr;
 }
 
 static void load_graph(folty_graph* g, const int32_t* src, const int32_t* dst, const int64_t* t,
@@ -311,7 +425,12 @@ static void load_graph(folty_graph* g, const int32_t* src, const int32_t* dst, c
     g->in_t = graph_alloc<int64_t>(g, m, s);
     g->dev_err = graph_alloc<int>(g, 1, s);
     FOLTY_CUDA(cudaMemsetAsync(g->dev_err, 0, sizeof(int), s));
-    if (m > 0) {
+    auto a16 = [](const void* p) { return p && ((uintptr_t)p & 15) == 0; };
+    const void* ksrc = m > 0 ? kernel_address(src) : nullptr;
+    const void* kdst = m > 0 ? kernel_address(dst) : nullptr;
+    const void* kt = m > 0 ? kernel_address(t) : nullptr;
+    const bool fused = a16(ksrc) && a16(kdst) && a16(kt) && a16(g->in_src) && a16(g->in_dst) && a16(g->in_t);
+    if (m > 0 && !fused) {
         FOLTY_CUDA(cudaMemcpyAsync(g->in_src, src, sizeof(int32_t) * (size_t)m, cudaMemcpyDefault, s));
         FOLTY_CUDA(cudaMemcpyAsync(g->in_dst, dst, sizeof(int32_t) * (size_t)m, cudaMemcpyDefault, s));
         FOLTY_CUDA(cudaMemcpyAsync(g->in_t, t, sizeof(int64_t) * (size_t)m, cudaMemcpyDefault, s));
@@ -320,8 +439,13 @@ static void load_graph(folty_graph* g, const int32_t* src, const int32_t* dst, c
     unsigned long long* stat = sc.get<unsigned long long>(5);
     unsigned long long init[5] = {~0ull, ~0ull, 0ull, 0ull, 0ull};
     std::memcpy(g->host_stage + READBACK_MAX, init, sizeof(init));
+    g->stage_busy = 1;
     FOLTY_CUDA(cudaMemcpyAsync(stat, g->host_stage + READBACK_MAX, sizeof(init), cudaMemcpyHostToDevice, s));
-    if (m > 0) FOLTY_LAUNCH(k_validate, grid_for(m, 256), 256, 0, s, g->in_src, g->in_dst, g->in_t, m, g->n, stat);
+    if (fused)
+        FOLTY_LAUNCH(k_load_copy, grid_for(m / 4 + 1, 256, 4), 256, 0, s, (const int32_t*)ksrc,
+                     (const int32_t*)kdst, (const int64_t*)kt, m, g->n, g->in_src, g->in_dst, g->in_t, stat);
+    else if (m > 0)
+        FOLTY_LAUNCH(k_validate, grid_for(m, 256), 256, 0, s, g->in_src, g->in_dst, g->in_t, m, g->n, stat);
     const void* ptrs[5] = {stat, stat + 1, stat + 2, stat + 3, stat + 4};
     int sizes[5] = {8, 8, 8, 8, 8};
     int64_t v[5];
@@ -387,7 +511,7 @@ folty_status folty_load_temporal_graph(int32_t n, int64_t m, const int32_t* src,
             g->alloc.user = true;
         }
         FOLTY_CUDA(cudaGetDevice(&g->device));
-        FOLTY_CUDA(cudaMallocHost((void**)&g->host_stage, HOST_STAGE * sizeof(int64_t)));
+        g->host_stage = stage_take();
         g->n = n;
         g->m = m;
         load_graph(g, src, dst, t, s);

@@ -174,6 +174,7 @@ struct folty_graph {
     folty_graph_info info;
     // ---- pinned host staging for small device->host reads
     int64_t* host_stage;  // HOST_STAGE entries
+    int stage_busy;       // an asynchronous copy into or out of host_stage may be pending
     int* dev_err;         // device error word: a bounded wait in a kernel ran out
     std::vector<void*>* owned;  // device buffers owned by the graph
 };

@@ -2304,6 +2304,7 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         init[C_MIN + 1] = INT_MAX;
         int* init_dev = (int*)(g->host_stage + READBACK_MAX + 16);  // pinned staging
         std::memcpy(init_dev, init, sizeof(init));
+        g->stage_busy = 1;
         FOLTY_CUDA(cudaMemcpyAsync(pa.ctl, init_dev, sizeof(init), cudaMemcpyHostToDevice, s));
         FOLTY_LAUNCH(k_iota, grid_for(n, T), T, 0, s, pa.alive[0], (int64_t)n);
         int per_sm = 0;

@@ -120,6 +120,58 @@ def test_unsorted_input_equals_sorted(F):
             _assert_same(r, og.query(q))
 
 
+def _device_load_cases():
+    """Input graphs for the fused copy-and-check load of device-resident arrays: a ragged
+    length (m mod 4 = 3), shuffled times, a time inversion only across a 4-edge group
+    boundary, self-loops, and a bad id inside a group and in the ragged tail."""
+    rng = np.random.default_rng(21)
+    g = W.config_graph(2, scale=0.01)
+    m = g.m - (g.m % 4) - 1
+    base = W.TemporalGraph(g.n, g.src[:m].copy(), g.dst[:m].copy(), g.t[:m].copy())
+    perm = rng.permutation(m)
+    shuffled = W.TemporalGraph(g.n, base.src[perm].copy(), base.dst[perm].copy(), base.t[perm].copy())
+    assert np.all(base.t[1:] >= base.t[:-1])
+    t = base.t.copy()
+    j = 4 * (m // 8)
+    t[j - 1] = t[j] + 1
+    boundary = W.TemporalGraph(g.n, base.src.copy(), base.dst.copy(), t)
+    loops = W.TemporalGraph(g.n, base.src.copy(), base.src.copy(), base.t.copy())
+    loops.dst[1::3] = base.dst[1::3]
+    return base, shuffled, boundary, loops
+
+
+def test_device_resident_input_equals_host_input(F):
+    import torch
+    base, shuffled, boundary, loops = _device_load_cases()
+    assert base.m % 4 == 3
+    # the boundary case is out of time order at exactly one place, across groups of 4
+    inv = np.nonzero(boundary.t[1:] < boundary.t[:-1])[0]
+    assert len(inv) == 1 and (inv[0] + 1) % 4 == 0
+    qs = [W.Query(3600, 1, 2, want_edge_counts=True),
+          W.Query(86400, 1, 5, W.Q_FORALL_T, W.DIR_EITHER, W.U_COMMON, True)]
+    for g in (base, shuffled, boundary, loops):
+        want, want_info = _lib_results(F, g, qs)
+        dev = [torch.from_numpy(a).cuda() for a in (g.src, g.dst, g.t)]
+        pinned = [torch.from_numpy(a).pin_memory() for a in (g.src, g.dst, g.t)]
+        # offset views: 4-byte and 8-byte aligned but not 16-byte aligned (the copy path)
+        pad = [torch.cat([a[:1], a]) for a in dev]
+        for arrs in (dev, pinned, [a[1:] for a in pad]):
+            with F.TemporalGraph(g.n, *arrs) as G:
+                got, info = [G.query(q) for q in qs], G.info()
+            assert info == want_info
+            assert info["time_sorted"] == (0 if g is shuffled or g is boundary else 1)
+            for q, a, b in zip(qs, want, got):
+                _assert_same(b, a, what=str(q))
+    for pos in (4 * (base.m // 8) + 2, base.m - 1):  # inside a group of 4; the ragged tail
+        src = base.src.copy()
+        src[pos] = base.n
+        for arrs in ([src, base.dst, base.t], [torch.from_numpy(a).cuda() for a in (src, base.dst, base.t)],
+                     [torch.from_numpy(a).pin_memory() for a in (src, base.dst, base.t)]):
+            with pytest.raises(F.FoltyError) as ei:
+                F.folty_load_temporal_graph(base.n, *arrs)
+            assert ei.value.status == F.FOLTY_EINVAL and f"edge {pos}:" in str(ei.value)
+
+
 def _edge_case_graphs():
     out = {}
     e = np.zeros(0, np.int32)
