@@ -151,29 +151,45 @@ void graph_release(folty_graph* g, void* p, cudaStream_t s) {
     }
 }
 
+// The values of one read-back, gathered by one thread block into the pinned stage (one
+// launch instead of a copy per value).
+struct ReadbackArgs {
+    const void* p[READBACK_MAX];
+    uint8_t wide[READBACK_MAX];  // 1: an int64 value, 0: an int32 one (sign-extended)
+    int count;
+    const int* dev_err;  // may be null
+    int64_t* out;        // device address of the stage's slots [0, count)
+    int32_t* herr;       // device address of the error slot
+};
+
+__global__ void k_read_back(const __grid_constant__ ReadbackArgs a) {
+    for (int i = threadIdx.x; i < a.count; i += blockDim.x)
+        a.out[i] = a.wide[i] ? *static_cast<const int64_t*>(a.p[i]) : (int64_t)*static_cast<const int32_t*>(a.p[i]);
+    if (threadIdx.x == 0) *a.herr = a.dev_err ? *a.dev_err : 0;
+}
+
 void read_back(folty_graph* g, const void* const* dev_ptrs, const int* sizes, int count, int64_t* out,
                cudaStream_t s) {
     if (count > READBACK_MAX) fail(FOLTY_EINVAL, "read_back: too many values");
+    ReadbackArgs a;
+    for (int i = 0; i < count; i++) {
+        if (sizes[i] != 4 && sizes[i] != 8) fail(FOLTY_EINVAL, "read_back: values are 4 or 8 bytes");
+        a.p[i] = dev_ptrs[i];
+        a.wide[i] = sizes[i] == 8;
+    }
+    a.count = count;
+    a.dev_err = g->dev_err;
+    a.out = g->stage_dev;
+    a.herr = (int32_t*)(g->stage_dev + ERR_SLOT);
     g->stage_busy = 1;
-    for (int i = 0; i < count; i++)
-        FOLTY_CUDA(cudaMemcpyAsync(g->host_stage + i, dev_ptrs[i], (size_t)sizes[i], cudaMemcpyDeviceToHost, s));
-    int32_t* herr = (int32_t*)(g->host_stage + ERR_SLOT);
-    *herr = 0;
-    if (g->dev_err) FOLTY_CUDA(cudaMemcpyAsync(herr, g->dev_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    FOLTY_LAUNCH(k_read_back, 1, 128, 0, s, a);
     FOLTY_CUDA(cudaStreamSynchronize(s));
     g->stage_busy = 0;
-    if (*herr) {
+    if (*(volatile int32_t*)(g->host_stage + ERR_SLOT)) {
         FOLTY_CUDA(cudaMemsetAsync(g->dev_err, 0, sizeof(int32_t), s));
         fail(FOLTY_ETIMEOUT, "a bounded wait in a device look-back ran out; the results of this call are void");
     }
-    for (int i = 0; i < count; i++) {
-        if (sizes[i] == 8) out[i] = g->host_stage[i];
-        else {
-            int32_t v;
-            std::memcpy(&v, &g->host_stage[i], 4);
-            out[i] = v;
-        }
-    }
+    for (int i = 0; i < count; i++) out[i] = ((volatile int64_t*)g->host_stage)[i];
 }
 
 int64_t read_i64(folty_graph* g, const int64_t* p, cudaStream_t s) {
@@ -255,7 +271,8 @@ void release_result(folty_result* r) {
     r->tag = FREED_TAG;
 }
 
-// Pinned staging blocks of HOST_STAGE entries, recycled across graphs: a cudaMallocHost
+// Pinned staging blocks (HOST_STAGE int64 read-back slots, then room for PAIR_STAGE
+// solution pairs), recycled across graphs: a cudaMallocHost
 // and its cudaFreeHost (which synchronises the device) cost more than a medium
 // graph's whole query. A block goes back to the list only when no copy into or out of
 // it can still be pending; otherwise it is freed.
@@ -273,7 +290,7 @@ static int64_t* stage_take() {
         }
     }
     int64_t* p = nullptr;
-    FOLTY_CUDA(cudaMallocHost((void**)&p, HOST_STAGE * sizeof(int64_t)));
+    FOLTY_CUDA(cudaMallocHost((void**)&p, HOST_STAGE * sizeof(int64_t) + 4 * PAIR_STAGE * sizeof(int32_t)));
     return p;
 }
 
@@ -512,6 +529,10 @@ folty_status folty_load_temporal_graph(int32_t n, int64_t m, const int32_t* src,
         }
         FOLTY_CUDA(cudaGetDevice(&g->device));
         g->host_stage = stage_take();
+        void* dp = nullptr;
+        FOLTY_CUDA(cudaHostGetDevicePointer(&dp, g->host_stage, 0));
+        g->stage_dev = (int64_t*)dp;
+        g->pair_stage = (int32_t*)(g->stage_dev + HOST_STAGE);
         g->n = n;
         g->m = m;
         load_graph(g, src, dst, t, s);

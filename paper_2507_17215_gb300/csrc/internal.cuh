@@ -123,6 +123,7 @@ class Scratch {
 
 constexpr int PROF_SLOTS = 64;       // probe-stage byte counters per graph
 constexpr int HOST_STAGE = 512;      // pinned int64 slots per graph
+constexpr int64_t PAIR_STAGE = 1 << 16;  // solution pairs staged in pinned memory per read-back
 constexpr int READBACK_MAX = 384;    // slots [0, READBACK_MAX) serve read_back
 constexpr int ERR_SLOT = READBACK_MAX + 8;  // the device error word's copy (load uses +0..+4, peeling +16..+27)
 constexpr uint64_t GRAPH_TAG = 0x464f4c5459475248ull;   // "FOLTYGRH"
@@ -173,7 +174,9 @@ struct folty_graph {
     // ---- statistics
     folty_graph_info info;
     // ---- pinned host staging for small device->host reads
-    int64_t* host_stage;  // HOST_STAGE entries
+    int64_t* host_stage;  // HOST_STAGE entries, then 4 * PAIR_STAGE int32 (pair_stage)
+    int64_t* stage_dev;   // device address of host_stage
+    int32_t* pair_stage;  // kernel-written pair output (device address of the same memory)
     int stage_busy;       // an asynchronous copy into or out of host_stage may be pending
     int* dev_err;         // device error word: a bounded wait in a kernel ran out
     std::vector<void*>* owned;  // device buffers owned by the graph
@@ -270,7 +273,7 @@ bool profiling_on();
 // Window-probe pass of one query into counters cnt[m_kept] (sorted order, zeroed).
 void launch_probe(folty_graph* g, int64_t delta, int dir, int32_t* cnt, cudaStream_t s);
 // Window probes of the roles that can hit (live.cu): mode 0 counts hits at delta into
-// cnt; mode 1 bins gaps <= delta into bins[k][m_kept] against the k sorted bounds
+// cnt or, with bins16 (cnt null), into 16-bit counters two to a word; mode 1 bins gaps <= delta into bins[k][m_kept] against the k sorted bounds
 // `deltas` (in the timestamp store's type), as int32 or, with bins16 (bins null), as
 // 16-bit counts (element j * m_kept + e of a uint16 array; counts must stay below 2^16).
 // rflag (mode 0, may be null): byte 6 * triangle + role set to 1 when the role has a hit.
@@ -279,17 +282,15 @@ void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t
 void build_role_summary(folty_graph* g, cudaStream_t s);
 // The same pass with the counters in a file-scope device array (noalloc.cu).
 void edge_counts_noalloc(folty_graph* g, int64_t delta, int dir, int32_t* edge_count, cudaStream_t s);
-// Threshold, pair output and result copy-out for per-edge counts cnt[m_kept] (sorted
-// order); synchronises the stream.
-void finish_query(folty_graph* g, const folty_query_params& q, const int32_t* cnt, folty_result* out,
-                  cudaStream_t s);
 // Per-edge counts of one query: int32 (c32) or 16-bit (c16), the other null.
 struct CountView {
     const int32_t* c32;
     const uint16_t* c16;
 };
-// The same for nq queries at once (counts cnts[i]), with two stream synchronisations
-// for the whole group.
+// Threshold, pair output and result copy-out of nq queries at once (per-edge counts
+// cnts[i], sorted order): one stream synchronisation for the whole group, a second
+// one only when lists that did not fit the pinned pair stage (or edge counts,
+// certificates, vertex lists) are copied out after it.
 void finish_queries(folty_graph* g, const folty_query_params* const* qs, const CountView* cnts, int nq,
                     folty_result* const* outs, cudaStream_t s);
 

@@ -388,7 +388,8 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS*
             const TS gap = (TS)(t3 - t);
             if (gap > delta) continue;
             if (MODE == 0) {
-                atomicAdd(&a.cnt[pos], 1);
+                if (a.bins16) atomicAdd(&a.bins16[pos >> 1], 1u << (16 * (pos & 1)));
+                else atomicAdd(&a.cnt[pos], 1);
                 if (a.rflag) a.rflag[6 * (int64_t)a.L[t0 + j] + r] = 1;
             } else {
                 const int jb = lower_bound_ts<TS>(sD, 0, a.k, gap);

@@ -12,6 +12,7 @@
 //       compaction of the solution pairs and a sort by (u, v).
 #include <algorithm>
 #include <climits>
+#include <cstring>
 
 #include "internal.cuh"
 #include "scan.cuh"
@@ -283,6 +284,24 @@ __global__ void k_pair_merge(const uint64_t* __restrict__ key, const int32_t* __
     }
 }
 
+// The same merge written straight into pinned host memory, for a pair count known only
+// on the device (nA = pos[S], np = pos[2S]): skipped when np exceeds cap.
+__global__ void k_pair_merge_stage(const uint64_t* __restrict__ key, const int32_t* __restrict__ cnt_c,
+                                   const int32_t* __restrict__ nc_c, const int32_t* __restrict__ pos, int64_t S,
+                                   int64_t cap, int32_t* __restrict__ out) {
+    const int64_t nA = pos[S], np = pos[2 * S];
+    if (np > cap) return;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = key[p];
+        const int64_t f = (p < nA) ? p + lower_bound_u64(key + nA, np - nA, k) : (p - nA) + lower_bound_u64(key, nA, k);
+        out[f] = (int32_t)(k >> 32);
+        out[np + f] = (int32_t)(k & 0xffffffffull);
+        out[2 * np + f] = cnt_c[p];
+        out[3 * np + f] = nc_c[p];
+    }
+}
+
 template <typename C>
 __global__ void k_edge_counts_input_order(const C* __restrict__ cnt, const int32_t* __restrict__ perm,
                                           int64_t mk, int32_t* __restrict__ out) {
@@ -454,9 +473,15 @@ void finish_queries(folty_graph* g, const folty_query_params* const* qs, const C
         const int ng = std::min(G, nq - g0);
         Scratch sc(g->alloc, s, g->dev_err);
         std::vector<PairStage> st;
+        // each query's pairs go straight to its share of the pinned pair stage when they
+        // fit, and come back with the read-back below
+        const int64_t cap = PAIR_STAGE / ng;
+        g->stage_busy = 1;
         for (int i = 0; i < ng; i++) {
             st.push_back(pair_stage(sc, g, *qs[g0 + i]));
             pairs_device(g, *qs[g0 + i], cnts[g0 + i], st.back(), sc, s);
+            FOLTY_LAUNCH(k_pair_merge_stage, grid_for(cap, T, 1), T, 0, s, st.back().key, st.back().cnt_c,
+                         st.back().nc_c, st.back().pos, S, cap, g->pair_stage + 4 * cap * i);
         }
         // one read-back for the group: pairs x < y, all pairs, certificates
         std::vector<const void*> ptrs;
@@ -470,6 +495,7 @@ void finish_queries(folty_graph* g, const folty_query_params* const* qs, const C
         }
         std::vector<int64_t> rb(4 * (size_t)ng);
         read_back(g, ptrs.data(), sizes.data(), 4 * ng, rb.data(), s);
+        bool copies = false;  // device-to-host copies left to wait for
         for (int i = 0; i < ng; i++) {
             const folty_query_params& q = *qs[g0 + i];
             folty_result* out = outs[g0 + i];
@@ -482,17 +508,23 @@ void finish_queries(folty_graph* g, const folty_query_params* const* qs, const C
                 FOLTY_LAUNCH(k_vertex_compact, grid_for(g->n, T), T, 0, s, st[i].vflag, st[i].vpos, st[i].vcnt,
                              (int64_t)g->n, nv, vout);
                 FOLTY_CUDA(cudaMemcpyAsync(out->vertex, vout, sizeof(int32_t) * 2 * (size_t)nv, cudaMemcpyDeviceToHost, s));
+                copies = true;
             }
             if (q.want_certificates && nc > 0) {
                 int64_t* cout = sc.get<int64_t>(nc);
                 FOLTY_LAUNCH(k_compact_indices, grid_for(g->m, T), T, 0, s, st[i].cert_flag, st[i].cert_pos, g->m, cout);
                 FOLTY_CUDA(cudaMemcpyAsync(out->certificate, cout, sizeof(int64_t) * (size_t)nc, cudaMemcpyDeviceToHost, s));
+                copies = true;
             }
-            if (np > 0) {
+            if (np > 0 && np <= cap) {
+                const int32_t* staged = (const int32_t*)(g->host_stage + HOST_STAGE) + 4 * cap * i;
+                std::memcpy(out->u, staged, sizeof(int32_t) * 4 * (size_t)np);
+            } else if (np > 0) {
                 int32_t* packed = sc.get<int32_t>(4 * np);
                 FOLTY_LAUNCH(k_pair_merge, grid_for(np, T), T, 0, s, st[i].key, st[i].cnt_c, st[i].nc_c, nA, np,
                              packed);
                 FOLTY_CUDA(cudaMemcpyAsync(out->u, packed, sizeof(int32_t) * 4 * (size_t)np, cudaMemcpyDeviceToHost, s));
+                copies = true;
             }
             if (q.want_edge_counts && g->m > 0) {
                 int32_t* ec = sc.get<int32_t>(g->m);
@@ -504,17 +536,11 @@ void finish_queries(folty_graph* g, const folty_query_params* const* qs, const C
                     FOLTY_LAUNCH(k_edge_counts_input_order<int32_t>, grid_for(mk, T), T, 0, s, cnts[g0 + i].c32, g->perm,
                                  mk, ec);
                 FOLTY_CUDA(cudaMemcpyAsync(out->edge_count, ec, sizeof(int32_t) * (size_t)g->m, cudaMemcpyDeviceToHost, s));
+                copies = true;
             }
         }
-        FOLTY_CUDA(cudaStreamSynchronize(s));
+        if (copies) FOLTY_CUDA(cudaStreamSynchronize(s));
     }
-}
-
-void finish_query(folty_graph* g, const folty_query_params& q, const int32_t* cnt, folty_result* out,
-                  cudaStream_t s) {
-    const folty_query_params* qp = &q;
-    const CountView cv{cnt, nullptr};
-    finish_queries(g, &qp, &cv, 1, &out, s);
 }
 
 // ------------------------------------------------------------------ all-existential triples
@@ -616,15 +642,22 @@ static void triples_result(folty_graph* g, const uint8_t* rflag, folty_result* o
 void run_query(folty_graph* g, const folty_query_params& q, folty_result* out, cudaStream_t s) {
     Scratch sc(g->alloc, s, g->dev_err);
     const int64_t mk = g->m_kept;
-    int32_t* cnt = sc.get<int32_t>(mk);
-    if (mk > 0) FOLTY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)mk, s));
+    // c_e counts distinct witnesses, so it is at most the largest degree of G_S: below
+    // 2^16 - 1 the counters are 16 bits, two to a word (no carry reaches a neighbour)
+    const bool c16 = g->info.max_degree < 65535;
+    int32_t* cnt = c16 ? nullptr : sc.get<int32_t>(mk);
+    uint16_t* cnt16 = c16 ? sc.get<uint16_t>(mk + 2) : nullptr;  // + 2: the last word is whole
+    if (mk > 0 && c16) FOLTY_CUDA(cudaMemsetAsync(cnt16, 0, sizeof(uint16_t) * (size_t)(mk + 2), s));
+    if (mk > 0 && !c16) FOLTY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)mk, s));
     uint8_t* rflag = nullptr;
     if (q.want_triples) {
         rflag = sc.get<uint8_t>(6 * g->ntri + 1);
         FOLTY_CUDA(cudaMemsetAsync(rflag, 0, (size_t)(6 * g->ntri + 1), s));
     }
-    launch_probe_live(g, q.delta, q.dir, 0, cnt, nullptr, 0, nullptr, s, rflag);
-    finish_query(g, q, cnt, out, s);  // synchronises the stream
+    launch_probe_live(g, q.delta, q.dir, 0, cnt, nullptr, 0, nullptr, s, rflag, cnt16);
+    const folty_query_params* qp = &q;
+    const CountView cv{cnt, cnt16};
+    finish_queries(g, &qp, &cv, 1, &out, s);  // synchronises the stream
     if (q.want_triples) {
         try {
             triples_result(g, rflag, out, s);

@@ -279,8 +279,8 @@ def test_batch_equals_sequential(F):
 
 
 def test_batch_with_a_hub_of_degree_past_16_bits(F):
-    """A vertex with 66,000 neighbours: batched counts no longer fit 16-bit bins, so the
-    batch keeps 32-bit ones; results equal the single queries' and the oracle's."""
+    """A vertex with 66,000 neighbours: counts no longer fit 16-bit counters, so single
+    queries and the batch keep 32-bit ones; results equal each other and the oracle's."""
     rng = np.random.default_rng(12)
     n, leaves = 70_000, 66_000
     src = [np.zeros(leaves, np.int32)]
@@ -556,3 +556,39 @@ def test_pair_table_past_its_first_size(F):
     qs.append(W.Query(500, 1, 10, W.Q_FORALL_T, W.DIR_IN, W.U_COMMON, True))
     info = _check_graph(F, g, qs)
     assert info["static_edges"] > (1 << 20)
+
+
+def _clique_graph(k=20000, size=4, seed=6):
+    """k disjoint cliques of `size` vertices, one temporal edge per ordered pair, times
+    within 20 s: every ordered pair of a clique has witnesses, so a query has up to
+    k * size * (size - 1) solution pairs."""
+    rng = np.random.default_rng(seed)
+    a, b = zip(*[(i, j) for i in range(size) for j in range(size) if i != j])
+    base = (np.arange(k, dtype=np.int32) * size)[:, None]
+    src = (base + np.array(a, np.int32)[None, :]).ravel()
+    dst = (base + np.array(b, np.int32)[None, :]).ravel()
+    t = rng.integers(0, 20, src.shape[0]).astype(np.int64)
+    o = np.argsort(t, kind="stable")
+    return W.TemporalGraph(k * size, src[o], dst[o], t[o])
+
+
+def test_pair_lists_past_the_pinned_stage(F):
+    """Pair lists longer than the pinned stage that small results come back through
+    (2^16 pairs per read-back, shared by a batch's queries) take the copy-out path;
+    short and long lists in one batch, single and batched, equal the oracle's."""
+    g = _clique_graph()
+    qs = [W.Query(100, 1, 2, W.Q_EXISTS, W.DIR_OUT, W.U_HEAD, True),
+          W.Query(100, 1, 3, W.Q_FORALL_T, W.DIR_EITHER, W.U_COMMON, True),
+          W.Query(3, 1, 1, W.Q_FORALL_T, W.DIR_IN, W.U_TAIL, True),
+          W.Query(1, 1, 2, W.Q_EXISTS, W.DIR_OUT, W.U_HEAD, True),
+          W.Query(0, 1, 1, W.Q_FORALL_T, W.DIR_OUT, W.U_HEAD, True)]
+    with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
+        seq = [G.query(q) for q in qs]
+        bat = G.query_batch(qs)
+    with oracle.OracleGraph.of(g) as og:
+        want = [og.query(q) for q in qs]
+    sizes = [len(w["u"]) for w in want]
+    assert max(sizes) > (1 << 16) and 0 < sorted(sizes)[2] < (1 << 16) // len(qs)
+    for q, a1, b1, w in zip(qs, seq, bat, want):
+        _assert_same(a1, w, str(q))
+        _assert_same(b1, w, str(q))
