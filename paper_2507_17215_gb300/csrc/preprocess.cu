@@ -2060,14 +2060,95 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
 
 // ================================================================== driver
 
+// A non-blocking stream of this thread for work that runs beside the caller's stream:
+// fork() makes it wait for everything enqueued on the caller's stream so far, join()
+// makes the caller's stream wait for everything enqueued on it. A fork that was not
+// joined (an error in between) is drained on destruction.
+class SideStream {
+  public:
+    explicit SideStream(cudaStream_t s) : s_(s) {}
+    ~SideStream() {
+        if (forked_) cudaStreamSynchronize(aux_);
+        if (ev_[0]) cudaEventDestroy(ev_[0]);
+        if (ev_[1]) cudaEventDestroy(ev_[1]);
+    }
+    SideStream(const SideStream&) = delete;
+    SideStream& operator=(const SideStream&) = delete;
+
+    cudaStream_t fork() {
+        thread_local std::vector<cudaStream_t> streams;  // per device, kept for the thread's life
+        int dev = 0;
+        FOLTY_CUDA(cudaGetDevice(&dev));
+        if ((int)streams.size() <= dev) streams.resize(dev + 1, nullptr);
+        if (!streams[dev]) FOLTY_CUDA(cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking));
+        aux_ = streams[dev];
+        for (auto& e : ev_)
+            if (!e) FOLTY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        FOLTY_CUDA(cudaEventRecord(ev_[0], s_));
+        FOLTY_CUDA(cudaStreamWaitEvent(aux_, ev_[0], 0));
+        forked_ = true;
+        return aux_;
+    }
+    void join() {
+        FOLTY_CUDA(cudaEventRecord(ev_[1], aux_));
+        FOLTY_CUDA(cudaStreamWaitEvent(s_, ev_[1], 0));
+        forked_ = false;
+    }
+
+  private:
+    cudaStream_t s_;
+    cudaStream_t aux_ = nullptr;
+    cudaEvent_t ev_[2] = {nullptr, nullptr};
+    bool forked_ = false;
+};
+
 // The sorted values index other arrays: a sort whose look-back ran out must stop here
 // (read_back checks the graph's error word).
 static void sort_check(folty_graph* g, cudaStream_t s) { read_back(g, nullptr, nullptr, 0, nullptr, s); }
 
-// A1 with dense pair ids (see k_pair_insert): false, with nothing of the graph written,
-// when the table cannot serve (too many distinct pairs, a probe sequence ran out, or
-// ids and time ranks do not fit one word); FOLTY_PAIR_SORT=keys forces that answer.
-static bool pair_ids_sort(folty_graph* g, Scratch& sc, const uint32_t* order, uint32_t* t32, cudaStream_t s) {
+// The second half of A1 with dense pair ids: the temporal edges sorted by (pair id,
+// direction, time rank) into the store (perm, T, sd, seg). It needs nothing of the
+// static graph's later steps, and they nothing of it before the triangle pass, so it
+// runs on a second stream beside the peeling.
+struct StoreJob {
+    const uint32_t* slotw;  // [m] pair table slot and direction of each input edge
+    const uint32_t* order;  // time order of an unsorted input, or null
+    const int32_t* sid;     // [table] dense pair id of each table slot
+    uint32_t* t32;          // [m] 32-bit time offsets (ts32), or null
+    int ib;                 // bits of a time rank
+};
+
+static void temporal_store(folty_graph* g, const StoreJob& job, Scratch& sc) {
+    const int T = 256;
+    const int64_t m = g->m, mk = g->m_kept;
+    const int32_t S = g->S;
+    const int ib = job.ib;
+    cudaStream_t s = sc.stream();
+    // edges by (pair id, direction, time rank): keys only, on the id and direction bits
+    uint64_t* packed = sc.get<uint64_t>(m);
+    uint64_t* packed_alt = sc.get<uint64_t>(m);
+    FOLTY_LAUNCH(k_pair_pack, grid_for(m, T), T, 0, s, job.slotw, job.order, m, job.sid, S, ib, packed);
+    const bool palt = radix_sort_keys(sc, packed, packed_alt, m, ib, bit_length((uint64_t)(2 * S)));
+    const uint64_t* sp = palt ? packed_alt : packed;
+    if (job.t32) FOLTY_LAUNCH(k_offsets32, grid_for(m, T), T, 0, s, g->in_t, m, g->tmin, job.t32);
+    if (g->ts32)
+        FOLTY_LAUNCH(k_pair_store<uint32_t>, grid_for(mk, T), T, 0, s, sp, job.order, mk, S, ib, job.t32, g->perm,
+                     (uint32_t*)g->T, g->sd, g->seg);
+    else
+        FOLTY_LAUNCH(k_pair_store<int64_t>, grid_for(mk, T), T, 0, s, sp, job.order, mk, S, ib, g->in_t, g->perm,
+                     (int64_t*)g->T, g->sd, g->seg);
+    FOLTY_LAUNCH(k_segments_split, grid_for(mk, T), T, 0, s, g->sd, mk, S, g->seg);
+    FOLTY_LAUNCH(k_segments_fix, grid_for(S, T), T, 0, s, S, mk, g->seg);
+}
+
+// A1 with dense pair ids (see k_pair_insert) up to the static edge list (ea, eb) and
+// the job of the temporal store: false, with nothing of the graph written, when the
+// table cannot serve (too many distinct pairs, a probe sequence ran out, or ids and
+// time ranks do not fit one word); FOLTY_PAIR_SORT=keys forces that answer. The
+// distinct-pair sort is checked by the next read-back (before any of its consumers but
+// the guarded k_pair_ids index with it).
+static bool pair_ids_sort(folty_graph* g, Scratch& sc, const uint32_t* order, uint32_t* t32, cudaStream_t s,
+                          StoreJob* job) {
     const int T = 256;
     const int64_t m = g->m, mk = g->m_kept;
     const int32_t n = g->n;
@@ -2121,22 +2202,7 @@ static bool pair_ids_sort(folty_graph* g, Scratch& sc, const uint32_t* order, ui
     g->seg = graph_alloc<int32_t>(g, 2 * (int64_t)S + 1, s);
     int32_t* sid = sc.get<int32_t>(tb);
     FOLTY_LAUNCH(k_pair_ids, grid_for(S, T), T, 0, s, ur, us, S, n, tb, sid, g->ea, g->eb);
-    // edges by (pair id, direction, time rank): keys only, on the id and direction bits
-    uint64_t* packed = sc.get<uint64_t>(m);
-    uint64_t* packed_alt = sc.get<uint64_t>(m);
-    FOLTY_LAUNCH(k_pair_pack, grid_for(m, T), T, 0, s, slotw, order, m, sid, S, ib, packed);
-    const bool palt = radix_sort_keys(sc, packed, packed_alt, m, ib, bit_length((uint64_t)(2 * S)));
-    const uint64_t* sp = palt ? packed_alt : packed;
-    if (t32) FOLTY_LAUNCH(k_offsets32, grid_for(m, T), T, 0, s, g->in_t, m, g->tmin, t32);
-    if (g->ts32)
-        FOLTY_LAUNCH(k_pair_store<uint32_t>, grid_for(mk, T), T, 0, s, sp, order, mk, S, ib, t32, g->perm,
-                     (uint32_t*)g->T, g->sd, g->seg);
-    else
-        FOLTY_LAUNCH(k_pair_store<int64_t>, grid_for(mk, T), T, 0, s, sp, order, mk, S, ib, g->in_t, g->perm,
-                     (int64_t*)g->T, g->sd, g->seg);
-    FOLTY_LAUNCH(k_segments_split, grid_for(mk, T), T, 0, s, g->sd, mk, S, g->seg);
-    FOLTY_LAUNCH(k_segments_fix, grid_for(S, T), T, 0, s, S, mk, g->seg);
-    sort_check(g, s);  // the sort's look-back and the pair lookups
+    *job = StoreJob{slotw, order, sid, t32, ib};
     return true;
 }
 
@@ -2225,14 +2291,15 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         sort_check(g, s);
         order = alt ? iv_alt : iv;
     }
-    if (!pair_ids_sort(g, sc, order, t32, s)) pair_key_sort(g, sc, order, t32, s);
+    StoreJob job{};
+    const bool ids = pair_ids_sort(g, sc, order, t32, s, &job);
+    if (!ids) pair_key_sort(g, sc, order, t32, s);
     const int32_t S = g->S;
-    // the raw input is no longer needed
-    graph_release(g, g->in_src, s);
-    graph_release(g, g->in_dst, s);
-    graph_release(g, g->in_t, s);
-    g->in_src = g->in_dst = nullptr;
-    g->in_t = nullptr;
+    // the temporal store of the dense-id path: forked to the side stream once the grid
+    // peeling kernel has finished (its grid barriers want every SM), joined before the
+    // triangle pass; on an error in between, the side stream is drained before the
+    // call's buffers go
+    SideStream side(s);
 
     // ---------------- A2: static CSR
     // static edges are sorted by (a, b); a stable sort by b lists them by (b, a)
@@ -2318,6 +2385,10 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
             FOLTY_CUDA(cudaLaunchCooperativeKernel((const void*)k_peel, grid, block, args, 0, s));
             after_launch("k_peel");
         }
+        if (ids) {
+            Scratch sc2(g->alloc, side.fork(), g->dev_err);
+            temporal_store(g, job, sc2);
+        }
         if (n > 0) {
             // cluster tail on the induced subgraph of the vertices the grid kernel left;
             // always enqueued (its kernels do nothing when the grid kernel finished), so
@@ -2388,6 +2459,13 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
                      out_eid, out_src);
 
     // ---------------- A5: triangles
+    if (ids) side.join();
+    // the raw input is no longer needed
+    graph_release(g, g->in_src, s);
+    graph_release(g, g->in_dst, s);
+    graph_release(g, g->in_t, s);
+    g->in_src = g->in_dst = nullptr;
+    g->in_t = nullptr;
     g->common = graph_alloc<int32_t>(g, S, s);
     FOLTY_CUDA(cudaMemsetAsync(g->common, 0, sizeof(int32_t) * ((size_t)S > 0 ? (size_t)S : 1), s));
     int32_t* tcnt = sc.get<int32_t>((int64_t)S + 1);
