@@ -2060,13 +2060,14 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
 
 // ================================================================== driver
 
-// A non-blocking stream of this thread for work that runs beside the caller's stream:
-// fork() makes it wait for everything enqueued on the caller's stream so far, join()
-// makes the caller's stream wait for everything enqueued on it. A fork that was not
-// joined (an error in between) is drained on destruction.
+// A non-blocking stream of this thread (of the device's highest or default priority)
+// for work that runs beside the caller's stream: fork() makes it wait for everything
+// enqueued on the caller's stream so far, join() makes the caller's stream wait for
+// everything enqueued on it. A fork that was not joined (an error in between) is
+// drained on destruction.
 class SideStream {
   public:
-    explicit SideStream(cudaStream_t s) : s_(s) {}
+    SideStream(cudaStream_t s, bool high) : s_(s), high_(high) {}
     ~SideStream() {
         if (forked_) cudaStreamSynchronize(aux_);
         if (ev_[0]) cudaEventDestroy(ev_[0]);
@@ -2076,12 +2077,18 @@ class SideStream {
     SideStream& operator=(const SideStream&) = delete;
 
     cudaStream_t fork() {
-        thread_local std::vector<cudaStream_t> streams;  // per device, kept for the thread's life
+        // per device and priority, kept for the thread's life
+        thread_local std::vector<cudaStream_t> streams[2];
         int dev = 0;
         FOLTY_CUDA(cudaGetDevice(&dev));
-        if ((int)streams.size() <= dev) streams.resize(dev + 1, nullptr);
-        if (!streams[dev]) FOLTY_CUDA(cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking));
-        aux_ = streams[dev];
+        auto& v = streams[high_ ? 1 : 0];
+        if ((int)v.size() <= dev) v.resize(dev + 1, nullptr);
+        if (!v[dev]) {
+            int least = 0, greatest = 0;
+            FOLTY_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+            FOLTY_CUDA(cudaStreamCreateWithPriority(&v[dev], cudaStreamNonBlocking, high_ ? greatest : least));
+        }
+        aux_ = v[dev];
         for (auto& e : ev_)
             if (!e) FOLTY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         FOLTY_CUDA(cudaEventRecord(ev_[0], s_));
@@ -2097,6 +2104,7 @@ class SideStream {
 
   private:
     cudaStream_t s_;
+    bool high_;
     cudaStream_t aux_ = nullptr;
     cudaEvent_t ev_[2] = {nullptr, nullptr};
     bool forked_ = false;
@@ -2295,11 +2303,12 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     const bool ids = pair_ids_sort(g, sc, order, t32, s, &job);
     if (!ids) pair_key_sort(g, sc, order, t32, s);
     const int32_t S = g->S;
-    // the temporal store of the dense-id path: forked to the side stream once the grid
+    // the temporal store of the dense-id path: forked to a side stream once the grid
     // peeling kernel has finished (its grid barriers want every SM), joined before the
-    // triangle pass; on an error in between, the side stream is drained before the
-    // call's buffers go
-    SideStream side(s);
+    // triangle pass; the later peeling phases on a second one of high priority. On an
+    // error in between, the side streams are drained before the call's buffers go.
+    SideStream side(s, false);
+    SideStream hi(s, true);
 
     // ---------------- A2: static CSR
     // static edges are sorted by (a, b); a stable sort by b lists them by (b, a)
@@ -2390,54 +2399,60 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
             temporal_store(g, job, sc2);
         }
         if (n > 0) {
+            // the cluster and single-CTA phases: latency-bound chains of small rounds, on
+            // a high-priority side stream so that their blocks go first on SMs that the
+            // temporal store's kernels free
+            const cudaStream_t ts = hi.fork();
+            Scratch sct(g->alloc, ts, g->dev_err);
             // cluster tail on the induced subgraph of the vertices the grid kernel left;
             // always enqueued (its kernels do nothing when the grid kernel finished), so
             // no host round trip separates the two
             const int tn = pa.tail_n;
-            int32_t* L = sc.get<int32_t>(tn);
-            int32_t* gmap = sc.get<int32_t>(n);
-            int32_t* ld = sc.get<int32_t>(tn + 1);
-            int32_t* d0 = sc.get<int32_t>(tn + 1);
-            int32_t* lrow = sc.get<int32_t>(tn + 1);
-            int32_t* eoff = sc.get<int32_t>(tn + 1);
+            int32_t* L = sct.get<int32_t>(tn);
+            int32_t* gmap = sct.get<int32_t>(n);
+            int32_t* ld = sct.get<int32_t>(tn + 1);
+            int32_t* d0 = sct.get<int32_t>(tn + 1);
+            int32_t* lrow = sct.get<int32_t>(tn + 1);
+            int32_t* eoff = sct.get<int32_t>(tn + 1);
             // zeroed together: the local vertex count, then the fill counters
-            int32_t* zblk = sc.get<int32_t>(tn + 1);
+            int32_t* zblk = sct.get<int32_t>(tn + 1);
             int* nl = zblk;
             int32_t* fillc = zblk + 1;
-            uint32_t* ladj = sc.get<uint32_t>(2 * (int64_t)S);
-            FOLTY_CUDA(cudaMemsetAsync(zblk, 0, sizeof(int32_t) * (size_t)(tn + 1), s));
-            FOLTY_LAUNCH(k_tail_select, grid_for(n, T), T, 0, s, pa.alive[0], pa.alive[1], pa.ctl, rnd, tn, L, gmap,
+            uint32_t* ladj = sct.get<uint32_t>(2 * (int64_t)S);
+            FOLTY_CUDA(cudaMemsetAsync(zblk, 0, sizeof(int32_t) * (size_t)(tn + 1), ts));
+            FOLTY_LAUNCH(k_tail_select, grid_for(n, T), T, 0, ts, pa.alive[0], pa.alive[1], pa.ctl, rnd, tn, L, gmap,
                          nl, pa.ctl + C_ERR);
-            FOLTY_LAUNCH(k_tail_degrees, grid_for(tn, T), T, 0, s, L, nl, pa.deg, rowptr, tn, ld, d0);
-            exclusive_scan(sc, ld, lrow, tn);
-            exclusive_scan(sc, d0, eoff, tn);
-            FOLTY_LAUNCH(k_tail_fill, grid_for(2 * (int64_t)S, T), T, 0, s, L, eoff, tn, rowptr, adj, rnd, gmap,
+            FOLTY_LAUNCH(k_tail_degrees, grid_for(tn, T), T, 0, ts, L, nl, pa.deg, rowptr, tn, ld, d0);
+            exclusive_scan(sct, ld, lrow, tn);
+            exclusive_scan(sct, d0, eoff, tn);
+            FOLTY_LAUNCH(k_tail_fill, grid_for(2 * (int64_t)S, T), T, 0, ts, L, eoff, tn, rowptr, adj, rnd, gmap,
                          lrow, ld, fillc, ladj, pa.ctl + C_ERR);
             // single-CTA phase for the last SOLO_CAP vertices (does nothing unless the
             // cluster hands off)
             // zeroed together: the exported count, the degrees, the fill counters
-            int32_t* sblk = sc.get<int32_t>(1 + (SOLO_CAP + 1) + SOLO_CAP);
+            int32_t* sblk = sct.get<int32_t>(1 + (SOLO_CAP + 1) + SOLO_CAP);
             int* ns = sblk;
             int32_t* sdeg = sblk + 1;
             int32_t* fc = sdeg + (SOLO_CAP + 1);
-            int32_t* slist = sc.get<int32_t>(SOLO_CAP);
-            int32_t* srow = sc.get<int32_t>(SOLO_CAP + 1);
-            int32_t* dl = sc.get<int32_t>(SOLO_CAP + 1);
-            int32_t* eo = sc.get<int32_t>(SOLO_CAP + 1);
-            int32_t* sgid = sc.get<int32_t>(SOLO_CAP);
-            int32_t* map2 = sc.get<int32_t>(tn);
-            uint16_t* sadj = sc.get<uint16_t>(2 * (int64_t)S);
-            FOLTY_CUDA(cudaMemsetAsync(sblk, 0, sizeof(int32_t) * (size_t)(1 + (SOLO_CAP + 1) + SOLO_CAP), s));
-            FOLTY_CUDA(cudaMemsetAsync(map2, 0xff, sizeof(int32_t) * (size_t)tn, s));
+            int32_t* slist = sct.get<int32_t>(SOLO_CAP);
+            int32_t* srow = sct.get<int32_t>(SOLO_CAP + 1);
+            int32_t* dl = sct.get<int32_t>(SOLO_CAP + 1);
+            int32_t* eo = sct.get<int32_t>(SOLO_CAP + 1);
+            int32_t* sgid = sct.get<int32_t>(SOLO_CAP);
+            int32_t* map2 = sct.get<int32_t>(tn);
+            uint16_t* sadj = sct.get<uint16_t>(2 * (int64_t)S);
+            FOLTY_CUDA(cudaMemsetAsync(sblk, 0, sizeof(int32_t) * (size_t)(1 + (SOLO_CAP + 1) + SOLO_CAP), ts));
+            FOLTY_CUDA(cudaMemsetAsync(map2, 0xff, sizeof(int32_t) * (size_t)tn, ts));
             TailArgs ta{nl, L, ld, lrow, ladj, rnd, core, pa.ctl, SOLO_CAP, ns, slist, sdeg, map2};
-            if (tail_c == 16) launch_tail<16>(ta, s);
-            else launch_tail<8>(ta, s);
-            FOLTY_LAUNCH(k_solo_rows, grid_for(SOLO_CAP, T), T, 0, s, pa.ctl, ns, slist, lrow, L, dl, sgid);
-            exclusive_scan(sc, sdeg, srow, SOLO_CAP);
-            exclusive_scan(sc, dl, eo, SOLO_CAP);
-            FOLTY_LAUNCH(k_solo_fill, grid_for(2 * (int64_t)S, T), T, 0, s, pa.ctl, eo, slist, sdeg, srow, lrow, ladj,
+            if (tail_c == 16) launch_tail<16>(ta, ts);
+            else launch_tail<8>(ta, ts);
+            FOLTY_LAUNCH(k_solo_rows, grid_for(SOLO_CAP, T), T, 0, ts, pa.ctl, ns, slist, lrow, L, dl, sgid);
+            exclusive_scan(sct, sdeg, srow, SOLO_CAP);
+            exclusive_scan(sct, dl, eo, SOLO_CAP);
+            FOLTY_LAUNCH(k_solo_fill, grid_for(2 * (int64_t)S, T), T, 0, ts, pa.ctl, eo, slist, sdeg, srow, lrow, ladj,
                          map2, fc, sadj, pa.ctl + C_ERR);
-            launch_solo(SoloArgs{ns, sdeg, fc, srow, sadj, sgid, rnd, core, pa.ctl}, s);
+            launch_solo(SoloArgs{ns, sdeg, fc, srow, sadj, sgid, rnd, core, pa.ctl}, ts);
+            hi.join();
         }
         peel_ctl = pa.ctl;  // rounds, alpha and the error word are read with the triangle totals
     }
