@@ -1316,12 +1316,36 @@ __global__ void k_solo_rows(const int* __restrict__ ctl, const int* __restrict__
 // solo ids (order within a row is irrelevant). Every row must come out with exactly the
 // degree the cluster exported (its alive neighbours): fc counts them, and the
 // single-CTA kernel checks the count; an entry beyond it is recorded in *err (4).
+// L2 residency of the single-CTA phase's rows: written and read with an "evict last"
+// policy, so that the streaming kernels of the temporal store, which run beside the
+// peeling, evict their own lines first; set back to normal when the phase ends.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ int ld_keep_u16(const uint16_t* p, uint64_t pol) {
+    unsigned short v;
+    asm("ld.global.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+    return (int)v;
+}
+
+__device__ __forceinline__ void st_keep_u16(uint16_t* p, uint16_t v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.u16 [%0], %1, %2;" ::"l"(p), "h"(v), "l"(pol) : "memory");
+}
+
+__device__ __forceinline__ void l2_release_line(const void* p) {
+    asm volatile("applypriority.global.L2::evict_normal [%0], 128;" ::"l"(p) : "memory");
+}
+
 __global__ void k_solo_fill(const int* __restrict__ ctl, const int32_t* __restrict__ eo,
                             const int32_t* __restrict__ slist, const int32_t* __restrict__ sdeg,
                             const int32_t* __restrict__ srow, const int32_t* __restrict__ lrow,
                             const uint32_t* __restrict__ ladj, const int32_t* __restrict__ map2,
                             int32_t* __restrict__ fc, uint16_t* __restrict__ sadj, int* __restrict__ err) {
     if (ctl[C_SOLO] != 1 || ctl[C_ERR] != 0) return;
+    const uint64_t keep = l2_keep_policy();
     const int64_t total = eo[SOLO_CAP];
     const int64_t step = (int64_t)gridDim.x * blockDim.x * FILL_RUN;
     for (int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * FILL_RUN; e0 < total; e0 += step) {
@@ -1337,7 +1361,7 @@ __global__ void k_solo_fill(const int* __restrict__ ctl, const int32_t* __restri
             const int32_t m = map2[ladj[lrow[slist[lo]] + (int32_t)(e - eo[lo])]];
             if (m >= 0) {
                 const int p = atomicAdd(&fc[lo], 1);
-                if (p < sdeg[lo]) sadj[srow[lo] + p] = (uint16_t)m;
+                if (p < sdeg[lo]) st_keep_u16(&sadj[srow[lo] + p], (uint16_t)m, keep);
                 else atomicExch(err, 4);
             }
         }
@@ -1406,6 +1430,20 @@ __device__ __forceinline__ void solo_push(int v, uint16_t* fl, int* cnt, int cap
     if (at < cap) fl[at] = (uint16_t)v;
 }
 
+// Row entries at or past ns cannot come from rows that k_solo_fill checked; such an
+// entry is dropped and flags an internal error. Checked after all N loads were issued,
+// so that the loads overlap.
+template <int N>
+__device__ __forceinline__ void solo_check_rows(int (&vv)[N], int ns, int* ctl) {
+#pragma unroll
+    for (int c = 0; c < N; c++) {
+        if (vv[c] >= ns) {
+            atomicExch(&ctl[C_ERR], 5);
+            vv[c] = -1;
+        }
+    }
+}
+
 // Neighbours vv[0..N) (negative: none) lose one degree each at level k; a k + 1 -> k
 // crossing files the vertex in the next frontier. Only the first nch items can hold
 // neighbours; nch must be the same across the warp, which must call it whole.
@@ -1429,6 +1467,7 @@ __device__ __forceinline__ void solo_decrement(SoloShared& sh, const int (&vv)[N
 __device__ __forceinline__ void bm_phase(SoloShared& sh, const SoloArgs& a, int ns, int n3, unsigned mine, int& k,
                                          int& r, int& rounds, int& lvl, int& steps, bool& bad) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t keep = l2_keep_policy();
     constexpr uint16_t NONE = 0xffff;
     uint16_t* map = sh.FL[0];
     int32_t* deg3 = reinterpret_cast<int32_t*>(sh.FL[1]);
@@ -1485,7 +1524,7 @@ __device__ __forceinline__ void bm_phase(SoloShared& sh, const SoloArgs& a, int 
 #pragma unroll
             for (int t = 0; t < 8; t++) {
                 const int j = j0 + t * 32 + lane;
-                nb[t] = j < e ? a.sadj[j] : -1;
+                nb[t] = j < e ? ld_keep_u16(&a.sadj[j], keep) : -1;
             }
 #pragma unroll
             for (int t = 0; t < 8; t++) {
@@ -1584,6 +1623,7 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
     const int ns = *a.ns;
     if (ns > SOLO_CAP) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t keep = l2_keep_policy();
     int miscount = 0;
     for (int i = tid; i <= ns; i += SOLO_THREADS) {
         if (i < ns) {
@@ -1706,13 +1746,10 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
 #pragma unroll
                             for (int st = 16; st > 0; st >>= 1)
                                 if (lo + st < nL && sh.sx[lo + st] <= x) lo += st;
-                            vv[c] = a.sadj[sh.sb[lo] + x];
-                            if (vv[c] >= ns) {  // cannot happen for rows k_solo_fill checked
-                                atomicExch(&a.ctl[C_ERR], 5);
-                                vv[c] = -1;
-                            }
+                            vv[c] = ld_keep_u16(&a.sadj[sh.sb[lo] + x], keep);
                         }
                     }
+                    solo_check_rows(vv, ns, a.ctl);
                     solo_decrement(sh, vv, nch, k, fn, cn);
                 }
                 if (gid >= 0) {
@@ -1798,13 +1835,10 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
                                     if (sh.P[mid] <= x) lo = mid;
                                     else hi = mid - 1;
                                 }
-                                vv[c] = a.sadj[sh.D[lo] + x];
-                                if (vv[c] >= ns) {
-                                    atomicExch(&a.ctl[C_ERR], 5);
-                                    vv[c] = -1;
-                                }
+                                vv[c] = ld_keep_u16(&a.sadj[sh.D[lo] + x], keep);
                             }
                         }
+                        solo_check_rows(vv, ns, a.ctl);
                         solo_decrement(sh, vv, nch, k, fn, cn);
                     }
 #pragma unroll
@@ -1823,6 +1857,8 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
         if (bad) break;
     }
     if (n3 > 0 && !bad) bm_phase(sh, a, ns, n3, mine, k, r, rounds, lvl, steps, bad);
+    // the rows' lines go back to normal eviction priority
+    for (int x = tid * 64; x < sh.rs[ns]; x += SOLO_THREADS * 64) l2_release_line(a.sadj + x);
     if (tid == 0) {
         if (bad) atomicExch(&a.ctl[C_ERR], 2);
         a.ctl[C_ROUNDS] = rounds;
