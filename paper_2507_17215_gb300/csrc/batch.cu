@@ -11,6 +11,7 @@
 // memory budget, the deltas are cut into chunks, one probe pass per chunk (bin 0 of a
 // chunk also holds every smaller gap).
 #include <algorithm>
+#include <cstring>
 #include <map>
 
 #include "internal.cuh"
@@ -19,6 +20,7 @@
 namespace folty {
 
 constexpr int BATCH_MAX_BINS = 1024;
+static_assert(BATCH_MAX_BINS * sizeof(int64_t) <= 4 * PAIR_STAGE * sizeof(int32_t), "bin bounds fit the pair stage");
 
 // bins[j][e] <- sum_{i <= j} bins[i][e]
 template <typename C>
@@ -116,19 +118,24 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
             std::vector<int64_t> hd(D.begin() + (long)c0, D.begin() + (long)c0 + k);
             // the bin bounds in the store's timestamp type (32-bit offsets: gaps stay
             // below 2^32 - 1, so larger windows behave as 2^32 - 2)
-            std::vector<uint32_t> hd32(hd.size());
-            for (size_t i = 0; i < hd.size(); i++) hd32[i] = hd[i] >= 0xfffffffell ? 0xfffffffeu : (uint32_t)hd[i];
-            if (g->ts32)
-                FOLTY_CUDA(cudaMemcpyAsync(dd, hd32.data(), sizeof(uint32_t) * (size_t)k, cudaMemcpyHostToDevice, s));
-            else
-                FOLTY_CUDA(cudaMemcpyAsync(dd, hd.data(), sizeof(int64_t) * (size_t)k, cudaMemcpyHostToDevice, s));
+            // staged in the graph's pinned pair stage, which nothing uses before this
+            // chunk's threshold pass (the last chunk's read-back has completed)
+            void* hb = g->host_stage + HOST_STAGE;
+            if (g->ts32) {
+                uint32_t* h32 = static_cast<uint32_t*>(hb);
+                for (int i = 0; i < k; i++) h32[i] = hd[i] >= 0xfffffffell ? 0xfffffffeu : (uint32_t)hd[i];
+            } else {
+                std::memcpy(hb, hd.data(), sizeof(int64_t) * (size_t)k);
+            }
+            g->stage_busy = 1;
+            FOLTY_CUDA(cudaMemcpyAsync(dd, hb, (g->ts32 ? sizeof(uint32_t) : sizeof(int64_t)) * (size_t)k,
+                                       cudaMemcpyHostToDevice, s));
             if (mk > 0) {
                 if (b16) FOLTY_CUDA(cudaMemsetAsync(bins16, 0, sizeof(uint16_t) * (size_t)(mk * k + 2), s));
                 else FOLTY_CUDA(cudaMemsetAsync(bins, 0, sizeof(int32_t) * (size_t)(mk * k), s));
                 if (P > 0) launch_probe_live(g, hd[k - 1], dir, 1, nullptr, bins, k, dd, s, nullptr, bins16);
                 if (k > 1 && b16) FOLTY_LAUNCH(k_bins_prefix<uint16_t>, grid_for(mk, 256), 256, 0, s, bins16, k, mk);
                 if (k > 1 && !b16) FOLTY_LAUNCH(k_bins_prefix<int32_t>, grid_for(mk, 256), 256, 0, s, bins, k, mk);
-                FOLTY_CUDA(cudaStreamSynchronize(s));  // the host bounds must outlive the copy
             }
             std::vector<const folty_query_params*> fq;
             std::vector<CountView> fc;
