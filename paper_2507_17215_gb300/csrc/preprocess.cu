@@ -1449,13 +1449,19 @@ __device__ __forceinline__ void solo_check_rows(int (&vv)[N], int ns, int* ctl) 
 // neighbours; nch must be the same across the warp, which must call it whole.
 template <int N>
 __device__ __forceinline__ void solo_decrement(SoloShared& sh, const int (&vv)[N], int nch, int k, uint16_t* fn,
-                                               int* cn) {
+                                               int* cn, const uint16_t* sadj) {
     int old[N];
 #pragma unroll
     for (int c = 0; c < N; c++) old[c] = vv[c] >= 0 ? atomicSub(&sh.u.deg[vv[c]], 1) : 0;
 #pragma unroll
-    for (int c = 0; c < N; c++)
-        if (c < nch) solo_append(vv[c] >= 0 && old[c] == k + 1, vv[c], fn, cn);
+    for (int c = 0; c < N; c++) {
+        if (c < nch) {
+            const bool joins = vv[c] >= 0 && old[c] == k + 1;
+            solo_append(joins, vv[c], fn, cn);
+            // the next round reads this vertex's row: start its first line on the way to L1
+            if (joins) asm volatile("prefetch.global.L1 [%0];" ::"l"(sadj + sh.rs[vv[c]]));
+        }
+    }
 }
 
 // The last levels on the bit matrix. At entry every thread's mask lists its alive slots
@@ -1750,7 +1756,7 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
                         }
                     }
                     solo_check_rows(vv, ns, a.ctl);
-                    solo_decrement(sh, vv, nch, k, fn, cn);
+                    solo_decrement(sh, vv, nch, k, fn, cn, a.sadj);
                 }
                 if (gid >= 0) {
                     a.rnd[gid] = r;
@@ -1839,7 +1845,7 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1) k_peel_solo(SoloArgs a) {
                             }
                         }
                         solo_check_rows(vv, ns, a.ctl);
-                        solo_decrement(sh, vv, nch, k, fn, cn);
+                        solo_decrement(sh, vv, nch, k, fn, cn, a.sadj);
                     }
 #pragma unroll
                     for (int u = 0; u < 2; u++) {
