@@ -182,25 +182,38 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const int32_t* __r
     __syncthreads();
     const int64_t tile = s_tile;
     const int64_t base = tile * LS_TILE;
-    // ---- the kept roles, in coalesced order
+    // ---- the kept roles, in coalesced order; every load of a thread is issued before any
+    // of them is used (the byte of a role is read whether or not its sigma1 is zero), so
+    // that a thread waits for memory once per group of items rather than once per role
+    constexpr int LS_GROUP = 4;
 #pragma unroll
-    for (int i = 0; i < LS_ITEMS; i++) {
-        const int idx = i * SCAN_THREADS + threadIdx.x;
-        const int64_t t = base + idx;
-        int m = 0;
-        int64_t lp = 0;
-        if (t < ntri) {
+    for (int i0 = 0; i0 < LS_ITEMS; i0 += LS_GROUP) {
+        int32_t s1[LS_GROUP][6];
+        uint8_t bk[LS_GROUP][6];
+#pragma unroll
+        for (int i = 0; i < LS_GROUP; i++) {
+            const int64_t t = base + (i0 + i) * SCAN_THREADS + threadIdx.x;
 #pragma unroll
             for (int r = 0; r < 6; r++) {
-                const int32_t s1 = rsig[r * ntri + t];
-                if (s1 > 0 && bucket_live(rmin_dir[r * ntri + t], delta)) {
-                    m |= 1 << r;
-                    lp += s1;
-                }
+                s1[i][r] = t < ntri ? __ldcs(&rsig[r * ntri + t]) : 0;
+                bk[i][r] = t < ntri ? __ldcs(&rmin_dir[r * ntri + t]) : 0;
             }
         }
-        scost[pad(idx)] = lp > 0 ? lp + LIVE_IDLE : 0;
-        smask[idx] = (uint8_t)m;
+#pragma unroll
+        for (int i = 0; i < LS_GROUP; i++) {
+            const int idx = (i0 + i) * SCAN_THREADS + threadIdx.x;
+            int m = 0;
+            int64_t lp = 0;
+#pragma unroll
+            for (int r = 0; r < 6; r++) {
+                if (s1[i][r] > 0 && bucket_live(bk[i][r], delta)) {
+                    m |= 1 << r;
+                    lp += s1[i][r];
+                }
+            }
+            scost[pad(idx)] = lp > 0 ? lp + LIVE_IDLE : 0;
+            smask[idx] = (uint8_t)m;
+        }
     }
     __syncthreads();
     // ---- thread sums over LS_ITEMS consecutive triangles, block scans, look-backs
