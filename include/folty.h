@@ -137,7 +137,9 @@ typedef struct {
 /* Section 1.2 / Section 2 input. Copies the m edges (src[i] -> dst[i] at t[i]) into
  * device memory owned by the new graph and validates them. The three arrays may be
  * host or device pointers (detected per pointer); they stay owned by the caller and
- * are not referenced after the call returns. alloc may be NULL. On success *out
+ * are not referenced after the call returns. Memory of the current device and pinned
+ * host memory, all three 16-byte aligned, are copied and checked by one kernel pass;
+ * other input is copied first, then checked. alloc may be NULL. On success *out
  * receives a graph in the "loaded" state. Errors: FOLTY_EINVAL (n, m out of range, an
  * id outside [0, n), t outside [0, 2^62)), FOLTY_ENOMEM, FOLTY_ECUDA. */
 folty_status folty_load_temporal_graph(int32_t n, int64_t m, const int32_t *src,
