@@ -5,6 +5,7 @@
 #include <mutex>
 
 #include "internal.cuh"
+#include "pairs.cuh"
 
 namespace folty {
 
@@ -143,7 +144,8 @@ void graph_release(folty_graph* g, void* p, cudaStream_t s) {
     if (!p) return;
     auto& v = *g->owned;
     for (size_t i = 0; i < v.size(); i++) {
-        if (v[i] == p) {
+        if (v[i].first == p) {
+            g->info.device_bytes -= (int64_t)v[i].second;
             v.erase(v.begin() + (long)i);
             g->alloc.put(p, s);
             return;
@@ -307,7 +309,7 @@ static void stage_give(int64_t* p, bool busy) {
 
 static void free_graph(folty_graph* g) {
     if (g->owned) {
-        for (void* p : *g->owned) g->alloc.put(p, 0);
+        for (auto& o : *g->owned) g->alloc.put(o.first, 0);
         delete g->owned;
         g->owned = nullptr;
     }
@@ -364,16 +366,34 @@ __global__ void k_validate(const int32_t* __restrict__ src, const int32_t* __res
     st.flush(stat);
 }
 
+// The pair table's first try, filled while the load reads the edges (INSERT): the
+// slot word of every edge (PAIR_LOOP for a self-loop or an invalid edge, which fails the
+// load anyway).
+struct LoadPairs {
+    uint64_t* table;
+    int lg;
+    uint32_t* slotw;
+    int* over;
+};
+
+template <bool INSERT>
+__device__ __forceinline__ uint32_t load_slot_word(const LoadPairs& lp, int32_t x, int32_t y, int32_t n) {
+    if (!INSERT || x < 0 || x >= n || y < 0 || y >= n) return PAIR_LOOP;
+    return pair_slot_word(lp.table, lp.lg, x, y, n, lp.over);
+}
+
 // The same checks fused with the copy of the input into the graph's own arrays: one
 // read and one write of every input byte. The input is device memory or pinned host
-// memory (read over the host link, as fast as a copy engine's pull). Four edges per
-// thread and iteration (16-byte accesses; all six pointers 16-byte aligned), the
-// previous edge's timestamp from the neighbouring lane, the m mod 4 last edges one by
-// one.
+// memory (read over the host link, as fast as a copy engine's pull); with INSERT the
+// edges' pairs also go into the pair table (work that the host link's pace leaves room
+// for). Four edges per thread and iteration (16-byte accesses; all pointers 16-byte
+// aligned), the previous edge's timestamp from the neighbouring lane, the m mod 4 last
+// edges one by one.
+template <bool INSERT>
 __global__ void k_load_copy(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
                             const int64_t* __restrict__ t, int64_t m, int32_t n, int32_t* __restrict__ osrc,
                             int32_t* __restrict__ odst, int64_t* __restrict__ ot,
-                            unsigned long long* __restrict__ stat) {
+                            unsigned long long* __restrict__ stat, LoadPairs lp) {
     EdgeStat st;
     const int lane = threadIdx.x & 31;
     const int64_t m4 = m >> 2;
@@ -402,6 +422,14 @@ __global__ void k_load_copy(const int32_t* __restrict__ src, const int32_t* __re
             st.edge(i + 1, x.y, y.y, t01.y, t01.x, n);
             st.edge(i + 2, x.z, y.z, t23.x, t01.y, n);
             st.edge(i + 3, x.w, y.w, t23.y, t23.x, n);
+            if (INSERT) {
+                uint4 w;
+                w.x = load_slot_word<INSERT>(lp, x.x, y.x, n);
+                w.y = load_slot_word<INSERT>(lp, x.y, y.y, n);
+                w.z = load_slot_word<INSERT>(lp, x.z, y.z, n);
+                w.w = load_slot_word<INSERT>(lp, x.w, y.w, n);
+                reinterpret_cast<uint4*>(lp.slotw)[j] = w;
+            }
         }
     }
     for (int64_t i = 4 * m4 + tid; i < m; i += stride) {
@@ -411,6 +439,7 @@ __global__ void k_load_copy(const int32_t* __restrict__ src, const int32_t* __re
         odst[i] = y;
         ot[i] = ti;
         st.edge(i, x, y, ti, i > 0 ? t[i - 1] : 0, n);
+        if (INSERT) lp.slotw[i] = load_slot_word<INSERT>(lp, x, y, n);
     }
     st.flush(stat);
 }
@@ -458,9 +487,26 @@ static void load_graph(folty_graph* g, const int32_t* src, const int32_t* dst, c
     std::memcpy(g->host_stage + READBACK_MAX, init, sizeof(init));
     g->stage_busy = 1;
     FOLTY_CUDA(cudaMemcpyAsync(stat, g->host_stage + READBACK_MAX, sizeof(init), cudaMemcpyHostToDevice, s));
-    if (fused)
-        FOLTY_LAUNCH(k_load_copy, grid_for(m / 4 + 1, 256, 4), 256, 0, s, (const int32_t*)ksrc,
-                     (const int32_t*)kdst, (const int64_t*)kt, m, g->n, g->in_src, g->in_dst, g->in_t, stat);
+    // the pair table's first try rides along with a fused load (the preprocessing uses
+    // it when its first try has the same size)
+    const bool insert = fused && g->n >= 2 && !pair_table_forced_off();
+    LoadPairs lp{nullptr, 0, nullptr, nullptr};
+    if (insert) {
+        lp.lg = pair_table_lg_first(m);
+        g->pre_lg = lp.lg;
+        g->pre_table = graph_alloc<uint64_t>(g, 1ll << lp.lg, s);
+        g->pre_slotw = graph_alloc<uint32_t>(g, m, s);
+        g->pre_flags = graph_alloc<int>(g, 2, s);
+        FOLTY_CUDA(cudaMemsetAsync(g->pre_table, 0, sizeof(uint64_t) * ((size_t)1 << lp.lg), s));
+        FOLTY_CUDA(cudaMemsetAsync(g->pre_flags, 0, 2 * sizeof(int), s));
+        lp = LoadPairs{g->pre_table, lp.lg, g->pre_slotw, g->pre_flags};
+    }
+    if (fused && insert)
+        FOLTY_LAUNCH(k_load_copy<true>, grid_for(m / 4 + 1, 256, 4), 256, 0, s, (const int32_t*)ksrc,
+                     (const int32_t*)kdst, (const int64_t*)kt, m, g->n, g->in_src, g->in_dst, g->in_t, stat, lp);
+    else if (fused)
+        FOLTY_LAUNCH(k_load_copy<false>, grid_for(m / 4 + 1, 256, 4), 256, 0, s, (const int32_t*)ksrc,
+                     (const int32_t*)kdst, (const int64_t*)kt, m, g->n, g->in_src, g->in_dst, g->in_t, stat, lp);
     else if (m > 0)
         FOLTY_LAUNCH(k_validate, grid_for(m, 256), 256, 0, s, g->in_src, g->in_dst, g->in_t, m, g->n, stat);
     const void* ptrs[5] = {stat, stat + 1, stat + 2, stat + 3, stat + 4};
@@ -522,7 +568,7 @@ folty_status folty_load_temporal_graph(int32_t n, int64_t m, const int32_t* src,
         g = new folty_graph();
         std::memset((void*)g, 0, sizeof(*g));
         g->tag = GRAPH_TAG;
-        g->owned = new std::vector<void*>();
+        g->owned = new std::vector<std::pair<void*, size_t>>();
         if (alloc) {
             g->alloc.a = *alloc;
             g->alloc.user = true;

@@ -7,6 +7,7 @@
 #include <atomic>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "folty.h"
@@ -145,6 +146,12 @@ struct folty_graph {
     int32_t* in_src;
     int32_t* in_dst;
     int64_t* in_t;
+    // the first try of the pair table, filled by a load of device or pinned input
+    // (pairs.cuh; released by preprocess): table of 2^pre_lg slots, slot words, flags
+    uint64_t* pre_table;
+    uint32_t* pre_slotw;
+    int* pre_flags;
+    int pre_lg;
     // ---- preprocessed store (device)
     int64_t m_kept;
     int32_t* perm;    // [m_kept] input index of each sorted temporal edge
@@ -179,7 +186,7 @@ struct folty_graph {
     int32_t* pair_stage;  // kernel-written pair output (device address of the same memory)
     int stage_busy;       // an asynchronous copy into or out of host_stage may be pending
     int* dev_err;         // device error word: a bounded wait in a kernel ran out
-    std::vector<void*>* owned;  // device buffers owned by the graph
+    std::vector<std::pair<void*, size_t>>* owned;  // device buffers owned by the graph
 };
 
 namespace folty {
@@ -190,7 +197,7 @@ T* graph_alloc(folty_graph* g, int64_t count, cudaStream_t s) {
     size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
     void* p = g->alloc.get(bytes, s);
     if (!p) fail(FOLTY_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
-    g->owned->push_back(p);
+    g->owned->push_back({p, bytes});
     g->info.device_bytes += (int64_t)bytes;
     return static_cast<T*>(p);
 }

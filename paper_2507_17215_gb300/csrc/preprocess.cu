@@ -14,6 +14,7 @@
 #include <cstring>
 
 #include "internal.cuh"
+#include "pairs.cuh"
 
 #include <cooperative_groups.h>
 namespace cg = cooperative_groups;
@@ -148,35 +149,7 @@ __global__ void k_pair_ends(const uint64_t* __restrict__ key, const int32_t* __r
 // rank); they are sorted on their own (S entries), and each edge looks its id up by the
 // table slot it kept from the insert.
 
-constexpr int PAIR_MAX_PROBE = 4096;              // longer probe sequences abandon the table
 constexpr int PAIR_COMPACT_ITEMS = 16;            // table slots per thread and step of the compaction
-constexpr uint64_t PAIR_HASH_MUL = 0x9E3779B97F4A7C15ull;  // 2^64 / golden ratio (Fibonacci hashing)
-
-__device__ __forceinline__ uint64_t pair_rank_of(int32_t x, int32_t y, int32_t n) {
-    const uint64_t a = (uint64_t)min(x, y), b = (uint64_t)max(x, y);
-    return a * (2 * (uint64_t)n - a - 1) / 2 + (b - a - 1);
-}
-
-// Slot holding table value key (rank + 1), placing it in the first empty slot of its probe
-// sequence when absent; -1 after PAIR_MAX_PROBE steps.
-__device__ __forceinline__ int64_t pair_slot(uint64_t* table, int lg, uint64_t key) {
-    const uint64_t mask = (1ull << lg) - 1;
-    uint64_t h = (key * PAIR_HASH_MUL) >> (64 - lg);
-    for (int pr = 0; pr < PAIR_MAX_PROBE; pr++) {
-        const uint64_t cur = __ldcg(&table[h]);
-        if (cur == key) return (int64_t)h;
-        if (cur == 0) {
-            const unsigned long long old =
-                atomicCAS((unsigned long long*)&table[h], 0ull, (unsigned long long)key);
-            if (old == 0 || old == key) return (int64_t)h;
-        }
-        h = (h + 1) & mask;
-    }
-    return -1;
-}
-
-constexpr uint32_t PAIR_LOOP = 0x7fffffffu;  // slot word of a self-loop
-constexpr uint32_t PAIR_DIR = 0x80000000u;   // direction bit of a slot word (tables hold < 2^31 slots)
 
 // Every non-loop edge's pair goes into the table (value rank + 1, 0 = empty), and edge i
 // keeps its slot and direction in slotw[i] (PAIR_LOOP for a self-loop). A probe sequence
@@ -184,16 +157,8 @@ constexpr uint32_t PAIR_DIR = 0x80000000u;   // direction bit of a slot word (ta
 __global__ void k_pair_insert(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m, int32_t n,
                               uint64_t* __restrict__ table, int lg, uint32_t* __restrict__ slotw,
                               int* __restrict__ over) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t x = src[i], y = dst[i];
-        uint32_t w = PAIR_LOOP;
-        if (x != y) {
-            const int64_t sl = pair_slot(table, lg, pair_rank_of(x, y, n) + 1);
-            if (sl < 0) atomicExch(over, 1);
-            else w = (uint32_t)sl | (x > y ? PAIR_DIR : 0u);
-        }
-        __stcs(slotw + i, w);
-    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        __stcs(slotw + i, pair_slot_word(table, lg, src[i], dst[i], n, over));
 }
 
 // The occupied slots as (rank, slot) lists, in no particular order: each block takes
@@ -2202,28 +2167,34 @@ static bool pair_ids_sort(folty_graph* g, Scratch& sc, const uint32_t* order, ui
     const int T = 256;
     const int64_t m = g->m, mk = g->m_kept;
     const int32_t n = g->n;
-    const char* env = std::getenv("FOLTY_PAIR_SORT");
-    if (env && std::strcmp(env, "keys") == 0) return false;
+    if (pair_table_forced_off()) return false;
     if (mk == 0 || n < 2) return false;
     const int ib = bit_length((uint64_t)(m - 1));
-    // at least 2m slots, up to 2^23; a first try with at most 2^21 slots (16 MB, which
-    // stays in L2) serves up to a million distinct pairs
-    const int lg_max = std::min(23, std::max(10, bit_length((uint64_t)(2 * m - 1))));
-    int lg = std::min(21, lg_max);
+    const int lg_max = pair_table_lg_max(m);
+    int lg = pair_table_lg_first(m);
     int64_t tb = 0, S64 = 0;
     int cap = 0;
     uint64_t* table = nullptr;
     uint64_t* urank = nullptr;
     uint32_t* uslot = nullptr;
-    int* flags = sc.get<int>(2);  // [0] a probe ran out, [1] distinct pairs
-    uint32_t* slotw = sc.get<uint32_t>(m);
+    // the first try's table, slot words and flags ([0] a probe ran out, [1] distinct
+    // pairs) may already be filled by the load
+    const bool pre = g->pre_table != nullptr && g->pre_lg == lg;
+    int* flags = pre ? g->pre_flags : sc.get<int>(2);
+    uint32_t* slotw = pre ? g->pre_slotw : sc.get<uint32_t>(m);
+    bool first = true;
     while (true) {
         tb = 1ll << lg;
         cap = (int)(tb / 2);  // load factor at most 1/2
-        table = sc.get<uint64_t>(tb);
-        FOLTY_CUDA(cudaMemsetAsync(table, 0, sizeof(uint64_t) * (size_t)tb, s));
-        FOLTY_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), s));
-        FOLTY_LAUNCH(k_pair_insert, grid_for(m, T), T, 0, s, g->in_src, g->in_dst, m, n, table, lg, slotw, flags);
+        if (first && pre) {
+            table = g->pre_table;
+        } else {
+            table = sc.get<uint64_t>(tb);
+            FOLTY_CUDA(cudaMemsetAsync(table, 0, sizeof(uint64_t) * (size_t)tb, s));
+            FOLTY_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), s));
+            FOLTY_LAUNCH(k_pair_insert, grid_for(m, T), T, 0, s, g->in_src, g->in_dst, m, n, table, lg, slotw, flags);
+        }
+        first = false;
         urank = sc.get<uint64_t>(cap);
         uslot = sc.get<uint32_t>(cap);
         FOLTY_LAUNCH(k_pair_table_compact, grid_for(tb, (int64_t)T * PAIR_COMPACT_ITEMS), T, 0, s, table, tb, urank, uslot,
@@ -2523,6 +2494,13 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     graph_release(g, g->in_t, s);
     g->in_src = g->in_dst = nullptr;
     g->in_t = nullptr;
+    // and neither is the pair table the load filled
+    graph_release(g, g->pre_table, s);
+    graph_release(g, g->pre_slotw, s);
+    graph_release(g, g->pre_flags, s);
+    g->pre_table = nullptr;
+    g->pre_slotw = nullptr;
+    g->pre_flags = nullptr;
     g->common = graph_alloc<int32_t>(g, S, s);
     FOLTY_CUDA(cudaMemsetAsync(g->common, 0, sizeof(int32_t) * ((size_t)S > 0 ? (size_t)S : 1), s));
     int32_t* tcnt = sc.get<int32_t>((int64_t)S + 1);

@@ -551,11 +551,19 @@ def _many_pairs_graph(seed=5):
 def test_pair_table_past_its_first_size(F):
     """More distinct pairs than the pair table's first size holds: the library retries
     with a larger table (or sorts full keys); results are the oracle's either way."""
+    import torch
     g = _many_pairs_graph()
     qs = [W.Query(d, 1, 2, W.Q_FORALL_T, dr, W.U_HEAD, True) for d in (50, 2000) for dr in (W.DIR_OUT, W.DIR_EITHER)]
     qs.append(W.Query(500, 1, 10, W.Q_FORALL_T, W.DIR_IN, W.U_COMMON, True))
     info = _check_graph(F, g, qs)
     assert info["static_edges"] > (1 << 20)
+    # device-resident input: the load fills the table's first try, which overflows too
+    want, _ = _lib_results(F, g, qs)
+    with F.TemporalGraph(g.n, *[torch.from_numpy(a).cuda() for a in (g.src, g.dst, g.t)]) as G:
+        got, dinfo = [G.query(q) for q in qs], G.info()
+    assert dinfo == info
+    for q, a, b in zip(qs, want, got):
+        _assert_same(b, a, what=str(q))
 
 
 def _clique_graph(k=20000, size=4, seed=6):
