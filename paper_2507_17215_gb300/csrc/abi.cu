@@ -489,7 +489,7 @@ static void load_graph(folty_graph* g, const int32_t* src, const int32_t* dst, c
     FOLTY_CUDA(cudaMemcpyAsync(stat, g->host_stage + READBACK_MAX, sizeof(init), cudaMemcpyHostToDevice, s));
     // the pair table's first try rides along with a fused load (the preprocessing uses
     // it when its first try has the same size)
-    const bool insert = fused && g->n >= 2 && !pair_table_forced_off();
+    bool insert = fused && g->n >= 2 && !pair_table_forced_off();
     LoadPairs lp{nullptr, 0, nullptr, nullptr};
     if (insert) {
         lp.lg = pair_table_lg_first(m);
@@ -497,9 +497,19 @@ static void load_graph(folty_graph* g, const int32_t* src, const int32_t* dst, c
         g->pre_table = graph_alloc<uint64_t>(g, 1ll << lp.lg, s);
         g->pre_slotw = graph_alloc<uint32_t>(g, m, s);
         g->pre_flags = graph_alloc<int>(g, 2, s);
-        FOLTY_CUDA(cudaMemsetAsync(g->pre_table, 0, sizeof(uint64_t) * ((size_t)1 << lp.lg), s));
-        FOLTY_CUDA(cudaMemsetAsync(g->pre_flags, 0, 2 * sizeof(int), s));
-        lp = LoadPairs{g->pre_table, lp.lg, g->pre_slotw, g->pre_flags};
+        if (!a16(g->pre_slotw)) {  // a caller's allocator may not align it for 16-byte stores
+            graph_release(g, g->pre_table, s);
+            graph_release(g, g->pre_slotw, s);
+            graph_release(g, g->pre_flags, s);
+            g->pre_table = nullptr;
+            g->pre_slotw = nullptr;
+            g->pre_flags = nullptr;
+            insert = false;
+        } else {
+            FOLTY_CUDA(cudaMemsetAsync(g->pre_table, 0, sizeof(uint64_t) * ((size_t)1 << lp.lg), s));
+            FOLTY_CUDA(cudaMemsetAsync(g->pre_flags, 0, 2 * sizeof(int), s));
+            lp = LoadPairs{g->pre_table, lp.lg, g->pre_slotw, g->pre_flags};
+        }
     }
     if (fused && insert)
         FOLTY_LAUNCH(k_load_copy<true>, grid_for(m / 4 + 1, 256, 4), 256, 0, s, (const int32_t*)ksrc,
