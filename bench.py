@@ -88,7 +88,9 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms while running; start()
+    returns once the first sample is in, mark() opens the timed region, and stop() summarises
+    the samples taken after mark() (the last earlier one when none came after it)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -99,18 +101,25 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.thread = None
+        self.first = 0
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        t_end = time.time() + 5.0
+        while not self.lines and time.time() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
+
+    def mark(self):
+        self.first = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -128,7 +137,8 @@ class ClockSampler:
             self.thread.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines[self.first:] or self.lines[max(0, self.first - 1):self.first]
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -327,7 +337,7 @@ def measure_batch(F, g, d_src, d_dst, d_t, sh, nq, stream, reps=3):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="folty", choices=["folty", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -396,12 +406,13 @@ def main():
 
     # ---- device-resident timed region
     clocks = ClockSampler(local)
+    clocks.start()
     barrier()
     torch.cuda.synchronize()
-    clocks.start()
     launches0 = F.folty_kernel_launches()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    clocks.mark()
     ev0.record(stream)
     for _ in range(args.steps):
         res = step(d_src, d_dst, d_t)
