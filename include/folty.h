@@ -295,9 +295,14 @@ void folty_server_destroy(folty_server *sv);
  *   - All calls share the array, which keeps the last call's contents; each call clears
  *     the part it uses before probing. Calls whose work overlaps on the GPU (other
  *     streams, other threads) race on it and give wrong counts: serialise them.
+ *   - Call it with the graph's device current (the device that was current when the
+ *     graph was loaded); edge_count must be memory of that device (cudaMalloc, a pool,
+ *     PyTorch's allocator) holding at least m int32. The library checks the device and
+ *     the kind of memory, not the length.
  *   - Stream-ordered on "stream"; does not synchronise it.
- * Errors: FOLTY_EINVAL (NULL, delta outside [0, 2^62), unknown dir, graph too large),
- * FOLTY_ESTATE (not preprocessed), FOLTY_ECUDA. */
+ * Errors: FOLTY_EINVAL (NULL, delta outside [0, 2^62), unknown dir, graph too large,
+ * another device current, edge_count not memory of the graph's device), FOLTY_ESTATE
+ * (not preprocessed), FOLTY_ECUDA. */
 #define FOLTY_NOALLOC_MAX_EDGES (1 << 20)
 folty_status folty_edge_counts_noalloc(folty_graph *g, int64_t delta, int32_t dir,
                                        int32_t *edge_count, void *stream);

@@ -347,7 +347,23 @@ NOALLOC_MAX_EDGES = 1 << 20  # FOLTY_NOALLOC_MAX_EDGES
 
 def folty_edge_counts_noalloc(g: int, delta: int, dir: int, edge_count, stream: Optional[int] = None) -> None:
     """Per-edge counts of one (delta, dir) into a caller-owned device int32 tensor of
-    length m (input order), with no allocation inside the library; see folty.h."""
+    length m (input order), with no allocation inside the library; see folty.h.
+
+    edge_count must be a contiguous int32 CUDA tensor of at least m elements on the
+    current device (the graph's); anything else is refused before the call, since the
+    library's kernels write m int32 through the pointer."""
+    import torch
+    if not isinstance(edge_count, torch.Tensor) or not edge_count.is_cuda:
+        raise TypeError("edge_count must be a CUDA torch tensor")
+    if edge_count.dtype != torch.int32:
+        raise TypeError(f"edge_count must be int32, not {edge_count.dtype}")
+    if not edge_count.is_contiguous():
+        raise ValueError("edge_count must be contiguous")
+    if edge_count.device.index != torch.cuda.current_device():
+        raise ValueError("edge_count must live on the current device (the graph's)")
+    m = folty_graph_get_info(g)["m"]
+    if edge_count.numel() < m:
+        raise ValueError(f"edge_count holds {edge_count.numel()} elements, the graph has {m} edges")
     _check(lib.folty_edge_counts_noalloc(g, int(delta), int(dir), _ptr(edge_count),
                                          current_stream() if stream is None else stream))
 

@@ -707,6 +707,23 @@ folty_status folty_edge_counts_noalloc(folty_graph* g, int64_t delta, int32_t di
         if (delta < 0 || delta >= (1ll << 62)) fail(FOLTY_EINVAL, "delta outside [0, 2^62)");
         if (dir < 0 || dir > FOLTY_DIR_EITHER) fail(FOLTY_EINVAL, "unknown direction variant");
         if (g->state != 1) fail(FOLTY_ESTATE, "graph not preprocessed");
+        // the kernels run on the current device and read the graph's arrays: that must be
+        // the graph's device, and edge_count must be memory of it (the kernels write m
+        // int32 through it; host memory or another device's memory is refused here)
+        int dev = -1;
+        FOLTY_CUDA(cudaGetDevice(&dev));
+        if (dev != g->device)
+            fail(FOLTY_EINVAL, "the current device (" + std::to_string(dev) + ") is not the graph's device (" +
+                                   std::to_string(g->device) + ")");
+        if (g->m > 0) {
+            cudaPointerAttributes pa{};
+            if (cudaPointerGetAttributes(&pa, edge_count) != cudaSuccess) {
+                cudaGetLastError();
+                fail(FOLTY_EINVAL, "edge_count is not device memory");
+            }
+            if (pa.type != cudaMemoryTypeDevice || pa.device != dev)
+                fail(FOLTY_EINVAL, "edge_count must be device memory of the graph's device");
+        }
         edge_counts_noalloc(g, delta, dir, edge_count, (cudaStream_t)stream);
     });
 }

@@ -186,3 +186,17 @@ def complete_graph(k: int, t: int = 0) -> W.TemporalGraph:
     m = len(src)
     return W.TemporalGraph(k, np.array(src, np.int32), np.array(dst, np.int32),
                            np.full(m, t, np.int64))
+
+
+def wide_time_span_graph(seed=13, n=8, m=200):
+    """Timestamps spread over [0, 2^40]: 5 clusters 2^38 s apart, each edge placed
+    uniformly within 2^34 s of its cluster's start. The span is far above 2^32, so the
+    library keeps 64-bit timestamps; windows below and above 2^32 both find triangles
+    inside a cluster, and only windows of 2^38 or more join clusters."""
+    rng = np.random.default_rng(seed)
+    g = W.random_small_graph(rng, n, m, 0, self_loops=True)
+    t = rng.integers(0, 5, m).astype(np.int64) * (1 << 38) + rng.integers(0, 1 << 34, m).astype(np.int64)
+    return W.TemporalGraph(n, g.src, g.dst, t)
+
+
+WIDE_DELTAS = (0, 1 << 31, (1 << 32) - 1, (1 << 32) + 5, 1 << 33, 1 << 38, (1 << 62) - 1)

@@ -7,7 +7,7 @@ import oracle
 import workloads as W
 import dataclasses
 
-from _support import golden_files, pairs_of, parse_fixture, vertices_of
+from _support import WIDE_DELTAS, golden_files, pairs_of, parse_fixture, vertices_of, wide_time_span_graph
 
 pytestmark = pytest.mark.gpu
 
@@ -206,6 +206,32 @@ def test_edge_cases(F, name):
     g = _edge_case_graphs()[name]
     deltas = (0, 5, (1 << 62) - 1)
     _check_graph(F, g, _full_mix(deltas))
+
+
+
+
+def test_int64_timestamp_store(F):
+    """The 64-bit timestamp store (time span at least 2^32 - 1), single queries and the
+    batch, against the oracle, with windows below and above 2^32."""
+    for seed in (13, 14, 15):
+        g = wide_time_span_graph(seed)
+        assert int(g.t.max() - g.t.min()) >= (1 << 32)
+        qs = _full_mix(WIDE_DELTAS)
+        res, _ = _lib_results(F, g, qs)
+        bat, _ = _lib_results(F, g, qs, batch=True)
+        with oracle.OracleGraph.of(g) as og:
+            hits = 0
+            for q, r, rb in zip(qs, res, bat):
+                want = og.query(q)
+                _assert_same(r, want, str(q))
+                _assert_same(rb, want, str(q))
+                hits += int(want["edge_count"].sum())
+        assert hits > 0
+        # windows on either side of 2^32 both find triangles, and not the same ones
+        with oracle.OracleGraph.of(g) as og:
+            below, _ = og.counts(1 << 31, W.DIR_EITHER)
+            above, _ = og.counts(1 << 33, W.DIR_EITHER)
+        assert below.sum() > 0 and (above > below).any()
 
 
 def _core_numbers(n, src, dst):

@@ -87,3 +87,42 @@ def test_noalloc_rejects_graphs_above_its_limit(F):
             F.folty_edge_counts_noalloc(G.handle, 3600, W.DIR_OUT, out)
         assert ei.value.status == F.FOLTY_EINVAL
         assert "at most" in str(ei.value)
+
+
+def test_noalloc_on_the_64_bit_timestamp_store(F):
+    """A time span past 2^32 keeps 64-bit timestamps; windows below and above 2^32."""
+    import torch
+    from _support import WIDE_DELTAS, wide_time_span_graph
+    g = wide_time_span_graph(14)
+    with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
+        for delta in WIDE_DELTAS:
+            for dr in (W.DIR_OUT, W.DIR_IN, W.DIR_EITHER):
+                out = torch.full((g.m,), -7, dtype=torch.int32, device="cuda")
+                F.folty_edge_counts_noalloc(G.handle, delta, dr, out)
+                want = G.query(W.Query(delta, 1, 2, W.Q_FORALL_T, dr, W.U_HEAD, True))["edge_count"]
+                np.testing.assert_array_equal(out.cpu().numpy(), want)
+
+
+def test_noalloc_refuses_buffers_it_cannot_write(F):
+    """Host arrays, the wrong dtype or a short buffer are refused by the binding; host
+    memory handed to the C entry point directly is refused by the library (FOLTY_EINVAL)
+    before any kernel runs."""
+    import torch
+    g = W.config_graph(1)
+    with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
+        with pytest.raises(TypeError):
+            F.folty_edge_counts_noalloc(G.handle, 3600, W.DIR_OUT, np.zeros(g.m, np.int32))
+        with pytest.raises(TypeError):
+            F.folty_edge_counts_noalloc(G.handle, 3600, W.DIR_OUT, torch.zeros(g.m, dtype=torch.int64, device="cuda"))
+        with pytest.raises(ValueError):
+            F.folty_edge_counts_noalloc(G.handle, 3600, W.DIR_OUT, torch.zeros(g.m - 1, dtype=torch.int32, device="cuda"))
+        for host in (np.zeros(g.m, np.int32), torch.zeros(g.m, dtype=torch.int32).pin_memory()):
+            ptr = host.ctypes.data if isinstance(host, np.ndarray) else host.data_ptr()
+            st = F.lib.folty_edge_counts_noalloc(G.handle, 3600, W.DIR_OUT, ptr, F.current_stream())
+            assert st == F.FOLTY_EINVAL, F.folty_last_error()
+            assert "device memory" in F.folty_last_error()
+        # the graph still answers afterwards
+        out = torch.zeros(g.m, dtype=torch.int32, device="cuda")
+        F.folty_edge_counts_noalloc(G.handle, 10 ** 6, W.DIR_OUT, out)
+        want = G.query(W.Query(10 ** 6, 1, 2, W.Q_FORALL_T, W.DIR_OUT, W.U_HEAD, True))["edge_count"]
+        np.testing.assert_array_equal(out.cpu().numpy(), want)
