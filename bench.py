@@ -1,19 +1,28 @@
 #!/usr/bin/env python
 """Benchmark of the temporal-graph triadic query path on GB300.
 
-Workload (default): the medium synthetic temporal graph -- 1,000,000 vertices,
-20,000,000 temporal edges, Chung-Lu exponent 2.1, Zipf(1.5) multiplicities capped at
-1000, bursty lognormal timestamps over one year -- and its three queries
-exists u exists v forall_{1/2} w in N(u) with delta in {600, 3600, 86400} s ("out"
-motif). One step = the whole path on one batch of input: load (copy + validation),
-preprocessing (sort, static graph, peeling, orientation, triangle listing) and the
-three queries (probes, counts, threshold, solution pairs back on the host).
+Workload (default, "paper"): the paper-scale synthetic temporal graph -- 5,000,000
+vertices, 70,000,000 temporal edges, Chung-Lu exponent 2.0 plus 50 planted
+300-vertex communities (intra-pair probability 0.7), Zipf(1.3) multiplicities (capped at
+10,000, 16 inside the communities), bursty lognormal timestamps over one year -- and its
+query exists u exists v forall_{3/10} w in N(u) with delta = 3600 s ("out" motif).
+"--workload medium" runs the medium graph (1,000,000 vertices, 20,000,000 edges) and its
+three queries (delta in {600, 3600, 86400} s, rho = 1/2) instead.
 
-value  = (queries x temporal edges) processed per second over all ranks, inputs
-         resident in HBM when the timed region starts (device CUDA-event time);
-e2e    = the same through the C ABI from pinned host buffers: host->device copy of the
-         edge list and device->host copy of the results inside every step;
-roofline = the window-probe kernel, model bytes per launch / its event-timed duration.
+One step = the whole path on one batch of input: load (copy + validation),
+preprocessing (sort, static graph, peeling, orientation, triangle listing, role summary)
+and the workload's queries (selection, probes, counts, threshold, solution pairs back on
+the host).
+
+value    = (queries x temporal edges) per second of whole steps, over all ranks, inputs
+           resident in HBM when the timed region starts (device CUDA-event time);
+query    = the per-query metric m / t_query: device time of folty_query alone on a
+           preprocessed graph (preprocessing reported beside it as preprocess_ms);
+e2e      = the same steps through the C ABI from pinned host buffers: host->device copy
+           of the edge list and device->host copy of the results inside every step;
+roofline = the step's dominant stage (largest device time per step): model bytes per
+           span over its CUDA-event duration against the measured HBM peak;
+query_roofline = the same for the dominant stage of the query path.
 
 Multi-GPU: every rank runs its own replica of the workload (the query path has no
 exchange step); value sums the ranks' work over the slowest rank's time.
@@ -42,40 +51,54 @@ import workloads as W  # noqa: E402
 
 METRIC = "temporal edges/s per FOL triadic query on 1xGB300"
 UNIT = "temporal edges/s"
-WORKLOAD = ("medium synthetic temporal graph: n=1,000,000, m=20,000,000, Chung-Lu gamma=2.1, "
-            "Zipf(1.5) multiplicity capped at 1000, bursty lognormal(6,2) times over 1 year; "
-            "3 queries exists-exists-forall_{1/2} over N(u), delta in {600,3600,86400} s")
-
-
-STAGE_KERNELS = {
-    "probe": "window-probe stage: k_live_tri, scans, k_live_compact, k_live_tiles, k_probe_live",
-    "sort": "radix sort spans: k_rs_hist_all + k_rs_bases (all digit histograms), or one k_rs_onesweep digit pass",
-    "peel": "k_peel (cooperative) + k_tail_* + k_peel_tail",
-    "threshold": "k_threshold",
+WORKLOADS = {
+    "paper": (3, "paper-scale synthetic temporal graph: n=5,000,000, m=70,000,000, Chung-Lu gamma=2.0 plus 50 "
+                 "planted 300-vertex communities (p=0.7), Zipf(1.3) multiplicity capped at 10,000 (16 inside "
+                 "the communities), bursty lognormal(6,2) times over 1 year; query exists-exists-forall_{3/10} "
+                 "over N(u), delta=3600 s", "3/10"),
+    "medium": (2, "medium synthetic temporal graph: n=1,000,000, m=20,000,000, Chung-Lu gamma=2.1, "
+                  "Zipf(1.5) multiplicity capped at 1000, bursty lognormal(6,2) times over 1 year; "
+                  "3 queries exists-exists-forall_{1/2} over N(u), delta in {600,3600,86400} s", "1/2"),
 }
 
+STAGE_KERNELS = {
+    "probe": "k_probe_live (persistent window probes over the kept roles)",
+    "select": "k_live_select (liveness, scan and compaction of the kept triangles)",
+    "sort": "radix sort spans: k_rs_hist_all + k_rs_bases (all digit histograms), or one k_rs_onesweep digit pass",
+    "peel": "k_peel (cooperative) + k_tail_* + k_peel_tail + k_solo_* + k_peel_solo",
+    "threshold": "k_threshold",
+    "triangles": "k_tri_count, k_tri_write",
+    "roles": "k_run_ends + k_role_summary",
+    "batch": "k_batch_threshold",
+}
+STAGE_SOURCES = {"probe": ("live.cu", "probe.cuh"), "select": ("live.cu", "scan.cuh"), "sort": ("prims.cu",),
+                 "peel": ("preprocess.cu",), "threshold": ("query.cu",), "triangles": ("preprocess.cu",),
+                 "roles": ("live.cu",), "batch": ("batch.cu",)}
+QUERY_STAGES = ("select", "probe", "threshold")
 
-def stage_traffic(stage, model_bytes):
-    """DRAM bytes per span of a stage from the committed ncu summary, when it was taken
-    on the current sources (profiles/traffic_medium_workload.md lists 'traffic <stage>
-    <bytes> <sha256 of the stage's sources>'); None otherwise."""
+
+def stage_traffic(stage, workload):
+    """DRAM bytes per span of a stage from the committed ncu summary of the workload, when
+    it was taken on the current sources (profiles/traffic_<workload>_workload.md lists
+    'traffic <stage> <bytes> <sha256 of the stage's sources>'); None otherwise."""
     import hashlib
     import re
-    path = os.path.join(ROOT, "profiles", "traffic_medium_workload.md")
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}_workload.md")
     if not os.path.exists(path):
         return None
     for m in re.finditer(r"^traffic (\w+) (\d+) ([0-9a-f]{64})$", open(path).read(), re.M):
         if m.group(1) != stage:
             continue
-        h = hashlib.sha256()
-        for f in STAGE_SOURCES.get(stage, ()):
-            h.update(open(os.path.join(ROOT, "paper_2507_17215_gb300", "csrc", f), "rb").read())
-        return int(m.group(2)) if h.hexdigest() == m.group(3) else None
+        return int(m.group(2)) if source_hash(stage) == m.group(3) else None
     return None
 
 
-STAGE_SOURCES = {"probe": ("live.cu", "probe.cuh"), "sort": ("prims.cu",),
-                 "peel": ("preprocess.cu",), "threshold": ("query.cu",)}
+def source_hash(stage):
+    import hashlib
+    h = hashlib.sha256()
+    for f in STAGE_SOURCES.get(stage, ()):
+        h.update(open(os.path.join(ROOT, "paper_2507_17215_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
 
 
 def _peaks():
@@ -157,54 +180,65 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- CPU oracle
 
-def oracle_sample_time(g, queries, budget_s: float, seed: int = 0):
-    """Oracle on a bounded sample: full build of its edge lists and neighbourhoods, then
-    the per-edge counts of uniformly drawn temporal edges for every query. Returns the
-    extrapolated seconds for the whole step and a description."""
-    import oracle
-    t0 = time.perf_counter()
-    og = oracle.OracleGraph.of(g)
-    build_s = time.perf_counter() - t0
-    rng = np.random.default_rng(seed)
-    size = 4000
-    t0 = time.perf_counter()
-    for q in queries:
-        og.counts(q.delta, q.dir, idx=rng.integers(0, g.m, size))
-    calib = time.perf_counter() - t0
-    per = calib / (size * len(queries))
-    size = int(min(g.m, max(size, budget_s / max(per, 1e-9) / len(queries))))
-    t0 = time.perf_counter()
-    for q in queries:
-        og.counts(q.delta, q.dir, idx=rng.integers(0, g.m, size))
-    eval_s = time.perf_counter() - t0
-    og.close()
-    per = eval_s / (size * len(queries))
-    step_s = build_s + per * g.m * len(queries)
-    sample = (f"oracle build on all {g.m} edges ({build_s:.1f} s) + per-edge counts of "
-              f"{size} uniformly drawn edges x {len(queries)} queries ({eval_s:.1f} s), "
-              f"extrapolated to all edges")
-    return step_s, sample, oracle.threads()
+class OracleArm:
+    """The CPU oracle on the host cores: its edge lists and neighbourhoods are built once
+    for the whole graph (timed), then every sample draws temporal edges uniformly and
+    computes their counts for each query; a step's time is extrapolated as the build plus
+    the per-edge time times all edges and queries."""
+
+    def __init__(self, g):
+        import oracle
+        self.oracle = oracle
+        self.g = g
+        t0 = time.perf_counter()
+        self.og = oracle.OracleGraph.of(g)
+        self.build_s = time.perf_counter() - t0
+        self.cores = oracle.threads()
+
+    def step_seconds(self, queries, budget_s: float, seed: int = 0):
+        g = self.g
+        rng = np.random.default_rng(seed)
+        size = 4000
+        t0 = time.perf_counter()
+        for q in queries:
+            self.og.counts(q.delta, q.dir, idx=rng.integers(0, g.m, size))
+        per = (time.perf_counter() - t0) / (size * len(queries))
+        size = int(min(g.m, max(size, budget_s / max(per, 1e-9) / len(queries))))
+        t0 = time.perf_counter()
+        for q in queries:
+            self.og.counts(q.delta, q.dir, idx=rng.integers(0, g.m, size))
+        eval_s = time.perf_counter() - t0
+        per = eval_s / (size * len(queries))
+        step_s = self.build_s + per * g.m * len(queries)
+        sample = (f"oracle build on all {g.m} edges ({self.build_s:.1f} s, once) + per-edge counts of "
+                  f"{size} uniformly drawn edges x {len(queries)} queries ({eval_s:.1f} s), extrapolated "
+                  f"to all edges")
+        return step_s, sample
+
+    def close(self):
+        self.og.close()
 
 
-def run_reference(args, g, queries):
+def run_reference(args, g, queries, workload):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    arm = OracleArm(g)
     vals = []
     sample = ""
-    cores = 1
     for i in range(args.warmup + args.steps):
-        step_s, sample, cores = oracle_sample_time(g, queries, budget_s=args.ref_budget, seed=i)
+        step_s, sample = arm.step_seconds(queries, budget_s=args.ref_budget, seed=i)
         if i >= args.warmup:
             vals.append(step_s)
+    arm.close()
     mean_s = sum(vals) / len(vals)
     value = len(queries) * g.m / mean_s
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "queries": len(queries), "m": g.m, "n": g.n},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "config": {"workload": WORKLOADS[workload][1], "queries": len(queries), "m": g.m, "n": g.n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": arm.cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -296,16 +330,18 @@ def measure_serving(F, seconds, rate=200.0, sizes=SERVE_SIZES, seed=5):
             "peak_memory_bytes": stats["peak_memory_bytes"]}
 
 
-def measure_batch(F, g, d_src, d_dst, d_t, sh, nq, stream, reps=3):
+def measure_batch(F, g, sh, nq, stream, reps=3):
     """nq mixed queries (delta log-uniform on [60 s, 7 d], rho = k/10, quantifier and
     direction uniform) on the preprocessed graph: folty_query_batch against nq
     back-to-back folty_query calls, results compared pair list by pair list."""
     import torch
     rng = np.random.default_rng(4)
     qs = W.random_query_mix(nq, rng)
-    h = F.folty_load_temporal_graph(g.n, d_src, d_dst, d_t, stream=sh)
+    d = [torch.from_numpy(a).cuda() for a in (g.src, g.dst, g.t)]
+    h = F.folty_load_temporal_graph(g.n, *d, stream=sh)
     try:
         F.folty_preprocess(h, sh)
+        del d
         F.folty_query_batch(h, qs, sh)  # warm-up (allocator, module load)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         batch_ms = []
@@ -316,6 +352,10 @@ def measure_batch(F, g, d_src, d_dst, d_t, sh, nq, stream, reps=3):
             ev[1].record(stream)
             torch.cuda.synchronize()
             batch_ms.append(ev[0].elapsed_time(ev[1]))
+        F.folty_profile_enable(True)
+        F.folty_query_batch(h, qs, sh)
+        prof = F.folty_profile_read()
+        F.folty_profile_enable(False)
         torch.cuda.synchronize()
         ev[0].record(stream)
         res_s = [F.folty_query(h, q, sh) for q in qs]
@@ -327,37 +367,110 @@ def measure_batch(F, g, d_src, d_dst, d_t, sh, nq, stream, reps=3):
     same = all(a["n_cert_edges"] == b["n_cert_edges"] and all(np.array_equal(a[k], b[k]) for k in
                ("u", "v", "count", "ncert")) for a, b in zip(res_b, res_s))
     bm = float(np.median(batch_ms))
+    stages = {k: {"ms": v["ms"], "spans": v["launches"], "model_bytes": v["bytes"]}
+              for k, v in prof.items() if v["launches"]}
     return {"queries": nq, "workload": "medium graph, mixed queries (delta log-uniform 60 s..7 d, "
             "rho k/10, exists/forall, out/in/either, universe N(u))",
             "batch_ms": bm, "sequential_ms": seq_ms, "speedup": seq_ms / bm,
             "edges_per_s": nq * g.m / (bm / 1e3), "results_equal": bool(same),
-            "solution_pairs_total": int(sum(len(r["u"]) for r in res_b))}
+            "solution_pairs_total": int(sum(len(r["u"]) for r in res_b)), "stages": stages}
+
+
+def stage_table(prof, steps, peak):
+    out = {}
+    for name, p in prof.items():
+        if p["launches"] == 0 or p["ms"] <= 0:
+            continue
+        gbs = p["bytes"] / (p["ms"] / 1e3) / 1e9
+        out[name] = {"ms_per_step": p["ms"] / steps, "spans_per_step": p["launches"] / steps,
+                     "model_bytes_per_span": p["bytes"] / p["launches"],
+                     "ms_per_span": p["ms"] / p["launches"], "achieved_gbs": gbs, "frac": gbs / peak}
+    return out
+
+
+def roofline_of(prof, stage, peak, peak_kind, workload):
+    d = prof[stage]
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": stage_traffic(stage, workload), "stage": stage, "kernel": STAGE_KERNELS[stage],
+            "peak_kind": f"{peak_kind} hbm_gbs (of {peak_kind})",
+            "model_bytes_per_launch": d["bytes"] / d["launches"], "launch_ms": d["ms"] / d["launches"]}
+
+
+def time_queries(F, g, d_src, d_dst, d_t, sh, stream, queries, reps=10):
+    """Load and preprocessing alone (events around each call, median of 3), then every
+    query of the workload alone on the preprocessed graph (median of reps), and what each
+    query's probe pass keeps."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    load_ms, pre_ms = [], []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        h = F.folty_load_temporal_graph(g.n, d_src, d_dst, d_t, stream=sh)
+        ev[1].record(stream)
+        F.folty_preprocess(h, sh)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        load_ms.append(ev[0].elapsed_time(ev[1]))
+        pre_ms.append(ev[1].elapsed_time(ev[2]))
+        F.folty_free(h)
+    h = F.folty_load_temporal_graph(g.n, d_src, d_dst, d_t, stream=sh)
+    F.folty_preprocess(h, sh)
+    info = F.folty_graph_get_info(h)
+    q_ms = []
+    kept = []
+    for q in queries:
+        F.folty_query(h, q, sh)
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            F.folty_query(h, q, sh)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ts.append(ev[0].elapsed_time(ev[1]))
+        q_ms.append(float(np.median(ts)))
+        st = F.folty_graph_probe_stats(h, q.delta, q.dir, sh)
+        kept.append({"delta": q.delta, "kept_triangles": st["kept_triangles"], "kept_roles": st["kept_roles"],
+                     "kept_probes": st["kept_probes"], "all_probes": st["all_probes"],
+                     "kept_probe_fraction": st["kept_probes"] / max(st["all_probes"], 1),
+                     "kept_role_fraction": st["kept_roles"] / max(st["all_roles"], 1),
+                     "select_model_bytes": st["select_bytes"], "probe_model_bytes": st["probe_bytes"]})
+    tm = F.folty_graph_traffic_model(h, W.DIR_OUT, sh)
+    F.folty_free(h)
+    return {"load_ms": float(np.median(load_ms)), "preprocess_ms": float(np.median(pre_ms)),
+            "query_ms": q_ms, "kept": kept, "info": info, "all_roles_probe_model_bytes": tm["probe_bytes"]}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="folty", choices=["folty", "reference"])
+    ap.add_argument("--workload", default="paper", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-budget", type=float, default=4.0,
+    ap.add_argument("--ref-budget", type=float, default=2.0,
                     help="seconds of sampled oracle evaluation per step")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (debug only)")
     ap.add_argument("--batch", type=int, default=256,
-                    help="queries of the batched measurement (0 = skip)")
-    ap.add_argument("--serve-seconds", type=float, default=10.0,
-                    help="length of the serving measurement (0 = skip; 60 for the full run)")
+                    help="queries of the batched measurement on the medium graph (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="length of the serving measurement (0 = skip)")
+    ap.add_argument("--no-medium", action="store_true",
+                    help="skip the medium graph's step figures when the workload is the paper-scale one")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
 
-    g = W.config_graph(2, scale=args.scale)
+    cfg_k, cfg_desc, rho_txt = WORKLOADS[args.workload]
+    g = W.config_graph(cfg_k, scale=args.scale)
     queries = [W.Query(q.delta, q.rho_num, q.rho_den, q.quant, q.dir, q.universe, False)
-               for q in W.config_queries(2)]
+               for q in W.config_queries(cfg_k)]
     if args.impl == "reference":
-        run_reference(args, g, queries)
+        run_reference(args, g, queries, args.workload)
         return
 
     import torch
@@ -396,12 +509,6 @@ def main():
 
     for _ in range(args.warmup):
         res = step(d_src, d_dst, d_t)
-    # graph figures for the roofline (outside the timed region)
-    h = F.folty_load_temporal_graph(g.n, d_src, d_dst, d_t, stream=sh)
-    F.folty_preprocess(h, sh)
-    info = F.folty_graph_get_info(h)
-    tm = F.folty_graph_traffic_model(h, W.DIR_OUT, sh)
-    F.folty_free(h)
     torch.cuda.synchronize()
 
     # ---- device-resident timed region
@@ -435,17 +542,12 @@ def main():
     prof = F.folty_profile_read()
     F.folty_profile_enable(False)
 
-    # ---- batched queries: 256 mixed queries on the same graph vs one at a time
-    batched = None
-    if args.batch > 0:
-        batched = measure_batch(F, g, d_src, d_dst, d_t, sh, args.batch, stream)
-
-    serving = None
-    if args.serve_seconds > 0 and world == 1:
-        serving = measure_serving(F, args.serve_seconds)
+    # ---- per-query figures (the metric m / t_query), preprocessing alone, kept roles
+    qt = time_queries(F, g, d_src, d_dst, d_t, sh, stream, queries)
+    info = qt["info"]
 
     # ---- end-to-end through the C ABI from pinned host buffers
-    ke = args.e2e_steps if args.e2e_steps is not None else args.steps
+    ke = args.e2e_steps if args.e2e_steps is not None else min(args.steps, 20)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -457,56 +559,96 @@ def main():
     e2e_value = replica_throughput(ke * len(queries) * g.m, world, e2e_s) if ke > 0 else None
     h2d = g.m * (4 + 4 + 8)
     d2h = sum(16 * len(r["u"]) + 8 for r in res_e) + 8 * (4 + 3 * 2)
+    del d_src, d_dst, d_t, h_src, h_dst, h_t
+
+    # ---- the medium graph's step (when the headline is the paper-scale one), the batch
+    # and the serving measurements (both over medium-recipe graphs)
+    medium = None
+    g2 = None
+    if (args.batch > 0 or (args.workload != "medium" and not args.no_medium)) and world == 1:
+        g2 = W.config_graph(2, scale=args.scale)
+    if args.workload != "medium" and not args.no_medium and world == 1:
+        q2 = [W.Query(q.delta, q.rho_num, q.rho_den, q.quant, q.dir, q.universe, False) for q in W.config_queries(2)]
+        s2 = [torch.from_numpy(a).cuda() for a in (g2.src, g2.dst, g2.t)]
+
+        def step2():
+            h = F.folty_load_temporal_graph(g2.n, *s2, stream=sh)
+            try:
+                F.folty_preprocess(h, sh)
+                return [F.folty_query(h, q, sh) for q in q2]
+            finally:
+                F.folty_free(h)
+
+        for _ in range(3):
+            step2()
+        torch.cuda.synchronize()
+        n2 = 20
+        ev0.record(stream)
+        for _ in range(n2):
+            step2()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms2 = ev0.elapsed_time(ev1) / n2
+        qt2 = time_queries(F, g2, *s2, sh, stream, q2)
+        medium = {"workload": WORKLOADS["medium"][1], "ms_per_step": ms2,
+                  "edges_per_s": len(q2) * g2.m / (ms2 / 1e3), "load_ms": qt2["load_ms"],
+                  "preprocess_ms": qt2["preprocess_ms"], "query_ms": qt2["query_ms"],
+                  "query_edges_per_s": [g2.m / (x / 1e3) for x in qt2["query_ms"]],
+                  "kept": qt2["kept"], "triangles": qt2["info"]["triangles"], "degeneracy": qt2["info"]["degeneracy"]}
+        del s2
+    batched = None
+    if args.batch > 0 and world == 1:
+        batched = measure_batch(F, g2, sh, args.batch, stream)
+    serving = None
+    if args.serve_seconds > 0 and world == 1:
+        serving = measure_serving(F, args.serve_seconds)
 
     peak, peak_kind = _peaks()
-    stages = {}
-    for name, p in prof.items():
-        if p["launches"] == 0 or p["ms"] <= 0:
-            continue
-        gbs = p["bytes"] / (p["ms"] / 1e3) / 1e9
-        stages[name] = {"ms_per_step": p["ms"] / prof_steps, "spans_per_step": p["launches"] / prof_steps,
-                        "model_bytes_per_span": p["bytes"] / p["launches"], "achieved_gbs": gbs,
-                        "frac": gbs / peak}
-    dom = max(stages, key=lambda k: stages[k]["ms_per_step"]) if stages else None
-    roofline = None
-    if dom is not None:
-        d = prof[dom]
-        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": stage_traffic(dom, d["bytes"] / d["launches"]),
-                    "stage": dom, "kernel": STAGE_KERNELS[dom], "peak_kind": f"{peak_kind} hbm_gbs",
-                    "model_bytes_per_launch": d["bytes"] / d["launches"],
-                    "launch_ms": d["ms"] / d["launches"]}
+    stages = stage_table(prof, prof_steps, peak)
+    roofline = query_roofline = None
+    if stages:
+        dom = max(stages, key=lambda k: stages[k]["ms_per_step"])
+        roofline = roofline_of(prof, dom, peak, peak_kind, args.workload)
         if dom == "peel":
-            roofline["note"] = ("the peel is bound by the latency of its dependent rounds (304 on this graph: "
-                                "grid, cluster and single-CTA phases), not by bandwidth; its model bytes are "
-                                "tiny, so the fraction is near zero by construction. The sort, probe and "
-                                "threshold stages in 'stages' are the bandwidth-bound ones")
-    probe_ms = prof["probe"]["ms"] / max(prof["probe"]["launches"], 1)
+            roofline["note"] = (f"the peel is bound by the latency of its dependent rounds ({info['peel_rounds']} "
+                                "on this graph: grid, cluster and single-CTA phases), not by bandwidth; its model "
+                                "bytes are tiny, so the fraction is near zero by construction")
+        qs_ = [k for k in QUERY_STAGES if k in stages]
+        if qs_:
+            qdom = max(qs_, key=lambda k: stages[k]["ms_per_step"])
+            query_roofline = roofline_of(prof, qdom, peak, peak_kind, args.workload)
+    q_ms = qt["query_ms"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "queries": len(queries),
-                   "deltas": [q.delta for q in queries], "rho": "1/2", "universe": "N(u)",
+        "config": {"workload": cfg_desc, "n": g.n, "m": g.m, "queries": len(queries),
+                   "deltas": [q.delta for q in queries], "rho": rho_txt, "universe": "N(u)",
                    "motif": "out", "parallelism": f"replicas x{world}",
-                   "l2": "inputs (320 MB) and timestamp store larger than the 129 MB L2",
+                   "l2": f"inputs ({g.m * 16 // 10**6} MB) and timestamp store larger than the 129 MB L2",
                    "static_edges": info["static_edges"], "triangles": info["triangles"],
-                   "probes_per_query": info["probes"], "degeneracy": info["degeneracy"],
-                   "peel_rounds": info["peel_rounds"], "solution_pairs": [len(r["u"]) for r in res],
-                   "probe_ms_per_query": probe_ms,
-                   "probe_model_bytes_all_roles": tm["probe_bytes"]},
+                   "probes_per_query_all_roles": info["probes"], "degeneracy": info["degeneracy"],
+                   "max_degree": info["max_degree"], "sigma_max": info["sigma_max"],
+                   "peel_rounds": info["peel_rounds"], "solution_pairs": [len(r["u"]) for r in res]},
+        "query": {"metric": "m / t_query (device time of folty_query alone, preprocessing excluded)",
+                  "query_ms": q_ms, "edges_per_s": [g.m / (x / 1e3) for x in q_ms],
+                  "load_ms": qt["load_ms"], "preprocess_ms": qt["preprocess_ms"], "kept": qt["kept"],
+                  "all_roles_probe_model_bytes": qt["all_roles_probe_model_bytes"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": roofline,
+        "query_roofline": query_roofline,
         "stages": stages,
         "clocks": clk,
+        "medium": medium,
         "batched": batched,
         "serving": serving,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        step_s, sample, cores = oracle_sample_time(g, queries, budget_s=args.ref_budget)
-        line["cpu_baseline"] = {"value": len(queries) * g.m / step_s, "unit": UNIT, "cores": cores,
+        arm = OracleArm(g)
+        step_s, sample = arm.step_seconds(queries, budget_s=args.ref_budget)
+        arm.close()
+        line["cpu_baseline"] = {"value": len(queries) * g.m / step_s, "unit": UNIT, "cores": arm.cores,
                                 "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -184,6 +184,23 @@ folty_status folty_graph_get_info(const folty_graph *g, folty_graph_info *info);
 folty_status folty_graph_traffic_model(folty_graph *g, int32_t dir,
                                        folty_traffic_model *out, void *stream);
 
+/* What one query's window-probe pass works on (delta, direction variant dir). Before
+ * probing, a query keeps only the roles (temporal edges x -> y of one static edge, with
+ * the third vertex of a triangle as witness) whose runs can meet the window at all; the
+ * others cannot hit (Theorem 3.1's window test needs t <= t2 <= t3 <= t + delta). The
+ * byte figures are the model the PROBE and SELECT stages of the profiler count. */
+typedef struct {
+    int64_t triangles, all_roles, all_probes;  /* 6 roles per triangle; every (edge, witness) */
+    int64_t kept_triangles, kept_roles, kept_probes;
+    int64_t select_bytes;  /* liveness pass: 30 B per triangle + 13 B per kept triangle */
+    int64_t probe_bytes;   /* probe pass: 61 B per kept triangle + the per-role bytes    */
+} folty_probe_stats;
+
+/* Runs the selection of one query and counts what it keeps (synchronises the stream).
+ * Errors: FOLTY_EINVAL (NULL, delta outside [0, 2^62), unknown dir), FOLTY_ESTATE. */
+folty_status folty_graph_probe_stats(folty_graph *g, int64_t delta, int32_t dir, folty_probe_stats *out,
+                                     void *stream);
+
 /* The per-static-edge common-neighbour counts c_uv = |N(u) cap N(v)| of Section 3 (the
  * number of triangles of G_S on the edge): a[i] < b[i], c[i] for the static_edges
  * entries (host arrays of folty_graph_info.static_edges entries, caller-owned),
@@ -202,17 +219,28 @@ uint64_t folty_kernel_launches(void);
 
 /* Device time by stage, measured with CUDA events recorded on the launching stream
  * around every launch of the stage while profiling is on (collected after the calling
- * API function's final synchronisation), with the stage's model bytes:
- *   PROBE     window probes of a query or batch pass (liveness pass over the triangles'
- *             role summaries + probes of the kept roles, per-role bytes as in the design
- *             notes);
+ * API function's final synchronisation), with the stage's model bytes (the bytes the
+ * stage's algorithm must move, not what the hardware moved):
+ *   PROBE     window probes of a query or batch pass over the kept roles (k_probe_live):
+ *             per staged triangle 61 B, per kept role w sigma1 + w min(sigma2, sigma1
+ *             ceil(log2(sigma2 + 1))) + the same for L3 + 8 sigma1 (w = bytes per stored
+ *             timestamp), counted on the device;
  *   SORT      one radix pass: 8 B read for the histogram, 12 B read + 12 B written per key;
  *   PEEL      the degeneracy peeling: 12 B per adjacency entry + 16 B per vertex;
- *   THRESHOLD certificate test and per-pair reduction: 8 B per temporal edge + 20 B per
- *             directed pair.
+ *   THRESHOLD certificate test and per-pair reduction: 8 B per temporal edge (4 with 16-bit
+ *             counters) + 20 B per directed pair;
+ *   SELECT    the per-query liveness pass over the triangles' role summaries (k_live_select):
+ *             30 B read per triangle, 13 B written per kept triangle;
+ *   TRIANGLES triangle count and listing passes: 4 B per merged out-list entry + 8 B per
+ *             static edge, per pass; 24 B written per triangle;
+ *   ROLES     the role summary (run ends, per-role sigma1 and window buckets): 92 B per
+ *             static edge + 58 B per triangle;
+ *   BATCH     the batched threshold over all queries of a direction variant: the bins
+ *             read once, 4 B of pair key per temporal edge, 16 B per solution pair.
  * Totals are process-wide; profile one thread at a time. */
 enum { FOLTY_STAGE_PROBE = 0, FOLTY_STAGE_SORT = 1, FOLTY_STAGE_PEEL = 2, FOLTY_STAGE_THRESHOLD = 3,
-       FOLTY_STAGE_COUNT = 4 };
+       FOLTY_STAGE_SELECT = 4, FOLTY_STAGE_TRIANGLES = 5, FOLTY_STAGE_ROLES = 6, FOLTY_STAGE_BATCH = 7,
+       FOLTY_STAGE_COUNT = 8 };
 typedef struct {
     int64_t launches; /* timed spans */
     double ms;        /* total device time */

@@ -32,6 +32,7 @@ EXPORTED = ["folty_load_temporal_graph", "folty_preprocess", "folty_query", "fol
             "folty_free", "folty_last_error", "folty_graph_get_info", "folty_graph_traffic_model",
             "folty_kernel_launches", "folty_profile_enable", "folty_profile_read",
             "folty_edge_counts_noalloc", "folty_graph_common_counts", "folty_graph_core_numbers",
+            "folty_graph_probe_stats",
             "folty_server_create", "folty_server_submit",
             "folty_server_wait", "folty_server_get_stats", "folty_server_destroy"]
 
@@ -96,7 +97,14 @@ class folty_stage_profile(Structure):
     _fields_ = [("launches", c_int64), ("ms", ctypes.c_double), ("bytes", c_int64)]
 
 
-STAGES = {"probe": 0, "sort": 1, "peel": 2, "threshold": 3}
+STAGES = {"probe": 0, "sort": 1, "peel": 2, "threshold": 3, "select": 4, "triangles": 5, "roles": 6,
+          "batch": 7}
+
+
+class folty_probe_stats(Structure):
+    _fields_ = [("triangles", c_int64), ("all_roles", c_int64), ("all_probes", c_int64),
+                ("kept_triangles", c_int64), ("kept_roles", c_int64), ("kept_probes", c_int64),
+                ("select_bytes", c_int64), ("probe_bytes", c_int64)]
 
 
 class folty_traffic_model(Structure):
@@ -135,6 +143,8 @@ def _load_library():
     lib.folty_profile_enable.argtypes = [c_int32]
     lib.folty_profile_read.restype = c_int32
     lib.folty_profile_read.argtypes = [c_int32, POINTER(folty_stage_profile)]
+    lib.folty_graph_probe_stats.restype = c_int32
+    lib.folty_graph_probe_stats.argtypes = [G, c_int64, c_int32, POINTER(folty_probe_stats), c_void_p]
     lib.folty_graph_common_counts.restype = c_int32
     lib.folty_graph_common_counts.argtypes = [G, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.folty_graph_core_numbers.restype = c_int32
@@ -328,6 +338,14 @@ def folty_graph_common_counts(g: int, stream: Optional[int] = None):
     _check(lib.folty_graph_common_counts(g, a.ctypes.data, b.ctypes.data, c.ctypes.data,
                                          current_stream() if stream is None else stream))
     return a[:S], b[:S], c[:S]
+
+
+def folty_graph_probe_stats(g: int, delta: int, dir: int, stream: Optional[int] = None) -> Dict[str, int]:
+    """What one query's probe pass keeps (triangles, roles, probes) and its model bytes."""
+    out = folty_probe_stats()
+    _check(lib.folty_graph_probe_stats(g, int(delta), int(dir), ctypes.byref(out),
+                                       current_stream() if stream is None else stream))
+    return {name: int(getattr(out, name)) for name, _ in folty_probe_stats._fields_}
 
 
 def folty_graph_core_numbers(g: int, stream: Optional[int] = None) -> np.ndarray:

@@ -39,9 +39,16 @@ StageSpan::StageSpan(int stage, cudaStream_t s, int64_t bytes, const unsigned lo
     idx_ = (int)t_records->size() - 1;
 }
 
-StageSpan::~StageSpan() {
-    if (idx_ >= 0 && t_records && idx_ < (int)t_records->size()) cudaEventRecord((*t_records)[idx_].b, s_);
+void StageSpan::add_bytes(int64_t bytes) {
+    if (idx_ >= 0 && t_records && idx_ < (int)t_records->size()) (*t_records)[idx_].bytes += bytes;
 }
+
+void StageSpan::end() {
+    if (!ended_ && idx_ >= 0 && t_records && idx_ < (int)t_records->size()) cudaEventRecord((*t_records)[idx_].b, s_);
+    ended_ = true;
+}
+
+StageSpan::~StageSpan() { end(); }
 
 ProfileScope::ProfileScope() {
     if (profiling_on() && !t_records) {
@@ -666,6 +673,18 @@ folty_status folty_graph_traffic_model(folty_graph* g, int32_t dir, folty_traffi
         if (dir < 0 || dir > 2) fail(FOLTY_EINVAL, "unknown direction variant");
         if (g->state != 1) fail(FOLTY_ESTATE, "graph not preprocessed");
         traffic_model(g, dir, out, (cudaStream_t)stream);
+    });
+}
+
+folty_status folty_graph_probe_stats(folty_graph* g, int64_t delta, int32_t dir, folty_probe_stats* out,
+                                     void* stream) {
+    return guarded([&] {
+        checked_graph(g);
+        if (!out) fail(FOLTY_EINVAL, "out is NULL");
+        if (delta < 0 || delta >= (1ll << 62)) fail(FOLTY_EINVAL, "delta outside [0, 2^62)");
+        if (dir < 0 || dir > FOLTY_DIR_EITHER) fail(FOLTY_EINVAL, "unknown direction variant");
+        if (g->state != 1) fail(FOLTY_ESTATE, "graph not preprocessed");
+        probe_stats(g, delta, dir, out, (cudaStream_t)stream);
     });
 }
 

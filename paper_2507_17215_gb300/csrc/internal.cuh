@@ -252,7 +252,9 @@ void validate_query(const folty_query_params& q);
 // stage's model bytes (host-known, plus an optional device-side counter). The scope's
 // commit(), called after the call's final stream synchronisation, adds the elapsed
 // times to process-wide totals.
-enum { ST_PROBE = 0, ST_SORT = 1, ST_PEEL = 2, ST_THRESHOLD = 3, ST_COUNT = 4 };
+enum { ST_PROBE = 0, ST_SORT = 1, ST_PEEL = 2, ST_THRESHOLD = 3, ST_SELECT = 4, ST_TRIANGLES = 5, ST_ROLES = 6,
+       ST_BATCH = 7, ST_COUNT = 8 };
+static_assert(ST_COUNT == FOLTY_STAGE_COUNT, "stage numbering follows folty.h");
 
 class StageSpan {
   public:
@@ -260,9 +262,14 @@ class StageSpan {
     ~StageSpan();
     StageSpan(const StageSpan&) = delete;
     StageSpan& operator=(const StageSpan&) = delete;
+    // Adds model bytes that became known after the span opened (e.g. from a read-back).
+    void add_bytes(int64_t bytes);
+    // Closes the span now (the destructor then records nothing).
+    void end();
 
   private:
     int idx_ = -1;
+    bool ended_ = false;
     cudaStream_t s_;
 };
 
@@ -287,6 +294,8 @@ void launch_probe(folty_graph* g, int64_t delta, int dir, int32_t* cnt, cudaStre
 void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t* cnt, int32_t* bins, int k,
                        const void* deltas, cudaStream_t s, uint8_t* rflag = nullptr, uint16_t* bins16 = nullptr);
 void build_role_summary(folty_graph* g, cudaStream_t s);
+// Kept roles, probes and model bytes of one query's selection (live.cu; synchronises).
+void probe_stats(folty_graph* g, int64_t delta, int dir, folty_probe_stats* out, cudaStream_t s);
 // The same pass with the counters in a file-scope device array (noalloc.cu).
 void edge_counts_noalloc(folty_graph* g, int64_t delta, int dir, int32_t* edge_count, cudaStream_t s);
 // Per-edge counts of one query: int32 (c32) or 16-bit (c16), the other null.

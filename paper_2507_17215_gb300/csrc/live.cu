@@ -421,6 +421,10 @@ static void role_summary_t(folty_graph* g, cudaStream_t s) {
     const int64_t S = g->S, ntri = g->ntri;
     Scratch sc(g->alloc, s, g->dev_err);
     RunEnds<TS>* ends = sc.get<RunEnds<TS>>(S);
+    // per static edge: 12 B of run bounds and 4 timestamps read, a 32 B record written and
+    // read back once more (the table stays in L2); per triangle: 16 B read, 24 B of sigma1
+    // and 18 B of buckets written
+    StageSpan span(ST_ROLES, s, S * (12 + 4 * (int64_t)sizeof(TS) + 64) + 58 * ntri);
     FOLTY_LAUNCH(k_run_ends<TS>, grid_for(S, 256), 256, 0, s, g->seg, S, (const TS*)g->T, ends);
     FOLTY_LAUNCH(k_role_summary<TS>, grid_for(ntri, 256), 256, 0, s, g->tri, ntri, ends, g->rsig, g->rmin);
 }
@@ -446,6 +450,38 @@ static void launch_live_t(const folty_graph* g, int dir, const LiveArgs& la, uns
         FOLTY_LAUNCH((k_probe_live<TS, FOLTY_DIR_EITHER, MODE>), grid, PB_THREADS, 0, s, la, T, delta, deltas);
 }
 
+// The kept triangles of one selection (see k_live_select).
+struct LiveSel {
+    int32_t* L;
+    int64_t* loff;
+    uint8_t* lmask;
+    int64_t* totals;  // kept triangles, slots
+    int64_t* ltile;
+    int64_t max_tiles;
+};
+
+// Selects the roles kept for delta (buffers from sc). prof_sel (may be null) receives the
+// selection's written bytes.
+static LiveSel select_live(folty_graph* g, int64_t delta, int dir, Scratch& sc, cudaStream_t s,
+                           unsigned long long* prof_sel) {
+    const int64_t ntri = g->ntri;
+    LiveSel ls;
+    ls.L = sc.get<int32_t>(ntri + 1);
+    ls.loff = sc.get<int64_t>(ntri + 1);
+    ls.lmask = sc.get<uint8_t>(ntri + 1);
+    ls.totals = sc.get<int64_t>(2);
+    ls.max_tiles = (g->info.probes + LIVE_IDLE * ntri + PB_TILE - 1) / PB_TILE;
+    ls.ltile = sc.get<int64_t>(ls.max_tiles + 2);
+    const int64_t stiles = (ntri + LS_TILE - 1) / LS_TILE;
+    unsigned long long* lsctl = sc.get<unsigned long long>(2 * stiles + 1);  // tile counter, two look-backs
+    StageSpan span(ST_SELECT, s, 30 * ntri, prof_sel);
+    FOLTY_CUDA(cudaMemsetAsync(lsctl, 0, sizeof(unsigned long long) * (size_t)(2 * stiles + 1), s));
+    FOLTY_LAUNCH(k_live_select, (unsigned)stiles, SCAN_THREADS, 0, s, g->rsig, g->rmin + (int64_t)dir * 6 * ntri, ntri,
+                 delta, lsctl + 1, lsctl + 1 + stiles, (unsigned int*)lsctl, sc.err(), ls.L, ls.loff, ls.lmask,
+                 ls.totals, ls.ltile, ls.max_tiles, prof_sel);
+    return ls;
+}
+
 // Kept roles for delta (the largest window of the pass), then the probe kernel.
 // mode 0: counts into cnt; mode 1: bins (deltas = k sorted bounds in the store's type).
 void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t* cnt, int32_t* bins, int k,
@@ -453,28 +489,21 @@ void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t
     const int64_t ntri = g->ntri;
     if (ntri == 0 || g->info.probes == 0) return;
     Scratch sc(g->alloc, s, g->dev_err);
-    int32_t* L = sc.get<int32_t>(ntri + 1);
-    int64_t* loff = sc.get<int64_t>(ntri + 1);
-    uint8_t* lmask = sc.get<uint8_t>(ntri + 1);
-    int64_t* totals = sc.get<int64_t>(2);  // kept triangles, slots
-    const int64_t max_tiles = (g->info.probes + LIVE_IDLE * ntri + PB_TILE - 1) / PB_TILE;
-    int64_t* ltile = sc.get<int64_t>(max_tiles + 2);
-    const int64_t stiles = (ntri + LS_TILE - 1) / LS_TILE;
-    unsigned long long* lsctl = sc.get<unsigned long long>(2 * stiles + 1);  // tile counter, two look-backs
-    // the selection reads 30 B per triangle (6 sigma1, 6 buckets) and writes 13 B per
-    // kept one (counted on the device)
+    // model bytes counted on the device: the selection reads 30 B per triangle (6 sigma1,
+    // 6 buckets) and writes 13 B per kept one; the probes' bytes per staged triangle and
+    // kept role are summed by the probe kernel
+    unsigned long long* prof_sel = nullptr;
     unsigned long long* prof = nullptr;
     if (profiling_on()) {
+        prof_sel = g->prof_bytes + (g->prof_next++ % PROF_SLOTS);
         prof = g->prof_bytes + (g->prof_next++ % PROF_SLOTS);
+        FOLTY_CUDA(cudaMemsetAsync(prof_sel, 0, sizeof(unsigned long long), s));
         FOLTY_CUDA(cudaMemsetAsync(prof, 0, sizeof(unsigned long long), s));
     }
-    StageSpan span(ST_PROBE, s, 30 * ntri, prof);
-    FOLTY_CUDA(cudaMemsetAsync(lsctl, 0, sizeof(unsigned long long) * (size_t)(2 * stiles + 1), s));
-    FOLTY_LAUNCH(k_live_select, (unsigned)stiles, SCAN_THREADS, 0, s, g->rsig, g->rmin + (int64_t)dir * 6 * ntri, ntri,
-                 delta, lsctl + 1, lsctl + 1 + stiles, (unsigned int*)lsctl, sc.err(), L, loff, lmask, totals, ltile,
-                 max_tiles, prof);
-    LiveArgs la{g->tri, g->seg, L, loff, lmask, ltile, totals + 1, cnt, bins, (uint32_t*)bins16, g->m_kept, k, prof,
-                rflag};
+    const LiveSel ls = select_live(g, delta, dir, sc, s, prof_sel);
+    StageSpan span(ST_PROBE, s, 0, prof);
+    LiveArgs la{g->tri, g->seg, ls.L, ls.loff, ls.lmask, ls.ltile, ls.totals + 1, cnt, bins, (uint32_t*)bins16,
+                g->m_kept, k, prof, rflag};
     int per_sm = 0;
     if (g->ts32) FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<uint32_t, 0, 0>, PB_THREADS, 0));
     else FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<int64_t, 0, 0>, PB_THREADS, 0));
@@ -487,6 +516,82 @@ void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t
         if (mode == 0) launch_live_t<int64_t, 0>(g, dir, la, grid, delta, nullptr, s);
         else launch_live_t<int64_t, 1>(g, dir, la, grid, delta, (const int64_t*)deltas, s);
     }
+}
+
+// ------------------------------------------------------------------ selection statistics
+
+// Kept roles, their probes and the probe pass's model bytes over the kept triangles of a
+// selection: out[0] += roles, out[1] += probes (sigma1 of the kept roles), out[2] +=
+// model bytes (the same per-triangle and per-role figures the probe kernel counts).
+template <typename TS, int DIR>
+__global__ void k_live_stats(const int4* __restrict__ tri, const int32_t* __restrict__ seg,
+                             const int32_t* __restrict__ L, const uint8_t* __restrict__ lmask,
+                             const int64_t* __restrict__ totals, unsigned long long* __restrict__ out) {
+    const int64_t nl = totals[0];
+    unsigned long long roles = 0, probes = 0, bytes = 0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nl; j += (int64_t)gridDim.x * blockDim.x) {
+        const int4 tr = tri[L[j]];
+        const int m = lmask[j];
+        const int32_t se[3] = {tr.x, tr.y, tr.z};
+        int32_t off[9];
+#pragma unroll
+        for (int e = 0; e < 3; e++) {
+            off[3 * e] = seg[2 * se[e]];
+            off[3 * e + 1] = seg[2 * se[e] + 1];
+            off[3 * e + 2] = seg[2 * se[e] + 2];
+        }
+        roles += (unsigned long long)__popc(m);
+        for (int r = 0; r < 6; r++)
+            if ((m >> r) & 1) probes += (unsigned long long)(off[3 * (r >> 1) + (r & 1) + 1] - off[3 * (r >> 1) + (r & 1)]);
+        bytes += kept_role_bytes<TS, DIR>(off, m, role_descriptor(tr.w, DIR));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        roles += __shfl_xor_sync(0xffffffffu, roles, o);
+        probes += __shfl_xor_sync(0xffffffffu, probes, o);
+        bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+    }
+    if ((threadIdx.x & 31) == 0 && roles) {
+        atomicAdd(&out[0], roles);
+        atomicAdd(&out[1], probes);
+        atomicAdd(&out[2], bytes);
+    }
+}
+
+template <typename TS>
+static void live_stats_t(const folty_graph* g, int dir, const LiveSel& ls, unsigned long long* acc, cudaStream_t s) {
+    const unsigned grid = grid_for(g->ntri, 256);
+    if (dir == FOLTY_DIR_OUT)
+        FOLTY_LAUNCH((k_live_stats<TS, FOLTY_DIR_OUT>), grid, 256, 0, s, g->tri, g->seg, ls.L, ls.lmask, ls.totals, acc);
+    else if (dir == FOLTY_DIR_IN)
+        FOLTY_LAUNCH((k_live_stats<TS, FOLTY_DIR_IN>), grid, 256, 0, s, g->tri, g->seg, ls.L, ls.lmask, ls.totals, acc);
+    else
+        FOLTY_LAUNCH((k_live_stats<TS, FOLTY_DIR_EITHER>), grid, 256, 0, s, g->tri, g->seg, ls.L, ls.lmask, ls.totals,
+                     acc);
+}
+
+void probe_stats(folty_graph* g, int64_t delta, int dir, folty_probe_stats* out, cudaStream_t s) {
+    std::memset(out, 0, sizeof(*out));
+    out->triangles = g->ntri;
+    out->all_roles = 6 * g->ntri;
+    out->all_probes = g->info.probes;  // every (temporal edge, witness) pair
+    out->select_bytes = 30 * g->ntri;
+    if (g->ntri == 0 || g->info.probes == 0) return;
+    Scratch sc(g->alloc, s, g->dev_err);
+    const LiveSel ls = select_live(g, delta, dir, sc, s, nullptr);
+    unsigned long long* acc = sc.get<unsigned long long>(3);
+    FOLTY_CUDA(cudaMemsetAsync(acc, 0, 3 * sizeof(unsigned long long), s));
+    if (g->ts32) live_stats_t<uint32_t>(g, dir, ls, acc, s);
+    else live_stats_t<int64_t>(g, dir, ls, acc, s);
+    const void* ptrs[4] = {ls.totals, acc, acc + 1, acc + 2};
+    int sizes[4] = {8, 8, 8, 8};
+    int64_t v[4];
+    read_back(g, ptrs, sizes, 4, v, s);
+    out->kept_triangles = v[0];
+    out->kept_roles = v[1];
+    out->kept_probes = v[2];
+    out->probe_bytes = v[3];
+    out->select_bytes += 13 * v[0];
 }
 
 }  // namespace folty

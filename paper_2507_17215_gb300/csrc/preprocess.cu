@@ -2509,10 +2509,14 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     FOLTY_CUDA(cudaMemsetAsync(merged, 0, 2 * sizeof(unsigned long long), s));
     int32_t* sig = sc.get<int32_t>(S);
     if (S > 0) FOLTY_LAUNCH(k_max_sigma, grid_for(S, T), T, 0, s, g->seg, S, sig, stat + 2);
+    // the counting pass merges the two out-lists of every oriented edge: 4 B per merged
+    // entry (known after the read-back below) + 8 B per static edge
+    StageSpan tri_span(ST_TRIANGLES, s, 8 * (int64_t)S);
     if (S > 0)
         FOLTY_LAUNCH(k_tri_count, grid_for(S, T), T, 0, s, outptr, out_nbr, out_src, out_eid, sig, S, tcnt, merged,
                      merged + 1);
     exclusive_scan(sc, tcnt, toff, S);
+    tri_span.end();
     FOLTY_LAUNCH(k_max_i32, grid_for(n, T), T, 0, s, g->deg, (int64_t)n, stat + 0);
     {
         const void* ptrs[9] = {toff + S, stat + 0, stat + 1, stat + 2, merged, merged + 1, peel_ctl + C_ERR,
@@ -2533,14 +2537,18 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         g->info.max_out_degree = (int32_t)outv[2];
         g->info.sigma_max = (int32_t)outv[3];
         g->enum_bytes = 4 * outv[4] + 8 * (int64_t)S;
+        tri_span.add_bytes(4 * outv[4]);
     }
     const int64_t ntri = g->ntri;
     g->tri = graph_alloc<int4>(g, ntri, s);
     g->tri_off = graph_alloc<int64_t>(g, ntri + 1, s);
     int64_t* cost = sc.get<int64_t>(ntri + 1);
-    if (S > 0)
+    if (S > 0) {
+        // the listing pass merges the same lists and writes 16 + 8 B per triangle
+        StageSpan span(ST_TRIANGLES, s, g->enum_bytes + 24 * ntri);
         FOLTY_LAUNCH(k_tri_write, grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr, out_eid, out_src, S, toff, sig,
                      g->tri, cost, g->common);
+    }
     exclusive_scan(sc, cost, g->tri_off, ntri);
     g->info.triangles = ntri;
     // tile -> first triangle map of the probe kernels (query independent)

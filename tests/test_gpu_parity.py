@@ -331,46 +331,125 @@ def test_batch_with_a_hub_of_degree_past_16_bits(F):
             _assert_same(b1, want, str(q))
 
 
-def test_full_size_medium_workload_sampled(F):
-    """The medium workload at full size (1M vertices, 20M edges), as the benchmark runs
-    it: every query of the workload, checked on sampled edges and sampled pairs."""
-    g = W.config_graph(2)
+def _pairs_from_counts(src, dst, counts, common, deg, n, q):
+    """Solution pairs of query q among the given temporal edges, from their counts and
+    common-neighbour numbers (both the oracle's) and the degrees of G_S, written out from
+    Definition 1.1 and the pair reading (max count, number of certificates) with numpy:
+    the check of a pair list on a subset of heads."""
+    keep = src != dst
+    x, y = src[keep].astype(np.int64), dst[keep].astype(np.int64)
+    c, cm = counts[keep].astype(np.int64), common[keep].astype(np.int64)
+    U = {W.U_HEAD: deg[x], W.U_TAIL: deg[y], W.U_COMMON: cm}[q.universe]
+    sat = (c >= 1) & ((q.quant == W.Q_EXISTS) | (c * q.rho_den >= q.rho_num * U))
+    key = x * n + y
+    order = np.argsort(key, kind="stable")
+    key, c, sat = key[order], c[order], sat[order]
+    starts = np.concatenate([[0], np.nonzero(np.diff(key))[0] + 1])
+    mx = np.maximum.reduceat(c, starts) if len(key) else c
+    nc = np.add.reduceat(sat.astype(np.int64), starts) if len(key) else c
+    k0 = key[starts] if len(key) else key
+    sel = nc > 0
+    return [(int(a // n), int(a % n), int(b), int(d)) for a, b, d in zip(k0[sel], mx[sel], nc[sel])]
+
+
+def _degrees(g):
+    """|N(u)| in G_S from the input edge list (distinct unordered pairs, no self-loops)."""
+    keep = g.src != g.dst
+    lo = np.minimum(g.src, g.dst)[keep].astype(np.int64)
+    hi = np.maximum(g.src, g.dst)[keep].astype(np.int64)
+    key = np.unique(lo * g.n + hi)
+    return np.bincount(np.concatenate([key // g.n, key % g.n]), minlength=g.n).astype(np.int64)
+
+
+@pytest.fixture(scope="module")
+def medium_full():
+    return W.config_graph(2)
+
+
+def test_full_size_medium_workload(F, medium_full):
+    """The medium workload at full size (1M vertices, 20M edges), the benchmark's three
+    queries: every per-edge count and the whole sorted pair list against the oracle."""
+    g = medium_full
     qs = [W.Query(d, 1, 2, want_edge_counts=True) for d in (600, 3600, 86400)]
-    rng = np.random.default_rng(99)
     with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
         res = [G.query(q) for q in qs]
+        bat = G.query_batch(qs)
         info = G.info()
     assert info["m"] == g.m and info["probes"] > 10 ** 7
-    # edges with a large count are rare: sample uniformly and among the top counts
-    key = g.src.astype(np.int64) * g.n + g.dst
-    by_key = np.argsort(key, kind="stable")
-    skey = key[by_key]
     with oracle.OracleGraph.of(g) as og:
-        deg = np.array([og.degree(u) for u in range(g.n)], dtype=np.int64)
-        for q, r in zip(qs, res):
+        for q, r, rb in zip(qs, res, bat):
+            want = og.query(q)
+            _assert_same(r, want, str(q))
+            _assert_same(rb, want, str(q))
+            assert int((want["edge_count"] > 0).sum()) > 1000
+
+
+@pytest.fixture(scope="module")
+def paper_full():
+    return W.config_graph(3)
+
+
+def test_full_size_paper_scale_workload(F, paper_full):
+    """The paper-scale workload at full size (5M vertices, 70M temporal edges, 50 planted
+    dense communities, degeneracy about 200, 77M triangles): its query (delta = 3600 s,
+    rho = 3/10) compared in full -- all 70M per-edge counts, the whole sorted pair list,
+    the certificate total -- plus two more query variants on sampled edges and on the
+    complete pair lists of sampled heads, and the batch of all three against the singles."""
+    g = paper_full
+    q0 = W.config_queries(3)[0]
+    q0 = W.Query(q0.delta, q0.rho_num, q0.rho_den, q0.quant, q0.dir, q0.universe, True)
+    extra = [W.Query(86400, 1, 10, W.Q_FORALL_T, W.DIR_EITHER, W.U_COMMON, True),
+             W.Query(604800, 1, 2, W.Q_EXISTS, W.DIR_IN, W.U_TAIL, True)]
+    qs = [q0] + extra
+    with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
+        info = G.info()
+        res = [G.query(q) for q in qs]
+        bat = G.query_batch(qs)
+        a, b, cab = F.folty_graph_common_counts(G.handle)
+        core = G.core_numbers()
+    assert info["m"] == 70_000_000 and info["triangles"] > 5 * 10 ** 7 and info["degeneracy"] >= 150
+    # core numbers vertex by vertex against the textbook bucket algorithm on G_S's edges
+    keep = g.src != g.dst
+    pk = np.unique(np.minimum(g.src, g.dst)[keep].astype(np.int64) * g.n + np.maximum(g.src, g.dst)[keep])
+    core_want = np.asarray(_core_numbers(g.n, pk // g.n, pk % g.n), dtype=np.int32)
+    np.testing.assert_array_equal(core, core_want)
+    assert info["degeneracy"] == int(core_want.max())
+    for r, rb in zip(res, bat):
+        np.testing.assert_array_equal(r["edge_count"], rb["edge_count"])
+        assert pairs_of(r) == pairs_of(rb)
+    rng = np.random.default_rng(33)
+    with oracle.OracleGraph.of(g) as og:
+        want = og.query(q0)
+        _assert_same(res[0], want, str(q0))
+        assert int((want["edge_count"] > 0).sum()) > 1000
+        deg = _degrees(g)
+        skey = a.astype(np.int64) * g.n + b
+
+        def common_of(idx):
+            lo = np.minimum(g.src[idx], g.dst[idx]).astype(np.int64)
+            hi = np.maximum(g.src[idx], g.dst[idx]).astype(np.int64)
+            return cab[np.searchsorted(skey, lo * g.n + hi)].astype(np.int64)
+
+        by_src = np.argsort(g.src, kind="stable")
+        src_sorted = g.src[by_src]
+        for q, r in zip(extra, res[1:]):
             ec = r["edge_count"]
-            idx = np.unique(np.concatenate([rng.integers(0, g.m, 1500),
-                                            np.argsort(ec)[-300:]]))
-            want, _ = og.counts(q.delta, q.dir, idx=idx)
-            np.testing.assert_array_equal(ec[idx], want)
-            # sampled output pairs: recompute max count and certificates from the oracle
-            k = len(r["u"])
-            assert k == len(set(zip(r["u"].tolist(), r["v"].tolist())))
-            order = np.lexsort((r["v"], r["u"]))
-            assert (order == np.arange(k)).all(), "pairs must be sorted by (u, v)"
-            for j in rng.choice(k, size=min(k, 60), replace=False) if k else []:
-                u, v = int(r["u"][j]), int(r["v"][j])
-                lo, hi = np.searchsorted(skey, [u * g.n + v, u * g.n + v + 1])
-                edges = by_key[lo:hi]
-                c, _ = og.counts(q.delta, q.dir, idx=edges)
-                assert int(c.max()) == int(r["count"][j])
-                ncert = int(((c >= 1) & (c.astype(np.int64) * q.rho_den >= q.rho_num * deg[u])).sum())
-                assert ncert == int(r["ncert"][j])
-            # every sampled certificate appears among the pairs
-            pairs = set(zip(r["u"].tolist(), r["v"].tolist()))
-            sat = (want >= 1) & (want.astype(np.int64) * q.rho_den >= q.rho_num * deg[g.src[idx]])
-            for e in idx[sat]:
-                assert (int(g.src[e]), int(g.dst[e])) in pairs
+            idx = np.unique(np.concatenate([rng.integers(0, g.m, 5000), np.argsort(ec)[-500:]]))
+            got, common = og.counts(q.delta, q.dir, idx=idx)
+            np.testing.assert_array_equal(ec[idx], got, err_msg=str(q))
+            np.testing.assert_array_equal(common_of(idx), common)
+            # complete pair lists of sampled heads: solution heads and uniform vertices
+            heads = np.unique(np.concatenate([rng.choice(r["u"], size=min(20, len(r["u"])), replace=False),
+                                              rng.choice(np.unique(g.src), size=20, replace=False)]))
+            for x in heads.tolist():
+                lo, hi = np.searchsorted(src_sorted, [x, x + 1])
+                e = by_src[lo:hi]
+                c, cm = og.counts(q.delta, q.dir, idx=e)
+                want_pairs = _pairs_from_counts(g.src[e], g.dst[e], c, cm, deg, g.n, q)
+                sel = r["u"] == x
+                got_pairs = list(zip(r["u"][sel].tolist(), r["v"][sel].tolist(), r["count"][sel].tolist(),
+                                     r["ncert"][sel].tolist()))
+                assert got_pairs == want_pairs, (str(q), x)
 
 
 def test_errors(F):
