@@ -4,15 +4,20 @@
 // of Theorem 3.1 do not depend on delta, so hit(delta) <=> g(e, w) = t3 - t <= delta.
 // One probe pass per direction variant therefore serves every delta of that variant
 // (live.cu, binning mode, roles kept for the largest delta of the pass): the pass bins
-// g by the sorted distinct deltas D (bin j = first D_j >= g), a prefix
-// over the bins gives c_e(D_j) = #{w : g(e, w) <= D_j} for all j at once, and each
-// query's threshold pass (the single-query code) reads its column. Quantifier, rho and
-// universe only enter that last pass. When the bins of all deltas do not fit in the
-// memory budget, the deltas are cut into chunks, one probe pass per chunk (bin 0 of a
-// chunk also holds every smaller gap).
+// g by the sorted distinct deltas D (bin j = first D_j >= g), and a prefix over the bins
+// gives c_e(D_j) = #{w : g(e, w) <= D_j} for all j at once. Quantifier, rho and universe
+// only enter the threshold (Definition 1.1; Algorithm 5), so one pass over the bins
+// answers every query of the variant: k_batch_threshold walks each edge's bins in order,
+// keeps the prefix in a register, tests each query's certificate condition at its bin and
+// reduces each directed pair's run of edges within the warp; the solution pairs of all
+// queries are appended as (query, rank of the pair in (u, v) order) keys and sorted once.
+// Queries that also want per-edge counts, certificates or vertex solutions take the
+// single-query threshold path on the prefix-summed bins instead. When the bins of all
+// deltas do not fit in the memory budget, the deltas are cut into chunks, one probe pass
+// per chunk (bin 0 of a chunk also holds every smaller gap).
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
-#include <map>
 
 #include "internal.cuh"
 #include "probe.cuh"
@@ -36,6 +41,294 @@ __global__ void k_bins_prefix(C* __restrict__ bins, int k, int64_t mk) {
     }
 }
 
+// ------------------------------------------------------------------ pair ranks
+
+__device__ __forceinline__ int64_t lower_bound_pair(const int32_t* __restrict__ ka, const int32_t* __restrict__ kb,
+                                                    const int32_t* __restrict__ idx, int64_t n, int32_t x, int32_t y) {
+    int64_t lo = 0;
+    while (n > 0) {
+        const int64_t half = n >> 1;
+        const int32_t i = idx ? idx[lo + half] : (int32_t)(lo + half);
+        if (ka[i] < x || (ka[i] == x && kb[i] < y)) {
+            lo += half + 1;
+            n -= half + 1;
+        } else {
+            n = half;
+        }
+    }
+    return lo;
+}
+
+// prank[2s + d] = position of the directed pair (x, y) of static edge s, direction d, in
+// the (x, y) order of all directed pairs: pairs x < y are the static edges in (a, b)
+// order, pairs x > y the static edges in (b, a) order (by_b); a pair's position is its
+// index in its own list plus the number of pairs of the other list before it.
+__global__ void k_pair_ranks(const int32_t* __restrict__ ea, const int32_t* __restrict__ eb,
+                             const int32_t* __restrict__ by_b, int64_t S, int32_t* __restrict__ prank) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * S; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < S) {  // (a, b) of static edge i; pairs (b', a') with b' < a, or b' == a and a' < b, precede it
+            prank[2 * i] = (int32_t)(i + lower_bound_pair(eb, ea, by_b, S, ea[i], eb[i]));
+        } else {  // (b, a) of static edge by_b[j]
+            const int64_t j = i - S;
+            const int32_t s = by_b[j];
+            prank[2 * (int64_t)s + 1] = (int32_t)(j + lower_bound_pair(ea, eb, nullptr, S, eb[s], ea[s]));
+        }
+    }
+}
+
+static const int32_t* pair_ranks(folty_graph* g, cudaStream_t s) {
+    if (!g->prank) {
+        g->prank = graph_alloc<int32_t>(g, 2 * (int64_t)g->S, s);
+        if (g->S > 0)
+            FOLTY_LAUNCH(k_pair_ranks, grid_for(2 * (int64_t)g->S, 256), 256, 0, s, g->ea, g->eb, g->by_b,
+                         (int64_t)g->S, g->prank);
+    }
+    return g->prank;
+}
+
+// ------------------------------------------------------------------ fused threshold
+
+constexpr int BT_THREADS = 256;
+constexpr int BT_WARPS = BT_THREADS / 32;
+constexpr int BT_MAXQ = 256;  // queries of one fused pass
+constexpr int BT_UNROLL = 8;  // bins loaded together per lane
+
+// One query of a fused pass, the queries sorted by bin.
+struct BatchQuery {
+    int32_t j;     // bin of its delta
+    int32_t slot;  // index among the pass's queries (high bits of its output keys)
+    int32_t quant, universe;
+    int64_t num, den;
+};
+
+struct BatchArgs {
+    const void* bins;  // C[k][mk]
+    int k;
+    int64_t mk;
+    const int32_t* sd;   // 2 * static edge + direction of every sorted edge
+    const int32_t* seg;  // run bounds: run r = [seg[r], seg[r + 1])
+    const int32_t* ea;
+    const int32_t* eb;
+    const int32_t* deg;
+    const int32_t* common;
+    const int32_t* prank;
+    const BatchQuery* qs;
+    int nq;
+    int rb;  // bits of a pair rank
+    int64_t per_warp;
+    int64_t cap;
+    unsigned long long* n_out;
+    uint64_t* out_key;  // (slot << rb) | pair rank
+    int32_t* out_run;   // the pair's run id 2s + d
+    int32_t* out_cnt;   // max c_e over the pair's edges
+    int32_t* out_nc;    // certificates among them
+};
+
+// x rounded up to the next start of a run (runs of one directed pair are contiguous).
+__device__ __forceinline__ int64_t run_aligned(const int32_t* __restrict__ sd, const int32_t* __restrict__ seg,
+                                               int64_t x, int64_t mk) {
+    if (x <= 0) return 0;
+    if (x >= mk) return mk;
+    const int32_t r = sd[x];
+    return (sd[x - 1] != r) ? x : (int64_t)seg[r + 1];
+}
+
+// Universe sizes of the pair of run r: |N(x)|, |N(y)|, |N(x) cap N(y)|.
+__device__ __forceinline__ void universes(const BatchArgs& a, int32_t r, int64_t& uh, int64_t& ut, int64_t& uc) {
+    const int32_t s = r >> 1;
+    const int32_t x = (r & 1) ? a.eb[s] : a.ea[s], y = (r & 1) ? a.ea[s] : a.eb[s];
+    uh = a.deg[x];
+    ut = a.deg[y];
+    uc = a.common[s];
+}
+
+__device__ __forceinline__ bool certifies_q(const BatchQuery& q, uint32_t c, int64_t uh, int64_t ut, int64_t uc) {
+    if (c == 0) return false;
+    if (q.quant == FOLTY_Q_EXISTS) return true;
+    const int64_t U = q.universe == FOLTY_U_HEAD ? uh : q.universe == FOLTY_U_TAIL ? ut : uc;
+    return (int64_t)c * q.den >= q.num * U;
+}
+
+// Appends the pairs of the lanes with emit set (one atomic per warp).
+__device__ __forceinline__ void emit_pairs(const BatchArgs& a, bool emit, int slot, int32_t r, int32_t cnt, int32_t nc) {
+    const unsigned em = __ballot_sync(0xffffffffu, emit);
+    if (!em) return;
+    const int lane = threadIdx.x & 31;
+    const int first = __ffs(em) - 1;
+    unsigned long long base = 0;
+    if (lane == first) base = atomicAdd(a.n_out, (unsigned long long)__popc(em));
+    base = __shfl_sync(0xffffffffu, base, first);
+    if (emit) {
+        const unsigned long long i = base + __popc(em & ((1u << lane) - 1u));
+        if (i < (unsigned long long)a.cap) {
+            a.out_key[i] = ((uint64_t)slot << a.rb) | (uint64_t)(uint32_t)a.prank[r];
+            a.out_run[i] = r;
+            a.out_cnt[i] = cnt;
+            a.out_nc[i] = nc;
+        }
+    }
+}
+
+// The prefix c_e(D_j) of the bins of one lane's edge, BT_UNROLL bins at a time (their
+// loads in flight together): c[u] = c_e(D_{j0 + u}).
+template <typename C>
+__device__ __forceinline__ void bin_block(const C* __restrict__ bins, int64_t mk, int k, int j0, int64_t e, bool on,
+                                          uint32_t& run, uint32_t* c) {
+    C v[BT_UNROLL];
+#pragma unroll
+    for (int u = 0; u < BT_UNROLL; u++) v[u] = (on && j0 + u < k) ? __ldcs(&bins[(int64_t)(j0 + u) * mk + e]) : (C)0;
+#pragma unroll
+    for (int u = 0; u < BT_UNROLL; u++) {
+        run += (uint32_t)v[u];
+        c[u] = run;
+    }
+}
+
+__device__ __forceinline__ uint32_t pick(const uint32_t* c, int d) {
+    uint32_t x = c[0];
+#pragma unroll
+    for (int u = 1; u < BT_UNROLL; u++) x = (d == u) ? c[u] : x;
+    return x;
+}
+
+// Every warp takes a contiguous range of sorted edges whose ends are moved to run
+// starts, so that no directed pair's run is split between warps. It walks the range in
+// windows of at most 32 edges made of whole runs (lane = edge), or, for a run longer
+// than 32 edges, in 32-edge pieces of that run with per-query totals in shared memory.
+template <typename C>
+__global__ void __launch_bounds__(BT_THREADS) k_batch_threshold(const BatchArgs a) {
+    __shared__ BatchQuery sq[BT_MAXQ];
+    __shared__ int32_t lmax[BT_WARPS][BT_MAXQ];
+    __shared__ int32_t lnc[BT_WARPS][BT_MAXQ];
+    for (int i = threadIdx.x; i < a.nq; i += blockDim.x) sq[i] = a.qs[i];
+    __syncthreads();
+    const C* bins = static_cast<const C*>(a.bins);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t p = run_aligned(a.sd, a.seg, warp * a.per_warp, a.mk);
+    const int64_t hi = run_aligned(a.sd, a.seg, (warp + 1) * a.per_warp, a.mk);
+    while (p < hi) {
+        const int64_t we = min(p + 32, hi);
+        int64_t L = we - p;
+        if (we < hi) {
+            const int32_t rl = a.sd[we - 1];
+            if (a.sd[we] == rl) L = (int64_t)a.seg[rl] - p;  // drop the run that continues past the window
+        }
+        if (L > 0) {
+            // ---- whole runs in lanes [0, L)
+            const bool on = lane < L;
+            const int64_t e = p + lane;
+            const int32_t key = on ? a.sd[e] : -1;
+            const int32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+            const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || key != prev);
+            const unsigned above = heads & ~((2u << lane) - 1u);
+            const int start = 31 - __clz(heads & ((2u << lane) - 1u));
+            const unsigned peers = (above ? (above & (0u - above)) - 1u : 0xffffffffu) & ~((1u << start) - 1u);
+            const bool leader = on && lane == start;
+            int64_t uh = 0, ut = 0, uc = 0;
+            bool uload = false;
+            uint32_t run = 0;
+            int qi = 0;
+            for (int j0 = 0; j0 < a.k && qi < a.nq; j0 += BT_UNROLL) {
+                uint32_t c[BT_UNROLL];
+                bin_block<C>(bins, a.mk, a.k, j0, e, on, run, c);
+                const bool any = __any_sync(0xffffffffu, run > 0);  // c is non-decreasing in j
+                while (qi < a.nq && sq[qi].j < j0 + BT_UNROLL) {
+                    if (!any) {
+                        qi++;
+                        continue;
+                    }
+                    const BatchQuery q = sq[qi++];
+                    const uint32_t cq = pick(c, q.j - j0);
+                    if (cq > 0 && q.quant != FOLTY_Q_EXISTS && !uload) {
+                        universes(a, key, uh, ut, uc);
+                        uload = true;
+                    }
+                    const bool sat = certifies_q(q, cq, uh, ut, uc);
+                    if (!__any_sync(0xffffffffu, sat)) continue;
+                    const int rmax = __reduce_max_sync(peers, (int)cq);
+                    const int rsat = __reduce_add_sync(peers, sat ? 1 : 0);
+                    emit_pairs(a, leader && rsat > 0, q.slot, key, rmax, rsat);
+                }
+            }
+            p += L;
+        } else {
+            // ---- one run longer than 32 edges, in pieces
+            const int32_t key = a.sd[p];
+            const int64_t re = a.seg[key + 1];
+            for (int i = lane; i < a.nq; i += 32) {
+                lmax[wib][i] = 0;
+                lnc[wib][i] = 0;
+            }
+            __syncwarp();
+            int64_t uh, ut, uc;
+            universes(a, key, uh, ut, uc);
+            for (int64_t b = p; b < re; b += 32) {
+                const int64_t e = b + lane;
+                const bool on = e < re;
+                uint32_t run = 0;
+                int qi = 0;
+                for (int j0 = 0; j0 < a.k && qi < a.nq; j0 += BT_UNROLL) {
+                    uint32_t c[BT_UNROLL];
+                    bin_block<C>(bins, a.mk, a.k, j0, e, on, run, c);
+                    const bool any = __any_sync(0xffffffffu, run > 0);
+                    while (qi < a.nq && sq[qi].j < j0 + BT_UNROLL) {
+                        if (!any) {
+                            qi++;
+                            continue;
+                        }
+                        const int i = qi;
+                        const BatchQuery q = sq[qi++];
+                        const uint32_t cq = pick(c, q.j - j0);
+                        const bool sat = certifies_q(q, cq, uh, ut, uc);
+                        if (!__any_sync(0xffffffffu, sat)) continue;
+                        const int rmax = __reduce_max_sync(0xffffffffu, (int)cq);
+                        const int rsat = __reduce_add_sync(0xffffffffu, sat ? 1 : 0);
+                        if (lane == 0) {
+                            lmax[wib][i] = max(lmax[wib][i], rmax);
+                            lnc[wib][i] += rsat;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            for (int i0 = 0; i0 < a.nq; i0 += 32) {
+                const int i = i0 + lane;
+                const bool emit = i < a.nq && lnc[wib][i] > 0;
+                emit_pairs(a, emit, emit ? sq[i].slot : 0, key, emit ? lmax[wib][i] : 0, emit ? lnc[wib][i] : 0);
+            }
+            __syncwarp();
+            p = re;
+        }
+    }
+}
+
+// Sorted solutions -> out = [u... | v... | count... | ncert...]; qstart[slot] = first
+// index of the slot's solutions (left at -1 for a slot without any).
+__global__ void k_batch_gather(const uint64_t* __restrict__ key, const uint32_t* __restrict__ order,
+                               const int32_t* __restrict__ run, const int32_t* __restrict__ cnt,
+                               const int32_t* __restrict__ nc, const int32_t* __restrict__ ea,
+                               const int32_t* __restrict__ eb, int64_t n, int rb, int32_t* __restrict__ out,
+                               int32_t* __restrict__ qstart) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t o = order[i];
+        const int32_t r = run[o], s = r >> 1;
+        out[i] = (r & 1) ? eb[s] : ea[s];
+        out[n + i] = (r & 1) ? ea[s] : eb[s];
+        out[2 * n + i] = cnt[o];
+        out[3 * n + i] = nc[o];
+        const int q = (int)(key[i] >> rb);
+        if (i == 0 || (int)(key[i - 1] >> rb) != q) qstart[q] = (int32_t)i;
+    }
+}
+
+__global__ void k_iota_u32(uint32_t* __restrict__ a, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = (uint32_t)i;
+}
+
+// ------------------------------------------------------------------ host side
+
 static int64_t batch_bin_budget_bytes() {
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
@@ -46,6 +339,15 @@ static int64_t batch_bin_budget_bytes() {
     const int64_t cap = (int64_t)16 << 30;
     return b < cap ? b : cap;
 }
+
+static bool plain_query(const folty_query_params& q) {
+    return !q.want_edge_counts && !q.want_certificates && !q.outer && !q.want_triples;
+}
+
+// Solution buffer entries of a fused pass: key, alternate key, run, count, certificates,
+// two sort values (36 B each).
+constexpr int64_t BT_ENTRY_BYTES = 36;
+constexpr int64_t BT_DEFAULT_CAP = int64_t(1) << 22;
 
 // Bins of one probe pass: the largest number of distinct deltas of one direction variant.
 int64_t batch_footprint(const folty_graph* g, const folty_query_params* qs, int nq, int64_t* bins_part) {
@@ -60,27 +362,158 @@ int64_t batch_footprint(const folty_graph* g, const folty_query_params* qs, int 
     }
     kmax = std::min<int64_t>(kmax, BATCH_MAX_BINS);
     const int64_t bins = kmax * g->m_kept * 4;
-    // output stage per query of a read-back group (see finish_queries): 6 int32 arrays
-    // of 2S + 1, compacted keys, packed output, edge counts when asked
+    // the fused pass: its solution buffer and the pair ranks
+    int64_t fused = 0;
+    bool any_plain = false;
+    for (int i = 0; i < nq; i++) any_plain = any_plain || plain_query(qs[i]);
+    if (any_plain) fused = BT_DEFAULT_CAP * BT_ENTRY_BYTES + 4 * 2 * (int64_t)g->S;
+    // output stage per query of a read-back group of the single-query path (see
+    // finish_queries): 6 int32 arrays of 2S + 1, compacted keys, packed output, edge counts
+    // when asked
     const int64_t n2 = 2 * (int64_t)g->S;
     int64_t per_q = 6 * 4 * (n2 + 1) + 8 * n2 + 16 * n2 + 64;
-    bool edges = false, certs = false, outer = false;
+    bool edges = false, certs = false, outer = false, other = false;
     for (int i = 0; i < nq; i++) {
         edges = edges || qs[i].want_edge_counts;
         certs = certs || qs[i].want_certificates;
         outer = outer || qs[i].outer;
+        other = other || (!plain_query(qs[i]) && !qs[i].want_triples);
     }
     if (edges) per_q += 4 * g->m;
     if (certs) per_q += 16 * (g->m + 1);
     if (outer) per_q += 14 * ((int64_t)g->n + 1);
-    const int64_t group = std::min<int64_t>(nq, READBACK_MAX / 4);
+    const int64_t group = other ? std::min<int64_t>(nq, READBACK_MAX / 4) : 0;
     // a triple query runs alone: role flags and scan (9 B per role), and up to one triple
     // per role through the two sorts (44 B each), on top of its own counters
     bool triples = false;
     for (int i = 0; i < nq; i++) triples = triples || qs[i].want_triples;
     const int64_t tri_part = triples ? 53 * 6 * g->ntri + 4 * g->m_kept + per_q : 0;
     if (bins_part) *bins_part = bins;
-    return std::max(bins + group * per_q, tri_part);
+    return std::max(bins + fused + group * per_q, tri_part);
+}
+
+// The fused threshold of the plain queries `fq` (at most BT_MAXQ, with their bins j) over
+// the raw (not prefix-summed) bins of one probe pass; fills their results.
+template <typename C>
+static void fused_threshold(folty_graph* g, const C* bins, int k, const std::vector<const folty_query_params*>& fq,
+                            const std::vector<int>& fj, const std::vector<folty_result*>& fo, cudaStream_t s) {
+    const int nq = (int)fq.size();
+    const int64_t mk = g->m_kept;
+    const int64_t S = g->S;
+    Scratch sc(g->alloc, s, g->dev_err);
+    const int32_t* prank = pair_ranks(g, s);
+    // the queries sorted by bin
+    std::vector<BatchQuery> hq((size_t)nq);
+    std::vector<int> order((size_t)nq);
+    for (int i = 0; i < nq; i++) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return fj[(size_t)x] < fj[(size_t)y]; });
+    for (int i = 0; i < nq; i++) {
+        const folty_query_params& q = *fq[(size_t)order[(size_t)i]];
+        hq[(size_t)i] = BatchQuery{fj[(size_t)order[(size_t)i]], order[(size_t)i], (int)q.quant, (int)q.universe,
+                                   (int64_t)q.rho_num, (int64_t)q.rho_den};
+    }
+    BatchQuery* dq = sc.get<BatchQuery>(nq);
+    FOLTY_CUDA(cudaMemcpyAsync(dq, hq.data(), sizeof(BatchQuery) * (size_t)nq, cudaMemcpyHostToDevice, s));
+    int per_sm = 0;
+    FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_threshold<C>, BT_THREADS, 0));
+    const int64_t blocks = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
+    const int64_t nwarps = blocks * BT_WARPS;
+    BatchArgs a{};
+    a.bins = bins;
+    a.k = k;
+    a.mk = mk;
+    a.sd = g->sd;
+    a.seg = g->seg;
+    a.ea = g->ea;
+    a.eb = g->eb;
+    a.deg = g->deg;
+    a.common = g->common;
+    a.prank = prank;
+    a.qs = dq;
+    a.nq = nq;
+    a.rb = bit_length((uint64_t)(2 * S > 1 ? 2 * S - 1 : 1));
+    a.per_warp = (mk + nwarps - 1) / nwarps;
+    a.n_out = sc.get<unsigned long long>(1);
+    // each (query, directed pair) is emitted at most once; FOLTY_BATCH_SOLUTION_CAP sets a
+    // smaller first buffer (the tests use it to run the second pass)
+    int64_t cap = BT_DEFAULT_CAP;
+    if (const char* env = std::getenv("FOLTY_BATCH_SOLUTION_CAP")) cap = std::max<int64_t>(1, std::atoll(env));
+    cap = std::min<int64_t>(cap, std::max<int64_t>(1, (int64_t)nq * 2 * S));
+    int64_t n_out = 0;
+    for (int attempt = 0; attempt < 2; attempt++) {
+        Scratch so(g->alloc, s, g->dev_err);
+        a.cap = cap;
+        a.out_key = so.get<uint64_t>(cap);
+        a.out_run = so.get<int32_t>(cap);
+        a.out_cnt = so.get<int32_t>(cap);
+        a.out_nc = so.get<int32_t>(cap);
+        FOLTY_CUDA(cudaMemsetAsync(a.n_out, 0, sizeof(unsigned long long), s));
+        {
+            StageSpan span(ST_BATCH, s, (int64_t)k * (int64_t)sizeof(C) * mk + 4 * mk);
+            if (mk > 0) FOLTY_LAUNCH(k_batch_threshold<C>, (unsigned)blocks, BT_THREADS, 0, s, a);
+        }
+        n_out = read_i64(g, (const int64_t*)a.n_out, s);
+        if (n_out > cap) {  // the buffer was too small: run again with room for all
+            cap = n_out;
+            continue;
+        }
+        // sort by (query slot, pair rank); gather into per-query (u, v, count, ncert)
+        const int64_t n = n_out;
+        std::vector<int32_t> qstart((size_t)nq + 1, -1);
+        std::vector<int32_t> host;
+        const int32_t* packed_h = nullptr;
+        if (n > 0) {
+            uint64_t* kalt = so.get<uint64_t>(n);
+            uint32_t* v0 = so.get<uint32_t>(n);
+            uint32_t* v1 = so.get<uint32_t>(n);
+            int32_t* packed = so.get<int32_t>(4 * n + nq + 1);
+            int32_t* qs_dev = packed + 4 * n;
+            FOLTY_LAUNCH(k_iota_u32, grid_for(n, 256), 256, 0, s, v0, n);
+            const int bits = a.rb + bit_length((uint64_t)(nq > 1 ? nq - 1 : 1));
+            const bool alt = radix_sort_pairs(so, a.out_key, kalt, v0, v1, n, bits);
+            read_back(g, nullptr, nullptr, 0, nullptr, s);  // the sort's look-backs completed
+            const uint64_t* ks = alt ? kalt : a.out_key;
+            const uint32_t* ord = alt ? v1 : v0;
+            FOLTY_CUDA(cudaMemsetAsync(qs_dev, 0xff, sizeof(int32_t) * (size_t)(nq + 1), s));
+            FOLTY_LAUNCH(k_batch_gather, grid_for(n, 256), 256, 0, s, ks, ord, a.out_run, a.out_cnt, a.out_nc, g->ea,
+                         g->eb, n, a.rb, packed, qs_dev);
+            const size_t bytes = sizeof(int32_t) * (size_t)(4 * n + nq);
+            if (bytes <= sizeof(int32_t) * 4 * (size_t)PAIR_STAGE) {
+                g->stage_busy = 1;
+                FOLTY_CUDA(cudaMemcpyAsync(g->pair_stage, packed, bytes, cudaMemcpyDeviceToHost, s));
+                FOLTY_CUDA(cudaStreamSynchronize(s));
+                g->stage_busy = 0;
+                packed_h = (const int32_t*)(g->host_stage + HOST_STAGE);
+            } else {
+                host.resize(4 * (size_t)n + (size_t)nq);
+                FOLTY_CUDA(cudaMemcpyAsync(host.data(), packed, bytes, cudaMemcpyDeviceToHost, s));
+                FOLTY_CUDA(cudaStreamSynchronize(s));
+                packed_h = host.data();
+            }
+            std::memcpy(qstart.data(), packed_h + 4 * n, sizeof(int32_t) * (size_t)nq);
+        }
+        qstart[(size_t)nq] = (int32_t)n;
+        // the end of a slot's solutions is the next slot's start (slots without any are -1)
+        for (int i = nq - 1; i >= 0; i--) {
+            if (qstart[(size_t)i] < 0) qstart[(size_t)i] = qstart[(size_t)i + 1];
+        }
+        for (int i = 0; i < nq; i++) {
+            const int64_t b = qstart[(size_t)i], e = qstart[(size_t)i + 1], np = e - b;
+            folty_result* out = fo[(size_t)i];
+            fill_result_host(out, np, g->m, false, 0, false, 0, false);
+            int64_t ncert = 0;
+            if (np > 0) {
+                std::memcpy(out->u, packed_h + b, sizeof(int32_t) * (size_t)np);
+                std::memcpy(out->v, packed_h + n + b, sizeof(int32_t) * (size_t)np);
+                std::memcpy(out->count, packed_h + 2 * n + b, sizeof(int32_t) * (size_t)np);
+                std::memcpy(out->ncert, packed_h + 3 * n + b, sizeof(int32_t) * (size_t)np);
+                for (int64_t x = 0; x < np; x++) ncert += out->ncert[x];
+            }
+            out->n_cert_edges = ncert;
+        }
+        return;
+    }
+    fail(FOLTY_ECUDA, "batched threshold: the solution count grew between two passes over the same bins");
 }
 
 void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty_result* outs,
@@ -103,7 +536,7 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
         D.erase(std::unique(D.begin(), D.end()), D.end());
         // 16-bit bins while no count can reach 2^16 (a count is at most the number of
         // common neighbours of an edge's ends, at most the largest degree): half the
-        // memory traffic of the bins, their prefix and the threshold's column reads
+        // memory traffic of the bins and of the threshold's reads
         const bool b16 = g->info.max_degree < 65535;
         const int64_t per_bin = mk * (int64_t)(b16 ? sizeof(uint16_t) : sizeof(int32_t));
         const int64_t budget = bin_budget > 0 ? bin_budget : batch_bin_budget_bytes();
@@ -117,9 +550,9 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
             int64_t* dd = sc.get<int64_t>(k);
             std::vector<int64_t> hd(D.begin() + (long)c0, D.begin() + (long)c0 + k);
             // the bin bounds in the store's timestamp type (32-bit offsets: gaps stay
-            // below 2^32 - 1, so larger windows behave as 2^32 - 2)
-            // staged in the graph's pinned pair stage, which nothing uses before this
-            // chunk's threshold pass (the last chunk's read-back has completed)
+            // below 2^32 - 1, so larger windows behave as 2^32 - 2), staged in the graph's
+            // pinned pair stage, which nothing uses before this chunk's threshold pass
+            // (the last chunk's read-back has completed)
             void* hb = g->host_stage + HOST_STAGE;
             if (g->ts32) {
                 uint32_t* h32 = static_cast<uint32_t*>(hb);
@@ -134,22 +567,42 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
                 if (b16) FOLTY_CUDA(cudaMemsetAsync(bins16, 0, sizeof(uint16_t) * (size_t)(mk * k + 2), s));
                 else FOLTY_CUDA(cudaMemsetAsync(bins, 0, sizeof(int32_t) * (size_t)(mk * k), s));
                 if (P > 0) launch_probe_live(g, hd[k - 1], dir, 1, nullptr, bins, k, dd, s, nullptr, bins16);
-                if (k > 1 && b16) FOLTY_LAUNCH(k_bins_prefix<uint16_t>, grid_for(mk, 256), 256, 0, s, bins16, k, mk);
-                if (k > 1 && !b16) FOLTY_LAUNCH(k_bins_prefix<int32_t>, grid_for(mk, 256), 256, 0, s, bins, k, mk);
             }
-            std::vector<const folty_query_params*> fq;
+            // the chunk's queries: plain ones through the fused pass over the raw bins,
+            // the others through the single-query path over the prefix-summed bins
+            std::vector<const folty_query_params*> pq, fq;
+            std::vector<int> pj;
             std::vector<CountView> fc;
-            std::vector<folty_result*> fo;
+            std::vector<folty_result*> po, fo;
             for (int i : members) {
                 auto it = std::lower_bound(hd.begin(), hd.end(), qs[i].delta);
                 if (it == hd.end() || *it != qs[i].delta) continue;  // another chunk
                 const int j = (int)(it - hd.begin());
+                if (plain_query(qs[i])) {
+                    pq.push_back(&qs[i]);
+                    pj.push_back(j);
+                    po.push_back(&outs[i]);
+                    continue;
+                }
                 fq.push_back(&qs[i]);
                 if (b16) fc.push_back(CountView{nullptr, bins16 + (int64_t)j * mk});
                 else fc.push_back(CountView{bins + (int64_t)j * mk, nullptr});
                 fo.push_back(&outs[i]);
             }
-            finish_queries(g, fq.data(), fc.data(), (int)fq.size(), fo.data(), s);
+            for (size_t q0 = 0; q0 < pq.size(); q0 += BT_MAXQ) {
+                const size_t q1 = std::min(pq.size(), q0 + (size_t)BT_MAXQ);
+                std::vector<const folty_query_params*> gq(pq.begin() + (long)q0, pq.begin() + (long)q1);
+                std::vector<int> gj(pj.begin() + (long)q0, pj.begin() + (long)q1);
+                std::vector<folty_result*> go(po.begin() + (long)q0, po.begin() + (long)q1);
+                if (b16) fused_threshold<uint16_t>(g, bins16, k, gq, gj, go, s);
+                else fused_threshold<int32_t>(g, bins, k, gq, gj, go, s);
+            }
+            if (!fq.empty()) {
+                if (mk > 0 && k > 1 && b16)
+                    FOLTY_LAUNCH(k_bins_prefix<uint16_t>, grid_for(mk, 256), 256, 0, s, bins16, k, mk);
+                if (mk > 0 && k > 1 && !b16) FOLTY_LAUNCH(k_bins_prefix<int32_t>, grid_for(mk, 256), 256, 0, s, bins, k, mk);
+                finish_queries(g, fq.data(), fc.data(), (int)fq.size(), fo.data(), s);
+            }
         }
     }
 }

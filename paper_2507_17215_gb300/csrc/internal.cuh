@@ -167,14 +167,16 @@ struct folty_graph {
     int32_t* core;  // [n] core numbers of G_S     // [n] |N(u)|
     int32_t* common;  // [S] |N(a) cap N(b)| = triangles on the static edge
     int32_t* by_b;    // [S] static edge ids ordered by (b, a)
+    int32_t* prank;   // [2S] rank of directed pair 2s + d in (u, v) order (batched queries; made on first use)
     int64_t ntri;
     int4* tri;        // [ntri] {s_uv, s_uw, s_vw, id-order bits}, u < v < w in degeneracy rank
     int64_t* tri_off; // [ntri + 1] prefix of per-triangle probe counts
     int64_t* tile_tri;  // [probe tiles + 1] triangle holding each tile's first probe
     unsigned long long* prof_bytes;  // [PROF_SLOTS] device counters of probe-stage model bytes
     int prof_next;                   // next slot
-    int32_t* rsig;      // [6][ntri] |L1| of every role (role r = 2 * edge + direction)
-    uint8_t* rmin;      // [3][6][ntri] bucket of the smallest window a role can hit with
+    void* run_ends;     // [S] first and last timestamp and size of both runs of every static edge
+    uint8_t* tlive;     // [3][tlive_stride] per direction variant, the smallest window bucket of a triangle's roles
+    int64_t tlive_stride;
     int64_t n_tiles;
     int64_t enum_bytes; // model bytes of the triangle enumeration
     int64_t tmin, tmax; // timestamp range of the input
@@ -293,7 +295,8 @@ void launch_probe(folty_graph* g, int64_t delta, int dir, int32_t* cnt, cudaStre
 // rflag (mode 0, may be null): byte 6 * triangle + role set to 1 when the role has a hit.
 void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t* cnt, int32_t* bins, int k,
                        const void* deltas, cudaStream_t s, uint8_t* rflag = nullptr, uint16_t* bins16 = nullptr);
-void build_role_summary(folty_graph* g, cudaStream_t s);
+// Run-ends table and per-triangle liveness bytes (live.cu).
+void build_liveness(folty_graph* g, cudaStream_t s);
 // Kept roles, probes and model bytes of one query's selection (live.cu; synchronises).
 void probe_stats(folty_graph* g, int64_t delta, int dir, folty_probe_stats* out, cudaStream_t s);
 // The same pass with the counters in a file-scope device array (noalloc.cu).

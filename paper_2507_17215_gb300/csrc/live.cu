@@ -7,14 +7,16 @@
 // two conditions do not depend on delta; the last two hold exactly when
 // delta >= dmin = max(0, L2.first - L1.last, L3.first - L1.last).
 //
-// Preprocessing stores, per triangle and role, sigma1 = |L1| and a conservative bucket of
-// dmin per direction variant: its bit length b (0 for dmin = 0, 255 for "never"), so
-// 2^(b-1) <= dmin. A query keeps a role when delta >= 2^(b-1), which holds whenever
-// delta >= dmin: no role that can hit is dropped (a few that cannot are kept). Each
-// query then lists the triangles with a kept role, lays their kept roles out in a flat
-// probe space (3 idle slots per triangle keep the tile staging bound) and probes only
-// those, with the exact window test of Theorem 3.1. On the synthetic workloads about
-// 1-7 % of all (edge, witness) pairs lie in kept roles.
+// A role's bucket is a conservative form of dmin for one direction variant: its bit
+// length b (0 for dmin = 0, 255 for "never"), so 2^(b-1) <= dmin. A query keeps a role
+// when delta >= 2^(b-1), which holds whenever delta >= dmin: no role that can hit is
+// dropped (a few that cannot are kept). Preprocessing stores the first and last
+// timestamp and the size of every run (the run-ends table) and, per triangle and
+// direction variant, the smallest bucket of its six roles (one byte). A query reads that
+// byte for every triangle; only the triangles it keeps (typically a few in ten thousand)
+// get their six roles' buckets and sizes from the run-ends table. It then lays the kept
+// roles out in a flat probe space (3 idle slots per triangle keep the tile staging bound)
+// and probes only those, with the exact window test of Theorem 3.1.
 #include "internal.cuh"
 #include "probe.cuh"
 #include "scan.cuh"
@@ -43,37 +45,24 @@ __device__ __forceinline__ bool span_of(const int64_t* f, const int64_t* l, cons
     return any;
 }
 
-// The eighteen (role, direction variant) buckets of one triangle whose local vertices
-// 0, 1, 2 are in id order (flags = 7, so that every run index below is a constant). The
-// caller relabels each triangle into that frame; role 2k + d of the frame is role
-// 2 oe[k] + d of the triangle as stored.
-__device__ __forceinline__ void role_buckets_sorted(const int64_t* f, const int64_t* l, const bool* ne,
-                                                    const int* oe, int64_t t, int64_t ntri,
-                                                    uint8_t* __restrict__ rmin) {
-#pragma unroll
-    for (int r = 0; r < 6; r++) {
-        const int64_t row = 2 * oe[r >> 1] + (r & 1);
-#pragma unroll
-        for (int dir = 0; dir < 3; dir++) {
-            uint8_t bucket = DMIN_NEVER;
-            if (ne[r]) {
-                int s2, s3;
-                role_segments(7, r >> 1, r & 1, dir, s2, s3);
-                const bool both = dir == FOLTY_DIR_EITHER;  // s2, s3 are the d = 0 runs then
-                int64_t f2 = 0, l2 = 0, f3 = 0, l3 = 0;
-                const bool a2 = span_of(f, l, ne, s2, both ? s2 + 1 : -1, f2, l2);
-                const bool a3 = span_of(f, l, ne, s3, both ? s3 + 1 : -1, f3, l3);
-                const int64_t f1 = f[r], l1 = l[r];
-                if (a2 && a3 && l2 >= f1 && l3 >= (f2 > f1 ? f2 : f1)) {
-                    int64_t dmin = f2 - l1;
-                    if (f3 - l1 > dmin) dmin = f3 - l1;
-                    if (dmin < 0) dmin = 0;
-                    bucket = (uint8_t)(64 - __clzll((unsigned long long)dmin));  // 0 for dmin = 0
-                }
-            }
-            rmin[((int64_t)dir * 6 + row) * ntri + t] = bucket;
-        }
-    }
+// Bucket of role r (= 2k + d: direction d of frame edge k) for direction variant DIR, of
+// a triangle whose local vertices 0, 1, 2 are in id order (flags = 7, so that every run
+// index below is a constant), from the first and last timestamps of its six runs.
+template <int DIR>
+__device__ __forceinline__ uint8_t frame_bucket(const int64_t* f, const int64_t* l, const bool* ne, int r) {
+    if (!ne[r]) return DMIN_NEVER;
+    int s2, s3;
+    role_segments(7, r >> 1, r & 1, DIR, s2, s3);
+    const bool both = DIR == FOLTY_DIR_EITHER;  // s2, s3 are the d = 0 runs then
+    int64_t f2 = 0, l2 = 0, f3 = 0, l3 = 0;
+    const bool a2 = span_of(f, l, ne, s2, both ? s2 + 1 : -1, f2, l2);
+    const bool a3 = span_of(f, l, ne, s3, both ? s3 + 1 : -1, f3, l3);
+    const int64_t f1 = f[r], l1 = l[r];
+    if (!(a2 && a3 && l2 >= f1 && l3 >= (f2 > f1 ? f2 : f1))) return DMIN_NEVER;
+    int64_t dmin = f2 - l1;
+    if (f3 - l1 > dmin) dmin = f3 - l1;
+    if (dmin < 0) dmin = 0;
+    return (uint8_t)(64 - __clzll((unsigned long long)dmin));  // 0 for dmin = 0
 }
 
 // First and last timestamp and size of both runs of one static edge (direction 0 =
@@ -101,45 +90,66 @@ __global__ void k_run_ends(const int32_t* __restrict__ seg, int64_t S, const TS*
     }
 }
 
-// rsig[r][t] = sigma1 of role r = 2e + d; rmin[dir][r][t] = dmin bucket. Each triangle
-// is relabelled so that its local vertices are in id order (a rank per vertex from the
-// three id-order bits); its three static edges are then read from the run-ends table in
-// that frame, one aligned record each, and every thread runs the same code whatever the
-// triangle's id order.
+// The six runs of triangle tr in its id-order frame: the triangle is relabelled so that
+// its local vertices are in id order (a rank per vertex from the three id-order bits);
+// its three static edges are then read from the run-ends table in that frame, one
+// aligned record each, so that every thread runs the same code whatever the triangle's
+// id order. oe[k] = the stored edge (0: s_uv, 1: s_uw, 2: s_vw) that is frame edge k.
 template <typename TS>
-__global__ void k_role_summary(const int4* __restrict__ tri, int64_t ntri, const RunEnds<TS>* __restrict__ ends,
-                               int32_t* __restrict__ rsig, uint8_t* __restrict__ rmin) {
+struct FrameRuns {
+    int64_t f[6], l[6];
+    int32_t n[6];
+    bool ne[6];
+    int oe[3];
+};
+
+template <typename TS>
+__device__ __forceinline__ void frame_runs(const int4 tr, const RunEnds<TS>* __restrict__ ends, FrameRuns<TS>& fr) {
+    const int b0 = tr.w & 1, b1 = (tr.w >> 1) & 1, b2 = (tr.w >> 2) & 1;
+    // rank of each local vertex among the three ids
+    const int rk0 = (b0 ^ 1) + (b1 ^ 1), rk1 = b0 + (b2 ^ 1), rk2 = b1 + b2;
+    // stored edge e joins local vertices (0,1), (0,2), (1,2); in the sorted frame it
+    // joins ranks (rk_p, rk_q), i.e. frame edge rk_p + rk_q - 1
+    const int k0 = rk0 + rk1 - 1, k1 = rk0 + rk2 - 1;
+    int32_t se[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        fr.oe[k] = (k == k0) ? 0 : (k == k1) ? 1 : 2;
+        se[k] = (k == k0) ? tr.x : (k == k1) ? tr.y : tr.z;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const RunEnds<TS> re = ends[se[k]];
+        fr.n[2 * k] = re.n0;
+        fr.n[2 * k + 1] = re.n1;
+        fr.ne[2 * k] = re.n0 > 0;
+        fr.ne[2 * k + 1] = re.n1 > 0;
+        fr.f[2 * k] = (int64_t)re.f0;
+        fr.l[2 * k] = (int64_t)re.l0;
+        fr.f[2 * k + 1] = (int64_t)re.f1;
+        fr.l[2 * k + 1] = (int64_t)re.l1;
+    }
+}
+
+// tlive[dir][t] = the smallest bucket of the six roles of triangle t for direction
+// variant dir (DMIN_NEVER when none can hit at any window). Rows are tstride bytes apart.
+template <typename TS>
+__global__ void k_tri_live(const int4* __restrict__ tri, int64_t ntri, const RunEnds<TS>* __restrict__ ends,
+                           int64_t tstride, uint8_t* __restrict__ tlive) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntri;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int4 tr = tri[t];
-        const int b0 = tr.w & 1, b1 = (tr.w >> 1) & 1, b2 = (tr.w >> 2) & 1;
-        // rank of each local vertex among the three ids
-        const int rk0 = (b0 ^ 1) + (b1 ^ 1), rk1 = b0 + (b2 ^ 1), rk2 = b1 + b2;
-        // stored edge e joins local vertices (0,1), (0,2), (1,2); in the sorted frame it
-        // joins ranks (rk_p, rk_q), i.e. frame edge rk_p + rk_q - 1
-        const int k0 = rk0 + rk1 - 1, k1 = rk0 + rk2 - 1;
-        int oe[3];
-        int32_t se[3];
+        FrameRuns<TS> fr;
+        frame_runs<TS>(tri[t], ends, fr);
+        uint8_t m0 = DMIN_NEVER, m1 = DMIN_NEVER, m2 = DMIN_NEVER;
 #pragma unroll
-        for (int k = 0; k < 3; k++) {
-            oe[k] = (k == k0) ? 0 : (k == k1) ? 1 : 2;
-            se[k] = (k == k0) ? tr.x : (k == k1) ? tr.y : tr.z;
+        for (int r = 0; r < 6; r++) {
+            m0 = min(m0, frame_bucket<FOLTY_DIR_OUT>(fr.f, fr.l, fr.ne, r));
+            m1 = min(m1, frame_bucket<FOLTY_DIR_IN>(fr.f, fr.l, fr.ne, r));
+            m2 = min(m2, frame_bucket<FOLTY_DIR_EITHER>(fr.f, fr.l, fr.ne, r));
         }
-        int64_t f[6], l[6];
-        bool ne[6];
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            const RunEnds<TS> re = ends[se[k]];
-            ne[2 * k] = re.n0 > 0;
-            ne[2 * k + 1] = re.n1 > 0;
-            f[2 * k] = (int64_t)re.f0;
-            l[2 * k] = (int64_t)re.l0;
-            f[2 * k + 1] = (int64_t)re.f1;
-            l[2 * k + 1] = (int64_t)re.l1;
-            rsig[(int64_t)(2 * oe[k]) * ntri + t] = re.n0;
-            rsig[(int64_t)(2 * oe[k] + 1) * ntri + t] = re.n1;
-        }
-        role_buckets_sorted(f, l, ne, oe, t, ntri, rmin);
+        tlive[t] = m0;
+        tlive[tstride + t] = m1;
+        tlive[2 * tstride + t] = m2;
     }
 }
 
@@ -147,20 +157,46 @@ __device__ __forceinline__ bool bucket_live(uint8_t b, int64_t delta) {
     return b != DMIN_NEVER && (b == 0 || delta >= ((int64_t)1 << (b - 1)));
 }
 
+// Role mask (stored role order: bit 2e + d = direction d of stored edge e) and kept
+// probes of triangle tr at window delta for direction variant DIR.
+template <typename TS, int DIR>
+__device__ __forceinline__ int kept_roles_of(const int4 tr, const RunEnds<TS>* __restrict__ ends, int64_t delta,
+                                             int64_t& probes) {
+    FrameRuns<TS> fr;
+    frame_runs<TS>(tr, ends, fr);
+    int m = 0;
+    int64_t c = 0;
+#pragma unroll
+    for (int r = 0; r < 6; r++) {
+        if (bucket_live(frame_bucket<DIR>(fr.f, fr.l, fr.ne, r), delta)) {  // never for an empty run
+            m |= 1 << (2 * fr.oe[r >> 1] + (r & 1));
+            c += fr.n[r];
+        }
+    }
+    probes = c;
+    return m;
+}
+
 // Kept roles of every triangle for one query, selected and compacted in one pass: kept
 // triangle j = L[j] with its role mask lmask[j] and its first probe slot loff[j] (prefix
 // of the kept triangles' costs = kept probes + LIVE_IDLE idle slots); totals[0] = kept
 // triangles, totals[1] = slots, loff[totals[0]] = totals[1]; and the probe tiles' map:
 // ltile[b] = kept triangle holding slot min(b * PB_TILE, slots - 1) for b <= the number
-// of probe tiles (each kept triangle writes the tile starts inside its slots). Tiles of
-// LS_TILE triangles are taken in block start order; the two prefix sums (kept count,
-// cost) come from a block scan and two decoupled look-backs by warp 0. *prof (may be
-// null) gets the bytes written for the kept triangles.
-constexpr int LS_ITEMS = 8;
-constexpr int LS_TILE = SCAN_THREADS * LS_ITEMS;  // 2048 triangles
+// of probe tiles (each kept triangle writes the tile starts inside its slots). A thread
+// takes LS_ITEMS consecutive triangles and reads their liveness bytes (tlive, the
+// smallest bucket of each triangle's roles for this direction variant) with two 16-byte
+// loads; only the triangles whose byte admits delta read their record and run ends, once
+// to count and once to write (they are few). Tiles of LS_TILE triangles are taken in
+// block start order; the two prefix sums (kept count, cost) come from a block scan and
+// two decoupled look-backs by warp 0. *prof (may be null) gets the bytes read and written
+// for the kept triangles.
+constexpr int LS_ITEMS = 32;
+constexpr int LS_TILE = SCAN_THREADS * LS_ITEMS;  // 8192 triangles
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const int32_t* __restrict__ rsig,
-                                                              const uint8_t* __restrict__ rmin_dir, int64_t ntri,
+template <typename TS, int DIR>
+__global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const uint8_t* __restrict__ tlive,
+                                                              const int4* __restrict__ tri,
+                                                              const RunEnds<TS>* __restrict__ ends, int64_t ntri,
                                                               int64_t delta, unsigned long long* lbc,
                                                               unsigned long long* lbp, unsigned int* counter,
                                                               int* err, int32_t* __restrict__ L,
@@ -168,63 +204,39 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const int32_t* __r
                                                               int64_t* __restrict__ totals,
                                                               int64_t* __restrict__ ltile, int64_t max_tiles,
                                                               unsigned long long* __restrict__ prof) {
-    constexpr int PADW = 16;  // one pad element per 128 bytes of int64
-    __shared__ int64_t scost[LS_TILE + LS_TILE / PADW];
-    __shared__ uint8_t smask[LS_TILE];
     __shared__ int32_t wc[SCAN_THREADS / 32];
     __shared__ int64_t wp[SCAN_THREADS / 32];
     __shared__ int32_t totc;
     __shared__ int64_t totp;
     __shared__ unsigned long long s_exc, s_exp;
     __shared__ int64_t s_tile;
-    auto pad = [](int i) { return i + i / PADW; };
     if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(counter, 1u);
     __syncthreads();
     const int64_t tile = s_tile;
     const int64_t base = tile * LS_TILE;
-    // ---- the kept roles, in coalesced order; every load of a thread is issued before any
-    // of them is used (the byte of a role is read whether or not its sigma1 is zero), so
-    // that a thread waits for memory once per group of items rather than once per role
-    constexpr int LS_GROUP = 4;
+    const int64_t t0 = base + (int64_t)threadIdx.x * LS_ITEMS;
+    // ---- the thread's liveness bytes (rows are padded with DMIN_NEVER to whole 16-byte
+    // chunks) as a bit mask of the triangles whose byte admits delta
+    uint32_t lm = 0;
 #pragma unroll
-    for (int i0 = 0; i0 < LS_ITEMS; i0 += LS_GROUP) {
-        int32_t s1[LS_GROUP][6];
-        uint8_t bk[LS_GROUP][6];
+    for (int h = 0; h < LS_ITEMS / 16; h++) {
+        uint4 w = make_uint4(~0u, ~0u, ~0u, ~0u);
+        if (t0 + 16 * h < ntri) w = __ldcs(reinterpret_cast<const uint4*>(tlive + t0 + 16 * h));
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-        for (int i = 0; i < LS_GROUP; i++) {
-            const int64_t t = base + (i0 + i) * SCAN_THREADS + threadIdx.x;
-#pragma unroll
-            for (int r = 0; r < 6; r++) {
-                s1[i][r] = t < ntri ? __ldcs(&rsig[r * ntri + t]) : 0;
-                bk[i][r] = t < ntri ? __ldcs(&rmin_dir[r * ntri + t]) : 0;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < LS_GROUP; i++) {
-            const int idx = (i0 + i) * SCAN_THREADS + threadIdx.x;
-            int m = 0;
-            int64_t lp = 0;
-#pragma unroll
-            for (int r = 0; r < 6; r++) {
-                if (s1[i][r] > 0 && bucket_live(bk[i][r], delta)) {
-                    m |= 1 << r;
-                    lp += s1[i][r];
-                }
-            }
-            scost[pad(idx)] = lp > 0 ? lp + LIVE_IDLE : 0;
-            smask[idx] = (uint8_t)m;
-        }
+        for (int i = 0; i < 16; i++)
+            if (bucket_live((uint8_t)(ws[i >> 2] >> (8 * (i & 3))), delta)) lm |= 1u << (16 * h + i);
     }
-    __syncthreads();
-    // ---- thread sums over LS_ITEMS consecutive triangles, block scans, look-backs
     int32_t c = 0;
     int64_t cs = 0;
-#pragma unroll
-    for (int i = 0; i < LS_ITEMS; i++) {
-        const int64_t v = scost[pad(threadIdx.x * LS_ITEMS + i)];
-        c += v > 0;
-        cs += v;
+    for (uint32_t x = lm; x; x &= x - 1) {
+        const int64_t t = t0 + __ffs(x) - 1;
+        int64_t pr;
+        kept_roles_of<TS, DIR>(tri[t], ends, delta, pr);
+        c++;
+        cs += pr + LIVE_IDLE;
     }
+    // ---- block scans, look-backs
     const int32_t offc = block_exclusive_sum<int32_t>(c, wc, &totc);
     const int64_t offp = block_exclusive_sum<int64_t>(cs, wp, &totp);
     if (threadIdx.x < 32) {
@@ -254,18 +266,17 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const int32_t* __r
     __syncthreads();
     // ---- the kept triangles of this thread's run
     int64_t jc = (int64_t)s_exc + offc, jp = (int64_t)s_exp + offp;
-#pragma unroll
-    for (int i = 0; i < LS_ITEMS; i++) {
-        const int item = threadIdx.x * LS_ITEMS + i;
-        const int64_t v = scost[pad(item)];
-        if (v > 0) {
-            L[jc] = (int32_t)(base + item);
-            loff[jc] = jp;
-            lmask[jc] = smask[item];
-            for (int64_t b = (jp + PB_TILE - 1) / PB_TILE; b * PB_TILE < jp + v && b <= max_tiles; b++) ltile[b] = jc;
-            jc++;
-            jp += v;
-        }
+    for (uint32_t x = lm; x; x &= x - 1) {
+        const int64_t t = t0 + __ffs(x) - 1;
+        int64_t pr;
+        const int m = kept_roles_of<TS, DIR>(tri[t], ends, delta, pr);
+        const int64_t v = pr + LIVE_IDLE;
+        L[jc] = (int32_t)t;
+        loff[jc] = jp;
+        lmask[jc] = (uint8_t)m;
+        for (int64_t b = (jp + PB_TILE - 1) / PB_TILE; b * PB_TILE < jp + v && b <= max_tiles; b++) ltile[b] = jc;
+        jc++;
+        jp += v;
     }
     if (base + LS_TILE >= ntri && threadIdx.x == 0) {
         const int64_t nl = (int64_t)s_exc + totc, P = (int64_t)s_exp + totp;
@@ -274,7 +285,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const int32_t* __r
         loff[nl] = P;
         const int64_t tiles = (P + PB_TILE - 1) / PB_TILE;
         if (P > 0 && tiles <= max_tiles) ltile[tiles] = nl - 1;
-        if (prof) atomicAdd(prof, (unsigned long long)(13 * nl));
+        if (prof) atomicAdd(prof, (unsigned long long)((16 + 3 * sizeof(RunEnds<TS>) + 13) * nl));
     }
 }
 
@@ -417,25 +428,31 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS*
 // ------------------------------------------------------------------ host side
 
 template <typename TS>
-static void role_summary_t(folty_graph* g, cudaStream_t s) {
+static void liveness_t(folty_graph* g, cudaStream_t s) {
     const int64_t S = g->S, ntri = g->ntri;
-    Scratch sc(g->alloc, s, g->dev_err);
-    RunEnds<TS>* ends = sc.get<RunEnds<TS>>(S);
-    // per static edge: 12 B of run bounds and 4 timestamps read, a 32 B record written and
-    // read back once more (the table stays in L2); per triangle: 16 B read, 24 B of sigma1
-    // and 18 B of buckets written
-    StageSpan span(ST_ROLES, s, S * (12 + 4 * (int64_t)sizeof(TS) + 64) + 58 * ntri);
-    FOLTY_LAUNCH(k_run_ends<TS>, grid_for(S, 256), 256, 0, s, g->seg, S, (const TS*)g->T, ends);
-    FOLTY_LAUNCH(k_role_summary<TS>, grid_for(ntri, 256), 256, 0, s, g->tri, ntri, ends, g->rsig, g->rmin);
+    RunEnds<TS>* ends = static_cast<RunEnds<TS>*>(g->run_ends);
+    // per static edge: 12 B of run bounds and 4 timestamps read, its record written; per
+    // triangle: 16 B read, one byte per direction variant written (the run-ends table is
+    // read back from L2)
+    StageSpan span(ST_ROLES, s, S * (12 + 4 * (int64_t)sizeof(TS) + (int64_t)sizeof(RunEnds<TS>)) + 19 * ntri);
+    if (S > 0) FOLTY_LAUNCH(k_run_ends<TS>, grid_for(S, 256), 256, 0, s, g->seg, S, (const TS*)g->T, ends);
+    if (ntri > 0)
+        FOLTY_LAUNCH(k_tri_live<TS>, grid_for(ntri, 256), 256, 0, s, g->tri, ntri, ends, g->tlive_stride, g->tlive);
 }
 
-void build_role_summary(folty_graph* g, cudaStream_t s) {
+void build_liveness(folty_graph* g, cudaStream_t s) {
     const int64_t ntri = g->ntri;
-    g->rsig = graph_alloc<int32_t>(g, 6 * ntri, s);
-    g->rmin = graph_alloc<uint8_t>(g, 18 * ntri, s);
-    if (ntri == 0) return;
-    if (g->ts32) role_summary_t<uint32_t>(g, s);
-    else role_summary_t<int64_t>(g, s);
+    g->run_ends = g->ts32 ? (void*)graph_alloc<RunEnds<uint32_t>>(g, g->S, s)
+                          : (void*)graph_alloc<RunEnds<int64_t>>(g, g->S, s);
+    // three rows of liveness bytes, each padded with DMIN_NEVER to whole 16-byte chunks
+    g->tlive_stride = (ntri + 15) & ~int64_t(15);
+    g->tlive = graph_alloc<uint8_t>(g, 3 * g->tlive_stride, s);
+    for (int d = 0; d < 3; d++)
+        if (g->tlive_stride > ntri)
+            FOLTY_CUDA(cudaMemsetAsync(g->tlive + d * g->tlive_stride + ntri, DMIN_NEVER,
+                                       (size_t)(g->tlive_stride - ntri), s));
+    if (g->ts32) liveness_t<uint32_t>(g, s);
+    else liveness_t<int64_t>(g, s);
 }
 
 template <typename TS, int MODE>
@@ -460,8 +477,26 @@ struct LiveSel {
     int64_t max_tiles;
 };
 
+template <typename TS>
+static void launch_select_t(const folty_graph* g, int dir, const uint8_t* tl, int64_t delta,
+                            unsigned long long* lsctl, int64_t stiles, int* err, const LiveSel& ls,
+                            unsigned long long* prof, cudaStream_t s) {
+    const RunEnds<TS>* ends = static_cast<const RunEnds<TS>*>(g->run_ends);
+    const int64_t ntri = g->ntri;
+#define FOLTY_SELECT_ARGS                                                                                          \
+    tl, g->tri, ends, ntri, delta, lsctl + 1, lsctl + 1 + stiles, (unsigned int*)lsctl, err, ls.L, ls.loff, ls.lmask, \
+        ls.totals, ls.ltile, ls.max_tiles, prof
+    if (dir == FOLTY_DIR_OUT)
+        FOLTY_LAUNCH((k_live_select<TS, FOLTY_DIR_OUT>), (unsigned)stiles, SCAN_THREADS, 0, s, FOLTY_SELECT_ARGS);
+    else if (dir == FOLTY_DIR_IN)
+        FOLTY_LAUNCH((k_live_select<TS, FOLTY_DIR_IN>), (unsigned)stiles, SCAN_THREADS, 0, s, FOLTY_SELECT_ARGS);
+    else
+        FOLTY_LAUNCH((k_live_select<TS, FOLTY_DIR_EITHER>), (unsigned)stiles, SCAN_THREADS, 0, s, FOLTY_SELECT_ARGS);
+#undef FOLTY_SELECT_ARGS
+}
+
 // Selects the roles kept for delta (buffers from sc). prof_sel (may be null) receives the
-// selection's written bytes.
+// selection's model bytes beyond its one byte per triangle.
 static LiveSel select_live(folty_graph* g, int64_t delta, int dir, Scratch& sc, cudaStream_t s,
                            unsigned long long* prof_sel) {
     const int64_t ntri = g->ntri;
@@ -474,11 +509,11 @@ static LiveSel select_live(folty_graph* g, int64_t delta, int dir, Scratch& sc, 
     ls.ltile = sc.get<int64_t>(ls.max_tiles + 2);
     const int64_t stiles = (ntri + LS_TILE - 1) / LS_TILE;
     unsigned long long* lsctl = sc.get<unsigned long long>(2 * stiles + 1);  // tile counter, two look-backs
-    StageSpan span(ST_SELECT, s, 30 * ntri, prof_sel);
+    StageSpan span(ST_SELECT, s, ntri, prof_sel);
     FOLTY_CUDA(cudaMemsetAsync(lsctl, 0, sizeof(unsigned long long) * (size_t)(2 * stiles + 1), s));
-    FOLTY_LAUNCH(k_live_select, (unsigned)stiles, SCAN_THREADS, 0, s, g->rsig, g->rmin + (int64_t)dir * 6 * ntri, ntri,
-                 delta, lsctl + 1, lsctl + 1 + stiles, (unsigned int*)lsctl, sc.err(), ls.L, ls.loff, ls.lmask,
-                 ls.totals, ls.ltile, ls.max_tiles, prof_sel);
+    const uint8_t* tl = g->tlive + (int64_t)dir * g->tlive_stride;
+    if (g->ts32) launch_select_t<uint32_t>(g, dir, tl, delta, lsctl, stiles, sc.err(), ls, prof_sel, s);
+    else launch_select_t<int64_t>(g, dir, tl, delta, lsctl, stiles, sc.err(), ls, prof_sel, s);
     return ls;
 }
 
@@ -489,9 +524,9 @@ void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t
     const int64_t ntri = g->ntri;
     if (ntri == 0 || g->info.probes == 0) return;
     Scratch sc(g->alloc, s, g->dev_err);
-    // model bytes counted on the device: the selection reads 30 B per triangle (6 sigma1,
-    // 6 buckets) and writes 13 B per kept one; the probes' bytes per staged triangle and
-    // kept role are summed by the probe kernel
+    // model bytes counted on the device: the selection reads one liveness byte per
+    // triangle, and per kept one its record and run ends, and writes 13 B; the probes'
+    // bytes per staged triangle and kept role are summed by the probe kernel
     unsigned long long* prof_sel = nullptr;
     unsigned long long* prof = nullptr;
     if (profiling_on()) {
@@ -575,7 +610,7 @@ void probe_stats(folty_graph* g, int64_t delta, int dir, folty_probe_stats* out,
     out->triangles = g->ntri;
     out->all_roles = 6 * g->ntri;
     out->all_probes = g->info.probes;  // every (temporal edge, witness) pair
-    out->select_bytes = 30 * g->ntri;
+    out->select_bytes = g->ntri;
     if (g->ntri == 0 || g->info.probes == 0) return;
     Scratch sc(g->alloc, s, g->dev_err);
     const LiveSel ls = select_live(g, delta, dir, sc, s, nullptr);
@@ -591,7 +626,7 @@ void probe_stats(folty_graph* g, int64_t delta, int dir, folty_probe_stats* out,
     out->kept_roles = v[1];
     out->kept_probes = v[2];
     out->probe_bytes = v[3];
-    out->select_bytes += 13 * v[0];
+    out->select_bytes += (int64_t)(16 + 3 * (g->ts32 ? sizeof(RunEnds<uint32_t>) : sizeof(RunEnds<int64_t>)) + 13) * v[0];
 }
 
 }  // namespace folty

@@ -52,14 +52,20 @@ __device__ __forceinline__ uint32_t pair_slot_word(uint64_t* table, int lg, int3
 }
 
 // log2 of the table's largest size for m edges (at least 2m slots, up to 2^23) and of
-// its first try (at most 2^21 slots: 16 MB, which stays in L2, and up to a million
-// distinct pairs).
+// its first try: at least m / 12 slots (room for m / 24 distinct pairs at a load factor
+// of 1/2, i.e. a mean multiplicity of 24 or more, as in the workloads' Zipf
+// multiplicities), at most 2^22 slots (32 MB, which stays in L2).
 inline int pair_table_lg_max(int64_t m) {
     int b = 0;
     for (uint64_t v = (uint64_t)(2 * m - 1); v; v >>= 1) b++;
     return b < 10 ? 10 : (b > 23 ? 23 : b);
 }
-inline int pair_table_lg_first(int64_t m) { return pair_table_lg_max(m) < 21 ? pair_table_lg_max(m) : 21; }
+inline int pair_table_lg_first(int64_t m) {
+    int b = 0;
+    for (uint64_t v = (uint64_t)((m + 11) / 12); v; v >>= 1) b++;
+    b = b < 10 ? 10 : (b > 22 ? 22 : b);
+    return pair_table_lg_max(m) < b ? pair_table_lg_max(m) : b;
+}
 
 // The dense-id path is off when FOLTY_PAIR_SORT=keys (the full-key sort then runs).
 inline bool pair_table_forced_off() {

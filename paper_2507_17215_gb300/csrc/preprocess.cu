@@ -2557,7 +2557,7 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     if (g->info.probes > 0)
         FOLTY_LAUNCH(k_tile_starts, grid_for(g->n_tiles + 1, T), T, 0, s, g->tri_off, ntri, g->info.probes,
                      g->n_tiles, PB_TILE, g->tile_tri);
-    build_role_summary(g, s);
+    build_liveness(g, s);
     g->prof_bytes = graph_alloc<unsigned long long>(g, PROF_SLOTS, s);
     g->info.static_edges = S;
     g->state = 1;
