@@ -177,8 +177,7 @@ __global__ void k_read_back(const __grid_constant__ ReadbackArgs a) {
     if (threadIdx.x == 0) *a.herr = a.dev_err ? *a.dev_err : 0;
 }
 
-void read_back(folty_graph* g, const void* const* dev_ptrs, const int* sizes, int count, int64_t* out,
-               cudaStream_t s) {
+void enqueue_read_back(folty_graph* g, const void* const* dev_ptrs, const int* sizes, int count, cudaStream_t s) {
     if (count > READBACK_MAX) fail(FOLTY_EINVAL, "read_back: too many values");
     ReadbackArgs a;
     for (int i = 0; i < count; i++) {
@@ -192,13 +191,22 @@ void read_back(folty_graph* g, const void* const* dev_ptrs, const int* sizes, in
     a.herr = (int32_t*)(g->stage_dev + ERR_SLOT);
     g->stage_busy = 1;
     FOLTY_LAUNCH(k_read_back, 1, 128, 0, s, a);
-    FOLTY_CUDA(cudaStreamSynchronize(s));
+}
+
+void collect_read_back(folty_graph* g, int count, int64_t* out, cudaStream_t s) {
     g->stage_busy = 0;
     if (*(volatile int32_t*)(g->host_stage + ERR_SLOT)) {
         FOLTY_CUDA(cudaMemsetAsync(g->dev_err, 0, sizeof(int32_t), s));
         fail(FOLTY_ETIMEOUT, "a bounded wait in a device look-back ran out; the results of this call are void");
     }
     for (int i = 0; i < count; i++) out[i] = ((volatile int64_t*)g->host_stage)[i];
+}
+
+void read_back(folty_graph* g, const void* const* dev_ptrs, const int* sizes, int count, int64_t* out,
+               cudaStream_t s) {
+    enqueue_read_back(g, dev_ptrs, sizes, count, s);
+    FOLTY_CUDA(cudaStreamSynchronize(s));
+    collect_read_back(g, count, out, s);
 }
 
 int64_t read_i64(folty_graph* g, const int64_t* p, cudaStream_t s) {
@@ -315,6 +323,7 @@ static void stage_give(int64_t* p, bool busy) {
 }
 
 static void free_graph(folty_graph* g) {
+    destroy_plans(g);
     if (g->owned) {
         for (auto& o : *g->owned) g->alloc.put(o.first, 0);
         delete g->owned;

@@ -520,6 +520,12 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
                      cudaStream_t s, int64_t bin_budget) {
     const int64_t mk = g->m_kept;
     const int64_t P = g->info.probes;
+    // a batch of one (a server's batch under light load) is a single query: its captured
+    // launch sequence is the shortest path
+    if (nq == 1) {
+        run_query(g, qs[0], &outs[0], s);
+        return;
+    }
     // a query that also wants the all-existential triples needs its own probe pass (the
     // role flags are per window, not per bin)
     for (int i = 0; i < nq; i++)

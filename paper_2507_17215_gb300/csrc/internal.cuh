@@ -131,7 +131,7 @@ constexpr uint64_t GRAPH_TAG = 0x464f4c5459475248ull;   // "FOLTYGRH"
 constexpr uint64_t RESULT_TAG = 0x464f4c5459525354ull;  // "FOLTYRST"
 constexpr uint64_t FREED_TAG = 0x464f4c5459465245ull;   // "FOLTYFRE"
 
-struct DeviceArrays;  // defined below
+struct QueryPlans;  // query.cu
 
 }  // namespace folty
 
@@ -189,6 +189,7 @@ struct folty_graph {
     int stage_busy;       // an asynchronous copy into or out of host_stage may be pending
     int* dev_err;         // device error word: a bounded wait in a kernel ran out
     std::vector<std::pair<void*, size_t>>* owned;  // device buffers owned by the graph
+    folty::QueryPlans* plans;  // captured launch sequences of plain queries (query.cu), made on first use
 };
 
 namespace folty {
@@ -211,6 +212,11 @@ void graph_release(folty_graph* g, void* p, cudaStream_t s);
 // FOLTY_ETIMEOUT before any value is used. count may be 0 (a plain check).
 void read_back(folty_graph* g, const void* const* dev_ptrs, const int* sizes, int count,
                int64_t* out, cudaStream_t s);
+// The two halves of read_back: the gathering launch (no synchronisation; capturable in
+// a CUDA graph), and, after the caller synchronised the stream, the error check and the
+// values.
+void enqueue_read_back(folty_graph* g, const void* const* dev_ptrs, const int* sizes, int count, cudaStream_t s);
+void collect_read_back(folty_graph* g, int count, int64_t* out, cudaStream_t s);
 int64_t read_i64(folty_graph* g, const int64_t* p, cudaStream_t s);
 int32_t read_i32(folty_graph* g, const int32_t* p, cudaStream_t s);
 
@@ -239,6 +245,7 @@ int bit_length(uint64_t x);
 void preprocess_graph(folty_graph* g, cudaStream_t s);          // preprocess.cu
 void run_query(folty_graph* g, const folty_query_params& q, folty_result* out,
                cudaStream_t s);                                  // query.cu
+void destroy_plans(folty_graph* g);                              // query.cu
 // bin_budget: device bytes the per-delta bins may take (<= 0: a quarter of the free
 // memory, at most 16 GiB); deltas beyond it are handled in further probe passes.
 void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq,
@@ -297,6 +304,26 @@ void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t
                        const void* deltas, cudaStream_t s, uint8_t* rflag = nullptr, uint16_t* bins16 = nullptr);
 // Run-ends table and per-triangle liveness bytes (live.cu).
 void build_liveness(folty_graph* g, cudaStream_t s);
+// Device buffers of one query's probe stage (kept triangles, probe tiles, look-back
+// control).
+struct ProbeBuffers {
+    int32_t* L;
+    int64_t* loff;
+    uint8_t* lmask;
+    int64_t* totals;  // kept triangles, slots
+    int64_t* ltile;
+    int64_t max_tiles;
+    unsigned long long* lsctl;
+    int64_t stiles;
+};
+// The same buffers owned by the graph (held by its query plans).
+ProbeBuffers probe_buffers(folty_graph* g, cudaStream_t s);
+// Selection and probes of one query into counters (cnt or cnt16, zeroed), the window
+// taken from the device parameter block qp (slot 0: 64-bit, slot 1: the 32-bit store's
+// clamped value): no host value in any launch, so a captured sequence replays for any
+// window.
+void enqueue_probe_pass(folty_graph* g, const int64_t* qp, int dir, const ProbeBuffers& pb, int32_t* cnt,
+                        uint16_t* cnt16, cudaStream_t s);
 // Kept roles, probes and model bytes of one query's selection (live.cu; synchronises).
 void probe_stats(folty_graph* g, int64_t delta, int dir, folty_probe_stats* out, cudaStream_t s);
 // The same pass with the counters in a file-scope device array (noalloc.cu).

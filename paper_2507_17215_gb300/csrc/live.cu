@@ -17,6 +17,8 @@
 // get their six roles' buckets and sizes from the run-ends table. It then lays the kept
 // roles out in a flat probe space (3 idle slots per triangle keep the tile staging bound)
 // and probes only those, with the exact window test of Theorem 3.1.
+#include <type_traits>
+
 #include "internal.cuh"
 #include "probe.cuh"
 #include "scan.cuh"
@@ -27,10 +29,10 @@ constexpr int LIVE_IDLE = 3;  // idle slots per kept triangle (keeps >= 3 slots 
 constexpr uint8_t DMIN_NEVER = 255;
 
 // Time span of the union of runs a and b (b < 0: run a alone) from the first and last
-// timestamps of the six runs of a triangle. Called with indices the compiler knows, so
-// the arrays stay in registers.
-__device__ __forceinline__ bool span_of(const int64_t* f, const int64_t* l, const bool* ne, int a, int b,
-                                        int64_t& first, int64_t& last) {
+// timestamps of the six runs of a triangle, in the store's timestamp type V. Called with
+// indices the compiler knows, so the arrays stay in registers.
+template <typename V>
+__device__ __forceinline__ bool span_of(const V* f, const V* l, const bool* ne, int a, int b, V& first, V& last) {
     bool any = false;
     if (ne[a]) {
         first = f[a];
@@ -45,24 +47,27 @@ __device__ __forceinline__ bool span_of(const int64_t* f, const int64_t* l, cons
     return any;
 }
 
+__device__ __forceinline__ int bit_len(uint32_t x) { return 32 - __clz(x); }
+__device__ __forceinline__ int bit_len(int64_t x) { return 64 - __clzll((unsigned long long)x); }
+
 // Bucket of role r (= 2k + d: direction d of frame edge k) for direction variant DIR, of
 // a triangle whose local vertices 0, 1, 2 are in id order (flags = 7, so that every run
-// index below is a constant), from the first and last timestamps of its six runs.
-template <int DIR>
-__device__ __forceinline__ uint8_t frame_bucket(const int64_t* f, const int64_t* l, const bool* ne, int r) {
+// index below is a constant), from the first and last timestamps of its six runs. The
+// arithmetic stays in the store's type (32-bit offsets for most graphs): dmin =
+// max(0, L2.first - L1.last, L3.first - L1.last) never needs a sign.
+template <int DIR, typename V>
+__device__ __forceinline__ uint8_t frame_bucket(const V* f, const V* l, const bool* ne, int r) {
     if (!ne[r]) return DMIN_NEVER;
     int s2, s3;
     role_segments(7, r >> 1, r & 1, DIR, s2, s3);
     const bool both = DIR == FOLTY_DIR_EITHER;  // s2, s3 are the d = 0 runs then
-    int64_t f2 = 0, l2 = 0, f3 = 0, l3 = 0;
-    const bool a2 = span_of(f, l, ne, s2, both ? s2 + 1 : -1, f2, l2);
-    const bool a3 = span_of(f, l, ne, s3, both ? s3 + 1 : -1, f3, l3);
-    const int64_t f1 = f[r], l1 = l[r];
+    V f2 = 0, l2 = 0, f3 = 0, l3 = 0;
+    const bool a2 = span_of<V>(f, l, ne, s2, both ? s2 + 1 : -1, f2, l2);
+    const bool a3 = span_of<V>(f, l, ne, s3, both ? s3 + 1 : -1, f3, l3);
+    const V f1 = f[r], l1 = l[r];
     if (!(a2 && a3 && l2 >= f1 && l3 >= (f2 > f1 ? f2 : f1))) return DMIN_NEVER;
-    int64_t dmin = f2 - l1;
-    if (f3 - l1 > dmin) dmin = f3 - l1;
-    if (dmin < 0) dmin = 0;
-    return (uint8_t)(64 - __clzll((unsigned long long)dmin));  // 0 for dmin = 0
+    const V d2 = f2 > l1 ? (V)(f2 - l1) : (V)0, d3 = f3 > l1 ? (V)(f3 - l1) : (V)0;
+    return (uint8_t)bit_len(d2 > d3 ? d2 : d3);  // 0 for dmin = 0
 }
 
 // First and last timestamp and size of both runs of one static edge (direction 0 =
@@ -97,7 +102,7 @@ __global__ void k_run_ends(const int32_t* __restrict__ seg, int64_t S, const TS*
 // id order. oe[k] = the stored edge (0: s_uv, 1: s_uw, 2: s_vw) that is frame edge k.
 template <typename TS>
 struct FrameRuns {
-    int64_t f[6], l[6];
+    TS f[6], l[6];
     int32_t n[6];
     bool ne[6];
     int oe[3];
@@ -124,10 +129,10 @@ __device__ __forceinline__ void frame_runs(const int4 tr, const RunEnds<TS>* __r
         fr.n[2 * k + 1] = re.n1;
         fr.ne[2 * k] = re.n0 > 0;
         fr.ne[2 * k + 1] = re.n1 > 0;
-        fr.f[2 * k] = (int64_t)re.f0;
-        fr.l[2 * k] = (int64_t)re.l0;
-        fr.f[2 * k + 1] = (int64_t)re.f1;
-        fr.l[2 * k + 1] = (int64_t)re.l1;
+        fr.f[2 * k] = re.f0;
+        fr.l[2 * k] = re.l0;
+        fr.f[2 * k + 1] = re.f1;
+        fr.l[2 * k + 1] = re.l1;
     }
 }
 
@@ -143,9 +148,9 @@ __global__ void k_tri_live(const int4* __restrict__ tri, int64_t ntri, const Run
         uint8_t m0 = DMIN_NEVER, m1 = DMIN_NEVER, m2 = DMIN_NEVER;
 #pragma unroll
         for (int r = 0; r < 6; r++) {
-            m0 = min(m0, frame_bucket<FOLTY_DIR_OUT>(fr.f, fr.l, fr.ne, r));
-            m1 = min(m1, frame_bucket<FOLTY_DIR_IN>(fr.f, fr.l, fr.ne, r));
-            m2 = min(m2, frame_bucket<FOLTY_DIR_EITHER>(fr.f, fr.l, fr.ne, r));
+            m0 = min(m0, frame_bucket<FOLTY_DIR_OUT, TS>(fr.f, fr.l, fr.ne, r));
+            m1 = min(m1, frame_bucket<FOLTY_DIR_IN, TS>(fr.f, fr.l, fr.ne, r));
+            m2 = min(m2, frame_bucket<FOLTY_DIR_EITHER, TS>(fr.f, fr.l, fr.ne, r));
         }
         tlive[t] = m0;
         tlive[tstride + t] = m1;
@@ -168,7 +173,7 @@ __device__ __forceinline__ int kept_roles_of(const int4 tr, const RunEnds<TS>* _
     int64_t c = 0;
 #pragma unroll
     for (int r = 0; r < 6; r++) {
-        if (bucket_live(frame_bucket<DIR>(fr.f, fr.l, fr.ne, r), delta)) {  // never for an empty run
+        if (bucket_live(frame_bucket<DIR, TS>(fr.f, fr.l, fr.ne, r), delta)) {  // never for an empty run
             m |= 1 << (2 * fr.oe[r >> 1] + (r & 1));
             c += fr.n[r];
         }
@@ -185,11 +190,13 @@ __device__ __forceinline__ int kept_roles_of(const int4 tr, const RunEnds<TS>* _
 // of probe tiles (each kept triangle writes the tile starts inside its slots). A thread
 // takes LS_ITEMS consecutive triangles and reads their liveness bytes (tlive, the
 // smallest bucket of each triangle's roles for this direction variant) with two 16-byte
-// loads; only the triangles whose byte admits delta read their record and run ends, once
-// to count and once to write (they are few). Tiles of LS_TILE triangles are taken in
-// block start order; the two prefix sums (kept count, cost) come from a block scan and
-// two decoupled look-backs by warp 0. *prof (may be null) gets the bytes read and written
-// for the kept triangles.
+// loads; only the triangles whose byte admits delta read their record and run ends (they
+// are few, but cluster: a warp deals its candidates round-robin over its lanes, so that
+// no lane works through a long run of them alone, and keeps each one's role mask and cost
+// in shared memory for the write). Tiles of LS_TILE triangles are taken in block start
+// order; the two prefix sums (kept count, cost) come from a block scan and two decoupled
+// look-backs by warp 0. *prof (may be null) gets the bytes read and written for the kept
+// triangles.
 constexpr int LS_ITEMS = 32;
 constexpr int LS_TILE = SCAN_THREADS * LS_ITEMS;  // 8192 triangles
 
@@ -203,8 +210,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const uint8_t* __r
                                                               int64_t* __restrict__ loff, uint8_t* __restrict__ lmask,
                                                               int64_t* __restrict__ totals,
                                                               int64_t* __restrict__ ltile, int64_t max_tiles,
-                                                              unsigned long long* __restrict__ prof) {
+                                                              unsigned long long* __restrict__ prof,
+                                                              const int64_t* __restrict__ qp) {
     __shared__ int32_t wc[SCAN_THREADS / 32];
+    if (qp) delta = qp[0];  // the window from a device parameter block (replayed query plans)
     __shared__ int64_t wp[SCAN_THREADS / 32];
     __shared__ int32_t totc;
     __shared__ int64_t totp;
@@ -227,15 +236,42 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const uint8_t* __r
         for (int i = 0; i < 16; i++)
             if (bucket_live((uint8_t)(ws[i >> 2] >> (8 * (i & 3))), delta)) lm |= 1u << (16 * h + i);
     }
-    int32_t c = 0;
-    int64_t cs = 0;
-    for (uint32_t x = lm; x; x &= x - 1) {
-        const int64_t t = t0 + __ffs(x) - 1;
-        int64_t pr;
-        kept_roles_of<TS, DIR>(tri[t], ends, delta, pr);
-        c++;
-        cs += pr + LIVE_IDLE;
+    // ---- the warp's candidates dealt round-robin over its lanes: candidate k of the warp
+    // is the (k - pre[l] + 1)-th set bit of lane l's mask, l the last lane with pre[l] <= k;
+    // its role mask and cost (kept probes + LIVE_IDLE) go to the tile's shared arrays
+    __shared__ uint32_t s_lm[SCAN_THREADS];
+    __shared__ int32_t s_pre[SCAN_THREADS];
+    __shared__ uint8_t s_mask[LS_TILE];
+    __shared__ int32_t s_cost[LS_TILE];  // kept probes: a triangle's fit 32 bits (at most m < 2^31)
+    const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+    const int32_t own = __popc(lm);
+    int32_t inc = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
     }
+    const int32_t wtotal = __shfl_sync(0xffffffffu, inc, 31);
+    s_lm[threadIdx.x] = lm;
+    s_pre[threadIdx.x] = inc - own;
+    __syncwarp();
+    for (int32_t k = lane; k < wtotal; k += 32) {
+        int lo = 0, hi = 31;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_pre[wbase + mid] <= k) lo = mid;
+            else hi = mid - 1;
+        }
+        const int bit = __fns(s_lm[wbase + lo], 0, k - s_pre[wbase + lo] + 1);
+        const int p = (wbase + lo) * LS_ITEMS + bit;  // position in the tile
+        int64_t pr;
+        s_mask[p] = (uint8_t)kept_roles_of<TS, DIR>(tri[base + p], ends, delta, pr);
+        s_cost[p] = (int32_t)pr;
+    }
+    __syncwarp();
+    const int32_t c = own;
+    int64_t cs = 0;
+    for (uint32_t x = lm; x; x &= x - 1) cs += (int64_t)s_cost[threadIdx.x * LS_ITEMS + __ffs(x) - 1] + LIVE_IDLE;
     // ---- block scans, look-backs
     const int32_t offc = block_exclusive_sum<int32_t>(c, wc, &totc);
     const int64_t offp = block_exclusive_sum<int64_t>(cs, wp, &totp);
@@ -267,13 +303,12 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const uint8_t* __r
     // ---- the kept triangles of this thread's run
     int64_t jc = (int64_t)s_exc + offc, jp = (int64_t)s_exp + offp;
     for (uint32_t x = lm; x; x &= x - 1) {
-        const int64_t t = t0 + __ffs(x) - 1;
-        int64_t pr;
-        const int m = kept_roles_of<TS, DIR>(tri[t], ends, delta, pr);
-        const int64_t v = pr + LIVE_IDLE;
+        const int i = __ffs(x) - 1;
+        const int64_t t = t0 + i;
+        const int64_t v = (int64_t)s_cost[threadIdx.x * LS_ITEMS + i] + LIVE_IDLE;
         L[jc] = (int32_t)t;
         loff[jc] = jp;
-        lmask[jc] = (uint8_t)m;
+        lmask[jc] = s_mask[threadIdx.x * LS_ITEMS + i];
         for (int64_t b = (jp + PB_TILE - 1) / PB_TILE; b * PB_TILE < jp + v && b <= max_tiles; b++) ltile[b] = jc;
         jc++;
         jp += v;
@@ -326,6 +361,8 @@ struct LiveArgs {
     int k;             // MODE 1: number of bins
     unsigned long long* prof;  // model bytes of the kept roles (may be null)
     uint8_t* rflag;    // MODE 0, may be null: 6 * triangle + role flags of roles with a hit
+    const int64_t* qp; // may be null: a device block whose slot 0 (64-bit store) or 1 (32-bit
+                       // store) holds the window, read instead of the delta argument
 };
 
 // MODE 0: cnt[pos] += hit at window delta. MODE 1: bin the gap t3 - t (<= delta, the
@@ -336,6 +373,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS*
     __shared__ TriStage st;
     __shared__ uint8_t smask[PB_MAXTRI];
     __shared__ TS sD[1024];
+    if (a.qp) delta = (TS)a.qp[sizeof(TS) == 4 ? 1 : 0];
     if (MODE == 1)
         for (int i = threadIdx.x; i < a.k; i += blockDim.x) sD[i] = deltas[i];
     const int64_t P = *a.P;
@@ -467,25 +505,15 @@ static void launch_live_t(const folty_graph* g, int dir, const LiveArgs& la, uns
         FOLTY_LAUNCH((k_probe_live<TS, FOLTY_DIR_EITHER, MODE>), grid, PB_THREADS, 0, s, la, T, delta, deltas);
 }
 
-// The kept triangles of one selection (see k_live_select).
-struct LiveSel {
-    int32_t* L;
-    int64_t* loff;
-    uint8_t* lmask;
-    int64_t* totals;  // kept triangles, slots
-    int64_t* ltile;
-    int64_t max_tiles;
-};
-
 template <typename TS>
-static void launch_select_t(const folty_graph* g, int dir, const uint8_t* tl, int64_t delta,
-                            unsigned long long* lsctl, int64_t stiles, int* err, const LiveSel& ls,
-                            unsigned long long* prof, cudaStream_t s) {
+static void launch_select_t(const folty_graph* g, int dir, const uint8_t* tl, int64_t delta, int* err,
+                            const ProbeBuffers& ls, unsigned long long* prof, const int64_t* qp, cudaStream_t s) {
     const RunEnds<TS>* ends = static_cast<const RunEnds<TS>*>(g->run_ends);
-    const int64_t ntri = g->ntri;
+    const int64_t ntri = g->ntri, stiles = ls.stiles;
+    unsigned long long* lsctl = ls.lsctl;
 #define FOLTY_SELECT_ARGS                                                                                          \
     tl, g->tri, ends, ntri, delta, lsctl + 1, lsctl + 1 + stiles, (unsigned int*)lsctl, err, ls.L, ls.loff, ls.lmask, \
-        ls.totals, ls.ltile, ls.max_tiles, prof
+        ls.totals, ls.ltile, ls.max_tiles, prof, qp
     if (dir == FOLTY_DIR_OUT)
         FOLTY_LAUNCH((k_live_select<TS, FOLTY_DIR_OUT>), (unsigned)stiles, SCAN_THREADS, 0, s, FOLTY_SELECT_ARGS);
     else if (dir == FOLTY_DIR_IN)
@@ -495,25 +523,45 @@ static void launch_select_t(const folty_graph* g, int dir, const uint8_t* tl, in
 #undef FOLTY_SELECT_ARGS
 }
 
-// Selects the roles kept for delta (buffers from sc). prof_sel (may be null) receives the
-// selection's model bytes beyond its one byte per triangle.
-static LiveSel select_live(folty_graph* g, int64_t delta, int dir, Scratch& sc, cudaStream_t s,
-                           unsigned long long* prof_sel) {
+// Buffers of one selection: from a call's scratch, or (alloc = graph) owned by the graph.
+template <typename A>
+static ProbeBuffers make_probe_buffers(const folty_graph* g, A&& get) {
     const int64_t ntri = g->ntri;
-    LiveSel ls;
-    ls.L = sc.get<int32_t>(ntri + 1);
-    ls.loff = sc.get<int64_t>(ntri + 1);
-    ls.lmask = sc.get<uint8_t>(ntri + 1);
-    ls.totals = sc.get<int64_t>(2);
+    ProbeBuffers ls;
+    ls.L = get((int32_t*)nullptr, ntri + 1);
+    ls.loff = get((int64_t*)nullptr, ntri + 1);
+    ls.lmask = get((uint8_t*)nullptr, ntri + 1);
+    ls.totals = get((int64_t*)nullptr, 2);
     ls.max_tiles = (g->info.probes + LIVE_IDLE * ntri + PB_TILE - 1) / PB_TILE;
-    ls.ltile = sc.get<int64_t>(ls.max_tiles + 2);
-    const int64_t stiles = (ntri + LS_TILE - 1) / LS_TILE;
-    unsigned long long* lsctl = sc.get<unsigned long long>(2 * stiles + 1);  // tile counter, two look-backs
-    StageSpan span(ST_SELECT, s, ntri, prof_sel);
-    FOLTY_CUDA(cudaMemsetAsync(lsctl, 0, sizeof(unsigned long long) * (size_t)(2 * stiles + 1), s));
+    ls.ltile = get((int64_t*)nullptr, ls.max_tiles + 2);
+    ls.stiles = (ntri + LS_TILE - 1) / LS_TILE;
+    ls.lsctl = get((unsigned long long*)nullptr, 2 * ls.stiles + 1);  // tile counter, two look-backs
+    return ls;
+}
+
+ProbeBuffers probe_buffers(folty_graph* g, cudaStream_t s) {
+    return make_probe_buffers(g, [&](auto* tag, int64_t n) {
+        return graph_alloc<std::remove_pointer_t<decltype(tag)>>(g, n, s);
+    });
+}
+
+// Selects the roles kept for delta (or the window in qp) into ls. prof_sel (may be null)
+// receives the selection's model bytes beyond its one byte per triangle.
+static void enqueue_select(folty_graph* g, int64_t delta, int dir, const ProbeBuffers& ls, int* err,
+                           unsigned long long* prof_sel, const int64_t* qp, cudaStream_t s) {
+    StageSpan span(ST_SELECT, s, g->ntri, prof_sel);
+    FOLTY_CUDA(cudaMemsetAsync(ls.lsctl, 0, sizeof(unsigned long long) * (size_t)(2 * ls.stiles + 1), s));
     const uint8_t* tl = g->tlive + (int64_t)dir * g->tlive_stride;
-    if (g->ts32) launch_select_t<uint32_t>(g, dir, tl, delta, lsctl, stiles, sc.err(), ls, prof_sel, s);
-    else launch_select_t<int64_t>(g, dir, tl, delta, lsctl, stiles, sc.err(), ls, prof_sel, s);
+    if (g->ts32) launch_select_t<uint32_t>(g, dir, tl, delta, err, ls, prof_sel, qp, s);
+    else launch_select_t<int64_t>(g, dir, tl, delta, err, ls, prof_sel, qp, s);
+}
+
+static ProbeBuffers select_live(folty_graph* g, int64_t delta, int dir, Scratch& sc, cudaStream_t s,
+                                unsigned long long* prof_sel) {
+    const ProbeBuffers ls = make_probe_buffers(g, [&](auto* tag, int64_t n) {
+        return sc.get<std::remove_pointer_t<decltype(tag)>>(n);
+    });
+    enqueue_select(g, delta, dir, ls, sc.err(), prof_sel, nullptr, s);
     return ls;
 }
 
@@ -535,10 +583,10 @@ void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t
         FOLTY_CUDA(cudaMemsetAsync(prof_sel, 0, sizeof(unsigned long long), s));
         FOLTY_CUDA(cudaMemsetAsync(prof, 0, sizeof(unsigned long long), s));
     }
-    const LiveSel ls = select_live(g, delta, dir, sc, s, prof_sel);
+    const ProbeBuffers ls = select_live(g, delta, dir, sc, s, prof_sel);
     StageSpan span(ST_PROBE, s, 0, prof);
     LiveArgs la{g->tri, g->seg, ls.L, ls.loff, ls.lmask, ls.ltile, ls.totals + 1, cnt, bins, (uint32_t*)bins16,
-                g->m_kept, k, prof, rflag};
+                g->m_kept, k, prof, rflag, nullptr};
     int per_sm = 0;
     if (g->ts32) FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<uint32_t, 0, 0>, PB_THREADS, 0));
     else FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<int64_t, 0, 0>, PB_THREADS, 0));
@@ -551,6 +599,20 @@ void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t
         if (mode == 0) launch_live_t<int64_t, 0>(g, dir, la, grid, delta, nullptr, s);
         else launch_live_t<int64_t, 1>(g, dir, la, grid, delta, (const int64_t*)deltas, s);
     }
+}
+
+void enqueue_probe_pass(folty_graph* g, const int64_t* qp, int dir, const ProbeBuffers& pb, int32_t* cnt,
+                        uint16_t* cnt16, cudaStream_t s) {
+    if (g->ntri == 0 || g->info.probes == 0) return;
+    enqueue_select(g, 0, dir, pb, g->dev_err, nullptr, qp, s);
+    LiveArgs la{g->tri, g->seg, pb.L, pb.loff, pb.lmask, pb.ltile, pb.totals + 1, cnt, nullptr, (uint32_t*)cnt16,
+                g->m_kept, 0, nullptr, nullptr, qp};
+    int per_sm = 0;
+    if (g->ts32) FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<uint32_t, 0, 0>, PB_THREADS, 0));
+    else FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<int64_t, 0, 0>, PB_THREADS, 0));
+    const unsigned grid = (unsigned)(num_sms() * (per_sm > 0 ? per_sm : 1));
+    if (g->ts32) launch_live_t<uint32_t, 0>(g, dir, la, grid, 0u, nullptr, s);
+    else launch_live_t<int64_t, 0>(g, dir, la, grid, 0, nullptr, s);
 }
 
 // ------------------------------------------------------------------ selection statistics
@@ -594,7 +656,8 @@ __global__ void k_live_stats(const int4* __restrict__ tri, const int32_t* __rest
 }
 
 template <typename TS>
-static void live_stats_t(const folty_graph* g, int dir, const LiveSel& ls, unsigned long long* acc, cudaStream_t s) {
+static void live_stats_t(const folty_graph* g, int dir, const ProbeBuffers& ls, unsigned long long* acc,
+                         cudaStream_t s) {
     const unsigned grid = grid_for(g->ntri, 256);
     if (dir == FOLTY_DIR_OUT)
         FOLTY_LAUNCH((k_live_stats<TS, FOLTY_DIR_OUT>), grid, 256, 0, s, g->tri, g->seg, ls.L, ls.lmask, ls.totals, acc);
@@ -613,7 +676,7 @@ void probe_stats(folty_graph* g, int64_t delta, int dir, folty_probe_stats* out,
     out->select_bytes = g->ntri;
     if (g->ntri == 0 || g->info.probes == 0) return;
     Scratch sc(g->alloc, s, g->dev_err);
-    const LiveSel ls = select_live(g, delta, dir, sc, s, nullptr);
+    const ProbeBuffers ls = select_live(g, delta, dir, sc, s, nullptr);
     unsigned long long* acc = sc.get<unsigned long long>(3);
     FOLTY_CUDA(cudaMemsetAsync(acc, 0, 3 * sizeof(unsigned long long), s));
     if (g->ts32) live_stats_t<uint32_t>(g, dir, ls, acc, s);

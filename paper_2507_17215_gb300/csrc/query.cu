@@ -12,6 +12,7 @@
 //       compaction of the solution pairs and a sort by (u, v).
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.cuh"
@@ -68,6 +69,7 @@ struct ThresholdArgs {
     const int32_t* perm;  // with cert_in: certificate flag of input edge perm[i]
     int32_t* cert_in;     // [m] or null
     const uint16_t* cnt16;  // 16-bit counts instead of cnt (batched queries), or null
+    const int64_t* qp;      // may be null: a device block whose slots 2, 3 hold num, den
 };
 
 // Certificate test of Definition 1.1 with rho = num / den, exact in int64.
@@ -90,6 +92,7 @@ __global__ void __launch_bounds__(TH_THREADS) k_threshold(ThresholdArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t num = a.qp ? a.qp[2] : a.num, den = a.qp ? a.qp[3] : a.den;
     unsigned long long my_cert = 0;
     for (int64_t b0 = gw * 32 * TH_BATCH; b0 < a.mk; b0 += nw * 32 * TH_BATCH) {
         const int32_t* sd = a.sd + b0;
@@ -122,8 +125,7 @@ __global__ void __launch_bounds__(TH_THREADS) k_threshold(ThresholdArgs a) {
             if (k * 32 >= rem) break;  // warp-uniform
             const int32_t i = k * 32 + lane;
             const int32_t key = kb[k], c = cb[k];
-            const bool sat = c >= 1 && (QUANT == FOLTY_Q_EXISTS ||
-                                        (int64_t)c * a.den >= a.num * (int64_t)ub[k]);
+            const bool sat = c >= 1 && (QUANT == FOLTY_Q_EXISTS || (int64_t)c * den >= num * (int64_t)ub[k]);
             if (CERT && i < rem) a.cert_in[a.perm[b0 + i]] = sat;
             if (!__any_sync(0xffffffffu, c > 0)) continue;  // nothing to reduce in this chunk
             // runs of one pair are contiguous lanes (past-the-end lanes hold key -1 and
@@ -401,6 +403,7 @@ struct PairStage {
     int32_t* vcnt;       // [n + 1] solution pairs per head vertex (outer queries)
     int32_t* vflag;      // [n + 1]
     int32_t* vpos;       // [n + 1]
+    unsigned long long* ctl;  // tile counter and look-back of k_pair_select
 };
 
 static PairStage pair_stage(Scratch& sc, const folty_graph* g, const folty_query_params& q) {
@@ -424,12 +427,13 @@ static PairStage pair_stage(Scratch& sc, const folty_graph* g, const folty_query
     p.cnt_c = sc.get<int32_t>(2 * n2 + 2);
     p.nc_c = p.cnt_c + n2 + 1;
     p.n_cert = sc.get<unsigned long long>(1);
+    p.ctl = sc.get<unsigned long long>((n2 + PS_TILE - 1) / PS_TILE + 1);
     return p;
 }
 
 // Certificate test, per-pair reduction, flags, positions, compaction (no host sync).
 static void pairs_device(folty_graph* g, const folty_query_params& q, const CountView& cnt, const PairStage& p,
-                         Scratch& sc, cudaStream_t s) {
+                         Scratch* sc, cudaStream_t s, const int64_t* qp = nullptr) {
     const int T = 256;
     const int64_t mk = g->m_kept;
     const int64_t S = g->S, n2 = 2 * S;
@@ -439,17 +443,17 @@ static void pairs_device(folty_graph* g, const folty_query_params& q, const Coun
     if (mk > 0) {
         ThresholdArgs a{cnt.c32, g->sd, mk, g->ea, g->eb, g->deg, g->common, (int)q.quant, (int)q.universe,
                         (int64_t)q.rho_num, (int64_t)q.rho_den, p.seg_max, p.seg_ncert, p.n_cert,
-                        g->perm, p.cert_flag, cnt.c16};
+                        g->perm, p.cert_flag, cnt.c16, qp};
         StageSpan span(ST_THRESHOLD, s, 8 * mk);  // pair key + count per edge
         launch_threshold(a, grid_for((mk + TH_BATCH - 1) / TH_BATCH, TH_THREADS), s);
     }
-    if (p.cert_flag) exclusive_scan(sc, p.cert_flag, p.cert_pos, g->m);
+    if (p.cert_flag) exclusive_scan(*sc, p.cert_flag, p.cert_pos, g->m);
     if (n2 > 0) {
         const int64_t tiles = (n2 + PS_TILE - 1) / PS_TILE;
-        unsigned long long* ctl = sc.get<unsigned long long>(tiles + 1);  // tile counter, look-back
+        unsigned long long* ctl = p.ctl;  // tile counter, look-back
         FOLTY_CUDA(cudaMemsetAsync(ctl, 0, sizeof(unsigned long long) * (size_t)(tiles + 1), s));
         FOLTY_LAUNCH(k_pair_select, (unsigned)tiles, SCAN_THREADS, 0, s, p.seg_ncert, p.seg_max, g->ea, g->eb, g->by_b,
-                     S, ctl + 1, (unsigned int*)ctl, sc.err(), p.flag, p.pos, p.key, p.cnt_c, p.nc_c);
+                     S, ctl + 1, (unsigned int*)ctl, g->dev_err, p.flag, p.pos, p.key, p.cnt_c, p.nc_c);
     } else {
         FOLTY_CUDA(cudaMemsetAsync(p.pos, 0, sizeof(int32_t), s));
     }
@@ -459,7 +463,7 @@ static void pairs_device(folty_graph* g, const folty_query_params& q, const Coun
         if (n2 > 0) FOLTY_LAUNCH(k_vertex_count, grid_for(n2, T), T, 0, s, p.flag, S, g->ea, g->eb, g->by_b, p.vcnt);
         FOLTY_LAUNCH(k_vertex_flags, grid_for(n, T), T, 0, s, p.vcnt, g->deg, n, (int64_t)q.outer_rho_num,
                      (int64_t)q.outer_rho_den, p.vflag);
-        exclusive_scan(sc, p.vflag, p.vpos, n);
+        exclusive_scan(*sc, p.vflag, p.vpos, n);
     }
 }
 
@@ -479,7 +483,7 @@ void finish_queries(folty_graph* g, const folty_query_params* const* qs, const C
         g->stage_busy = 1;
         for (int i = 0; i < ng; i++) {
             st.push_back(pair_stage(sc, g, *qs[g0 + i]));
-            pairs_device(g, *qs[g0 + i], cnts[g0 + i], st.back(), sc, s);
+            pairs_device(g, *qs[g0 + i], cnts[g0 + i], st.back(), &sc, s);
             FOLTY_LAUNCH(k_pair_merge_stage, grid_for(cap, T, 1), T, 0, s, st.back().key, st.back().cnt_c,
                          st.back().nc_c, st.back().pos, S, cap, g->pair_stage + 4 * cap * i);
         }
@@ -639,7 +643,166 @@ static void triples_result(folty_graph* g, const uint8_t* rflag, folty_result* o
     FOLTY_CUDA(cudaStreamSynchronize(s));
 }
 
+// ------------------------------------------------------------------ query plans
+
+// A plain query (no per-edge counts, certificates, vertex or triple outputs) replays a
+// CUDA graph captured once per graph and query shape (direction variant, quantifier,
+// universe). Its window and rho reach the kernels through a device parameter block that
+// the graph's first node copies from the graph's pinned stage, so no launch argument
+// changes between queries: a query costs one graph launch and one synchronisation
+// instead of about fifteen launches, memsets and allocations. The buffers the graphs
+// work in are allocated once and owned by the graph.
+constexpr int QP_SLOT = 448;  // pinned stage slots [QP_SLOT, QP_SLOT + 4): delta, delta32, num, den
+static_assert(QP_SLOT > ERR_SLOT && QP_SLOT + 4 <= HOST_STAGE, "the parameter block has its own stage slots");
+
+struct QueryPlans {
+    CountView cnt;
+    int32_t* cnt32 = nullptr;
+    uint16_t* cnt16 = nullptr;
+    ProbeBuffers pb{};
+    PairStage ps{};
+    int64_t* qp = nullptr;  // device parameter block [4]
+    cudaStream_t cs = nullptr;  // capture stream
+    cudaGraphExec_t exec[3][2][3] = {};
+    int kernels[3][2][3] = {};  // kernel nodes of each captured sequence
+};
+
+void destroy_plans(folty_graph* g) {
+    QueryPlans* qp = g->plans;
+    if (!qp) return;
+    for (auto& a : qp->exec)
+        for (auto& b : a)
+            for (auto& e : b)
+                if (e) cudaGraphExecDestroy(e);
+    if (qp->cs) cudaStreamDestroy(qp->cs);
+    delete qp;
+    g->plans = nullptr;
+}
+
+static QueryPlans* plans_of(folty_graph* g, cudaStream_t s) {
+    if (g->plans) return g->plans;
+    QueryPlans* p = new QueryPlans();
+    g->plans = p;  // the buffers below are graph-owned; destroy_plans releases the rest
+    const int64_t mk = g->m_kept, n2 = 2 * (int64_t)g->S;
+    if (g->info.max_degree < 65535) p->cnt16 = graph_alloc<uint16_t>(g, mk + 2, s);
+    else p->cnt32 = graph_alloc<int32_t>(g, mk, s);
+    p->cnt = CountView{p->cnt32, p->cnt16};
+    p->pb = probe_buffers(g, s);
+    PairStage& ps = p->ps;
+    std::memset(&ps, 0, sizeof(ps));
+    ps.seg_max = graph_alloc<int32_t>(g, 2 * n2 + 2, s);
+    ps.seg_ncert = ps.seg_max + n2 + 1;
+    ps.flag = graph_alloc<int32_t>(g, 2 * n2 + 2, s);
+    ps.pos = ps.flag + n2 + 1;
+    ps.key = graph_alloc<uint64_t>(g, n2, s);
+    ps.cnt_c = graph_alloc<int32_t>(g, 2 * n2 + 2, s);
+    ps.nc_c = ps.cnt_c + n2 + 1;
+    ps.n_cert = graph_alloc<unsigned long long>(g, 1, s);
+    ps.ctl = graph_alloc<unsigned long long>(g, (n2 + PS_TILE - 1) / PS_TILE + 1, s);
+    p->qp = graph_alloc<int64_t>(g, 4, s);
+    FOLTY_CUDA(cudaStreamCreateWithFlags(&p->cs, cudaStreamNonBlocking));
+    return p;
+}
+
+// The launch sequence of one plain query of shape (dir, quant, universe) on stream cs.
+static void enqueue_plain_query(folty_graph* g, QueryPlans* p, int dir, int quant, int universe, cudaStream_t cs) {
+    const int64_t mk = g->m_kept, S = g->S;
+    FOLTY_CUDA(cudaMemcpyAsync(p->qp, g->host_stage + QP_SLOT, 4 * sizeof(int64_t), cudaMemcpyHostToDevice, cs));
+    if (mk > 0 && p->cnt16) FOLTY_CUDA(cudaMemsetAsync(p->cnt16, 0, sizeof(uint16_t) * (size_t)(mk + 2), cs));
+    if (mk > 0 && p->cnt32) FOLTY_CUDA(cudaMemsetAsync(p->cnt32, 0, sizeof(int32_t) * (size_t)mk, cs));
+    enqueue_probe_pass(g, p->qp, dir, p->pb, p->cnt32, p->cnt16, cs);
+    folty_query_params q{};
+    q.dir = (uint8_t)dir;
+    q.quant = (uint8_t)quant;
+    q.universe = (uint8_t)universe;
+    q.rho_den = 1;
+    pairs_device(g, q, p->cnt, p->ps, nullptr, cs, p->qp);
+    FOLTY_LAUNCH(k_pair_merge_stage, grid_for(PAIR_STAGE, 256, 1), 256, 0, cs, p->ps.key, p->ps.cnt_c, p->ps.nc_c,
+                 p->ps.pos, S, PAIR_STAGE, g->pair_stage);
+    const void* ptrs[3] = {p->ps.pos + S, p->ps.pos + 2 * S, p->ps.n_cert};
+    const int sizes[3] = {4, 4, 8};
+    enqueue_read_back(g, ptrs, sizes, 3, cs);
+}
+
+static cudaGraphExec_t plan_exec(folty_graph* g, QueryPlans* p, int dir, int quant, int universe) {
+    cudaGraphExec_t& e = p->exec[dir][quant][universe];
+    if (e) return e;
+    FOLTY_CUDA(cudaStreamBeginCapture(p->cs, cudaStreamCaptureModeThreadLocal));
+    cudaGraph_t graph = nullptr;
+    try {
+        enqueue_plain_query(g, p, dir, quant, universe, p->cs);
+    } catch (...) {
+        cudaStreamEndCapture(p->cs, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        throw;
+    }
+    FOLTY_CUDA(cudaStreamEndCapture(p->cs, &graph));
+    // the kernels a replay launches (the library's launch counter counts them)
+    size_t nn = 0;
+    int kernels = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+            for (size_t i = 0; i < nn; i++) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) kernels++;
+            }
+    }
+    cudaGetLastError();
+    p->kernels[dir][quant][universe] = kernels;
+    const cudaError_t ie = cudaGraphInstantiate(&e, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        e = nullptr;
+        fail(FOLTY_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+    }
+    return e;
+}
+
+static bool plans_enabled() {
+    const char* env = std::getenv("FOLTY_QUERY_GRAPHS");
+    return !(env && std::strcmp(env, "0") == 0);
+}
+
+static bool run_query_plan(folty_graph* g, const folty_query_params& q, folty_result* out, cudaStream_t s) {
+    if (q.want_edge_counts || q.want_certificates || q.outer || q.want_triples) return false;
+    if (profiling_on() || !plans_enabled()) return false;  // stage events are recorded by the launch path
+    QueryPlans* p = plans_of(g, s);
+    const cudaGraphExec_t e = plan_exec(g, p, q.dir, q.quant, q.universe);
+    int64_t* hp = g->host_stage + QP_SLOT;
+    hp[0] = q.delta;
+    hp[1] = q.delta >= 0xfffffffell ? 0xfffffffell - 1 : q.delta;  // gaps of the 32-bit store stay below 2^32 - 1
+    hp[2] = q.rho_num;
+    hp[3] = q.rho_den;
+    g->stage_busy = 1;
+    FOLTY_CUDA(cudaGraphLaunch(e, s));
+    g_launches.fetch_add((uint64_t)p->kernels[q.dir][q.quant][q.universe], std::memory_order_relaxed);
+    FOLTY_CUDA(cudaStreamSynchronize(s));
+    int64_t rb[3];
+    collect_read_back(g, 3, rb, s);
+    const int64_t nA = rb[0], np = rb[1], nc = rb[2];
+    fill_result_host(out, np, g->m, false, 0, false, nc, false);
+    out->n_cert_edges = nc;
+    if (np > 0 && np <= PAIR_STAGE) {
+        std::memcpy(out->u, (const int32_t*)(g->host_stage + HOST_STAGE), sizeof(int32_t) * 4 * (size_t)np);
+    } else if (np > 0) {
+        try {
+            Scratch sc(g->alloc, s, g->dev_err);
+            int32_t* packed = sc.get<int32_t>(4 * np);
+            FOLTY_LAUNCH(k_pair_merge, grid_for(np, 256), 256, 0, s, p->ps.key, p->ps.cnt_c, p->ps.nc_c, nA, np, packed);
+            FOLTY_CUDA(cudaMemcpyAsync(out->u, packed, sizeof(int32_t) * 4 * (size_t)np, cudaMemcpyDeviceToHost, s));
+            FOLTY_CUDA(cudaStreamSynchronize(s));
+        } catch (...) {
+            release_result(out);
+            throw;
+        }
+    }
+    return true;
+}
+
 void run_query(folty_graph* g, const folty_query_params& q, folty_result* out, cudaStream_t s) {
+    if (run_query_plan(g, q, out, s)) return;
     Scratch sc(g->alloc, s, g->dev_err);
     const int64_t mk = g->m_kept;
     // c_e counts distinct witnesses, so it is at most the largest degree of G_S: below

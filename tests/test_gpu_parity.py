@@ -812,3 +812,36 @@ def test_batch_of_plain_queries_with_32_bit_bins_and_long_lists(F):
         for q, r, w in zip(queries, bat, want):
             _assert_pairs(r, w, str(q))
     assert max(len(w["u"]) for w in want) > (1 << 16)
+
+
+def test_plain_single_queries_through_captured_plans(F, monkeypatch):
+    """Plain single queries replay a CUDA graph captured once per graph and query shape,
+    with the window and rho in a device parameter block: results equal the oracle's and,
+    bit for bit, those of the same queries launched one kernel at a time
+    (FOLTY_QUERY_GRAPHS=0); several windows and rhos replay each shape."""
+    rng = np.random.default_rng(61)
+    graphs = [W.random_small_graph(rng, 12, 90, 20) for _ in range(3)]
+    graphs += [W.config_graph(1), W.config_graph(2, scale=0.01), wide_time_span_graph(15), _long_run_graph(19),
+               _clique_graph()]
+    for g in graphs:
+        span = int(g.t.max() - g.t.min()) if g.m else 1
+        deltas = sorted({0, 3, max(1, span // 50), max(1, span // 5), span + 1})
+        qs = [W.Query(d, k, 10, quant, dr, uni, False) for d in deltas
+              for (k, quant, dr, uni) in ((5, W.Q_FORALL_T, W.DIR_OUT, W.U_HEAD), (1, W.Q_EXISTS, W.DIR_IN, W.U_TAIL),
+                                          (3, W.Q_FORALL_T, W.DIR_EITHER, W.U_COMMON),
+                                          (9, W.Q_FORALL_T, W.DIR_OUT, W.U_HEAD))]
+        with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
+            before = F.folty_kernel_launches()
+            got = [G.query(q) for q in qs]
+            assert F.folty_kernel_launches() > before
+            monkeypatch.setenv("FOLTY_QUERY_GRAPHS", "0")
+            ref = [G.query(q) for q in qs]
+            monkeypatch.delenv("FOLTY_QUERY_GRAPHS")
+            again = [G.query(q) for q in reversed(qs)][::-1]
+        with oracle.OracleGraph.of(g) as og:
+            for q, a, b, c in zip(qs, got, ref, again):
+                for k in ("u", "v", "count", "ncert"):
+                    np.testing.assert_array_equal(a[k], b[k], err_msg=str(q))
+                    np.testing.assert_array_equal(c[k], b[k], err_msg=str(q))
+                assert a["n_cert_edges"] == b["n_cert_edges"] == c["n_cert_edges"]
+                _assert_pairs(a, og.query(q), str(q))
