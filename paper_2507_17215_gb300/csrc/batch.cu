@@ -18,6 +18,9 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <numeric>
+#include <tuple>
 
 #include "internal.cuh"
 #include "probe.cuh"
@@ -92,13 +95,21 @@ constexpr int BT_THREADS = 256;
 constexpr int BT_WARPS = BT_THREADS / 32;
 constexpr int BT_MAXQ = 256;  // queries of one fused pass
 constexpr int BT_UNROLL = 8;  // bins loaded together per lane
+// bins of one fused pass (their prefix sums sit in shared memory, per warp and lane)
+constexpr int BT_KMAX = 128;
 
-// One query of a fused pass, the queries sorted by bin.
+// A class of a pass's queries that differ only in their window: the same quantifier,
+// universe and rho. Its queries are qs[qb, qe), sorted by bin; jmax = the last one's bin.
+struct BatchClass {
+    int32_t quant, universe;
+    int64_t num, den;
+    int32_t qb, qe, jmax, pad;
+};
+
+// One query of a fused pass.
 struct BatchQuery {
     int32_t j;     // bin of its delta
     int32_t slot;  // index among the pass's queries (high bits of its output keys)
-    int32_t quant, universe;
-    int64_t num, den;
 };
 
 struct BatchArgs {
@@ -112,7 +123,9 @@ struct BatchArgs {
     const int32_t* deg;
     const int32_t* common;
     const int32_t* prank;
-    const BatchQuery* qs;
+    const BatchClass* cls;
+    int ncls;
+    const BatchQuery* qs;  // by class, then bin
     int nq;
     int rb;  // bits of a pair rank
     int64_t per_warp;
@@ -142,11 +155,13 @@ __device__ __forceinline__ void universes(const BatchArgs& a, int32_t r, int64_t
     uc = a.common[s];
 }
 
-__device__ __forceinline__ bool certifies_q(const BatchQuery& q, uint32_t c, int64_t uh, int64_t ut, int64_t uc) {
-    if (c == 0) return false;
-    if (q.quant == FOLTY_Q_EXISTS) return true;
-    const int64_t U = q.universe == FOLTY_U_HEAD ? uh : q.universe == FOLTY_U_TAIL ? ut : uc;
-    return (int64_t)c * q.den >= q.num * U;
+// The smallest count that certifies for class c (Definition 1.1: c >= 1, and for
+// forall_rho c * den >= num * U, i.e. c >= ceil(num * U / den) in integers).
+__device__ __forceinline__ int64_t needed(const BatchClass& c, int64_t uh, int64_t ut, int64_t uc) {
+    if (c.quant == FOLTY_Q_EXISTS) return 1;
+    const int64_t U = c.universe == FOLTY_U_HEAD ? uh : c.universe == FOLTY_U_TAIL ? ut : uc;
+    const int64_t v = (c.num * U + c.den - 1) / c.den;
+    return v > 1 ? v : 1;
 }
 
 // Appends the pairs of the lanes with emit set (one atomic per warp).
@@ -169,41 +184,68 @@ __device__ __forceinline__ void emit_pairs(const BatchArgs& a, bool emit, int sl
     }
 }
 
-// The prefix c_e(D_j) of the bins of one lane's edge, BT_UNROLL bins at a time (their
-// loads in flight together): c[u] = c_e(D_{j0 + u}).
+// Prefix sums c_e(D_j) of the bins of one lane's edge into pref[j * 32 + lane] (zeros for
+// an idle lane), BT_UNROLL bins' loads in flight together; returns c_e(D_{k-1}).
 template <typename C>
-__device__ __forceinline__ void bin_block(const C* __restrict__ bins, int64_t mk, int k, int j0, int64_t e, bool on,
-                                          uint32_t& run, uint32_t* c) {
-    C v[BT_UNROLL];
+__device__ __forceinline__ uint32_t bin_prefix(const C* __restrict__ bins, int64_t mk, int k, int64_t e, bool on,
+                                               C* pref) {
+    const int lane = threadIdx.x & 31;
+    uint32_t run = 0;
+    for (int j0 = 0; j0 < k; j0 += BT_UNROLL) {
+        C v[BT_UNROLL];
 #pragma unroll
-    for (int u = 0; u < BT_UNROLL; u++) v[u] = (on && j0 + u < k) ? __ldcs(&bins[(int64_t)(j0 + u) * mk + e]) : (C)0;
+        for (int u = 0; u < BT_UNROLL; u++) v[u] = (on && j0 + u < k) ? __ldcs(&bins[(int64_t)(j0 + u) * mk + e]) : (C)0;
 #pragma unroll
-    for (int u = 0; u < BT_UNROLL; u++) {
-        run += (uint32_t)v[u];
-        c[u] = run;
+        for (int u = 0; u < BT_UNROLL; u++) {
+            run += (uint32_t)v[u];
+            if (j0 + u < k) pref[(j0 + u) * 32 + lane] = (C)run;
+        }
     }
+    return run;
 }
 
-__device__ __forceinline__ uint32_t pick(const uint32_t* c, int d) {
-    uint32_t x = c[0];
-#pragma unroll
-    for (int u = 1; u < BT_UNROLL; u++) x = (d == u) ? c[u] : x;
-    return x;
+// First bin j with pref[j * 32 + lane] >= need (k if none; the prefix is non-decreasing).
+template <typename C>
+__device__ __forceinline__ int first_bin(const C* pref, int k, int64_t need) {
+    const int lane = threadIdx.x & 31;
+    int lo = 0, len = k;
+    while (len > 0) {
+        const int half = len >> 1;
+        if ((int64_t)pref[(lo + half) * 32 + lane] < need) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return lo;
 }
 
 // Every warp takes a contiguous range of sorted edges whose ends are moved to run
 // starts, so that no directed pair's run is split between warps. It walks the range in
 // windows of at most 32 edges made of whole runs (lane = edge), or, for a run longer
 // than 32 edges, in 32-edge pieces of that run with per-query totals in shared memory.
+// For a window it keeps the prefix sums of its edges' bins in shared memory; per class
+// of queries each lane finds, by a binary search, the first bin at which its edge
+// certifies, and only the class's queries at or past the warp's smallest such bin are
+// evaluated (c_e(D_j) grows with j, so an edge certifies exactly for those bins). A
+// window whose edges have no witness at any window of the pass costs its bin reads only.
 template <typename C>
 __global__ void __launch_bounds__(BT_THREADS) k_batch_threshold(const BatchArgs a) {
-    __shared__ BatchQuery sq[BT_MAXQ];
-    __shared__ int32_t lmax[BT_WARPS][BT_MAXQ];
-    __shared__ int32_t lnc[BT_WARPS][BT_MAXQ];
+    extern __shared__ __align__(16) unsigned char bt_smem[];
+    BatchClass* scls = reinterpret_cast<BatchClass*>(bt_smem);
+    BatchQuery* sq = reinterpret_cast<BatchQuery*>(scls + a.ncls);
+    int32_t* lmax = reinterpret_cast<int32_t*>(sq + a.nq);  // [BT_WARPS][nq]
+    int32_t* lnc = lmax + BT_WARPS * a.nq;                  // [BT_WARPS][nq]
+    C* prefs = reinterpret_cast<C*>(lnc + BT_WARPS * a.nq);  // [BT_WARPS][k][32]
+    for (int i = threadIdx.x; i < a.ncls; i += blockDim.x) scls[i] = a.cls[i];
     for (int i = threadIdx.x; i < a.nq; i += blockDim.x) sq[i] = a.qs[i];
     __syncthreads();
     const C* bins = static_cast<const C*>(a.bins);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    C* pref = prefs + (int64_t)wib * a.k * 32;
+    int32_t* wmax = lmax + wib * a.nq;
+    int32_t* wnc = lnc + wib * a.nq;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t p = run_aligned(a.sd, a.seg, warp * a.per_warp, a.mk);
     const int64_t hi = run_aligned(a.sd, a.seg, (warp + 1) * a.per_warp, a.mk);
@@ -219,6 +261,10 @@ __global__ void __launch_bounds__(BT_THREADS) k_batch_threshold(const BatchArgs 
             const bool on = lane < L;
             const int64_t e = p + lane;
             const int32_t key = on ? a.sd[e] : -1;
+            const uint32_t cmax = bin_prefix<C>(bins, a.mk, a.k, e, on, pref);
+            p += L;
+            if (!__any_sync(0xffffffffu, cmax > 0)) continue;
+            __syncwarp();
             const int32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
             const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || key != prev);
             const unsigned above = heads & ~((2u << lane) - 1u);
@@ -226,39 +272,31 @@ __global__ void __launch_bounds__(BT_THREADS) k_batch_threshold(const BatchArgs 
             const unsigned peers = (above ? (above & (0u - above)) - 1u : 0xffffffffu) & ~((1u << start) - 1u);
             const bool leader = on && lane == start;
             int64_t uh = 0, ut = 0, uc = 0;
-            bool uload = false;
-            uint32_t run = 0;
-            int qi = 0;
-            for (int j0 = 0; j0 < a.k && qi < a.nq; j0 += BT_UNROLL) {
-                uint32_t c[BT_UNROLL];
-                bin_block<C>(bins, a.mk, a.k, j0, e, on, run, c);
-                const bool any = __any_sync(0xffffffffu, run > 0);  // c is non-decreasing in j
-                while (qi < a.nq && sq[qi].j < j0 + BT_UNROLL) {
-                    if (!any) {
-                        qi++;
-                        continue;
-                    }
-                    const BatchQuery q = sq[qi++];
-                    const uint32_t cq = pick(c, q.j - j0);
-                    if (cq > 0 && q.quant != FOLTY_Q_EXISTS && !uload) {
-                        universes(a, key, uh, ut, uc);
-                        uload = true;
-                    }
-                    const bool sat = certifies_q(q, cq, uh, ut, uc);
-                    if (!__any_sync(0xffffffffu, sat)) continue;
-                    const int rmax = __reduce_max_sync(peers, (int)cq);
+            if (cmax > 0) universes(a, key, uh, ut, uc);
+            for (int ci = 0; ci < a.ncls; ci++) {
+                const BatchClass c = scls[ci];
+                const int64_t need = needed(c, uh, ut, uc);
+                const int jmin = (cmax > 0 && (int64_t)cmax >= need) ? first_bin<C>(pref, a.k, need) : a.k;
+                const int jlo = __reduce_min_sync(0xffffffffu, jmin);
+                if (jlo > c.jmax) continue;  // no edge of the window certifies for this class
+                for (int qi = c.qb; qi < c.qe; qi++) {
+                    const BatchQuery q = sq[qi];
+                    if (q.j < jlo) continue;
+                    const bool sat = q.j >= jmin;
+                    const int cq = (int)pref[q.j * 32 + lane];
+                    const int rmax = __reduce_max_sync(peers, cq);
                     const int rsat = __reduce_add_sync(peers, sat ? 1 : 0);
                     emit_pairs(a, leader && rsat > 0, q.slot, key, rmax, rsat);
                 }
             }
-            p += L;
+            __syncwarp();
         } else {
             // ---- one run longer than 32 edges, in pieces
             const int32_t key = a.sd[p];
             const int64_t re = a.seg[key + 1];
             for (int i = lane; i < a.nq; i += 32) {
-                lmax[wib][i] = 0;
-                lnc[wib][i] = 0;
+                wmax[i] = 0;
+                wnc[i] = 0;
             }
             __syncwarp();
             int64_t uh, ut, uc;
@@ -266,36 +304,33 @@ __global__ void __launch_bounds__(BT_THREADS) k_batch_threshold(const BatchArgs 
             for (int64_t b = p; b < re; b += 32) {
                 const int64_t e = b + lane;
                 const bool on = e < re;
-                uint32_t run = 0;
-                int qi = 0;
-                for (int j0 = 0; j0 < a.k && qi < a.nq; j0 += BT_UNROLL) {
-                    uint32_t c[BT_UNROLL];
-                    bin_block<C>(bins, a.mk, a.k, j0, e, on, run, c);
-                    const bool any = __any_sync(0xffffffffu, run > 0);
-                    while (qi < a.nq && sq[qi].j < j0 + BT_UNROLL) {
-                        if (!any) {
-                            qi++;
-                            continue;
-                        }
-                        const int i = qi;
-                        const BatchQuery q = sq[qi++];
-                        const uint32_t cq = pick(c, q.j - j0);
-                        const bool sat = certifies_q(q, cq, uh, ut, uc);
-                        if (!__any_sync(0xffffffffu, sat)) continue;
-                        const int rmax = __reduce_max_sync(0xffffffffu, (int)cq);
-                        const int rsat = __reduce_add_sync(0xffffffffu, sat ? 1 : 0);
+                const uint32_t cmax = bin_prefix<C>(bins, a.mk, a.k, e, on, pref);
+                if (!__any_sync(0xffffffffu, cmax > 0)) continue;
+                __syncwarp();
+                for (int ci = 0; ci < a.ncls; ci++) {
+                    const BatchClass c = scls[ci];
+                    const int64_t need = needed(c, uh, ut, uc);
+                    const int jmin = (cmax > 0 && (int64_t)cmax >= need) ? first_bin<C>(pref, a.k, need) : a.k;
+                    const int jlo = __reduce_min_sync(0xffffffffu, jmin);
+                    if (jlo > c.jmax) continue;
+                    for (int qi = c.qb; qi < c.qe; qi++) {
+                        const BatchQuery q = sq[qi];
+                        if (q.j < jlo) continue;
+                        const int rmax = __reduce_max_sync(0xffffffffu, (int)pref[q.j * 32 + lane]);
+                        const int rsat = __reduce_add_sync(0xffffffffu, q.j >= jmin ? 1 : 0);
                         if (lane == 0) {
-                            lmax[wib][i] = max(lmax[wib][i], rmax);
-                            lnc[wib][i] += rsat;
+                            wmax[qi] = max(wmax[qi], rmax);
+                            wnc[qi] += rsat;
                         }
                     }
                 }
+                __syncwarp();
             }
             __syncwarp();
             for (int i0 = 0; i0 < a.nq; i0 += 32) {
                 const int i = i0 + lane;
-                const bool emit = i < a.nq && lnc[wib][i] > 0;
-                emit_pairs(a, emit, emit ? sq[i].slot : 0, key, emit ? lmax[wib][i] : 0, emit ? lnc[wib][i] : 0);
+                const bool emit = i < a.nq && wnc[i] > 0;
+                emit_pairs(a, emit, emit ? sq[i].slot : 0, key, emit ? wmax[i] : 0, emit ? wnc[i] : 0);
             }
             __syncwarp();
             p = re;
@@ -402,20 +437,49 @@ static void fused_threshold(folty_graph* g, const C* bins, int k, const std::vec
     const int64_t S = g->S;
     Scratch sc(g->alloc, s, g->dev_err);
     const int32_t* prank = pair_ranks(g, s);
-    // the queries sorted by bin
-    std::vector<BatchQuery> hq((size_t)nq);
-    std::vector<int> order((size_t)nq);
-    for (int i = 0; i < nq; i++) order[(size_t)i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return fj[(size_t)x] < fj[(size_t)y]; });
+    // classes of queries that differ only in their window (quantifier, universe and rho
+    // in lowest terms; rho is irrelevant to the existential quantifier), each sorted by bin
+    struct Key {
+        int quant, universe;
+        int64_t num, den;
+        bool operator<(const Key& o) const {
+            return std::tie(quant, universe, num, den) < std::tie(o.quant, o.universe, o.num, o.den);
+        }
+    };
+    std::map<Key, std::vector<int>> groups;
     for (int i = 0; i < nq; i++) {
-        const folty_query_params& q = *fq[(size_t)order[(size_t)i]];
-        hq[(size_t)i] = BatchQuery{fj[(size_t)order[(size_t)i]], order[(size_t)i], (int)q.quant, (int)q.universe,
-                                   (int64_t)q.rho_num, (int64_t)q.rho_den};
+        const folty_query_params& q = *fq[(size_t)i];
+        Key key{(int)q.quant, (int)q.universe, (int64_t)q.rho_num, (int64_t)q.rho_den};
+        if (q.quant == FOLTY_Q_EXISTS) key = Key{FOLTY_Q_EXISTS, 0, 0, 1};
+        else {
+            const int64_t gcd = std::gcd(key.num, key.den);
+            key.num /= gcd;
+            key.den /= gcd;
+        }
+        groups[key].push_back(i);
     }
+    std::vector<BatchClass> hc;
+    std::vector<BatchQuery> hq;
+    for (auto& kv : groups) {
+        std::vector<int>& v = kv.second;
+        std::stable_sort(v.begin(), v.end(), [&](int x, int y) { return fj[(size_t)x] < fj[(size_t)y]; });
+        BatchClass c{kv.first.quant, kv.first.universe, kv.first.num, kv.first.den, (int32_t)hq.size(), 0, 0, 0};
+        for (int i : v) hq.push_back(BatchQuery{fj[(size_t)i], i});
+        c.qe = (int32_t)hq.size();
+        c.jmax = hq.back().j;
+        hc.push_back(c);
+    }
+    const int ncls = (int)hc.size();
+    BatchClass* dc = sc.get<BatchClass>(ncls);
     BatchQuery* dq = sc.get<BatchQuery>(nq);
+    FOLTY_CUDA(cudaMemcpyAsync(dc, hc.data(), sizeof(BatchClass) * (size_t)ncls, cudaMemcpyHostToDevice, s));
     FOLTY_CUDA(cudaMemcpyAsync(dq, hq.data(), sizeof(BatchQuery) * (size_t)nq, cudaMemcpyHostToDevice, s));
+    // shared memory: classes, queries, per-warp long-run totals, per-warp prefix sums
+    const size_t smem = sizeof(BatchClass) * (size_t)ncls + sizeof(BatchQuery) * (size_t)nq +
+                        2 * sizeof(int32_t) * BT_WARPS * (size_t)nq + sizeof(C) * BT_WARPS * 32 * (size_t)k;
+    FOLTY_CUDA(cudaFuncSetAttribute(k_batch_threshold<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_threshold<C>, BT_THREADS, 0));
+    FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_threshold<C>, BT_THREADS, smem));
     const int64_t blocks = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
     const int64_t nwarps = blocks * BT_WARPS;
     BatchArgs a{};
@@ -429,6 +493,8 @@ static void fused_threshold(folty_graph* g, const C* bins, int k, const std::vec
     a.deg = g->deg;
     a.common = g->common;
     a.prank = prank;
+    a.cls = dc;
+    a.ncls = ncls;
     a.qs = dq;
     a.nq = nq;
     a.rb = bit_length((uint64_t)(2 * S > 1 ? 2 * S - 1 : 1));
@@ -450,7 +516,7 @@ static void fused_threshold(folty_graph* g, const C* bins, int k, const std::vec
         FOLTY_CUDA(cudaMemsetAsync(a.n_out, 0, sizeof(unsigned long long), s));
         {
             StageSpan span(ST_BATCH, s, (int64_t)k * (int64_t)sizeof(C) * mk + 4 * mk);
-            if (mk > 0) FOLTY_LAUNCH(k_batch_threshold<C>, (unsigned)blocks, BT_THREADS, 0, s, a);
+            if (mk > 0) FOLTY_LAUNCH(k_batch_threshold<C>, (unsigned)blocks, BT_THREADS, smem, s, a);
         }
         n_out = read_i64(g, (const int64_t*)a.n_out, s);
         if (n_out > cap) {  // the buffer was too small: run again with room for all
@@ -548,6 +614,11 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
         const int64_t budget = bin_budget > 0 ? bin_budget : batch_bin_budget_bytes();
         int64_t chunk = per_bin > 0 ? budget / per_bin : (int64_t)D.size();
         chunk = std::max<int64_t>(1, std::min<int64_t>({chunk, (int64_t)BATCH_MAX_BINS, (int64_t)D.size()}));
+        // the fused pass keeps every window's prefix sums in shared memory: at most BT_KMAX
+        // 16-bit (BT_KMAX / 2 32-bit) bins per probe pass when plain queries are present
+        bool plain = false;
+        for (int i : members) plain = plain || plain_query(qs[i]);
+        if (plain) chunk = std::min<int64_t>(chunk, b16 ? BT_KMAX : BT_KMAX / 2);
         for (size_t c0 = 0; c0 < D.size(); c0 += (size_t)chunk) {
             const int k = (int)std::min<int64_t>(chunk, (int64_t)D.size() - (int64_t)c0);
             Scratch sc(g->alloc, s, g->dev_err);

@@ -1942,14 +1942,12 @@ __device__ __forceinline__ void warp_intersect(const int32_t* __restrict__ nbr, 
 __global__ void k_tri_count(const int32_t* __restrict__ outptr, const int32_t* __restrict__ out_nbr,
                             const int32_t* __restrict__ out_src, const int32_t* __restrict__ out_eid,
                             const int32_t* __restrict__ sig, int32_t S, int32_t* __restrict__ cnt,
-                            unsigned long long* __restrict__ merged, unsigned long long* __restrict__ probes,
-                            int min_out) {
+                            unsigned long long* __restrict__ merged, unsigned long long* __restrict__ probes) {
     unsigned long long acc = 0, pacc = 0;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < S;
          j += (int64_t)gridDim.x * blockDim.x) {
         int32_t u = out_src[j], v = out_nbr[j];
         int32_t i1 = outptr[u], e1 = outptr[u + 1], i2 = outptr[v], e2 = outptr[v + 1];
-        if (e1 - i1 < min_out) continue;  // the vertex-centric pass has this edge
         acc += (unsigned long long)((e1 - i1) + (e2 - i2));
         int32_t c = 0;
         unsigned long long ps = 0;
@@ -1997,8 +1995,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
                                                            const int32_t* __restrict__ out_src, int32_t S,
                                                            const int64_t* __restrict__ toff,
                                                            const int32_t* __restrict__ sig, int4* __restrict__ tri,
-                                                           int64_t* __restrict__ cost, int32_t* __restrict__ common,
-                                                           int min_out) {
+                                                           int64_t* __restrict__ cost, int32_t* __restrict__ common) {
     __shared__ int32_t stage[TRI_THREADS / 32][TRI_STAGE];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -2014,9 +2011,8 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
             i2 = outptr[v];
             e2 = outptr[v + 1];
         }
-        const bool mine = j < S && e1 - i1 >= min_out;  // else the vertex-centric pass has it
-        const bool heavy = mine && (e1 - i1) + (e2 - i2) > TRI_HEAVY && e2 - i2 <= TRI_STAGE;
-        if (mine && !heavy) {
+        const bool heavy = j < S && (e1 - i1) + (e2 - i2) > TRI_HEAVY && e2 - i2 <= TRI_STAGE;
+        if (j < S && !heavy) {
             int64_t p = toff[j];
             int32_t n_here = 0;
             const int32_t sig_uv = sig[s_uv];
@@ -2065,210 +2061,6 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
                 n_here += __popc(m);
             });
             if (lane == 0 && n_here) atomicAdd(&common[hs], n_here);
-        }
-    }
-}
-
-// Vertex-centric triangle passes for vertices of out-degree at most TV_CAP (every vertex
-// when the degeneracy is at most TV_CAP): one warp per vertex u stages N+(u) (ascending
-// ids, with the sigma, static edge and row start of every out-neighbour v) in shared
-// memory once, then walks the concatenation of the lists N+(v), v in N+(u), 32 entries at
-// a time, each lane testing its entry w for membership in N+(u) by a binary search in
-// shared memory. Every test is independent of the others (no merge chain), N+(u) is read
-// once per u instead of once per edge, and the lanes stay busy whatever the lengths of the
-// single lists. Edge (u, v_i) finds its triangles in ascending w, as the edge-centric
-// merge does, so both passes number the triangles the same way.
-constexpr int TV_CAP = 256;
-constexpr int TV_WARPS = 4;
-
-struct TriVStage {
-    int32_t nbr[TV_CAP];      // N+(u)
-    int32_t sig[TV_CAP];      // sigma of the static edge u - nbr[i]
-    int32_t eid[TV_CAP];      // its static edge id
-    int32_t row[TV_CAP];      // outptr[nbr[i]]
-    int32_t pre[TV_CAP + 1];  // prefix of |N+(nbr[i])|
-    int32_t cnt[TV_CAP];      // triangles of edge (u, nbr[i]) found so far
-    int32_t hitw[TV_CAP];     // triangles in which u - nbr[i] is the edge u - w
-};
-
-// Stages u's out-list; returns the number of (v, w) entries to test.
-__device__ __forceinline__ int32_t tv_stage(TriVStage& st, const int32_t* __restrict__ outptr,
-                                            const int32_t* __restrict__ out_nbr, const int32_t* __restrict__ out_eid,
-                                            const int32_t* __restrict__ sig, int32_t ou, int32_t du) {
-    const int lane = threadIdx.x & 31;
-    int32_t carry = 0;
-    for (int32_t i0 = 0; i0 < du; i0 += 32) {
-        const int32_t i = i0 + lane;
-        int32_t d = 0;
-        if (i < du) {
-            const int32_t v = out_nbr[ou + i], e = out_eid[ou + i], r = outptr[v];
-            st.nbr[i] = v;
-            st.eid[i] = e;
-            st.sig[i] = sig[e];
-            st.row[i] = r;
-            st.cnt[i] = 0;
-            st.hitw[i] = 0;
-            d = outptr[v + 1] - r;
-        }
-        int32_t inc = d;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (i < du) st.pre[i] = carry + inc - d;
-        carry += __shfl_sync(0xffffffffu, inc, 31);
-    }
-    if (lane == 0) st.pre[du] = carry;
-    __syncwarp();
-    return carry;
-}
-
-// Entry q of the concatenated lists: out-neighbour index i (largest with pre[i] <= q).
-__device__ __forceinline__ int32_t tv_owner(const TriVStage& st, int32_t du, int32_t q) {
-    int32_t lo = 0, hi = du - 1;
-    while (lo < hi) {
-        const int32_t mid = (lo + hi + 1) >> 1;
-        if (st.pre[mid] <= q) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Position of w in the staged N+(u), or -1.
-__device__ __forceinline__ int32_t tv_find(const TriVStage& st, int32_t du, int32_t w) {
-    int32_t lo = 0, len = du;
-    while (len > 1) {
-        const int32_t half = len >> 1;
-        lo = (st.nbr[lo + half - 1] < w) ? lo + half : lo;
-        len -= half;
-    }
-    if (len == 1 && st.nbr[lo] < w) lo++;
-    return (lo < du && st.nbr[lo] == w) ? lo : -1;
-}
-
-// The next batch of 32 vertices for a warp; returns the lanes' mask of those of out-degree in
-// [1, TV_CAP] (out-degree 1 only zeroes its edge's count).
-__device__ __forceinline__ unsigned tv_fetch(unsigned int* next, int32_t n, const int32_t* __restrict__ outptr,
-                                             int32_t& u0) {
-    const int lane = threadIdx.x & 31;
-    unsigned int b = 0;
-    if (lane == 0) b = atomicAdd(next, 32u);
-    b = __shfl_sync(0xffffffffu, b, 0);
-    u0 = (int32_t)b;
-    const int32_t u = (int32_t)b + lane;
-    int32_t du = 0;
-    if ((int64_t)b + lane < n) du = outptr[u + 1] - outptr[u];
-    return __ballot_sync(0xffffffffu, du >= 1 && du <= TV_CAP);
-}
-
-__global__ void __launch_bounds__(TV_WARPS * 32) k_tri_count_v(const int32_t* __restrict__ outptr,
-                                                              const int32_t* __restrict__ out_nbr,
-                                                              const int32_t* __restrict__ out_eid,
-                                                              const int32_t* __restrict__ sig, int32_t n,
-                                                              unsigned int* next, int32_t* __restrict__ cnt,
-                                                              unsigned long long* __restrict__ merged,
-                                                              unsigned long long* __restrict__ probes) {
-    __shared__ TriVStage stages[TV_WARPS];
-    TriVStage& st = stages[threadIdx.x >> 5];
-    const int lane = threadIdx.x & 31;
-    unsigned long long acc = 0, pacc = 0;
-    while (true) {
-        int32_t u0;
-        unsigned todo = tv_fetch(next, n, outptr, u0);
-        if ((int64_t)u0 >= n) break;
-        while (todo) {
-            const int32_t u = u0 + __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int32_t ou = outptr[u], du = outptr[u + 1] - ou;
-            if (du == 1) {
-                if (lane == 0) cnt[ou] = 0;
-                acc += (lane == 0) ? 1ull + (unsigned long long)(outptr[out_nbr[ou] + 1] - outptr[out_nbr[ou]]) : 0ull;
-                continue;
-            }
-            const int32_t total = tv_stage(st, outptr, out_nbr, out_eid, sig, ou, du);
-            if (lane == 0) acc += (unsigned long long)du * (unsigned long long)du + (unsigned long long)total;
-            for (int32_t q0 = 0; q0 < total; q0 += 32) {
-                const int32_t q = q0 + lane;
-                if (q < total) {
-                    const int32_t i = tv_owner(st, du, q);
-                    const int32_t at = st.row[i] + (q - st.pre[i]);
-                    const int32_t pos = tv_find(st, du, out_nbr[at]);
-                    if (pos >= 0) {
-                        atomicAdd(&st.cnt[i], 1);
-                        pacc += (unsigned long long)(st.sig[i] + st.sig[pos] + sig[out_eid[at]]);
-                    }
-                }
-            }
-            __syncwarp();
-            for (int32_t i = lane; i < du; i += 32) cnt[ou + i] = st.cnt[i];
-            __syncwarp();
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        pacc += __shfl_xor_sync(0xffffffffu, pacc, o);
-    }
-    if (lane == 0 && acc) atomicAdd(merged, acc);
-    if (lane == 0 && pacc) atomicAdd(probes, pacc);
-}
-
-__global__ void __launch_bounds__(TV_WARPS * 32) k_tri_write_v(const int32_t* __restrict__ outptr,
-                                                              const int32_t* __restrict__ out_nbr,
-                                                              const int32_t* __restrict__ out_eid,
-                                                              const int32_t* __restrict__ sig, int32_t n,
-                                                              unsigned int* next, const int64_t* __restrict__ toff,
-                                                              int4* __restrict__ tri, int64_t* __restrict__ cost,
-                                                              int32_t* __restrict__ common) {
-    __shared__ TriVStage stages[TV_WARPS];
-    TriVStage& st = stages[threadIdx.x >> 5];
-    const int lane = threadIdx.x & 31;
-    while (true) {
-        int32_t u0;
-        unsigned todo = tv_fetch(next, n, outptr, u0);
-        if ((int64_t)u0 >= n) break;
-        while (todo) {
-            const int32_t u = u0 + __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int32_t ou = outptr[u], du = outptr[u + 1] - ou;
-            if (du < 2) continue;
-            const int32_t total = tv_stage(st, outptr, out_nbr, out_eid, sig, ou, du);
-            for (int32_t q0 = 0; q0 < total; q0 += 32) {
-                const int32_t q = q0 + lane;
-                const bool on = q < total;
-                int32_t i = du, at = 0, pos = -1;  // past-the-end lanes: a segment of their own
-                if (on) {
-                    i = tv_owner(st, du, q);
-                    at = st.row[i] + (q - st.pre[i]);
-                    pos = tv_find(st, du, out_nbr[at]);
-                }
-                const bool hit = pos >= 0;
-                // lanes of one out-neighbour index are contiguous: rank of each hit among
-                // the hits of its edge (u, v_i) in this chunk, after those of earlier chunks
-                const int32_t prev = __shfl_up_sync(0xffffffffu, i, 1);
-                const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || i != prev);
-                const unsigned hm = __ballot_sync(0xffffffffu, hit);
-                const int start = 31 - __clz(heads & ((2u << lane) - 1u));
-                const unsigned above = heads & ~((2u << lane) - 1u);
-                const unsigned seg = (above ? (above & (0u - above)) - 1u : 0xffffffffu) & ~((1u << start) - 1u);
-                if (hit) {
-                    const int64_t p = toff[ou + i] + st.cnt[i] + __popc(hm & seg & ((1u << lane) - 1u));
-                    const int32_t w = st.nbr[pos], v = st.nbr[i], s_vw = out_eid[at];
-                    const int flags = (u < v ? 1 : 0) | (u < w ? 2 : 0) | (v < w ? 4 : 0);
-                    tri[p] = make_int4(st.eid[i], st.eid[pos], s_vw, flags);
-                    cost[p] = (int64_t)st.sig[i] + st.sig[pos] + sig[s_vw];
-                    atomicAdd(&st.hitw[pos], 1);
-                    atomicAdd(&common[s_vw], 1);
-                }
-                __syncwarp();
-                if (on && lane == start) st.cnt[i] += __popc(hm & seg);
-                __syncwarp();
-            }
-            // edge u - v_i: its own triangles and those in which it is the edge u - w
-            for (int32_t i = lane; i < du; i += 32)
-                if (st.cnt[i] + st.hitw[i]) atomicAdd(&common[st.eid[i]], st.cnt[i] + st.hitw[i]);
-            __syncwarp();
         }
     }
 }
@@ -2720,15 +2512,9 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     // the counting pass merges the two out-lists of every oriented edge: 4 B per merged
     // entry (known after the read-back below) + 8 B per static edge
     StageSpan tri_span(ST_TRIANGLES, s, 8 * (int64_t)S);
-    unsigned int* tv_next = sc.get<unsigned int>(2);  // vertex counters of the two vertex-centric passes
-    FOLTY_CUDA(cudaMemsetAsync(tv_next, 0, 2 * sizeof(unsigned int), s));
-    if (S > 0) {
-        FOLTY_LAUNCH(k_tri_count_v, (unsigned)(num_sms() * 8), TV_WARPS * 32, 0, s, outptr, out_nbr, out_eid, sig, n,
-                     tv_next, tcnt, merged, merged + 1);
-        // vertices of out-degree above TV_CAP, edge by edge
+    if (S > 0)
         FOLTY_LAUNCH(k_tri_count, grid_for(S, T), T, 0, s, outptr, out_nbr, out_src, out_eid, sig, S, tcnt, merged,
-                     merged + 1, TV_CAP + 1);
-    }
+                     merged + 1);
     exclusive_scan(sc, tcnt, toff, S);
     tri_span.end();
     FOLTY_LAUNCH(k_max_i32, grid_for(n, T), T, 0, s, g->deg, (int64_t)n, stat + 0);
@@ -2760,10 +2546,8 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     if (S > 0) {
         // the listing pass merges the same lists and writes 16 + 8 B per triangle
         StageSpan span(ST_TRIANGLES, s, g->enum_bytes + 24 * ntri);
-        FOLTY_LAUNCH(k_tri_write_v, (unsigned)(num_sms() * 8), TV_WARPS * 32, 0, s, outptr, out_nbr, out_eid, sig, n,
-                     tv_next + 1, toff, g->tri, cost, g->common);
         FOLTY_LAUNCH(k_tri_write, grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr, out_eid, out_src, S, toff, sig,
-                     g->tri, cost, g->common, TV_CAP + 1);
+                     g->tri, cost, g->common);
     }
     exclusive_scan(sc, cost, g->tri_off, ntri);
     g->info.triangles = ntri;

@@ -70,6 +70,54 @@ def test_results_alone_equal_results_in_the_mix(F, graphs):
         assert r["info"]["latency_ms"] >= r["info"]["run_ms"] >= 0
 
 
+def test_poisson_arrivals_results_equal_results_alone(F, graphs):
+    """Queries arriving one by one at Poisson times (3,000 per second over 2 s, each for a
+    uniformly drawn graph), submitted from one thread as they arrive and collected by
+    another: every result equals folty_query alone, and queries that arrived while a batch
+    ran were batched together."""
+    import queue
+    import time
+    rng = np.random.default_rng(23)
+    arrivals = np.cumsum(rng.exponential(1.0 / 3000.0, 6000))
+    arrivals = arrivals[arrivals < 2.0]
+    qs = _mix(rng, len(arrivals))
+    gis = rng.integers(0, len(graphs), len(arrivals))
+    sv = F.folty_server_create([G.handle for G in graphs])
+    got = []
+    try:
+        pending = queue.Queue()
+
+        def collect():
+            while True:
+                t = pending.get()
+                if t is None:
+                    return
+                got.append(F.folty_server_wait(sv, t, timeout_ms=120_000))
+
+        th = threading.Thread(target=collect)
+        th.start()
+        t0 = time.perf_counter()
+        for at, q, gi in zip(arrivals, qs, gis):
+            delay = t0 + at - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            pending.put(F.folty_server_submit(sv, int(gi), q))
+        pending.put(None)
+        th.join()
+        stats = F.folty_server_get_stats(sv)
+    finally:
+        F.folty_server_destroy(sv)
+    assert len(got) == len(arrivals) and stats["queries"] == len(arrivals)
+    assert max(r["info"]["batch_size"] for r in got) > 1
+    alone = {}
+    for q, gi, r in zip(qs, gis, got):
+        assert r["info"]["graph_index"] == gi
+        key = (int(gi), q)
+        if key not in alone:
+            alone[key] = graphs[int(gi)].query(q)
+        assert _same(r, alone[key]), (gi, q)
+
+
 def test_memory_budget_admits_one_query_at_a_time(F, graphs):
     rng = np.random.default_rng(22)
     jobs = [(int(rng.integers(0, len(graphs))), q) for q in _mix(rng, 30)]
