@@ -438,9 +438,11 @@ def time_queries(F, g, d_src, d_dst, d_t, sh, stream, queries, reps=10):
                      "kept_role_fraction": st["kept_roles"] / max(st["all_roles"], 1),
                      "select_model_bytes": st["select_bytes"], "probe_model_bytes": st["probe_bytes"]})
     tm = F.folty_graph_traffic_model(h, W.DIR_OUT, sh)
+    tuning = F.folty_graph_tuning(h)
     F.folty_free(h)
     return {"load_ms": float(np.median(load_ms)), "preprocess_ms": float(np.median(pre_ms)),
-            "query_ms": q_ms, "kept": kept, "info": info, "all_roles_probe_model_bytes": tm["probe_bytes"]}
+            "query_ms": q_ms, "kept": kept, "info": info, "all_roles_probe_model_bytes": tm["probe_bytes"],
+            "tuning": tuning}
 
 
 def main():
@@ -633,7 +635,11 @@ def main():
         "query": {"metric": "m / t_query (device time of folty_query alone, preprocessing excluded)",
                   "query_ms": q_ms, "edges_per_s": [g.m / (x / 1e3) for x in q_ms],
                   "load_ms": qt["load_ms"], "preprocess_ms": qt["preprocess_ms"], "kept": qt["kept"],
-                  "all_roles_probe_model_bytes": qt["all_roles_probe_model_bytes"]},
+                  "all_roles_probe_model_bytes": qt["all_roles_probe_model_bytes"],
+                  "note": "the probe stage's algorithmic bytes count the kept roles only (kept_* and "
+                          "probe_model_bytes per query); all_roles_probe_model_bytes is the model of probing "
+                          "every role, which the liveness selection avoids"},
+        "tuning": qt["tuning"],
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": roofline,

@@ -307,6 +307,37 @@ folty_status folty_server_get_stats(folty_server *sv, folty_server_stats *out);
 /* Runs every queued query, stops the workers and frees uncollected results. */
 void folty_server_destroy(folty_server *sv);
 
+/* ------------------------------------------------------------------ autotuning
+ * The library picks two kernel shapes per graph by timed trials on the device: the split
+ * of the triangle passes between one thread and one whole warp per oriented edge (by
+ * the total length of the edge's two out-lists), and the probe tile (the granularity in
+ * which the flat probe space of the kept roles is partitioned over thread blocks) with
+ * the probe kernel's blocks per SM. The split is timed during folty_preprocess, the
+ * probe shape on the graph's first query; both are cached for the process under the
+ * graph's statistics (sizes, triangles, probes), so later graphs of the same statistics
+ * skip the trials. Every shape gives the same results. */
+typedef struct {
+    int32_t tri_heavy;           /* an oriented edge whose two out-lists hold more entries is
+                                    intersected by a warp, otherwise by one thread          */
+    int32_t probe_items;         /* probe tile = 256 * probe_items slots (4 or 8)          */
+    int32_t probe_blocks_per_sm; /* 0: as many as fit                                      */
+    int32_t tri_source;          /* 0 not yet chosen, 1 timed trials, 2 cache, 3 forced    */
+    int32_t probe_source;
+    float tri_ms[4];             /* trial times of the candidate splits (24, 48, 96, never) */
+    float probe_ms[4];           /* of the candidate shapes (4, all), (8, all), (8, 2), (4, 4) */
+} folty_tuning;
+
+/* The shapes chosen for g. Errors: FOLTY_EINVAL (NULL), FOLTY_ESTATE (not preprocessed). */
+folty_status folty_graph_tuning(const folty_graph *g, folty_tuning *out);
+
+/* Uses the given shapes for every graph preprocessed or first queried afterwards instead
+ * of tuning (all three 0: tune again). Errors: FOLTY_EINVAL (tri_heavy < 1, probe_items
+ * not 4 or 8, probe_blocks_per_sm < 0). */
+folty_status folty_tuning_force(int32_t tri_heavy, int32_t probe_items, int32_t probe_blocks_per_sm);
+
+/* Forgets the cached shapes (the next graph of any statistics is tuned by trials). */
+void folty_tuning_clear_cache(void);
+
 /* Per-edge counts of one query without allocating anything (the paper has no
  * counterpart). For callers that cannot allocate device memory when they query: a
  * serving process that reserved its whole memory budget at start-up, latency-bound code

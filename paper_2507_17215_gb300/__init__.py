@@ -32,7 +32,7 @@ EXPORTED = ["folty_load_temporal_graph", "folty_preprocess", "folty_query", "fol
             "folty_free", "folty_last_error", "folty_graph_get_info", "folty_graph_traffic_model",
             "folty_kernel_launches", "folty_profile_enable", "folty_profile_read",
             "folty_edge_counts_noalloc", "folty_graph_common_counts", "folty_graph_core_numbers",
-            "folty_graph_probe_stats",
+            "folty_graph_probe_stats", "folty_graph_tuning", "folty_tuning_force", "folty_tuning_clear_cache",
             "folty_server_create", "folty_server_submit",
             "folty_server_wait", "folty_server_get_stats", "folty_server_destroy"]
 
@@ -107,6 +107,15 @@ class folty_probe_stats(Structure):
                 ("select_bytes", c_int64), ("probe_bytes", c_int64)]
 
 
+class folty_tuning(Structure):
+    _fields_ = [("tri_heavy", c_int32), ("probe_items", c_int32), ("probe_blocks_per_sm", c_int32),
+                ("tri_source", c_int32), ("probe_source", c_int32), ("tri_ms", ctypes.c_float * 4),
+                ("probe_ms", ctypes.c_float * 4)]
+
+
+TUNE_SOURCES = {0: "default", 1: "timed trials", 2: "cache", 3: "forced"}
+
+
 class folty_traffic_model(Structure):
     _fields_ = [("enum_bytes", c_int64), ("probe_bytes", c_int64), ("threshold_bytes", c_int64)]
 
@@ -143,6 +152,12 @@ def _load_library():
     lib.folty_profile_enable.argtypes = [c_int32]
     lib.folty_profile_read.restype = c_int32
     lib.folty_profile_read.argtypes = [c_int32, POINTER(folty_stage_profile)]
+    lib.folty_graph_tuning.restype = c_int32
+    lib.folty_graph_tuning.argtypes = [G, POINTER(folty_tuning)]
+    lib.folty_tuning_force.restype = c_int32
+    lib.folty_tuning_force.argtypes = [c_int32, c_int32, c_int32]
+    lib.folty_tuning_clear_cache.restype = None
+    lib.folty_tuning_clear_cache.argtypes = []
     lib.folty_graph_probe_stats.restype = c_int32
     lib.folty_graph_probe_stats.argtypes = [G, c_int64, c_int32, POINTER(folty_probe_stats), c_void_p]
     lib.folty_graph_common_counts.restype = c_int32
@@ -346,6 +361,25 @@ def folty_graph_probe_stats(g: int, delta: int, dir: int, stream: Optional[int] 
     _check(lib.folty_graph_probe_stats(g, int(delta), int(dir), ctypes.byref(out),
                                        current_stream() if stream is None else stream))
     return {name: int(getattr(out, name)) for name, _ in folty_probe_stats._fields_}
+
+
+def folty_graph_tuning(g: int) -> Dict[str, object]:
+    """The kernel shapes chosen for a graph and how (trials, cache, forced)."""
+    t = folty_tuning()
+    _check(lib.folty_graph_tuning(g, ctypes.byref(t)))
+    return {"tri_heavy": int(t.tri_heavy), "probe_items": int(t.probe_items),
+            "probe_tile": 256 * int(t.probe_items), "probe_blocks_per_sm": int(t.probe_blocks_per_sm),
+            "tri_source": TUNE_SOURCES.get(int(t.tri_source)), "probe_source": TUNE_SOURCES.get(int(t.probe_source)),
+            "tri_trial_ms": [float(x) for x in t.tri_ms], "probe_trial_ms": [float(x) for x in t.probe_ms]}
+
+
+def folty_tuning_force(tri_heavy: int = 0, probe_items: int = 0, probe_blocks_per_sm: int = 0) -> None:
+    """Fixed shapes for graphs preprocessed or first queried afterwards (all 0: tune again)."""
+    _check(lib.folty_tuning_force(int(tri_heavy), int(probe_items), int(probe_blocks_per_sm)))
+
+
+def folty_tuning_clear_cache() -> None:
+    lib.folty_tuning_clear_cache()
 
 
 def folty_graph_core_numbers(g: int, stream: Optional[int] = None) -> np.ndarray:

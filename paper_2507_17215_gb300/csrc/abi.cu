@@ -685,6 +685,24 @@ folty_status folty_graph_traffic_model(folty_graph* g, int32_t dir, folty_traffi
     });
 }
 
+folty_status folty_graph_tuning(const folty_graph* g, folty_tuning* out) {
+    return guarded([&] {
+        folty_graph* gg = checked_graph(g);
+        if (!out) fail(FOLTY_EINVAL, "out is NULL");
+        if (gg->state != 1) fail(FOLTY_ESTATE, "graph not preprocessed");
+        const TuneParams& t = gg->tune;
+        out->tri_heavy = t.tri_heavy;
+        out->probe_items = t.probe_items;
+        out->probe_blocks_per_sm = t.probe_blocks;
+        out->tri_source = t.tri_source;
+        out->probe_source = t.probe_source;
+        for (int i = 0; i < 4; i++) {
+            out->tri_ms[i] = t.tri_ms[i];
+            out->probe_ms[i] = t.probe_ms[i];
+        }
+    });
+}
+
 folty_status folty_graph_probe_stats(folty_graph* g, int64_t delta, int32_t dir, folty_probe_stats* out,
                                      void* stream) {
     return guarded([&] {

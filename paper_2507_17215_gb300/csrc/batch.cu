@@ -30,17 +30,19 @@ namespace folty {
 constexpr int BATCH_MAX_BINS = 1024;
 static_assert(BATCH_MAX_BINS * sizeof(int64_t) <= 4 * PAIR_STAGE * sizeof(int32_t), "bin bounds fit the pair stage");
 
-// bins[j][e] <- sum_{i <= j} bins[i][e]
+// Bins are edge-major: the kstride bins of sorted edge e are contiguous (k used, the rest
+// zero), so that a thread reads an edge's bins with 16-byte loads.
+//
+// out[e] = c_e(D_j) = sum_{i <= j} bins[e][i]: the counts of one window (a query that
+// wants per-edge outputs goes through the single-query threshold path on them).
 template <typename C>
-__global__ void k_bins_prefix(C* __restrict__ bins, int k, int64_t mk) {
+__global__ void k_bins_column(const C* __restrict__ bins, int kstride, int j, int64_t mk, C* __restrict__ out) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < mk;
          e += (int64_t)gridDim.x * blockDim.x) {
+        const C* row = bins + e * kstride;
         uint32_t run = 0;
-        for (int j = 0; j < k; j++) {
-            int64_t o = (int64_t)j * mk + e;
-            run += bins[o];
-            bins[o] = (C)run;
-        }
+        for (int i = 0; i <= j; i++) run += row[i];
+        out[e] = (C)run;
     }
 }
 
@@ -94,7 +96,7 @@ static const int32_t* pair_ranks(folty_graph* g, cudaStream_t s) {
 constexpr int BT_THREADS = 256;
 constexpr int BT_WARPS = BT_THREADS / 32;
 constexpr int BT_MAXQ = 256;  // queries of one fused pass
-constexpr int BT_UNROLL = 8;  // bins loaded together per lane
+constexpr int BT_CHUNKS = 4;  // 16-byte chunks of an edge's bins loaded together per lane
 // bins of one fused pass (their prefix sums sit in shared memory, per warp and lane)
 constexpr int BT_KMAX = 128;
 
@@ -113,8 +115,8 @@ struct BatchQuery {
 };
 
 struct BatchArgs {
-    const void* bins;  // C[k][mk]
-    int k;
+    const void* bins;  // C[mk][kstride], k bins used per row
+    int k, kstride;
     int64_t mk;
     const int32_t* sd;   // 2 * static edge + direction of every sorted edge
     const int32_t* seg;  // run bounds: run r = [seg[r], seg[r + 1])
@@ -184,21 +186,30 @@ __device__ __forceinline__ void emit_pairs(const BatchArgs& a, bool emit, int sl
     }
 }
 
-// Prefix sums c_e(D_j) of the bins of one lane's edge into pref[j * 32 + lane] (zeros for
-// an idle lane), BT_UNROLL bins' loads in flight together; returns c_e(D_{k-1}).
+// Prefix sums c_e(D_j) of the bins of one lane's edge (its row of kstride bins) into
+// pref[j * 32 + lane] (zeros for an idle lane), BT_CHUNKS 16-byte loads in flight
+// together; returns c_e(D_{k-1}).
 template <typename C>
-__device__ __forceinline__ uint32_t bin_prefix(const C* __restrict__ bins, int64_t mk, int k, int64_t e, bool on,
+__device__ __forceinline__ uint32_t bin_prefix(const C* __restrict__ bins, int kstride, int k, int64_t e, bool on,
                                                C* pref) {
+    constexpr int PER = 16 / sizeof(C);  // bins per 16-byte chunk of a row
     const int lane = threadIdx.x & 31;
+    const uint4* row = reinterpret_cast<const uint4*>(bins + e * (int64_t)kstride);
+    const int nch = (k + PER - 1) / PER;
     uint32_t run = 0;
-    for (int j0 = 0; j0 < k; j0 += BT_UNROLL) {
-        C v[BT_UNROLL];
+    for (int c0 = 0; c0 < nch; c0 += BT_CHUNKS) {
+        uint4 w[BT_CHUNKS];
 #pragma unroll
-        for (int u = 0; u < BT_UNROLL; u++) v[u] = (on && j0 + u < k) ? __ldcs(&bins[(int64_t)(j0 + u) * mk + e]) : (C)0;
+        for (int u = 0; u < BT_CHUNKS; u++) w[u] = (on && c0 + u < nch) ? __ldcs(row + c0 + u) : make_uint4(0, 0, 0, 0);
 #pragma unroll
-        for (int u = 0; u < BT_UNROLL; u++) {
-            run += (uint32_t)v[u];
-            if (j0 + u < k) pref[(j0 + u) * 32 + lane] = (C)run;
+        for (int u = 0; u < BT_CHUNKS; u++) {
+            const uint32_t ws[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+#pragma unroll
+            for (int i = 0; i < PER; i++) {
+                const int j = (c0 + u) * PER + i;
+                run += sizeof(C) == 2 ? (ws[i >> 1] >> (16 * (i & 1))) & 0xffffu : ws[i & 3];
+                if (j < k) pref[j * 32 + lane] = (C)run;
+            }
         }
     }
     return run;
@@ -261,7 +272,7 @@ __global__ void __launch_bounds__(BT_THREADS) k_batch_threshold(const BatchArgs 
             const bool on = lane < L;
             const int64_t e = p + lane;
             const int32_t key = on ? a.sd[e] : -1;
-            const uint32_t cmax = bin_prefix<C>(bins, a.mk, a.k, e, on, pref);
+            const uint32_t cmax = bin_prefix<C>(bins, a.kstride, a.k, e, on, pref);
             p += L;
             if (!__any_sync(0xffffffffu, cmax > 0)) continue;
             __syncwarp();
@@ -304,7 +315,7 @@ __global__ void __launch_bounds__(BT_THREADS) k_batch_threshold(const BatchArgs 
             for (int64_t b = p; b < re; b += 32) {
                 const int64_t e = b + lane;
                 const bool on = e < re;
-                const uint32_t cmax = bin_prefix<C>(bins, a.mk, a.k, e, on, pref);
+                const uint32_t cmax = bin_prefix<C>(bins, a.kstride, a.k, e, on, pref);
                 if (!__any_sync(0xffffffffu, cmax > 0)) continue;
                 __syncwarp();
                 for (int ci = 0; ci < a.ncls; ci++) {
@@ -396,7 +407,7 @@ int64_t batch_footprint(const folty_graph* g, const folty_query_params* qs, int 
         kmax = std::max<int64_t>(kmax, (int64_t)D.size());
     }
     kmax = std::min<int64_t>(kmax, BATCH_MAX_BINS);
-    const int64_t bins = kmax * g->m_kept * 4;
+    const int64_t bins = ((kmax + 7) & ~int64_t(7)) * g->m_kept * 4;  // rows padded to 16 bytes
     // the fused pass: its solution buffer and the pair ranks
     int64_t fused = 0;
     bool any_plain = false;
@@ -415,6 +426,7 @@ int64_t batch_footprint(const folty_graph* g, const folty_query_params* qs, int 
         other = other || (!plain_query(qs[i]) && !qs[i].want_triples);
     }
     if (edges) per_q += 4 * g->m;
+    if (other) per_q += 4 * g->m_kept;  // the query's counts gathered from the bin rows
     if (certs) per_q += 16 * (g->m + 1);
     if (outer) per_q += 14 * ((int64_t)g->n + 1);
     const int64_t group = other ? std::min<int64_t>(nq, READBACK_MAX / 4) : 0;
@@ -428,10 +440,11 @@ int64_t batch_footprint(const folty_graph* g, const folty_query_params* qs, int 
 }
 
 // The fused threshold of the plain queries `fq` (at most BT_MAXQ, with their bins j) over
-// the raw (not prefix-summed) bins of one probe pass; fills their results.
+// the bins of one probe pass (edge-major rows of kstride); fills their results.
 template <typename C>
-static void fused_threshold(folty_graph* g, const C* bins, int k, const std::vector<const folty_query_params*>& fq,
-                            const std::vector<int>& fj, const std::vector<folty_result*>& fo, cudaStream_t s) {
+static void fused_threshold(folty_graph* g, const C* bins, int k, int kstride,
+                            const std::vector<const folty_query_params*>& fq, const std::vector<int>& fj,
+                            const std::vector<folty_result*>& fo, cudaStream_t s) {
     const int nq = (int)fq.size();
     const int64_t mk = g->m_kept;
     const int64_t S = g->S;
@@ -477,7 +490,13 @@ static void fused_threshold(folty_graph* g, const C* bins, int k, const std::vec
     // shared memory: classes, queries, per-warp long-run totals, per-warp prefix sums
     const size_t smem = sizeof(BatchClass) * (size_t)ncls + sizeof(BatchQuery) * (size_t)nq +
                         2 * sizeof(int32_t) * BT_WARPS * (size_t)nq + sizeof(C) * BT_WARPS * 32 * (size_t)k;
-    FOLTY_CUDA(cudaFuncSetAttribute(k_batch_threshold<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the attribute is the kernel's, shared by every thread: always the same bound (the
+    // largest pass: BT_KMAX 16-bit or BT_KMAX / 2 32-bit bins), so that concurrent batches
+    // (a server's workers) never lower it under one another's launch
+    constexpr size_t smem_max = sizeof(BatchClass) * BT_MAXQ + sizeof(BatchQuery) * BT_MAXQ +
+                                2 * sizeof(int32_t) * BT_WARPS * BT_MAXQ + 2 * BT_WARPS * 32 * BT_KMAX;
+    if (smem > smem_max) fail(FOLTY_EINVAL, "batched threshold: too many bins or queries for one pass");
+    FOLTY_CUDA(cudaFuncSetAttribute(k_batch_threshold<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
     int per_sm = 0;
     FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_threshold<C>, BT_THREADS, smem));
     const int64_t blocks = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
@@ -485,6 +504,7 @@ static void fused_threshold(folty_graph* g, const C* bins, int k, const std::vec
     BatchArgs a{};
     a.bins = bins;
     a.k = k;
+    a.kstride = kstride;
     a.mk = mk;
     a.sd = g->sd;
     a.seg = g->seg;
@@ -515,7 +535,7 @@ static void fused_threshold(folty_graph* g, const C* bins, int k, const std::vec
         a.out_nc = so.get<int32_t>(cap);
         FOLTY_CUDA(cudaMemsetAsync(a.n_out, 0, sizeof(unsigned long long), s));
         {
-            StageSpan span(ST_BATCH, s, (int64_t)k * (int64_t)sizeof(C) * mk + 4 * mk);
+            StageSpan span(ST_BATCH, s, (int64_t)kstride * (int64_t)sizeof(C) * mk + 4 * mk);
             if (mk > 0) FOLTY_LAUNCH(k_batch_threshold<C>, (unsigned)blocks, BT_THREADS, smem, s, a);
         }
         n_out = read_i64(g, (const int64_t*)a.n_out, s);
@@ -621,9 +641,11 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
         if (plain) chunk = std::min<int64_t>(chunk, b16 ? BT_KMAX : BT_KMAX / 2);
         for (size_t c0 = 0; c0 < D.size(); c0 += (size_t)chunk) {
             const int k = (int)std::min<int64_t>(chunk, (int64_t)D.size() - (int64_t)c0);
+            // edge-major rows of whole 16-byte chunks
+            const int kstride = b16 ? (k + 7) & ~7 : (k + 3) & ~3;
             Scratch sc(g->alloc, s, g->dev_err);
-            int32_t* bins = b16 ? nullptr : sc.get<int32_t>(mk * k);
-            uint16_t* bins16 = b16 ? sc.get<uint16_t>(mk * k + 2) : nullptr;  // + 2: the last word is whole
+            int32_t* bins = b16 ? nullptr : sc.get<int32_t>(mk * kstride);
+            uint16_t* bins16 = b16 ? sc.get<uint16_t>(mk * kstride) : nullptr;
             int64_t* dd = sc.get<int64_t>(k);
             std::vector<int64_t> hd(D.begin() + (long)c0, D.begin() + (long)c0 + k);
             // the bin bounds in the store's timestamp type (32-bit offsets: gaps stay
@@ -641,12 +663,12 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
             FOLTY_CUDA(cudaMemcpyAsync(dd, hb, (g->ts32 ? sizeof(uint32_t) : sizeof(int64_t)) * (size_t)k,
                                        cudaMemcpyHostToDevice, s));
             if (mk > 0) {
-                if (b16) FOLTY_CUDA(cudaMemsetAsync(bins16, 0, sizeof(uint16_t) * (size_t)(mk * k + 2), s));
-                else FOLTY_CUDA(cudaMemsetAsync(bins, 0, sizeof(int32_t) * (size_t)(mk * k), s));
-                if (P > 0) launch_probe_live(g, hd[k - 1], dir, 1, nullptr, bins, k, dd, s, nullptr, bins16);
+                if (b16) FOLTY_CUDA(cudaMemsetAsync(bins16, 0, sizeof(uint16_t) * (size_t)(mk * kstride), s));
+                else FOLTY_CUDA(cudaMemsetAsync(bins, 0, sizeof(int32_t) * (size_t)(mk * kstride), s));
+                if (P > 0) launch_probe_live(g, hd[k - 1], dir, 1, nullptr, bins, k, kstride, dd, s, nullptr, bins16);
             }
-            // the chunk's queries: plain ones through the fused pass over the raw bins,
-            // the others through the single-query path over the prefix-summed bins
+            // the chunk's queries: plain ones through the fused pass over the bins, the
+            // others through the single-query path over their window's counts
             std::vector<const folty_query_params*> pq, fq;
             std::vector<int> pj;
             std::vector<CountView> fc;
@@ -662,8 +684,18 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
                     continue;
                 }
                 fq.push_back(&qs[i]);
-                if (b16) fc.push_back(CountView{nullptr, bins16 + (int64_t)j * mk});
-                else fc.push_back(CountView{bins + (int64_t)j * mk, nullptr});
+                // the query's counts c_e(D_j), gathered from the rows
+                if (b16) {
+                    uint16_t* col = sc.get<uint16_t>(mk + 2);
+                    if (mk > 0)
+                        FOLTY_LAUNCH(k_bins_column<uint16_t>, grid_for(mk, 256), 256, 0, s, bins16, kstride, j, mk, col);
+                    fc.push_back(CountView{nullptr, col});
+                } else {
+                    int32_t* col = sc.get<int32_t>(mk);
+                    if (mk > 0)
+                        FOLTY_LAUNCH(k_bins_column<int32_t>, grid_for(mk, 256), 256, 0, s, bins, kstride, j, mk, col);
+                    fc.push_back(CountView{col, nullptr});
+                }
                 fo.push_back(&outs[i]);
             }
             for (size_t q0 = 0; q0 < pq.size(); q0 += BT_MAXQ) {
@@ -671,15 +703,10 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
                 std::vector<const folty_query_params*> gq(pq.begin() + (long)q0, pq.begin() + (long)q1);
                 std::vector<int> gj(pj.begin() + (long)q0, pj.begin() + (long)q1);
                 std::vector<folty_result*> go(po.begin() + (long)q0, po.begin() + (long)q1);
-                if (b16) fused_threshold<uint16_t>(g, bins16, k, gq, gj, go, s);
-                else fused_threshold<int32_t>(g, bins, k, gq, gj, go, s);
+                if (b16) fused_threshold<uint16_t>(g, bins16, k, kstride, gq, gj, go, s);
+                else fused_threshold<int32_t>(g, bins, k, kstride, gq, gj, go, s);
             }
-            if (!fq.empty()) {
-                if (mk > 0 && k > 1 && b16)
-                    FOLTY_LAUNCH(k_bins_prefix<uint16_t>, grid_for(mk, 256), 256, 0, s, bins16, k, mk);
-                if (mk > 0 && k > 1 && !b16) FOLTY_LAUNCH(k_bins_prefix<int32_t>, grid_for(mk, 256), 256, 0, s, bins, k, mk);
-                finish_queries(g, fq.data(), fc.data(), (int)fq.size(), fo.data(), s);
-            }
+            if (!fq.empty()) finish_queries(g, fq.data(), fc.data(), (int)fq.size(), fo.data(), s);
         }
     }
 }

@@ -133,6 +133,23 @@ constexpr uint64_t FREED_TAG = 0x464f4c5459465245ull;   // "FOLTYFRE"
 
 struct QueryPlans;  // query.cu
 
+// Kernel shapes the autotuner (tune.cu) picks for a graph: the split of the triangle
+// passes between one thread and one warp per oriented edge (by the length of the two
+// out-lists), and the probe tile (the granularity the flat probe space is partitioned in)
+// and grid of the probe kernel.
+constexpr int TUNE_TRIALS = 4;
+struct TuneParams {
+    int32_t tri_heavy = 48;   // edges whose two out-lists hold more entries go to a whole warp
+    int32_t probe_items = 8;  // probe tile = PB_THREADS * probe_items slots (4 or 8)
+    int32_t probe_blocks = 0; // probe blocks per SM (0 = as many as fit)
+    int32_t tri_source = 0;   // 0 default, 1 timed trials, 2 cache, 3 forced
+    int32_t probe_source = 0;
+    float tri_ms[TUNE_TRIALS] = {0, 0, 0, 0};    // trial times of the candidates
+    float probe_ms[TUNE_TRIALS] = {0, 0, 0, 0};
+};
+constexpr int32_t TRI_HEAVY_CAND[TUNE_TRIALS] = {24, 48, 96, 1 << 30};
+constexpr int32_t PROBE_CAND[TUNE_TRIALS][2] = {{4, 0}, {8, 0}, {8, 2}, {4, 4}};  // (items, blocks per SM)
+
 }  // namespace folty
 
 struct folty_graph {
@@ -190,6 +207,7 @@ struct folty_graph {
     int* dev_err;         // device error word: a bounded wait in a kernel ran out
     std::vector<std::pair<void*, size_t>>* owned;  // device buffers owned by the graph
     folty::QueryPlans* plans;  // captured launch sequences of plain queries (query.cu), made on first use
+    folty::TuneParams tune;    // kernel shapes (tune.cu)
 };
 
 namespace folty {
@@ -296,12 +314,23 @@ bool profiling_on();
 // Window-probe pass of one query into counters cnt[m_kept] (sorted order, zeroed).
 void launch_probe(folty_graph* g, int64_t delta, int dir, int32_t* cnt, cudaStream_t s);
 // Window probes of the roles that can hit (live.cu): mode 0 counts hits at delta into
-// cnt or, with bins16 (cnt null), into 16-bit counters two to a word; mode 1 bins gaps <= delta into bins[k][m_kept] against the k sorted bounds
-// `deltas` (in the timestamp store's type), as int32 or, with bins16 (bins null), as
-// 16-bit counts (element j * m_kept + e of a uint16 array; counts must stay below 2^16).
+// cnt or, with bins16 (cnt null), into 16-bit counters two to a word; mode 1 bins gaps
+// <= delta against the k sorted bounds `deltas` (in the timestamp store's type) into
+// edge-major rows of kstride bins (bin j of sorted edge e at e * kstride + j), as int32 or,
+// with bins16 (bins null), as 16-bit counts (counts must stay below 2^16).
 // rflag (mode 0, may be null): byte 6 * triangle + role set to 1 when the role has a hit.
 void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t* cnt, int32_t* bins, int k,
-                       const void* deltas, cudaStream_t s, uint8_t* rflag = nullptr, uint16_t* bins16 = nullptr);
+                       int kstride, const void* deltas, cudaStream_t s, uint8_t* rflag = nullptr,
+                       uint16_t* bins16 = nullptr);
+// Autotuner (tune.cu). Parameters are cached process-wide by graph statistics (a key of
+// int64 values); forced parameters (folty_tuning_force) take precedence over both.
+bool tune_lookup(const std::vector<int64_t>& key, TuneParams* p, bool probe);
+void tune_store(const std::vector<int64_t>& key, const TuneParams& p, bool probe);
+bool tune_forced(TuneParams* p, bool probe);
+// Picks the probe tile and grid for g by timed trials of the probe pass of (delta, dir),
+// unless forced or cached (live.cu); the triangle split is picked in preprocess.cu.
+void tune_probe(folty_graph* g, int64_t delta, int dir, cudaStream_t s);
+
 // Run-ends table and per-triangle liveness bytes (live.cu).
 void build_liveness(folty_graph* g, cudaStream_t s);
 // Device buffers of one query's probe stage (kept triangles, probe tiles, look-back

@@ -186,7 +186,7 @@ __device__ __forceinline__ int kept_roles_of(const int4 tr, const RunEnds<TS>* _
 // triangle j = L[j] with its role mask lmask[j] and its first probe slot loff[j] (prefix
 // of the kept triangles' costs = kept probes + LIVE_IDLE idle slots); totals[0] = kept
 // triangles, totals[1] = slots, loff[totals[0]] = totals[1]; and the probe tiles' map:
-// ltile[b] = kept triangle holding slot min(b * PB_TILE, slots - 1) for b <= the number
+// ltile[b] = kept triangle holding slot min(b * ptile, slots - 1) for b <= the number
 // of probe tiles (each kept triangle writes the tile starts inside its slots). A thread
 // takes LS_ITEMS consecutive triangles and reads their liveness bytes (tlive, the
 // smallest bucket of each triangle's roles for this direction variant) with two 16-byte
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const uint8_t* __r
                                                               int64_t* __restrict__ loff, uint8_t* __restrict__ lmask,
                                                               int64_t* __restrict__ totals,
                                                               int64_t* __restrict__ ltile, int64_t max_tiles,
-                                                              unsigned long long* __restrict__ prof,
+                                                              int64_t ptile, unsigned long long* __restrict__ prof,
                                                               const int64_t* __restrict__ qp) {
     __shared__ int32_t wc[SCAN_THREADS / 32];
     if (qp) delta = qp[0];  // the window from a device parameter block (replayed query plans)
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const uint8_t* __r
         L[jc] = (int32_t)t;
         loff[jc] = jp;
         lmask[jc] = s_mask[threadIdx.x * LS_ITEMS + i];
-        for (int64_t b = (jp + PB_TILE - 1) / PB_TILE; b * PB_TILE < jp + v && b <= max_tiles; b++) ltile[b] = jc;
+        for (int64_t b = (jp + ptile - 1) / ptile; b * ptile < jp + v && b <= max_tiles; b++) ltile[b] = jc;
         jc++;
         jp += v;
     }
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const uint8_t* __r
         totals[0] = nl;
         totals[1] = P;
         loff[nl] = P;
-        const int64_t tiles = (P + PB_TILE - 1) / PB_TILE;
+        const int64_t tiles = (P + ptile - 1) / ptile;
         if (P > 0 && tiles <= max_tiles) ltile[tiles] = nl - 1;
         if (prof) atomicAdd(prof, (unsigned long long)((16 + 3 * sizeof(RunEnds<TS>) + 13) * nl));
     }
@@ -359,6 +359,7 @@ struct LiveArgs {
     uint32_t* bins16;  // MODE 1: 16-bit counts, two to a word
     int64_t mk;
     int k;             // MODE 1: number of bins
+    int kstride;       // MODE 1: bins per edge row (k rounded up to whole 16-byte rows)
     unsigned long long* prof;  // model bytes of the kept roles (may be null)
     uint8_t* rflag;    // MODE 0, may be null: 6 * triangle + role flags of roles with a hit
     const int64_t* qp; // may be null: a device block whose slot 0 (64-bit store) or 1 (32-bit
@@ -366,23 +367,26 @@ struct LiveArgs {
 };
 
 // MODE 0: cnt[pos] += hit at window delta. MODE 1: bin the gap t3 - t (<= delta, the
-// largest bin bound) against the sorted bounds deltas[0..k).
-template <typename TS, int DIR, int MODE>
+// largest bin bound) against the sorted bounds deltas[0..k). A block takes probe tiles of
+// PB_THREADS * ITEMS slots (the tile size the autotuner picks).
+template <typename TS, int DIR, int MODE, int ITEMS>
 __global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS* __restrict__ T, TS delta,
                                                            const TS* __restrict__ deltas) {
-    __shared__ TriStage st;
-    __shared__ uint8_t smask[PB_MAXTRI];
+    constexpr int TILE = PB_THREADS * ITEMS;
+    constexpr int MAXTRI = TILE / 3 + 4;  // every kept triangle holds >= 3 slots
+    __shared__ TriStageT<MAXTRI> st;
+    __shared__ uint8_t smask[MAXTRI];
     __shared__ TS sD[1024];
     if (a.qp) delta = (TS)a.qp[sizeof(TS) == 4 ? 1 : 0];
     if (MODE == 1)
         for (int i = threadIdx.x; i < a.k; i += blockDim.x) sD[i] = deltas[i];
     const int64_t P = *a.P;
-    const int64_t tiles = (P + PB_TILE - 1) / PB_TILE;
+    const int64_t tiles = (P + TILE - 1) / TILE;
     for (int64_t b = blockIdx.x; b < tiles; b += gridDim.x) {
         __syncthreads();  // the previous tile's stage is no longer read
         const int64_t t0 = a.ltile[b];
         const int nt = (int)(a.ltile[b + 1] - t0 + 1);
-        const int64_t p0 = b * (int64_t)PB_TILE;
+        const int64_t p0 = b * (int64_t)TILE;
         unsigned long long pbytes = 0;
         for (int j = threadIdx.x; j < nt; j += blockDim.x) {
             const int4 tr = a.tri[a.L[t0 + j]];
@@ -408,9 +412,9 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS*
             st.base[nt] = INT_MAX;
         }
         __syncthreads();
-        const int32_t count = (int32_t)min((int64_t)PB_TILE, P - p0);
+        const int32_t count = (int32_t)min((int64_t)TILE, P - p0);
 #pragma unroll 1
-        for (int it = 0; it < PB_ITEMS; it++) {
+        for (int it = 0; it < ITEMS; it++) {
             const int32_t local = it * PB_THREADS + (int32_t)threadIdx.x;
             if ((local & ~31) >= count) break;  // warp-uniform
             bool active = local < count;
@@ -455,7 +459,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS*
                 if (a.rflag) a.rflag[6 * (int64_t)a.L[t0 + j] + r] = 1;
             } else {
                 const int jb = lower_bound_ts<TS>(sD, 0, a.k, gap);
-                const int64_t x = (int64_t)jb * a.mk + pos;
+                const int64_t x = (int64_t)pos * a.kstride + jb;  // edge-major: an edge's bins are contiguous
                 if (a.bins16) atomicAdd(&a.bins16[x >> 1], 1u << (16 * (int)(x & 1)));
                 else atomicAdd(&a.bins[x], 1);
             }
@@ -493,16 +497,30 @@ void build_liveness(folty_graph* g, cudaStream_t s) {
     else liveness_t<int64_t>(g, s);
 }
 
-template <typename TS, int MODE>
-static void launch_live_t(const folty_graph* g, int dir, const LiveArgs& la, unsigned grid, TS delta,
-                          const TS* deltas, cudaStream_t s) {
+// The probe kernel of the graph's tuned shape: tile of PB_THREADS * items slots,
+// blocks per SM as many as fit or the tuned count.
+template <typename TS, int MODE, int ITEMS>
+static void launch_live_shape(const folty_graph* g, int dir, const LiveArgs& la, int blocks, TS delta,
+                              const TS* deltas, cudaStream_t s) {
+    int per_sm = 0;
+    FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<TS, 0, MODE, ITEMS>, PB_THREADS, 0));
+    if (per_sm < 1) per_sm = 1;
+    if (blocks > 0 && blocks < per_sm) per_sm = blocks;
+    const unsigned grid = (unsigned)(num_sms() * per_sm);
     const TS* T = (const TS*)g->T;
     if (dir == FOLTY_DIR_OUT)
-        FOLTY_LAUNCH((k_probe_live<TS, FOLTY_DIR_OUT, MODE>), grid, PB_THREADS, 0, s, la, T, delta, deltas);
+        FOLTY_LAUNCH((k_probe_live<TS, FOLTY_DIR_OUT, MODE, ITEMS>), grid, PB_THREADS, 0, s, la, T, delta, deltas);
     else if (dir == FOLTY_DIR_IN)
-        FOLTY_LAUNCH((k_probe_live<TS, FOLTY_DIR_IN, MODE>), grid, PB_THREADS, 0, s, la, T, delta, deltas);
+        FOLTY_LAUNCH((k_probe_live<TS, FOLTY_DIR_IN, MODE, ITEMS>), grid, PB_THREADS, 0, s, la, T, delta, deltas);
     else
-        FOLTY_LAUNCH((k_probe_live<TS, FOLTY_DIR_EITHER, MODE>), grid, PB_THREADS, 0, s, la, T, delta, deltas);
+        FOLTY_LAUNCH((k_probe_live<TS, FOLTY_DIR_EITHER, MODE, ITEMS>), grid, PB_THREADS, 0, s, la, T, delta, deltas);
+}
+
+template <typename TS, int MODE>
+static void launch_live_t(const folty_graph* g, int dir, const LiveArgs& la, TS delta, const TS* deltas,
+                          cudaStream_t s) {
+    if (g->tune.probe_items == 4) launch_live_shape<TS, MODE, 4>(g, dir, la, g->tune.probe_blocks, delta, deltas, s);
+    else launch_live_shape<TS, MODE, 8>(g, dir, la, g->tune.probe_blocks, delta, deltas, s);
 }
 
 template <typename TS>
@@ -510,10 +528,11 @@ static void launch_select_t(const folty_graph* g, int dir, const uint8_t* tl, in
                             const ProbeBuffers& ls, unsigned long long* prof, const int64_t* qp, cudaStream_t s) {
     const RunEnds<TS>* ends = static_cast<const RunEnds<TS>*>(g->run_ends);
     const int64_t ntri = g->ntri, stiles = ls.stiles;
+    const int64_t tile = (int64_t)PB_THREADS * g->tune.probe_items;
     unsigned long long* lsctl = ls.lsctl;
 #define FOLTY_SELECT_ARGS                                                                                          \
     tl, g->tri, ends, ntri, delta, lsctl + 1, lsctl + 1 + stiles, (unsigned int*)lsctl, err, ls.L, ls.loff, ls.lmask, \
-        ls.totals, ls.ltile, ls.max_tiles, prof, qp
+        ls.totals, ls.ltile, ls.max_tiles, tile, prof, qp
     if (dir == FOLTY_DIR_OUT)
         FOLTY_LAUNCH((k_live_select<TS, FOLTY_DIR_OUT>), (unsigned)stiles, SCAN_THREADS, 0, s, FOLTY_SELECT_ARGS);
     else if (dir == FOLTY_DIR_IN)
@@ -523,7 +542,10 @@ static void launch_select_t(const folty_graph* g, int dir, const uint8_t* tl, in
 #undef FOLTY_SELECT_ARGS
 }
 
-// Buffers of one selection: from a call's scratch, or (alloc = graph) owned by the graph.
+// Buffers of one selection: from a call's scratch, or owned by the graph. The tile map
+// has room for the smallest probe tile the tuner may pick.
+constexpr int PB_TILE_MIN = PB_THREADS * 4;
+
 template <typename A>
 static ProbeBuffers make_probe_buffers(const folty_graph* g, A&& get) {
     const int64_t ntri = g->ntri;
@@ -532,7 +554,7 @@ static ProbeBuffers make_probe_buffers(const folty_graph* g, A&& get) {
     ls.loff = get((int64_t*)nullptr, ntri + 1);
     ls.lmask = get((uint8_t*)nullptr, ntri + 1);
     ls.totals = get((int64_t*)nullptr, 2);
-    ls.max_tiles = (g->info.probes + LIVE_IDLE * ntri + PB_TILE - 1) / PB_TILE;
+    ls.max_tiles = (g->info.probes + LIVE_IDLE * ntri + PB_TILE_MIN - 1) / PB_TILE_MIN;
     ls.ltile = get((int64_t*)nullptr, ls.max_tiles + 2);
     ls.stiles = (ntri + LS_TILE - 1) / LS_TILE;
     ls.lsctl = get((unsigned long long*)nullptr, 2 * ls.stiles + 1);  // tile counter, two look-backs
@@ -568,9 +590,10 @@ static ProbeBuffers select_live(folty_graph* g, int64_t delta, int dir, Scratch&
 // Kept roles for delta (the largest window of the pass), then the probe kernel.
 // mode 0: counts into cnt; mode 1: bins (deltas = k sorted bounds in the store's type).
 void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t* cnt, int32_t* bins, int k,
-                       const void* deltas, cudaStream_t s, uint8_t* rflag, uint16_t* bins16) {
+                       int kstride, const void* deltas, cudaStream_t s, uint8_t* rflag, uint16_t* bins16) {
     const int64_t ntri = g->ntri;
     if (ntri == 0 || g->info.probes == 0) return;
+    tune_probe(g, delta, dir, s);
     Scratch sc(g->alloc, s, g->dev_err);
     // model bytes counted on the device: the selection reads one liveness byte per
     // triangle, and per kept one its record and run ends, and writes 13 B; the probes'
@@ -586,18 +609,14 @@ void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t
     const ProbeBuffers ls = select_live(g, delta, dir, sc, s, prof_sel);
     StageSpan span(ST_PROBE, s, 0, prof);
     LiveArgs la{g->tri, g->seg, ls.L, ls.loff, ls.lmask, ls.ltile, ls.totals + 1, cnt, bins, (uint32_t*)bins16,
-                g->m_kept, k, prof, rflag, nullptr};
-    int per_sm = 0;
-    if (g->ts32) FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<uint32_t, 0, 0>, PB_THREADS, 0));
-    else FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<int64_t, 0, 0>, PB_THREADS, 0));
-    const unsigned grid = (unsigned)(num_sms() * (per_sm > 0 ? per_sm : 1));
+                g->m_kept, k, kstride, prof, rflag, nullptr};
     if (g->ts32) {
         const uint32_t d32 = delta >= 0xfffffffell ? 0xfffffffeu : (uint32_t)delta;
-        if (mode == 0) launch_live_t<uint32_t, 0>(g, dir, la, grid, d32, nullptr, s);
-        else launch_live_t<uint32_t, 1>(g, dir, la, grid, d32, (const uint32_t*)deltas, s);
+        if (mode == 0) launch_live_t<uint32_t, 0>(g, dir, la, d32, nullptr, s);
+        else launch_live_t<uint32_t, 1>(g, dir, la, d32, (const uint32_t*)deltas, s);
     } else {
-        if (mode == 0) launch_live_t<int64_t, 0>(g, dir, la, grid, delta, nullptr, s);
-        else launch_live_t<int64_t, 1>(g, dir, la, grid, delta, (const int64_t*)deltas, s);
+        if (mode == 0) launch_live_t<int64_t, 0>(g, dir, la, delta, nullptr, s);
+        else launch_live_t<int64_t, 1>(g, dir, la, delta, (const int64_t*)deltas, s);
     }
 }
 
@@ -606,13 +625,77 @@ void enqueue_probe_pass(folty_graph* g, const int64_t* qp, int dir, const ProbeB
     if (g->ntri == 0 || g->info.probes == 0) return;
     enqueue_select(g, 0, dir, pb, g->dev_err, nullptr, qp, s);
     LiveArgs la{g->tri, g->seg, pb.L, pb.loff, pb.lmask, pb.ltile, pb.totals + 1, cnt, nullptr, (uint32_t*)cnt16,
-                g->m_kept, 0, nullptr, nullptr, qp};
-    int per_sm = 0;
-    if (g->ts32) FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<uint32_t, 0, 0>, PB_THREADS, 0));
-    else FOLTY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_live<int64_t, 0, 0>, PB_THREADS, 0));
-    const unsigned grid = (unsigned)(num_sms() * (per_sm > 0 ? per_sm : 1));
-    if (g->ts32) launch_live_t<uint32_t, 0>(g, dir, la, grid, 0u, nullptr, s);
-    else launch_live_t<int64_t, 0>(g, dir, la, grid, 0, nullptr, s);
+                g->m_kept, 0, 0, nullptr, nullptr, qp};
+    if (g->ts32) launch_live_t<uint32_t, 0>(g, dir, la, 0u, nullptr, s);
+    else launch_live_t<int64_t, 0>(g, dir, la, 0, nullptr, s);
+}
+
+// ------------------------------------------------------------------ autotuning
+
+// The probe shape of g: forced, cached under the graph's statistics, or picked by timing
+// each candidate (tile, blocks per SM) on the probe pass of the first query's (delta,
+// dir) after one selection; the candidates give identical counts (every probe is made
+// once whatever the tile), so only their times differ.
+void tune_probe(folty_graph* g, int64_t delta, int dir, cudaStream_t s) {
+    if (g->tune.probe_source != 0) return;
+    if (tune_forced(&g->tune, true)) return;
+    const std::vector<int64_t> key{g->n, g->m_kept, g->S, g->ntri, g->info.probes, g->ts32};
+    if (tune_lookup(key, &g->tune, true)) return;
+    if (g->ntri == 0 || g->info.probes == 0 || profiling_on()) return;  // nothing to time (or events in use)
+    Scratch sc(g->alloc, s, g->dev_err);
+    const int64_t mk = g->m_kept;
+    const bool c16 = g->info.max_degree < 65535;
+    int32_t* cnt = c16 ? nullptr : sc.get<int32_t>(mk);
+    uint16_t* cnt16 = c16 ? sc.get<uint16_t>(mk + 2) : nullptr;
+    cudaEvent_t ev[TUNE_TRIALS + 1];
+    for (auto& e : ev) FOLTY_CUDA(cudaEventCreate(&e));
+    float best = 0.f;
+    int bi = 1;
+    try {
+        TuneParams t = g->tune;
+        for (int c = 0; c < TUNE_TRIALS; c++) {
+            g->tune.probe_items = PROBE_CAND[c][0];
+            g->tune.probe_blocks = PROBE_CAND[c][1];
+            // the selection's tile map depends on the tile, so each trial selects again
+            // (outside its timed span)
+            const ProbeBuffers ls = select_live(g, delta, dir, sc, s, nullptr);
+            if (cnt16) FOLTY_CUDA(cudaMemsetAsync(cnt16, 0, sizeof(uint16_t) * (size_t)(mk + 2), s));
+            else FOLTY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)mk, s));
+            LiveArgs la{g->tri, g->seg, ls.L, ls.loff, ls.lmask, ls.ltile, ls.totals + 1, cnt, nullptr,
+                        (uint32_t*)cnt16, mk, 0, 0, nullptr, nullptr, nullptr};
+            FOLTY_CUDA(cudaEventRecord(ev[0], s));
+            if (g->ts32) {
+                const uint32_t d32 = delta >= 0xfffffffell ? 0xfffffffeu : (uint32_t)delta;
+                launch_live_t<uint32_t, 0>(g, dir, la, d32, nullptr, s);
+            } else {
+                launch_live_t<int64_t, 0>(g, dir, la, delta, nullptr, s);
+            }
+            FOLTY_CUDA(cudaEventRecord(ev[c + 1], s));
+            FOLTY_CUDA(cudaEventSynchronize(ev[c + 1]));
+            float ms = 0.f;
+            FOLTY_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[c + 1]));
+            t.probe_ms[c] = ms;
+            if (c == 0 || ms < best) {
+                best = ms;
+                bi = c;
+            }
+        }
+        t.probe_items = PROBE_CAND[bi][0];
+        t.probe_blocks = PROBE_CAND[bi][1];
+        t.probe_source = 1;
+        g->tune.probe_items = t.probe_items;
+        g->tune.probe_blocks = t.probe_blocks;
+        g->tune.probe_source = 1;
+        std::memcpy(g->tune.probe_ms, t.probe_ms, sizeof(t.probe_ms));
+        tune_store(key, g->tune, true);
+    } catch (...) {
+        for (auto& e : ev) cudaEventDestroy(e);
+        g->tune.probe_items = 8;
+        g->tune.probe_blocks = 0;
+        throw;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    read_back(g, nullptr, nullptr, 0, nullptr, s);  // a trial's look-back wait that ran out surfaces here
 }
 
 // ------------------------------------------------------------------ selection statistics

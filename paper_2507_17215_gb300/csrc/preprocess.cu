@@ -804,6 +804,7 @@ __global__ void __launch_bounds__(PEEL_THREADS, 1) k_peel(PeelArgs a) {
 // in the CTAs' shared memory (each CTA owns the local ids congruent to its rank) and a
 // round ends with one cluster barrier instead of a grid barrier.
 constexpr int TAIL_THREADS = 1024;
+constexpr int SOLO_DEG_CAP = 1 << 18;  // degree sum (remaining decrements) the single CTA takes over
 constexpr int TAIL_OWN = 10240;  // local vertices owned per CTA: a C-CTA tail takes up to 10240 C
 
 // Local ids for the vertices of the grid kernel's alive list that are still alive (at
@@ -931,7 +932,8 @@ struct TailShared {
     uint16_t FH[TAIL_HCAP];      // heavy rows of the current round
     int cntL[3], cntH[2], smin[2];
     int acnt[2];                 // owned vertices alive at the level start, by level parity
-    int bc[2][3];                // cluster-wide values, published by tail_gather
+    int adeg[2];                 // their degree sum (twice the edges left), by level parity
+    int bc[2][4];                // cluster-wide values, published by tail_gather
 };
 
 // Neighbours vv[0..N) (negative: none) lose one degree each in round r at level k: all N
@@ -954,34 +956,37 @@ __device__ __forceinline__ void tail_decrement(TailShared<C>& sh, cg::cluster_gr
     }
 }
 
-// Cluster-wide frontier size of round t, minimum of the level minima smin[p] and sum of
-// the alive counts acnt[p]: warp 0 reads every CTA's values (lane c reads CTA c) and
+// Cluster-wide frontier size of round t, minimum of the level minima smin[p], sum of
+// the alive counts acnt[p] and of their degrees adeg[p]: warp 0 reads every CTA's values (lane c reads CTA c) and
 // publishes them in this CTA's shared memory slot s (callers alternate s, so that a slot
 // is rewritten only after a barrier that follows every read of it). The whole CTA must
 // call it; every CTA gets the same values when no CTA appends to slot t % 3 or changes
 // smin[p] or acnt[p] meanwhile.
 template <int C>
-__device__ __forceinline__ int3 tail_gather(TailShared<C>& sh, cg::cluster_group& cl, int t, int p, int s) {
+__device__ __forceinline__ int4 tail_gather(TailShared<C>& sh, cg::cluster_group& cl, int t, int p, int s) {
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
-        int v = 0, m = INT_MAX, al = 0;
+        int v = 0, m = INT_MAX, al = 0, ad = 0;
         if (lane < C) {
             const TailShared<C>* q = cl.map_shared_rank(&sh, lane);
             v = q->cntL[t % 3];
             m = q->smin[p];
             al = q->acnt[p];
+            ad = q->adeg[p];
         }
         v = __reduce_add_sync(0xffffffffu, v);
         m = __reduce_min_sync(0xffffffffu, m);
         al = __reduce_add_sync(0xffffffffu, al);
+        ad = __reduce_add_sync(0xffffffffu, ad);
         if (lane == 0) {
             sh.bc[s][0] = v;
             sh.bc[s][1] = m;
             sh.bc[s][2] = al;
+            sh.bc[s][3] = ad;
         }
     }
     __syncthreads();
-    return make_int3(sh.bc[s][0], sh.bc[s][1], sh.bc[s][2]);
+    return make_int4(sh.bc[s][0], sh.bc[s][1], sh.bc[s][2], sh.bc[s][3]);
 }
 
 // The same peeling as k_peel (levels, rounds, k + 1 -> k crossings), on the local
@@ -1021,6 +1026,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
         sh.cntH[tid] = 0;
         sh.smin[tid] = INT_MAX;
         sh.acnt[tid] = 0;
+        sh.adeg[tid] = 0;
     }
     int k = a.ctl[C_TAIL_K], r = a.ctl[C_TAIL_R], rounds = a.ctl[C_ROUNDS], lvl = 0, gs = 0;
     bool handed = false;
@@ -1032,6 +1038,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
             sh.cntH[(r + 1) & 1] = 0;
             sh.smin[(lvl + 1) & 1] = INT_MAX;
             sh.acnt[(lvl + 1) & 1] = 0;
+            sh.adeg[(lvl + 1) & 1] = 0;
         }
         int kk = k + 1;
         int lmin = INT_MAX;
@@ -1047,6 +1054,8 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
                 }
             }
             warp_count(alive, &sh.acnt[lvl & 1]);
+            const int dsum = __reduce_add_sync(0xffffffffu, alive ? sh.odeg[q] : 0);
+            if (lane == 0 && dsum) atomicAdd(&sh.adeg[lvl & 1], dsum);
             const unsigned m = __ballot_sync(0xffffffffu, rem);
             if (m) {
                 const int leader = __ffs(m) - 1;
@@ -1059,8 +1068,10 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
         lmin = __reduce_min_sync(0xffffffffu, lmin);
         if (lane == 0 && lmin != INT_MAX) atomicMin(&sh.smin[lvl & 1], lmin);
         cl.sync();
-        const int3 g = tail_gather(sh, cl, r + 1, lvl & 1, gs++ & 1);
-        if (g.z > 0 && g.z <= a.solo_cap) {
+        const int4 g = tail_gather(sh, cl, r + 1, lvl & 1, gs++ & 1);
+        // the single CTA takes over once few vertices and few edges are left (dense
+        // remainders, such as planted communities, keep the cluster's sixteen SMs)
+        if (g.z > 0 && g.z <= a.solo_cap && g.w <= SOLO_DEG_CAP) {
             // few vertices left: export them (local id, current degree) to the single-CTA
             // phase, which starts this level again; the frontier filed above is dropped
             for (int q0 = 0; q0 < OWN; q0 += TAIL_THREADS) {
@@ -1939,38 +1950,79 @@ __device__ __forceinline__ void warp_intersect(const int32_t* __restrict__ nbr, 
 
 // Also the probe slots of all triangles (sum over triangles of the three edges' temporal
 // edge counts sig) into *probes, so that they are known before the triangles are written.
-__global__ void k_tri_count(const int32_t* __restrict__ outptr, const int32_t* __restrict__ out_nbr,
-                            const int32_t* __restrict__ out_src, const int32_t* __restrict__ out_eid,
-                            const int32_t* __restrict__ sig, int32_t S, int32_t* __restrict__ cnt,
-                            unsigned long long* __restrict__ merged, unsigned long long* __restrict__ probes) {
+// Like the writing pass, an edge whose two out-lists hold more than heavy_min entries is
+// intersected by the whole warp (the thread-versus-warp split the autotuner picks).
+__global__ void __launch_bounds__(TRI_THREADS) k_tri_count(const int32_t* __restrict__ outptr,
+                                                           const int32_t* __restrict__ out_nbr,
+                                                           const int32_t* __restrict__ out_src,
+                                                           const int32_t* __restrict__ out_eid,
+                                                           const int32_t* __restrict__ sig, int32_t S,
+                                                           int32_t* __restrict__ cnt,
+                                                           unsigned long long* __restrict__ merged,
+                                                           unsigned long long* __restrict__ probes, int heavy_min) {
+    __shared__ int32_t stage[TRI_THREADS / 32][TRI_STAGE];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long acc = 0, pacc = 0;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < S;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        int32_t u = out_src[j], v = out_nbr[j];
-        int32_t i1 = outptr[u], e1 = outptr[u + 1], i2 = outptr[v], e2 = outptr[v + 1];
-        acc += (unsigned long long)((e1 - i1) + (e2 - i2));
-        int32_t c = 0;
-        unsigned long long ps = 0;
-        while (i1 < e1 && i2 < e2) {
-            int32_t x = out_nbr[i1], y = out_nbr[i2];
-            if (x == y) {
-                c++;
-                ps += (unsigned long long)(sig[out_eid[i1]] + sig[out_eid[i2]]);
-            }
-            i1 += (x <= y);
-            i2 += (y <= x);
+    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); j0 < S; j0 += stride) {
+        const int64_t j = j0 + lane;
+        int32_t i1 = 0, e1 = 0, i2 = 0, e2 = 0, s_uv = 0;
+        if (j < S) {
+            const int32_t u = out_src[j], v = out_nbr[j];
+            s_uv = out_eid[j];
+            i1 = outptr[u];
+            e1 = outptr[u + 1];
+            i2 = outptr[v];
+            e2 = outptr[v + 1];
+            acc += (unsigned long long)((e1 - i1) + (e2 - i2));
         }
-        if (c) ps += (unsigned long long)c * (unsigned long long)sig[out_eid[j]];
-        pacc += ps;
-        cnt[j] = c;
+        const bool heavy = j < S && (e1 - i1) + (e2 - i2) > heavy_min && e2 - i2 <= TRI_STAGE;
+        if (j < S && !heavy) {
+            int32_t c = 0;
+            unsigned long long ps = 0;
+            int32_t a1 = i1, a2 = i2;
+            while (a1 < e1 && a2 < e2) {
+                const int32_t x = out_nbr[a1], y = out_nbr[a2];
+                if (x == y) {
+                    c++;
+                    ps += (unsigned long long)(sig[out_eid[a1]] + sig[out_eid[a2]]);
+                }
+                a1 += (x <= y);
+                a2 += (y <= x);
+            }
+            if (c) ps += (unsigned long long)c * (unsigned long long)sig[s_uv];
+            pacc += ps;
+            cnt[j] = c;
+        }
+        unsigned hm = __ballot_sync(0xffffffffu, heavy);
+        while (hm) {
+            const int src = __ffs(hm) - 1;
+            hm &= hm - 1;
+            const int32_t b1 = __shfl_sync(0xffffffffu, i1, src), f1 = __shfl_sync(0xffffffffu, e1, src);
+            const int32_t b2 = __shfl_sync(0xffffffffu, i2, src), f2 = __shfl_sync(0xffffffffu, e2, src);
+            const int32_t hs = __shfl_sync(0xffffffffu, s_uv, src);
+            int32_t c = 0;
+            warp_intersect(out_nbr, b1, f1, b2, f2, stage[warp], [&](int32_t ia, int pos) {
+                if (pos >= 0) {
+                    c++;
+                    pacc += (unsigned long long)(sig[out_eid[ia]] + sig[out_eid[b2 + pos]]);
+                }
+            });
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (lane == 0) {
+                cnt[j0 + src] = c;
+                pacc += (unsigned long long)c * (unsigned long long)sig[hs];
+            }
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         acc += __shfl_xor_sync(0xffffffffu, acc, o);
         pacc += __shfl_xor_sync(0xffffffffu, pacc, o);
     }
-    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(merged, acc);
-    if ((threadIdx.x & 31) == 0 && pacc) atomicAdd(probes, pacc);
+    if (lane == 0 && acc) atomicAdd(merged, acc);
+    if (lane == 0 && pacc) atomicAdd(probes, pacc);
 }
 
 // tile_tri[b] = triangle holding probe min(b * tile, P - 1), for b in [0, tiles].
@@ -1995,7 +2047,8 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
                                                            const int32_t* __restrict__ out_src, int32_t S,
                                                            const int64_t* __restrict__ toff,
                                                            const int32_t* __restrict__ sig, int4* __restrict__ tri,
-                                                           int64_t* __restrict__ cost, int32_t* __restrict__ common) {
+                                                           int64_t* __restrict__ cost, int32_t* __restrict__ common,
+                                                           int heavy_min) {
     __shared__ int32_t stage[TRI_THREADS / 32][TRI_STAGE];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -2011,7 +2064,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
             i2 = outptr[v];
             e2 = outptr[v + 1];
         }
-        const bool heavy = j < S && (e1 - i1) + (e2 - i2) > TRI_HEAVY && e2 - i2 <= TRI_STAGE;
+        const bool heavy = j < S && (e1 - i1) + (e2 - i2) > heavy_min && e2 - i2 <= TRI_STAGE;
         if (j < S && !heavy) {
             int64_t p = toff[j];
             int32_t n_here = 0;
@@ -2282,6 +2335,48 @@ static void pair_key_sort(folty_graph* g, Scratch& sc, const uint32_t* order, ui
     }
 }
 
+// The counting pass of the triangle listing (tcnt per oriented edge; merged list entries
+// and probe slots into merged[0], merged[1], zeroed here) under the graph's split between
+// one thread and one warp per oriented edge: forced, cached under the graph's statistics,
+// or picked by timing the pass under each candidate split. All candidates count the same
+// triangles, so the last trial's outputs stand.
+static void tune_triangles(folty_graph* g, const int32_t* outptr, const int32_t* out_nbr, const int32_t* out_src,
+                           const int32_t* out_eid, const int32_t* sig, int32_t* tcnt, unsigned long long* merged,
+                           cudaStream_t s) {
+    const int32_t S = g->S;
+    const unsigned grid = grid_for(S, TRI_THREADS);
+    const std::vector<int64_t> key{g->n, g->m_kept, S};
+    bool trials = !(tune_forced(&g->tune, false) || tune_lookup(key, &g->tune, false)) && !profiling_on();
+    if (!trials) {
+        FOLTY_CUDA(cudaMemsetAsync(merged, 0, 2 * sizeof(unsigned long long), s));
+        FOLTY_LAUNCH(k_tri_count, grid, TRI_THREADS, 0, s, outptr, out_nbr, out_src, out_eid, sig, S, tcnt, merged,
+                     merged + 1, g->tune.tri_heavy);
+        return;
+    }
+    cudaEvent_t ev[TUNE_TRIALS + 1];
+    for (auto& e : ev) FOLTY_CUDA(cudaEventCreate(&e));
+    int best = 1;
+    try {
+        for (int c = 0; c < TUNE_TRIALS; c++) {
+            FOLTY_CUDA(cudaMemsetAsync(merged, 0, 2 * sizeof(unsigned long long), s));
+            FOLTY_CUDA(cudaEventRecord(ev[0], s));
+            FOLTY_LAUNCH(k_tri_count, grid, TRI_THREADS, 0, s, outptr, out_nbr, out_src, out_eid, sig, S, tcnt, merged,
+                         merged + 1, TRI_HEAVY_CAND[c]);
+            FOLTY_CUDA(cudaEventRecord(ev[c + 1], s));
+            FOLTY_CUDA(cudaEventSynchronize(ev[c + 1]));
+            FOLTY_CUDA(cudaEventElapsedTime(&g->tune.tri_ms[c], ev[0], ev[c + 1]));
+            if (g->tune.tri_ms[c] < g->tune.tri_ms[best]) best = c;
+        }
+    } catch (...) {
+        for (auto& e : ev) cudaEventDestroy(e);
+        throw;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    g->tune.tri_heavy = TRI_HEAVY_CAND[best];
+    g->tune.tri_source = 1;
+    tune_store(key, g->tune, false);
+}
+
 void preprocess_graph(folty_graph* g, cudaStream_t s) {
     const int T = 256;
     const int64_t m = g->m;
@@ -2512,9 +2607,7 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     // the counting pass merges the two out-lists of every oriented edge: 4 B per merged
     // entry (known after the read-back below) + 8 B per static edge
     StageSpan tri_span(ST_TRIANGLES, s, 8 * (int64_t)S);
-    if (S > 0)
-        FOLTY_LAUNCH(k_tri_count, grid_for(S, T), T, 0, s, outptr, out_nbr, out_src, out_eid, sig, S, tcnt, merged,
-                     merged + 1);
+    if (S > 0) tune_triangles(g, outptr, out_nbr, out_src, out_eid, sig, tcnt, merged, s);
     exclusive_scan(sc, tcnt, toff, S);
     tri_span.end();
     FOLTY_LAUNCH(k_max_i32, grid_for(n, T), T, 0, s, g->deg, (int64_t)n, stat + 0);
@@ -2547,7 +2640,7 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         // the listing pass merges the same lists and writes 16 + 8 B per triangle
         StageSpan span(ST_TRIANGLES, s, g->enum_bytes + 24 * ntri);
         FOLTY_LAUNCH(k_tri_write, grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr, out_eid, out_src, S, toff, sig,
-                     g->tri, cost, g->common);
+                     g->tri, cost, g->common, g->tune.tri_heavy);
     }
     exclusive_scan(sc, cost, g->tri_off, ntri);
     g->info.triangles = ntri;

@@ -36,13 +36,16 @@ struct TsNone<int64_t> {
 };
 
 // Segment k (0..5) of a staged triangle = direction k & 1 of its static edge k >> 1:
-// [off[3 * (k >> 1) + (k & 1)], off[3 * (k >> 1) + (k & 1) + 1]).
-struct TriStage {
-    int32_t base[PB_MAXTRI + 1];  // first probe of the triangle, relative to the tile start
-    int32_t off[PB_MAXTRI][9];    // per static edge e: [start of a->b, start of b->a, end]
-    uint64_t desc[PB_MAXTRI];     // per (e, d): L2 segment code | L3 segment code << 3
+// [off[3 * (k >> 1) + (k & 1)], off[3 * (k >> 1) + (k & 1) + 1]). MAXTRI = the triangles a
+// tile can overlap.
+template <int MAXTRI>
+struct TriStageT {
+    int32_t base[MAXTRI + 1];  // first probe of the triangle, relative to the tile start
+    int32_t off[MAXTRI][9];    // per static edge e: [start of a->b, start of b->a, end]
+    uint64_t desc[MAXTRI];     // per (e, d): L2 segment code | L3 segment code << 3
     int32_t nt;
 };
+using TriStage = TriStageT<PB_MAXTRI>;
 
 // id(vertex a) < id(vertex b) for triangle-local vertices a != b in {0 = u, 1 = v, 2 = w};
 // flags bit0: id(u) < id(v), bit1: id(u) < id(w), bit2: id(v) < id(w).

@@ -768,6 +768,7 @@ static bool plans_enabled() {
 static bool run_query_plan(folty_graph* g, const folty_query_params& q, folty_result* out, cudaStream_t s) {
     if (q.want_edge_counts || q.want_certificates || q.outer || q.want_triples) return false;
     if (profiling_on() || !plans_enabled()) return false;  // stage events are recorded by the launch path
+    tune_probe(g, q.delta, q.dir, s);  // the captured sequence takes the tuned probe shape
     QueryPlans* p = plans_of(g, s);
     const cudaGraphExec_t e = plan_exec(g, p, q.dir, q.quant, q.universe);
     int64_t* hp = g->host_stage + QP_SLOT;
@@ -817,7 +818,7 @@ void run_query(folty_graph* g, const folty_query_params& q, folty_result* out, c
         rflag = sc.get<uint8_t>(6 * g->ntri + 1);
         FOLTY_CUDA(cudaMemsetAsync(rflag, 0, (size_t)(6 * g->ntri + 1), s));
     }
-    launch_probe_live(g, q.delta, q.dir, 0, cnt, nullptr, 0, nullptr, s, rflag, cnt16);
+    launch_probe_live(g, q.delta, q.dir, 0, cnt, nullptr, 0, 0, nullptr, s, rflag, cnt16);
     const folty_query_params* qp = &q;
     const CountView cv{cnt, cnt16};
     finish_queries(g, &qp, &cv, 1, &out, s);  // synchronises the stream

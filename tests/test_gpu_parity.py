@@ -845,3 +845,54 @@ def test_plain_single_queries_through_captured_plans(F, monkeypatch):
                     np.testing.assert_array_equal(c[k], b[k], err_msg=str(q))
                 assert a["n_cert_edges"] == b["n_cert_edges"] == c["n_cert_edges"]
                 _assert_pairs(a, og.query(q), str(q))
+
+
+def test_autotuned_shapes_give_identical_results(F):
+    """Every kernel shape the autotuner may pick (thread-versus-warp split of the triangle
+    passes, probe tile and grid) gives the same per-edge counts, pairs, batch results and
+    triangle statistics; a tuned graph records its trial times, and a second graph of the
+    same statistics takes its shapes from the cache."""
+    import torch
+    rng = np.random.default_rng(71)
+    graphs = [W.config_graph(2, scale=0.02), W.config_graph(3, scale=0.004), _long_run_graph(20)]
+    shapes = [(24, 4, 0), (48, 8, 0), (96, 8, 2), (1 << 30, 4, 4), (1, 4, 1)]
+    for g in graphs:
+        qs = [W.Query(d, 1, 2, W.Q_FORALL_T, dr, W.U_HEAD, True) for d in (600, 86400, 10 ** 7)
+              for dr in (W.DIR_OUT, W.DIR_EITHER)]
+        plain = _plain(qs) + W.random_query_mix(12, rng)
+        outs = []
+        try:
+            for sh in shapes:
+                F.folty_tuning_force(*sh)
+                with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
+                    t = F.folty_graph_tuning(G.handle)
+                    assert (t["tri_heavy"], t["tri_source"]) == (sh[0], "forced")
+                    res = [G.query(q) for q in qs] + [G.query(q) for q in plain] + G.query_batch(plain)
+                    t = F.folty_graph_tuning(G.handle)
+                    assert (t["probe_items"], t["probe_blocks_per_sm"]) == sh[1:]
+                    outs.append((res, G.info()))
+        finally:
+            F.folty_tuning_force(0, 0, 0)
+        base, info = outs[0]
+        for res, inf in outs[1:]:
+            assert inf["triangles"] == info["triangles"] and inf["probes"] == info["probes"]
+            for a, b in zip(base, res):
+                assert pairs_of(a) == pairs_of(b) and a["n_cert_edges"] == b["n_cert_edges"]
+                if a["edge_count"] is not None:
+                    np.testing.assert_array_equal(a["edge_count"], b["edge_count"])
+    # tuned by trials once, then from the cache
+    F.folty_tuning_clear_cache()
+    g = graphs[0]
+    with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
+        G.query(W.Query(3600))
+        t1 = F.folty_graph_tuning(G.handle)
+    with F.TemporalGraph(g.n, g.src, g.dst, g.t) as G:
+        G.query(W.Query(3600))
+        t2 = F.folty_graph_tuning(G.handle)
+    assert t1["tri_source"] == "timed trials" and t1["probe_source"] == "timed trials"
+    assert all(x > 0 for x in t1["tri_trial_ms"]) and all(x > 0 for x in t1["probe_trial_ms"])
+    assert t2["tri_source"] == "cache" and t2["probe_source"] == "cache"
+    assert (t2["tri_heavy"], t2["probe_items"], t2["probe_blocks_per_sm"]) == \
+        (t1["tri_heavy"], t1["probe_items"], t1["probe_blocks_per_sm"])
+    with pytest.raises(F.FoltyError):
+        F.folty_tuning_force(48, 5, 0)
