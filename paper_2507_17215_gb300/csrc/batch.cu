@@ -200,7 +200,7 @@ __device__ __forceinline__ uint32_t bin_prefix(const C* __restrict__ bins, int k
     for (int c0 = 0; c0 < nch; c0 += BT_CHUNKS) {
         uint4 w[BT_CHUNKS];
 #pragma unroll
-        for (int u = 0; u < BT_CHUNKS; u++) w[u] = (on && c0 + u < nch) ? __ldcs(row + c0 + u) : make_uint4(0, 0, 0, 0);
+        for (int u = 0; u < BT_CHUNKS; u++) w[u] = (on && c0 + u < nch) ? __ldg(row + c0 + u) : make_uint4(0, 0, 0, 0);
 #pragma unroll
         for (int u = 0; u < BT_CHUNKS; u++) {
             const uint32_t ws[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
@@ -213,6 +213,30 @@ __device__ __forceinline__ uint32_t bin_prefix(const C* __restrict__ bins, int k
         }
     }
     return run;
+}
+
+// c_e(D_{k-1}), the sum of one lane's row (its padding is zero), from registers only:
+// most windows have no witness at any bin and skip the prefix sums in shared memory.
+template <typename C>
+__device__ __forceinline__ uint32_t row_sum(const C* __restrict__ bins, int kstride, int64_t e, bool on) {
+    constexpr int PER = 16 / sizeof(C);
+    const uint4* row = reinterpret_cast<const uint4*>(bins + e * (int64_t)kstride);
+    const int nch = kstride / PER;
+    uint32_t sum = 0;
+    for (int c0 = 0; c0 < nch; c0 += BT_CHUNKS) {
+        uint4 w[BT_CHUNKS];
+#pragma unroll
+        for (int u = 0; u < BT_CHUNKS; u++) w[u] = (on && c0 + u < nch) ? __ldcs(row + c0 + u) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int u = 0; u < BT_CHUNKS; u++) {
+            if (sizeof(C) == 2)
+                sum += (w[u].x & 0xffffu) + (w[u].x >> 16) + (w[u].y & 0xffffu) + (w[u].y >> 16) + (w[u].z & 0xffffu) +
+                       (w[u].z >> 16) + (w[u].w & 0xffffu) + (w[u].w >> 16);
+            else
+                sum += w[u].x + w[u].y + w[u].z + w[u].w;
+        }
+    }
+    return sum;
 }
 
 // First bin j with pref[j * 32 + lane] >= need (k if none; the prefix is non-decreasing).
@@ -272,9 +296,11 @@ __global__ void __launch_bounds__(BT_THREADS) k_batch_threshold(const BatchArgs 
             const bool on = lane < L;
             const int64_t e = p + lane;
             const int32_t key = on ? a.sd[e] : -1;
-            const uint32_t cmax = bin_prefix<C>(bins, a.kstride, a.k, e, on, pref);
+            const uint32_t cmax = row_sum<C>(bins, a.kstride, e, on);
             p += L;
             if (!__any_sync(0xffffffffu, cmax > 0)) continue;
+            // only lanes with a witness need their prefix sums (the others read zero)
+            if (cmax > 0) bin_prefix<C>(bins, a.kstride, a.k, e, true, pref);
             __syncwarp();
             const int32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
             const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || key != prev);
@@ -294,7 +320,7 @@ __global__ void __launch_bounds__(BT_THREADS) k_batch_threshold(const BatchArgs 
                     const BatchQuery q = sq[qi];
                     if (q.j < jlo) continue;
                     const bool sat = q.j >= jmin;
-                    const int cq = (int)pref[q.j * 32 + lane];
+                    const int cq = cmax > 0 ? (int)pref[q.j * 32 + lane] : 0;
                     const int rmax = __reduce_max_sync(peers, cq);
                     const int rsat = __reduce_add_sync(peers, sat ? 1 : 0);
                     emit_pairs(a, leader && rsat > 0, q.slot, key, rmax, rsat);
@@ -315,8 +341,9 @@ __global__ void __launch_bounds__(BT_THREADS) k_batch_threshold(const BatchArgs 
             for (int64_t b = p; b < re; b += 32) {
                 const int64_t e = b + lane;
                 const bool on = e < re;
-                const uint32_t cmax = bin_prefix<C>(bins, a.kstride, a.k, e, on, pref);
+                const uint32_t cmax = row_sum<C>(bins, a.kstride, e, on);
                 if (!__any_sync(0xffffffffu, cmax > 0)) continue;
+                if (cmax > 0) bin_prefix<C>(bins, a.kstride, a.k, e, true, pref);
                 __syncwarp();
                 for (int ci = 0; ci < a.ncls; ci++) {
                     const BatchClass c = scls[ci];
@@ -327,7 +354,7 @@ __global__ void __launch_bounds__(BT_THREADS) k_batch_threshold(const BatchArgs 
                     for (int qi = c.qb; qi < c.qe; qi++) {
                         const BatchQuery q = sq[qi];
                         if (q.j < jlo) continue;
-                        const int rmax = __reduce_max_sync(0xffffffffu, (int)pref[q.j * 32 + lane]);
+                        const int rmax = __reduce_max_sync(0xffffffffu, cmax > 0 ? (int)pref[q.j * 32 + lane] : 0);
                         const int rsat = __reduce_add_sync(0xffffffffu, q.j >= jmin ? 1 : 0);
                         if (lane == 0) {
                             wmax[qi] = max(wmax[qi], rmax);

@@ -331,8 +331,9 @@ bool tune_forced(TuneParams* p, bool probe);
 // unless forced or cached (live.cu); the triangle split is picked in preprocess.cu.
 void tune_probe(folty_graph* g, int64_t delta, int dir, cudaStream_t s);
 
-// Run-ends table and per-triangle liveness bytes (live.cu).
-void build_liveness(folty_graph* g, cudaStream_t s);
+// The run-ends table, and the rows of per-triangle liveness bytes with their padding
+// (live.cu); the triangle listing fills the rows.
+void prepare_liveness(folty_graph* g, cudaStream_t s);
 // Device buffers of one query's probe stage (kept triangles, probe tiles, look-back
 // control).
 struct ProbeBuffers {

@@ -20,63 +20,13 @@
 #include <type_traits>
 
 #include "internal.cuh"
+#include "liveness.cuh"
 #include "probe.cuh"
 #include "scan.cuh"
 
 namespace folty {
 
 constexpr int LIVE_IDLE = 3;  // idle slots per kept triangle (keeps >= 3 slots per triangle)
-constexpr uint8_t DMIN_NEVER = 255;
-
-// Time span of the union of runs a and b (b < 0: run a alone) from the first and last
-// timestamps of the six runs of a triangle, in the store's timestamp type V. Called with
-// indices the compiler knows, so the arrays stay in registers.
-template <typename V>
-__device__ __forceinline__ bool span_of(const V* f, const V* l, const bool* ne, int a, int b, V& first, V& last) {
-    bool any = false;
-    if (ne[a]) {
-        first = f[a];
-        last = l[a];
-        any = true;
-    }
-    if (b >= 0 && ne[b]) {
-        first = any ? min(first, f[b]) : f[b];
-        last = any ? max(last, l[b]) : l[b];
-        any = true;
-    }
-    return any;
-}
-
-__device__ __forceinline__ int bit_len(uint32_t x) { return 32 - __clz(x); }
-__device__ __forceinline__ int bit_len(int64_t x) { return 64 - __clzll((unsigned long long)x); }
-
-// Bucket of role r (= 2k + d: direction d of frame edge k) for direction variant DIR, of
-// a triangle whose local vertices 0, 1, 2 are in id order (flags = 7, so that every run
-// index below is a constant), from the first and last timestamps of its six runs. The
-// arithmetic stays in the store's type (32-bit offsets for most graphs): dmin =
-// max(0, L2.first - L1.last, L3.first - L1.last) never needs a sign.
-template <int DIR, typename V>
-__device__ __forceinline__ uint8_t frame_bucket(const V* f, const V* l, const bool* ne, int r) {
-    if (!ne[r]) return DMIN_NEVER;
-    int s2, s3;
-    role_segments(7, r >> 1, r & 1, DIR, s2, s3);
-    const bool both = DIR == FOLTY_DIR_EITHER;  // s2, s3 are the d = 0 runs then
-    V f2 = 0, l2 = 0, f3 = 0, l3 = 0;
-    const bool a2 = span_of<V>(f, l, ne, s2, both ? s2 + 1 : -1, f2, l2);
-    const bool a3 = span_of<V>(f, l, ne, s3, both ? s3 + 1 : -1, f3, l3);
-    const V f1 = f[r], l1 = l[r];
-    if (!(a2 && a3 && l2 >= f1 && l3 >= (f2 > f1 ? f2 : f1))) return DMIN_NEVER;
-    const V d2 = f2 > l1 ? (V)(f2 - l1) : (V)0, d3 = f3 > l1 ? (V)(f3 - l1) : (V)0;
-    return (uint8_t)bit_len(d2 > d3 ? d2 : d3);  // 0 for dmin = 0
-}
-
-// First and last timestamp and size of both runs of one static edge (direction 0 =
-// small id -> large id, then direction 1); first = last = 0 for an empty run.
-template <typename TS>
-struct __align__(16) RunEnds {
-    TS f0, l0, f1, l1;
-    int32_t n0, n1, pad0, pad1;
-};
 
 template <typename TS>
 __global__ void k_run_ends(const int32_t* __restrict__ seg, int64_t S, const TS* __restrict__ T,
@@ -92,69 +42,6 @@ __global__ void k_run_ends(const int32_t* __restrict__ seg, int64_t S, const TS*
         r.l1 = r.n1 > 0 ? T[o2 - 1] : (TS)0;
         r.pad0 = r.pad1 = 0;
         ends[e] = r;
-    }
-}
-
-// The six runs of triangle tr in its id-order frame: the triangle is relabelled so that
-// its local vertices are in id order (a rank per vertex from the three id-order bits);
-// its three static edges are then read from the run-ends table in that frame, one
-// aligned record each, so that every thread runs the same code whatever the triangle's
-// id order. oe[k] = the stored edge (0: s_uv, 1: s_uw, 2: s_vw) that is frame edge k.
-template <typename TS>
-struct FrameRuns {
-    TS f[6], l[6];
-    int32_t n[6];
-    bool ne[6];
-    int oe[3];
-};
-
-template <typename TS>
-__device__ __forceinline__ void frame_runs(const int4 tr, const RunEnds<TS>* __restrict__ ends, FrameRuns<TS>& fr) {
-    const int b0 = tr.w & 1, b1 = (tr.w >> 1) & 1, b2 = (tr.w >> 2) & 1;
-    // rank of each local vertex among the three ids
-    const int rk0 = (b0 ^ 1) + (b1 ^ 1), rk1 = b0 + (b2 ^ 1), rk2 = b1 + b2;
-    // stored edge e joins local vertices (0,1), (0,2), (1,2); in the sorted frame it
-    // joins ranks (rk_p, rk_q), i.e. frame edge rk_p + rk_q - 1
-    const int k0 = rk0 + rk1 - 1, k1 = rk0 + rk2 - 1;
-    int32_t se[3];
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        fr.oe[k] = (k == k0) ? 0 : (k == k1) ? 1 : 2;
-        se[k] = (k == k0) ? tr.x : (k == k1) ? tr.y : tr.z;
-    }
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const RunEnds<TS> re = ends[se[k]];
-        fr.n[2 * k] = re.n0;
-        fr.n[2 * k + 1] = re.n1;
-        fr.ne[2 * k] = re.n0 > 0;
-        fr.ne[2 * k + 1] = re.n1 > 0;
-        fr.f[2 * k] = re.f0;
-        fr.l[2 * k] = re.l0;
-        fr.f[2 * k + 1] = re.f1;
-        fr.l[2 * k + 1] = re.l1;
-    }
-}
-
-// tlive[dir][t] = the smallest bucket of the six roles of triangle t for direction
-// variant dir (DMIN_NEVER when none can hit at any window). Rows are tstride bytes apart.
-template <typename TS>
-__global__ void k_tri_live(const int4* __restrict__ tri, int64_t ntri, const RunEnds<TS>* __restrict__ ends,
-                           int64_t tstride, uint8_t* __restrict__ tlive) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntri;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        FrameRuns<TS> fr;
-        frame_runs<TS>(tri[t], ends, fr);
-        uint8_t m0 = DMIN_NEVER, m1 = DMIN_NEVER, m2 = DMIN_NEVER;
-#pragma unroll
-        for (int r = 0; r < 6; r++) {
-            m0 = min(m0, frame_bucket<FOLTY_DIR_OUT, TS>(fr.f, fr.l, fr.ne, r));
-            m1 = min(m1, frame_bucket<FOLTY_DIR_IN, TS>(fr.f, fr.l, fr.ne, r));
-            m2 = min(m2, frame_bucket<FOLTY_DIR_EITHER, TS>(fr.f, fr.l, fr.ne, r));
-        }
-        tlive[t] = m0;
-        tlive[tstride + t] = m1;
-        tlive[2 * tstride + t] = m2;
     }
 }
 
@@ -470,31 +357,28 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS*
 // ------------------------------------------------------------------ host side
 
 template <typename TS>
-static void liveness_t(folty_graph* g, cudaStream_t s) {
-    const int64_t S = g->S, ntri = g->ntri;
+static void run_ends_t(folty_graph* g, cudaStream_t s) {
+    const int64_t S = g->S;
     RunEnds<TS>* ends = static_cast<RunEnds<TS>*>(g->run_ends);
-    // per static edge: 12 B of run bounds and 4 timestamps read, its record written; per
-    // triangle: 16 B read, one byte per direction variant written (the run-ends table is
-    // read back from L2)
-    StageSpan span(ST_ROLES, s, S * (12 + 4 * (int64_t)sizeof(TS) + (int64_t)sizeof(RunEnds<TS>)) + 19 * ntri);
+    // per static edge: 12 B of run bounds and 4 timestamps read, its record written
+    StageSpan span(ST_ROLES, s, S * (12 + 4 * (int64_t)sizeof(TS) + (int64_t)sizeof(RunEnds<TS>)));
     if (S > 0) FOLTY_LAUNCH(k_run_ends<TS>, grid_for(S, 256), 256, 0, s, g->seg, S, (const TS*)g->T, ends);
-    if (ntri > 0)
-        FOLTY_LAUNCH(k_tri_live<TS>, grid_for(ntri, 256), 256, 0, s, g->tri, ntri, ends, g->tlive_stride, g->tlive);
 }
 
-void build_liveness(folty_graph* g, cudaStream_t s) {
+void prepare_liveness(folty_graph* g, cudaStream_t s) {
     const int64_t ntri = g->ntri;
     g->run_ends = g->ts32 ? (void*)graph_alloc<RunEnds<uint32_t>>(g, g->S, s)
                           : (void*)graph_alloc<RunEnds<int64_t>>(g, g->S, s);
     // three rows of liveness bytes, each padded with DMIN_NEVER to whole 16-byte chunks
+    // (the triangle listing writes the first ntri bytes of each)
     g->tlive_stride = (ntri + 15) & ~int64_t(15);
     g->tlive = graph_alloc<uint8_t>(g, 3 * g->tlive_stride, s);
     for (int d = 0; d < 3; d++)
         if (g->tlive_stride > ntri)
             FOLTY_CUDA(cudaMemsetAsync(g->tlive + d * g->tlive_stride + ntri, DMIN_NEVER,
                                        (size_t)(g->tlive_stride - ntri), s));
-    if (g->ts32) liveness_t<uint32_t>(g, s);
-    else liveness_t<int64_t>(g, s);
+    if (g->ts32) run_ends_t<uint32_t>(g, s);
+    else run_ends_t<int64_t>(g, s);
 }
 
 // The probe kernel of the graph's tuned shape: tile of PB_THREADS * items slots,

@@ -14,6 +14,7 @@
 #include <cstring>
 
 #include "internal.cuh"
+#include "liveness.cuh"
 #include "pairs.cuh"
 
 #include <cooperative_groups.h>
@@ -1948,8 +1949,9 @@ __device__ __forceinline__ void warp_intersect(const int32_t* __restrict__ nbr, 
     __syncwarp();
 }
 
-// Also the probe slots of all triangles (sum over triangles of the three edges' temporal
-// edge counts sig) into *probes, so that they are known before the triangles are written.
+// Also the probe slots of each oriented edge's triangles (sum over them of the three
+// edges' temporal edge counts sig) into pcnt, and of all triangles into *probes, so that
+// the triangles' probe offsets are known before they are written.
 // Like the writing pass, an edge whose two out-lists hold more than heavy_min entries is
 // intersected by the whole warp (the thread-versus-warp split the autotuner picks).
 __global__ void __launch_bounds__(TRI_THREADS) k_tri_count(const int32_t* __restrict__ outptr,
@@ -1957,7 +1959,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_count(const int32_t* __rest
                                                            const int32_t* __restrict__ out_src,
                                                            const int32_t* __restrict__ out_eid,
                                                            const int32_t* __restrict__ sig, int32_t S,
-                                                           int32_t* __restrict__ cnt,
+                                                           int32_t* __restrict__ cnt, int64_t* __restrict__ pcnt,
                                                            unsigned long long* __restrict__ merged,
                                                            unsigned long long* __restrict__ probes, int heavy_min) {
     __shared__ int32_t stage[TRI_THREADS / 32][TRI_STAGE];
@@ -1993,6 +1995,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_count(const int32_t* __rest
             if (c) ps += (unsigned long long)c * (unsigned long long)sig[s_uv];
             pacc += ps;
             cnt[j] = c;
+            pcnt[j] = (int64_t)ps;
         }
         unsigned hm = __ballot_sync(0xffffffffu, heavy);
         while (hm) {
@@ -2002,17 +2005,23 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_count(const int32_t* __rest
             const int32_t b2 = __shfl_sync(0xffffffffu, i2, src), f2 = __shfl_sync(0xffffffffu, e2, src);
             const int32_t hs = __shfl_sync(0xffffffffu, s_uv, src);
             int32_t c = 0;
+            unsigned long long hp = 0;
             warp_intersect(out_nbr, b1, f1, b2, f2, stage[warp], [&](int32_t ia, int pos) {
                 if (pos >= 0) {
                     c++;
-                    pacc += (unsigned long long)(sig[out_eid[ia]] + sig[out_eid[b2 + pos]]);
+                    hp += (unsigned long long)(sig[out_eid[ia]] + sig[out_eid[b2 + pos]]);
                 }
             });
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                c += __shfl_xor_sync(0xffffffffu, c, o);
+                hp += __shfl_xor_sync(0xffffffffu, hp, o);
+            }
             if (lane == 0) {
+                hp += (unsigned long long)c * (unsigned long long)sig[hs];
                 cnt[j0 + src] = c;
-                pacc += (unsigned long long)c * (unsigned long long)sig[hs];
+                pcnt[j0 + src] = (int64_t)hp;
+                pacc += hp;
             }
         }
     }
@@ -2041,14 +2050,20 @@ __global__ void k_tile_starts(const int64_t* __restrict__ tri_off, int64_t ntri,
     }
 }
 
-__global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __restrict__ outptr,
+// Each triangle's liveness bytes (the smallest window bucket of its roles per direction
+// variant, liveness.cuh) are computed as it is written, while the merges of other threads
+// wait for memory.
+template <typename TS>
+__global__ void __launch_bounds__(TRI_THREADS, 4) k_tri_write(const int32_t* __restrict__ outptr,
                                                            const int32_t* __restrict__ out_nbr,
                                                            const int32_t* __restrict__ out_eid,
                                                            const int32_t* __restrict__ out_src, int32_t S,
                                                            const int64_t* __restrict__ toff,
+                                                           const int64_t* __restrict__ poff,
                                                            const int32_t* __restrict__ sig, int4* __restrict__ tri,
-                                                           int64_t* __restrict__ cost, int32_t* __restrict__ common,
-                                                           int heavy_min) {
+                                                           int64_t* __restrict__ tri_off, int32_t* __restrict__ common,
+                                                           int heavy_min, const RunEnds<TS>* __restrict__ ends,
+                                                           int64_t tstride, uint8_t* __restrict__ tlive) {
     __shared__ int32_t stage[TRI_THREADS / 32][TRI_STAGE];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -2066,7 +2081,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
         }
         const bool heavy = j < S && (e1 - i1) + (e2 - i2) > heavy_min && e2 - i2 <= TRI_STAGE;
         if (j < S && !heavy) {
-            int64_t p = toff[j];
+            int64_t p = toff[j], q = poff[j];
             int32_t n_here = 0;
             const int32_t sig_uv = sig[s_uv];
             int32_t a1 = i1, a2 = i2;
@@ -2075,8 +2090,11 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
                 if (x == y) {
                     const int32_t w = x, s_uw = out_eid[a1], s_vw = out_eid[a2];
                     const int flags = (u < v ? 1 : 0) | (u < w ? 2 : 0) | (v < w ? 4 : 0);
-                    tri[p] = make_int4(s_uv, s_uw, s_vw, flags);
-                    cost[p] = (int64_t)sig_uv + sig[s_uw] + sig[s_vw];
+                    const int4 tr = make_int4(s_uv, s_uw, s_vw, flags);
+                    tri[p] = tr;
+                    tri_off[p] = q;
+                    write_liveness<TS>(tr, ends, p, tstride, tlive);
+                    q += (int64_t)sig_uv + sig[s_uw] + sig[s_vw];
                     atomicAdd(&common[s_uw], 1);
                     atomicAdd(&common[s_vw], 1);
                     p++;
@@ -2095,22 +2113,40 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
             const int32_t b2 = __shfl_sync(0xffffffffu, i2, src), f2 = __shfl_sync(0xffffffffu, e2, src);
             const int32_t hu = __shfl_sync(0xffffffffu, u, src), hv = __shfl_sync(0xffffffffu, v, src);
             const int32_t hs = __shfl_sync(0xffffffffu, s_uv, src);
-            int64_t p = (lane == 0) ? toff[j0 + src] : 0;
+            int64_t p = (lane == 0) ? toff[j0 + src] : 0, q = (lane == 0) ? poff[j0 + src] : 0;
             p = __shfl_sync(0xffffffffu, p, 0);
+            q = __shfl_sync(0xffffffffu, q, 0);
             const int32_t sig_uv = sig[hs];
             int n_here = 0;
             warp_intersect(out_nbr, b1, f1, b2, f2, stage[warp], [&](int32_t ia, int pos) {
                 const unsigned m = __ballot_sync(0xffffffffu, pos >= 0);
+                int64_t c = 0;
+                int32_t s_uw = 0, s_vw = 0;
+                if (pos >= 0) {
+                    s_uw = out_eid[ia];
+                    s_vw = out_eid[b2 + pos];
+                    c = (int64_t)sig_uv + sig[s_uw] + sig[s_vw];
+                }
+                // the hits' probe offsets: a warp prefix of their costs, in lane order
+                int64_t inc = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += y;
+                }
                 if (pos >= 0) {
                     const int64_t at = p + __popc(m & ((1u << lane) - 1u));
-                    const int32_t w = out_nbr[ia], s_uw = out_eid[ia], s_vw = out_eid[b2 + pos];
+                    const int32_t w = out_nbr[ia];
                     const int flags = (hu < hv ? 1 : 0) | (hu < w ? 2 : 0) | (hv < w ? 4 : 0);
-                    tri[at] = make_int4(hs, s_uw, s_vw, flags);
-                    cost[at] = (int64_t)sig_uv + sig[s_uw] + sig[s_vw];
+                    const int4 tr = make_int4(hs, s_uw, s_vw, flags);
+                    tri[at] = tr;
+                    tri_off[at] = q + inc - c;
+                    write_liveness<TS>(tr, ends, at, tstride, tlive);
                     atomicAdd(&common[s_uw], 1);
                     atomicAdd(&common[s_vw], 1);
                 }
                 p += __popc(m);
+                q += __shfl_sync(0xffffffffu, inc, 31);
                 n_here += __popc(m);
             });
             if (lane == 0 && n_here) atomicAdd(&common[hs], n_here);
@@ -2341,16 +2377,16 @@ static void pair_key_sort(folty_graph* g, Scratch& sc, const uint32_t* order, ui
 // or picked by timing the pass under each candidate split. All candidates count the same
 // triangles, so the last trial's outputs stand.
 static void tune_triangles(folty_graph* g, const int32_t* outptr, const int32_t* out_nbr, const int32_t* out_src,
-                           const int32_t* out_eid, const int32_t* sig, int32_t* tcnt, unsigned long long* merged,
-                           cudaStream_t s) {
+                           const int32_t* out_eid, const int32_t* sig, int32_t* tcnt, int64_t* pcnt,
+                           unsigned long long* merged, cudaStream_t s) {
     const int32_t S = g->S;
     const unsigned grid = grid_for(S, TRI_THREADS);
     const std::vector<int64_t> key{g->n, g->m_kept, S};
     bool trials = !(tune_forced(&g->tune, false) || tune_lookup(key, &g->tune, false)) && !profiling_on();
     if (!trials) {
         FOLTY_CUDA(cudaMemsetAsync(merged, 0, 2 * sizeof(unsigned long long), s));
-        FOLTY_LAUNCH(k_tri_count, grid, TRI_THREADS, 0, s, outptr, out_nbr, out_src, out_eid, sig, S, tcnt, merged,
-                     merged + 1, g->tune.tri_heavy);
+        FOLTY_LAUNCH(k_tri_count, grid, TRI_THREADS, 0, s, outptr, out_nbr, out_src, out_eid, sig, S, tcnt, pcnt,
+                     merged, merged + 1, g->tune.tri_heavy);
         return;
     }
     cudaEvent_t ev[TUNE_TRIALS + 1];
@@ -2360,8 +2396,8 @@ static void tune_triangles(folty_graph* g, const int32_t* outptr, const int32_t*
         for (int c = 0; c < TUNE_TRIALS; c++) {
             FOLTY_CUDA(cudaMemsetAsync(merged, 0, 2 * sizeof(unsigned long long), s));
             FOLTY_CUDA(cudaEventRecord(ev[0], s));
-            FOLTY_LAUNCH(k_tri_count, grid, TRI_THREADS, 0, s, outptr, out_nbr, out_src, out_eid, sig, S, tcnt, merged,
-                         merged + 1, TRI_HEAVY_CAND[c]);
+            FOLTY_LAUNCH(k_tri_count, grid, TRI_THREADS, 0, s, outptr, out_nbr, out_src, out_eid, sig, S, tcnt, pcnt,
+                         merged, merged + 1, TRI_HEAVY_CAND[c]);
             FOLTY_CUDA(cudaEventRecord(ev[c + 1], s));
             FOLTY_CUDA(cudaEventSynchronize(ev[c + 1]));
             FOLTY_CUDA(cudaEventElapsedTime(&g->tune.tri_ms[c], ev[0], ev[c + 1]));
@@ -2607,8 +2643,10 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     // the counting pass merges the two out-lists of every oriented edge: 4 B per merged
     // entry (known after the read-back below) + 8 B per static edge
     StageSpan tri_span(ST_TRIANGLES, s, 8 * (int64_t)S);
-    if (S > 0) tune_triangles(g, outptr, out_nbr, out_src, out_eid, sig, tcnt, merged, s);
+    int64_t* pcnt = sc.get<int64_t>((int64_t)S + 1);  // probe slots per oriented edge, then their prefix
+    if (S > 0) tune_triangles(g, outptr, out_nbr, out_src, out_eid, sig, tcnt, pcnt, merged, s);
     exclusive_scan(sc, tcnt, toff, S);
+    exclusive_scan(sc, pcnt, pcnt, S);
     tri_span.end();
     FOLTY_LAUNCH(k_max_i32, grid_for(n, T), T, 0, s, g->deg, (int64_t)n, stat + 0);
     {
@@ -2635,14 +2673,22 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     const int64_t ntri = g->ntri;
     g->tri = graph_alloc<int4>(g, ntri, s);
     g->tri_off = graph_alloc<int64_t>(g, ntri + 1, s);
-    int64_t* cost = sc.get<int64_t>(ntri + 1);
+    prepare_liveness(g, s);  // the run-ends table the listing reads for the liveness bytes
+
     if (S > 0) {
         // the listing pass merges the same lists and writes 16 + 8 B per triangle
-        StageSpan span(ST_TRIANGLES, s, g->enum_bytes + 24 * ntri);
-        FOLTY_LAUNCH(k_tri_write, grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr, out_eid, out_src, S, toff, sig,
-                     g->tri, cost, g->common, g->tune.tri_heavy);
+        StageSpan span(ST_TRIANGLES, s, g->enum_bytes + 27 * ntri);  // + 16 B triangle, 8 B offset, 3 liveness bytes
+        if (g->ts32)
+            FOLTY_LAUNCH(k_tri_write<uint32_t>, grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr, out_eid,
+                         out_src, S, toff, pcnt, sig, g->tri, g->tri_off, g->common, g->tune.tri_heavy,
+                         (const RunEnds<uint32_t>*)g->run_ends, g->tlive_stride, g->tlive);
+        else
+            FOLTY_LAUNCH(k_tri_write<int64_t>, grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr, out_eid,
+                         out_src, S, toff, pcnt, sig, g->tri, g->tri_off, g->common, g->tune.tri_heavy,
+                         (const RunEnds<int64_t>*)g->run_ends, g->tlive_stride, g->tlive);
     }
-    exclusive_scan(sc, cost, g->tri_off, ntri);
+    // the probe offsets of the triangles come from the writing pass; the last entry is the total
+    FOLTY_CUDA(cudaMemcpyAsync(g->tri_off + ntri, pcnt + S, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     g->info.triangles = ntri;
     // tile -> first triangle map of the probe kernels (query independent)
     g->n_tiles = (g->info.probes + PB_TILE - 1) / PB_TILE;
@@ -2650,7 +2696,6 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     if (g->info.probes > 0)
         FOLTY_LAUNCH(k_tile_starts, grid_for(g->n_tiles + 1, T), T, 0, s, g->tri_off, ntri, g->info.probes,
                      g->n_tiles, PB_TILE, g->tile_tri);
-    build_liveness(g, s);
     g->prof_bytes = graph_alloc<unsigned long long>(g, PROF_SLOTS, s);
     g->info.static_edges = S;
     g->state = 1;
