@@ -229,18 +229,25 @@ uint64_t folty_kernel_launches(void);
  *   PEEL      the degeneracy peeling: 12 B per adjacency entry + 16 B per vertex;
  *   THRESHOLD certificate test and per-pair reduction: 8 B per temporal edge (4 with 16-bit
  *             counters) + 20 B per directed pair;
- *   SELECT    the per-query liveness pass over the triangles' role summaries (k_live_select):
- *             30 B read per triangle, 13 B written per kept triangle;
+ *   SELECT    the per-query selection of the triangles whose liveness byte admits the
+ *             window (k_live_select): 1 B read per triangle; per kept triangle its record
+ *             and its edges' run ends read and 13 B written, counted on the device;
  *   TRIANGLES triangle count and listing passes: 4 B per merged out-list entry + 8 B per
  *             static edge, per pass; 24 B written per triangle;
- *   ROLES     the role summary (run ends, per-role sigma1 and window buckets): 92 B per
- *             static edge + 58 B per triangle;
- *   BATCH     the batched threshold over all queries of a direction variant: the bins
- *             read once, 4 B of pair key per temporal edge, 16 B per solution pair.
+ *   ROLES     the run-ends table (12 B of run bounds + 4 timestamps read, one record
+ *             written per static edge) and the liveness pass (16 B read and 3 B written
+ *             per triangle, the run-ends table read once);
+ *   BATCH     the batched threshold over the plain queries of a direction variant: the
+ *             32-edge group bits, and (counted on the device) the bin row and 4 B of pair
+ *             key of every edge in a group with a hit;
+ *   STORE     the temporal store built beside the peeling (pair words, their sort, the
+ *             gather into the sorted arrays, the run bounds): its span contains SORT spans;
+ *             8 B per input edge for the pair words and 28 B per kept edge for the gather
+ *             and the run bounds (the sort's bytes are in SORT).
  * Totals are process-wide; profile one thread at a time. */
 enum { FOLTY_STAGE_PROBE = 0, FOLTY_STAGE_SORT = 1, FOLTY_STAGE_PEEL = 2, FOLTY_STAGE_THRESHOLD = 3,
        FOLTY_STAGE_SELECT = 4, FOLTY_STAGE_TRIANGLES = 5, FOLTY_STAGE_ROLES = 6, FOLTY_STAGE_BATCH = 7,
-       FOLTY_STAGE_COUNT = 8 };
+       FOLTY_STAGE_STORE = 8, FOLTY_STAGE_COUNT = 9 };
 typedef struct {
     int64_t launches; /* timed spans */
     double ms;        /* total device time */

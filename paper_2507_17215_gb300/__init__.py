@@ -98,7 +98,7 @@ class folty_stage_profile(Structure):
 
 
 STAGES = {"probe": 0, "sort": 1, "peel": 2, "threshold": 3, "select": 4, "triangles": 5, "roles": 6,
-          "batch": 7}
+          "batch": 7, "store": 8}
 
 
 class folty_probe_stats(Structure):

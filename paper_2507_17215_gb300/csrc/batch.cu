@@ -137,6 +137,8 @@ struct BatchArgs {
     int32_t* out_run;   // the pair's run id 2s + d
     int32_t* out_cnt;   // max c_e over the pair's edges
     int32_t* out_nc;    // certificates among them
+    const uint32_t* touched;    // bit g: some edge of [32 g, 32 g + 32) has a nonzero bin
+    unsigned long long* prof;   // may be null: model bytes of the rows read
 };
 
 // x rounded up to the next start of a run (runs of one directed pair are contiguous).
@@ -164,6 +166,14 @@ __device__ __forceinline__ int64_t needed(const BatchClass& c, int64_t uh, int64
     const int64_t U = c.universe == FOLTY_U_HEAD ? uh : c.universe == FOLTY_U_TAIL ? ut : uc;
     const int64_t v = (c.num * U + c.den - 1) / c.den;
     return v > 1 ? v : 1;
+}
+
+// Whether a sorted edge of [b, e) (e - b <= 32, so at most two groups) has a nonzero bin.
+__device__ __forceinline__ bool touched_any(const uint32_t* __restrict__ t, int64_t b, int64_t e) {
+    const int64_t g0 = b >> 5, g1 = (e - 1) >> 5;
+    bool any = (__ldg(t + (g0 >> 5)) >> (g0 & 31)) & 1u;
+    if (g1 != g0) any = any || ((__ldg(t + (g1 >> 5)) >> (g1 & 31)) & 1u);
+    return any;
 }
 
 // Appends the pairs of the lanes with emit set (one atomic per warp).
@@ -260,6 +270,11 @@ __device__ __forceinline__ int first_bin(const C* pref, int k, int64_t need) {
 // starts, so that no directed pair's run is split between warps. It walks the range in
 // windows of at most 32 edges made of whole runs (lane = edge), or, for a run longer
 // than 32 edges, in 32-edge pieces of that run with per-query totals in shared memory.
+// Windows and pieces whose 32-edge groups received no hit are passed over without
+// reading their rows: their counts are all zero. Such a skip may end inside a run; the
+// run's remaining edges then form the next window (a window that starts inside a run
+// treats its first edge as the run's head), and the skipped edges contribute nothing to
+// the pair's maximum or certificates.
 // For a window it keeps the prefix sums of its edges' bins in shared memory; per class
 // of queries each lane finds, by a binary search, the first bin at which its edge
 // certifies, and only the class's queries at or past the warp's smallest such bin are
@@ -284,8 +299,14 @@ __global__ void __launch_bounds__(BT_THREADS) k_batch_threshold(const BatchArgs 
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t p = run_aligned(a.sd, a.seg, warp * a.per_warp, a.mk);
     const int64_t hi = run_aligned(a.sd, a.seg, (warp + 1) * a.per_warp, a.mk);
+    const int64_t row_bytes = (int64_t)a.kstride * (int64_t)sizeof(C);
+    unsigned long long rows_read = 0;
     while (p < hi) {
         const int64_t we = min(p + 32, hi);
+        if (!touched_any(a.touched, p, we)) {
+            p = we;
+            continue;
+        }
         int64_t L = we - p;
         if (we < hi) {
             const int32_t rl = a.sd[we - 1];
@@ -297,6 +318,7 @@ __global__ void __launch_bounds__(BT_THREADS) k_batch_threshold(const BatchArgs 
             const int64_t e = p + lane;
             const int32_t key = on ? a.sd[e] : -1;
             const uint32_t cmax = row_sum<C>(bins, a.kstride, e, on);
+            rows_read += (unsigned long long)L;
             p += L;
             if (!__any_sync(0xffffffffu, cmax > 0)) continue;
             // only lanes with a witness need their prefix sums (the others read zero)
@@ -339,9 +361,11 @@ __global__ void __launch_bounds__(BT_THREADS) k_batch_threshold(const BatchArgs 
             int64_t uh, ut, uc;
             universes(a, key, uh, ut, uc);
             for (int64_t b = p; b < re; b += 32) {
+                if (!touched_any(a.touched, b, min(b + 32, re))) continue;
                 const int64_t e = b + lane;
                 const bool on = e < re;
                 const uint32_t cmax = row_sum<C>(bins, a.kstride, e, on);
+                rows_read += (unsigned long long)min((int64_t)32, re - b);
                 if (!__any_sync(0xffffffffu, cmax > 0)) continue;
                 if (cmax > 0) bin_prefix<C>(bins, a.kstride, a.k, e, true, pref);
                 __syncwarp();
@@ -373,6 +397,26 @@ __global__ void __launch_bounds__(BT_THREADS) k_batch_threshold(const BatchArgs 
             __syncwarp();
             p = re;
         }
+    }
+    // model bytes: the rows read and their run keys, once per warp
+    if (a.prof && lane == 0 && rows_read)
+        atomicAdd(a.prof, rows_read * (unsigned long long)(row_bytes + 4));
+}
+
+// Zeroes the rows of every 32-edge group marked in touched (the only rows a binned probe
+// pass wrote), so that the bins are clear again for the next pass: one warp per group.
+template <typename C>
+__global__ void k_bins_clear(const uint32_t* __restrict__ touched, C* __restrict__ bins, int kstride, int64_t mk) {
+    const int lane = threadIdx.x & 31;
+    const int64_t ng = (mk + 31) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gi < ng; gi += nw) {
+        if (!((__ldg(touched + (gi >> 5)) >> (gi & 31)) & 1u)) continue;
+        const int64_t r0 = gi << 5, r1 = min(r0 + 32, mk);
+        // rows of kstride * sizeof(C) bytes, a multiple of 16
+        uint4* q = reinterpret_cast<uint4*>(bins + r0 * (int64_t)kstride);
+        const int64_t n16 = (r1 - r0) * (int64_t)kstride * (int64_t)sizeof(C) / 16;
+        for (int64_t i = lane; i < n16; i += 32) q[i] = make_uint4(0, 0, 0, 0);
     }
 }
 
@@ -469,7 +513,7 @@ int64_t batch_footprint(const folty_graph* g, const folty_query_params* qs, int 
 // The fused threshold of the plain queries `fq` (at most BT_MAXQ, with their bins j) over
 // the bins of one probe pass (edge-major rows of kstride); fills their results.
 template <typename C>
-static void fused_threshold(folty_graph* g, const C* bins, int k, int kstride,
+static void fused_threshold(folty_graph* g, const C* bins, const uint32_t* touched, int k, int kstride,
                             const std::vector<const folty_query_params*>& fq, const std::vector<int>& fj,
                             const std::vector<folty_result*>& fo, cudaStream_t s) {
     const int nq = (int)fq.size();
@@ -530,6 +574,7 @@ static void fused_threshold(folty_graph* g, const C* bins, int k, int kstride,
     const int64_t nwarps = blocks * BT_WARPS;
     BatchArgs a{};
     a.bins = bins;
+    a.touched = touched;
     a.k = k;
     a.kstride = kstride;
     a.mk = mk;
@@ -561,8 +606,15 @@ static void fused_threshold(folty_graph* g, const C* bins, int k, int kstride,
         a.out_cnt = so.get<int32_t>(cap);
         a.out_nc = so.get<int32_t>(cap);
         FOLTY_CUDA(cudaMemsetAsync(a.n_out, 0, sizeof(unsigned long long), s));
+        a.prof = nullptr;
+        if (profiling_on()) {
+            a.prof = g->prof_bytes + (g->prof_next++ % PROF_SLOTS);
+            FOLTY_CUDA(cudaMemsetAsync(a.prof, 0, sizeof(unsigned long long), s));
+        }
         {
-            StageSpan span(ST_BATCH, s, (int64_t)kstride * (int64_t)sizeof(C) * mk + 4 * mk);
+            // model bytes: the group bits, plus (counted on the device) the rows of the
+            // groups with a hit and their run keys
+            StageSpan span(ST_BATCH, s, 4 * ((mk + 1023) / 1024), a.prof);
             if (mk > 0) FOLTY_LAUNCH(k_batch_threshold<C>, (unsigned)blocks, BT_THREADS, smem, s, a);
         }
         n_out = read_i64(g, (const int64_t*)a.n_out, s);
@@ -644,35 +696,62 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
     for (int i = 0; i < nq; i++)
         if (qs[i].want_triples) run_query(g, qs[i], &outs[i], s);
     // group the queries by direction variant; distinct sorted deltas per group
-    for (int dir = 0; dir <= FOLTY_DIR_EITHER; dir++) {
+    // 16-bit bins while no count can reach 2^16 (a count is at most the number of common
+    // neighbours of an edge's ends, at most the largest degree): half the memory traffic
+    // of the bins and of the threshold's reads
+    const bool b16 = g->info.max_degree < 65535;
+    const int64_t per_bin = mk * (int64_t)(b16 ? sizeof(uint16_t) : sizeof(int32_t));
+    const int64_t budget = bin_budget > 0 ? bin_budget : batch_bin_budget_bytes();
+    struct Pass {
+        int dir;
         std::vector<int> members;
-        for (int i = 0; i < nq; i++)
-            if (qs[i].dir == dir && !qs[i].want_triples) members.push_back(i);
-        if (members.empty()) continue;
         std::vector<int64_t> D;
-        for (int i : members) D.push_back(qs[i].delta);
-        std::sort(D.begin(), D.end());
-        D.erase(std::unique(D.begin(), D.end()), D.end());
-        // 16-bit bins while no count can reach 2^16 (a count is at most the number of
-        // common neighbours of an edge's ends, at most the largest degree): half the
-        // memory traffic of the bins and of the threshold's reads
-        const bool b16 = g->info.max_degree < 65535;
-        const int64_t per_bin = mk * (int64_t)(b16 ? sizeof(uint16_t) : sizeof(int32_t));
-        const int64_t budget = bin_budget > 0 ? bin_budget : batch_bin_budget_bytes();
-        int64_t chunk = per_bin > 0 ? budget / per_bin : (int64_t)D.size();
-        chunk = std::max<int64_t>(1, std::min<int64_t>({chunk, (int64_t)BATCH_MAX_BINS, (int64_t)D.size()}));
+        int64_t chunk;
+    };
+    std::vector<Pass> passes;
+    int kstride_max = 0;
+    for (int dir = 0; dir <= FOLTY_DIR_EITHER; dir++) {
+        Pass ps{dir, {}, {}, 0};
+        for (int i = 0; i < nq; i++)
+            if (qs[i].dir == dir && !qs[i].want_triples) ps.members.push_back(i);
+        if (ps.members.empty()) continue;
+        for (int i : ps.members) ps.D.push_back(qs[i].delta);
+        std::sort(ps.D.begin(), ps.D.end());
+        ps.D.erase(std::unique(ps.D.begin(), ps.D.end()), ps.D.end());
+        int64_t chunk = per_bin > 0 ? budget / per_bin : (int64_t)ps.D.size();
+        chunk = std::max<int64_t>(1, std::min<int64_t>({chunk, (int64_t)BATCH_MAX_BINS, (int64_t)ps.D.size()}));
         // the fused pass keeps every window's prefix sums in shared memory: at most BT_KMAX
         // 16-bit (BT_KMAX / 2 32-bit) bins per probe pass when plain queries are present
         bool plain = false;
-        for (int i : members) plain = plain || plain_query(qs[i]);
+        for (int i : ps.members) plain = plain || plain_query(qs[i]);
         if (plain) chunk = std::min<int64_t>(chunk, b16 ? BT_KMAX : BT_KMAX / 2);
+        ps.chunk = chunk;
+        const int kk = (int)chunk;
+        kstride_max = std::max(kstride_max, b16 ? (kk + 7) & ~7 : (kk + 3) & ~3);
+        passes.push_back(std::move(ps));
+    }
+    if (passes.empty()) return;
+    // one bin buffer for every pass, cleared once: each pass marks the 32-edge groups it
+    // writes, its consumers read only those, and k_bins_clear zeroes them again
+    Scratch sb(g->alloc, s, g->dev_err);
+    int32_t* bins = b16 ? nullptr : sb.get<int32_t>(mk * kstride_max);
+    uint16_t* bins16 = b16 ? sb.get<uint16_t>(mk * kstride_max) : nullptr;
+    const int64_t twords = (mk + 1023) / 1024 + 1;
+    uint32_t* touched = sb.get<uint32_t>(twords);
+    if (mk > 0) {
+        if (b16) FOLTY_CUDA(cudaMemsetAsync(bins16, 0, sizeof(uint16_t) * (size_t)(mk * kstride_max), s));
+        else FOLTY_CUDA(cudaMemsetAsync(bins, 0, sizeof(int32_t) * (size_t)(mk * kstride_max), s));
+    }
+    for (const Pass& ps : passes) {
+        const int dir = ps.dir;
+        const std::vector<int>& members = ps.members;
+        const std::vector<int64_t>& D = ps.D;
+        const int64_t chunk = ps.chunk;
         for (size_t c0 = 0; c0 < D.size(); c0 += (size_t)chunk) {
             const int k = (int)std::min<int64_t>(chunk, (int64_t)D.size() - (int64_t)c0);
             // edge-major rows of whole 16-byte chunks
             const int kstride = b16 ? (k + 7) & ~7 : (k + 3) & ~3;
             Scratch sc(g->alloc, s, g->dev_err);
-            int32_t* bins = b16 ? nullptr : sc.get<int32_t>(mk * kstride);
-            uint16_t* bins16 = b16 ? sc.get<uint16_t>(mk * kstride) : nullptr;
             int64_t* dd = sc.get<int64_t>(k);
             std::vector<int64_t> hd(D.begin() + (long)c0, D.begin() + (long)c0 + k);
             // the bin bounds in the store's timestamp type (32-bit offsets: gaps stay
@@ -690,9 +769,10 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
             FOLTY_CUDA(cudaMemcpyAsync(dd, hb, (g->ts32 ? sizeof(uint32_t) : sizeof(int64_t)) * (size_t)k,
                                        cudaMemcpyHostToDevice, s));
             if (mk > 0) {
-                if (b16) FOLTY_CUDA(cudaMemsetAsync(bins16, 0, sizeof(uint16_t) * (size_t)(mk * kstride), s));
-                else FOLTY_CUDA(cudaMemsetAsync(bins, 0, sizeof(int32_t) * (size_t)(mk * kstride), s));
-                if (P > 0) launch_probe_live(g, hd[k - 1], dir, 1, nullptr, bins, k, kstride, dd, s, nullptr, bins16);
+                FOLTY_CUDA(cudaMemsetAsync(touched, 0, sizeof(uint32_t) * (size_t)twords, s));
+                if (P > 0)
+                    launch_probe_live(g, hd[k - 1], dir, 1, nullptr, bins, k, kstride, dd, s, nullptr, bins16,
+                                      touched);
             }
             // the chunk's queries: plain ones through the fused pass over the bins, the
             // others through the single-query path over their window's counts
@@ -730,10 +810,17 @@ void run_query_batch(folty_graph* g, const folty_query_params* qs, int nq, folty
                 std::vector<const folty_query_params*> gq(pq.begin() + (long)q0, pq.begin() + (long)q1);
                 std::vector<int> gj(pj.begin() + (long)q0, pj.begin() + (long)q1);
                 std::vector<folty_result*> go(po.begin() + (long)q0, po.begin() + (long)q1);
-                if (b16) fused_threshold<uint16_t>(g, bins16, k, kstride, gq, gj, go, s);
-                else fused_threshold<int32_t>(g, bins, k, kstride, gq, gj, go, s);
+                if (b16) fused_threshold<uint16_t>(g, bins16, touched, k, kstride, gq, gj, go, s);
+                else fused_threshold<int32_t>(g, bins, touched, k, kstride, gq, gj, go, s);
             }
             if (!fq.empty()) finish_queries(g, fq.data(), fc.data(), (int)fq.size(), fo.data(), s);
+            // every reader of this pass's bins is enqueued: clear the rows it wrote
+            if (mk > 0) {
+                const int64_t ng = (mk + 31) / 32;
+                const unsigned blocks = (unsigned)std::min<int64_t>((ng + 7) / 8, (int64_t)num_sms() * 16);
+                if (b16) FOLTY_LAUNCH(k_bins_clear<uint16_t>, blocks, 256, 0, s, touched, bins16, kstride, mk);
+                else FOLTY_LAUNCH(k_bins_clear<int32_t>, blocks, 256, 0, s, touched, bins, kstride, mk);
+            }
         }
     }
 }

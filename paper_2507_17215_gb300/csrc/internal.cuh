@@ -253,6 +253,9 @@ void exclusive_scan(Scratch& sc, const uint32_t* in, uint32_t* out, int64_t n);
 // leaves the output unusable: the caller checks the word before the values index anything.
 bool radix_sort_pairs(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
                       uint32_t* vals_alt, int64_t n, int bits);
+// The same ordered by key bits [lo, lo + bits) (lower bits ride along).
+bool radix_sort_pairs(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
+                      int64_t n, int lo, int bits);
 // The same for keys alone, ordered by key bits [lo, lo + bits) (lower bits ride along).
 bool radix_sort_keys(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, int64_t n, int lo, int bits);
 
@@ -280,7 +283,7 @@ void validate_query(const folty_query_params& q);
 // commit(), called after the call's final stream synchronisation, adds the elapsed
 // times to process-wide totals.
 enum { ST_PROBE = 0, ST_SORT = 1, ST_PEEL = 2, ST_THRESHOLD = 3, ST_SELECT = 4, ST_TRIANGLES = 5, ST_ROLES = 6,
-       ST_BATCH = 7, ST_COUNT = 8 };
+       ST_BATCH = 7, ST_STORE = 8, ST_COUNT = 9 };
 static_assert(ST_COUNT == FOLTY_STAGE_COUNT, "stage numbering follows folty.h");
 
 class StageSpan {
@@ -319,9 +322,11 @@ void launch_probe(folty_graph* g, int64_t delta, int dir, int32_t* cnt, cudaStre
 // edge-major rows of kstride bins (bin j of sorted edge e at e * kstride + j), as int32 or,
 // with bins16 (bins null), as 16-bit counts (counts must stay below 2^16).
 // rflag (mode 0, may be null): byte 6 * triangle + role set to 1 when the role has a hit.
+// touched (mode 1, may be null): bit g of word g / 32 set when one of sorted edges
+// [32 g, 32 g + 32) received a binned hit (the caller clears the words first).
 void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t* cnt, int32_t* bins, int k,
                        int kstride, const void* deltas, cudaStream_t s, uint8_t* rflag = nullptr,
-                       uint16_t* bins16 = nullptr);
+                       uint16_t* bins16 = nullptr, uint32_t* touched = nullptr);
 // Autotuner (tune.cu). Parameters are cached process-wide by graph statistics (a key of
 // int64 values); forced parameters (folty_tuning_force) take precedence over both.
 bool tune_lookup(const std::vector<int64_t>& key, TuneParams* p, bool probe);
@@ -332,8 +337,9 @@ bool tune_forced(TuneParams* p, bool probe);
 void tune_probe(folty_graph* g, int64_t delta, int dir, cudaStream_t s);
 
 // The run-ends table, and the rows of per-triangle liveness bytes with their padding
-// (live.cu); the triangle listing fills the rows.
+// (live.cu); triangle_liveness then fills the rows from the listed triangles.
 void prepare_liveness(folty_graph* g, cudaStream_t s);
+void triangle_liveness(folty_graph* g, cudaStream_t s);
 // Device buffers of one query's probe stage (kept triangles, probe tiles, look-back
 // control).
 struct ProbeBuffers {

@@ -36,13 +36,22 @@ __global__ void k_run_ends(const int32_t* __restrict__ seg, int64_t S, const TS*
         RunEnds<TS> r;
         r.n0 = o1 - o0;
         r.n1 = o2 - o1;
-        r.f0 = r.n0 > 0 ? T[o0] : (TS)0;
-        r.l0 = r.n0 > 0 ? T[o1 - 1] : (TS)0;
-        r.f1 = r.n1 > 0 ? T[o1] : (TS)0;
-        r.l1 = r.n1 > 0 ? T[o2 - 1] : (TS)0;
+        r.f0 = r.n0 > 0 ? T[o0] : RunEmpty<TS>::first;
+        r.l0 = r.n0 > 0 ? T[o1 - 1] : RunEmpty<TS>::last;
+        r.f1 = r.n1 > 0 ? T[o1] : RunEmpty<TS>::first;
+        r.l1 = r.n1 > 0 ? T[o2 - 1] : RunEmpty<TS>::last;
         r.pad0 = r.pad1 = 0;
         ends[e] = r;
     }
+}
+
+// The liveness bytes of every listed triangle (write_liveness), one thread per triangle:
+// consecutive triangles share their first edge, so its record mostly comes from L1.
+template <typename TS>
+__global__ void k_tri_live(const int4* __restrict__ tri, int64_t ntri, const RunEnds<TS>* __restrict__ ends,
+                           int64_t tstride, uint8_t* __restrict__ tlive) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntri; t += (int64_t)gridDim.x * blockDim.x)
+        write_liveness<TS>(__ldcs(tri + t), ends, t, tstride, tlive);
 }
 
 __device__ __forceinline__ bool bucket_live(uint8_t b, int64_t delta) {
@@ -60,7 +69,7 @@ __device__ __forceinline__ int kept_roles_of(const int4 tr, const RunEnds<TS>* _
     int64_t c = 0;
 #pragma unroll
     for (int r = 0; r < 6; r++) {
-        if (bucket_live(frame_bucket<DIR, TS>(fr.f, fr.l, fr.ne, r), delta)) {  // never for an empty run
+        if (bucket_live(frame_bucket<DIR, TS>(fr, r), delta)) {  // never for an empty run
             m |= 1 << (2 * fr.oe[r >> 1] + (r & 1));
             c += fr.n[r];
         }
@@ -251,6 +260,8 @@ struct LiveArgs {
     uint8_t* rflag;    // MODE 0, may be null: 6 * triangle + role flags of roles with a hit
     const int64_t* qp; // may be null: a device block whose slot 0 (64-bit store) or 1 (32-bit
                        // store) holds the window, read instead of the delta argument
+    uint32_t* touched; // MODE 1, may be null: bit g set when a sorted edge of group g (edges
+                       // [32 g, 32 g + 32)) received a binned hit
 };
 
 // MODE 0: cnt[pos] += hit at window delta. MODE 1: bin the gap t3 - t (<= delta, the
@@ -300,27 +311,31 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS*
         }
         __syncthreads();
         const int32_t count = (int32_t)min((int64_t)TILE, P - p0);
-#pragma unroll 1
-        for (int it = 0; it < ITEMS; it++) {
-            const int32_t local = it * PB_THREADS + (int32_t)threadIdx.x;
-            if ((local & ~31) >= count) break;  // warp-uniform
-            bool active = local < count;
-            // triangle of the slot: one lane bisects for the warp, lanes walk forward
-            const int lane = threadIdx.x & 31;
-            const int32_t first = __shfl_sync(0xffffffffu, local, 0);
-            int j0 = 0;
-            if (lane == 0) {
-                int lo = 0, hi = st.nt - 1;
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (st.base[mid] <= first) lo = mid;
-                    else hi = mid - 1;
-                }
-                j0 = lo;
+        // ITEMS consecutive slots per thread: consecutive slots of one role probe
+        // consecutive entries t of its sorted L1, so the answers t2 and t3 only move
+        // forward in L2 and L3 and each search gallops on from where the last one ended
+        const int32_t l0 = (int32_t)threadIdx.x * ITEMS;
+        if (l0 >= count) continue;
+        int j = 0;
+        {
+            int lo = 0, hi = st.nt - 1;  // the last staged triangle starting at or before l0
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (st.base[mid] <= l0) lo = mid;
+                else hi = mid - 1;
             }
-            int j = __shfl_sync(0xffffffffu, j0, 0);
-            if (!active) continue;
-            while (st.base[j + 1] <= local) j++;
+            j = lo;
+        }
+        int cur = -1;  // role of the pointers below (-1: none yet)
+        int32_t q2a = 0, q2b = 0, q3a = 0, q3b = 0;  // lower bounds of the searches in L2, L3 runs
+#pragma unroll 1
+        for (int k = 0; k < ITEMS; k++) {
+            const int32_t local = l0 + k;
+            if (local >= count) break;
+            while (st.base[j + 1] <= local) {
+                j++;
+                cur = -1;
+            }
             int32_t o = local - st.base[j] - LIVE_IDLE;
             if (o < 0) continue;  // idle slot
             const int32_t* off = st.off[j];
@@ -333,11 +348,50 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS*
                 o -= s1;
             }
             if (r == 6) continue;  // cannot happen: o < the kept roles' total
-            const int32_t pos = off[3 * (r >> 1) + (r & 1)] + o;
             const int code = (int)((st.desc[j] >> (6 * r)) & 63);
+            const int c2 = code & 7, c3 = code >> 3;
+            const int o2 = 3 * (c2 >> 1) + (c2 & 1), o3 = 3 * (c3 >> 1) + (c3 & 1);
+            if (r != cur) {
+                cur = r;
+                q2a = off[o2];
+                q2b = off[o2 + 1];
+                q3a = off[o3];
+                q3b = off[o3 + 1];
+            }
+            const int32_t pos = off[3 * (r >> 1) + (r & 1)] + o;
             const TS t = T[pos];
-            const TS t3 = probe_window<TS, DIR>(T, off, code & 7, code >> 3, t, delta);
-            if (t3 == TsNone<TS>::value) continue;
+            // Theorem 3.1: t2 = first entry >= t of L2, t3 = first entry >= t2 of L3 (the
+            // union of both directions' runs for "either"); a run whose first entry is
+            // already beyond t + delta is not searched
+            const TS NONE = TsNone<TS>::value;
+            TS t2 = NONE;
+            {
+                const int32_t b = off[o2], e = off[o2 + 1];
+                if (b < e && !(T[b] > t && beyond(T[b], t, delta))) {
+                    q2a = gallop_at_least<TS>(T, q2a, e, t);
+                    if (q2a < e) t2 = T[q2a];
+                }
+            }
+            if (DIR == FOLTY_DIR_EITHER) {
+                const int32_t b = off[o2 + 1], e = off[o2 + 2];
+                if (b < e && !(T[b] > t && beyond(T[b], t, delta))) {
+                    q2b = gallop_at_least<TS>(T, q2b, e, t);
+                    if (q2b < e && T[q2b] < t2) t2 = T[q2b];
+                }
+            }
+            if (t2 == NONE || beyond(t2, t, delta)) continue;
+            TS t3 = NONE;
+            {
+                const int32_t e = off[o3 + 1];
+                q3a = gallop_at_least<TS>(T, q3a, e, t2);
+                if (q3a < e) t3 = T[q3a];
+            }
+            if (DIR == FOLTY_DIR_EITHER) {
+                const int32_t e = off[o3 + 2];
+                q3b = gallop_at_least<TS>(T, q3b, e, t2);
+                if (q3b < e && T[q3b] < t3) t3 = T[q3b];
+            }
+            if (t3 == NONE) continue;
             const TS gap = (TS)(t3 - t);
             if (gap > delta) continue;
             if (MODE == 0) {
@@ -349,6 +403,11 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS*
                 const int64_t x = (int64_t)pos * a.kstride + jb;  // edge-major: an edge's bins are contiguous
                 if (a.bins16) atomicAdd(&a.bins16[x >> 1], 1u << (16 * (int)(x & 1)));
                 else atomicAdd(&a.bins[x], 1);
+                if (a.touched) {
+                    // a plain read first: most hits find their group's bit already set
+                    const uint32_t bit = 1u << ((pos >> 5) & 31);
+                    if (!(a.touched[pos >> 10] & bit)) atomicOr(&a.touched[pos >> 10], bit);
+                }
             }
         }
     }
@@ -370,7 +429,7 @@ void prepare_liveness(folty_graph* g, cudaStream_t s) {
     g->run_ends = g->ts32 ? (void*)graph_alloc<RunEnds<uint32_t>>(g, g->S, s)
                           : (void*)graph_alloc<RunEnds<int64_t>>(g, g->S, s);
     // three rows of liveness bytes, each padded with DMIN_NEVER to whole 16-byte chunks
-    // (the triangle listing writes the first ntri bytes of each)
+    // (triangle_liveness writes the first ntri bytes of each)
     g->tlive_stride = (ntri + 15) & ~int64_t(15);
     g->tlive = graph_alloc<uint8_t>(g, 3 * g->tlive_stride, s);
     for (int d = 0; d < 3; d++)
@@ -379,6 +438,22 @@ void prepare_liveness(folty_graph* g, cudaStream_t s) {
                                        (size_t)(g->tlive_stride - ntri), s));
     if (g->ts32) run_ends_t<uint32_t>(g, s);
     else run_ends_t<int64_t>(g, s);
+}
+
+template <typename TS>
+static void triangle_liveness_t(folty_graph* g, cudaStream_t s) {
+    const int64_t ntri = g->ntri;
+    // per triangle: its record read and three bytes written; the run-ends table (shared by
+    // the triangles of an edge, and small) read once
+    StageSpan span(ST_ROLES, s, ntri * (16 + 3) + g->S * (int64_t)sizeof(RunEnds<TS>));
+    if (ntri > 0)
+        FOLTY_LAUNCH(k_tri_live<TS>, grid_for(ntri, 256), 256, 0, s, g->tri, ntri,
+                     (const RunEnds<TS>*)g->run_ends, g->tlive_stride, g->tlive);
+}
+
+void triangle_liveness(folty_graph* g, cudaStream_t s) {
+    if (g->ts32) triangle_liveness_t<uint32_t>(g, s);
+    else triangle_liveness_t<int64_t>(g, s);
 }
 
 // The probe kernel of the graph's tuned shape: tile of PB_THREADS * items slots,
@@ -474,7 +549,8 @@ static ProbeBuffers select_live(folty_graph* g, int64_t delta, int dir, Scratch&
 // Kept roles for delta (the largest window of the pass), then the probe kernel.
 // mode 0: counts into cnt; mode 1: bins (deltas = k sorted bounds in the store's type).
 void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t* cnt, int32_t* bins, int k,
-                       int kstride, const void* deltas, cudaStream_t s, uint8_t* rflag, uint16_t* bins16) {
+                       int kstride, const void* deltas, cudaStream_t s, uint8_t* rflag, uint16_t* bins16,
+                       uint32_t* touched) {
     const int64_t ntri = g->ntri;
     if (ntri == 0 || g->info.probes == 0) return;
     tune_probe(g, delta, dir, s);
@@ -493,7 +569,7 @@ void launch_probe_live(folty_graph* g, int64_t delta, int dir, int mode, int32_t
     const ProbeBuffers ls = select_live(g, delta, dir, sc, s, prof_sel);
     StageSpan span(ST_PROBE, s, 0, prof);
     LiveArgs la{g->tri, g->seg, ls.L, ls.loff, ls.lmask, ls.ltile, ls.totals + 1, cnt, bins, (uint32_t*)bins16,
-                g->m_kept, k, kstride, prof, rflag, nullptr};
+                g->m_kept, k, kstride, prof, rflag, nullptr, touched};
     if (g->ts32) {
         const uint32_t d32 = delta >= 0xfffffffell ? 0xfffffffeu : (uint32_t)delta;
         if (mode == 0) launch_live_t<uint32_t, 0>(g, dir, la, d32, nullptr, s);

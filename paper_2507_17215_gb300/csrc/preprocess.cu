@@ -14,7 +14,6 @@
 #include <cstring>
 
 #include "internal.cuh"
-#include "liveness.cuh"
 #include "pairs.cuh"
 
 #include <cooperative_groups.h>
@@ -230,21 +229,46 @@ __global__ void k_pair_ids(const uint64_t* __restrict__ urank, const uint32_t* _
     }
 }
 
-// Sort word of the edge at time rank j (input index order[j], or j when the input is in
-// time order): (2 pair id + direction) << ib | j; self-loops get 2S and sort last.
+// Sort word of the edge at time rank j (input index o = order[j], or j when the input is
+// in time order): (2 pair id + direction) << ib | j; self-loops get 2S and sort last.
+// With tv (32-bit stores), also the edge's 32-bit time offset t[o] - tmin, the value the
+// sort carries along, so that the sorted timestamps need no gather; and sigma[p] counts
+// the temporal edges of pair p, which the triangle passes need before the sort is done.
 __global__ void k_pair_pack(const uint32_t* __restrict__ slotw, const uint32_t* __restrict__ order, int64_t m,
-                            const int32_t* __restrict__ sid, int32_t S, int ib, uint64_t* __restrict__ packed) {
+                            const int32_t* __restrict__ sid, int32_t S, int ib, uint64_t* __restrict__ packed,
+                            const int64_t* __restrict__ t, int64_t tmin, uint32_t* __restrict__ tv,
+                            int32_t* __restrict__ sigma) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t w = order ? slotw[order[j]] : __ldcs(slotw + j);
+        const int64_t o = order ? (int64_t)order[j] : j;
+        const uint32_t w = order ? slotw[o] : __ldcs(slotw + j);
         uint64_t c = 2 * (uint64_t)S;
-        if (w != PAIR_LOOP) c = 2 * (uint64_t)sid[w & ~PAIR_DIR] + (w >> 31);
+        if (w != PAIR_LOOP) {
+            const int32_t p = sid[w & ~PAIR_DIR];
+            c = 2 * (uint64_t)p + (w >> 31);
+            if ((unsigned)p < (unsigned)S) atomicAdd(&sigma[p], 1);
+        }
         packed[j] = (c << ib) | (uint64_t)j;
+        if (tv) tv[j] = (uint32_t)((order ? t[o] : __ldcs(t + j)) - tmin);
     }
 }
 
-// perm, T, sd and the pair starts from the sorted words: position i holds time rank
+// The run starts of sorted position i with word pk (its predecessor's word prev, ~0 for
+// i = 0): seg[2s] = i where static edge s begins, seg[2s + 1] = i where its b -> a run
+// begins (seg is all -1 before; k_segments_fix fills the b -> a starts of edges without
+// one). c < 2S unless the pair ids' sort failed, which the host learns right after.
+__device__ __forceinline__ void pair_run_starts(uint64_t pk, uint64_t prev, int ib, int32_t S, int64_t i,
+                                                int32_t* __restrict__ seg) {
+    const int32_t c = (int32_t)(pk >> ib);
+    if ((unsigned)c >= (unsigned)(2 * S)) return;
+    if ((prev >> (ib + 1)) != (uint64_t)(c >> 1)) seg[c & ~1] = (int32_t)i;
+    if ((c & 1) && (prev >> ib) != (uint64_t)c) seg[c] = (int32_t)i;
+}
+
+// perm, T, sd and the run starts from the sorted words: position i holds time rank
 // j = word mod 2^ib (input index order[j], or j) of pair id and direction word >> ib.
-template <typename TS>
+// SORTED: t holds the timestamps in sorted order already (the sort's values); otherwise
+// they are gathered from the input order.
+template <typename TS, bool SORTED>
 __global__ void k_pair_store(const uint64_t* __restrict__ packed, const uint32_t* __restrict__ order, int64_t mk,
                              int32_t S, int ib, const TS* __restrict__ t, int32_t* __restrict__ perm,
                              TS* __restrict__ T, int32_t* __restrict__ sd, int32_t* __restrict__ seg) {
@@ -254,18 +278,75 @@ __global__ void k_pair_store(const uint64_t* __restrict__ packed, const uint32_t
         const int64_t j = (int64_t)(pk & jm);
         const uint32_t o = order ? order[j] : (uint32_t)j;
         __stcs(perm + i, (int32_t)o);
-        T[i] = t[o];
-        const int32_t c = (int32_t)(pk >> ib);
-        __stcs(sd + i, c);
-        // (c < 2S unless the pair ids' sort failed, which the host learns right after)
-        if ((unsigned)c < (unsigned)(2 * S) && (i == 0 || (int32_t)(packed[i - 1] >> (ib + 1)) != (c >> 1))) {
-            seg[c & ~1] = (int32_t)i;
-            seg[(c & ~1) + 1] = -1;
+        T[i] = SORTED ? __ldcs(t + i) : t[o];
+        __stcs(sd + i, (int32_t)(pk >> ib));
+        pair_run_starts(pk, i > 0 ? packed[i - 1] : ~0ull, ib, S, i, seg);
+    }
+}
+
+// The same for a 32-bit store whose timestamps came sorted with the words, four
+// positions per thread with 16-byte loads and stores (the last quad may be partial).
+__global__ void k_pair_store4(const uint64_t* __restrict__ packed, const uint32_t* __restrict__ order, int64_t mk,
+                              int32_t S, int ib, const uint32_t* __restrict__ ts, int32_t* __restrict__ perm,
+                              uint32_t* __restrict__ T, int32_t* __restrict__ sd, int32_t* __restrict__ seg) {
+    const uint64_t jm = (1ull << ib) - 1;
+    const int64_t nq = (mk + 3) >> 2;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i0 = q << 2;
+        const bool full = i0 + 4 <= mk;
+        uint64_t pk[4];
+        uint32_t tv[4];
+        if (full) {
+            const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2*>(packed + i0));
+            const ulonglong2 b = __ldcs(reinterpret_cast<const ulonglong2*>(packed + i0 + 2));
+            const uint4 tt = __ldcs(reinterpret_cast<const uint4*>(ts + i0));
+            pk[0] = a.x;
+            pk[1] = a.y;
+            pk[2] = b.x;
+            pk[3] = b.y;
+            tv[0] = tt.x;
+            tv[1] = tt.y;
+            tv[2] = tt.z;
+            tv[3] = tt.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                pk[e] = i0 + e < mk ? packed[i0 + e] : 0;
+                tv[e] = i0 + e < mk ? ts[i0 + e] : 0;
+            }
+        }
+        int32_t o[4], c[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const int64_t j = (int64_t)(pk[e] & jm);
+            o[e] = order ? (int32_t)order[j] : (int32_t)j;
+            c[e] = (int32_t)(pk[e] >> ib);
+        }
+        uint64_t prev = i0 > 0 ? packed[i0 - 1] : ~0ull;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            if (i0 + e < mk) pair_run_starts(pk[e], prev, ib, S, i0 + e, seg);
+            prev = pk[e];
+        }
+        if (full) {
+            __stcs(reinterpret_cast<int4*>(perm + i0), make_int4(o[0], o[1], o[2], o[3]));
+            __stcs(reinterpret_cast<uint4*>(T + i0), make_uint4(tv[0], tv[1], tv[2], tv[3]));
+            __stcs(reinterpret_cast<int4*>(sd + i0), make_int4(c[0], c[1], c[2], c[3]));
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                if (i0 + e < mk) {
+                    perm[i0 + e] = o[e];
+                    T[i0 + e] = tv[e];
+                    sd[i0 + e] = c[e];
+                }
+            }
         }
     }
 }
 
-// seg[2s+1] = first b->a position of s, or the end of s when it has none.
+// seg[2s+1] = first b->a position of s (the full-key path, whose k_segments marks every
+// b->a start -1 first).
 __global__ void k_segments_split(const int32_t* __restrict__ sd, int64_t mk, int32_t S,
                                  int32_t* __restrict__ seg) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mk;
@@ -275,6 +356,7 @@ __global__ void k_segments_split(const int32_t* __restrict__ sd, int64_t mk, int
     }
 }
 
+// seg[2s+1] = the end of s when it has no b->a run.
 __global__ void k_segments_fix(int32_t S, int64_t mk, int32_t* __restrict__ seg) {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S;
          s += (int64_t)gridDim.x * blockDim.x) {
@@ -353,14 +435,19 @@ __global__ void k_max_i32(const int32_t* __restrict__ a, int64_t n, int* __restr
     if ((threadIdx.x & 31) == 0) atomicMax(out, best);
 }
 
-// sig[s] = temporal edges of static edge s (both directions), and their maximum.
-__global__ void k_max_sigma(const int32_t* __restrict__ seg, int32_t S, int32_t* __restrict__ sig,
+// osig[j] = temporal edges (both directions) of the static edge at out-list position j,
+// and their maximum: the probe slots a triangle adds per edge, read by the triangle
+// passes next to the out-list entries themselves. From the per-pair counts sigma when
+// given, else from the run bounds.
+__global__ void k_out_sigma(const int32_t* __restrict__ sigma, const int32_t* __restrict__ seg,
+                            const int32_t* __restrict__ out_eid, int32_t S, int32_t* __restrict__ osig,
                             int* __restrict__ out) {
     int best = 0;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t c = seg[2 * s + 2] - seg[2 * s];
-        sig[s] = c;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < S;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = out_eid[j];
+        const int32_t c = sigma ? sigma[e] : seg[2 * e + 2] - seg[2 * e];
+        osig[j] = c;
         best = max(best, c);
     }
 #pragma unroll
@@ -1911,67 +1998,97 @@ __global__ void k_outptr(const int32_t* __restrict__ rowptr, const int32_t* __re
 
 // Thread per oriented edge (u, v): merge N+(u) and N+(v) (both ascending by id).
 // Triangles of oriented edge u -> v: the common out-neighbours w of u and v (both lists
-// sorted). The counting pass merges the two lists in one thread per edge. The writing
-// pass (more work per triangle) does the same for a light edge, while the lists of a
-// heavy edge (|out(u)| + |out(v)| > TRI_HEAVY, the degeneracy core) are intersected by
-// the whole warp: out(v) is staged in shared memory and every lane binary-searches its
-// share of out(u) in it, so that the latency is a few searches instead of one long
-// merge chain. Both passes find the same set, so the counts match the writes.
+// sorted). A light edge is merged by one thread; the lists of a heavy edge
+// (|out(u)| + |out(v)| > heavy_min, the degeneracy core) are intersected by the whole
+// warp: out(v) is staged in shared memory with its entries' edge ids and temporal edge
+// counts, and every lane binary-searches its share of out(u) in it, the loads of its next
+// share issued before the search, so that a hit needs no further global load. Both
+// passes find the same set, so the counts match the writes.
 constexpr int TRI_THREADS = 256;
 constexpr int TRI_HEAVY = 48;
 constexpr int TRI_STAGE = 256;  // staged out-list entries per warp (longer lists are merged by one lane)
 
-// Lane-parallel intersection of out(u) = nbr[i1, e1) with out(v) = nbr[i2, e2) staged in
-// sb (e2 - i2 <= TRI_STAGE). Calls hit(ia, ib) for every common entry (ia in out(u), ib in
-// out(v)) on the lane that found it. The whole warp must call it.
-template <typename F>
-__device__ __forceinline__ void warp_intersect(const int32_t* __restrict__ nbr, int32_t i1, int32_t e1, int32_t i2,
-                                               int32_t e2, int32_t* sb, F&& hit) {
+// One warp's staged out(v): neighbour ids, and per entry the static edge id and its
+// temporal edge count.
+struct TriStageW {
+    int32_t nbr[TRI_STAGE];
+    int32_t sig[TRI_STAGE];
+    int32_t eid[TRI_STAGE];
+};
+
+// Lane-parallel intersection of out(u) = [i1, e1) with out(v) = [i2, e2) (e2 - i2 <=
+// TRI_STAGE) of the out-lists (nbr, osig and, when EID, eid by position). Calls
+// hit(ia, pos, w, sig_u, eid_u, sig_v, eid_v) once per lane and step: ia the lane's
+// position in out(u), pos the matching position in out(v) or -1, w = nbr[ia], and the
+// edge counts and (EID) ids of the static edges (u, w) and (v, w) when pos >= 0. The whole
+// warp must call it.
+template <bool EID, typename F>
+__device__ __forceinline__ void warp_intersect(const int32_t* __restrict__ nbr, const int32_t* __restrict__ osig,
+                                               const int32_t* __restrict__ eid, int32_t i1, int32_t e1, int32_t i2,
+                                               int32_t e2, TriStageW& st, F&& hit) {
     const int lane = threadIdx.x & 31;
     const int nb = e2 - i2;
-    for (int t = lane; t < nb; t += 32) sb[t] = nbr[i2 + t];
+    for (int t = lane; t < nb; t += 32) {
+        st.nbr[t] = nbr[i2 + t];
+        st.sig[t] = osig[i2 + t];
+        if (EID) st.eid[t] = eid[i2 + t];
+    }
+    int32_t x = 0, su = 0, eu = 0;
+    if (i1 + lane < e1) {
+        x = nbr[i1 + lane];
+        su = osig[i1 + lane];
+        if (EID) eu = eid[i1 + lane];
+    }
     __syncwarp();
     for (int32_t ia0 = i1; ia0 < e1; ia0 += 32) {
         const int32_t ia = ia0 + lane;
+        // the next share's loads, in flight during this share's search
+        int32_t xn = 0, sn = 0, en = 0;
+        if (ia + 32 < e1) {
+            xn = nbr[ia + 32];
+            sn = osig[ia + 32];
+            if (EID) en = eid[ia + 32];
+        }
         int pos = -1;
         if (ia < e1) {
-            const int32_t x = nbr[ia];
             int lo = 0, hi = nb;  // first staged entry >= x
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                if (sb[mid] < x) lo = mid + 1;
+                if (st.nbr[mid] < x) lo = mid + 1;
                 else hi = mid;
             }
-            if (lo < nb && sb[lo] == x) pos = lo;
+            if (lo < nb && st.nbr[lo] == x) pos = lo;
         }
-        hit(ia, pos);
+        hit(ia, pos, x, su, eu, pos >= 0 ? st.sig[pos] : 0, (EID && pos >= 0) ? st.eid[pos] : 0);
+        x = xn;
+        su = sn;
+        eu = en;
     }
     __syncwarp();
 }
 
 // Also the probe slots of each oriented edge's triangles (sum over them of the three
-// edges' temporal edge counts sig) into pcnt, and of all triangles into *probes, so that
+// edges' temporal edge counts) into pcnt, and of all triangles into *probes, so that
 // the triangles' probe offsets are known before they are written.
 // Like the writing pass, an edge whose two out-lists hold more than heavy_min entries is
 // intersected by the whole warp (the thread-versus-warp split the autotuner picks).
 __global__ void __launch_bounds__(TRI_THREADS) k_tri_count(const int32_t* __restrict__ outptr,
                                                            const int32_t* __restrict__ out_nbr,
                                                            const int32_t* __restrict__ out_src,
-                                                           const int32_t* __restrict__ out_eid,
-                                                           const int32_t* __restrict__ sig, int32_t S,
+                                                           const int32_t* __restrict__ osig, int32_t S,
                                                            int32_t* __restrict__ cnt, int64_t* __restrict__ pcnt,
                                                            unsigned long long* __restrict__ merged,
                                                            unsigned long long* __restrict__ probes, int heavy_min) {
-    __shared__ int32_t stage[TRI_THREADS / 32][TRI_STAGE];
+    __shared__ TriStageW stage[TRI_THREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long acc = 0, pacc = 0;
     for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); j0 < S; j0 += stride) {
         const int64_t j = j0 + lane;
-        int32_t i1 = 0, e1 = 0, i2 = 0, e2 = 0, s_uv = 0;
+        int32_t i1 = 0, e1 = 0, i2 = 0, e2 = 0, sig_uv = 0;
         if (j < S) {
             const int32_t u = out_src[j], v = out_nbr[j];
-            s_uv = out_eid[j];
+            sig_uv = osig[j];
             i1 = outptr[u];
             e1 = outptr[u + 1];
             i2 = outptr[v];
@@ -1987,12 +2104,12 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_count(const int32_t* __rest
                 const int32_t x = out_nbr[a1], y = out_nbr[a2];
                 if (x == y) {
                     c++;
-                    ps += (unsigned long long)(sig[out_eid[a1]] + sig[out_eid[a2]]);
+                    ps += (unsigned long long)(osig[a1] + osig[a2]);
                 }
                 a1 += (x <= y);
                 a2 += (y <= x);
             }
-            if (c) ps += (unsigned long long)c * (unsigned long long)sig[s_uv];
+            if (c) ps += (unsigned long long)c * (unsigned long long)sig_uv;
             pacc += ps;
             cnt[j] = c;
             pcnt[j] = (int64_t)ps;
@@ -2003,22 +2120,23 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_count(const int32_t* __rest
             hm &= hm - 1;
             const int32_t b1 = __shfl_sync(0xffffffffu, i1, src), f1 = __shfl_sync(0xffffffffu, e1, src);
             const int32_t b2 = __shfl_sync(0xffffffffu, i2, src), f2 = __shfl_sync(0xffffffffu, e2, src);
-            const int32_t hs = __shfl_sync(0xffffffffu, s_uv, src);
+            const int32_t hs = __shfl_sync(0xffffffffu, sig_uv, src);
             int32_t c = 0;
             unsigned long long hp = 0;
-            warp_intersect(out_nbr, b1, f1, b2, f2, stage[warp], [&](int32_t ia, int pos) {
-                if (pos >= 0) {
-                    c++;
-                    hp += (unsigned long long)(sig[out_eid[ia]] + sig[out_eid[b2 + pos]]);
-                }
-            });
+            warp_intersect<false>(out_nbr, osig, nullptr, b1, f1, b2, f2, stage[warp],
+                                  [&](int32_t, int pos, int32_t, int32_t su, int32_t, int32_t sv, int32_t) {
+                                      if (pos >= 0) {
+                                          c++;
+                                          hp += (unsigned long long)(su + sv);
+                                      }
+                                  });
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 c += __shfl_xor_sync(0xffffffffu, c, o);
                 hp += __shfl_xor_sync(0xffffffffu, hp, o);
             }
             if (lane == 0) {
-                hp += (unsigned long long)c * (unsigned long long)sig[hs];
+                hp += (unsigned long long)c * (unsigned long long)hs;
                 cnt[j0 + src] = c;
                 pcnt[j0 + src] = (int64_t)hp;
                 pacc += hp;
@@ -2050,30 +2168,29 @@ __global__ void k_tile_starts(const int64_t* __restrict__ tri_off, int64_t ntri,
     }
 }
 
-// Each triangle's liveness bytes (the smallest window bucket of its roles per direction
-// variant, liveness.cuh) are computed as it is written, while the merges of other threads
-// wait for memory.
-template <typename TS>
-__global__ void __launch_bounds__(TRI_THREADS, 4) k_tri_write(const int32_t* __restrict__ outptr,
+// Writes every triangle with its probe offset (the running sum of the probe slots of the
+// triangles before it, from the counting pass's prefix per oriented edge) and counts the
+// triangles on every static edge.
+__global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __restrict__ outptr,
                                                            const int32_t* __restrict__ out_nbr,
                                                            const int32_t* __restrict__ out_eid,
-                                                           const int32_t* __restrict__ out_src, int32_t S,
+                                                           const int32_t* __restrict__ out_src,
+                                                           const int32_t* __restrict__ osig, int32_t S,
                                                            const int64_t* __restrict__ toff,
-                                                           const int64_t* __restrict__ poff,
-                                                           const int32_t* __restrict__ sig, int4* __restrict__ tri,
+                                                           const int64_t* __restrict__ poff, int4* __restrict__ tri,
                                                            int64_t* __restrict__ tri_off, int32_t* __restrict__ common,
-                                                           int heavy_min, const RunEnds<TS>* __restrict__ ends,
-                                                           int64_t tstride, uint8_t* __restrict__ tlive) {
-    __shared__ int32_t stage[TRI_THREADS / 32][TRI_STAGE];
+                                                           int heavy_min) {
+    __shared__ TriStageW stage[TRI_THREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); j0 < S; j0 += stride) {
         const int64_t j = j0 + lane;
-        int32_t u = 0, v = 0, s_uv = 0, i1 = 0, e1 = 0, i2 = 0, e2 = 0;
+        int32_t u = 0, v = 0, s_uv = 0, sig_uv = 0, i1 = 0, e1 = 0, i2 = 0, e2 = 0;
         if (j < S) {
             u = out_src[j];
             v = out_nbr[j];
             s_uv = out_eid[j];
+            sig_uv = osig[j];
             i1 = outptr[u];
             e1 = outptr[u + 1];
             i2 = outptr[v];
@@ -2083,18 +2200,15 @@ __global__ void __launch_bounds__(TRI_THREADS, 4) k_tri_write(const int32_t* __r
         if (j < S && !heavy) {
             int64_t p = toff[j], q = poff[j];
             int32_t n_here = 0;
-            const int32_t sig_uv = sig[s_uv];
             int32_t a1 = i1, a2 = i2;
             while (a1 < e1 && a2 < e2) {
                 const int32_t x = out_nbr[a1], y = out_nbr[a2];
                 if (x == y) {
                     const int32_t w = x, s_uw = out_eid[a1], s_vw = out_eid[a2];
                     const int flags = (u < v ? 1 : 0) | (u < w ? 2 : 0) | (v < w ? 4 : 0);
-                    const int4 tr = make_int4(s_uv, s_uw, s_vw, flags);
-                    tri[p] = tr;
+                    tri[p] = make_int4(s_uv, s_uw, s_vw, flags);
                     tri_off[p] = q;
-                    write_liveness<TS>(tr, ends, p, tstride, tlive);
-                    q += (int64_t)sig_uv + sig[s_uw] + sig[s_vw];
+                    q += (int64_t)sig_uv + osig[a1] + osig[a2];
                     atomicAdd(&common[s_uw], 1);
                     atomicAdd(&common[s_vw], 1);
                     p++;
@@ -2112,43 +2226,35 @@ __global__ void __launch_bounds__(TRI_THREADS, 4) k_tri_write(const int32_t* __r
             const int32_t b1 = __shfl_sync(0xffffffffu, i1, src), f1 = __shfl_sync(0xffffffffu, e1, src);
             const int32_t b2 = __shfl_sync(0xffffffffu, i2, src), f2 = __shfl_sync(0xffffffffu, e2, src);
             const int32_t hu = __shfl_sync(0xffffffffu, u, src), hv = __shfl_sync(0xffffffffu, v, src);
-            const int32_t hs = __shfl_sync(0xffffffffu, s_uv, src);
+            const int32_t hs = __shfl_sync(0xffffffffu, s_uv, src), hsig = __shfl_sync(0xffffffffu, sig_uv, src);
             int64_t p = (lane == 0) ? toff[j0 + src] : 0, q = (lane == 0) ? poff[j0 + src] : 0;
             p = __shfl_sync(0xffffffffu, p, 0);
             q = __shfl_sync(0xffffffffu, q, 0);
-            const int32_t sig_uv = sig[hs];
             int n_here = 0;
-            warp_intersect(out_nbr, b1, f1, b2, f2, stage[warp], [&](int32_t ia, int pos) {
-                const unsigned m = __ballot_sync(0xffffffffu, pos >= 0);
-                int64_t c = 0;
-                int32_t s_uw = 0, s_vw = 0;
-                if (pos >= 0) {
-                    s_uw = out_eid[ia];
-                    s_vw = out_eid[b2 + pos];
-                    c = (int64_t)sig_uv + sig[s_uw] + sig[s_vw];
-                }
-                // the hits' probe offsets: a warp prefix of their costs, in lane order
-                int64_t inc = c;
+            warp_intersect<true>(
+                out_nbr, osig, out_eid, b1, f1, b2, f2, stage[warp],
+                [&](int32_t, int pos, int32_t w, int32_t su, int32_t s_uw, int32_t sv, int32_t s_vw) {
+                    const unsigned m = __ballot_sync(0xffffffffu, pos >= 0);
+                    const int64_t c = pos >= 0 ? (int64_t)hsig + su + sv : 0;
+                    // the hits' probe offsets: a warp prefix of their costs, in lane order
+                    int64_t inc = c;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                    if (lane >= o) inc += y;
-                }
-                if (pos >= 0) {
-                    const int64_t at = p + __popc(m & ((1u << lane) - 1u));
-                    const int32_t w = out_nbr[ia];
-                    const int flags = (hu < hv ? 1 : 0) | (hu < w ? 2 : 0) | (hv < w ? 4 : 0);
-                    const int4 tr = make_int4(hs, s_uw, s_vw, flags);
-                    tri[at] = tr;
-                    tri_off[at] = q + inc - c;
-                    write_liveness<TS>(tr, ends, at, tstride, tlive);
-                    atomicAdd(&common[s_uw], 1);
-                    atomicAdd(&common[s_vw], 1);
-                }
-                p += __popc(m);
-                q += __shfl_sync(0xffffffffu, inc, 31);
-                n_here += __popc(m);
-            });
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += y;
+                    }
+                    if (pos >= 0) {
+                        const int64_t at = p + __popc(m & ((1u << lane) - 1u));
+                        const int flags = (hu < hv ? 1 : 0) | (hu < w ? 2 : 0) | (hv < w ? 4 : 0);
+                        tri[at] = make_int4(hs, s_uw, s_vw, flags);
+                        tri_off[at] = q + inc - c;
+                        atomicAdd(&common[s_uw], 1);
+                        atomicAdd(&common[s_vw], 1);
+                    }
+                    p += __popc(m);
+                    q += __shfl_sync(0xffffffffu, inc, 31);
+                    n_here += __popc(m);
+                });
             if (lane == 0 && n_here) atomicAdd(&common[hs], n_here);
         }
     }
@@ -2218,30 +2324,43 @@ struct StoreJob {
     const uint32_t* slotw;  // [m] pair table slot and direction of each input edge
     const uint32_t* order;  // time order of an unsorted input, or null
     const int32_t* sid;     // [table] dense pair id of each table slot
-    uint32_t* t32;          // [m] 32-bit time offsets (ts32), or null
     int ib;                 // bits of a time rank
 };
 
-static void temporal_store(folty_graph* g, const StoreJob& job, Scratch& sc) {
+// sigma (S entries, zeroed here) receives each static edge's temporal edge count, and
+// packed_ev is recorded once it is complete.
+static void temporal_store(folty_graph* g, const StoreJob& job, Scratch& sc, int32_t* sigma, cudaEvent_t packed_ev) {
     const int T = 256;
     const int64_t m = g->m, mk = g->m_kept;
     const int32_t S = g->S;
     const int ib = job.ib;
     cudaStream_t s = sc.stream();
-    // edges by (pair id, direction, time rank): keys only, on the id and direction bits
+    // the whole store, beside the peeling: its pair words and time offsets (4 B slot and
+    // 8 B time read, 12 B written per input edge) and the sorted arrays (the word and the
+    // time read, perm, T and sd written: 24 B per kept edge); the sort passes inside are
+    // also SORT spans
+    StageSpan span(ST_STORE, s, 24 * m + 24 * mk);
+    // edges by (pair id, direction, time rank), sorted on the id and direction bits; a
+    // 32-bit store carries each edge's time offset through the sort as its value
     uint64_t* packed = sc.get<uint64_t>(m);
     uint64_t* packed_alt = sc.get<uint64_t>(m);
-    FOLTY_LAUNCH(k_pair_pack, grid_for(m, T), T, 0, s, job.slotw, job.order, m, job.sid, S, ib, packed);
-    const bool palt = radix_sort_keys(sc, packed, packed_alt, m, ib, bit_length((uint64_t)(2 * S)));
+    uint32_t* tv = g->ts32 ? sc.get<uint32_t>(m) : nullptr;
+    uint32_t* tv_alt = g->ts32 ? sc.get<uint32_t>(m) : nullptr;
+    FOLTY_CUDA(cudaMemsetAsync(sigma, 0, sizeof(int32_t) * (size_t)S, s));
+    FOLTY_LAUNCH(k_pair_pack, grid_for(m, T), T, 0, s, job.slotw, job.order, m, job.sid, S, ib, packed, g->in_t,
+                 g->tmin, tv, sigma);
+    FOLTY_CUDA(cudaEventRecord(packed_ev, s));
+    const int cbits = bit_length((uint64_t)(2 * S));
+    const bool palt = g->ts32 ? radix_sort_pairs(sc, packed, packed_alt, tv, tv_alt, m, ib, cbits)
+                              : radix_sort_keys(sc, packed, packed_alt, m, ib, cbits);
     const uint64_t* sp = palt ? packed_alt : packed;
-    if (job.t32) FOLTY_LAUNCH(k_offsets32, grid_for(m, T), T, 0, s, g->in_t, m, g->tmin, job.t32);
+    FOLTY_CUDA(cudaMemsetAsync(g->seg, 0xff, sizeof(int32_t) * (2 * (size_t)S + 1), s));
     if (g->ts32)
-        FOLTY_LAUNCH(k_pair_store<uint32_t>, grid_for(mk, T), T, 0, s, sp, job.order, mk, S, ib, job.t32, g->perm,
-                     (uint32_t*)g->T, g->sd, g->seg);
+        FOLTY_LAUNCH(k_pair_store4, grid_for((mk + 3) / 4, T), T, 0, s, sp, job.order, mk, S, ib,
+                     palt ? tv_alt : tv, g->perm, (uint32_t*)g->T, g->sd, g->seg);
     else
-        FOLTY_LAUNCH(k_pair_store<int64_t>, grid_for(mk, T), T, 0, s, sp, job.order, mk, S, ib, g->in_t, g->perm,
-                     (int64_t*)g->T, g->sd, g->seg);
-    FOLTY_LAUNCH(k_segments_split, grid_for(mk, T), T, 0, s, g->sd, mk, S, g->seg);
+        FOLTY_LAUNCH((k_pair_store<int64_t, false>), grid_for(mk, T), T, 0, s, sp, job.order, mk, S, ib, g->in_t,
+                     g->perm, (int64_t*)g->T, g->sd, g->seg);
     FOLTY_LAUNCH(k_segments_fix, grid_for(S, T), T, 0, s, S, mk, g->seg);
 }
 
@@ -2251,8 +2370,7 @@ static void temporal_store(folty_graph* g, const StoreJob& job, Scratch& sc) {
 // time ranks do not fit one word); FOLTY_PAIR_SORT=keys forces that answer. The
 // distinct-pair sort is checked by the next read-back (before any of its consumers but
 // the guarded k_pair_ids index with it).
-static bool pair_ids_sort(folty_graph* g, Scratch& sc, const uint32_t* order, uint32_t* t32, cudaStream_t s,
-                          StoreJob* job) {
+static bool pair_ids_sort(folty_graph* g, Scratch& sc, const uint32_t* order, cudaStream_t s, StoreJob* job) {
     const int T = 256;
     const int64_t m = g->m, mk = g->m_kept;
     const int32_t n = g->n;
@@ -2312,13 +2430,13 @@ static bool pair_ids_sort(folty_graph* g, Scratch& sc, const uint32_t* order, ui
     g->seg = graph_alloc<int32_t>(g, 2 * (int64_t)S + 1, s);
     int32_t* sid = sc.get<int32_t>(tb);
     FOLTY_LAUNCH(k_pair_ids, grid_for(S, T), T, 0, s, ur, us, S, n, tb, sid, g->ea, g->eb);
-    *job = StoreJob{slotw, order, sid, t32, ib};
+    *job = StoreJob{slotw, order, sid, ib};
     return true;
 }
 
 // A1 with the full pair key (2 p(a, b) + direction, see k_build_keys) and the input
 // index (or time rank) as the value.
-static void pair_key_sort(folty_graph* g, Scratch& sc, const uint32_t* order, uint32_t* t32, cudaStream_t s) {
+static void pair_key_sort(folty_graph* g, Scratch& sc, const uint32_t* order, cudaStream_t s) {
     const int T = 256;
     const int64_t m = g->m, mk = g->m_kept;
     const int32_t n = g->n;
@@ -2346,6 +2464,9 @@ static void pair_key_sort(folty_graph* g, Scratch& sc, const uint32_t* order, ui
     sort_check(g, s);
     int32_t* newpair = sc.get<int32_t>(mk + 1);
     int32_t* pscan = sc.get<int32_t>(mk + 1);
+    // 32-bit offsets of the input timestamps, written right before the gather so that
+    // they are still in L2 there
+    uint32_t* t32 = (g->ts32 && mk > 0) ? sc.get<uint32_t>(m) : nullptr;
     if (mk > 0) {
         if (t32) FOLTY_LAUNCH(k_offsets32, grid_for(m, T), T, 0, s, g->in_t, m, g->tmin, t32);
         if (g->ts32)
@@ -2377,16 +2498,16 @@ static void pair_key_sort(folty_graph* g, Scratch& sc, const uint32_t* order, ui
 // or picked by timing the pass under each candidate split. All candidates count the same
 // triangles, so the last trial's outputs stand.
 static void tune_triangles(folty_graph* g, const int32_t* outptr, const int32_t* out_nbr, const int32_t* out_src,
-                           const int32_t* out_eid, const int32_t* sig, int32_t* tcnt, int64_t* pcnt,
-                           unsigned long long* merged, cudaStream_t s) {
+                           const int32_t* osig, int32_t* tcnt, int64_t* pcnt, unsigned long long* merged,
+                           cudaStream_t s) {
     const int32_t S = g->S;
     const unsigned grid = grid_for(S, TRI_THREADS);
     const std::vector<int64_t> key{g->n, g->m_kept, S};
     bool trials = !(tune_forced(&g->tune, false) || tune_lookup(key, &g->tune, false)) && !profiling_on();
     if (!trials) {
         FOLTY_CUDA(cudaMemsetAsync(merged, 0, 2 * sizeof(unsigned long long), s));
-        FOLTY_LAUNCH(k_tri_count, grid, TRI_THREADS, 0, s, outptr, out_nbr, out_src, out_eid, sig, S, tcnt, pcnt,
-                     merged, merged + 1, g->tune.tri_heavy);
+        FOLTY_LAUNCH(k_tri_count, grid, TRI_THREADS, 0, s, outptr, out_nbr, out_src, osig, S, tcnt, pcnt, merged,
+                     merged + 1, g->tune.tri_heavy);
         return;
     }
     cudaEvent_t ev[TUNE_TRIALS + 1];
@@ -2396,8 +2517,8 @@ static void tune_triangles(folty_graph* g, const int32_t* outptr, const int32_t*
         for (int c = 0; c < TUNE_TRIALS; c++) {
             FOLTY_CUDA(cudaMemsetAsync(merged, 0, 2 * sizeof(unsigned long long), s));
             FOLTY_CUDA(cudaEventRecord(ev[0], s));
-            FOLTY_LAUNCH(k_tri_count, grid, TRI_THREADS, 0, s, outptr, out_nbr, out_src, out_eid, sig, S, tcnt, pcnt,
-                         merged, merged + 1, TRI_HEAVY_CAND[c]);
+            FOLTY_LAUNCH(k_tri_count, grid, TRI_THREADS, 0, s, outptr, out_nbr, out_src, osig, S, tcnt, pcnt, merged,
+                         merged + 1, TRI_HEAVY_CAND[c]);
             FOLTY_CUDA(cudaEventRecord(ev[c + 1], s));
             FOLTY_CUDA(cudaEventSynchronize(ev[c + 1]));
             FOLTY_CUDA(cudaEventElapsedTime(&g->tune.tri_ms[c], ev[0], ev[c + 1]));
@@ -2428,9 +2549,6 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     if (g->ts32) g->T = graph_alloc<uint32_t>(g, mk, s);
     else g->T = graph_alloc<int64_t>(g, mk, s);
     g->sd = graph_alloc<int32_t>(g, mk, s);
-    // 32-bit offsets of the input timestamps, written by the sort path right before its
-    // gather so that they are still in L2 there
-    uint32_t* t32 = (g->ts32 && mk > 0) ? sc.get<uint32_t>(m) : nullptr;
     // time order of an input that is not sorted by time (stable): order[j] = input index
     uint32_t* order = nullptr;
     if (!g->info.time_sorted && m > 1) {
@@ -2444,15 +2562,27 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         order = alt ? iv_alt : iv;
     }
     StoreJob job{};
-    const bool ids = pair_ids_sort(g, sc, order, t32, s, &job);
-    if (!ids) pair_key_sort(g, sc, order, t32, s);
+    const bool ids = pair_ids_sort(g, sc, order, s, &job);
+    if (!ids) pair_key_sort(g, sc, order, s);
     const int32_t S = g->S;
     // the temporal store of the dense-id path: forked to a side stream once the grid
-    // peeling kernel has finished (its grid barriers want every SM), joined before the
-    // triangle pass; the later peeling phases on a second one of high priority. On an
-    // error in between, the side streams are drained before the call's buffers go.
+    // peeling kernel has finished (its grid barriers want every SM), joined after the
+    // triangle passes (which need only its per-pair counts); the later peeling phases on
+    // a second one of high priority. On an error in between, the side streams are
+    // drained before the call's buffers go.
     SideStream side(s, false);
     SideStream hi(s, true);
+    struct EventHolder {
+        cudaEvent_t e = nullptr;
+        ~EventHolder() {
+            if (e) cudaEventDestroy(e);
+        }
+    } packed_ev;
+    int32_t* sigma = nullptr;
+    if (ids) {
+        FOLTY_CUDA(cudaEventCreateWithFlags(&packed_ev.e, cudaEventDisableTiming));
+        sigma = sc.get<int32_t>(S > 0 ? S : 1);
+    }
 
     // ---------------- A2: static CSR
     // static edges are sorted by (a, b); a stable sort by b lists them by (b, a)
@@ -2540,7 +2670,7 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         }
         if (ids) {
             Scratch sc2(g->alloc, side.fork(), g->dev_err);
-            temporal_store(g, job, sc2);
+            temporal_store(g, job, sc2, sigma, packed_ev.e);
         }
         if (n > 0) {
             // the cluster and single-CTA phases: latency-bound chains of small rounds, on
@@ -2618,33 +2748,23 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
                      out_eid, out_src);
 
     // ---------------- A5: triangles
-    if (ids) side.join();
-    // the raw input is no longer needed
-    graph_release(g, g->in_src, s);
-    graph_release(g, g->in_dst, s);
-    graph_release(g, g->in_t, s);
-    g->in_src = g->in_dst = nullptr;
-    g->in_t = nullptr;
-    // and neither is the pair table the load filled
-    graph_release(g, g->pre_table, s);
-    graph_release(g, g->pre_slotw, s);
-    graph_release(g, g->pre_flags, s);
-    g->pre_table = nullptr;
-    g->pre_slotw = nullptr;
-    g->pre_flags = nullptr;
+    // the two triangle passes need the static graph and every static edge's temporal edge
+    // count, not the store itself: they run beside the store's sort (joined before the
+    // run-ends table)
+    if (ids) FOLTY_CUDA(cudaStreamWaitEvent(s, packed_ev.e, 0));
     g->common = graph_alloc<int32_t>(g, S, s);
     FOLTY_CUDA(cudaMemsetAsync(g->common, 0, sizeof(int32_t) * ((size_t)S > 0 ? (size_t)S : 1), s));
     int32_t* tcnt = sc.get<int32_t>((int64_t)S + 1);
     int64_t* toff = sc.get<int64_t>((int64_t)S + 1);
     unsigned long long* merged = sc.get<unsigned long long>(2);  // list lengths merged, probe slots
     FOLTY_CUDA(cudaMemsetAsync(merged, 0, 2 * sizeof(unsigned long long), s));
-    int32_t* sig = sc.get<int32_t>(S);
-    if (S > 0) FOLTY_LAUNCH(k_max_sigma, grid_for(S, T), T, 0, s, g->seg, S, sig, stat + 2);
+    int32_t* osig = sc.get<int32_t>(S);
+    if (S > 0) FOLTY_LAUNCH(k_out_sigma, grid_for(S, T), T, 0, s, sigma, g->seg, out_eid, S, osig, stat + 2);
     // the counting pass merges the two out-lists of every oriented edge: 4 B per merged
     // entry (known after the read-back below) + 8 B per static edge
     StageSpan tri_span(ST_TRIANGLES, s, 8 * (int64_t)S);
     int64_t* pcnt = sc.get<int64_t>((int64_t)S + 1);  // probe slots per oriented edge, then their prefix
-    if (S > 0) tune_triangles(g, outptr, out_nbr, out_src, out_eid, sig, tcnt, pcnt, merged, s);
+    if (S > 0) tune_triangles(g, outptr, out_nbr, out_src, osig, tcnt, pcnt, merged, s);
     exclusive_scan(sc, tcnt, toff, S);
     exclusive_scan(sc, pcnt, pcnt, S);
     tri_span.end();
@@ -2673,22 +2793,34 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     const int64_t ntri = g->ntri;
     g->tri = graph_alloc<int4>(g, ntri, s);
     g->tri_off = graph_alloc<int64_t>(g, ntri + 1, s);
-    prepare_liveness(g, s);  // the run-ends table the listing reads for the liveness bytes
-
     if (S > 0) {
         // the listing pass merges the same lists and writes 16 + 8 B per triangle
-        StageSpan span(ST_TRIANGLES, s, g->enum_bytes + 27 * ntri);  // + 16 B triangle, 8 B offset, 3 liveness bytes
-        if (g->ts32)
-            FOLTY_LAUNCH(k_tri_write<uint32_t>, grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr, out_eid,
-                         out_src, S, toff, pcnt, sig, g->tri, g->tri_off, g->common, g->tune.tri_heavy,
-                         (const RunEnds<uint32_t>*)g->run_ends, g->tlive_stride, g->tlive);
-        else
-            FOLTY_LAUNCH(k_tri_write<int64_t>, grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr, out_eid,
-                         out_src, S, toff, pcnt, sig, g->tri, g->tri_off, g->common, g->tune.tri_heavy,
-                         (const RunEnds<int64_t>*)g->run_ends, g->tlive_stride, g->tlive);
+        StageSpan span(ST_TRIANGLES, s, g->enum_bytes + 24 * ntri);
+        FOLTY_LAUNCH(k_tri_write, grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr, out_eid, out_src, osig,
+                     S, toff, pcnt, g->tri, g->tri_off, g->common, g->tune.tri_heavy);
     }
     // the probe offsets of the triangles come from the writing pass; the last entry is the total
     FOLTY_CUDA(cudaMemcpyAsync(g->tri_off + ntri, pcnt + S, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    if (ids) {
+        side.join();
+        sort_check(g, s);  // the store's sort completed before its arrays index anything
+    }
+    // the raw input is no longer needed
+    graph_release(g, g->in_src, s);
+    graph_release(g, g->in_dst, s);
+    graph_release(g, g->in_t, s);
+    g->in_src = g->in_dst = nullptr;
+    g->in_t = nullptr;
+    // and neither is the pair table the load filled
+    graph_release(g, g->pre_table, s);
+    graph_release(g, g->pre_slotw, s);
+    graph_release(g, g->pre_flags, s);
+    g->pre_table = nullptr;
+    g->pre_slotw = nullptr;
+    g->pre_flags = nullptr;
+    // the run-ends table and every triangle's liveness bytes
+    prepare_liveness(g, s);
+    triangle_liveness(g, s);
     g->info.triangles = ntri;
     // tile -> first triangle map of the probe kernels (query independent)
     g->n_tiles = (g->info.probes + PB_TILE - 1) / PB_TILE;

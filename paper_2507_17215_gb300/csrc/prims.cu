@@ -427,6 +427,11 @@ bool radix_sort_pairs(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uint32_t*
     return radix_sort_impl(sc, keys, keys_alt, vals, vals_alt, n, 0, bits);
 }
 
+bool radix_sort_pairs(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
+                      int64_t n, int lo, int bits) {
+    return radix_sort_impl(sc, keys, keys_alt, vals, vals_alt, n, lo, bits);
+}
+
 bool radix_sort_keys(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, int64_t n, int lo, int bits) {
     return radix_sort_impl(sc, keys, keys_alt, nullptr, nullptr, n, lo, bits);
 }
