@@ -63,7 +63,7 @@ WORKLOADS = {
 
 STAGE_KERNELS = {
     "probe": "k_probe_live (persistent window probes over the kept roles)",
-    "select": "k_live_select (liveness, scan and compaction of the kept triangles)",
+    "select": "k_live_sums + k_live_offsets + k_live_write (selection of the kept triangles by their liveness bytes)",
     "sort": "radix sort spans: k_rs_hist_all + k_rs_bases (all digit histograms), or one k_rs_onesweep digit pass",
     "peel": "k_peel (cooperative) + k_tail_* + k_peel_tail + k_solo_* + k_peel_solo",
     "threshold": "k_threshold",

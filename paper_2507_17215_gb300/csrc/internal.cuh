@@ -349,8 +349,9 @@ struct ProbeBuffers {
     int64_t* totals;  // kept triangles, slots
     int64_t* ltile;
     int64_t max_tiles;
-    unsigned long long* lsctl;
-    int64_t stiles;
+    int32_t* wcnt;    // per selection warp: kept triangles, then their exclusive prefix
+    int64_t* wcost;   // per selection warp: their slots, then the exclusive prefix
+    int64_t nw;
 };
 // The same buffers owned by the graph (held by its query plans).
 ProbeBuffers probe_buffers(folty_graph* g, cudaStream_t s);

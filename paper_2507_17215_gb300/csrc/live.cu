@@ -78,139 +78,174 @@ __device__ __forceinline__ int kept_roles_of(const int4 tr, const RunEnds<TS>* _
     return m;
 }
 
-// Kept roles of every triangle for one query, selected and compacted in one pass: kept
-// triangle j = L[j] with its role mask lmask[j] and its first probe slot loff[j] (prefix
-// of the kept triangles' costs = kept probes + LIVE_IDLE idle slots); totals[0] = kept
-// triangles, totals[1] = slots, loff[totals[0]] = totals[1]; and the probe tiles' map:
-// ltile[b] = kept triangle holding slot min(b * ptile, slots - 1) for b <= the number
-// of probe tiles (each kept triangle writes the tile starts inside its slots). A thread
-// takes LS_ITEMS consecutive triangles and reads their liveness bytes (tlive, the
-// smallest bucket of each triangle's roles for this direction variant) with two 16-byte
-// loads; only the triangles whose byte admits delta read their record and run ends (they
-// are few, but cluster: a warp deals its candidates round-robin over its lanes, so that
-// no lane works through a long run of them alone, and keeps each one's role mask and cost
-// in shared memory for the write). Tiles of LS_TILE triangles are taken in block start
-// order; the two prefix sums (kept count, cost) come from a block scan and two decoupled
-// look-backs by warp 0. *prof (may be null) gets the bytes read and written for the kept
-// triangles.
-constexpr int LS_ITEMS = 32;
-constexpr int LS_TILE = SCAN_THREADS * LS_ITEMS;  // 8192 triangles
+// Kept roles of every triangle for one query: kept triangle j = L[j] with its role mask
+// lmask[j] and its first probe slot loff[j] (prefix of the kept triangles' costs = kept
+// probes + LIVE_IDLE idle slots); totals[0] = kept triangles, totals[1] = slots,
+// loff[totals[0]] = totals[1]; and the probe tiles' map: ltile[b] = kept triangle holding
+// slot min(b * ptile, slots - 1) for b <= the number of probe tiles (each kept triangle
+// writes the tile starts inside its slots).
+//
+// Three passes without a look-back: every warp takes LS_WARP consecutive triangles (a
+// lane LS_ITEMS of them, read as 16-byte chunks of their liveness bytes: the smallest
+// bucket of each triangle's roles for this direction variant); k_live_sums writes the
+// warp's number of kept triangles and their cost, k_live_offsets turns those into
+// exclusive prefixes (one block), and k_live_write writes the kept triangles at them.
+// Only the triangles whose byte admits delta read their record and run ends: they are
+// few, but cluster, so a warp deals its candidates round-robin over its lanes (candidate
+// k of the warp, in triangle order, goes to lane k mod 32), and the write pass orders
+// their costs by a warp scan per round of 32.
+constexpr int LS_ITEMS = 64;
+constexpr int LS_WARP = 32 * LS_ITEMS;  // 2048 triangles per warp
+constexpr int LS_THREADS = 256;
+constexpr int LS_BLOCK = (LS_THREADS / 32) * LS_WARP;
 
-template <typename TS, int DIR>
-__global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const uint8_t* __restrict__ tlive,
-                                                              const int4* __restrict__ tri,
-                                                              const RunEnds<TS>* __restrict__ ends, int64_t ntri,
-                                                              int64_t delta, unsigned long long* lbc,
-                                                              unsigned long long* lbp, unsigned int* counter,
-                                                              int* err, int32_t* __restrict__ L,
-                                                              int64_t* __restrict__ loff, uint8_t* __restrict__ lmask,
-                                                              int64_t* __restrict__ totals,
-                                                              int64_t* __restrict__ ltile, int64_t max_tiles,
-                                                              int64_t ptile, unsigned long long* __restrict__ prof,
-                                                              const int64_t* __restrict__ qp) {
-    __shared__ int32_t wc[SCAN_THREADS / 32];
-    if (qp) delta = qp[0];  // the window from a device parameter block (replayed query plans)
-    __shared__ int64_t wp[SCAN_THREADS / 32];
-    __shared__ int32_t totc;
-    __shared__ int64_t totp;
-    __shared__ unsigned long long s_exc, s_exp;
-    __shared__ int64_t s_tile;
-    if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(counter, 1u);
-    __syncthreads();
-    const int64_t tile = s_tile;
-    const int64_t base = tile * LS_TILE;
-    const int64_t t0 = base + (int64_t)threadIdx.x * LS_ITEMS;
-    // ---- the thread's liveness bytes (rows are padded with DMIN_NEVER to whole 16-byte
-    // chunks) as a bit mask of the triangles whose byte admits delta
-    uint32_t lm = 0;
+// Bit i of the result: triangle t0 + i (i < LS_ITEMS) is kept at delta (rows are padded
+// with DMIN_NEVER to whole 16-byte chunks). A byte b admits delta exactly when
+// b <= B = bit length of delta (b = 0 always, b >= 1 when delta >= 2^(b-1); DMIN_NEVER
+// never, as B <= 63): four bytes at a time, (0x80 + B) - (b & 0x7f) keeps bit 7 set
+// exactly for b <= B (bytes never borrow from one another, and 255 & 0x7f = 127 > B), and
+// one multiplication gathers the four bit-7s.
+__device__ __forceinline__ uint64_t live_mask(const uint8_t* __restrict__ tlive, int64_t t0, int64_t ntri,
+                                              int64_t delta) {
+    const uint32_t B = delta > 0 ? (uint32_t)(64 - __clzll((unsigned long long)delta)) : 0u;
+    const uint32_t bias = 0x80808080u | (B * 0x01010101u);
+    uint64_t lm = 0;
 #pragma unroll
     for (int h = 0; h < LS_ITEMS / 16; h++) {
         uint4 w = make_uint4(~0u, ~0u, ~0u, ~0u);
         if (t0 + 16 * h < ntri) w = __ldcs(reinterpret_cast<const uint4*>(tlive + t0 + 16 * h));
         const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-        for (int i = 0; i < 16; i++)
-            if (bucket_live((uint8_t)(ws[i >> 2] >> (8 * (i & 3))), delta)) lm |= 1u << (16 * h + i);
+        for (int q = 0; q < 4; q++) {
+            const uint32_t hit = (bias - (ws[q] & 0x7f7f7f7fu)) & 0x80808080u;
+            const uint32_t nib = ((hit >> 7) * 0x10204080u) >> 28;  // bit j = byte j admits delta
+            lm |= (uint64_t)nib << (16 * h + 4 * q);
+        }
     }
-    // ---- the warp's candidates dealt round-robin over its lanes: candidate k of the warp
-    // is the (k - pre[l] + 1)-th set bit of lane l's mask, l the last lane with pre[l] <= k;
-    // its role mask and cost (kept probes + LIVE_IDLE) go to the tile's shared arrays
-    __shared__ uint32_t s_lm[SCAN_THREADS];
-    __shared__ int32_t s_pre[SCAN_THREADS];
-    __shared__ uint8_t s_mask[LS_TILE];
-    __shared__ int32_t s_cost[LS_TILE];  // kept probes: a triangle's fit 32 bits (at most m < 2^31)
-    const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
-    const int32_t own = __popc(lm);
-    int32_t inc = own;
+    return lm;
+}
+
+// The warp's candidates: this lane's mask lm, the number of candidates of the lanes
+// before it (pre) and of the warp (returned).
+__device__ __forceinline__ int warp_candidates(uint64_t lm, int& pre) {
+    const int lane = threadIdx.x & 31;
+    const int own = __popcll(lm);
+    int inc = own;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += y;
     }
-    const int32_t wtotal = __shfl_sync(0xffffffffu, inc, 31);
-    s_lm[threadIdx.x] = lm;
-    s_pre[threadIdx.x] = inc - own;
-    __syncwarp();
-    for (int32_t k = lane; k < wtotal; k += 32) {
-        int lo = 0, hi = 31;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_pre[wbase + mid] <= k) lo = mid;
-            else hi = mid - 1;
-        }
-        const int bit = __fns(s_lm[wbase + lo], 0, k - s_pre[wbase + lo] + 1);
-        const int p = (wbase + lo) * LS_ITEMS + bit;  // position in the tile
-        int64_t pr;
-        s_mask[p] = (uint8_t)kept_roles_of<TS, DIR>(tri[base + p], ends, delta, pr);
-        s_cost[p] = (int32_t)pr;
+    pre = inc - own;
+    return __shfl_sync(0xffffffffu, inc, 31);
+}
+
+// Position within the warp's range of candidate k (< the warp's total): the lane l with
+// pre[l] <= k < pre[l + 1], and the (k - pre[l])-th set bit of its mask. The whole warp
+// must call it.
+__device__ __forceinline__ int candidate_at(int k, uint64_t lm, int pre) {
+    int l = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int pc = __shfl_sync(0xffffffffu, pre, l + step);
+        if (pc <= k) l += step;
     }
-    __syncwarp();
-    const int32_t c = own;
-    int64_t cs = 0;
-    for (uint32_t x = lm; x; x &= x - 1) cs += (int64_t)s_cost[threadIdx.x * LS_ITEMS + __ffs(x) - 1] + LIVE_IDLE;
-    // ---- block scans, look-backs
-    const int32_t offc = block_exclusive_sum<int32_t>(c, wc, &totc);
-    const int64_t offp = block_exclusive_sum<int64_t>(cs, wp, &totp);
-    if (threadIdx.x < 32) {
-        volatile unsigned long long* vc = lbc;
-        volatile unsigned long long* vp = lbp;
-        const unsigned long long tc = (unsigned long long)totc, tp = (unsigned long long)totp;
-        if (tile == 0) {
-            if (threadIdx.x == 0) {
-                vc[0] = SC_PREFIX | tc;
-                vp[0] = SC_PREFIX | tp;
-                s_exc = 0;
-                s_exp = 0;
-            }
-        } else {
-            if (threadIdx.x == 0) {
-                vc[tile] = SC_AGG | tc;
-                vp[tile] = SC_AGG | tp;
-            }
-            const unsigned long long ec = warp_lookback(vc, tile, tc, err);
-            const unsigned long long ep = warp_lookback(vp, tile, tp, err);
-            if (threadIdx.x == 0) {
-                s_exc = ec;
-                s_exp = ep;
-            }
+    const uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)lm, l);
+    const uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)(lm >> 32), l);
+    const int n = k - __shfl_sync(0xffffffffu, pre, l);  // 0-based rank among l's candidates
+    const int plo = __popc(lo);
+    const int bit = n < plo ? __fns(lo, 0, n + 1) : 32 + __fns(hi, 0, n - plo + 1);
+    return l * LS_ITEMS + bit;
+}
+
+// Per warp: its kept triangles and their total cost.
+template <typename TS, int DIR>
+__global__ void __launch_bounds__(LS_THREADS) k_live_sums(const uint8_t* __restrict__ tlive,
+                                                          const int4* __restrict__ tri,
+                                                          const RunEnds<TS>* __restrict__ ends, int64_t ntri,
+                                                          int64_t delta, const int64_t* __restrict__ qp,
+                                                          int32_t* __restrict__ wcnt, int64_t* __restrict__ wcost) {
+    if (qp) delta = qp[0];  // the window from a device parameter block (replayed query plans)
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * LS_THREADS + threadIdx.x) >> 5;
+    const int64_t tw = w * LS_WARP;
+    const uint64_t lm = live_mask(tlive, tw + (int64_t)lane * LS_ITEMS, ntri, delta);
+    int pre;
+    const int total = warp_candidates(lm, pre);
+    int64_t cost = 0;
+    for (int k0 = 0; k0 < total; k0 += 32) {
+        const int k = k0 + lane;
+        const int at = candidate_at(min(k, total - 1), lm, pre);
+        if (k < total) {
+            int64_t pr;
+            kept_roles_of<TS, DIR>(tri[tw + at], ends, delta, pr);
+            cost += pr + LIVE_IDLE;
         }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cost += __shfl_xor_sync(0xffffffffu, cost, o);
+    if (lane == 0) {
+        wcnt[w] = total;
+        wcost[w] = cost;
+    }
+}
+
+// One block: the warps' counts and costs become exclusive prefixes in place; the totals,
+// the end of loff and of the tile map, and the kept triangles' model bytes.
+template <typename TS>
+__global__ void __launch_bounds__(1024) k_live_offsets(int32_t* __restrict__ wcnt, int64_t* __restrict__ wcost,
+                                                       int64_t nw, int64_t* __restrict__ totals,
+                                                       int64_t* __restrict__ loff, int64_t* __restrict__ ltile,
+                                                       int64_t max_tiles, int64_t ptile,
+                                                       unsigned long long* __restrict__ prof) {
+    __shared__ int64_t sc[32], sp[32];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int64_t per = (nw + 1023) / 1024;
+    const int64_t b = (int64_t)threadIdx.x * per, e = min(b + per, nw);
+    int64_t c = 0, p = 0;
+    for (int64_t i = b; i < e; i++) {
+        c += wcnt[i];
+        p += wcost[i];
+    }
+    int64_t ic = c, ip = p;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t yc = __shfl_up_sync(0xffffffffu, ic, o), yp = __shfl_up_sync(0xffffffffu, ip, o);
+        if (lane >= o) {
+            ic += yc;
+            ip += yp;
+        }
+    }
+    if (lane == 31) {
+        sc[wi] = ic;
+        sp[wi] = ip;
     }
     __syncthreads();
-    // ---- the kept triangles of this thread's run
-    int64_t jc = (int64_t)s_exc + offc, jp = (int64_t)s_exp + offp;
-    for (uint32_t x = lm; x; x &= x - 1) {
-        const int i = __ffs(x) - 1;
-        const int64_t t = t0 + i;
-        const int64_t v = (int64_t)s_cost[threadIdx.x * LS_ITEMS + i] + LIVE_IDLE;
-        L[jc] = (int32_t)t;
-        loff[jc] = jp;
-        lmask[jc] = s_mask[threadIdx.x * LS_ITEMS + i];
-        for (int64_t b = (jp + ptile - 1) / ptile; b * ptile < jp + v && b <= max_tiles; b++) ltile[b] = jc;
-        jc++;
-        jp += v;
+    if (wi == 0) {
+        int64_t xc = sc[lane], xp = sp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t yc = __shfl_up_sync(0xffffffffu, xc, o), yp = __shfl_up_sync(0xffffffffu, xp, o);
+            if (lane >= o) {
+                xc += yc;
+                xp += yp;
+            }
+        }
+        sc[lane] = xc;  // inclusive over warps
+        sp[lane] = xp;
     }
-    if (base + LS_TILE >= ntri && threadIdx.x == 0) {
-        const int64_t nl = (int64_t)s_exc + totc, P = (int64_t)s_exp + totp;
+    __syncthreads();
+    int64_t oc = ic - c + (wi ? sc[wi - 1] : 0), op = ip - p + (wi ? sp[wi - 1] : 0);
+    for (int64_t i = b; i < e; i++) {
+        const int32_t x = wcnt[i];
+        const int64_t y = wcost[i];
+        wcnt[i] = (int32_t)oc;
+        wcost[i] = op;
+        oc += x;
+        op += y;
+    }
+    if (threadIdx.x == 0) {
+        const int64_t nl = sc[31], P = sp[31];
         totals[0] = nl;
         totals[1] = P;
         loff[nl] = P;
@@ -220,6 +255,54 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_live_select(const uint8_t* __r
     }
 }
 
+// Per warp: its kept triangles at their prefixes, with their masks, first slots and tile
+// starts.
+template <typename TS, int DIR>
+__global__ void __launch_bounds__(LS_THREADS) k_live_write(const uint8_t* __restrict__ tlive,
+                                                           const int4* __restrict__ tri,
+                                                           const RunEnds<TS>* __restrict__ ends, int64_t ntri,
+                                                           int64_t delta, const int64_t* __restrict__ qp,
+                                                           const int32_t* __restrict__ woffc,
+                                                           const int64_t* __restrict__ woffp, int32_t* __restrict__ L,
+                                                           int64_t* __restrict__ loff, uint8_t* __restrict__ lmask,
+                                                           int64_t* __restrict__ ltile, int64_t max_tiles,
+                                                           int64_t ptile) {
+    if (qp) delta = qp[0];
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * LS_THREADS + threadIdx.x) >> 5;
+    const int64_t tw = w * LS_WARP;
+    const uint64_t lm = live_mask(tlive, tw + (int64_t)lane * LS_ITEMS, ntri, delta);
+    int pre;
+    const int total = warp_candidates(lm, pre);
+    if (total == 0) return;  // warp-uniform
+    const int64_t bc = woffc[w];
+    int64_t run = woffp[w];
+    for (int k0 = 0; k0 < total; k0 += 32) {
+        const int k = k0 + lane;
+        const int at = candidate_at(min(k, total - 1), lm, pre);
+        int m = 0;
+        int64_t v = 0;
+        if (k < total) {
+            int64_t pr;
+            m = kept_roles_of<TS, DIR>(tri[tw + at], ends, delta, pr);
+            v = pr + LIVE_IDLE;
+        }
+        int64_t inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (k < total) {
+            const int64_t jc = bc + k, jp = run + inc - v;
+            L[jc] = (int32_t)(tw + at);
+            loff[jc] = jp;
+            lmask[jc] = (uint8_t)m;
+            for (int64_t b = (jp + ptile - 1) / ptile; b * ptile < jp + v && b <= max_tiles; b++) ltile[b] = jc;
+        }
+        run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+}
 
 // Model bytes of a staged triangle's kept roles (its first slot lies in this tile):
 // staging 61 B, and per role w sigma1 + w min(sigma2, sigma1 ceil(log2(sigma2 + 1))) + the
@@ -311,31 +394,27 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS*
         }
         __syncthreads();
         const int32_t count = (int32_t)min((int64_t)TILE, P - p0);
-        // ITEMS consecutive slots per thread: consecutive slots of one role probe
-        // consecutive entries t of its sorted L1, so the answers t2 and t3 only move
-        // forward in L2 and L3 and each search gallops on from where the last one ended
-        const int32_t l0 = (int32_t)threadIdx.x * ITEMS;
-        if (l0 >= count) continue;
-        int j = 0;
-        {
-            int lo = 0, hi = st.nt - 1;  // the last staged triangle starting at or before l0
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (st.base[mid] <= l0) lo = mid;
-                else hi = mid - 1;
-            }
-            j = lo;
-        }
-        int cur = -1;  // role of the pointers below (-1: none yet)
-        int32_t q2a = 0, q2b = 0, q3a = 0, q3b = 0;  // lower bounds of the searches in L2, L3 runs
 #pragma unroll 1
-        for (int k = 0; k < ITEMS; k++) {
-            const int32_t local = l0 + k;
-            if (local >= count) break;
-            while (st.base[j + 1] <= local) {
-                j++;
-                cur = -1;
+        for (int it = 0; it < ITEMS; it++) {
+            const int32_t local = it * PB_THREADS + (int32_t)threadIdx.x;
+            if ((local & ~31) >= count) break;  // warp-uniform
+            bool active = local < count;
+            // triangle of the slot: one lane bisects for the warp, lanes walk forward
+            const int lane = threadIdx.x & 31;
+            const int32_t first = __shfl_sync(0xffffffffu, local, 0);
+            int j0 = 0;
+            if (lane == 0) {
+                int lo = 0, hi = st.nt - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (st.base[mid] <= first) lo = mid;
+                    else hi = mid - 1;
+                }
+                j0 = lo;
             }
+            int j = __shfl_sync(0xffffffffu, j0, 0);
+            if (!active) continue;
+            while (st.base[j + 1] <= local) j++;
             int32_t o = local - st.base[j] - LIVE_IDLE;
             if (o < 0) continue;  // idle slot
             const int32_t* off = st.off[j];
@@ -348,50 +427,11 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe_live(LiveArgs a, const TS*
                 o -= s1;
             }
             if (r == 6) continue;  // cannot happen: o < the kept roles' total
-            const int code = (int)((st.desc[j] >> (6 * r)) & 63);
-            const int c2 = code & 7, c3 = code >> 3;
-            const int o2 = 3 * (c2 >> 1) + (c2 & 1), o3 = 3 * (c3 >> 1) + (c3 & 1);
-            if (r != cur) {
-                cur = r;
-                q2a = off[o2];
-                q2b = off[o2 + 1];
-                q3a = off[o3];
-                q3b = off[o3 + 1];
-            }
             const int32_t pos = off[3 * (r >> 1) + (r & 1)] + o;
+            const int code = (int)((st.desc[j] >> (6 * r)) & 63);
             const TS t = T[pos];
-            // Theorem 3.1: t2 = first entry >= t of L2, t3 = first entry >= t2 of L3 (the
-            // union of both directions' runs for "either"); a run whose first entry is
-            // already beyond t + delta is not searched
-            const TS NONE = TsNone<TS>::value;
-            TS t2 = NONE;
-            {
-                const int32_t b = off[o2], e = off[o2 + 1];
-                if (b < e && !(T[b] > t && beyond(T[b], t, delta))) {
-                    q2a = gallop_at_least<TS>(T, q2a, e, t);
-                    if (q2a < e) t2 = T[q2a];
-                }
-            }
-            if (DIR == FOLTY_DIR_EITHER) {
-                const int32_t b = off[o2 + 1], e = off[o2 + 2];
-                if (b < e && !(T[b] > t && beyond(T[b], t, delta))) {
-                    q2b = gallop_at_least<TS>(T, q2b, e, t);
-                    if (q2b < e && T[q2b] < t2) t2 = T[q2b];
-                }
-            }
-            if (t2 == NONE || beyond(t2, t, delta)) continue;
-            TS t3 = NONE;
-            {
-                const int32_t e = off[o3 + 1];
-                q3a = gallop_at_least<TS>(T, q3a, e, t2);
-                if (q3a < e) t3 = T[q3a];
-            }
-            if (DIR == FOLTY_DIR_EITHER) {
-                const int32_t e = off[o3 + 2];
-                q3b = gallop_at_least<TS>(T, q3b, e, t2);
-                if (q3b < e && T[q3b] < t3) t3 = T[q3b];
-            }
-            if (t3 == NONE) continue;
+            const TS t3 = probe_window<TS, DIR>(T, off, code & 7, code >> 3, t, delta);
+            if (t3 == TsNone<TS>::value) continue;
             const TS gap = (TS)(t3 - t);
             if (gap > delta) continue;
             if (MODE == 0) {
@@ -483,22 +523,31 @@ static void launch_live_t(const folty_graph* g, int dir, const LiveArgs& la, TS 
 }
 
 template <typename TS>
-static void launch_select_t(const folty_graph* g, int dir, const uint8_t* tl, int64_t delta, int* err,
-                            const ProbeBuffers& ls, unsigned long long* prof, const int64_t* qp, cudaStream_t s) {
+static void launch_select_t(const folty_graph* g, int dir, const uint8_t* tl, int64_t delta, const ProbeBuffers& ls,
+                            unsigned long long* prof, const int64_t* qp, cudaStream_t s) {
     const RunEnds<TS>* ends = static_cast<const RunEnds<TS>*>(g->run_ends);
-    const int64_t ntri = g->ntri, stiles = ls.stiles;
+    const int64_t ntri = g->ntri;
     const int64_t tile = (int64_t)PB_THREADS * g->tune.probe_items;
-    unsigned long long* lsctl = ls.lsctl;
-#define FOLTY_SELECT_ARGS                                                                                          \
-    tl, g->tri, ends, ntri, delta, lsctl + 1, lsctl + 1 + stiles, (unsigned int*)lsctl, err, ls.L, ls.loff, ls.lmask, \
-        ls.totals, ls.ltile, ls.max_tiles, tile, prof, qp
+    const unsigned blocks = (unsigned)((ntri + LS_BLOCK - 1) / LS_BLOCK);
+#define FOLTY_SUMS_ARGS tl, g->tri, ends, ntri, delta, qp, ls.wcnt, ls.wcost
+#define FOLTY_WRITE_ARGS \
+    tl, g->tri, ends, ntri, delta, qp, ls.wcnt, ls.wcost, ls.L, ls.loff, ls.lmask, ls.ltile, ls.max_tiles, tile
     if (dir == FOLTY_DIR_OUT)
-        FOLTY_LAUNCH((k_live_select<TS, FOLTY_DIR_OUT>), (unsigned)stiles, SCAN_THREADS, 0, s, FOLTY_SELECT_ARGS);
+        FOLTY_LAUNCH((k_live_sums<TS, FOLTY_DIR_OUT>), blocks, LS_THREADS, 0, s, FOLTY_SUMS_ARGS);
     else if (dir == FOLTY_DIR_IN)
-        FOLTY_LAUNCH((k_live_select<TS, FOLTY_DIR_IN>), (unsigned)stiles, SCAN_THREADS, 0, s, FOLTY_SELECT_ARGS);
+        FOLTY_LAUNCH((k_live_sums<TS, FOLTY_DIR_IN>), blocks, LS_THREADS, 0, s, FOLTY_SUMS_ARGS);
     else
-        FOLTY_LAUNCH((k_live_select<TS, FOLTY_DIR_EITHER>), (unsigned)stiles, SCAN_THREADS, 0, s, FOLTY_SELECT_ARGS);
-#undef FOLTY_SELECT_ARGS
+        FOLTY_LAUNCH((k_live_sums<TS, FOLTY_DIR_EITHER>), blocks, LS_THREADS, 0, s, FOLTY_SUMS_ARGS);
+    FOLTY_LAUNCH(k_live_offsets<TS>, 1, 1024, 0, s, ls.wcnt, ls.wcost, ls.nw, ls.totals, ls.loff, ls.ltile,
+                 ls.max_tiles, tile, prof);
+    if (dir == FOLTY_DIR_OUT)
+        FOLTY_LAUNCH((k_live_write<TS, FOLTY_DIR_OUT>), blocks, LS_THREADS, 0, s, FOLTY_WRITE_ARGS);
+    else if (dir == FOLTY_DIR_IN)
+        FOLTY_LAUNCH((k_live_write<TS, FOLTY_DIR_IN>), blocks, LS_THREADS, 0, s, FOLTY_WRITE_ARGS);
+    else
+        FOLTY_LAUNCH((k_live_write<TS, FOLTY_DIR_EITHER>), blocks, LS_THREADS, 0, s, FOLTY_WRITE_ARGS);
+#undef FOLTY_SUMS_ARGS
+#undef FOLTY_WRITE_ARGS
 }
 
 // Buffers of one selection: from a call's scratch, or owned by the graph. The tile map
@@ -515,8 +564,9 @@ static ProbeBuffers make_probe_buffers(const folty_graph* g, A&& get) {
     ls.totals = get((int64_t*)nullptr, 2);
     ls.max_tiles = (g->info.probes + LIVE_IDLE * ntri + PB_TILE_MIN - 1) / PB_TILE_MIN;
     ls.ltile = get((int64_t*)nullptr, ls.max_tiles + 2);
-    ls.stiles = (ntri + LS_TILE - 1) / LS_TILE;
-    ls.lsctl = get((unsigned long long*)nullptr, 2 * ls.stiles + 1);  // tile counter, two look-backs
+    ls.nw = (ntri + LS_BLOCK - 1) / LS_BLOCK * (LS_THREADS / 32);  // the selection's warps
+    ls.wcnt = get((int32_t*)nullptr, ls.nw + 1);
+    ls.wcost = get((int64_t*)nullptr, ls.nw + 1);
     return ls;
 }
 
@@ -530,11 +580,11 @@ ProbeBuffers probe_buffers(folty_graph* g, cudaStream_t s) {
 // receives the selection's model bytes beyond its one byte per triangle.
 static void enqueue_select(folty_graph* g, int64_t delta, int dir, const ProbeBuffers& ls, int* err,
                            unsigned long long* prof_sel, const int64_t* qp, cudaStream_t s) {
+    (void)err;  // no waits: the selection cannot run out of time
     StageSpan span(ST_SELECT, s, g->ntri, prof_sel);
-    FOLTY_CUDA(cudaMemsetAsync(ls.lsctl, 0, sizeof(unsigned long long) * (size_t)(2 * ls.stiles + 1), s));
     const uint8_t* tl = g->tlive + (int64_t)dir * g->tlive_stride;
-    if (g->ts32) launch_select_t<uint32_t>(g, dir, tl, delta, err, ls, prof_sel, qp, s);
-    else launch_select_t<int64_t>(g, dir, tl, delta, err, ls, prof_sel, qp, s);
+    if (g->ts32) launch_select_t<uint32_t>(g, dir, tl, delta, ls, prof_sel, qp, s);
+    else launch_select_t<int64_t>(g, dir, tl, delta, ls, prof_sel, qp, s);
 }
 
 static ProbeBuffers select_live(folty_graph* g, int64_t delta, int dir, Scratch& sc, cudaStream_t s,

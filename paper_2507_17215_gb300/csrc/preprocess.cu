@@ -999,8 +999,12 @@ struct TailArgs {
     int32_t* slist;
     int32_t* sdeg;
     int32_t* map2;
+    // decrements of a heavy round, by owner and slot (owner * TAIL_OWN + slot), zero
+    // between rounds
+    int32_t* dec;
 };
 
+constexpr int TAIL_AGG_MIN = 128;  // frontier size from which a round's decrements go through L2
 constexpr int TAIL_SHORT = 32;   // rows up to this length: one thread, TAIL_CHUNK loads at a time
 constexpr int TAIL_CHUNK = 8;
 constexpr int TAIL_LIGHT = 256;  // rows up to this length: one warp, all loads in flight at once
@@ -1021,7 +1025,8 @@ struct TailShared {
     int cntL[3], cntH[2], smin[2];
     int acnt[2];                 // owned vertices alive at the level start, by level parity
     int adeg[2];                 // their degree sum (twice the edges left), by level parity
-    int bc[2][4];                // cluster-wide values, published by tail_gather
+    int made[2];                 // crossings this CTA filed (anywhere) in a round, by round parity
+    int slots[2][C][4];          // every CTA's values of one cluster barrier, by barrier parity
 };
 
 // Neighbours vv[0..N) (negative: none) lose one degree each in round r at level k: all N
@@ -1029,7 +1034,17 @@ struct TailShared {
 // its vertex in the owner's frontier of round r + 1.
 template <int C, int N>
 __device__ __forceinline__ void tail_decrement(TailShared<C>& sh, cg::cluster_group& cl, const int (&vv)[N], int k,
-                                               int r) {
+                                               int r, int32_t* __restrict__ dec) {
+    if (dec) {
+        // a heavy round: many frontier rows share their targets, and one shared-memory
+        // atomic of the target's owner per decrement would queue at that SM; the
+        // decrements add up in L2 instead, and each owner applies its own after the
+        // round's barrier
+#pragma unroll
+        for (int t = 0; t < N; t++)
+            if (vv[t] >= 0) atomicAdd(&dec[(vv[t] % C) * TAIL_OWN + vv[t] / C], 1);
+        return;
+    }
     int old[N];
 #pragma unroll
     for (int t = 0; t < N; t++)
@@ -1040,41 +1055,43 @@ __device__ __forceinline__ void tail_decrement(TailShared<C>& sh, cg::cluster_gr
             TailShared<C>* p = cl.map_shared_rank(&sh, vv[t] % C);
             const int at = atomicAdd(&p->cntL[(r + 1) % 3], 1);
             p->FL[(r + 1) & 1][at] = (uint16_t)(vv[t] / C);
+            atomicAdd(&sh.made[r & 1], 1);
         }
     }
 }
 
-// Cluster-wide frontier size of round t, minimum of the level minima smin[p], sum of
-// the alive counts acnt[p] and of their degrees adeg[p]: warp 0 reads every CTA's values (lane c reads CTA c) and
-// publishes them in this CTA's shared memory slot s (callers alternate s, so that a slot
-// is rewritten only after a barrier that follows every read of it). The whole CTA must
-// call it; every CTA gets the same values when no CTA appends to slot t % 3 or changes
-// smin[p] or acnt[p] meanwhile.
+// Publishes this CTA's values v of the next cluster barrier (number s) in every CTA's
+// slot s & 1 (threads 0..C-1 each write one CTA's copy); after the barrier, tail_totals
+// combines the C copies from this CTA's own shared memory, without a remote read after
+// the barrier. A slot is rewritten two barriers later, after every CTA has read it. The
+// values must be final (the caller's __syncthreads) before the call.
 template <int C>
-__device__ __forceinline__ int4 tail_gather(TailShared<C>& sh, cg::cluster_group& cl, int t, int p, int s) {
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        int v = 0, m = INT_MAX, al = 0, ad = 0;
-        if (lane < C) {
-            const TailShared<C>* q = cl.map_shared_rank(&sh, lane);
-            v = q->cntL[t % 3];
-            m = q->smin[p];
-            al = q->acnt[p];
-            ad = q->adeg[p];
-        }
-        v = __reduce_add_sync(0xffffffffu, v);
-        m = __reduce_min_sync(0xffffffffu, m);
-        al = __reduce_add_sync(0xffffffffu, al);
-        ad = __reduce_add_sync(0xffffffffu, ad);
-        if (lane == 0) {
-            sh.bc[s][0] = v;
-            sh.bc[s][1] = m;
-            sh.bc[s][2] = al;
-            sh.bc[s][3] = ad;
-        }
+__device__ __forceinline__ void tail_publish(TailShared<C>& sh, cg::cluster_group& cl, int s, int4 v) {
+    if (threadIdx.x < C) {
+        TailShared<C>* q = cl.map_shared_rank(&sh, (int)threadIdx.x);
+        int* d = q->slots[s & 1][cl.block_rank()];
+        d[0] = v.x;
+        d[1] = v.y;
+        d[2] = v.z;
+        d[3] = v.w;
     }
-    __syncthreads();
-    return make_int4(sh.bc[s][0], sh.bc[s][1], sh.bc[s][2], sh.bc[s][3]);
+}
+
+// After the barrier: the sums of the C copies' x, z, w and the minimum of their y (each
+// warp reduces them for itself).
+template <int C>
+__device__ __forceinline__ int4 tail_totals(const TailShared<C>& sh, int s) {
+    const int lane = threadIdx.x & 31;
+    int x = 0, y = INT_MAX, z = 0, w = 0;
+    if (lane < C) {
+        const int* d = sh.slots[s & 1][lane];
+        x = d[0];
+        y = d[1];
+        z = d[2];
+        w = d[3];
+    }
+    return make_int4(__reduce_add_sync(0xffffffffu, x), __reduce_min_sync(0xffffffffu, y),
+                     __reduce_add_sync(0xffffffffu, z), __reduce_add_sync(0xffffffffu, w));
 }
 
 // The same peeling as k_peel (levels, rounds, k + 1 -> k crossings), on the local
@@ -1115,6 +1132,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
         sh.smin[tid] = INT_MAX;
         sh.acnt[tid] = 0;
         sh.adeg[tid] = 0;
+        sh.made[tid] = 0;
     }
     int k = a.ctl[C_TAIL_K], r = a.ctl[C_TAIL_R], rounds = a.ctl[C_ROUNDS], lvl = 0, gs = 0;
     bool handed = false;
@@ -1124,6 +1142,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
         if (tid == 0) {
             sh.cntL[(r + 2) % 3] = 0;
             sh.cntH[(r + 1) & 1] = 0;
+            sh.made[0] = sh.made[1] = 0;  // no crossings are filed before the next round
             sh.smin[(lvl + 1) & 1] = INT_MAX;
             sh.acnt[(lvl + 1) & 1] = 0;
             sh.adeg[(lvl + 1) & 1] = 0;
@@ -1155,8 +1174,11 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
         }
         lmin = __reduce_min_sync(0xffffffffu, lmin);
         if (lane == 0 && lmin != INT_MAX) atomicMin(&sh.smin[lvl & 1], lmin);
+        __syncthreads();  // the level start's own filings, minimum and sums are final
+        tail_publish(sh, cl, gs,
+                     make_int4(sh.cntL[(r + 1) % 3], sh.smin[lvl & 1], sh.acnt[lvl & 1], sh.adeg[lvl & 1]));
         cl.sync();
-        const int4 g = tail_gather(sh, cl, r + 1, lvl & 1, gs++ & 1);
+        const int4 g = tail_totals(sh, gs++);
         // the single CTA takes over once few vertices and few edges are left (dense
         // remainders, such as planted communities, keep the cluster's sixteen SMs)
         if (g.z > 0 && g.z <= a.solo_cap && g.w <= SOLO_DEG_CAP) {
@@ -1197,7 +1219,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
         if (total == 0) {
             if (g.y == INT_MAX) break;  // nothing left anywhere
             kk = g.y;                   // jump to the smallest remaining degree
-            cl.sync();                  // every CTA has read the empty totals before appends resume
+            cl.sync();  // every CTA has read the empty totals before appends resume
             for (int q0 = 0; q0 < OWN; q0 += TAIL_THREADS) {
                 const int q = q0 + tid;
                 bool rem = false;
@@ -1222,9 +1244,11 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
         // ---- rounds at level k
         while (total > 0) {
             const int nL = sh.cntL[r % 3];
+            int32_t* const rdec = total >= TAIL_AGG_MIN ? a.dec : nullptr;  // the same in every CTA
             if (tid == 0) {
                 sh.cntL[(r + 2) % 3] = 0;
                 sh.cntH[(r + 1) & 1] = 0;  // read in round r + 1, after this round's barriers
+                sh.made[(r + 1) & 1] = 0;
             }
             // one pass, up to 32 frontier vertices per warp, dealt round-robin over the warps
             // (a small frontier spreads one vertex per warp): round and core number; a short
@@ -1241,7 +1265,11 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
                     a.rnd[sh.oL[q]] = r;
                     a.core[sh.oL[q]] = k;
                 }
-                const bool shortrow = have && e - b <= TAIL_SHORT;
+                // a short row is walked by its own lane (TAIL_CHUNK loads at a time) when the
+                // frontier gives every warp several rows, or when it takes one step anyway;
+                // in a small frontier the whole warp walks it in one step
+                const bool lanewalk = nL > 4 * NW || e - b <= TAIL_CHUNK;
+                const bool shortrow = have && e - b <= TAIL_SHORT && lanewalk;
                 bool medium = have && !shortrow;
                 if (have && e - b > TAIL_LIGHT) {
                     const int h = atomicAdd(&sh.cntH[r & 1], 1);
@@ -1255,7 +1283,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
                         int vv[TAIL_CHUNK];
 #pragma unroll
                         for (int t = 0; t < TAIL_CHUNK; t++) vv[t] = (j0 + t < e) ? (int)a.ladj[j0 + t] : -1;
-                        tail_decrement<C>(sh, cl, vv, k, r);
+                        tail_decrement<C>(sh, cl, vv, k, r, rdec);
                     }
                 }
                 unsigned mm = __ballot_sync(0xffffffffu, medium);
@@ -1270,7 +1298,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
                             const int j = j0 + t * 32 + lane;
                             vv[t] = (j < ee) ? (int)a.ladj[j] : -1;
                         }
-                        tail_decrement<C>(sh, cl, vv, k, r);
+                        tail_decrement<C>(sh, cl, vv, k, r, rdec);
                     }
                 }
             }
@@ -1287,13 +1315,45 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(TailArgs a) {
                         const int j = j0 + t * TAIL_THREADS + tid;
                         vv[t] = (j < e) ? (int)a.ladj[j] : -1;
                     }
-                    tail_decrement<C>(sh, cl, vv, k, r);
+                    tail_decrement<C>(sh, cl, vv, k, r, rdec);
                 }
             }
+            if (rdec) {
+                // every CTA's decrements are in L2: each owner applies its own, and files the
+                // vertices that crossed k + 1 -> k (the sum may cross in one step)
+                cl.sync();
+                for (int q0 = 0; q0 < OWN; q0 += TAIL_THREADS) {
+                    const int q = q0 + tid;
+                    bool cross = false;
+                    if (q < OWN && q * C + rank < nl) {
+                        int32_t* dp = rdec + rank * TAIL_OWN + q;
+                        const int d = __ldcg(dp);
+                        if (d) {
+                            *dp = 0;
+                            const int old = sh.odeg[q];
+                            sh.odeg[q] = old - d;
+                            cross = old > k && old - d <= k;
+                        }
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, cross);
+                    if (m) {
+                        const int leader = __ffs(m) - 1;
+                        int base = 0;
+                        if (lane == leader) {
+                            base = atomicAdd(&sh.cntL[(r + 1) % 3], __popc(m));
+                            atomicAdd(&sh.made[r & 1], __popc(m));
+                        }
+                        base = __shfl_sync(0xffffffffu, base, leader);
+                        if (cross) sh.FL[(r + 1) & 1][base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)q;
+                    }
+                }
+            }
+            __syncthreads();  // this CTA's crossings of the round are counted
+            tail_publish(sh, cl, gs, make_int4(sh.made[r & 1], INT_MAX, 0, 0));
             cl.sync();
             r++;
             rounds++;
-            total = tail_gather(sh, cl, r, 0, gs++ & 1).x;
+            total = tail_totals(sh, gs++).x;
         }
         lvl++;
     }
@@ -1998,73 +2058,96 @@ __global__ void k_outptr(const int32_t* __restrict__ rowptr, const int32_t* __re
 
 // Thread per oriented edge (u, v): merge N+(u) and N+(v) (both ascending by id).
 // Triangles of oriented edge u -> v: the common out-neighbours w of u and v (both lists
-// sorted). A light edge is merged by one thread; the lists of a heavy edge
-// (|out(u)| + |out(v)| > heavy_min, the degeneracy core) are intersected by the whole
-// warp: out(v) is staged in shared memory with its entries' edge ids and temporal edge
-// counts, and every lane binary-searches its share of out(u) in it, the loads of its next
-// share issued before the search, so that a hit needs no further global load. Both
-// passes find the same set, so the counts match the writes.
+// sorted). A light edge is merged by one thread; a heavy edge (|out(u)| + |out(v)| >
+// heavy_min, the degeneracy core) is intersected by the whole warp: out(u) goes into an
+// open-addressed hash table in the warp's shared memory, with each entry's edge id and
+// temporal edge count (built once for the consecutive edges of u the warp meets), and the
+// lanes look up their share of out(v), the loads of the next share issued before the
+// lookups. Both passes find the same set, so the counts match the writes.
 constexpr int TRI_THREADS = 256;
 constexpr int TRI_HEAVY = 48;
-constexpr int TRI_STAGE = 256;  // staged out-list entries per warp (longer lists are merged by one lane)
+constexpr int TRI_HCAP = 256;    // out(u) entries a warp's table holds (longer lists: one lane merges)
+constexpr int TRI_HSLOTS = 512;  // table slots (load at most one half)
 
-// One warp's staged out(v): neighbour ids, and per entry the static edge id and its
-// temporal edge count.
-struct TriStageW {
-    int32_t nbr[TRI_STAGE];
-    int32_t sig[TRI_STAGE];
-    int32_t eid[TRI_STAGE];
+// One warp's hash table of out(u): neighbour id per slot (-1: empty) and its position in
+// out(u); by position, the static edge id and temporal edge count of (u, w).
+struct TriHashW {
+    int32_t key[TRI_HSLOTS];
+    int16_t pos[TRI_HSLOTS];
+    int32_t sig[TRI_HCAP];
+    int32_t eid[TRI_HCAP];
 };
 
-// Lane-parallel intersection of out(u) = [i1, e1) with out(v) = [i2, e2) (e2 - i2 <=
-// TRI_STAGE) of the out-lists (nbr, osig and, when EID, eid by position). Calls
-// hit(ia, pos, w, sig_u, eid_u, sig_v, eid_v) once per lane and step: ia the lane's
-// position in out(u), pos the matching position in out(v) or -1, w = nbr[ia], and the
-// edge counts and (EID) ids of the static edges (u, w) and (v, w) when pos >= 0. The whole
-// warp must call it.
-template <bool EID, typename F>
-__device__ __forceinline__ void warp_intersect(const int32_t* __restrict__ nbr, const int32_t* __restrict__ osig,
-                                               const int32_t* __restrict__ eid, int32_t i1, int32_t e1, int32_t i2,
-                                               int32_t e2, TriStageW& st, F&& hit) {
+__device__ __forceinline__ uint32_t tri_hash(int32_t w) { return ((uint32_t)w * 0x9E3779B1u) >> 23; }
+
+// Builds the warp's table of out(u) = [i1, e1) (e1 - i1 <= TRI_HCAP). The whole warp
+// must call it. With at most TRI_HCAP keys in TRI_HSLOTS slots every probe sequence ends.
+template <bool EID>
+__device__ __forceinline__ void warp_hash_out(const int32_t* __restrict__ nbr, const int32_t* __restrict__ osig,
+                                              const int32_t* __restrict__ eid, int32_t i1, int32_t e1,
+                                              TriHashW& H) {
     const int lane = threadIdx.x & 31;
-    const int nb = e2 - i2;
-    for (int t = lane; t < nb; t += 32) {
-        st.nbr[t] = nbr[i2 + t];
-        st.sig[t] = osig[i2 + t];
-        if (EID) st.eid[t] = eid[i2 + t];
-    }
-    int32_t x = 0, su = 0, eu = 0;
-    if (i1 + lane < e1) {
-        x = nbr[i1 + lane];
-        su = osig[i1 + lane];
-        if (EID) eu = eid[i1 + lane];
-    }
+    __syncwarp();  // the previous table's lookups are done
+    for (int t = lane; t < TRI_HSLOTS; t += 32) H.key[t] = -1;
     __syncwarp();
-    for (int32_t ia0 = i1; ia0 < e1; ia0 += 32) {
-        const int32_t ia = ia0 + lane;
-        // the next share's loads, in flight during this share's search
-        int32_t xn = 0, sn = 0, en = 0;
-        if (ia + 32 < e1) {
-            xn = nbr[ia + 32];
-            sn = osig[ia + 32];
-            if (EID) en = eid[ia + 32];
-        }
-        int pos = -1;
-        if (ia < e1) {
-            int lo = 0, hi = nb;  // first staged entry >= x
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (st.nbr[mid] < x) lo = mid + 1;
-                else hi = mid;
+    for (int t = lane; t < e1 - i1; t += 32) {
+        const int32_t w = nbr[i1 + t];
+        H.sig[t] = osig[i1 + t];
+        if (EID) H.eid[t] = eid[i1 + t];
+        uint32_t h = tri_hash(w);
+        for (int p = 0; p < TRI_HSLOTS; p++) {
+            if (atomicCAS(&H.key[h], -1, w) == -1) {
+                H.pos[h] = (int16_t)t;
+                break;
             }
-            if (lo < nb && st.nbr[lo] == x) pos = lo;
+            h = (h + 1) & (TRI_HSLOTS - 1);
         }
-        hit(ia, pos, x, su, eu, pos >= 0 ? st.sig[pos] : 0, (EID && pos >= 0) ? st.eid[pos] : 0);
-        x = xn;
-        su = sn;
-        eu = en;
     }
     __syncwarp();
+}
+
+// Looks up out(v) = [i2, e2) of the out-lists (nbr, osig and, when EID, eid by position)
+// in the warp's table of out(u). Calls hit(found, w, sig_u, eid_u, sig_v, eid_v) once per
+// lane and step (w = -1 for an idle lane): the counts and (EID) ids of the static edges
+// (u, w) and (v, w) of a common neighbour w. The whole warp must call it.
+template <bool EID, typename F>
+__device__ __forceinline__ void warp_probe_out(const int32_t* __restrict__ nbr, const int32_t* __restrict__ osig,
+                                               const int32_t* __restrict__ eid, int32_t i2, int32_t e2,
+                                               const TriHashW& H, F&& hit) {
+    const int lane = threadIdx.x & 31;
+    int32_t w = -1, sv = 0, ev = 0;
+    if (i2 + lane < e2) {
+        w = nbr[i2 + lane];
+        sv = osig[i2 + lane];
+        if (EID) ev = eid[i2 + lane];
+    }
+    for (int32_t ib0 = i2; ib0 < e2; ib0 += 32) {
+        const int32_t ib = ib0 + lane;
+        // the next share's loads, in flight during this share's lookups
+        int32_t wn = -1, sn = 0, en = 0;
+        if (ib + 32 < e2) {
+            wn = nbr[ib + 32];
+            sn = osig[ib + 32];
+            if (EID) en = eid[ib + 32];
+        }
+        int pu = -1;
+        if (ib < e2) {
+            uint32_t h = tri_hash(w);
+            for (int p = 0; p < TRI_HSLOTS; p++) {
+                const int32_t k = H.key[h];
+                if (k == w) {
+                    pu = H.pos[h];
+                    break;
+                }
+                if (k < 0) break;
+                h = (h + 1) & (TRI_HSLOTS - 1);
+            }
+        }
+        hit(pu >= 0, w, pu >= 0 ? H.sig[pu] : 0, (EID && pu >= 0) ? H.eid[pu] : 0, sv, ev);
+        w = wn;
+        sv = sn;
+        ev = en;
+    }
 }
 
 // Also the probe slots of each oriented edge's triangles (sum over them of the three
@@ -2079,15 +2162,17 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_count(const int32_t* __rest
                                                            int32_t* __restrict__ cnt, int64_t* __restrict__ pcnt,
                                                            unsigned long long* __restrict__ merged,
                                                            unsigned long long* __restrict__ probes, int heavy_min) {
-    __shared__ TriStageW stage[TRI_THREADS / 32];
+    __shared__ TriHashW table[TRI_THREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long acc = 0, pacc = 0;
+    int32_t hashed = -1;  // the vertex whose out-list is in this warp's table
     for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); j0 < S; j0 += stride) {
         const int64_t j = j0 + lane;
-        int32_t i1 = 0, e1 = 0, i2 = 0, e2 = 0, sig_uv = 0;
+        int32_t u = 0, i1 = 0, e1 = 0, i2 = 0, e2 = 0, sig_uv = 0;
         if (j < S) {
-            const int32_t u = out_src[j], v = out_nbr[j];
+            u = out_src[j];
+            const int32_t v = out_nbr[j];
             sig_uv = osig[j];
             i1 = outptr[u];
             e1 = outptr[u + 1];
@@ -2095,7 +2180,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_count(const int32_t* __rest
             e2 = outptr[v + 1];
             acc += (unsigned long long)((e1 - i1) + (e2 - i2));
         }
-        const bool heavy = j < S && (e1 - i1) + (e2 - i2) > heavy_min && e2 - i2 <= TRI_STAGE;
+        const bool heavy = j < S && (e1 - i1) + (e2 - i2) > heavy_min && e1 - i1 <= TRI_HCAP;
         if (j < S && !heavy) {
             int32_t c = 0;
             unsigned long long ps = 0;
@@ -2120,12 +2205,16 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_count(const int32_t* __rest
             hm &= hm - 1;
             const int32_t b1 = __shfl_sync(0xffffffffu, i1, src), f1 = __shfl_sync(0xffffffffu, e1, src);
             const int32_t b2 = __shfl_sync(0xffffffffu, i2, src), f2 = __shfl_sync(0xffffffffu, e2, src);
-            const int32_t hs = __shfl_sync(0xffffffffu, sig_uv, src);
+            const int32_t hs = __shfl_sync(0xffffffffu, sig_uv, src), hu = __shfl_sync(0xffffffffu, u, src);
+            if (hu != hashed) {
+                warp_hash_out<false>(out_nbr, osig, nullptr, b1, f1, table[warp]);
+                hashed = hu;
+            }
             int32_t c = 0;
             unsigned long long hp = 0;
-            warp_intersect<false>(out_nbr, osig, nullptr, b1, f1, b2, f2, stage[warp],
-                                  [&](int32_t, int pos, int32_t, int32_t su, int32_t, int32_t sv, int32_t) {
-                                      if (pos >= 0) {
+            warp_probe_out<false>(out_nbr, osig, nullptr, b2, f2, table[warp],
+                                  [&](bool found, int32_t, int32_t su, int32_t, int32_t sv, int32_t) {
+                                      if (found) {
                                           c++;
                                           hp += (unsigned long long)(su + sv);
                                       }
@@ -2180,9 +2269,10 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
                                                            const int64_t* __restrict__ poff, int4* __restrict__ tri,
                                                            int64_t* __restrict__ tri_off, int32_t* __restrict__ common,
                                                            int heavy_min) {
-    __shared__ TriStageW stage[TRI_THREADS / 32];
+    __shared__ TriHashW table[TRI_THREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int32_t hashed = -1;  // the vertex whose out-list is in this warp's table
     for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); j0 < S; j0 += stride) {
         const int64_t j = j0 + lane;
         int32_t u = 0, v = 0, s_uv = 0, sig_uv = 0, i1 = 0, e1 = 0, i2 = 0, e2 = 0;
@@ -2196,7 +2286,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
             i2 = outptr[v];
             e2 = outptr[v + 1];
         }
-        const bool heavy = j < S && (e1 - i1) + (e2 - i2) > heavy_min && e2 - i2 <= TRI_STAGE;
+        const bool heavy = j < S && (e1 - i1) + (e2 - i2) > heavy_min && e1 - i1 <= TRI_HCAP;
         if (j < S && !heavy) {
             int64_t p = toff[j], q = poff[j];
             int32_t n_here = 0;
@@ -2231,19 +2321,23 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
             p = __shfl_sync(0xffffffffu, p, 0);
             q = __shfl_sync(0xffffffffu, q, 0);
             int n_here = 0;
-            warp_intersect<true>(
-                out_nbr, osig, out_eid, b1, f1, b2, f2, stage[warp],
-                [&](int32_t, int pos, int32_t w, int32_t su, int32_t s_uw, int32_t sv, int32_t s_vw) {
-                    const unsigned m = __ballot_sync(0xffffffffu, pos >= 0);
-                    const int64_t c = pos >= 0 ? (int64_t)hsig + su + sv : 0;
+            if (hu != hashed) {
+                warp_hash_out<true>(out_nbr, osig, out_eid, b1, f1, table[warp]);
+                hashed = hu;
+            }
+            warp_probe_out<true>(
+                out_nbr, osig, out_eid, b2, f2, table[warp],
+                [&](bool found, int32_t w, int32_t su, int32_t s_uw, int32_t sv, int32_t s_vw) {
+                    const unsigned m = __ballot_sync(0xffffffffu, found);
                     // the hits' probe offsets: a warp prefix of their costs, in lane order
+                    const int64_t c = found ? (int64_t)hsig + su + sv : 0;
                     int64_t inc = c;
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
                         const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
                         if (lane >= o) inc += y;
                     }
-                    if (pos >= 0) {
+                    if (found) {
                         const int64_t at = p + __popc(m & ((1u << lane) - 1u));
                         const int flags = (hu < hv ? 1 : 0) | (hu < w ? 2 : 0) | (hv < w ? 4 : 0);
                         tri[at] = make_int4(hs, s_uw, s_vw, flags);
@@ -2717,7 +2811,9 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
             uint16_t* sadj = sct.get<uint16_t>(2 * (int64_t)S);
             FOLTY_CUDA(cudaMemsetAsync(sblk, 0, sizeof(int32_t) * (size_t)(1 + (SOLO_CAP + 1) + SOLO_CAP), ts));
             FOLTY_CUDA(cudaMemsetAsync(map2, 0xff, sizeof(int32_t) * (size_t)tn, ts));
-            TailArgs ta{nl, L, ld, lrow, ladj, rnd, core, pa.ctl, SOLO_CAP, ns, slist, sdeg, map2};
+            int32_t* tdec = sct.get<int32_t>((int64_t)TAIL_OWN * tail_c);
+            FOLTY_CUDA(cudaMemsetAsync(tdec, 0, sizeof(int32_t) * (size_t)TAIL_OWN * (size_t)tail_c, ts));
+            TailArgs ta{nl, L, ld, lrow, ladj, rnd, core, pa.ctl, SOLO_CAP, ns, slist, sdeg, map2, tdec};
             if (tail_c == 16) launch_tail<16>(ta, ts);
             else launch_tail<8>(ta, ts);
             FOLTY_LAUNCH(k_solo_rows, grid_for(SOLO_CAP, T), T, 0, ts, pa.ctl, ns, slist, lrow, L, dl, sgid);

@@ -118,22 +118,6 @@ __device__ __forceinline__ TS first_at_least_checked(const TS* __restrict__ T, i
     return T[lower_bound_ts(T, b, e, key)];
 }
 
-// First index in [p, e) with T[i] >= key, when every entry before p is below key (p is
-// the answer for a smaller key of the same run): the last entry first (e when it is
-// below key), then steps of doubling length from p, then a binary search inside the
-// last step, so that a nearby answer costs few loads.
-template <typename TS>
-__device__ __forceinline__ int32_t gallop_at_least(const TS* __restrict__ T, int32_t p, int32_t e, TS key) {
-    if (p >= e || T[e - 1] < key) return e;
-    if (T[p] >= key) return p;
-    int32_t lo = p, step = 1;  // T[lo] < key <= T[e - 1]
-    while (lo + step < e && T[lo + step] < key) {
-        lo += step;
-        step <<= 1;
-    }
-    return lower_bound_ts(T, lo + 1, min(lo + step, e), key);
-}
-
 // x - t > delta for x >= t (no overflow)
 template <typename TS>
 __device__ __forceinline__ bool beyond(TS x, TS t, TS delta) {
