@@ -324,6 +324,8 @@ static void stage_give(int64_t* p, bool busy) {
 
 static void free_graph(folty_graph* g) {
     destroy_plans(g);
+    for (auto& e : g->live_ev)
+        if (e) cudaEventDestroy(e);
     if (g->owned) {
         for (auto& o : *g->owned) g->alloc.put(o.first, 0);
         delete g->owned;

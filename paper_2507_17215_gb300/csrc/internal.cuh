@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <mutex>
 #include <cstring>
 #include <string>
 #include <utility>
@@ -180,8 +181,8 @@ struct folty_graph {
     int32_t* seg;     // [2S + 1]: E_{a->b} = [seg[2s], seg[2s+1]), E_{b->a} = [seg[2s+1], seg[2s+2])
     int32_t* ea;      // [S] smaller endpoint a
     int32_t* eb;      // [S] larger endpoint b
-    int32_t* deg;
-    int32_t* core;  // [n] core numbers of G_S     // [n] |N(u)|
+    int32_t* deg;     // [n] |N(u)|
+    int32_t* core;    // [n] core numbers of G_S
     int32_t* common;  // [S] |N(a) cap N(b)| = triangles on the static edge
     int32_t* by_b;    // [S] static edge ids ordered by (b, a)
     int32_t* prank;   // [2S] rank of directed pair 2s + d in (u, v) order (batched queries; made on first use)
@@ -194,6 +195,12 @@ struct folty_graph {
     void* run_ends;     // [S] first and last timestamp and size of both runs of every static edge
     uint8_t* tlive;     // [3][tlive_stride] per direction variant, the smallest window bucket of a triangle's roles
     int64_t tlive_stride;
+    // a direction variant's row of tlive is written by the first call that needs it
+    // (ensure_liveness): the row is ready once live_ev[dir] (recorded on that call's
+    // stream) has completed
+    std::mutex live_mu;
+    int live_ready[3];
+    cudaEvent_t live_ev[3];
     int64_t n_tiles;
     int64_t enum_bytes; // model bytes of the triangle enumeration
     int64_t tmin, tmax; // timestamp range of the input
@@ -340,6 +347,10 @@ void tune_probe(folty_graph* g, int64_t delta, int dir, cudaStream_t s);
 // (live.cu); triangle_liveness then fills the rows from the listed triangles.
 void prepare_liveness(folty_graph* g, cudaStream_t s);
 void triangle_liveness(folty_graph* g, cudaStream_t s);
+// Makes the liveness row of direction variant dir ready for work enqueued on s after the
+// call: computes it on s the first time (thread-safe), else makes s wait for the
+// computation. Not while s is capturing.
+void ensure_liveness(folty_graph* g, int dir, cudaStream_t s);
 // Device buffers of one query's probe stage (kept triangles, probe tiles, look-back
 // control).
 struct ProbeBuffers {

@@ -45,13 +45,14 @@ __global__ void k_run_ends(const int32_t* __restrict__ seg, int64_t S, const TS*
     }
 }
 
-// The liveness bytes of every listed triangle (write_liveness), one thread per triangle:
-// consecutive triangles share their first edge, so its record mostly comes from L1.
-template <typename TS>
+// The liveness byte of every listed triangle for direction variant DIR (liveness_byte),
+// one thread per triangle: consecutive triangles share their first edge, so its record
+// mostly comes from L1.
+template <typename TS, int DIR>
 __global__ void k_tri_live(const int4* __restrict__ tri, int64_t ntri, const RunEnds<TS>* __restrict__ ends,
-                           int64_t tstride, uint8_t* __restrict__ tlive) {
+                           uint8_t* __restrict__ row) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntri; t += (int64_t)gridDim.x * blockDim.x)
-        write_liveness<TS>(__ldcs(tri + t), ends, t, tstride, tlive);
+        row[t] = liveness_byte<TS, DIR>(__ldcs(tri + t), ends);
 }
 
 __device__ __forceinline__ bool bucket_live(uint8_t b, int64_t delta) {
@@ -481,20 +482,37 @@ void prepare_liveness(folty_graph* g, cudaStream_t s) {
 }
 
 template <typename TS>
-static void triangle_liveness_t(folty_graph* g, cudaStream_t s) {
+static void liveness_row_t(folty_graph* g, int dir, cudaStream_t s) {
     const int64_t ntri = g->ntri;
-    // per triangle: its record read and three bytes written; the run-ends table (shared by
+    // per triangle: its record read and one byte written; the run-ends table (shared by
     // the triangles of an edge, and small) read once
-    StageSpan span(ST_ROLES, s, ntri * (16 + 3) + g->S * (int64_t)sizeof(RunEnds<TS>));
-    if (ntri > 0)
-        FOLTY_LAUNCH(k_tri_live<TS>, grid_for(ntri, 256), 256, 0, s, g->tri, ntri,
-                     (const RunEnds<TS>*)g->run_ends, g->tlive_stride, g->tlive);
+    StageSpan span(ST_ROLES, s, ntri * (16 + 1) + g->S * (int64_t)sizeof(RunEnds<TS>));
+    if (ntri == 0) return;
+    const RunEnds<TS>* ends = (const RunEnds<TS>*)g->run_ends;
+    uint8_t* row = g->tlive + (int64_t)dir * g->tlive_stride;
+    const unsigned grid = grid_for(ntri, 256);
+    if (dir == FOLTY_DIR_OUT) FOLTY_LAUNCH((k_tri_live<TS, FOLTY_DIR_OUT>), grid, 256, 0, s, g->tri, ntri, ends, row);
+    else if (dir == FOLTY_DIR_IN) FOLTY_LAUNCH((k_tri_live<TS, FOLTY_DIR_IN>), grid, 256, 0, s, g->tri, ntri, ends, row);
+    else FOLTY_LAUNCH((k_tri_live<TS, FOLTY_DIR_EITHER>), grid, 256, 0, s, g->tri, ntri, ends, row);
 }
 
-void triangle_liveness(folty_graph* g, cudaStream_t s) {
-    if (g->ts32) triangle_liveness_t<uint32_t>(g, s);
-    else triangle_liveness_t<int64_t>(g, s);
+// Each direction variant's liveness row is computed by the first call that needs it
+// (preprocessing computes the paper's "out" motif's): a graph queried with one variant
+// only pays for that one.
+void ensure_liveness(folty_graph* g, int dir, cudaStream_t s) {
+    std::lock_guard<std::mutex> lock(g->live_mu);
+    if (!g->live_ready[dir]) {
+        if (g->ts32) liveness_row_t<uint32_t>(g, dir, s);
+        else liveness_row_t<int64_t>(g, dir, s);
+        if (!g->live_ev[dir]) FOLTY_CUDA(cudaEventCreateWithFlags(&g->live_ev[dir], cudaEventDisableTiming));
+        FOLTY_CUDA(cudaEventRecord(g->live_ev[dir], s));
+        g->live_ready[dir] = 1;
+    } else {
+        FOLTY_CUDA(cudaStreamWaitEvent(s, g->live_ev[dir], 0));
+    }
 }
+
+void triangle_liveness(folty_graph* g, cudaStream_t s) { ensure_liveness(g, FOLTY_DIR_OUT, s); }
 
 // The probe kernel of the graph's tuned shape: tile of PB_THREADS * items slots,
 // blocks per SM as many as fit or the tuned count.
@@ -592,6 +610,7 @@ static ProbeBuffers select_live(folty_graph* g, int64_t delta, int dir, Scratch&
     const ProbeBuffers ls = make_probe_buffers(g, [&](auto* tag, int64_t n) {
         return sc.get<std::remove_pointer_t<decltype(tag)>>(n);
     });
+    ensure_liveness(g, dir, s);
     enqueue_select(g, delta, dir, ls, sc.err(), prof_sel, nullptr, s);
     return ls;
 }

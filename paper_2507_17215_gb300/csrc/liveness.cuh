@@ -121,26 +121,17 @@ __device__ __forceinline__ uint8_t frame_bucket(const FrameRuns<V>& fr, int r) {
     return dmin_bucket<V>(frame_dmin<DIR, V>(fr, r));
 }
 
-// The liveness bytes of triangle tr: per direction variant, the smallest bucket of its six
-// roles (DMIN_NEVER when none can hit at any window), written to tlive[dir * tstride + t].
-// The bit length is monotone, so the smallest bucket is the bucket of the smallest dmin.
-template <typename TS>
-__device__ __forceinline__ void write_liveness(const int4 tr, const RunEnds<TS>* __restrict__ ends, int64_t t,
-                                               int64_t tstride, uint8_t* __restrict__ tlive) {
+// The liveness byte of triangle tr for direction variant DIR: the smallest bucket of its
+// six roles (DMIN_NEVER when none can hit at any window). The bit length is monotone, so
+// the smallest bucket is the bucket of the smallest dmin.
+template <typename TS, int DIR>
+__device__ __forceinline__ uint8_t liveness_byte(const int4 tr, const RunEnds<TS>* __restrict__ ends) {
     FrameRuns<TS> fr;
     frame_runs<TS>(tr, ends, fr);
-    TS m0 = frame_dmin<FOLTY_DIR_OUT, TS>(fr, 0);
-    TS m1 = frame_dmin<FOLTY_DIR_IN, TS>(fr, 0);
-    TS m2 = frame_dmin<FOLTY_DIR_EITHER, TS>(fr, 0);
+    TS m = frame_dmin<DIR, TS>(fr, 0);
 #pragma unroll
-    for (int r = 1; r < 6; r++) {
-        m0 = min(m0, frame_dmin<FOLTY_DIR_OUT, TS>(fr, r));
-        m1 = min(m1, frame_dmin<FOLTY_DIR_IN, TS>(fr, r));
-        m2 = min(m2, frame_dmin<FOLTY_DIR_EITHER, TS>(fr, r));
-    }
-    tlive[t] = dmin_bucket<TS>(m0);
-    tlive[tstride + t] = dmin_bucket<TS>(m1);
-    tlive[2 * tstride + t] = dmin_bucket<TS>(m2);
+    for (int r = 1; r < 6; r++) m = min(m, frame_dmin<DIR, TS>(fr, r));
+    return dmin_bucket<TS>(m);
 }
 
 }  // namespace folty

@@ -2441,7 +2441,7 @@ static void temporal_store(folty_graph* g, const StoreJob& job, Scratch& sc, int
     uint32_t* tv = g->ts32 ? sc.get<uint32_t>(m) : nullptr;
     uint32_t* tv_alt = g->ts32 ? sc.get<uint32_t>(m) : nullptr;
     FOLTY_CUDA(cudaMemsetAsync(sigma, 0, sizeof(int32_t) * (size_t)S, s));
-    FOLTY_LAUNCH(k_pair_pack, grid_for(m, T), T, 0, s, job.slotw, job.order, m, job.sid, S, ib, packed, g->in_t,
+    FOLTY_LAUNCH(k_pair_pack, (unsigned)((m + T - 1) / T), T, 0, s, job.slotw, job.order, m, job.sid, S, ib, packed, g->in_t,
                  g->tmin, tv, sigma);
     FOLTY_CUDA(cudaEventRecord(packed_ev, s));
     const int cbits = bit_length((uint64_t)(2 * S));
@@ -2450,7 +2450,7 @@ static void temporal_store(folty_graph* g, const StoreJob& job, Scratch& sc, int
     const uint64_t* sp = palt ? packed_alt : packed;
     FOLTY_CUDA(cudaMemsetAsync(g->seg, 0xff, sizeof(int32_t) * (2 * (size_t)S + 1), s));
     if (g->ts32)
-        FOLTY_LAUNCH(k_pair_store4, grid_for((mk + 3) / 4, T), T, 0, s, sp, job.order, mk, S, ib,
+        FOLTY_LAUNCH(k_pair_store4, (unsigned)(((mk + 3) / 4 + T - 1) / T), T, 0, s, sp, job.order, mk, S, ib,
                      palt ? tv_alt : tv, g->perm, (uint32_t*)g->T, g->sd, g->seg);
     else
         FOLTY_LAUNCH((k_pair_store<int64_t, false>), grid_for(mk, T), T, 0, s, sp, job.order, mk, S, ib, g->in_t,
@@ -2628,7 +2628,7 @@ static void tune_triangles(folty_graph* g, const int32_t* outptr, const int32_t*
     tune_store(key, g->tune, false);
 }
 
-void preprocess_graph(folty_graph* g, cudaStream_t s) {
+static void preprocess_on(folty_graph* g, cudaStream_t s) {
     const int T = 256;
     const int64_t m = g->m;
     const int32_t n = g->n;
@@ -2659,11 +2659,12 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     const bool ids = pair_ids_sort(g, sc, order, s, &job);
     if (!ids) pair_key_sort(g, sc, order, s);
     const int32_t S = g->S;
-    // the temporal store of the dense-id path: forked to a side stream once the grid
-    // peeling kernel has finished (its grid barriers want every SM), joined after the
-    // triangle passes (which need only its per-pair counts); the later peeling phases on
-    // a second one of high priority. On an error in between, the side streams are
-    // drained before the call's buffers go.
+    // the temporal store of the dense-id path: on a side stream of default priority from
+    // here on (beside the static graph, the peel and the triangle passes, which run on
+    // this stream of the highest priority and take SMs first), joined after the triangle
+    // passes (which need only its per-pair counts); the cooperative grid peel waits for
+    // SMs that the store's short blocks free. On an error in between, the side streams
+    // are drained before the call's buffers go.
     SideStream side(s, false);
     SideStream hi(s, true);
     struct EventHolder {
@@ -2676,6 +2677,8 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     if (ids) {
         FOLTY_CUDA(cudaEventCreateWithFlags(&packed_ev.e, cudaEventDisableTiming));
         sigma = sc.get<int32_t>(S > 0 ? S : 1);
+        Scratch sc2(g->alloc, side.fork(), g->dev_err);
+        temporal_store(g, job, sc2, sigma, packed_ev.e);
     }
 
     // ---------------- A2: static CSR
@@ -2761,10 +2764,6 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
         if (n > 0) {
             FOLTY_CUDA(cudaLaunchCooperativeKernel((const void*)k_peel, grid, block, args, 0, s));
             after_launch("k_peel");
-        }
-        if (ids) {
-            Scratch sc2(g->alloc, side.fork(), g->dev_err);
-            temporal_store(g, job, sc2, sigma, packed_ev.e);
         }
         if (n > 0) {
             // the cluster and single-CTA phases: latency-bound chains of small rounds, on
@@ -2928,6 +2927,19 @@ void preprocess_graph(folty_graph* g, cudaStream_t s) {
     g->info.static_edges = S;
     g->state = 1;
     FOLTY_CUDA(cudaStreamSynchronize(s));
+}
+
+// Preprocessing runs on a stream of the device's highest priority, forked from the
+// caller's stream and joined back at the end. The temporal store runs beside the peel
+// and the triangle passes on a stream of default priority (its kernels take one block
+// per chunk of work, so their blocks retire quickly), and the chain that decides the
+// preprocessing's length takes SMs first whenever blocks retire: measured with events on
+// the paper-scale graph, the peel's set-up kernels and the orientation otherwise waited
+// behind the store's kernels for ≈ 1 ms each.
+void preprocess_graph(folty_graph* g, cudaStream_t s) {
+    SideStream pri(s, true);
+    preprocess_on(g, pri.fork());
+    pri.join();
 }
 
 }  // namespace folty

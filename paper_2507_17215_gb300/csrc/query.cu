@@ -769,6 +769,7 @@ static bool run_query_plan(folty_graph* g, const folty_query_params& q, folty_re
     if (q.want_edge_counts || q.want_certificates || q.outer || q.want_triples) return false;
     if (profiling_on() || !plans_enabled()) return false;  // stage events are recorded by the launch path
     tune_probe(g, q.delta, q.dir, s);  // the captured sequence takes the tuned probe shape
+    ensure_liveness(g, q.dir, s);      // the replay on s reads the variant's liveness row
     QueryPlans* p = plans_of(g, s);
     const cudaGraphExec_t e = plan_exec(g, p, q.dir, q.quant, q.universe);
     int64_t* hp = g->host_stage + QP_SLOT;
