@@ -188,8 +188,8 @@ struct folty_graph {
     int32_t* prank;   // [2S] rank of directed pair 2s + d in (u, v) order (batched queries; made on first use)
     int64_t ntri;
     int4* tri;        // [ntri] {s_uv, s_uw, s_vw, id-order bits}, u < v < w in degeneracy rank
-    int64_t* tri_off; // [ntri + 1] prefix of per-triangle probe counts
-    int64_t* tile_tri;  // [probe tiles + 1] triangle holding each tile's first probe
+    int64_t* tri_off; // [ntri + 1] prefix of per-triangle probe counts (null past FOLTY_NOALLOC_MAX_EDGES edges)
+    int64_t* tile_tri;  // [probe tiles + 1] triangle holding each tile's first probe (null with tri_off)
     unsigned long long* prof_bytes;  // [PROF_SLOTS] device counters of probe-stage model bytes
     int prof_next;                   // next slot
     void* run_ends;     // [S] first and last timestamp and size of both runs of every static edge
@@ -343,8 +343,10 @@ bool tune_forced(TuneParams* p, bool probe);
 // unless forced or cached (live.cu); the triangle split is picked in preprocess.cu.
 void tune_probe(folty_graph* g, int64_t delta, int dir, cudaStream_t s);
 
-// The run-ends table, and the rows of per-triangle liveness bytes with their padding
-// (live.cu); triangle_liveness then fills the rows from the listed triangles.
+// The run-ends table (live.cu; needs the sorted store), the rows of per-triangle
+// liveness bytes with their padding; triangle_liveness then fills the rows from the
+// listed triangles.
+void build_run_ends(folty_graph* g, cudaStream_t s);
 void prepare_liveness(folty_graph* g, cudaStream_t s);
 void triangle_liveness(folty_graph* g, cudaStream_t s);
 // Makes the liveness row of direction variant dir ready for work enqueued on s after the

@@ -465,10 +465,15 @@ static void run_ends_t(folty_graph* g, cudaStream_t s) {
     if (S > 0) FOLTY_LAUNCH(k_run_ends<TS>, grid_for(S, 256), 256, 0, s, g->seg, S, (const TS*)g->T, ends);
 }
 
-void prepare_liveness(folty_graph* g, cudaStream_t s) {
-    const int64_t ntri = g->ntri;
+void build_run_ends(folty_graph* g, cudaStream_t s) {
     g->run_ends = g->ts32 ? (void*)graph_alloc<RunEnds<uint32_t>>(g, g->S, s)
                           : (void*)graph_alloc<RunEnds<int64_t>>(g, g->S, s);
+    if (g->ts32) run_ends_t<uint32_t>(g, s);
+    else run_ends_t<int64_t>(g, s);
+}
+
+void prepare_liveness(folty_graph* g, cudaStream_t s) {
+    const int64_t ntri = g->ntri;
     // three rows of liveness bytes, each padded with DMIN_NEVER to whole 16-byte chunks
     // (triangle_liveness writes the first ntri bytes of each)
     g->tlive_stride = (ntri + 15) & ~int64_t(15);
@@ -477,8 +482,6 @@ void prepare_liveness(folty_graph* g, cudaStream_t s) {
         if (g->tlive_stride > ntri)
             FOLTY_CUDA(cudaMemsetAsync(g->tlive + d * g->tlive_stride + ntri, DMIN_NEVER,
                                        (size_t)(g->tlive_stride - ntri), s));
-    if (g->ts32) run_ends_t<uint32_t>(g, s);
-    else run_ends_t<int64_t>(g, s);
 }
 
 template <typename TS>

@@ -2151,8 +2151,8 @@ __device__ __forceinline__ void warp_probe_out(const int32_t* __restrict__ nbr, 
 }
 
 // Also the probe slots of each oriented edge's triangles (sum over them of the three
-// edges' temporal edge counts) into pcnt, and of all triangles into *probes, so that
-// the triangles' probe offsets are known before they are written.
+// edges' temporal edge counts) into pcnt (may be null), and of all triangles into
+// *probes, so that the triangles' probe offsets are known before they are written.
 // Like the writing pass, an edge whose two out-lists hold more than heavy_min entries is
 // intersected by the whole warp (the thread-versus-warp split the autotuner picks).
 __global__ void __launch_bounds__(TRI_THREADS) k_tri_count(const int32_t* __restrict__ outptr,
@@ -2197,7 +2197,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_count(const int32_t* __rest
             if (c) ps += (unsigned long long)c * (unsigned long long)sig_uv;
             pacc += ps;
             cnt[j] = c;
-            pcnt[j] = (int64_t)ps;
+            if (pcnt) pcnt[j] = (int64_t)ps;
         }
         unsigned hm = __ballot_sync(0xffffffffu, heavy);
         while (hm) {
@@ -2227,7 +2227,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_count(const int32_t* __rest
             if (lane == 0) {
                 hp += (unsigned long long)c * (unsigned long long)hs;
                 cnt[j0 + src] = c;
-                pcnt[j0 + src] = (int64_t)hp;
+                if (pcnt) pcnt[j0 + src] = (int64_t)hp;
                 pacc += hp;
             }
         }
@@ -2257,9 +2257,10 @@ __global__ void k_tile_starts(const int64_t* __restrict__ tri_off, int64_t ntri,
     }
 }
 
-// Writes every triangle with its probe offset (the running sum of the probe slots of the
-// triangles before it, from the counting pass's prefix per oriented edge) and counts the
-// triangles on every static edge.
+// Writes every triangle, with OFF its probe offset (the running sum of the probe slots of
+// the triangles before it, from the counting pass's prefix per oriented edge), and counts
+// the triangles on every static edge.
+template <bool OFF>
 __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __restrict__ outptr,
                                                            const int32_t* __restrict__ out_nbr,
                                                            const int32_t* __restrict__ out_eid,
@@ -2288,7 +2289,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
         }
         const bool heavy = j < S && (e1 - i1) + (e2 - i2) > heavy_min && e1 - i1 <= TRI_HCAP;
         if (j < S && !heavy) {
-            int64_t p = toff[j], q = poff[j];
+            int64_t p = toff[j], q = OFF ? poff[j] : 0;
             int32_t n_here = 0;
             int32_t a1 = i1, a2 = i2;
             while (a1 < e1 && a2 < e2) {
@@ -2297,8 +2298,10 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
                     const int32_t w = x, s_uw = out_eid[a1], s_vw = out_eid[a2];
                     const int flags = (u < v ? 1 : 0) | (u < w ? 2 : 0) | (v < w ? 4 : 0);
                     tri[p] = make_int4(s_uv, s_uw, s_vw, flags);
-                    tri_off[p] = q;
-                    q += (int64_t)sig_uv + osig[a1] + osig[a2];
+                    if (OFF) {
+                        tri_off[p] = q;
+                        q += (int64_t)sig_uv + osig[a1] + osig[a2];
+                    }
                     atomicAdd(&common[s_uw], 1);
                     atomicAdd(&common[s_vw], 1);
                     p++;
@@ -2317,7 +2320,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
             const int32_t b2 = __shfl_sync(0xffffffffu, i2, src), f2 = __shfl_sync(0xffffffffu, e2, src);
             const int32_t hu = __shfl_sync(0xffffffffu, u, src), hv = __shfl_sync(0xffffffffu, v, src);
             const int32_t hs = __shfl_sync(0xffffffffu, s_uv, src), hsig = __shfl_sync(0xffffffffu, sig_uv, src);
-            int64_t p = (lane == 0) ? toff[j0 + src] : 0, q = (lane == 0) ? poff[j0 + src] : 0;
+            int64_t p = (lane == 0) ? toff[j0 + src] : 0, q = (OFF && lane == 0) ? poff[j0 + src] : 0;
             p = __shfl_sync(0xffffffffu, p, 0);
             q = __shfl_sync(0xffffffffu, q, 0);
             int n_here = 0;
@@ -2332,21 +2335,23 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
                     // the hits' probe offsets: a warp prefix of their costs, in lane order
                     const int64_t c = found ? (int64_t)hsig + su + sv : 0;
                     int64_t inc = c;
+                    if (OFF) {
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                        if (lane >= o) inc += y;
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                            if (lane >= o) inc += y;
+                        }
                     }
                     if (found) {
                         const int64_t at = p + __popc(m & ((1u << lane) - 1u));
                         const int flags = (hu < hv ? 1 : 0) | (hu < w ? 2 : 0) | (hv < w ? 4 : 0);
                         tri[at] = make_int4(hs, s_uw, s_vw, flags);
-                        tri_off[at] = q + inc - c;
+                        if (OFF) tri_off[at] = q + inc - c;
                         atomicAdd(&common[s_uw], 1);
                         atomicAdd(&common[s_vw], 1);
                     }
                     p += __popc(m);
-                    q += __shfl_sync(0xffffffffu, inc, 31);
+                    if (OFF) q += __shfl_sync(0xffffffffu, inc, 31);
                     n_here += __popc(m);
                 });
             if (lane == 0 && n_here) atomicAdd(&common[hs], n_here);
@@ -2679,6 +2684,7 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
         sigma = sc.get<int32_t>(S > 0 ? S : 1);
         Scratch sc2(g->alloc, side.fork(), g->dev_err);
         temporal_store(g, job, sc2, sigma, packed_ev.e);
+        build_run_ends(g, sc2.stream());  // the store's own stream: ready when it is joined
     }
 
     // ---------------- A2: static CSR
@@ -2858,10 +2864,15 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
     // the counting pass merges the two out-lists of every oriented edge: 4 B per merged
     // entry (known after the read-back below) + 8 B per static edge
     StageSpan tri_span(ST_TRIANGLES, s, 8 * (int64_t)S);
-    int64_t* pcnt = sc.get<int64_t>((int64_t)S + 1);  // probe slots per oriented edge, then their prefix
+    // the all-roles probe map (each triangle's first slot in the flat space of every
+    // role's probes, and the tile starts) serves only the allocation-free per-edge counts,
+    // which take graphs of at most FOLTY_NOALLOC_MAX_EDGES edges; the queries lay out the
+    // kept roles of their own selection
+    const bool probe_map = g->m_kept <= FOLTY_NOALLOC_MAX_EDGES;
+    int64_t* pcnt = probe_map ? sc.get<int64_t>((int64_t)S + 1) : nullptr;  // slots per oriented edge, then prefix
     if (S > 0) tune_triangles(g, outptr, out_nbr, out_src, osig, tcnt, pcnt, merged, s);
     exclusive_scan(sc, tcnt, toff, S);
-    exclusive_scan(sc, pcnt, pcnt, S);
+    if (probe_map) exclusive_scan(sc, pcnt, pcnt, S);
     tri_span.end();
     FOLTY_LAUNCH(k_max_i32, grid_for(n, T), T, 0, s, g->deg, (int64_t)n, stat + 0);
     {
@@ -2887,15 +2898,20 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
     }
     const int64_t ntri = g->ntri;
     g->tri = graph_alloc<int4>(g, ntri, s);
-    g->tri_off = graph_alloc<int64_t>(g, ntri + 1, s);
+    g->tri_off = probe_map ? graph_alloc<int64_t>(g, ntri + 1, s) : nullptr;
     if (S > 0) {
         // the listing pass merges the same lists and writes 16 + 8 B per triangle
-        StageSpan span(ST_TRIANGLES, s, g->enum_bytes + 24 * ntri);
-        FOLTY_LAUNCH(k_tri_write, grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr, out_eid, out_src, osig,
-                     S, toff, pcnt, g->tri, g->tri_off, g->common, g->tune.tri_heavy);
+        StageSpan span(ST_TRIANGLES, s, g->enum_bytes + (probe_map ? 24 : 16) * ntri);
+        if (probe_map)
+            FOLTY_LAUNCH(k_tri_write<true>, grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr, out_eid,
+                         out_src, osig, S, toff, pcnt, g->tri, g->tri_off, g->common, g->tune.tri_heavy);
+        else
+            FOLTY_LAUNCH(k_tri_write<false>, grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr, out_eid,
+                         out_src, osig, S, toff, pcnt, g->tri, g->tri_off, g->common, g->tune.tri_heavy);
     }
     // the probe offsets of the triangles come from the writing pass; the last entry is the total
-    FOLTY_CUDA(cudaMemcpyAsync(g->tri_off + ntri, pcnt + S, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    if (probe_map)
+        FOLTY_CUDA(cudaMemcpyAsync(g->tri_off + ntri, pcnt + S, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     if (ids) {
         side.join();
         sort_check(g, s);  // the store's sort completed before its arrays index anything
@@ -2913,14 +2929,16 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
     g->pre_table = nullptr;
     g->pre_slotw = nullptr;
     g->pre_flags = nullptr;
-    // the run-ends table and every triangle's liveness bytes
+    // the run-ends table (built beside the triangle passes with the store) and every
+    // triangle's liveness bytes
+    if (!ids) build_run_ends(g, s);
     prepare_liveness(g, s);
     triangle_liveness(g, s);
     g->info.triangles = ntri;
-    // tile -> first triangle map of the probe kernels (query independent)
-    g->n_tiles = (g->info.probes + PB_TILE - 1) / PB_TILE;
-    g->tile_tri = graph_alloc<int64_t>(g, g->n_tiles + 1, s);
-    if (g->info.probes > 0)
+    // tile -> first triangle map of the all-roles probe kernel (query independent)
+    g->n_tiles = probe_map ? (g->info.probes + PB_TILE - 1) / PB_TILE : 0;
+    g->tile_tri = probe_map ? graph_alloc<int64_t>(g, g->n_tiles + 1, s) : nullptr;
+    if (probe_map && g->info.probes > 0)
         FOLTY_LAUNCH(k_tile_starts, grid_for(g->n_tiles + 1, T), T, 0, s, g->tri_off, ntri, g->info.probes,
                      g->n_tiles, PB_TILE, g->tile_tri);
     g->prof_bytes = graph_alloc<unsigned long long>(g, PROF_SLOTS, s);

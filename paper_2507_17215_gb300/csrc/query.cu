@@ -374,6 +374,7 @@ static void launch_probe_t(folty_graph* g, TS delta, int32_t* cnt, cudaStream_t 
 
 void launch_probe(folty_graph* g, int64_t delta, int dir, int32_t* cnt, cudaStream_t s) {
     if (g->info.probes <= 0) return;
+    if (!g->tri_off || !g->tile_tri) fail(FOLTY_EINVAL, "the all-roles probe map was not built for this graph");
     if (g->n_tiles > 0x7fffffffll) fail(FOLTY_EINVAL, "probe space too large");
     if (g->ts32) {
         // every gap is below 2^32 - 1, so larger windows behave as 2^32 - 2
