@@ -441,12 +441,26 @@ __global__ void k_load_copy(const int32_t* __restrict__ src, const int32_t* __re
             st.edge(i + 2, x.z, y.z, t23.x, t01.y, n);
             st.edge(i + 3, x.w, y.w, t23.y, t23.x, n);
             if (INSERT) {
-                uint4 w;
-                w.x = load_slot_word<INSERT>(lp, x.x, y.x, n);
-                w.y = load_slot_word<INSERT>(lp, x.y, y.y, n);
-                w.z = load_slot_word<INSERT>(lp, x.z, y.z, n);
-                w.w = load_slot_word<INSERT>(lp, x.w, y.w, n);
-                reinterpret_cast<uint4*>(lp.slotw)[j] = w;
+                // the four edges' first probes issued together (most find their pair, or
+                // an empty slot, there); the rest of a probe sequence one edge at a time
+                const int32_t xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+                uint32_t ws[4];
+                uint64_t key[4], h[4], cur[4];
+                bool ok[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    ok[e] = xs[e] >= 0 && xs[e] < n && ys[e] >= 0 && ys[e] < n && xs[e] != ys[e];
+                    key[e] = ok[e] ? pair_rank_of(xs[e], ys[e], n) + 1 : 0;
+                    h[e] = (key[e] * PAIR_HASH_MUL) >> (64 - lp.lg);
+                    cur[e] = ok[e] ? __ldcg(&lp.table[h[e]]) : 0;
+                }
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    if (!ok[e]) ws[e] = PAIR_LOOP;
+                    else if (cur[e] == key[e]) ws[e] = (uint32_t)h[e] | (xs[e] > ys[e] ? PAIR_DIR : 0u);
+                    else ws[e] = load_slot_word<INSERT>(lp, xs[e], ys[e], n);
+                }
+                reinterpret_cast<uint4*>(lp.slotw)[j] = make_uint4(ws[0], ws[1], ws[2], ws[3]);
             }
         }
     }
@@ -530,7 +544,7 @@ static void load_graph(folty_graph* g, const int32_t* src, const int32_t* dst, c
         }
     }
     if (fused && insert)
-        FOLTY_LAUNCH(k_load_copy<true>, grid_for(m / 4 + 1, 256, 4), 256, 0, s, (const int32_t*)ksrc,
+        FOLTY_LAUNCH(k_load_copy<true>, grid_for(m / 4 + 1, 256, 8), 256, 0, s, (const int32_t*)ksrc,
                      (const int32_t*)kdst, (const int64_t*)kt, m, g->n, g->in_src, g->in_dst, g->in_t, stat, lp);
     else if (fused)
         FOLTY_LAUNCH(k_load_copy<false>, grid_for(m / 4 + 1, 256, 4), 256, 0, s, (const int32_t*)ksrc,

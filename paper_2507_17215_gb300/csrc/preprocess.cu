@@ -252,6 +252,73 @@ __global__ void k_pair_pack(const uint32_t* __restrict__ slotw, const uint32_t* 
     }
 }
 
+// The same for input in time order with a 32-bit store, four edges per thread with
+// 16-byte loads and stores; of four consecutive edges of one pair (bursts keep a pair's
+// edges close in time) only the first adds to its count, by their number.
+__global__ void k_pair_pack4(const uint32_t* __restrict__ slotw, int64_t m, const int32_t* __restrict__ sid,
+                             int32_t S, int ib, uint64_t* __restrict__ packed, const int64_t* __restrict__ t,
+                             int64_t tmin, uint32_t* __restrict__ tv, int32_t* __restrict__ sigma) {
+    const int64_t nq = (m + 3) >> 2;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j0 = q << 2;
+        const bool full = j0 + 4 <= m;
+        uint32_t w[4];
+        int64_t tt[4];
+        if (full) {
+            const uint4 ww = __ldcs(reinterpret_cast<const uint4*>(slotw + j0));
+            const longlong2 a = __ldcs(reinterpret_cast<const longlong2*>(t + j0));
+            const longlong2 b = __ldcs(reinterpret_cast<const longlong2*>(t + j0 + 2));
+            w[0] = ww.x;
+            w[1] = ww.y;
+            w[2] = ww.z;
+            w[3] = ww.w;
+            tt[0] = a.x;
+            tt[1] = a.y;
+            tt[2] = b.x;
+            tt[3] = b.y;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                w[e] = j0 + e < m ? slotw[j0 + e] : PAIR_LOOP;
+                tt[e] = j0 + e < m ? t[j0 + e] : tmin;
+            }
+        }
+        int32_t p[4];
+        uint64_t c[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            p[e] = w[e] != PAIR_LOOP ? sid[w[e] & ~PAIR_DIR] : -1;
+            c[e] = (unsigned)p[e] < (unsigned)S ? 2 * (uint64_t)p[e] + (w[e] >> 31) : 2 * (uint64_t)S;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            if ((unsigned)p[e] >= (unsigned)S || (e > 0 && p[e - 1] == p[e])) continue;
+            int run = 1;
+#pragma unroll
+            for (int f = e + 1; f < 4; f++)
+                if (f == e + run && p[f] == p[e]) run++;
+            atomicAdd(&sigma[p[e]], run);
+        }
+        if (full) {
+            __stcs(reinterpret_cast<ulonglong2*>(packed + j0),
+                   make_ulonglong2((c[0] << ib) | (uint64_t)j0, (c[1] << ib) | (uint64_t)(j0 + 1)));
+            __stcs(reinterpret_cast<ulonglong2*>(packed + j0 + 2),
+                   make_ulonglong2((c[2] << ib) | (uint64_t)(j0 + 2), (c[3] << ib) | (uint64_t)(j0 + 3)));
+            __stcs(reinterpret_cast<uint4*>(tv + j0),
+                   make_uint4((uint32_t)(tt[0] - tmin), (uint32_t)(tt[1] - tmin), (uint32_t)(tt[2] - tmin),
+                              (uint32_t)(tt[3] - tmin)));
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                if (j0 + e < m) {
+                    packed[j0 + e] = (c[e] << ib) | (uint64_t)(j0 + e);
+                    tv[j0 + e] = (uint32_t)(tt[e] - tmin);
+                }
+            }
+        }
+    }
+}
+
 // The run starts of sorted position i with word pk (its predecessor's word prev, ~0 for
 // i = 0): seg[2s] = i where static edge s begins, seg[2s + 1] = i where its b -> a run
 // begins (seg is all -1 before; k_segments_fix fills the b -> a starts of edges without
@@ -2446,8 +2513,12 @@ static void temporal_store(folty_graph* g, const StoreJob& job, Scratch& sc, int
     uint32_t* tv = g->ts32 ? sc.get<uint32_t>(m) : nullptr;
     uint32_t* tv_alt = g->ts32 ? sc.get<uint32_t>(m) : nullptr;
     FOLTY_CUDA(cudaMemsetAsync(sigma, 0, sizeof(int32_t) * (size_t)S, s));
-    FOLTY_LAUNCH(k_pair_pack, (unsigned)((m + T - 1) / T), T, 0, s, job.slotw, job.order, m, job.sid, S, ib, packed, g->in_t,
-                 g->tmin, tv, sigma);
+    if (!job.order && tv)
+        FOLTY_LAUNCH(k_pair_pack4, (unsigned)(((m + 3) / 4 + T - 1) / T), T, 0, s, job.slotw, m, job.sid, S, ib, packed,
+                     g->in_t, g->tmin, tv, sigma);
+    else
+        FOLTY_LAUNCH(k_pair_pack, (unsigned)((m + T - 1) / T), T, 0, s, job.slotw, job.order, m, job.sid, S, ib,
+                     packed, g->in_t, g->tmin, tv, sigma);
     FOLTY_CUDA(cudaEventRecord(packed_ev, s));
     const int cbits = bit_length((uint64_t)(2 * S));
     const bool palt = g->ts32 ? radix_sort_pairs(sc, packed, packed_alt, tv, tv_alt, m, ib, cbits)
@@ -2679,12 +2750,11 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
         }
     } packed_ev;
     int32_t* sigma = nullptr;
+    cudaStream_t store_s = nullptr;
     if (ids) {
         FOLTY_CUDA(cudaEventCreateWithFlags(&packed_ev.e, cudaEventDisableTiming));
         sigma = sc.get<int32_t>(S > 0 ? S : 1);
-        Scratch sc2(g->alloc, side.fork(), g->dev_err);
-        temporal_store(g, job, sc2, sigma, packed_ev.e);
-        build_run_ends(g, sc2.stream());  // the store's own stream: ready when it is joined
+        store_s = side.fork();
     }
 
     // ---------------- A2: static CSR
@@ -2770,6 +2840,13 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
         if (n > 0) {
             FOLTY_CUDA(cudaLaunchCooperativeKernel((const void*)k_peel, grid, block, args, 0, s));
             after_launch("k_peel");
+        }
+        // the run-ends table at the end of the store's stream (ready when it is joined);
+        // its allocation is made here, once the static graph and the grid peel are enqueued
+        if (ids) {
+            Scratch sc2(g->alloc, store_s, g->dev_err);
+            temporal_store(g, job, sc2, sigma, packed_ev.e);
+            build_run_ends(g, store_s);
         }
         if (n > 0) {
             // the cluster and single-CTA phases: latency-bound chains of small rounds, on
