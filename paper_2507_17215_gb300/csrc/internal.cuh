@@ -266,6 +266,30 @@ bool radix_sort_pairs(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uint32_t*
 // The same for keys alone, ordered by key bits [lo, lo + bits) (lower bits ride along).
 bool radix_sort_keys(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, int64_t n, int lo, int bits);
 
+// The temporal store's sort of a time-ordered edge list: the n edges by sort id cw[j]
+// (< 2^cbits; equal ids keep input order), each carrying its time offset t[j] - tmin;
+// sorted position i < limit receives perm[i] = j, T[i] = t[j] - tmin and sd[i] = cw[j]
+// (the positions past limit hold the largest ids and are dropped). hist[p][b]: the
+// number of ids whose 8-bit digit p (bits 8p ...) is b, for the ceil(cbits / 8) passes,
+// counted by the caller. ib: bits of an input index (n <= 2^ib, ib + cbits <= 64). Like
+// radix_sort_pairs, a look-back wait that runs out sets the scratch error word.
+constexpr int STORE_DIGIT_BITS = 8;
+constexpr int STORE_MAX_PASSES = 4;
+struct StoreSortArgs {
+    const uint32_t* cw;
+    const int64_t* t;
+    int64_t tmin;
+    int64_t n;
+    int ib;
+    int cbits;
+    const uint32_t* hist;  // [STORE_MAX_PASSES][1 << STORE_DIGIT_BITS]
+    int32_t* perm;
+    uint32_t* T;
+    int32_t* sd;
+    int64_t limit;
+};
+void store_sort(Scratch& sc, const StoreSortArgs& a);
+
 int bit_length(uint64_t x);
 
 // ------------------------------------------------------------------ pipeline stages

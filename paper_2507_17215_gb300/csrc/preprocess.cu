@@ -252,71 +252,84 @@ __global__ void k_pair_pack(const uint32_t* __restrict__ slotw, const uint32_t* 
     }
 }
 
-// The same for input in time order with a 32-bit store, four edges per thread with
-// 16-byte loads and stores; of four consecutive edges of one pair (bursts keep a pair's
-// edges close in time) only the first adds to its count, by their number.
-__global__ void k_pair_pack4(const uint32_t* __restrict__ slotw, int64_t m, const int32_t* __restrict__ sid,
-                             int32_t S, int ib, uint64_t* __restrict__ packed, const int64_t* __restrict__ t,
-                             int64_t tmin, uint32_t* __restrict__ tv, int32_t* __restrict__ sigma) {
+// The first step of the store of a time-ordered input with 32-bit time offsets: each
+// edge's sort id c = 2 pair id + direction (2S for a self-loop) into cw, and the number
+// of edges of every id into cnt[0..2S] (zeroed; of consecutive edges of one id a thread
+// sees, only the first adds, by their number; the self-loops are summed per warp first).
+// Four edges per thread, 16-byte loads and stores.
+__global__ void __launch_bounds__(256) k_store_ids(const uint32_t* __restrict__ slotw, int64_t m,
+                                                   const int32_t* __restrict__ sid, int32_t S,
+                                                   uint32_t* __restrict__ cw, int32_t* __restrict__ cnt) {
     const int64_t nq = (m + 3) >> 2;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j0 = q << 2;
         const bool full = j0 + 4 <= m;
         uint32_t w[4];
-        int64_t tt[4];
         if (full) {
             const uint4 ww = __ldcs(reinterpret_cast<const uint4*>(slotw + j0));
-            const longlong2 a = __ldcs(reinterpret_cast<const longlong2*>(t + j0));
-            const longlong2 b = __ldcs(reinterpret_cast<const longlong2*>(t + j0 + 2));
             w[0] = ww.x;
             w[1] = ww.y;
             w[2] = ww.z;
             w[3] = ww.w;
-            tt[0] = a.x;
-            tt[1] = a.y;
-            tt[2] = b.x;
-            tt[3] = b.y;
         } else {
 #pragma unroll
-            for (int e = 0; e < 4; e++) {
-                w[e] = j0 + e < m ? slotw[j0 + e] : PAIR_LOOP;
-                tt[e] = j0 + e < m ? t[j0 + e] : tmin;
+            for (int e = 0; e < 4; e++) w[e] = j0 + e < m ? slotw[j0 + e] : PAIR_LOOP;
+        }
+        uint32_t c[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const int32_t p = w[e] != PAIR_LOOP ? sid[w[e] & ~PAIR_DIR] : -1;
+            c[e] = (unsigned)p < (unsigned)S ? 2 * (uint32_t)p + (w[e] >> 31) : 2 * (uint32_t)S;
+        }
+        int loops = 0;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            if (c[e] >= 2 * (uint32_t)S) {
+                loops += j0 + e < m;
+                continue;
             }
-        }
-        int32_t p[4];
-        uint64_t c[4];
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            p[e] = w[e] != PAIR_LOOP ? sid[w[e] & ~PAIR_DIR] : -1;
-            c[e] = (unsigned)p[e] < (unsigned)S ? 2 * (uint64_t)p[e] + (w[e] >> 31) : 2 * (uint64_t)S;
-        }
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            if ((unsigned)p[e] >= (unsigned)S || (e > 0 && p[e - 1] == p[e])) continue;
+            if (e > 0 && c[e - 1] == c[e]) continue;
             int run = 1;
 #pragma unroll
             for (int f = e + 1; f < 4; f++)
-                if (f == e + run && p[f] == p[e]) run++;
-            atomicAdd(&sigma[p[e]], run);
+                if (f == e + run && c[f] == c[e]) run++;
+            atomicAdd(&cnt[c[e]], run);
         }
-        if (full) {
-            __stcs(reinterpret_cast<ulonglong2*>(packed + j0),
-                   make_ulonglong2((c[0] << ib) | (uint64_t)j0, (c[1] << ib) | (uint64_t)(j0 + 1)));
-            __stcs(reinterpret_cast<ulonglong2*>(packed + j0 + 2),
-                   make_ulonglong2((c[2] << ib) | (uint64_t)(j0 + 2), (c[3] << ib) | (uint64_t)(j0 + 3)));
-            __stcs(reinterpret_cast<uint4*>(tv + j0),
-                   make_uint4((uint32_t)(tt[0] - tmin), (uint32_t)(tt[1] - tmin), (uint32_t)(tt[2] - tmin),
-                              (uint32_t)(tt[3] - tmin)));
-        } else {
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                if (j0 + e < m) {
-                    packed[j0 + e] = (c[e] << ib) | (uint64_t)(j0 + e);
-                    tv[j0 + e] = (uint32_t)(tt[e] - tmin);
-                }
-            }
-        }
+        const unsigned am = __activemask();
+        loops = __reduce_add_sync(am, loops);
+        if (loops && (threadIdx.x & 31) == __ffs(am) - 1) atomicAdd(&cnt[2 * (int64_t)S], loops);
+        if (full) __stcs(reinterpret_cast<uint4*>(cw + j0), make_uint4(c[0], c[1], c[2], c[3]));
+        else
+            for (int e = 0; e < 4 && j0 + e < m; e++) cw[j0 + e] = c[e];
     }
+}
+
+// hist[p][b] (zeroed) = number of edges whose sort id has 8-bit digit p equal to b, for
+// the sort's passes digits: from the per-id counts cnt[0..2S], one weighted addition per
+// id rather than one per edge.
+__global__ void __launch_bounds__(256) k_store_hist(const int32_t* __restrict__ cnt, int32_t S, int passes,
+                                                    uint32_t* __restrict__ hist) {
+    constexpr int B = 1 << STORE_DIGIT_BITS;
+    __shared__ uint32_t h[STORE_MAX_PASSES][B];
+    for (int i = threadIdx.x; i < STORE_MAX_PASSES * B; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t nc = 2 * (int64_t)S + 1;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = (uint32_t)cnt[c];
+        if (v == 0) continue;
+        for (int p = 0; p < passes; p++) atomicAdd(&h[p][((uint32_t)c >> (STORE_DIGIT_BITS * p)) & (B - 1)], v);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * B; i += blockDim.x) {
+        const uint32_t v = (&h[0][0])[i];
+        if (v) atomicAdd(&hist[i], v);
+    }
+}
+
+// sigma[p] = number of temporal edges of static edge p, from the runs' starts.
+__global__ void k_store_sigma(const int32_t* __restrict__ seg, int32_t S, int32_t* __restrict__ sigma) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < S; p += (int64_t)gridDim.x * blockDim.x)
+        sigma[p] = seg[2 * p + 2] - seg[2 * p];
 }
 
 // The run starts of sorted position i with word pk (its predecessor's word prev, ~0 for
@@ -2501,6 +2514,27 @@ static void temporal_store(folty_graph* g, const StoreJob& job, Scratch& sc, int
     const int32_t S = g->S;
     const int ib = job.ib;
     cudaStream_t s = sc.stream();
+    const int cbits = bit_length((uint64_t)(2 * S));
+    if (!job.order && g->ts32) {
+        // time-ordered input with 32-bit offsets: the sort ids and their counts (4 B slot
+        // word read and 4 B id written per edge), then the sort, whose first pass reads
+        // the ids and times and whose last writes perm, T and sd (24 B per edge and pass)
+        const int passes = cbits > STORE_DIGIT_BITS ? (cbits + STORE_DIGIT_BITS - 1) / STORE_DIGIT_BITS : 1;
+        StageSpan span(ST_STORE, s, 8 * m + 24 * m * passes);
+        uint32_t* cw = sc.get<uint32_t>(m);
+        int32_t* cnt = sc.get<int32_t>(2 * (int64_t)S + 1);
+        uint32_t* hist = sc.get<uint32_t>(STORE_MAX_PASSES << STORE_DIGIT_BITS);
+        FOLTY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (2 * (size_t)S + 1), s));
+        FOLTY_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (STORE_MAX_PASSES << STORE_DIGIT_BITS), s));
+        FOLTY_LAUNCH(k_store_ids, grid_for((m + 3) / 4, T), T, 0, s, job.slotw, m, job.sid, S, cw, cnt);
+        // the runs: seg[c] = first sorted position of id c, seg[2S] = mk
+        exclusive_scan(sc, cnt, g->seg, 2 * (int64_t)S);
+        FOLTY_LAUNCH(k_store_sigma, grid_for(S, T), T, 0, s, g->seg, S, sigma);
+        FOLTY_CUDA(cudaEventRecord(packed_ev, s));
+        FOLTY_LAUNCH(k_store_hist, grid_for(2 * (int64_t)S + 1, T, 2), T, 0, s, cnt, S, passes, hist);
+        store_sort(sc, StoreSortArgs{cw, g->in_t, g->tmin, m, ib, cbits, hist, g->perm, (uint32_t*)g->T, g->sd, mk});
+        return;
+    }
     // the whole store, beside the peeling: its pair words and time offsets (4 B slot and
     // 8 B time read, 12 B written per input edge) and the sorted arrays (the word and the
     // time read, perm, T and sd written: 24 B per kept edge); the sort passes inside are
@@ -2513,14 +2547,9 @@ static void temporal_store(folty_graph* g, const StoreJob& job, Scratch& sc, int
     uint32_t* tv = g->ts32 ? sc.get<uint32_t>(m) : nullptr;
     uint32_t* tv_alt = g->ts32 ? sc.get<uint32_t>(m) : nullptr;
     FOLTY_CUDA(cudaMemsetAsync(sigma, 0, sizeof(int32_t) * (size_t)S, s));
-    if (!job.order && tv)
-        FOLTY_LAUNCH(k_pair_pack4, (unsigned)(((m + 3) / 4 + T - 1) / T), T, 0, s, job.slotw, m, job.sid, S, ib, packed,
-                     g->in_t, g->tmin, tv, sigma);
-    else
-        FOLTY_LAUNCH(k_pair_pack, (unsigned)((m + T - 1) / T), T, 0, s, job.slotw, job.order, m, job.sid, S, ib,
-                     packed, g->in_t, g->tmin, tv, sigma);
+    FOLTY_LAUNCH(k_pair_pack, (unsigned)((m + T - 1) / T), T, 0, s, job.slotw, job.order, m, job.sid, S, ib, packed,
+                 g->in_t, g->tmin, tv, sigma);
     FOLTY_CUDA(cudaEventRecord(packed_ev, s));
-    const int cbits = bit_length((uint64_t)(2 * S));
     const bool palt = g->ts32 ? radix_sort_pairs(sc, packed, packed_alt, tv, tv_alt, m, ib, cbits)
                               : radix_sort_keys(sc, packed, packed_alt, m, ib, cbits);
     const uint64_t* sp = palt ? packed_alt : packed;
@@ -2841,8 +2870,9 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
             FOLTY_CUDA(cudaLaunchCooperativeKernel((const void*)k_peel, grid, block, args, 0, s));
             after_launch("k_peel");
         }
-        // the run-ends table at the end of the store's stream (ready when it is joined);
-        // its allocation is made here, once the static graph and the grid peel are enqueued
+        // the store and, at the end of its stream, the run-ends table (ready when it is
+        // joined): enqueued once the static graph and the grid peel are (enqueued first,
+        // the store's buffer allocations held up the host before the static graph's launches)
         if (ids) {
             Scratch sc2(g->alloc, store_s, g->dev_err);
             temporal_store(g, job, sc2, sigma, packed_ev.e);

@@ -186,7 +186,23 @@ struct OnesweepArgs {
     unsigned int* tile_counter;  // zeroed
     int* err;
     long long timeout_ns;
+    // the temporal store's first pass (ST_FIRST): key j = (cw[j] << ib) | j, value
+    // t[j] - tmin, read from the edge list itself (keys and vals unused)
+    const uint32_t* cw;
+    const int64_t* t;
+    int64_t tmin;
+    int ib;
+    // its last pass (ST_LAST): sorted position i < limit gets perm[i] = key mod 2^ib,
+    // T[i] = value, sd[i] = key >> ib (okeys and ovals unused; positions past limit,
+    // the self-loops' ids, are dropped)
+    int32_t* perm;
+    uint32_t* T;
+    int32_t* sd;
+    int64_t limit;
 };
+
+constexpr int ST_FIRST = 1;
+constexpr int ST_LAST = 2;
 
 // Lanes whose 8-bit digit equals this lane's, from one ballot per bit (far cheaper than
 // __match_any_sync on this GPU).
@@ -215,8 +231,11 @@ __device__ __forceinline__ unsigned digit_peers(unsigned d) {
 // NT: threads per block. The keys-only sort runs 512-thread blocks: tiles of 8192 keys
 // halve the tiles in flight, and with them the depth of every look-back, and double the
 // length of each digit's written run.
-template <bool V, int NT>
+// MODE (ST_FIRST, ST_LAST flags, key-value only): the temporal store's passes that build
+// their keys from the edge list and write the store's arrays instead of keys and values.
+template <bool V, int NT, int MODE = 0>
 __global__ void __launch_bounds__(NT, V ? 3 : (NT == 512 ? 2 : 4)) k_rs_onesweep(OnesweepArgs a) {
+    static_assert(MODE == 0 || V, "the store's passes carry values");
     constexpr int WARPS = NT / 32;
     constexpr int TILE = NT * RS_ITEMS;
     static_assert(NT % RS_BINS == 0 && NT >= RS_BINS, "one thread per digit at least");
@@ -250,8 +269,13 @@ __global__ void __launch_bounds__(NT, V ? 3 : (NT == 512 ? 2 : 4)) k_rs_onesweep
 #pragma unroll
         for (int i = 0; i < RS_ITEMS; i++) {
             const int idx = wbase + i * 32 + lane;
-            kr[i] = (idx < tn) ? kin[idx] : 0ull;
-            if (V) vr[i] = (idx < tn) ? vin[idx] : 0u;
+            if (MODE & ST_FIRST) {
+                kr[i] = (idx < tn) ? (((uint64_t)__ldcs(a.cw + t0 + idx) << a.ib) | (uint64_t)(t0 + idx)) : 0ull;
+                vr[i] = (idx < tn) ? (uint32_t)(__ldcs(a.t + t0 + idx) - a.tmin) : 0u;
+            } else {
+                kr[i] = (idx < tn) ? kin[idx] : 0ull;
+                if (V) vr[i] = (idx < tn) ? vin[idx] : 0u;
+            }
         }
 #pragma unroll
         for (int i = 0; i < RS_ITEMS; i++) {
@@ -368,8 +392,16 @@ __global__ void __launch_bounds__(NT, V ? 3 : (NT == 512 ? 2 : 4)) k_rs_onesweep
         const int src = sperm[j];
         const uint64_t kk = skey[src];
         const uint32_t pos = adj[(unsigned)(kk >> a.shift) & (RS_BINS - 1)] + (uint32_t)j;
-        a.okeys[pos] = kk;
-        if (V) a.ovals[pos] = sval[src];
+        if (MODE & ST_LAST) {
+            if ((int64_t)pos < a.limit) {
+                __stcs(a.perm + pos, (int32_t)(kk & ((1ull << a.ib) - 1)));
+                __stcs(a.T + pos, sval[src]);
+                __stcs(a.sd + pos, (int32_t)(kk >> a.ib));
+            }
+        } else {
+            a.okeys[pos] = kk;
+            if (V) a.ovals[pos] = sval[src];
+        }
     }
 }
 
@@ -434,6 +466,69 @@ bool radix_sort_pairs(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, uint32_t*
 
 bool radix_sort_keys(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, int64_t n, int lo, int bits) {
     return radix_sort_impl(sc, keys, keys_alt, nullptr, nullptr, n, lo, bits);
+}
+
+static_assert(STORE_DIGIT_BITS == RS_BITS, "the caller's digit histograms match the passes");
+
+template <int MODE>
+static void store_pass(const OnesweepArgs& oa, int64_t tiles, cudaStream_t s) {
+    FOLTY_CUDA(cudaFuncSetAttribute(k_rs_onesweep<true, RS_THREADS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)RS_DYN_SMEM));
+    FOLTY_LAUNCH((k_rs_onesweep<true, RS_THREADS, MODE>), (unsigned)tiles, RS_THREADS, RS_DYN_SMEM, s, oa);
+}
+
+// The key-value sort of radix_sort_pairs on key bits [ib, ib + cbits), whose first pass
+// forms the keys (sort id << ib | input index) and values (time offsets) from the edge
+// list, and whose last pass writes the store's three arrays: the packed words, the
+// offsets' copy and the pass that unpacks the sorted words are never made.
+void store_sort(Scratch& sc, const StoreSortArgs& a) {
+    const int64_t n = a.n;
+    if (n <= 0) return;
+    if (n >= (int64_t)0xffffffffll) fail(FOLTY_EINVAL, "store sort: too many edges");
+    const int passes = a.cbits > RS_BITS ? (a.cbits + RS_BITS - 1) / RS_BITS : 1;
+    if (passes > STORE_MAX_PASSES || a.ib + a.cbits > 64)
+        fail(FOLTY_EINVAL, "store sort: sort ids and input indices do not fit one word");
+    cudaStream_t s = sc.stream();
+    const int64_t tiles = (n + RS_TILE - 1) / RS_TILE;
+    uint32_t* base = sc.get<uint32_t>(STORE_MAX_PASSES * RS_BINS);
+    unsigned long long* lbc = sc.get<unsigned long long>(tiles * RS_BINS + 1);
+    FOLTY_LAUNCH(k_rs_bases, 1, RS_BINS, 0, s, a.hist, passes, base);
+    // the words and values between passes, ping-ponged
+    uint64_t* kb[2] = {nullptr, nullptr};
+    uint32_t* vb[2] = {nullptr, nullptr};
+    for (int i = 0; i < 2 && i < passes - 1; i++) {
+        kb[i] = sc.get<uint64_t>(n);
+        vb[i] = sc.get<uint32_t>(n);
+    }
+    for (int p = 0; p < passes; p++) {
+        StageSpan span(ST_SORT, s, 24 * n);  // 12 B read and 12 B written per edge
+        FOLTY_CUDA(cudaMemsetAsync(lbc, 0, sizeof(unsigned long long) * (size_t)(tiles * RS_BINS + 1), s));
+        OnesweepArgs oa{};
+        oa.keys = p > 0 ? kb[(p - 1) & 1] : nullptr;
+        oa.vals = p > 0 ? vb[(p - 1) & 1] : nullptr;
+        oa.okeys = kb[p & 1];
+        oa.ovals = vb[p & 1];
+        oa.n = n;
+        oa.shift = a.ib + RS_BITS * p;
+        oa.base = base + p * RS_BINS;
+        oa.lb = lbc + 1;
+        oa.tile_counter = (unsigned int*)lbc;
+        oa.err = sc.err();
+        oa.timeout_ns = LOOKBACK_TIMEOUT_NS;
+        oa.cw = a.cw;
+        oa.t = a.t;
+        oa.tmin = a.tmin;
+        oa.ib = a.ib;
+        oa.perm = a.perm;
+        oa.T = a.T;
+        oa.sd = a.sd;
+        oa.limit = a.limit;
+        const bool first = p == 0, last = p == passes - 1;
+        if (first && last) store_pass<ST_FIRST | ST_LAST>(oa, tiles, s);
+        else if (first) store_pass<ST_FIRST>(oa, tiles, s);
+        else if (last) store_pass<ST_LAST>(oa, tiles, s);
+        else store_pass<0>(oa, tiles, s);
+    }
 }
 
 }  // namespace folty
