@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <mutex>
+#include <unordered_map>
 
 #include "internal.cuh"
 #include "pairs.cuh"
@@ -129,22 +130,119 @@ static cudaMemPool_t library_pool() {
     return pools[dev];
 }
 
+// Freed blocks of the library pool, kept for the next request of the same rounded size:
+// an allocation from the pool that is not the size of a block just freed costs the host
+// about a microsecond per megabyte (measured: 0.3 ms for 280 MB, 1 to 1.4 ms for 1.8 GB,
+// with the pool's reserved memory unchanged), and the stream waits for the host meanwhile.
+// A cached block is handed out only once the event recorded at its free has completed
+// (all work before the free is done, on every stream ordered before it), so that reuse
+// adds no wait between streams; otherwise the request goes to the pool. At most a
+// quarter of the device's memory stays cached; the oldest blocks go back to the pool.
+namespace {
+struct CachedBlock {
+    void* p;
+    size_t bytes;
+    int dev;
+    cudaEvent_t ev;
+};
+std::mutex g_cache_mu;
+std::vector<CachedBlock> g_cache;                    // freed blocks, oldest first
+std::unordered_map<void*, std::pair<size_t, int>> g_live;  // pool block -> rounded size, device
+std::vector<cudaEvent_t> g_spare_events;
+size_t g_cache_bytes = 0;
+size_t g_cache_cap = 0;
+
+size_t round_block(size_t bytes) {
+    const size_t q = bytes >= (size_t(1) << 20) ? (size_t(2) << 20) : 512;
+    return (bytes + q - 1) / q * q;
+}
+}  // namespace
+
 void* Allocator::get(size_t bytes, cudaStream_t s) const {
     if (bytes == 0) bytes = 16;
     if (user) return a.alloc(bytes, (void*)s, a.ctx);
+    bytes = round_block(bytes);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_cache_mu);
+        for (size_t i = g_cache.size(); i-- > 0;) {
+            CachedBlock& c = g_cache[i];
+            if (c.dev != dev || c.bytes != bytes) continue;
+            const cudaError_t q = cudaEventQuery(c.ev);
+            if (q != cudaSuccess) {
+                if (q != cudaErrorNotReady) cudaGetLastError();
+                continue;
+            }
+            void* p = c.p;
+            g_spare_events.push_back(c.ev);
+            g_cache_bytes -= c.bytes;
+            g_cache.erase(g_cache.begin() + (long)i);
+            g_live[p] = {bytes, dev};
+            return p;
+        }
+    }
     cudaMemPool_t pool = library_pool();
     void* p = nullptr;
     if (!pool || cudaMallocFromPoolAsync(&p, bytes, pool, s) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    g_live[p] = {bytes, dev};
+    if (g_cache_cap == 0) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) cudaGetLastError();
+        g_cache_cap = total_b / 4 > 0 ? total_b / 4 : (size_t(1) << 30);
+    }
     return p;
 }
 
 void Allocator::put(void* p, cudaStream_t s) const {
     if (!p) return;
-    if (user) a.free(p, (void*)s, a.ctx);
-    else cudaFreeAsync(p, s);
+    if (user) {
+        a.free(p, (void*)s, a.ctx);
+        return;
+    }
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    auto it = g_live.find(p);
+    cudaEvent_t ev = nullptr;
+    if (!g_spare_events.empty()) {
+        ev = g_spare_events.back();
+        g_spare_events.pop_back();
+    } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        ev = nullptr;
+    }
+    if (it == g_live.end() || !ev || cudaEventRecord(ev, s) != cudaSuccess) {
+        cudaGetLastError();
+        if (ev) g_spare_events.push_back(ev);
+        if (it != g_live.end()) g_live.erase(it);
+        cudaFreeAsync(p, s);
+        return;
+    }
+    g_cache.push_back(CachedBlock{p, it->second.first, it->second.second, ev});
+    g_cache_bytes += it->second.first;
+    g_live.erase(it);
+    // over the cap: the oldest blocks of this device back to the pool, ordered after their
+    // frees (s is a stream of the current device)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
+    for (size_t i = 0; g_cache_bytes > g_cache_cap && i + 1 < g_cache.size();) {
+        CachedBlock c = g_cache[i];
+        if (c.dev != dev) {
+            i++;
+            continue;
+        }
+        g_cache.erase(g_cache.begin() + (long)i);
+        g_cache_bytes -= c.bytes;
+        if (cudaStreamWaitEvent(s, c.ev, 0) != cudaSuccess) cudaGetLastError();
+        cudaFreeAsync(c.p, s);
+        g_spare_events.push_back(c.ev);
+    }
 }
 
 void graph_release(folty_graph* g, void* p, cudaStream_t s) {
@@ -326,6 +424,7 @@ static void free_graph(folty_graph* g) {
     destroy_plans(g);
     for (auto& e : g->live_ev)
         if (e) cudaEventDestroy(e);
+    if (g->perm_ev) cudaEventDestroy(g->perm_ev);
     if (g->owned) {
         for (auto& o : *g->owned) g->alloc.put(o.first, 0);
         delete g->owned;

@@ -172,7 +172,14 @@ struct folty_graph {
     int pre_lg;
     // ---- preprocessed store (device)
     int64_t m_kept;
-    int32_t* perm;    // [m_kept] input index of each sorted temporal edge
+    int32_t* perm;    // [m_kept] input index of each sorted temporal edge (null while cw
+                      // is kept for it: ensure_perm)
+    uint32_t* cw;     // [m] sort id of each input edge (2 * static edge id + direction,
+                      // 2S for a self-loop), kept when perm is made on first use
+    uint32_t* store_hist;  // digit histograms of the sort ids (with cw)
+    int store_cbits;       // significant bits of a sort id (with cw)
+    std::mutex perm_mu;
+    cudaEvent_t perm_ev;   // recorded after perm's sort on the stream of its first use
     void* T;          // [m_kept] timestamps sorted by (static edge, direction, t): uint32
                       // offsets t - tmin when ts32, else int64
     int ts32;
@@ -268,11 +275,11 @@ bool radix_sort_keys(Scratch& sc, uint64_t* keys, uint64_t* keys_alt, int64_t n,
 
 // The temporal store's sort of a time-ordered edge list: the n edges by sort id cw[j]
 // (< 2^cbits; equal ids keep input order), each carrying its time offset t[j] - tmin;
-// sorted position i < limit receives perm[i] = j, T[i] = t[j] - tmin and sd[i] = cw[j]
-// (the positions past limit hold the largest ids and are dropped). hist[p][b]: the
-// number of ids whose 8-bit digit p (bits 8p ...) is b, for the ceil(cbits / 8) passes,
-// counted by the caller. ib: bits of an input index (n <= 2^ib, ib + cbits <= 64). Like
-// radix_sort_pairs, a look-back wait that runs out sets the scratch error word.
+// sorted position i < limit receives T[i] = t[j] - tmin and sd[i] = cw[j] (the positions
+// past limit hold the largest ids and are dropped). hist[p][b]: the number of ids whose
+// 8-bit digit p (bits 8p ...) is b, for the ceil(cbits / 8) passes, counted by the
+// caller. Like radix_sort_pairs, a look-back wait that runs out sets the scratch error
+// word. perm_sort: the same order, perm[i] = j (t, T and sd unused).
 constexpr int STORE_DIGIT_BITS = 8;
 constexpr int STORE_MAX_PASSES = 4;
 struct StoreSortArgs {
@@ -280,15 +287,15 @@ struct StoreSortArgs {
     const int64_t* t;
     int64_t tmin;
     int64_t n;
-    int ib;
     int cbits;
     const uint32_t* hist;  // [STORE_MAX_PASSES][1 << STORE_DIGIT_BITS]
-    int32_t* perm;
     uint32_t* T;
     int32_t* sd;
+    int32_t* perm;
     int64_t limit;
 };
 void store_sort(Scratch& sc, const StoreSortArgs& a);
+void perm_sort(Scratch& sc, const StoreSortArgs& a);
 
 int bit_length(uint64_t x);
 
@@ -377,6 +384,9 @@ void triangle_liveness(folty_graph* g, cudaStream_t s);
 // call: computes it on s the first time (thread-safe), else makes s wait for the
 // computation. Not while s is capturing.
 void ensure_liveness(folty_graph* g, int dir, cudaStream_t s);
+// Makes g->perm (sorted position -> input index) if the graph kept the sort ids instead,
+// on stream s, once; later calls make s wait for it.
+void ensure_perm(folty_graph* g, cudaStream_t s);
 // Device buffers of one query's probe stage (kept triangles, probe tiles, look-back
 // control).
 struct ProbeBuffers {

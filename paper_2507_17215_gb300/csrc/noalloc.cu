@@ -50,6 +50,7 @@ void edge_counts_noalloc(folty_graph* g, int64_t delta, int dir, int32_t* edge_c
     if (mk > FOLTY_NOALLOC_MAX_EDGES)
         fail(FOLTY_EINVAL, "graph has " + std::to_string(mk) + " non-loop edges; the allocation-free path holds at most " +
                                std::to_string((long long)FOLTY_NOALLOC_MAX_EDGES));
+    if (mk > 0 && !g->perm) fail(FOLTY_EINVAL, "graph has no input order of its store");  // made by preprocessing
     int32_t* cnt = noalloc_counts_on_current_device();
     if (g->m > 0) FOLTY_CUDA(cudaMemsetAsync(edge_count, 0, sizeof(int32_t) * (size_t)g->m, s));
     if (mk == 0) return;

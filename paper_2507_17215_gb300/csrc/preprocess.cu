@@ -12,6 +12,7 @@
 #include <climits>
 #include <cstdlib>
 #include <cstring>
+#include <optional>
 
 #include "internal.cuh"
 #include "pairs.cuh"
@@ -2148,6 +2149,15 @@ constexpr int TRI_THREADS = 256;
 constexpr int TRI_HEAVY = 48;
 constexpr int TRI_HCAP = 256;    // out(u) entries a warp's table holds (longer lists: one lane merges)
 constexpr int TRI_HSLOTS = 512;  // table slots (load at most one half)
+// the largest bounded layout of a one-pass listing (the scratch copy and the graph's
+// array each hold that many bytes); a larger bound takes the counting pass
+constexpr int64_t TRI_BOUND_MAX_BYTES = int64_t(16) << 30;
+
+// FOLTY_TRI_LAYOUT=counted: every graph takes the counting pass before the listing.
+inline bool tri_layout_counted() {
+    const char* env = std::getenv("FOLTY_TRI_LAYOUT");
+    return env && std::strcmp(env, "counted") == 0;
+}
 
 // One warp's hash table of out(u): neighbour id per slot (-1: empty) and its position in
 // out(u); by position, the static edge id and temporal edge count of (u, w).
@@ -2339,8 +2349,11 @@ __global__ void k_tile_starts(const int64_t* __restrict__ tri_off, int64_t ntri,
 
 // Writes every triangle, with OFF its probe offset (the running sum of the probe slots of
 // the triangles before it, from the counting pass's prefix per oriented edge), and counts
-// the triangles on every static edge.
-template <bool OFF>
+// the triangles on every static edge. The triangles of oriented edge j start at toff[j].
+// BOUND (no counting pass before it): toff[j] is the prefix of the per-edge bounds
+// min(|N+(u)|, |N+(v)|), the pass writes each edge's triangle count to cnt[j], and adds
+// the list lengths merged to merged[0] and the triangles' probe slots to merged[1].
+template <bool OFF, bool BOUND = false>
 __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __restrict__ outptr,
                                                            const int32_t* __restrict__ out_nbr,
                                                            const int32_t* __restrict__ out_eid,
@@ -2349,10 +2362,13 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
                                                            const int64_t* __restrict__ toff,
                                                            const int64_t* __restrict__ poff, int4* __restrict__ tri,
                                                            int64_t* __restrict__ tri_off, int32_t* __restrict__ common,
-                                                           int heavy_min) {
+                                                           int heavy_min, int32_t* __restrict__ cnt = nullptr,
+                                                           unsigned long long* __restrict__ merged = nullptr) {
+    static_assert(!(OFF && BOUND), "probe offsets need the counting pass");
     __shared__ TriHashW table[TRI_THREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long acc = 0, pacc = 0;  // BOUND: list lengths merged, probe slots
     int32_t hashed = -1;  // the vertex whose out-list is in this warp's table
     for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); j0 < S; j0 += stride) {
         const int64_t j = j0 + lane;
@@ -2366,11 +2382,13 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
             e1 = outptr[u + 1];
             i2 = outptr[v];
             e2 = outptr[v + 1];
+            if (BOUND) acc += (unsigned long long)((e1 - i1) + (e2 - i2));
         }
         const bool heavy = j < S && (e1 - i1) + (e2 - i2) > heavy_min && e1 - i1 <= TRI_HCAP;
         if (j < S && !heavy) {
             int64_t p = toff[j], q = OFF ? poff[j] : 0;
             int32_t n_here = 0;
+            unsigned long long ps = 0;
             int32_t a1 = i1, a2 = i2;
             while (a1 < e1 && a2 < e2) {
                 const int32_t x = out_nbr[a1], y = out_nbr[a2];
@@ -2382,6 +2400,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
                         tri_off[p] = q;
                         q += (int64_t)sig_uv + osig[a1] + osig[a2];
                     }
+                    if (BOUND) ps += (unsigned long long)(sig_uv + osig[a1] + osig[a2]);
                     atomicAdd(&common[s_uw], 1);
                     atomicAdd(&common[s_vw], 1);
                     p++;
@@ -2391,6 +2410,10 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
                 a2 += (y <= x);
             }
             if (n_here) atomicAdd(&common[s_uv], n_here);
+            if (BOUND) {
+                cnt[j] = n_here;
+                pacc += ps;
+            }
         }
         unsigned hm = __ballot_sync(0xffffffffu, heavy);
         while (hm) {
@@ -2430,11 +2453,69 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_write(const int32_t* __rest
                         atomicAdd(&common[s_uw], 1);
                         atomicAdd(&common[s_vw], 1);
                     }
+                    if (BOUND) pacc += (unsigned long long)c;
                     p += __popc(m);
                     if (OFF) q += __shfl_sync(0xffffffffu, inc, 31);
                     n_here += __popc(m);
                 });
             if (lane == 0 && n_here) atomicAdd(&common[hs], n_here);
+            if (BOUND && lane == 0) cnt[j0 + src] = n_here;
+        }
+    }
+    if (BOUND) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            pacc += __shfl_xor_sync(0xffffffffu, pacc, o);
+        }
+        if (lane == 0 && acc) atomicAdd(merged, acc);
+        if (lane == 0 && pacc) atomicAdd(merged + 1, pacc);
+    }
+}
+
+// bnd[j] = min(|N+(u)|, |N+(v)|) for oriented edge j = (u, v): at most that many common
+// out-neighbours, so an upper bound of the triangles the listing finds on j.
+__global__ void k_tri_bound(const int32_t* __restrict__ outptr, const int32_t* __restrict__ out_src,
+                            const int32_t* __restrict__ out_nbr, int32_t S, int64_t* __restrict__ bnd) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < S; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = out_src[j], v = out_nbr[j];
+        bnd[j] = min(outptr[u + 1] - outptr[u], outptr[v + 1] - outptr[v]);
+    }
+}
+
+// The bounded layout into the dense one: the cnt[j] triangles of oriented edge j move
+// from tri_b[boff[j] ...] to tri[toff[j] ...] (toff: prefix of cnt). A warp takes 32
+// consecutive edges; their triangles are contiguous in tri, so the warp's lanes stride
+// over them and find each one's edge by a binary search of the lanes' running counts.
+__global__ void k_tri_compact(const int32_t* __restrict__ cnt, const int64_t* __restrict__ toff,
+                              const int64_t* __restrict__ boff, int32_t S, const int4* __restrict__ tri_b,
+                              int4* __restrict__ tri) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) & ~31ll;
+    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); j0 < S; j0 += wstride) {
+        const int64_t j = j0 + lane;
+        const int32_t c = j < S ? cnt[j] : 0;
+        const int64_t src0 = j < S ? boff[j] : 0;
+        int32_t inc = c;  // inclusive running count over the warp's edges
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int32_t total = __shfl_sync(0xffffffffu, inc, 31);
+        if (total == 0) continue;
+        const int64_t dst0 = toff[j0];
+        for (int32_t t0 = 0; t0 < total; t0 += 32) {
+            const int32_t t = t0 + lane;
+            int e = 0;  // the first lane whose running count exceeds t
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int32_t v = __shfl_sync(0xffffffffu, inc, e + step - 1);
+                if (v <= t) e += step;
+            }
+            const int32_t before = __shfl_sync(0xffffffffu, inc - c, e);
+            const int64_t from = __shfl_sync(0xffffffffu, src0, e);
+            if (t < total) __stcs(tri + dst0 + t, __ldcs(tri_b + from + (t - before)));
         }
     }
 }
@@ -2517,13 +2598,19 @@ static void temporal_store(folty_graph* g, const StoreJob& job, Scratch& sc, int
     const int cbits = bit_length((uint64_t)(2 * S));
     if (!job.order && g->ts32) {
         // time-ordered input with 32-bit offsets: the sort ids and their counts (4 B slot
-        // word read and 4 B id written per edge), then the sort, whose first pass reads
-        // the ids and times and whose last writes perm, T and sd (24 B per edge and pass)
+        // word read and 4 B id written per edge), then the stable sort of the ids, whose
+        // first pass reads the ids and times (12 B per edge, 8 B written) and whose last
+        // writes T and sd (8 B read and written per edge, as the passes between). perm,
+        // the same order of the input indices, is sorted on first use from the ids the
+        // graph keeps, except for graphs the allocation-free entry point takes (it needs
+        // perm and may not allocate): they get it here.
         const int passes = cbits > STORE_DIGIT_BITS ? (cbits + STORE_DIGIT_BITS - 1) / STORE_DIGIT_BITS : 1;
-        StageSpan span(ST_STORE, s, 8 * m + 24 * m * passes);
-        uint32_t* cw = sc.get<uint32_t>(m);
+        StageSpan span(ST_STORE, s, 8 * m + 16 * m * passes + 4 * m);
+        const bool eager = mk <= FOLTY_NOALLOC_MAX_EDGES;
+        uint32_t* cw = eager ? sc.get<uint32_t>(m) : graph_alloc<uint32_t>(g, m, s);
         int32_t* cnt = sc.get<int32_t>(2 * (int64_t)S + 1);
-        uint32_t* hist = sc.get<uint32_t>(STORE_MAX_PASSES << STORE_DIGIT_BITS);
+        uint32_t* hist = eager ? sc.get<uint32_t>(STORE_MAX_PASSES << STORE_DIGIT_BITS)
+                               : graph_alloc<uint32_t>(g, STORE_MAX_PASSES << STORE_DIGIT_BITS, s);
         FOLTY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (2 * (size_t)S + 1), s));
         FOLTY_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (STORE_MAX_PASSES << STORE_DIGIT_BITS), s));
         FOLTY_LAUNCH(k_store_ids, grid_for((m + 3) / 4, T), T, 0, s, job.slotw, m, job.sid, S, cw, cnt);
@@ -2532,9 +2619,21 @@ static void temporal_store(folty_graph* g, const StoreJob& job, Scratch& sc, int
         FOLTY_LAUNCH(k_store_sigma, grid_for(S, T), T, 0, s, g->seg, S, sigma);
         FOLTY_CUDA(cudaEventRecord(packed_ev, s));
         FOLTY_LAUNCH(k_store_hist, grid_for(2 * (int64_t)S + 1, T, 2), T, 0, s, cnt, S, passes, hist);
-        store_sort(sc, StoreSortArgs{cw, g->in_t, g->tmin, m, ib, cbits, hist, g->perm, (uint32_t*)g->T, g->sd, mk});
+        const StoreSortArgs sa{cw, g->in_t, g->tmin, m, cbits, hist, (uint32_t*)g->T, g->sd, nullptr, mk};
+        store_sort(sc, sa);
+        if (eager) {
+            g->perm = graph_alloc<int32_t>(g, mk, s);
+            StoreSortArgs pa = sa;
+            pa.perm = g->perm;
+            perm_sort(sc, pa);
+        } else {
+            g->cw = cw;
+            g->store_hist = hist;
+            g->store_cbits = cbits;
+        }
         return;
     }
+    g->perm = graph_alloc<int32_t>(g, mk, s);
     // the whole store, beside the peeling: its pair words and time offsets (4 B slot and
     // 8 B time read, 12 B written per input edge) and the sorted arrays (the word and the
     // time read, perm, T and sd written: 24 B per kept edge); the sort passes inside are
@@ -2641,6 +2740,7 @@ static void pair_key_sort(folty_graph* g, Scratch& sc, const uint32_t* order, cu
     const int32_t n = g->n;
     const int key_bits = n > 1 ? bit_length((uint64_t)n * (uint64_t)(n - 1)) : 1;  // keys < n (n - 1)
     const uint64_t loop_key = (key_bits >= 64) ? ~0ull : ((1ull << key_bits) - 1);
+    g->perm = graph_alloc<int32_t>(g, mk, s);
     uint64_t* key = sc.get<uint64_t>(m);
     uint64_t* key_alt = sc.get<uint64_t>(m);
     uint32_t* val = sc.get<uint32_t>(m);
@@ -2695,14 +2795,16 @@ static void pair_key_sort(folty_graph* g, Scratch& sc, const uint32_t* order, cu
 // and probe slots into merged[0], merged[1], zeroed here) under the graph's split between
 // one thread and one warp per oriented edge: forced, cached under the graph's statistics,
 // or picked by timing the pass under each candidate split. All candidates count the same
-// triangles, so the last trial's outputs stand.
+// triangles, so the last trial's outputs stand. trials_only: the trials (when the split
+// is neither forced nor cached) and nothing else, for a listing without counting pass.
 static void tune_triangles(folty_graph* g, const int32_t* outptr, const int32_t* out_nbr, const int32_t* out_src,
                            const int32_t* osig, int32_t* tcnt, int64_t* pcnt, unsigned long long* merged,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool trials_only) {
     const int32_t S = g->S;
     const unsigned grid = grid_for(S, TRI_THREADS);
     const std::vector<int64_t> key{g->n, g->m_kept, S};
     bool trials = !(tune_forced(&g->tune, false) || tune_lookup(key, &g->tune, false)) && !profiling_on();
+    if (!trials && trials_only) return;
     if (!trials) {
         FOLTY_CUDA(cudaMemsetAsync(merged, 0, 2 * sizeof(unsigned long long), s));
         FOLTY_LAUNCH(k_tri_count, grid, TRI_THREADS, 0, s, outptr, out_nbr, out_src, osig, S, tcnt, pcnt, merged,
@@ -2733,6 +2835,22 @@ static void tune_triangles(folty_graph* g, const int32_t* outptr, const int32_t*
     tune_store(key, g->tune, false);
 }
 
+void ensure_perm(folty_graph* g, cudaStream_t s) {
+    std::lock_guard<std::mutex> lock(g->perm_mu);
+    if (g->perm) {
+        if (g->perm_ev) FOLTY_CUDA(cudaStreamWaitEvent(s, g->perm_ev, 0));
+        return;
+    }
+    if (!g->cw) fail(FOLTY_EINVAL, "graph has no store to order");
+    int32_t* perm = graph_alloc<int32_t>(g, g->m_kept, s);
+    Scratch sc(g->alloc, s, g->dev_err);
+    perm_sort(sc, StoreSortArgs{g->cw, nullptr, 0, g->m, g->store_cbits, g->store_hist, nullptr, nullptr, perm,
+                                g->m_kept});
+    FOLTY_CUDA(cudaEventCreateWithFlags(&g->perm_ev, cudaEventDisableTiming));
+    FOLTY_CUDA(cudaEventRecord(g->perm_ev, s));
+    g->perm = perm;
+}
+
 static void preprocess_on(folty_graph* g, cudaStream_t s) {
     const int T = 256;
     const int64_t m = g->m;
@@ -2742,7 +2860,6 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
     // ---------------- A1: canonical order
     const int nb = bit_length((uint64_t)(n > 1 ? n - 1 : 1));
     const int64_t mk = g->m_kept;
-    g->perm = graph_alloc<int32_t>(g, mk, s);
     // 32-bit offsets from tmin when the time range leaves room for the "none" marker
     g->ts32 = (g->tmax - g->tmin) < (int64_t)0xffffffffll;
     if (g->ts32) g->T = graph_alloc<uint32_t>(g, mk, s);
@@ -2968,23 +3085,48 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
     FOLTY_CUDA(cudaMemsetAsync(merged, 0, 2 * sizeof(unsigned long long), s));
     int32_t* osig = sc.get<int32_t>(S);
     if (S > 0) FOLTY_LAUNCH(k_out_sigma, grid_for(S, T), T, 0, s, sigma, g->seg, out_eid, S, osig, stat + 2);
-    // the counting pass merges the two out-lists of every oriented edge: 4 B per merged
-    // entry (known after the read-back below) + 8 B per static edge
-    StageSpan tri_span(ST_TRIANGLES, s, 8 * (int64_t)S);
+    FOLTY_LAUNCH(k_max_i32, grid_for(n, T), T, 0, s, g->deg, (int64_t)n, stat + 0);
     // the all-roles probe map (each triangle's first slot in the flat space of every
     // role's probes, and the tile starts) serves only the allocation-free per-edge counts,
     // which take graphs of at most FOLTY_NOALLOC_MAX_EDGES edges; the queries lay out the
     // kept roles of their own selection
     const bool probe_map = g->m_kept <= FOLTY_NOALLOC_MAX_EDGES;
     int64_t* pcnt = probe_map ? sc.get<int64_t>((int64_t)S + 1) : nullptr;  // slots per oriented edge, then prefix
-    if (S > 0) tune_triangles(g, outptr, out_nbr, out_src, osig, tcnt, pcnt, merged, s);
-    exclusive_scan(sc, tcnt, toff, S);
-    if (probe_map) exclusive_scan(sc, pcnt, pcnt, S);
-    tri_span.end();
-    FOLTY_LAUNCH(k_max_i32, grid_for(n, T), T, 0, s, g->deg, (int64_t)n, stat + 0);
+    // Larger graphs list their triangles in one pass into a bounded layout (the triangles
+    // of oriented edge (u, v) from the prefix of the bounds min(|N+(u)|, |N+(v)|) on)
+    // that a copy makes dense: no counting pass before the listing, and no wait for its
+    // total. The probe map needs the counting pass's slots per edge, and a bound past
+    // TRI_BOUND_MAX_BYTES takes the counting pass too.
+    bool bounded = !probe_map && S > 0 && !tri_layout_counted();
+    int64_t* boff = nullptr;
+    std::optional<StageSpan> tri_span;
+    if (bounded) {
+        boff = sc.get<int64_t>((int64_t)S + 1);
+        FOLTY_LAUNCH(k_tri_bound, grid_for(S, T), T, 0, s, outptr, out_src, out_nbr, S, boff);
+        exclusive_scan(sc, boff, boff, S);
+    }
+    // the counting pass merges the two out-lists of every oriented edge: 4 B per merged
+    // entry (known after its read-back) + 8 B per static edge
+    std::optional<StageSpan> count_span;
+    auto count_pass = [&]() {
+        count_span.emplace(ST_TRIANGLES, s, 8 * (int64_t)S);
+        FOLTY_CUDA(cudaMemsetAsync(merged, 0, 2 * sizeof(unsigned long long), s));
+        if (S > 0) tune_triangles(g, outptr, out_nbr, out_src, osig, tcnt, pcnt, merged, s, false);
+        exclusive_scan(sc, tcnt, toff, S);
+        if (probe_map) exclusive_scan(sc, pcnt, pcnt, S);
+        count_span->end();
+    };
+    auto counted = [&](int64_t total, int64_t list_len, int64_t probes) {
+        g->ntri = total;
+        g->info.probes = probes;
+        g->enum_bytes = 4 * list_len + 8 * (int64_t)S;
+        count_span->add_bytes(4 * list_len);
+    };
+    if (!bounded) count_pass();
+    int64_t bound = 0;
     {
-        const void* ptrs[9] = {toff + S, stat + 0, stat + 1, stat + 2, merged, merged + 1, peel_ctl + C_ERR,
-                               peel_ctl + C_ROUNDS, peel_ctl + C_ALPHA};
+        const void* ptrs[9] = {bounded ? (const void*)(boff + S) : (const void*)(toff + S), stat + 0, stat + 1,
+                               stat + 2, merged, merged + 1, peel_ctl + C_ERR, peel_ctl + C_ROUNDS, peel_ctl + C_ALPHA};
         int sizes[9] = {8, 4, 4, 4, 8, 8, 4, 4, 4};
         int64_t outv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         read_back(g, ptrs, sizes, peel_ctl ? 9 : 6, outv, s);  // no peeling state for n = 0
@@ -2995,32 +3137,72 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
                                   "is out of range)");
         g->info.peel_rounds = (int32_t)outv[7];
         g->info.degeneracy = (int32_t)outv[8];
-        g->info.probes = outv[5];
-        g->ntri = outv[0];
         g->info.max_degree = (int32_t)outv[1];
         g->info.max_out_degree = (int32_t)outv[2];
         g->info.sigma_max = (int32_t)outv[3];
-        g->enum_bytes = 4 * outv[4] + 8 * (int64_t)S;
-        tri_span.add_bytes(4 * outv[4]);
+        if (bounded) bound = outv[0];
+        else counted(outv[0], outv[4], outv[5]);
     }
-    const int64_t ntri = g->ntri;
-    g->tri = graph_alloc<int4>(g, ntri, s);
-    g->tri_off = probe_map ? graph_alloc<int64_t>(g, ntri + 1, s) : nullptr;
-    if (S > 0) {
-        // the listing pass merges the same lists and writes 16 + 8 B per triangle
-        StageSpan span(ST_TRIANGLES, s, g->enum_bytes + (probe_map ? 24 : 16) * ntri);
+    if (bounded && bound > TRI_BOUND_MAX_BYTES / (int64_t)sizeof(int4)) {
+        bounded = false;
+        count_pass();
+        const void* ptrs[3] = {toff + S, merged, merged + 1};
+        int sizes[3] = {8, 8, 8};
+        int64_t outv[3] = {0, 0, 0};
+        read_back(g, ptrs, sizes, 3, outv, s);
+        counted(outv[0], outv[1], outv[2]);
+    }
+    if (bounded) {
+        // the autotuner's trials (the first graph of its size only) time the counting pass
+        tune_triangles(g, outptr, out_nbr, out_src, osig, tcnt, pcnt, merged, s, true);
+        int4* tri_b = sc.get<int4>(bound);
+        // the graph's array holds bound entries, the first ntri of them the triangles: an
+        // array of ntri would wait for the listing's total (a host round trip) and for an
+        // allocation of its own while the stream stands idle
+        g->tri = graph_alloc<int4>(g, bound, s);
+        g->tri_off = nullptr;
+        FOLTY_CUDA(cudaMemsetAsync(merged, 0, 2 * sizeof(unsigned long long), s));
+        // the listing (8 B per static edge + 4 B per merged entry + 16 B per triangle) and
+        // the copy (16 B read and written per triangle): the totals come with the read-back
+        // after the store's join
+        tri_span.emplace(ST_TRIANGLES, s, 8 * (int64_t)S);
+        FOLTY_LAUNCH((k_tri_write<false, true>), grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr,
+                     out_eid, out_src, osig, S, boff, nullptr, tri_b, nullptr, g->common, g->tune.tri_heavy, tcnt,
+                     merged);
+        exclusive_scan(sc, tcnt, toff, S);
+        FOLTY_LAUNCH(k_tri_compact, grid_for(S, T), T, 0, s, tcnt, toff, boff, S, tri_b, g->tri);
+        tri_span->end();
+    } else {
+        const int64_t ntri = g->ntri;
+        g->tri = graph_alloc<int4>(g, ntri, s);
+        g->tri_off = probe_map ? graph_alloc<int64_t>(g, ntri + 1, s) : nullptr;
+        if (S > 0) {
+            // the listing pass merges the same lists and writes 16 + 8 B per triangle
+            StageSpan span(ST_TRIANGLES, s, g->enum_bytes + (probe_map ? 24 : 16) * ntri);
+            if (probe_map)
+                FOLTY_LAUNCH(k_tri_write<true>, grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr, out_eid,
+                             out_src, osig, S, toff, pcnt, g->tri, g->tri_off, g->common, g->tune.tri_heavy);
+            else
+                FOLTY_LAUNCH(k_tri_write<false>, grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr,
+                             out_eid, out_src, osig, S, toff, pcnt, g->tri, g->tri_off, g->common, g->tune.tri_heavy);
+        }
+        // the probe offsets of the triangles come from the writing pass; the last entry is the total
         if (probe_map)
-            FOLTY_LAUNCH(k_tri_write<true>, grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr, out_eid,
-                         out_src, osig, S, toff, pcnt, g->tri, g->tri_off, g->common, g->tune.tri_heavy);
-        else
-            FOLTY_LAUNCH(k_tri_write<false>, grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr, out_eid,
-                         out_src, osig, S, toff, pcnt, g->tri, g->tri_off, g->common, g->tune.tri_heavy);
+            FOLTY_CUDA(cudaMemcpyAsync(g->tri_off + ntri, pcnt + S, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     }
-    // the probe offsets of the triangles come from the writing pass; the last entry is the total
-    if (probe_map)
-        FOLTY_CUDA(cudaMemcpyAsync(g->tri_off + ntri, pcnt + S, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-    if (ids) {
-        side.join();
+    if (ids) side.join();
+    if (bounded) {
+        // the listing's totals; the same read-back checks the store's sort, which completed
+        // before its arrays index anything
+        const void* ptrs[3] = {toff + S, merged, merged + 1};
+        int sizes[3] = {8, 8, 8};
+        int64_t outv[3] = {0, 0, 0};
+        read_back(g, ptrs, sizes, 3, outv, s);
+        g->ntri = outv[0];
+        g->info.probes = outv[2];
+        g->enum_bytes = 4 * outv[1] + 8 * (int64_t)S;
+        tri_span->add_bytes(g->enum_bytes - 8 * (int64_t)S + 48 * g->ntri);
+    } else if (ids) {
         sort_check(g, s);  // the store's sort completed before its arrays index anything
     }
     // the raw input is no longer needed
@@ -3041,12 +3223,12 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
     if (!ids) build_run_ends(g, s);
     prepare_liveness(g, s);
     triangle_liveness(g, s);
-    g->info.triangles = ntri;
+    g->info.triangles = g->ntri;
     // tile -> first triangle map of the all-roles probe kernel (query independent)
     g->n_tiles = probe_map ? (g->info.probes + PB_TILE - 1) / PB_TILE : 0;
     g->tile_tri = probe_map ? graph_alloc<int64_t>(g, g->n_tiles + 1, s) : nullptr;
     if (probe_map && g->info.probes > 0)
-        FOLTY_LAUNCH(k_tile_starts, grid_for(g->n_tiles + 1, T), T, 0, s, g->tri_off, ntri, g->info.probes,
+        FOLTY_LAUNCH(k_tile_starts, grid_for(g->n_tiles + 1, T), T, 0, s, g->tri_off, g->ntri, g->info.probes,
                      g->n_tiles, PB_TILE, g->tile_tri);
     g->prof_bytes = graph_alloc<unsigned long long>(g, PROF_SLOTS, s);
     g->info.static_edges = S;

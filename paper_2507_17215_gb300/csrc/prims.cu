@@ -186,15 +186,17 @@ struct OnesweepArgs {
     unsigned int* tile_counter;  // zeroed
     int* err;
     long long timeout_ns;
-    // the temporal store's first pass (ST_FIRST): key j = (cw[j] << ib) | j, value
-    // t[j] - tmin, read from the edge list itself (keys and vals unused)
+    // 32-bit keys (the store's sorts): keys32 and okeys32 in place of keys and okeys
+    const uint32_t* keys32;
+    uint32_t* okeys32;
+    // the store's first pass (ST_FIRST): key j = cw[j], value t[j] - tmin (ST_IOTA: j),
+    // read from the edge list itself (keys and vals unused)
     const uint32_t* cw;
     const int64_t* t;
     int64_t tmin;
-    int ib;
-    // its last pass (ST_LAST): sorted position i < limit gets perm[i] = key mod 2^ib,
-    // T[i] = value, sd[i] = key >> ib (okeys and ovals unused; positions past limit,
-    // the self-loops' ids, are dropped)
+    // its last pass (ST_LAST): sorted position i < limit gets T[i] = value and sd[i] =
+    // key (ST_IOTA: perm[i] = value); okeys and ovals are unused, and the positions past
+    // limit (the self-loops' ids) are dropped
     int32_t* perm;
     uint32_t* T;
     int32_t* sd;
@@ -203,6 +205,7 @@ struct OnesweepArgs {
 
 constexpr int ST_FIRST = 1;
 constexpr int ST_LAST = 2;
+constexpr int ST_IOTA = 4;
 
 // Lanes whose 8-bit digit equals this lane's, from one ballot per bit (far cheaper than
 // __match_any_sync on this GPU).
@@ -231,16 +234,20 @@ __device__ __forceinline__ unsigned digit_peers(unsigned d) {
 // NT: threads per block. The keys-only sort runs 512-thread blocks: tiles of 8192 keys
 // halve the tiles in flight, and with them the depth of every look-back, and double the
 // length of each digit's written run.
-// MODE (ST_FIRST, ST_LAST flags, key-value only): the temporal store's passes that build
-// their keys from the edge list and write the store's arrays instead of keys and values.
-template <bool V, int NT, int MODE = 0>
-__global__ void __launch_bounds__(NT, V ? 3 : (NT == 512 ? 2 : 4)) k_rs_onesweep(OnesweepArgs a) {
-    static_assert(MODE == 0 || V, "the store's passes carry values");
+// K: the key type; 32-bit keys (the store's sorts, key-value only) move 8 bytes a key.
+// MODE (ST_FIRST, ST_LAST, ST_IOTA flags, 32-bit keys only): the store's passes that
+// build their keys from the edge list and write the store's arrays instead of keys and
+// values.
+template <bool V, int NT, int MODE = 0, typename K = uint64_t>
+__global__ void __launch_bounds__(NT, V ? (sizeof(K) == 4 ? 4 : 3) : (NT == 512 ? 2 : 4))
+    k_rs_onesweep(OnesweepArgs a) {
+    static_assert(sizeof(K) == 8 || V, "32-bit keys carry values");
+    static_assert(MODE == 0 || sizeof(K) == 4, "the store's passes sort 32-bit ids");
     constexpr int WARPS = NT / 32;
     constexpr int TILE = NT * RS_ITEMS;
     static_assert(NT % RS_BINS == 0 && NT >= RS_BINS, "one thread per digit at least");
     extern __shared__ __align__(16) unsigned char rs_smem[];
-    uint64_t* skey = (uint64_t*)rs_smem;                    // TILE, load order
+    K* skey = (K*)rs_smem;                                  // TILE, load order
     uint32_t* sval = (uint32_t*)(skey + TILE);              // TILE, load order (V only)
     uint16_t* sperm = (uint16_t*)(V ? (void*)(sval + TILE) : (void*)sval);  // TILE, digit order -> load order
     __shared__ uint16_t wh[WARPS][RS_BINS];                 // per-warp counts, then offsets
@@ -258,22 +265,24 @@ __global__ void __launch_bounds__(NT, V ? 3 : (NT == 512 ? 2 : 4)) k_rs_onesweep
     const int64_t tile = s_tile;
     const int64_t t0 = tile * TILE;
     const int tn = (int)min((int64_t)TILE, a.n - t0);
-    const uint64_t* kin = a.keys + t0;
+    const K* kin = (sizeof(K) == 8 ? (const K*)a.keys : (const K*)a.keys32) + t0;
+    K* kout = sizeof(K) == 8 ? (K*)a.okeys : (K*)a.okeys32;
     const uint32_t* vin = a.vals + t0;
     const int wbase = warp * 32 * RS_ITEMS;
     // ---- 1. loads, staging, digits
     uint32_t info[RS_ITEMS];  // digit | rank within (warp, digit) << 8
     {
-        uint64_t kr[RS_ITEMS];
+        K kr[RS_ITEMS];
         uint32_t vr[RS_ITEMS];
 #pragma unroll
         for (int i = 0; i < RS_ITEMS; i++) {
             const int idx = wbase + i * 32 + lane;
             if (MODE & ST_FIRST) {
-                kr[i] = (idx < tn) ? (((uint64_t)__ldcs(a.cw + t0 + idx) << a.ib) | (uint64_t)(t0 + idx)) : 0ull;
-                vr[i] = (idx < tn) ? (uint32_t)(__ldcs(a.t + t0 + idx) - a.tmin) : 0u;
+                kr[i] = (idx < tn) ? (K)__ldcs(a.cw + t0 + idx) : (K)0;
+                if (MODE & ST_IOTA) vr[i] = (uint32_t)(t0 + idx);
+                else vr[i] = (idx < tn) ? (uint32_t)(__ldcs(a.t + t0 + idx) - a.tmin) : 0u;
             } else {
-                kr[i] = (idx < tn) ? kin[idx] : 0ull;
+                kr[i] = (idx < tn) ? kin[idx] : (K)0;
                 if (V) vr[i] = (idx < tn) ? vin[idx] : 0u;
             }
         }
@@ -390,16 +399,19 @@ __global__ void __launch_bounds__(NT, V ? 3 : (NT == 512 ? 2 : 4)) k_rs_onesweep
     __syncthreads();
     for (int j = threadIdx.x; j < tn; j += NT) {
         const int src = sperm[j];
-        const uint64_t kk = skey[src];
+        const K kk = skey[src];
         const uint32_t pos = adj[(unsigned)(kk >> a.shift) & (RS_BINS - 1)] + (uint32_t)j;
         if (MODE & ST_LAST) {
             if ((int64_t)pos < a.limit) {
-                __stcs(a.perm + pos, (int32_t)(kk & ((1ull << a.ib) - 1)));
-                __stcs(a.T + pos, sval[src]);
-                __stcs(a.sd + pos, (int32_t)(kk >> a.ib));
+                if (MODE & ST_IOTA) {
+                    __stcs(a.perm + pos, (int32_t)sval[src]);
+                } else {
+                    __stcs(a.T + pos, sval[src]);
+                    __stcs(a.sd + pos, (int32_t)kk);
+                }
             }
         } else {
-            a.okeys[pos] = kk;
+            kout[pos] = kk;
             if (V) a.ovals[pos] = sval[src];
         }
     }
@@ -472,44 +484,47 @@ static_assert(STORE_DIGIT_BITS == RS_BITS, "the caller's digit histograms match 
 
 template <int MODE>
 static void store_pass(const OnesweepArgs& oa, int64_t tiles, cudaStream_t s) {
-    FOLTY_CUDA(cudaFuncSetAttribute(k_rs_onesweep<true, RS_THREADS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)RS_DYN_SMEM));
-    FOLTY_LAUNCH((k_rs_onesweep<true, RS_THREADS, MODE>), (unsigned)tiles, RS_THREADS, RS_DYN_SMEM, s, oa);
+    constexpr size_t smem = RS_TILE * (sizeof(uint32_t) + sizeof(uint32_t) + sizeof(uint16_t));
+    FOLTY_CUDA(cudaFuncSetAttribute(k_rs_onesweep<true, RS_THREADS, MODE, uint32_t>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FOLTY_LAUNCH((k_rs_onesweep<true, RS_THREADS, MODE, uint32_t>), (unsigned)tiles, RS_THREADS, smem, s, oa);
 }
 
-// The key-value sort of radix_sort_pairs on key bits [ib, ib + cbits), whose first pass
-// forms the keys (sort id << ib | input index) and values (time offsets) from the edge
-// list, and whose last pass writes the store's three arrays: the packed words, the
-// offsets' copy and the pass that unpacks the sorted words are never made.
-void store_sort(Scratch& sc, const StoreSortArgs& a) {
+// The key-value sort of 32-bit sort ids (radix_sort_pairs' passes on 32-bit keys) whose
+// first pass reads the ids and values from the edge list and whose last writes the
+// store's arrays: no packed words, and no pass that unpacks the sorted ones.
+template <bool IOTA>
+static void store_sort_impl(Scratch& sc, const StoreSortArgs& a) {
     const int64_t n = a.n;
     if (n <= 0) return;
     if (n >= (int64_t)0xffffffffll) fail(FOLTY_EINVAL, "store sort: too many edges");
     const int passes = a.cbits > RS_BITS ? (a.cbits + RS_BITS - 1) / RS_BITS : 1;
-    if (passes > STORE_MAX_PASSES || a.ib + a.cbits > 64)
-        fail(FOLTY_EINVAL, "store sort: sort ids and input indices do not fit one word");
+    if (passes > STORE_MAX_PASSES) fail(FOLTY_EINVAL, "store sort: sort ids past 32 bits");
     cudaStream_t s = sc.stream();
     const int64_t tiles = (n + RS_TILE - 1) / RS_TILE;
     uint32_t* base = sc.get<uint32_t>(STORE_MAX_PASSES * RS_BINS);
     unsigned long long* lbc = sc.get<unsigned long long>(tiles * RS_BINS + 1);
     FOLTY_LAUNCH(k_rs_bases, 1, RS_BINS, 0, s, a.hist, passes, base);
-    // the words and values between passes, ping-ponged
-    uint64_t* kb[2] = {nullptr, nullptr};
+    // the ids and values between passes, ping-ponged
+    uint32_t* kb[2] = {nullptr, nullptr};
     uint32_t* vb[2] = {nullptr, nullptr};
     for (int i = 0; i < 2 && i < passes - 1; i++) {
-        kb[i] = sc.get<uint64_t>(n);
+        kb[i] = sc.get<uint32_t>(n);
         vb[i] = sc.get<uint32_t>(n);
     }
+    constexpr int F = ST_FIRST | (IOTA ? ST_IOTA : 0), L = ST_LAST | (IOTA ? ST_IOTA : 0);
     for (int p = 0; p < passes; p++) {
-        StageSpan span(ST_SORT, s, 24 * n);  // 12 B read and 12 B written per edge
+        // 8 B read and written per edge (the first pass reads a 4 B id and an 8 B time, or
+        // the id alone; the last writes two 4 B entries, or one)
+        StageSpan span(ST_SORT, s, 16 * n);
         FOLTY_CUDA(cudaMemsetAsync(lbc, 0, sizeof(unsigned long long) * (size_t)(tiles * RS_BINS + 1), s));
         OnesweepArgs oa{};
-        oa.keys = p > 0 ? kb[(p - 1) & 1] : nullptr;
+        oa.keys32 = p > 0 ? kb[(p - 1) & 1] : nullptr;
         oa.vals = p > 0 ? vb[(p - 1) & 1] : nullptr;
-        oa.okeys = kb[p & 1];
+        oa.okeys32 = kb[p & 1];
         oa.ovals = vb[p & 1];
         oa.n = n;
-        oa.shift = a.ib + RS_BITS * p;
+        oa.shift = RS_BITS * p;
         oa.base = base + p * RS_BINS;
         oa.lb = lbc + 1;
         oa.tile_counter = (unsigned int*)lbc;
@@ -518,17 +533,19 @@ void store_sort(Scratch& sc, const StoreSortArgs& a) {
         oa.cw = a.cw;
         oa.t = a.t;
         oa.tmin = a.tmin;
-        oa.ib = a.ib;
         oa.perm = a.perm;
         oa.T = a.T;
         oa.sd = a.sd;
         oa.limit = a.limit;
         const bool first = p == 0, last = p == passes - 1;
-        if (first && last) store_pass<ST_FIRST | ST_LAST>(oa, tiles, s);
-        else if (first) store_pass<ST_FIRST>(oa, tiles, s);
-        else if (last) store_pass<ST_LAST>(oa, tiles, s);
+        if (first && last) store_pass<F | L>(oa, tiles, s);
+        else if (first) store_pass<F>(oa, tiles, s);
+        else if (last) store_pass<L>(oa, tiles, s);
         else store_pass<0>(oa, tiles, s);
     }
 }
+
+void store_sort(Scratch& sc, const StoreSortArgs& a) { store_sort_impl<false>(sc, a); }
+void perm_sort(Scratch& sc, const StoreSortArgs& a) { store_sort_impl<true>(sc, a); }
 
 }  // namespace folty

@@ -442,9 +442,10 @@ static void pairs_device(folty_graph* g, const folty_query_params& q, const Coun
     FOLTY_CUDA(cudaMemsetAsync(p.n_cert, 0, sizeof(unsigned long long), s));
     if (p.cert_flag) FOLTY_CUDA(cudaMemsetAsync(p.cert_flag, 0, sizeof(int32_t) * (size_t)(g->m + 1), s));
     if (mk > 0) {
+        if (p.cert_flag) ensure_perm(g, s);  // certificates are listed by input index
         ThresholdArgs a{cnt.c32, g->sd, mk, g->ea, g->eb, g->deg, g->common, (int)q.quant, (int)q.universe,
                         (int64_t)q.rho_num, (int64_t)q.rho_den, p.seg_max, p.seg_ncert, p.n_cert,
-                        g->perm, p.cert_flag, cnt.c16, qp};
+                        p.cert_flag ? g->perm : nullptr, p.cert_flag, cnt.c16, qp};
         StageSpan span(ST_THRESHOLD, s, 8 * mk);  // pair key + count per edge
         launch_threshold(a, grid_for((mk + TH_BATCH - 1) / TH_BATCH, TH_THREADS), s);
     }
@@ -532,6 +533,7 @@ void finish_queries(folty_graph* g, const folty_query_params* const* qs, const C
                 copies = true;
             }
             if (q.want_edge_counts && g->m > 0) {
+                if (mk > 0) ensure_perm(g, s);
                 int32_t* ec = sc.get<int32_t>(g->m);
                 FOLTY_CUDA(cudaMemsetAsync(ec, 0, sizeof(int32_t) * (size_t)g->m, s));
                 if (mk > 0 && cnts[g0 + i].c16)

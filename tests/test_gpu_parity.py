@@ -674,6 +674,28 @@ def test_pair_table_past_its_first_size(F):
         _assert_same(b, a, what=str(q))
 
 
+
+def test_triangle_layouts_agree(F, monkeypatch):
+    """Past the allocation-free entry point's size limit the listing runs once, into a
+    layout bounded per oriented edge by min(|N+(u)|, |N+(v)|), and a copy makes it dense;
+    FOLTY_TRI_LAYOUT=counted forces the counting pass before it. Both layouts give the
+    same triangle statistics and query results (the first matches the oracle in
+    test_pair_table_past_its_first_size), the all-existential triples included."""
+    g = _many_pairs_graph()
+    qs = [W.Query(d, 1, 2, W.Q_FORALL_T, dr, W.U_HEAD, True) for d in (50, 2000) for dr in (W.DIR_OUT, W.DIR_EITHER)]
+    qs.append(W.Query(500, 1, 2, W.Q_FORALL_T, W.DIR_OUT, W.U_HEAD, False, want_triples=True))
+    want, info = _lib_results(F, g, qs)
+    assert info["static_edges"] > (1 << 20) and info["triangles"] > 10 ** 5
+    monkeypatch.setenv("FOLTY_TRI_LAYOUT", "counted")
+    got, cinfo = _lib_results(F, g, qs)
+    # the bounded layout's array holds the bound's entries: more device memory
+    assert cinfo.pop("device_bytes") < info.pop("device_bytes")
+    assert cinfo == info
+    for q, a, b in zip(qs, want, got):
+        _assert_same(b, a, what=str(q))
+    np.testing.assert_array_equal(got[-1]["triples"], want[-1]["triples"])
+    assert len(want[-1]["triples"]) > 0
+
 def _clique_graph(k=20000, size=4, seed=6):
     """k disjoint cliques of `size` vertices, one temporal edge per ordered pair, times
     within 20 s: every ordered pair of a clique has witnesses, so a query has up to
