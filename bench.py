@@ -67,11 +67,11 @@ STAGE_KERNELS = {
     "sort": "radix sort spans: k_rs_hist_all + k_rs_bases (all digit histograms), or one k_rs_onesweep digit pass",
     "peel": "k_peel (cooperative) + k_tail_* + k_peel_tail + k_solo_* + k_peel_solo",
     "threshold": "k_threshold",
-    "triangles": "k_tri_count, k_tri_write",
-    "roles": "k_run_ends + k_tri_live",
+    "triangles": "k_tri_bound + k_tri_write (one pass into the bounded layout; k_tri_count first on small graphs)",
+    "roles": "k_run_ends + k_tri_live_copy (liveness bytes while the triangles move to the dense layout)",
     "batch": "k_batch_threshold",
-    "store": "temporal store beside the peel: k_pair_pack, its keys-only sort, k_offsets32, k_pair_store, "
-             "k_segments_* (contains sort spans)",
+    "store": "temporal store beside the peel: k_store_ids, k_store_hist, the id sort's k_rs_onesweep passes "
+             "(contains sort spans)",
 }
 STAGE_SOURCES = {"probe": ("live.cu", "probe.cuh"), "select": ("live.cu", "scan.cuh"), "sort": ("prims.cu",),
                  "peel": ("preprocess.cu",), "threshold": ("query.cu",), "triangles": ("preprocess.cu",),

@@ -375,11 +375,18 @@ bool tune_forced(TuneParams* p, bool probe);
 void tune_probe(folty_graph* g, int64_t delta, int dir, cudaStream_t s);
 
 // The run-ends table (live.cu; needs the sorted store), the rows of per-triangle
-// liveness bytes with their padding; triangle_liveness then fills the rows from the
-// listed triangles.
+// liveness bytes with their padding; triangle_liveness then fills the out motif's row
+// from the listed triangles. With from, the triangles still lie in the bounded layout
+// of a one-pass listing, and the same pass moves them into g->tri.
+struct TriLayout {
+    const int32_t* cnt;   // [S] triangles of each oriented edge
+    const int64_t* toff;  // [S + 1] prefix of cnt
+    const int64_t* boff;  // [S + 1] prefix of the per-edge bounds: edge j's triangles at tri_b[boff[j] ...]
+    const int4* tri_b;
+};
 void build_run_ends(folty_graph* g, cudaStream_t s);
 void prepare_liveness(folty_graph* g, cudaStream_t s);
-void triangle_liveness(folty_graph* g, cudaStream_t s);
+void triangle_liveness(folty_graph* g, cudaStream_t s, const TriLayout* from = nullptr);
 // Makes the liveness row of direction variant dir ready for work enqueued on s after the
 // call: computes it on s the first time (thread-safe), else makes s wait for the
 // computation. Not while s is capturing.

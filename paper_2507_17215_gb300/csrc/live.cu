@@ -55,6 +55,60 @@ __global__ void k_tri_live(const int4* __restrict__ tri, int64_t ntri, const Run
         row[t] = liveness_byte<TS, DIR>(__ldcs(tri + t), ends);
 }
 
+// The same while the triangles move from the bounded layout of a one-pass listing into
+// the dense one: the cnt[j] triangles of oriented edge j from tri_b[boff[j] ...] to
+// tri[toff[j] ...] (toff: prefix of cnt). A warp takes 32 consecutive edges, whose
+// triangles are contiguous in tri; its lanes stride over them, two triangles a lane per
+// step (both loads in flight before either is used), and find each one's edge by a
+// binary search of the lanes' running counts. One warp per 32 edges and short blocks:
+// the dense communities' edges hold far more triangles than the rest.
+template <typename TS, int DIR>
+__global__ void k_tri_live_copy(const int32_t* __restrict__ cnt, const int64_t* __restrict__ toff,
+                                const int64_t* __restrict__ boff, int32_t S, const int4* __restrict__ tri_b,
+                                int4* __restrict__ tri, const RunEnds<TS>* __restrict__ ends,
+                                uint8_t* __restrict__ row) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) & ~31ll;
+    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); j0 < S; j0 += wstride) {
+        const int64_t j = j0 + lane;
+        const int32_t c = j < S ? cnt[j] : 0;
+        const int64_t src0 = j < S ? boff[j] : 0;
+        int32_t inc = c;  // inclusive running count over the warp's edges
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int32_t total = __shfl_sync(0xffffffffu, inc, 31);
+        if (total == 0) continue;
+        const int64_t dst0 = toff[j0];
+        for (int32_t t0 = 0; t0 < total; t0 += 64) {
+            int4 tr[2];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int32_t t = t0 + 32 * h + lane;
+                int e = 0;  // the first lane whose running count exceeds t
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int32_t v = __shfl_sync(0xffffffffu, inc, e + step - 1);
+                    if (v <= t) e += step;
+                }
+                const int32_t before = __shfl_sync(0xffffffffu, inc - c, e);
+                const int64_t from = __shfl_sync(0xffffffffu, src0, e);
+                tr[h] = t < total ? __ldcs(tri_b + from + (t - before)) : make_int4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int32_t t = t0 + 32 * h + lane;
+                if (t < total) {
+                    tri[dst0 + t] = tr[h];
+                    row[dst0 + t] = liveness_byte<TS, DIR>(tr[h], ends);
+                }
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ bool bucket_live(uint8_t b, int64_t delta) {
     return b != DMIN_NEVER && (b == 0 || delta >= ((int64_t)1 << (b - 1)));
 }
@@ -515,7 +569,30 @@ void ensure_liveness(folty_graph* g, int dir, cudaStream_t s) {
     }
 }
 
-void triangle_liveness(folty_graph* g, cudaStream_t s) { ensure_liveness(g, FOLTY_DIR_OUT, s); }
+template <typename TS>
+static void liveness_copy_t(folty_graph* g, const TriLayout& from, cudaStream_t s) {
+    const int64_t ntri = g->ntri;
+    // per triangle: its record read in the bounded layout and written in the dense one,
+    // and one byte written; the per-edge counts, offsets and run ends read once
+    StageSpan span(ST_ROLES, s, ntri * (16 + 16 + 1) + g->S * (int64_t)(4 + 8 + 8 + sizeof(RunEnds<TS>)));
+    if (ntri == 0) return;
+    FOLTY_LAUNCH((k_tri_live_copy<TS, FOLTY_DIR_OUT>), (unsigned)((g->S + 255) / 256), 256, 0, s, from.cnt, from.toff,
+                 from.boff, g->S, from.tri_b, g->tri, (const RunEnds<TS>*)g->run_ends,
+                 g->tlive + (int64_t)FOLTY_DIR_OUT * g->tlive_stride);
+}
+
+void triangle_liveness(folty_graph* g, cudaStream_t s, const TriLayout* from) {
+    if (!from) {
+        ensure_liveness(g, FOLTY_DIR_OUT, s);
+        return;
+    }
+    std::lock_guard<std::mutex> lock(g->live_mu);
+    if (g->ts32) liveness_copy_t<uint32_t>(g, *from, s);
+    else liveness_copy_t<int64_t>(g, *from, s);
+    if (!g->live_ev[FOLTY_DIR_OUT]) FOLTY_CUDA(cudaEventCreateWithFlags(&g->live_ev[FOLTY_DIR_OUT], cudaEventDisableTiming));
+    FOLTY_CUDA(cudaEventRecord(g->live_ev[FOLTY_DIR_OUT], s));
+    g->live_ready[FOLTY_DIR_OUT] = 1;
+}
 
 // The probe kernel of the graph's tuned shape: tile of PB_THREADS * items slots,
 // blocks per SM as many as fit or the tuned count.

@@ -2483,43 +2483,6 @@ __global__ void k_tri_bound(const int32_t* __restrict__ outptr, const int32_t* _
     }
 }
 
-// The bounded layout into the dense one: the cnt[j] triangles of oriented edge j move
-// from tri_b[boff[j] ...] to tri[toff[j] ...] (toff: prefix of cnt). A warp takes 32
-// consecutive edges; their triangles are contiguous in tri, so the warp's lanes stride
-// over them and find each one's edge by a binary search of the lanes' running counts.
-__global__ void k_tri_compact(const int32_t* __restrict__ cnt, const int64_t* __restrict__ toff,
-                              const int64_t* __restrict__ boff, int32_t S, const int4* __restrict__ tri_b,
-                              int4* __restrict__ tri) {
-    const int lane = threadIdx.x & 31;
-    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) & ~31ll;
-    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); j0 < S; j0 += wstride) {
-        const int64_t j = j0 + lane;
-        const int32_t c = j < S ? cnt[j] : 0;
-        const int64_t src0 = j < S ? boff[j] : 0;
-        int32_t inc = c;  // inclusive running count over the warp's edges
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        const int32_t total = __shfl_sync(0xffffffffu, inc, 31);
-        if (total == 0) continue;
-        const int64_t dst0 = toff[j0];
-        for (int32_t t0 = 0; t0 < total; t0 += 32) {
-            const int32_t t = t0 + lane;
-            int e = 0;  // the first lane whose running count exceeds t
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int32_t v = __shfl_sync(0xffffffffu, inc, e + step - 1);
-                if (v <= t) e += step;
-            }
-            const int32_t before = __shfl_sync(0xffffffffu, inc - c, e);
-            const int64_t from = __shfl_sync(0xffffffffu, src0, e);
-            if (t < total) __stcs(tri + dst0 + t, __ldcs(tri_b + from + (t - before)));
-        }
-    }
-}
-
 // ================================================================== driver
 
 // A non-blocking stream of this thread (of the device's highest or default priority)
@@ -2613,7 +2576,9 @@ static void temporal_store(folty_graph* g, const StoreJob& job, Scratch& sc, int
                                : graph_alloc<uint32_t>(g, STORE_MAX_PASSES << STORE_DIGIT_BITS, s);
         FOLTY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (2 * (size_t)S + 1), s));
         FOLTY_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (STORE_MAX_PASSES << STORE_DIGIT_BITS), s));
-        FOLTY_LAUNCH(k_store_ids, grid_for((m + 3) / 4, T), T, 0, s, job.slotw, m, job.sid, S, cw, cnt);
+        // one block per 1024 edges: short blocks, so that the peel's kernels on the
+        // high-priority streams get SMs as soon as any block ends
+        FOLTY_LAUNCH(k_store_ids, (unsigned)(((m + 3) / 4 + T - 1) / T), T, 0, s, job.slotw, m, job.sid, S, cw, cnt);
         // the runs: seg[c] = first sorted position of id c, seg[2S] = mk
         exclusive_scan(sc, cnt, g->seg, 2 * (int64_t)S);
         FOLTY_LAUNCH(k_store_sigma, grid_for(S, T), T, 0, s, g->seg, S, sigma);
@@ -2882,11 +2847,10 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
     if (!ids) pair_key_sort(g, sc, order, s);
     const int32_t S = g->S;
     // the temporal store of the dense-id path: on a side stream of default priority from
-    // here on (beside the static graph, the peel and the triangle passes, which run on
-    // this stream of the highest priority and take SMs first), joined after the triangle
-    // passes (which need only its per-pair counts); the cooperative grid peel waits for
-    // SMs that the store's short blocks free. On an error in between, the side streams
-    // are drained before the call's buffers go.
+    // the end of the grid peel on (beside the rest of the peel and the triangle passes,
+    // which run on streams of the highest priority and take SMs first), joined after the
+    // triangle passes (which need only its per-pair counts). On an error in between, the
+    // side streams are drained before the call's buffers go.
     SideStream side(s, false);
     SideStream hi(s, true);
     struct EventHolder {
@@ -2900,7 +2864,6 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
     if (ids) {
         FOLTY_CUDA(cudaEventCreateWithFlags(&packed_ev.e, cudaEventDisableTiming));
         sigma = sc.get<int32_t>(S > 0 ? S : 1);
-        store_s = side.fork();
     }
 
     // ---------------- A2: static CSR
@@ -2988,9 +2951,11 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
             after_launch("k_peel");
         }
         // the store and, at the end of its stream, the run-ends table (ready when it is
-        // joined): enqueued once the static graph and the grid peel are (enqueued first,
-        // the store's buffer allocations held up the host before the static graph's launches)
+        // joined), after the grid peel: the cooperative peel waits for SMs that the store's
+        // blocks hold (it took 0.8 ms instead of 0.3 beside the store's first pass), and
+        // the store still ends before the triangle listing
         if (ids) {
+            store_s = side.fork();
             Scratch sc2(g->alloc, store_s, g->dev_err);
             temporal_store(g, job, sc2, sigma, packed_ev.e);
             build_run_ends(g, store_s);
@@ -3100,6 +3065,8 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
     bool bounded = !probe_map && S > 0 && !tri_layout_counted();
     int64_t* boff = nullptr;
     std::optional<StageSpan> tri_span;
+    int4* tri_b = nullptr;  // the bounded layout, moved into g->tri by the liveness pass
+    TriLayout layout{};
     if (bounded) {
         boff = sc.get<int64_t>((int64_t)S + 1);
         FOLTY_LAUNCH(k_tri_bound, grid_for(S, T), T, 0, s, outptr, out_src, out_nbr, S, boff);
@@ -3155,23 +3122,25 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
     if (bounded) {
         // the autotuner's trials (the first graph of its size only) time the counting pass
         tune_triangles(g, outptr, out_nbr, out_src, osig, tcnt, pcnt, merged, s, true);
-        int4* tri_b = sc.get<int4>(bound);
-        // the graph's array holds bound entries, the first ntri of them the triangles: an
-        // array of ntri would wait for the listing's total (a host round trip) and for an
-        // allocation of its own while the stream stands idle
+        tri_b = sc.get<int4>(bound);
+        // the graph's array holds bound entries, the first ntri of them the triangles
+        // (moved there by the liveness pass): an array of ntri would wait for the
+        // listing's total, a host round trip
         g->tri = graph_alloc<int4>(g, bound, s);
         g->tri_off = nullptr;
         FOLTY_CUDA(cudaMemsetAsync(merged, 0, 2 * sizeof(unsigned long long), s));
-        // the listing (8 B per static edge + 4 B per merged entry + 16 B per triangle) and
-        // the copy (16 B read and written per triangle): the totals come with the read-back
-        // after the store's join
+        // the listing (8 B per static edge + 4 B per merged entry + 16 B per triangle):
+        // the totals come with the read-back after the store's join
         tri_span.emplace(ST_TRIANGLES, s, 8 * (int64_t)S);
-        FOLTY_LAUNCH((k_tri_write<false, true>), grid_for(S, TRI_THREADS), TRI_THREADS, 0, s, outptr, out_nbr,
+        // one warp per 32 oriented edges, in short blocks: the dense communities' edges
+        // take far longer than the rest
+        FOLTY_LAUNCH((k_tri_write<false, true>), (unsigned)((S + TRI_THREADS - 1) / TRI_THREADS), TRI_THREADS, 0, s,
+                     outptr, out_nbr,
                      out_eid, out_src, osig, S, boff, nullptr, tri_b, nullptr, g->common, g->tune.tri_heavy, tcnt,
                      merged);
         exclusive_scan(sc, tcnt, toff, S);
-        FOLTY_LAUNCH(k_tri_compact, grid_for(S, T), T, 0, s, tcnt, toff, boff, S, tri_b, g->tri);
         tri_span->end();
+        layout = TriLayout{tcnt, toff, boff, tri_b};
     } else {
         const int64_t ntri = g->ntri;
         g->tri = graph_alloc<int4>(g, ntri, s);
@@ -3201,7 +3170,7 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
         g->ntri = outv[0];
         g->info.probes = outv[2];
         g->enum_bytes = 4 * outv[1] + 8 * (int64_t)S;
-        tri_span->add_bytes(g->enum_bytes - 8 * (int64_t)S + 48 * g->ntri);
+        tri_span->add_bytes(g->enum_bytes - 8 * (int64_t)S + 16 * g->ntri);
     } else if (ids) {
         sort_check(g, s);  // the store's sort completed before its arrays index anything
     }
@@ -3222,7 +3191,7 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
     // triangle's liveness bytes
     if (!ids) build_run_ends(g, s);
     prepare_liveness(g, s);
-    triangle_liveness(g, s);
+    triangle_liveness(g, s, bounded ? &layout : nullptr);
     g->info.triangles = g->ntri;
     // tile -> first triangle map of the all-roles probe kernel (query independent)
     g->n_tiles = probe_map ? (g->info.probes + PB_TILE - 1) / PB_TILE : 0;
