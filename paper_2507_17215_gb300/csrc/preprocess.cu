@@ -257,34 +257,41 @@ __global__ void k_pair_pack(const uint32_t* __restrict__ slotw, const uint32_t* 
 // edge's sort id c = 2 pair id + direction (2S for a self-loop) into cw, and the number
 // of edges of every id into cnt[0..2S] (zeroed; of consecutive edges of one id a thread
 // sees, only the first adds, by their number; the self-loops are summed per warp first).
-// Four edges per thread, 16-byte loads and stores.
+// Eight edges per thread (their id lookups in flight together), 16-byte loads and stores.
+constexpr int STORE_IDS_EDGES = 8;  // consecutive edges per thread of k_store_ids
 __global__ void __launch_bounds__(256) k_store_ids(const uint32_t* __restrict__ slotw, int64_t m,
                                                    const int32_t* __restrict__ sid, int32_t S,
                                                    uint32_t* __restrict__ cw, int32_t* __restrict__ cnt) {
-    const int64_t nq = (m + 3) >> 2;
+    constexpr int E = STORE_IDS_EDGES;
+    const int64_t nq = (m + E - 1) / E;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j0 = q << 2;
-        const bool full = j0 + 4 <= m;
-        uint32_t w[4];
+        const int64_t j0 = q * E;
+        const bool full = j0 + E <= m;
+        uint32_t w[E];
         if (full) {
-            const uint4 ww = __ldcs(reinterpret_cast<const uint4*>(slotw + j0));
-            w[0] = ww.x;
-            w[1] = ww.y;
-            w[2] = ww.z;
-            w[3] = ww.w;
+#pragma unroll
+            for (int h = 0; h < E / 4; h++) {
+                const uint4 ww = __ldcs(reinterpret_cast<const uint4*>(slotw + j0) + h);
+                w[4 * h] = ww.x;
+                w[4 * h + 1] = ww.y;
+                w[4 * h + 2] = ww.z;
+                w[4 * h + 3] = ww.w;
+            }
         } else {
 #pragma unroll
-            for (int e = 0; e < 4; e++) w[e] = j0 + e < m ? slotw[j0 + e] : PAIR_LOOP;
+            for (int e = 0; e < E; e++) w[e] = j0 + e < m ? slotw[j0 + e] : PAIR_LOOP;
         }
-        uint32_t c[4];
+        // all the id lookups in flight before any is used
+        int32_t p[E];
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
-            const int32_t p = w[e] != PAIR_LOOP ? sid[w[e] & ~PAIR_DIR] : -1;
-            c[e] = (unsigned)p < (unsigned)S ? 2 * (uint32_t)p + (w[e] >> 31) : 2 * (uint32_t)S;
-        }
+        for (int e = 0; e < E; e++) p[e] = w[e] != PAIR_LOOP ? sid[w[e] & ~PAIR_DIR] : -1;
+        uint32_t c[E];
+#pragma unroll
+        for (int e = 0; e < E; e++)
+            c[e] = (unsigned)p[e] < (unsigned)S ? 2 * (uint32_t)p[e] + (w[e] >> 31) : 2 * (uint32_t)S;
         int loops = 0;
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
+        for (int e = 0; e < E; e++) {
             if (c[e] >= 2 * (uint32_t)S) {
                 loops += j0 + e < m;
                 continue;
@@ -292,16 +299,20 @@ __global__ void __launch_bounds__(256) k_store_ids(const uint32_t* __restrict__ 
             if (e > 0 && c[e - 1] == c[e]) continue;
             int run = 1;
 #pragma unroll
-            for (int f = e + 1; f < 4; f++)
+            for (int f = e + 1; f < E; f++)
                 if (f == e + run && c[f] == c[e]) run++;
             atomicAdd(&cnt[c[e]], run);
         }
         const unsigned am = __activemask();
         loops = __reduce_add_sync(am, loops);
         if (loops && (threadIdx.x & 31) == __ffs(am) - 1) atomicAdd(&cnt[2 * (int64_t)S], loops);
-        if (full) __stcs(reinterpret_cast<uint4*>(cw + j0), make_uint4(c[0], c[1], c[2], c[3]));
-        else
-            for (int e = 0; e < 4 && j0 + e < m; e++) cw[j0 + e] = c[e];
+        if (full) {
+#pragma unroll
+            for (int h = 0; h < E / 4; h++)
+                __stcs(reinterpret_cast<uint4*>(cw + j0) + h, make_uint4(c[4 * h], c[4 * h + 1], c[4 * h + 2], c[4 * h + 3]));
+        } else {
+            for (int e = 0; e < E && j0 + e < m; e++) cw[j0 + e] = c[e];
+        }
     }
 }
 
@@ -2576,9 +2587,10 @@ static void temporal_store(folty_graph* g, const StoreJob& job, Scratch& sc, int
                                : graph_alloc<uint32_t>(g, STORE_MAX_PASSES << STORE_DIGIT_BITS, s);
         FOLTY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (2 * (size_t)S + 1), s));
         FOLTY_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (STORE_MAX_PASSES << STORE_DIGIT_BITS), s));
-        // one block per 1024 edges: short blocks, so that the peel's kernels on the
+        // one block per 2048 edges: short blocks, so that the peel's kernels on the
         // high-priority streams get SMs as soon as any block ends
-        FOLTY_LAUNCH(k_store_ids, (unsigned)(((m + 3) / 4 + T - 1) / T), T, 0, s, job.slotw, m, job.sid, S, cw, cnt);
+        FOLTY_LAUNCH(k_store_ids, (unsigned)(((m + STORE_IDS_EDGES - 1) / STORE_IDS_EDGES + T - 1) / T), T, 0, s,
+                     job.slotw, m, job.sid, S, cw, cnt);
         // the runs: seg[c] = first sorted position of id c, seg[2S] = mk
         exclusive_scan(sc, cnt, g->seg, 2 * (int64_t)S);
         FOLTY_LAUNCH(k_store_sigma, grid_for(S, T), T, 0, s, g->seg, S, sigma);
