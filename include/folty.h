@@ -225,25 +225,32 @@ uint64_t folty_kernel_launches(void);
  *             per staged triangle 61 B, per kept role w sigma1 + w min(sigma2, sigma1
  *             ceil(log2(sigma2 + 1))) + the same for L3 + 8 sigma1 (w = bytes per stored
  *             timestamp), counted on the device;
- *   SORT      one radix pass: 8 B read for the histogram, 12 B read + 12 B written per key;
+ *   SORT      one radix pass: 8 B read for the histogram, 12 B read + 12 B written per key
+ *             (8 B + 8 B for the temporal store's 32-bit sort ids with their values);
  *   PEEL      the degeneracy peeling: 12 B per adjacency entry + 16 B per vertex;
  *   THRESHOLD certificate test and per-pair reduction: 8 B per temporal edge (4 with 16-bit
  *             counters) + 20 B per directed pair;
  *   SELECT    the per-query selection of the triangles whose liveness byte admits the
  *             window (k_live_select): 1 B read per triangle; per kept triangle its record
  *             and its edges' run ends read and 13 B written, counted on the device;
- *   TRIANGLES triangle count and listing passes: 4 B per merged out-list entry + 8 B per
- *             static edge, per pass; 24 B written per triangle;
+ *   TRIANGLES triangle listing: 4 B per merged out-list entry + 8 B per static edge and
+ *             16 B written per triangle (graphs past FOLTY_NOALLOC_MAX_EDGES edges: one
+ *             pass into a layout bounded per oriented edge); graphs up to that size also
+ *             count first (the same merge bytes again) and write 8 B more per triangle;
  *   ROLES     the run-ends table (12 B of run bounds + 4 timestamps read, one record
- *             written per static edge) and the liveness pass (16 B read and 3 B written
- *             per triangle, the run-ends table read once);
+ *             written per static edge) and the liveness pass of one direction variant (16 B
+ *             read and 1 B written per triangle, the run-ends table read once; after a
+ *             one-pass listing, preprocessing's pass also moves each triangle into the
+ *             dense layout: 16 B more written per triangle, and the per-edge counts and
+ *             offsets read);
  *   BATCH     the batched threshold over the plain queries of a direction variant: the
  *             32-edge group bits, and (counted on the device) the bin row and 4 B of pair
  *             key of every edge in a group with a hit;
- *   STORE     the temporal store built beside the peeling (pair words, their sort, the
- *             gather into the sorted arrays, the run bounds): its span contains SORT spans;
- *             8 B per input edge for the pair words and 28 B per kept edge for the gather
- *             and the run bounds (the sort's bytes are in SORT).
+ *   STORE     the temporal store built beside the peeling: its span contains SORT spans.
+ *             Time-ordered input with 32-bit offsets: 8 B per input edge for the sort ids
+ *             and 16 B per edge and radix pass (the first pass reads 4 B more: the ids and
+ *             the input times); other inputs: 24 B per input edge for the pair words and
+ *             24 B per kept edge for the sorted arrays and run starts.
  * Totals are process-wide; profile one thread at a time. */
 enum { FOLTY_STAGE_PROBE = 0, FOLTY_STAGE_SORT = 1, FOLTY_STAGE_PEEL = 2, FOLTY_STAGE_THRESHOLD = 3,
        FOLTY_STAGE_SELECT = 4, FOLTY_STAGE_TRIANGLES = 5, FOLTY_STAGE_ROLES = 6, FOLTY_STAGE_BATCH = 7,

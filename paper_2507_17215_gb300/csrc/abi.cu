@@ -137,7 +137,8 @@ static cudaMemPool_t library_pool() {
 // A cached block is handed out only once the event recorded at its free has completed
 // (all work before the free is done, on every stream ordered before it), so that reuse
 // adds no wait between streams; otherwise the request goes to the pool. At most a
-// quarter of the device's memory stays cached; the oldest blocks go back to the pool.
+// quarter of the device's memory stays cached; the oldest blocks go back to the pool,
+// and all of a device's cached blocks do when the pool cannot serve a request.
 namespace {
 struct CachedBlock {
     void* p;
@@ -187,9 +188,30 @@ void* Allocator::get(size_t bytes, cudaStream_t s) const {
     }
     cudaMemPool_t pool = library_pool();
     void* p = nullptr;
-    if (!pool || cudaMallocFromPoolAsync(&p, bytes, pool, s) != cudaSuccess) {
+    if (!pool) return nullptr;
+    if (cudaMallocFromPoolAsync(&p, bytes, pool, s) != cudaSuccess) {
         cudaGetLastError();
-        return nullptr;
+        // the pool is out of memory: the cached blocks of this device go back to it first
+        // (ordered after their frees on s, where the retry allocates), then one more try
+        {
+            std::lock_guard<std::mutex> lock(g_cache_mu);
+            for (size_t i = 0; i < g_cache.size();) {
+                CachedBlock c = g_cache[i];
+                if (c.dev != dev) {
+                    i++;
+                    continue;
+                }
+                g_cache.erase(g_cache.begin() + (long)i);
+                g_cache_bytes -= c.bytes;
+                if (cudaStreamWaitEvent(s, c.ev, 0) != cudaSuccess) cudaGetLastError();
+                cudaFreeAsync(c.p, s);
+                g_spare_events.push_back(c.ev);
+            }
+        }
+        if (cudaMallocFromPoolAsync(&p, bytes, pool, s) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
     }
     std::lock_guard<std::mutex> lock(g_cache_mu);
     g_live[p] = {bytes, dev};
