@@ -3050,8 +3050,8 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
                      out_eid, out_src);
 
     // ---------------- A5: triangles
-    // the two triangle passes need the static graph and every static edge's temporal edge
-    // count, not the store itself: they run beside the store's sort (joined before the
+    // the triangle listing needs the static graph and every static edge's temporal edge
+    // count, not the store itself: it runs beside the store's sort (joined before the
     // run-ends table)
     if (ids) FOLTY_CUDA(cudaStreamWaitEvent(s, packed_ev.e, 0));
     g->common = graph_alloc<int32_t>(g, S, s);
@@ -3071,9 +3071,10 @@ static void preprocess_on(folty_graph* g, cudaStream_t s) {
     int64_t* pcnt = probe_map ? sc.get<int64_t>((int64_t)S + 1) : nullptr;  // slots per oriented edge, then prefix
     // Larger graphs list their triangles in one pass into a bounded layout (the triangles
     // of oriented edge (u, v) from the prefix of the bounds min(|N+(u)|, |N+(v)|) on)
-    // that a copy makes dense: no counting pass before the listing, and no wait for its
-    // total. The probe map needs the counting pass's slots per edge, and a bound past
-    // TRI_BOUND_MAX_BYTES takes the counting pass too.
+    // that the liveness pass makes dense while it computes the out motif's bytes: no
+    // counting pass before the listing, and no wait for its total. The probe map needs
+    // the counting pass's slots per edge, and a bound past TRI_BOUND_MAX_BYTES takes the
+    // counting pass too.
     bool bounded = !probe_map && S > 0 && !tri_layout_counted();
     int64_t* boff = nullptr;
     std::optional<StageSpan> tri_span;
